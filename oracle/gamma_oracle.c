@@ -43,7 +43,7 @@
  *   - Global mode: dD = dd_frac * D_norm, D_norm = dose_norm if > 0 else
  *     max(D_r).  Local mode: dD(v) = dd_frac * D_r(v).
  *   - A reference voxel is evaluated iff D_r(v) >= cutoff_frac * D_norm (and,
- *     in local mode, D_r(v) > 0).  Others get NaN.
+ *     in local mode, D_r(v) > 0), compared in float32.  Others get NaN.
  *   - Simplices with a vertex outside the grid do not exist (no
  *     extrapolation).  Every axis of the problem needs >= 2 voxels.
  */
@@ -267,9 +267,14 @@ static double or_delta_dose(const or_ctx *c, double dr)
     return c->local ? c->dd_frac * dr : c->dd_frac * c->d_norm;
 }
 
+/* The evaluated / not-evaluated decision is an integer outcome of floating
+ * point; it is taken in single precision, threshold = float(cutoff_frac) *
+ * float(D_norm) rounded to float, so that every implementation fed the same
+ * float32 doses and criteria decides it identically. */
 static int or_evaluated(const or_ctx *c, double dr)
 {
-    if (!(dr >= c->cutoff_frac * c->d_norm)) return 0;
+    const float thr = (float)c->cutoff_frac * (float)c->d_norm;
+    if (!((float)dr >= thr)) return 0;
     if (c->local && !(dr > 0)) return 0;
     return 1;
 }
