@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Gamma-index throughput benchmark (3D gamma voxels/s at 3%/3 mm).
+
+A step is one full gamma map of the 160x160x120, 2.5 mm synthetic IMRT pair
+(7 coplanar beams; evaluation = 1.03 * D(x - 1.5 mm) + smooth noise) at
+3 %/3 mm global with a 10 % cutoff: every launch of the hot path (dose norm,
+key-0 cells, cost ordering, table walk).  `value` is grid voxels per second,
+device-timed with CUDA events on the launching stream, inputs resident in HBM,
+L2 flushed between steps.  `e2e` times the same metric through the C ABI on
+pinned host buffers, host<->device copies included.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the problem has no exchange step); value = all ranks' voxels / max time.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "3D gamma voxels/s at 3%/3mm"
+UNIT = "voxels/s"
+WORKLOAD = "imrt_160"
+WORKLOAD_DESC = ("synthetic IMRT pair 160x160x120 at 2.5 mm (7 coplanar beams, 10x10 beamlets, "
+                 "3 mm penumbra); eval = 1.03*D(x-1.5mm) + smooth noise (sigma 10 mm, sd 0.01); "
+                 "3%/3mm global, 10% cutoff")
+# Algorithmic FP32 work per cell of the face formulation (FMA = 2 FLOP); the
+# count is derived in the design doc from cell_min_d2 (26 faces in 3D, 6 in 2D).
+FLOP_PER_CELL = {3: 651, 2: 115}
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+KERNELS_PER_RUN = 5          # prepare, shell, bucket scan, scatter, tail
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per queued voxel (0: library default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic work: cells with key < gamma* per voxel (implementation independent)
+# --------------------------------------------------------------------------
+
+def cell_census(gamma, spacing, dta: float):
+    """Cells the exact search must certify: for every evaluated voxel, the cells
+    (lower corner p = v + c inside the grid) whose box distance / dta is below
+    gamma*.  gamma: the gamma map as a torch tensor (NaN = not evaluated).
+    Returns (key-0 cells, other cells) summed over voxels.  A measurement
+    helper: it only counts, from the finished map."""
+    import torch
+    nd = gamma.dim()
+    shape = tuple(gamma.shape)
+    hn = np.array(spacing[::-1], dtype=np.float64) / dta          # x, y[, z]
+    g = torch.nan_to_num(gamma.double(), nan=-1.0)
+    gmax = float(g.max())
+    if gmax <= 0:
+        return 0, 0
+    lim = [int(math.ceil(gmax / h)) + 1 for h in hn]
+    rng = [np.arange(-l - 1, l + 1) for l in lim]
+    offs = np.stack(np.meshgrid(*rng, indexing="ij"), -1).reshape(-1, nd)   # x, y[, z]
+    gap = np.maximum(np.maximum(offs, -offs - 1), 0) * hn
+    keys = np.sqrt((gap ** 2).sum(-1))
+    keep = keys < gmax
+    offs, keys = offs[keep], keys[keep]
+    dims = shape[::-1]                                   # n_x, n_y[, n_z]
+    ar = [torch.arange(n, device=g.device) for n in dims]
+    shell = tail = 0
+    for off, key in zip(offs, keys):
+        masks = [((a + int(o)) >= 0) & ((a + int(o)) <= n - 1) for a, o, n in zip(ar, off, dims)]
+        if nd == 3:
+            inside = masks[2][:, None, None] & masks[1][None, :, None] & masks[0][None, None, :]
+        else:
+            inside = masks[1][:, None] & masks[0][None, :]
+        cnt = int(torch.count_nonzero(inside & (g > float(key))))
+        if key == 0.0:
+            shell += cnt
+        else:
+            tail += cnt
+    return shell, tail
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+
+def time_oracle(pair, target_s: float, seed: int = 0):
+    """Time the FP64 oracle on a uniform random sample of grid voxels sized to
+    about target_s seconds; returns (voxels/s, sample size, seconds, threads)."""
+    import oracle
+    c = pair.criteria
+    f32 = lambda x: float(np.float32(x))
+    rng = np.random.default_rng(seed)
+    probe = rng.choice(pair.nvox, min(pair.nvox, 50000), replace=False)
+    t0 = time.perf_counter()
+    oracle.gamma(pair.ref, pair.eval, pair.spacing, f32(c.dd_frac), f32(c.dta_mm), local=c.local,
+                 cutoff_frac=f32(c.cutoff_frac), dose_norm=f32(c.dose_norm), idx=probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(pair.nvox, max(probe.size, probe.size * target_s / dt)))
+    idx = None if n >= pair.nvox else rng.choice(pair.nvox, n, replace=False)
+    t0 = time.perf_counter()
+    oracle.gamma(pair.ref, pair.eval, pair.spacing, f32(c.dd_frac), f32(c.dta_mm), local=c.local,
+                 cutoff_frac=f32(c.cutoff_frac), dose_norm=f32(c.dose_norm), idx=idx)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, oracle.max_threads()
+
+
+def run_reference(args, pair, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    per_step_s = 4.0
+    for _ in range(args.warmup):
+        time_oracle(pair, per_step_s / 4)
+    times, voxels = [], []
+    threads = 0
+    for k in range(args.steps):
+        rate, n, dt, threads = time_oracle(pair, per_step_s, seed=k + 1)
+        times.append(dt)
+        voxels.append(n)
+    value = sum(voxels) / sum(times)
+    sample = (f"uniform random sample of {voxels[0]} of {pair.nvox} grid voxels per step "
+              f"(full grid)" if voxels[0] >= pair.nvox else
+              f"uniform random sample of ~{int(statistics.mean(voxels))} of {pair.nvox} grid voxels per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "name": args.workload},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def run_ours(args, pair, rank, world, local_rank):
+    import torch
+    import paper_1012_1900_gb300 as g
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    c = pair.criteria
+    crit = g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)
+    ndim = pair.ndim
+    shape = pair.ref.shape if ndim == 3 else (1,) + pair.ref.shape
+    spacing = pair.spacing if ndim == 3 else (1.0,) + pair.spacing
+    ref = torch.from_numpy(pair.ref).to(dev)
+    ev = torch.from_numpy(pair.eval).to(dev)
+    out = torch.empty_like(ref)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    h = g.gamma_create(ref, ev, ndim, shape, spacing, crit)
+    g.gamma_set_option(h, "timing", 1)
+    if args.lanes:
+        g.gamma_set_option(h, "lanes_per_voxel", args.lanes)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            g.gamma_run(h, out, stream)
+            g.gamma_pass_rate(h)
+        rate, n_eval, n_pass = g.gamma_pass_rate(h)
+        stats = g.gamma_get_stats(h)
+
+        sampler = ClockSampler(local_rank)
+        barrier()
+        torch.cuda.synchronize(dev)
+        sampler.start()
+        time.sleep(0.3)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        phase = {"prepare_ms": [], "shell_ms": [], "order_ms": [], "tail_ms": []}
+        for k in range(args.steps):
+            flush.zero_()                                  # evict the inputs from L2
+            starts[k].record(stream)
+            g.gamma_run(h, out, stream)
+            ends[k].record(stream)
+            tm = g.gamma_get_timings(h)                    # syncs this step
+            for key in phase:
+                phase[key].append(tm[key])
+        torch.cuda.synchronize(dev)
+        barrier()
+        clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * pair.nvox * args.steps / (total_ms / 1000.0)
+
+    # ---- end to end through the C ABI on pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hh = g.gamma_create(None, None, ndim, shape, spacing, crit)
+        try:
+            rh = torch.from_numpy(pair.ref).pin_memory()
+            eh = torch.from_numpy(pair.eval).pin_memory()
+            oh = torch.empty_like(rh).pin_memory()
+            for _ in range(max(args.warmup, 3)):
+                g.gamma_run_host(hh, rh, eh, oh, stream)
+                g.gamma_pass_rate(hh)
+            barrier()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                g.gamma_run_host(hh, rh, eh, oh, stream)
+                g.gamma_pass_rate(hh)                      # device->host read of the result
+            e2e_s = time.perf_counter() - t0
+            if world > 1:
+                t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                e2e_s = float(t.item())
+            nbytes = pair.nvox * 4
+            e2e = {"value": world * pair.nvox * args.steps / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes + 24}
+        finally:
+            g.gamma_destroy(hh)
+    g.gamma_destroy(h)
+
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel ----
+    mean_ph = {k: statistics.mean(v) for k, v in phase.items()}
+    kernel = "shell" if mean_ph["shell_ms"] >= mean_ph["tail_ms"] else "tail"
+    shell_cells = tail_cells = None
+    roofline = None
+    if not args.no_roofline:
+        shell_cells, tail_cells = cell_census(out, pair.spacing, c.dta_mm)
+        cells = shell_cells if kernel == "shell" else tail_cells
+        t_k = mean_ph[f"{kernel}_ms"] / 1000.0
+        flops = cells * FLOP_PER_CELL[ndim]
+        peaks = load_peaks()
+        sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        achieved = flops / t_k / 1e12 if t_k > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": f"k_{kernel}", "achieved": achieved,
+                    "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                    "traffic": None,
+                    "peak_basis": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                  f"{sm_max:.0f} MHz",
+                    "work": f"{cells} cells x {FLOP_PER_CELL[ndim]} FLOP"}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        v, n, dt, threads = time_oracle(pair, 15.0)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": (f"{n} of {pair.nvox} grid voxels" +
+                          (" (full grid)" if n >= pair.nvox else ", uniform random") +
+                          f", {dt:.1f} s")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "name": args.workload, "voxels": pair.nvox,
+                   "evaluated": n_eval, "pass_rate": rate,
+                   "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "phases_ms": mean_ph,
+        "search": {"tail_voxels": stats["tail_voxels"], "overflow_voxels": stats["overflow_voxels"],
+                   "fp64_cells": stats["fp64_cells"], "table_entries": stats["table_entries"],
+                   "r_max": stats["r_max"], "shell_cells": shell_cells, "tail_cells": tail_cells},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": KERNELS_PER_RUN * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference" and rank != 0:
+        return
+    pair = synth.workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, pair, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, pair, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

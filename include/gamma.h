@@ -1,0 +1,188 @@
+/*
+ * gamma.h -- C ABI of the GB300 gamma-index library (libgamma_gb300.so).
+ *
+ * Computes, for every reference voxel r_r, the gamma index of Eq. (1)
+ * (Section 2.1): the minimum Euclidean distance in the normalised
+ * dose-distance space (r / DTA, D / DD) from (r_r, D_r(r_r)) to the
+ * continuous evaluation surface spanned by the evaluation dose points (the
+ * geometric method of Ju et al. that the paper adopts, Section 2.1), using the
+ * radially sorted cell table and early exit of Algorithm A1 (steps 2-4) and a
+ * GPU kernel that evaluates every simplex face rather than recursing
+ * (Section 2.2, Algorithm A2 step 6).
+ *
+ * Conventions shared by every call:
+ *  - Dose grids are float32, C-ordered (z, y, x), contiguous.  A 2D problem
+ *    has ndim = 2 and shape[0] = 1; spacing[0] is then ignored.  Every axis of
+ *    the problem needs at least two voxels.  Reference and evaluation grids
+ *    coincide (same shape, spacing and origin).
+ *  - The evaluation surface is the graph of the piecewise-linear interpolant
+ *    of the evaluation dose over the Freudenthal triangulation of the grid
+ *    (each cube with lower corner p is split into the simplices
+ *    p -> p+e_s1 -> p+e_s1+e_s2 -> ... over the axis permutations s).
+ *    Simplices with a vertex outside the grid do not exist.
+ *  - Pointers named *_dev are device pointers on the handle's device; *_host
+ *    are host pointers (pinned memory recommended).  Device pointers passed to
+ *    gamma_create are borrowed: the caller keeps them alive and unchanged in
+ *    shape for the handle's lifetime; their contents may change between runs.
+ *  - Calls on one handle must not overlap: a handle owns one set of scratch
+ *    buffers, and two runs in flight at once race on them.
+ *  - Every call that takes a handle makes the handle's device current for the
+ *    duration of the call and restores the caller's device before returning.
+ *  - Return value: GAMMA_OK (0) or a negative gamma_status.  No call throws,
+ *    aborts or prints.
+ */
+#ifndef GAMMA_GB300_H
+#define GAMMA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gamma_ctx *gamma_handle;
+
+typedef enum {
+    GAMMA_OK = 0,
+    GAMMA_ERR_INVALID_ARG = -1,     /* null pointer, bad criteria, bad option */
+    GAMMA_ERR_SHAPE = -2,           /* ndim not 2/3, an axis with < 2 voxels, too many voxels */
+    GAMMA_ERR_NAN_INPUT = -3,       /* a NaN or Inf dose was seen by the last run */
+    GAMMA_ERR_OOM = -4,             /* device or host allocation failed */
+    GAMMA_ERR_TABLE_TOO_LARGE = -5, /* the requested cell table cannot be built */
+    GAMMA_ERR_TIMEOUT = -6,         /* a bounded device wait gave up */
+    GAMMA_ERR_CUDA = -7,            /* a CUDA runtime call failed (see gamma_last_cuda_error) */
+    GAMMA_ERR_NOT_RUN = -8,         /* results requested before any run */
+    GAMMA_ERR_MODEL = -9,           /* model file missing, malformed or of the wrong shape */
+    GAMMA_ERR_QUEUE_FULL = -10      /* internal work queue overflowed (results incomplete) */
+} gamma_status;
+
+typedef enum { GAMMA_GLOBAL = 0, GAMMA_LOCAL = 1 } gamma_mode;
+
+/* Gamma criteria (Eq. 1: Delta D and Delta d; Section 3.6).
+ *  dd_frac     DD criterion as a fraction (0.03 = 3 %), > 0.
+ *  dta_mm      DTA criterion in mm, > 0.
+ *  mode        GAMMA_GLOBAL: Delta D = dd_frac * D_norm for every voxel.
+ *              GAMMA_LOCAL:  Delta D(v) = dd_frac * D_r(v).
+ *  cutoff_frac a reference voxel is evaluated iff D_r(v) >= cutoff_frac *
+ *              D_norm (and, in local mode, D_r(v) > 0); the comparison is
+ *              taken in float32.  Others get NaN and are not counted.
+ *  dose_norm   D_norm; <= 0 means the maximum of the reference dose,
+ *              computed on the device at every run. */
+typedef struct {
+    float dd_frac;
+    float dta_mm;
+    int mode;
+    float cutoff_frac;
+    float dose_norm;
+} gamma_criteria;
+
+/* Counters of the last run (gamma_get_stats). */
+typedef struct {
+    int64_t n_voxels;        /* grid voxels */
+    int64_t n_eval;          /* evaluated voxels (passed the cutoff) */
+    int64_t n_pass;          /* evaluated voxels with gamma <= 1 */
+    int64_t tail_voxels;     /* voxels that searched past the key-0 cells */
+    int64_t overflow_voxels; /* voxels that ran past the table and scanned their box */
+    int64_t fp64_cells;      /* cells recomputed in FP64 (near-singular Gram matrix) */
+    int64_t cells_keyed;     /* stats mode: tail cells reached before the early exit */
+    int64_t cells_visited;   /* stats mode: tail cells whose faces were evaluated */
+    int64_t cells_pruned;    /* stats mode: tail cells skipped by the dose lower bound */
+    double d_norm;           /* dose norm used */
+    double r_max;            /* max over evaluated voxels of DD/Delta D (Algorithm A1 step 1) */
+    int64_t table_entries;   /* cell table length */
+    double table_radius;     /* every cell with key < table_radius is in the table */
+    uint32_t flags;          /* internal flags (non-finite input, queue overflow) */
+} gamma_stats;
+
+/* Per-phase device times of the last run, in ms, measured with CUDA events
+ * recorded on the run's stream (option "timing" = 1), in the split of
+ * Section 3.1: transfer (T_t: h2d + d2h, host-buffer runs only), processing
+ * (T_p: prepare + order) and search (T_gamma: shell + tail). */
+typedef struct {
+    float h2d_ms;       /* host-to-device copies (gamma_run_host) */
+    float prepare_ms;   /* dose norm and finite check */
+    float shell_ms;     /* gamma0 and the key-0 cells, every voxel */
+    float order_ms;     /* cost ordering of the queued voxels */
+    float tail_ms;      /* table walk of the queued voxels */
+    float d2h_ms;       /* device-to-host copy of the gamma map (gamma_run_host) */
+    float total_ms;     /* first to last event */
+} gamma_timings;
+
+/* Create a handle for one dose-pair geometry (Algorithm A1 steps 2-3: builds
+ * the radially sorted cell table on the host and uploads it).
+ *  out          receives the handle.
+ *  ref_dev,     reference / evaluation doses, device, float32, shape below,
+ *  eval_dev     borrowed.  Both NULL: the handle allocates its own device
+ *               buffers, to be filled by gamma_run_host.  One NULL: error.
+ *  ndim         2 or 3.
+ *  shape        (nz, ny, nx); nz = 1 for 2D.  nz*ny*nx < 2^31.
+ *  spacing_mm   (hz, hy, hx) voxel size in mm, > 0 (hz ignored for 2D).
+ *  crit         criteria (copied).
+ * Errors: INVALID_ARG, SHAPE, OOM, TABLE_TOO_LARGE, CUDA.  Synchronous. */
+int gamma_create(gamma_handle *out, const float *ref_dev, const float *eval_dev, int ndim,
+                 const int64_t shape[3], const float spacing_mm[3], const gamma_criteria *crit);
+
+/* Point an existing handle at a new dose pair of the same geometry (device,
+ * borrowed).  Errors: INVALID_ARG. */
+int gamma_set_inputs(gamma_handle h, const float *ref_dev, const float *eval_dev);
+
+/* Compute the gamma map (Algorithm A1 step 4 / A2 steps 2-7) on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  gamma_out_dev: device,
+ * float32, nz*ny*nx, written in full (NaN where not evaluated); the caller
+ * owns it.  Stream-ordered: returns once the work is queued, without
+ * synchronising and without allocating.  Errors: INVALID_ARG, CUDA. */
+int gamma_run(gamma_handle h, float *gamma_out_dev, void *cuda_stream);
+
+/* gamma_run on host buffers: copies ref_host and eval_host (float32, nz*ny*nx
+ * each) to the handle's own device buffers, runs, and copies the gamma map
+ * back into gamma_out_host, all on `cuda_stream`.  Only for handles created
+ * with NULL device inputs.  Stream-ordered like gamma_run: the host buffers
+ * must stay valid until the stream reaches the end of the copy (for example
+ * until gamma_pass_rate returns).  Errors: INVALID_ARG, CUDA. */
+int gamma_run_host(gamma_handle h, const float *ref_host, const float *eval_host,
+                   float *gamma_out_host, void *cuda_stream);
+
+/* Pass rate of the last run: rate = n_pass / n_eval (0 when n_eval = 0),
+ * pass iff gamma <= 1.  Synchronises the last run's stream.  Any output
+ * pointer may be NULL.  Errors: NOT_RUN, NAN_INPUT (the last run saw a
+ * non-finite dose; its results are meaningless), QUEUE_FULL, CUDA. */
+int gamma_pass_rate(gamma_handle h, double *rate, int64_t *n_eval, int64_t *n_pass);
+
+/* Counters of the last run (synchronises its stream).  Errors: NOT_RUN, CUDA. */
+int gamma_get_stats(gamma_handle h, gamma_stats *out);
+
+/* Phase times of the last run (needs option "timing" = 1 before the run;
+ * synchronises its stream).  Errors: NOT_RUN, INVALID_ARG (timing was off),
+ * CUDA. */
+int gamma_get_timings(gamma_handle h, gamma_timings *out);
+
+/* Tuning and diagnostic options (take effect at the next run):
+ *  "lanes_per_voxel"  4, 8, 16 or 32 lanes search one queued voxel together
+ *  "table_cap"        maximum cell-table length (rebuilds the table)
+ *  "fp64_tau_exp10"   FP64 redo when the normalised Gram determinant
+ *                     det(G)/prod(G_ii) < 10^-value; value <= 0 disables it
+ *  "stats"            1: count cells in the tail search (slower)
+ *  "sort_tail"        0: process queued voxels in discovery order instead
+ *                     of most-expensive-first (ablation)
+ *  "timing"           1: record per-phase CUDA events (gamma_get_timings)
+ * Errors: INVALID_ARG (unknown key or value), TABLE_TOO_LARGE, OOM. */
+int gamma_set_option(gamma_handle h, const char *key, int64_t value);
+
+/* Release the handle and everything it owns (synchronises its last stream).
+ * NULL is allowed. */
+void gamma_destroy(gamma_handle h);
+
+/* Static description of a status code. */
+const char *gamma_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *gamma_last_cuda_error(void);
+
+/* Library version string. */
+const char *gamma_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAMMA_GB300_H */

@@ -1,0 +1,202 @@
+"""GB300 gamma-index library: thin ctypes binding of libgamma_gb300.so.
+
+Every function here has the name of the C entry point it wraps (see
+include/gamma.h) and only marshals arguments: torch tensors become device
+pointers and CUDA stream handles, status codes become exceptions.  All
+gamma arithmetic runs in the library's CUDA kernels; there is no CPU path.
+If the library has not been built, importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+from . import _build
+
+__all__ = [
+    "GammaError", "gamma_criteria", "gamma_stats", "gamma_create", "gamma_set_inputs",
+    "gamma_run", "gamma_run_host", "gamma_pass_rate", "gamma_get_stats", "gamma_get_timings",
+    "gamma_set_option",
+    "gamma_destroy", "gamma_strerror", "gamma_version", "library_path", "criteria",
+    "GLOBAL", "LOCAL",
+]
+
+GLOBAL, LOCAL = 0, 1
+
+
+class gamma_criteria(ctypes.Structure):
+    _fields_ = [("dd_frac", ctypes.c_float), ("dta_mm", ctypes.c_float), ("mode", ctypes.c_int),
+                ("cutoff_frac", ctypes.c_float), ("dose_norm", ctypes.c_float)]
+
+
+class gamma_stats(ctypes.Structure):
+    _fields_ = [("n_voxels", ctypes.c_int64), ("n_eval", ctypes.c_int64),
+                ("n_pass", ctypes.c_int64), ("tail_voxels", ctypes.c_int64),
+                ("overflow_voxels", ctypes.c_int64), ("fp64_cells", ctypes.c_int64),
+                ("cells_keyed", ctypes.c_int64), ("cells_visited", ctypes.c_int64),
+                ("cells_pruned", ctypes.c_int64), ("d_norm", ctypes.c_double),
+                ("r_max", ctypes.c_double), ("table_entries", ctypes.c_int64),
+                ("table_radius", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class gamma_timings(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("h2d_ms", "prepare_ms", "shell_ms", "order_ms",
+                                              "tail_ms", "d2h_ms", "total_ms")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GammaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.gamma_strerror(code).decode()
+        if code == -7:
+            msg += ": " + _lib.gamma_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+    f32p = ctypes.POINTER(ctypes.c_float)
+    lib.gamma_create.argtypes = [ctypes.POINTER(vp), vp, vp, ctypes.c_int, i64p, f32p,
+                                 ctypes.POINTER(gamma_criteria)]
+    lib.gamma_set_inputs.argtypes = [vp, vp, vp]
+    lib.gamma_run.argtypes = [vp, vp, vp]
+    lib.gamma_run_host.argtypes = [vp, vp, vp, vp, vp]
+    lib.gamma_pass_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p]
+    lib.gamma_get_stats.argtypes = [vp, ctypes.POINTER(gamma_stats)]
+    lib.gamma_get_timings.argtypes = [vp, ctypes.POINTER(gamma_timings)]
+    lib.gamma_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
+    lib.gamma_destroy.argtypes = [vp]
+    lib.gamma_destroy.restype = None
+    lib.gamma_strerror.argtypes = [ctypes.c_int]
+    lib.gamma_strerror.restype = ctypes.c_char_p
+    lib.gamma_last_cuda_error.restype = ctypes.c_char_p
+    lib.gamma_version.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise GammaError(rc, where)
+
+
+def _dev_ptr(t) -> int:
+    """Device pointer of a contiguous float32 CUDA tensor (or an int)."""
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"expected a torch.Tensor, got {type(t).__name__}")
+    if t.device.type != "cuda" or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor, got "
+                         f"device={t.device} dtype={t.dtype} contiguous={t.is_contiguous()}")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def criteria(dd_frac: float, dta_mm: float, local: bool = False, cutoff_frac: float = 0.10,
+             dose_norm: float = 0.0) -> gamma_criteria:
+    return gamma_criteria(dd_frac, dta_mm, LOCAL if local else GLOBAL, cutoff_frac, dose_norm)
+
+
+def gamma_create(ref_dev, eval_dev, ndim: int, shape: Sequence[int], spacing_mm: Sequence[float],
+                 crit: gamma_criteria) -> int:
+    """Create a handle.  ref_dev/eval_dev: float32 CUDA tensors (or None for a
+    handle that owns its device buffers).  shape/spacing in (z, y, x) order,
+    shape[0] = 1 for 2D.  Returns the handle (an int)."""
+    h = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * 3)(*[int(s) for s in shape])
+    sp = (ctypes.c_float * 3)(*[float(s) for s in spacing_mm])
+    _check(_lib.gamma_create(ctypes.byref(h), _dev_ptr(ref_dev), _dev_ptr(eval_dev), int(ndim),
+                             shp, sp, ctypes.byref(crit)), "gamma_create")
+    return h.value
+
+
+def gamma_set_inputs(h: int, ref_dev, eval_dev) -> None:
+    _check(_lib.gamma_set_inputs(h, _dev_ptr(ref_dev), _dev_ptr(eval_dev)), "gamma_set_inputs")
+
+
+def gamma_run(h: int, gamma_out_dev, stream=None) -> None:
+    _check(_lib.gamma_run(h, _dev_ptr(gamma_out_dev), _stream_ptr(stream)), "gamma_run")
+
+
+def gamma_run_host(h: int, ref_host, eval_host, gamma_out_host, stream=None) -> None:
+    """Host-buffer run; arguments are CPU float32 tensors or numpy arrays
+    (pinned tensors give asynchronous copies)."""
+    def hp(a):
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError("expected a contiguous CPU tensor")
+            return a.data_ptr()
+        if not a.flags["C_CONTIGUOUS"] or a.dtype.name != "float32":
+            raise ValueError("expected a C-contiguous float32 array")
+        return a.ctypes.data
+    _check(_lib.gamma_run_host(h, hp(ref_host), hp(eval_host), hp(gamma_out_host),
+                               _stream_ptr(stream)), "gamma_run_host")
+
+
+def gamma_pass_rate(h: int):
+    """(rate, n_eval, n_pass) of the last run (synchronises its stream)."""
+    rate = ctypes.c_double()
+    ne, npass = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.gamma_pass_rate(h, ctypes.byref(rate), ctypes.byref(ne), ctypes.byref(npass)),
+           "gamma_pass_rate")
+    return rate.value, ne.value, npass.value
+
+
+def gamma_get_stats(h: int) -> dict:
+    st = gamma_stats()
+    _check(_lib.gamma_get_stats(h, ctypes.byref(st)), "gamma_get_stats")
+    return st.as_dict()
+
+
+def gamma_get_timings(h: int) -> dict:
+    """Per-phase device times (ms) of the last run (option "timing" must be 1)."""
+    t = gamma_timings()
+    _check(_lib.gamma_get_timings(h, ctypes.byref(t)), "gamma_get_timings")
+    return t.as_dict()
+
+
+def gamma_set_option(h: int, key: str, value: int) -> None:
+    _check(_lib.gamma_set_option(h, key.encode(), int(value)), f"gamma_set_option({key})")
+
+
+def gamma_destroy(h: Optional[int]) -> None:
+    if h:
+        _lib.gamma_destroy(h)
+
+
+def gamma_strerror(code: int) -> str:
+    return _lib.gamma_strerror(code).decode()
+
+
+def gamma_version() -> str:
+    return _lib.gamma_version().decode()

@@ -1,0 +1,507 @@
+// C ABI of the gamma library: handle management, the host-side cell table
+// (Algorithm A1 steps 2-3) and the launch sequence of one run.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gamma.h"
+#include "gamma_internal.h"
+
+using gk::Counters;
+using gk::Problem;
+using gk::TableEntry;
+
+namespace {
+
+thread_local std::string g_last_cuda;
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda = cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? GAMMA_ERR_OOM : GAMMA_ERR_CUDA;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+// Keeps the caller's current device across a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Largest float not above x (keys must stay lower bounds after rounding).
+float round_down(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = std::nextafterf(f, -INFINITY);
+    return f;
+}
+
+double axis_gap(int i) { return i >= 0 ? (double)i : (double)(-i - 1); }
+
+}  // namespace
+
+struct gamma_ctx {
+    int device = 0;
+    int ndim = 3;
+    int64_t nz = 1, ny = 1, nx = 1, nvox = 0;
+    double h[3] = {1, 1, 1};          // hx, hy, hz in mm
+    gamma_criteria crit{};
+    const float* ref = nullptr;
+    const float* ev = nullptr;
+    float* own_ref = nullptr;
+    float* own_ev = nullptr;
+    float* own_out = nullptr;
+    // cell table
+    std::vector<TableEntry> table;
+    TableEntry* table_dev = nullptr;
+    int t1 = 0;
+    double r_cover = 0;
+    int64_t table_cap = 1 << 17;
+    // scratch
+    Counters* ctr = nullptr;
+    unsigned* tail_raw = nullptr;
+    unsigned char* tail_bucket = nullptr;
+    unsigned* tail_sorted = nullptr;
+    unsigned tail_cap = 0;
+    // options
+    int lanes = 8;
+    double tau = 1e-6;
+    int stats = 0;
+    int sort_tail = 1;
+    int timing = 0;
+    // per-phase events: 0 start, 1 after h2d, 2 after prepare, 3 after shell,
+    // 4 after order, 5 after tail, 6 after d2h
+    cudaEvent_t tev[7] = {};
+    bool ev_h2d = false;     // the last run copied inputs from the host
+    // state
+    cudaStream_t last_stream = nullptr;
+    bool ran = false;
+};
+
+namespace {
+
+// Algorithm A1 steps 2-3 for the cells of the Freudenthal triangulation: every
+// lower-corner offset c whose cell can hold faces for some voxel, keyed by the
+// distance from the reference voxel to the closed cell box [c, c + 1] divided
+// by the DTA, sorted ascending (ties by z, y, x), cut to `cap` entries.
+int build_table(gamma_ctx* h)
+{
+    const double dta = h->crit.dta_mm;
+    const double hn[3] = {h->h[0] / dta, h->h[1] / dta, h->h[2] / dta};
+    const int nd = h->ndim;
+    const int64_t n[3] = {h->nx, h->ny, h->nz};
+    const int64_t cap = h->table_cap;
+    if (cap < (1 << nd)) return GAMMA_ERR_INVALID_ARG;
+    // radius from a ball-volume estimate of about 2 * cap cells
+    double cellvol = hn[0] * hn[1] * (nd == 3 ? hn[2] : 1.0);
+    double R = nd == 3 ? std::cbrt(2.0 * (double)cap * cellvol * 3.0 / (4.0 * M_PI))
+                       : std::sqrt(2.0 * (double)cap * cellvol / M_PI);
+    // the whole grid seen from any voxel
+    double diag = 0;
+    for (int a = 0; a < nd; ++a) diag += (double)(n[a] * n[a]) * hn[a] * hn[a];
+    diag = std::sqrt(diag) + 1.0;
+    bool clipped_by_grid = false;
+    if (R > diag) { R = diag; clipped_by_grid = true; }
+    int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    bool packing_limited = false;
+    for (int a = 0; a < nd; ++a) {
+        int64_t lim = (int64_t)std::ceil(R / hn[a]) + 1;
+        lo[a] = std::max<int64_t>(-(n[a] - 1), -lim - 1);
+        hi[a] = std::min<int64_t>(n[a] - 1, lim);
+        if (lo[a] < -511) { lo[a] = -511; packing_limited = true; }
+        if (hi[a] > 511) { hi[a] = 511; packing_limited = true; }
+    }
+    struct Tmp { double key; int x, y, z; };
+    std::vector<Tmp> all;
+    try {
+        for (int64_t z = lo[2]; z <= hi[2]; ++z)
+            for (int64_t y = lo[1]; y <= hi[1]; ++y)
+                for (int64_t x = lo[0]; x <= hi[0]; ++x) {
+                    double ax = axis_gap((int)x) * hn[0], ay = axis_gap((int)y) * hn[1];
+                    double az = nd == 3 ? axis_gap((int)z) * hn[2] : 0.0;
+                    double key = std::sqrt(ax * ax + ay * ay + az * az);
+                    if (key < R) all.push_back({key, (int)x, (int)y, (int)z});
+                }
+    } catch (const std::bad_alloc&) {
+        return GAMMA_ERR_OOM;
+    }
+    std::sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
+        if (a.key != b.key) return a.key < b.key;
+        if (a.z != b.z) return a.z < b.z;
+        if (a.y != b.y) return a.y < b.y;
+        return a.x < b.x;
+    });
+    double cover = clipped_by_grid ? INFINITY : R;
+    if (packing_limited) {
+        double m = INFINITY;
+        for (int a = 0; a < nd; ++a) m = std::min(m, 510.0 * hn[a]);
+        cover = std::min(cover, m);
+    }
+    size_t keep = all.size();
+    if ((int64_t)keep > cap) {
+        keep = (size_t)cap;
+        cover = std::min(cover, all[keep].key);
+    }
+    h->table.resize(keep);
+    int t1 = 0;
+    for (size_t i = 0; i < keep; ++i) {
+        h->table[i].off = gk::pack10(all[i].x, all[i].y, all[i].z);
+        h->table[i].key = round_down(all[i].key);
+        if (all[i].key == 0.0) ++t1;
+    }
+    if (keep > 0 && t1 != (1 << nd)) return GAMMA_ERR_TABLE_TOO_LARGE;  // cannot happen for n >= 2
+    h->t1 = t1;
+    h->r_cover = cover;
+    if (h->table_dev) { cudaFree(h->table_dev); h->table_dev = nullptr; }
+    if (keep) {
+        CK(cudaMalloc(&h->table_dev, keep * sizeof(TableEntry)));
+        CK(cudaMemcpy(h->table_dev, h->table.data(), keep * sizeof(TableEntry),
+                      cudaMemcpyHostToDevice));
+    }
+    return GAMMA_OK;
+}
+
+Problem make_problem(const gamma_ctx* h, float* out)
+{
+    Problem P{};
+    P.ref = h->ref;
+    P.ev = h->ev;
+    P.out = out;
+    P.nvox = h->nvox;
+    P.ndim = h->ndim;
+    P.nx = (int)h->nx;
+    P.ny = (int)h->ny;
+    P.nz = (int)h->nz;
+    const double dta = h->crit.dta_mm;
+    double hn2[3];
+    for (int a = 0; a < 3; ++a) {
+        const double hn = h->h[a] / dta;
+        P.hn[a] = (float)hn;
+        hn2[a] = hn * hn;
+        P.mt.hn2[a] = (float)hn2[a];
+        P.mtd.hn2[a] = hn2[a];
+    }
+    P.mt.kappa[0] = 0.f;
+    P.mtd.kappa[0] = 0.0;
+    for (int A = 1; A < 8; ++A) {
+        double s = 0;
+        for (int a = 0; a < 3; ++a)
+            if (A & (1 << a)) s += hn2[a];
+        P.mt.kappa[A] = (float)(1.0 / s);
+        P.mtd.kappa[A] = 1.0 / s;
+    }
+    P.dd_frac = h->crit.dd_frac;
+    P.cutoff_frac = h->crit.cutoff_frac;
+    P.dose_norm = h->crit.dose_norm;
+    P.local = h->crit.mode == GAMMA_LOCAL;
+    P.tau = (float)h->tau;
+    P.stats = h->stats;
+    P.table = h->table_dev;
+    P.ntable = (int)h->table.size();
+    P.t1 = h->t1;
+    P.r_cover = std::isinf(h->r_cover) ? INFINITY : round_down(h->r_cover);
+    P.tail_cap = h->tail_cap;
+    P.ctr = h->ctr;
+    P.tail_raw = h->tail_raw;
+    P.tail_bucket = h->tail_bucket;
+    P.tail_sorted = h->tail_sorted;
+    P.sort_tail = h->sort_tail;
+    return P;
+}
+
+void free_ctx(gamma_ctx* h)
+{
+    if (!h) return;
+    for (auto& e : h->tev)
+        if (e) cudaEventDestroy(e);
+    cudaFree(h->table_dev);
+    cudaFree(h->ctr);
+    cudaFree(h->tail_raw);
+    cudaFree(h->tail_bucket);
+    cudaFree(h->tail_sorted);
+    cudaFree(h->own_ref);
+    cudaFree(h->own_ev);
+    cudaFree(h->own_out);
+    delete h;
+}
+
+int check_criteria(const gamma_criteria* c)
+{
+    if (!c) return GAMMA_ERR_INVALID_ARG;
+    if (!(c->dd_frac > 0.f) || !std::isfinite(c->dd_frac)) return GAMMA_ERR_INVALID_ARG;
+    if (!(c->dta_mm > 0.f) || !std::isfinite(c->dta_mm)) return GAMMA_ERR_INVALID_ARG;
+    if (c->mode != GAMMA_GLOBAL && c->mode != GAMMA_LOCAL) return GAMMA_ERR_INVALID_ARG;
+    if (!std::isfinite(c->cutoff_frac) || !std::isfinite(c->dose_norm)) return GAMMA_ERR_INVALID_ARG;
+    return GAMMA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gamma_create(gamma_handle* out, const float* ref_dev, const float* eval_dev, int ndim,
+                 const int64_t shape[3], const float spacing_mm[3], const gamma_criteria* crit)
+{
+    if (!out || !shape || !spacing_mm) return GAMMA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if ((ref_dev == nullptr) != (eval_dev == nullptr)) return GAMMA_ERR_INVALID_ARG;
+    if (int rc = check_criteria(crit)) return rc;
+    if (ndim != 2 && ndim != 3) return GAMMA_ERR_SHAPE;
+    const int64_t nz = ndim == 3 ? shape[0] : 1, ny = shape[1], nx = shape[2];
+    if (ndim == 2 && shape[0] != 1) return GAMMA_ERR_SHAPE;
+    if (nx < 2 || ny < 2 || (ndim == 3 && nz < 2)) return GAMMA_ERR_SHAPE;
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) return GAMMA_ERR_SHAPE;
+    const int64_t nvox = nx * ny * nz;
+    if (nvox >= (int64_t(1) << 31)) return GAMMA_ERR_SHAPE;
+    for (int a = (ndim == 3 ? 0 : 1); a < 3; ++a)
+        if (!(spacing_mm[a] > 0.f) || !std::isfinite(spacing_mm[a])) return GAMMA_ERR_INVALID_ARG;
+
+    gamma_ctx* h = new (std::nothrow) gamma_ctx();
+    if (!h) return GAMMA_ERR_OOM;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return GAMMA_ERR_CUDA; }
+    h->ndim = ndim;
+    h->nz = nz; h->ny = ny; h->nx = nx; h->nvox = nvox;
+    h->h[0] = spacing_mm[2];
+    h->h[1] = spacing_mm[1];
+    h->h[2] = ndim == 3 ? spacing_mm[0] : 1.0;
+    h->crit = *crit;
+    h->ref = ref_dev;
+    h->ev = eval_dev;
+    int rc = GAMMA_OK;
+    auto fail = [&](int code) { free_ctx(h); return code; };
+    if ((rc = build_table(h)) != GAMMA_OK) return fail(rc);
+    cudaError_t e;
+    for (auto& te : h->tev)
+        if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = cudaMalloc(&h->ctr, sizeof(Counters))) != cudaSuccess) return fail(cuda_fail(e));
+    h->tail_cap = (unsigned)nvox;
+    if ((e = cudaMalloc(&h->tail_raw, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = cudaMalloc(&h->tail_sorted, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = cudaMalloc(&h->tail_bucket, nvox)) != cudaSuccess) return fail(cuda_fail(e));
+    if (!ref_dev) {
+        if ((e = cudaMalloc(&h->own_ref, sizeof(float) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
+        if ((e = cudaMalloc(&h->own_ev, sizeof(float) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
+        if ((e = cudaMalloc(&h->own_out, sizeof(float) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
+        h->ref = h->own_ref;
+        h->ev = h->own_ev;
+    }
+    *out = h;
+    return GAMMA_OK;
+}
+
+int gamma_set_inputs(gamma_handle h, const float* ref_dev, const float* eval_dev)
+{
+    if (!h || !ref_dev || !eval_dev || h->own_ref) return GAMMA_ERR_INVALID_ARG;
+    h->ref = ref_dev;
+    h->ev = eval_dev;
+    return GAMMA_OK;
+}
+
+int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
+{
+    if (!h || !gamma_out_dev) return GAMMA_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const Problem P = make_problem(h, gamma_out_dev);
+    const bool tm = h->timing != 0;
+    if (tm && !h->ev_h2d) {
+        CK(cudaEventRecord(h->tev[0], s));
+        CK(cudaEventRecord(h->tev[1], s));
+    }
+    CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), s));
+    CK(gk::launch_prepare(P, s));
+    if (tm) CK(cudaEventRecord(h->tev[2], s));
+    CK(gk::launch_shell(P, s));
+    if (tm) CK(cudaEventRecord(h->tev[3], s));
+    CK(gk::launch_order_tail(P, s));
+    if (tm) CK(cudaEventRecord(h->tev[4], s));
+    CK(gk::launch_tail(P, h->lanes, s));
+    if (tm) {
+        CK(cudaEventRecord(h->tev[5], s));
+        if (!h->ev_h2d) CK(cudaEventRecord(h->tev[6], s));
+    }
+    h->last_stream = s;
+    h->ran = true;
+    return GAMMA_OK;
+}
+
+int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host,
+                   float* gamma_out_host, void* cuda_stream)
+{
+    if (!h || !ref_host || !eval_host || !gamma_out_host || !h->own_ref) return GAMMA_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t bytes = sizeof(float) * (size_t)h->nvox;
+    const bool tm = h->timing != 0;
+    if (tm) CK(cudaEventRecord(h->tev[0], s));
+    CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->own_ev, eval_host, bytes, cudaMemcpyHostToDevice, s));
+    if (tm) CK(cudaEventRecord(h->tev[1], s));
+    h->ev_h2d = true;
+    int rc = gamma_run(h, h->own_out, cuda_stream);
+    h->ev_h2d = false;
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(gamma_out_host, h->own_out, bytes, cudaMemcpyDeviceToHost, s));
+    if (tm) CK(cudaEventRecord(h->tev[6], s));
+    return GAMMA_OK;
+}
+
+static int read_counters(gamma_handle h, Counters* c)
+{
+    if (!h->ran) return GAMMA_ERR_NOT_RUN;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    CK(cudaStreamSynchronize(h->last_stream));
+    CK(cudaMemcpy(c, h->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+    return GAMMA_OK;
+}
+
+int gamma_pass_rate(gamma_handle h, double* rate, int64_t* n_eval, int64_t* n_pass)
+{
+    if (!h) return GAMMA_ERR_INVALID_ARG;
+    Counters c;
+    if (int rc = read_counters(h, &c)) return rc;
+    if (c.flags & gk::kFlagNonFinite) return GAMMA_ERR_NAN_INPUT;
+    if (c.flags & gk::kFlagTailFull) return GAMMA_ERR_QUEUE_FULL;
+    if (n_eval) *n_eval = (int64_t)c.n_eval;
+    if (n_pass) *n_pass = (int64_t)c.n_pass;
+    if (rate) *rate = c.n_eval ? (double)c.n_pass / (double)c.n_eval : 0.0;
+    return GAMMA_OK;
+}
+
+int gamma_get_stats(gamma_handle h, gamma_stats* out)
+{
+    if (!h || !out) return GAMMA_ERR_INVALID_ARG;
+    Counters c;
+    if (int rc = read_counters(h, &c)) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->n_voxels = h->nvox;
+    out->n_eval = (int64_t)c.n_eval;
+    out->n_pass = (int64_t)c.n_pass;
+    out->tail_voxels = (int64_t)c.tail_count;
+    out->overflow_voxels = (int64_t)c.overflow_count;
+    out->fp64_cells = (int64_t)c.fp64_cells;
+    out->cells_keyed = (int64_t)c.cells_keyed;
+    out->cells_visited = (int64_t)c.cells_visited;
+    out->cells_pruned = (int64_t)c.cells_pruned;
+    out->d_norm = h->crit.dose_norm > 0 ? (double)h->crit.dose_norm : (double)gk::fdec(c.dnorm_enc);
+    out->r_max = (double)gk::fdec(c.rmax_enc);
+    out->table_entries = (int64_t)h->table.size();
+    out->table_radius = h->r_cover;
+    out->flags = c.flags;
+    return GAMMA_OK;
+}
+
+int gamma_get_timings(gamma_handle h, gamma_timings* out)
+{
+    if (!h || !out) return GAMMA_ERR_INVALID_ARG;
+    if (!h->ran) return GAMMA_ERR_NOT_RUN;
+    if (!h->timing) return GAMMA_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    CK(cudaStreamSynchronize(h->last_stream));
+    float t[6];
+    for (int i = 0; i < 6; ++i) CK(cudaEventElapsedTime(&t[i], h->tev[i], h->tev[i + 1]));
+    out->h2d_ms = t[0];
+    out->prepare_ms = t[1];
+    out->shell_ms = t[2];
+    out->order_ms = t[3];
+    out->tail_ms = t[4];
+    out->d2h_ms = t[5];
+    CK(cudaEventElapsedTime(&out->total_ms, h->tev[0], h->tev[6]));
+    return GAMMA_OK;
+}
+
+int gamma_set_option(gamma_handle h, const char* key, int64_t value)
+{
+    if (!h || !key) return GAMMA_ERR_INVALID_ARG;
+    if (!std::strcmp(key, "lanes_per_voxel")) {
+        if (value != 4 && value != 8 && value != 16 && value != 32) return GAMMA_ERR_INVALID_ARG;
+        h->lanes = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "table_cap")) {
+        if (value < 8 || value > (int64_t(1) << 26)) return GAMMA_ERR_INVALID_ARG;
+        DeviceGuard dg(h->device);
+        if (!dg.ok) return GAMMA_ERR_CUDA;
+        if (h->ran) { CK(cudaStreamSynchronize(h->last_stream)); }
+        h->table_cap = value;
+        return build_table(h);
+    }
+    if (!std::strcmp(key, "fp64_tau_exp10")) {
+        if (value > 30) return GAMMA_ERR_INVALID_ARG;
+        h->tau = value <= 0 ? 0.0 : std::pow(10.0, -(double)value);
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "stats")) {
+        if (value != 0 && value != 1) return GAMMA_ERR_INVALID_ARG;
+        h->stats = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "timing")) {
+        if (value != 0 && value != 1) return GAMMA_ERR_INVALID_ARG;
+        h->timing = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "sort_tail")) {
+        if (value != 0 && value != 1) return GAMMA_ERR_INVALID_ARG;
+        h->sort_tail = (int)value;
+        return GAMMA_OK;
+    }
+    return GAMMA_ERR_INVALID_ARG;
+}
+
+void gamma_destroy(gamma_handle h)
+{
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    if (h->ran) cudaStreamSynchronize(h->last_stream);
+    free_ctx(h);
+}
+
+const char* gamma_strerror(int code)
+{
+    switch (code) {
+    case GAMMA_OK: return "ok";
+    case GAMMA_ERR_INVALID_ARG: return "invalid argument";
+    case GAMMA_ERR_SHAPE: return "invalid shape";
+    case GAMMA_ERR_NAN_INPUT: return "non-finite dose in input";
+    case GAMMA_ERR_OOM: return "out of memory";
+    case GAMMA_ERR_TABLE_TOO_LARGE: return "cell table too large";
+    case GAMMA_ERR_TIMEOUT: return "device wait timed out";
+    case GAMMA_ERR_CUDA: return "CUDA error";
+    case GAMMA_ERR_NOT_RUN: return "no run yet";
+    case GAMMA_ERR_MODEL: return "bad model";
+    case GAMMA_ERR_QUEUE_FULL: return "work queue overflow";
+    default: return "unknown error";
+    }
+}
+
+const char* gamma_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+const char* gamma_version(void) { return "gamma_gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal structures shared by the CUDA kernels and the C-ABI layer.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gamma_face.cuh"
+
+namespace gk {
+
+constexpr int kNumBuckets = 32;
+
+// Flags raised by kernels (Counters::flags).
+enum : uint32_t {
+    kFlagNonFinite = 1u,     // a NaN or Inf dose was seen
+    kFlagTailFull = 2u,      // the tail queue overflowed its capacity
+};
+
+// One entry of the radially sorted cell table (Algorithm A1 steps 2-3):
+// the cell's lower-corner offset relative to the reference voxel, packed as
+// three signed 10-bit fields (x | y << 10 | z << 20), and the key: the
+// distance from the reference voxel to the cell box, divided by the DTA,
+// rounded down to float so that it stays a lower bound.
+struct TableEntry {
+    uint32_t off;
+    float key;
+};
+
+__host__ __device__ inline int unpack10(uint32_t v, int shift)
+{
+    int f = int((v >> shift) & 1023u);
+    return f >= 512 ? f - 1024 : f;
+}
+
+__host__ __device__ inline uint32_t pack10(int x, int y, int z)
+{
+    return (uint32_t(x) & 1023u) | ((uint32_t(y) & 1023u) << 10) | ((uint32_t(z) & 1023u) << 20);
+}
+
+// Device-side counters; zeroed at the start of every run.
+struct Counters {
+    unsigned long long n_eval;
+    unsigned long long n_pass;
+    unsigned long long cells_visited;   // stats mode: cells whose faces were evaluated
+    unsigned long long cells_pruned;    // stats mode: cells skipped by the lower bound
+    unsigned long long cells_keyed;     // stats mode: table cells reached before the break
+    unsigned int dnorm_enc;             // max reference dose, order-preserving int code
+    unsigned int rmax_enc;              // max gamma0 over evaluated voxels (same code)
+    unsigned int flags;
+    unsigned int tail_count;
+    unsigned int head;
+    unsigned int overflow_count;        // voxels that needed the box scan
+    unsigned int fp64_cells;            // cells redone in FP64
+    unsigned int pad;
+    unsigned int hist[kNumBuckets];
+    unsigned int cursor[kNumBuckets];
+};
+
+// Order-preserving encoding of a float into an unsigned int (for atomicMax).
+__host__ __device__ inline unsigned int fenc(float f)
+{
+    union { float f; unsigned int u; } c;
+    c.f = f;
+    return (c.u & 0x80000000u) ? ~c.u : (c.u | 0x80000000u);
+}
+__host__ __device__ inline float fdec(unsigned int e)
+{
+    union { float f; unsigned int u; } c;
+    c.u = (e & 0x80000000u) ? (e & 0x7fffffffu) : ~e;
+    return c.f;
+}
+
+// Everything a launch needs about one dose pair.
+struct Problem {
+    const float* ref;
+    const float* ev;
+    float* out;
+    long long nvox;
+    int ndim;
+    int nx, ny, nz;
+    float hn[3];             // h_a / dta
+    Metric mt;               // FP32 metric constants
+    MetricT<double> mtd;     // FP64 copies for the ill-conditioned redo
+    float dd_frac;
+    float cutoff_frac;
+    float dose_norm;         // > 0: fixed; else the device max of the reference
+    int local;
+    float tau;               // FP64 redo when det(G)/prod(G_ii) < tau (0: never)
+    int stats;               // count cells in the tail search
+    const TableEntry* table;
+    int ntable;
+    int t1;                  // first table index past the key-0 shell
+    float r_cover;           // every cell with key < r_cover is in the table
+    unsigned int tail_cap;
+    Counters* ctr;
+    unsigned int* tail_raw;      // unsorted tail voxels
+    unsigned char* tail_bucket;  // their cost buckets
+    unsigned int* tail_sorted;   // tail voxels, most expensive bucket first
+    int sort_tail;               // 0: keep discovery order (ablation)
+};
+
+// Launchers (gamma_kernels.cu).  All are stream-ordered and allocate nothing.
+cudaError_t launch_prepare(const Problem& P, cudaStream_t s);
+cudaError_t launch_shell(const Problem& P, cudaStream_t s);
+cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
+cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, cudaStream_t s);
+int device_sm_count();
+
+}  // namespace gk

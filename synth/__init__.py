@@ -114,8 +114,10 @@ def make_pair_2d(shape=(128, 128), spacing=(1.0, 1.0), seed: int = 0,
     rng = np.random.default_rng(seed + 7919)
     if noise_sd > 0:
         ev = ev + rng.normal(0.0, noise_sd, size=ev.shape)
-    return Pair(name or f"2d_{shape[0]}x{shape[1]}_s{seed}", ref.astype(np.float32),
-                ev.astype(np.float32), tuple(float(h) for h in spacing), criteria)
+    return Pair(name or f"2d_{shape[0]}x{shape[1]}_s{seed}",
+                np.ascontiguousarray(ref, dtype=np.float32),
+                np.ascontiguousarray(ev, dtype=np.float32), tuple(float(h) for h in spacing),
+                criteria)
 
 
 # ---------------------------------------------------------------------------
@@ -210,8 +212,9 @@ def make_pair_3d(shape=(120, 160, 160), spacing=(2.5, 2.5, 2.5), seed: int = 0,
     if noise_sd > 0:
         ev = ev + random_field(shape, spacing, seed + 104729, noise_sigma_mm, noise_sd)
     tag = "x".join(str(s) for s in shape[::-1])
-    return Pair(name or f"3d_{tag}_s{seed}", ref.astype(np.float32),
-                ev.astype(np.float32), tuple(float(h) for h in spacing), criteria)
+    return Pair(name or f"3d_{tag}_s{seed}", np.ascontiguousarray(ref, dtype=np.float32),
+                np.ascontiguousarray(ev, dtype=np.float32), tuple(float(h) for h in spacing),
+                criteria)
 
 
 # ---------------------------------------------------------------------------

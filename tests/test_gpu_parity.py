@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar: |gamma_gpu - gamma_oracle| <= 1e-4 absolute on every evaluated voxel,
+identical evaluated masks (NaN pattern), and identical pass/fail (gamma <= 1)
+except where |gamma_oracle - 1| < 1e-4.  Small grids are compared in full;
+the full-size workloads are compared on sampled voxels the oracle computes
+one by one, plus properties that hold at any size.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import _brute as brute
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-4
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def _geom(ref, spacing):
+    if ref.ndim == 2:
+        return 2, (1,) + ref.shape, (1.0,) + tuple(spacing)
+    return 3, ref.shape, tuple(spacing)
+
+
+def gpu_gamma(ref, ev, spacing, crit, options=None, runs=1):
+    import paper_1012_1900_gb300 as g
+    ndim, shape, sp = _geom(ref, spacing)
+    r = torch.from_numpy(np.ascontiguousarray(ref, dtype=np.float32)).cuda()
+    e = torch.from_numpy(np.ascontiguousarray(ev, dtype=np.float32)).cuda()
+    out = torch.full_like(r, -7.0)
+    h = g.gamma_create(r, e, ndim, shape, sp,
+                       g.criteria(crit.dd_frac, crit.dta_mm, crit.local, crit.cutoff_frac,
+                                  crit.dose_norm))
+    try:
+        for k, v in (options or {}).items():
+            g.gamma_set_option(h, k, v)
+        outs = []
+        for _ in range(runs):
+            g.gamma_run(h, out)
+            counts = g.gamma_pass_rate(h)
+            outs.append(out.cpu().numpy().astype(np.float64))
+        st = g.gamma_get_stats(h)
+    finally:
+        g.gamma_destroy(h)
+    return (outs[0] if runs == 1 else outs), counts, st
+
+
+def oracle_gamma(ref, ev, spacing, crit, idx=None, **kw):
+    return oracle.gamma(ref, ev, spacing, f32(crit.dd_frac), f32(crit.dta_mm), local=crit.local,
+                        cutoff_frac=f32(crit.cutoff_frac), dose_norm=f32(crit.dose_norm),
+                        idx=idx, **kw)
+
+
+def assert_parity(got, want, counts=None):
+    assert np.array_equal(np.isnan(got), np.isnan(want)), "evaluated masks differ"
+    ok = ~np.isnan(want)
+    if not ok.any():
+        return 0.0
+    err = np.abs(got[ok] - want[ok])
+    worst = float(err.max())
+    assert worst <= TOL, f"max |dgamma| = {worst:.3e} at {np.argmax(err)}"
+    band = np.abs(want[ok] - 1.0) < TOL
+    assert np.array_equal((got[ok] <= 1.0)[~band], (want[ok] <= 1.0)[~band]), "pass/fail differs"
+    if counts is not None:
+        rate, n_eval, n_pass = counts
+        gg = got[~np.isnan(got)]
+        assert n_eval == gg.size
+        assert n_pass == int((gg <= 1.0).sum())
+    return worst
+
+
+# --------------------------------------------------------------------------
+# Small grids, compared in full
+# --------------------------------------------------------------------------
+
+def test_plane_128_full():
+    p = synth.workload("plane_128")
+    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, p.criteria)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, p.criteria)
+    assert_parity(got, want, counts)
+    assert st["n_eval"] > 1000
+
+
+@pytest.mark.parametrize("local", [False, True])
+def test_plane_ragged(local):
+    p = synth.make_pair_2d(shape=(37, 53), spacing=(1.25, 0.8), seed=11, shift_mm=(0.4, -1.1),
+                           scale=0.97, noise_sd=0.01)
+    crit = synth.Criteria(0.02, 2.0, local=local, cutoff_frac=0.2)
+    got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
+CRITS = [synth.Criteria(0.03, 3.0), synth.Criteria(0.02, 2.0), synth.Criteria(0.01, 1.0, local=True),
+         synth.Criteria(0.01, 3.0), synth.Criteria(0.03, 1.0, cutoff_frac=0.0)]
+
+
+@pytest.mark.parametrize("crit", CRITS, ids=lambda c: c.label.replace("/", "_").replace(" ", "_"))
+def test_volume_small_full(crit):
+    p = synth.workload("imrt_small")
+    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, crit)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
+def test_volume_ragged_anisotropic():
+    p = synth.make_pair_3d(shape=(19, 33, 29), spacing=(3.0, 2.0, 1.5), seed=21,
+                           shift_mm=(1.0, -0.5, 2.0), scale=1.05)
+    crit = synth.Criteria(0.02, 2.0, cutoff_frac=0.05)
+    got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+@pytest.mark.parametrize("sort_tail", [0, 1])
+def test_launch_shapes_agree(lanes, sort_tail):
+    p = synth.workload("imrt_small")
+    crit = synth.Criteria(0.01, 1.0, local=True)
+    got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit,
+                               {"lanes_per_voxel": lanes, "sort_tail": sort_tail})
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_truncated_table_box_scan(ndim):
+    # A tiny table forces most voxels past its end, into the box scan.
+    if ndim == 2:
+        p = synth.make_pair_2d(shape=(30, 26), seed=5, shift_mm=(2.0, 1.0), scale=1.06)
+    else:
+        p = synth.make_pair_3d(shape=(14, 18, 16), spacing=(2.0, 2.0, 2.0), seed=6,
+                               shift_mm=(1.0, 2.0, 2.5), scale=1.06)
+    crit = synth.Criteria(0.01, 1.0, local=True)
+    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"table_cap": 16})
+    assert st["overflow_voxels"] > 0
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
+def test_fp64_redo_paths():
+    p = synth.workload("imrt_small")
+    crit = synth.Criteria(0.01, 1.0, local=True)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    g_off, c_off, s_off = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"fp64_tau_exp10": 0})
+    g_all, c_all, s_all = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"fp64_tau_exp10": 1})
+    assert s_off["fp64_cells"] == 0
+    assert s_all["fp64_cells"] > 0
+    assert_parity(g_off, want, c_off)
+    e_all = assert_parity(g_all, want, c_all)
+    assert e_all <= 1e-5
+
+
+def test_identical_doses_zero_and_flat_shift():
+    p = synth.workload("imrt_small")
+    crit = synth.Criteria(0.03, 3.0)
+    got, counts, _ = gpu_gamma(p.ref, p.ref, p.spacing, crit)
+    ok = ~np.isnan(got)
+    assert ok.sum() > 100 and np.all(got[ok] == 0.0)
+    ref = np.full((9, 10, 11), 0.5, np.float32)
+    ev = ref + np.float32(0.0625)
+    crit = synth.Criteria(0.02, 3.0, dose_norm=1.0, cutoff_frac=0.0)
+    got, counts, _ = gpu_gamma(ref, ev, (2.5, 1.0, 2.0), crit)
+    np.testing.assert_allclose(got, 0.0625 / f32(0.02), rtol=2e-6)
+
+
+def test_linear_ramp_closed_form():
+    shape, sp = (12, 13, 14), (2.0, 1.25, 1.5)
+    grad = np.array([0.004, 0.009, -0.006])
+    coords = np.meshgrid(*[np.arange(n) * h for n, h in zip(shape, sp)], indexing="ij")
+    ramp = 0.6 + sum(g_ * c for g_, c in zip(grad, coords))
+    ref = ramp.astype(np.float32)
+    ev = (ramp - 0.0125).astype(np.float32)
+    crit = synth.Criteria(0.02, 3.0, dose_norm=1.0, cutoff_frac=0.0)
+    got, _, _ = gpu_gamma(ref, ev, sp, crit)
+    dD = f32(0.02)
+    want = 0.0125 / dD / np.sqrt(1.0 + np.sum((grad * 3.0 / dD) ** 2))
+    inner = tuple(slice(3, -3) for _ in shape)
+    np.testing.assert_allclose(got[inner], want, atol=2e-5)
+
+
+@pytest.mark.parametrize("name", ["freudenthal_corner_2d.txt", "freudenthal_corner_3d.txt"])
+def test_tiny_golden_grids(name):
+    ref, ev, sp, c, expect = brute.read_golden(os.path.join(GOLDEN, name))
+    crit = synth.Criteria(c["dd_frac"], c["dta_mm"], cutoff_frac=c["cutoff_frac"],
+                          dose_norm=c["dose_norm"])
+    got, _, _ = gpu_gamma(ref, ev, sp, crit)
+    for flat, value, expr in expect:
+        assert abs(got.ravel()[flat] - value) <= 1e-6, expr
+
+
+def test_non_finite_input_reported():
+    import paper_1012_1900_gb300 as g
+    p = synth.workload("imrt_small")
+    ev = p.eval.copy()
+    ev[3, 4, 5] = np.nan
+    with pytest.raises(g.GammaError) as e:
+        gpu_gamma(p.ref, ev, p.spacing, p.criteria)
+    assert e.value.code == -3
+
+
+def test_repeat_runs_identical_and_counters_reset():
+    p = synth.workload("imrt_small")
+    outs, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, synth.Criteria(0.02, 2.0), runs=3)
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)
+    assert np.array_equal(outs[0], outs[2], equal_nan=True)
+    assert counts[1] == int((~np.isnan(outs[2])).sum())
+
+
+def test_run_host_matches_device_run():
+    import paper_1012_1900_gb300 as g
+    p = synth.workload("imrt_small")
+    crit = synth.Criteria(0.03, 3.0)
+    dev_out, dev_counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit)
+    h = g.gamma_create(None, None, 3, p.ref.shape, p.spacing,
+                       g.criteria(crit.dd_frac, crit.dta_mm, cutoff_frac=crit.cutoff_frac))
+    try:
+        ref = torch.from_numpy(p.ref).pin_memory()
+        ev = torch.from_numpy(p.eval).pin_memory()
+        out = torch.empty_like(ref).pin_memory()
+        g.gamma_run_host(h, ref, ev, out)
+        counts = g.gamma_pass_rate(h)
+    finally:
+        g.gamma_destroy(h)
+    assert np.array_equal(out.numpy().astype(np.float64), dev_out, equal_nan=True)
+    assert counts == dev_counts
+
+
+def test_stats_mode_counts_cells():
+    p = synth.workload("imrt_small")
+    crit = synth.Criteria(0.01, 1.0, local=True)
+    _, _, st = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"stats": 1})
+    assert st["tail_voxels"] > 0
+    assert st["cells_visited"] > 0 and st["cells_pruned"] > 0
+    # keyed cells whose corner falls outside the grid are neither visited nor pruned
+    assert st["cells_keyed"] >= st["cells_visited"] + st["cells_pruned"]
+
+
+# --------------------------------------------------------------------------
+# Full-size workloads: sampled voxels + properties at any size
+# --------------------------------------------------------------------------
+
+def _sample(got, n, seed):
+    rng = np.random.default_rng(seed)
+    ev = np.nonzero(~np.isnan(got.ravel()))[0]
+    pick = rng.choice(ev, min(n, ev.size), replace=False)
+    # always include the largest gammas (the longest searches)
+    top = ev[np.argsort(got.ravel()[ev])[-200:]]
+    return np.unique(np.concatenate([pick, top]))
+
+
+def _full_size_check(p, crit, n_sample, table_cap=1 << 22):
+    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, crit)
+    ok = ~np.isnan(got)
+    # mask from the cutoff rule, in float32 as specified
+    dn = np.float32(crit.dose_norm) if crit.dose_norm > 0 else p.ref.max()
+    thr = np.float32(np.float32(crit.cutoff_frac) * dn)
+    mask = p.ref >= thr
+    if crit.local:
+        mask &= p.ref > 0
+    assert np.array_equal(ok, mask)
+    # 0 <= gamma <= gamma0 everywhere
+    dD = np.broadcast_to(np.float32(crit.dd_frac) * (p.ref if crit.local else dn),
+                         p.ref.shape).astype(np.float64)
+    g0 = np.abs(p.eval.astype(np.float64) - p.ref)[ok] / dD[ok]
+    assert np.all(got[ok] >= 0)
+    assert np.all(got[ok] <= g0 * (1 + 1e-6) + 1e-6)
+    idx = _sample(got, n_sample, 7)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit, idx=idx, table_cap=table_cap)
+    worst = assert_parity(got.ravel()[idx], want)
+    rate, n_eval, n_pass = counts
+    assert n_eval == int(ok.sum()) and n_pass == int((got[ok] <= 1).sum())
+    return worst, st
+
+
+def test_imrt_160_3pct3mm_sampled():
+    p = synth.workload("imrt_160")
+    worst, st = _full_size_check(p, p.criteria, 20000)
+    assert st["tail_voxels"] > 0
+
+
+def test_imrt_160_2pct2mm_sampled():
+    p = synth.workload("imrt_160_2mm2pct")
+    _full_size_check(p, p.criteria, 20000)
+
+
+def test_imrt_320_local_sampled():
+    p = synth.workload("imrt_320_local")
+    _full_size_check(p, p.criteria, 4000, table_cap=1 << 20)
