@@ -53,7 +53,8 @@ typedef enum {
     GAMMA_ERR_CUDA = -7,            /* a CUDA runtime call failed (see gamma_last_cuda_error) */
     GAMMA_ERR_NOT_RUN = -8,         /* results requested before any run */
     GAMMA_ERR_MODEL = -9,           /* model file missing, malformed or of the wrong shape */
-    GAMMA_ERR_QUEUE_FULL = -10      /* internal work queue overflowed (results incomplete) */
+    GAMMA_ERR_QUEUE_FULL = -10,     /* internal work queue overflowed (results incomplete) */
+    GAMMA_ERR_TOO_LARGE = -11       /* grid larger than gamma_run_noalloc's fixed scratch */
 } gamma_status;
 
 typedef enum { GAMMA_GLOBAL = 0, GAMMA_LOCAL = 1 } gamma_mode;
@@ -180,6 +181,41 @@ const char *gamma_last_cuda_error(void);
 
 /* Library version string. */
 const char *gamma_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Allocation-free variant.  The paper has no counterpart: this entry point
+ * exists for callers that must not have a library allocate device memory --
+ * applications whose device memory is owned by their own pool allocator (a
+ * treatment-planning or QA system, a deep-learning framework operator), for
+ * which a hidden cudaMalloc/cudaFree would break their memory budget and may
+ * implicitly synchronise the whole device.
+ *
+ * gamma_run_noalloc computes the same gamma map as gamma_create + gamma_run
+ * (global or local criteria, cutoff, NaN outside it) without allocating any
+ * memory: no cudaMalloc, cudaFree, or heap allocation.  Its scratch (counters,
+ * cell table, queue) is one fixed device array inside the library, which every
+ * GPU that loads the library holds (about 20.3 MB) until the process exits.
+ *  ref_dev, eval_dev  device, float32, (nz, ny, nx) C-order, borrowed.
+ *  gamma_out_dev      device, float32, nz*ny*nx, written in full; caller-owned.
+ *  ndim, shape,       as in gamma_create; at most GAMMA_NOALLOC_MAX_VOXELS
+ *  spacing_mm, crit   voxels (else GAMMA_ERR_TOO_LARGE).
+ *  cuda_stream        cudaStream_t of the work (NULL = legacy default stream).
+ *  n_eval, n_pass     optional (may be NULL); when either is given the call
+ *                     synchronises the stream and returns the counts.
+ * Every call shares the one scratch array and leaves its contents there:
+ * calls whose GPU work overlaps (different streams, several host threads)
+ * race on it and give wrong results, so serialise them.  The first call on
+ * each device looks up the array's device address with that device current;
+ * make it before any stream capture begins.  Voxels whose search runs past the
+ * GAMMA_NOALLOC_MAX_TABLE-entry table finish with the exact box scan.
+ * Errors: INVALID_ARG, SHAPE, TOO_LARGE, TABLE_TOO_LARGE, NAN_INPUT (only when
+ * counts are requested), CUDA. */
+#define GAMMA_NOALLOC_MAX_VOXELS 4194304
+#define GAMMA_NOALLOC_MAX_TABLE 32768
+int gamma_run_noalloc(const float *ref_dev, const float *eval_dev, float *gamma_out_dev, int ndim,
+                      const int64_t shape[3], const float spacing_mm[3],
+                      const gamma_criteria *crit, void *cuda_stream, int64_t *n_eval,
+                      int64_t *n_pass);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,8 @@ __all__ = [
     "GammaError", "gamma_criteria", "gamma_stats", "gamma_create", "gamma_set_inputs",
     "gamma_run", "gamma_run_host", "gamma_pass_rate", "gamma_get_stats", "gamma_get_timings",
     "gamma_set_option",
-    "gamma_destroy", "gamma_strerror", "gamma_version", "library_path", "criteria",
+    "gamma_run_noalloc", "gamma_destroy", "gamma_strerror", "gamma_version", "library_path",
+    "criteria",
     "GLOBAL", "LOCAL",
 ]
 
@@ -82,6 +83,8 @@ def _load():
     lib.gamma_get_stats.argtypes = [vp, ctypes.POINTER(gamma_stats)]
     lib.gamma_get_timings.argtypes = [vp, ctypes.POINTER(gamma_timings)]
     lib.gamma_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
+    lib.gamma_run_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, i64p, f32p,
+                                      ctypes.POINTER(gamma_criteria), vp, i64p, i64p]
     lib.gamma_destroy.argtypes = [vp]
     lib.gamma_destroy.restype = None
     lib.gamma_strerror.argtypes = [ctypes.c_int]
@@ -187,6 +190,21 @@ def gamma_get_timings(h: int) -> dict:
 
 def gamma_set_option(h: int, key: str, value: int) -> None:
     _check(_lib.gamma_set_option(h, key.encode(), int(value)), f"gamma_set_option({key})")
+
+
+def gamma_run_noalloc(ref_dev, eval_dev, gamma_out_dev, ndim: int, shape: Sequence[int],
+                      spacing_mm: Sequence[float], crit: gamma_criteria, stream=None,
+                      counts: bool = True):
+    """One gamma map with no allocation (the library's fixed scratch array).
+    Returns (n_eval, n_pass) when counts is true (synchronises), else None."""
+    shp = (ctypes.c_int64 * 3)(*[int(s) for s in shape])
+    sp = (ctypes.c_float * 3)(*[float(s) for s in spacing_mm])
+    ne, npass = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.gamma_run_noalloc(_dev_ptr(ref_dev), _dev_ptr(eval_dev), _dev_ptr(gamma_out_dev),
+                                  int(ndim), shp, sp, ctypes.byref(crit), _stream_ptr(stream),
+                                  ctypes.byref(ne) if counts else None,
+                                  ctypes.byref(npass) if counts else None), "gamma_run_noalloc")
+    return (ne.value, npass.value) if counts else None
 
 
 def gamma_destroy(h: Optional[int]) -> None:

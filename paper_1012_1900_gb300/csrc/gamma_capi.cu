@@ -496,6 +496,7 @@ const char* gamma_strerror(int code)
     case GAMMA_ERR_NOT_RUN: return "no run yet";
     case GAMMA_ERR_MODEL: return "bad model";
     case GAMMA_ERR_QUEUE_FULL: return "work queue overflow";
+    case GAMMA_ERR_TOO_LARGE: return "grid exceeds the fixed scratch of gamma_run_noalloc";
     default: return "unknown error";
     }
 }
