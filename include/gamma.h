@@ -166,6 +166,8 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *  "sort_tail"        0: process queued voxels in discovery order instead
  *                     of most-expensive-first (ablation)
  *  "timing"           1: record per-phase CUDA events (gamma_get_timings)
+ *  "shell_blocks_per_sm"  1 or 2: register budget of the key-0 cell kernel
+ *                     (2 = 128 registers a thread, two blocks per SM)
  * Errors: INVALID_ARG (unknown key or value), TABLE_TOO_LARGE, OOM. */
 int gamma_set_option(gamma_handle h, const char *key, int64_t value);
 

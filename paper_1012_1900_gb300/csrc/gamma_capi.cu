@@ -90,6 +90,7 @@ struct gamma_ctx {
     int stats = 0;
     int sort_tail = 1;
     int timing = 0;
+    int shell_minblocks = 2;
     // per-phase events: 0 start, 1 after h2d, 2 after prepare, 3 after shell,
     // 4 after order, 5 after tail, 6 after d2h
     cudaEvent_t tev[7] = {};
@@ -227,6 +228,7 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.tail_bucket = h->tail_bucket;
     P.tail_sorted = h->tail_sorted;
     P.sort_tail = h->sort_tail;
+    P.shell_minblocks = h->shell_minblocks;
     return P;
 }
 
@@ -385,6 +387,7 @@ int gamma_pass_rate(gamma_handle h, double* rate, int64_t* n_eval, int64_t* n_pa
     Counters c;
     if (int rc = read_counters(h, &c)) return rc;
     if (c.flags & gk::kFlagNonFinite) return GAMMA_ERR_NAN_INPUT;
+    if (c.flags & gk::kFlagTimeout) return GAMMA_ERR_TIMEOUT;
     if (c.flags & gk::kFlagTailFull) return GAMMA_ERR_QUEUE_FULL;
     if (n_eval) *n_eval = (int64_t)c.n_eval;
     if (n_pass) *n_pass = (int64_t)c.n_pass;
@@ -459,6 +462,11 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
     if (!std::strcmp(key, "stats")) {
         if (value != 0 && value != 1) return GAMMA_ERR_INVALID_ARG;
         h->stats = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "shell_blocks_per_sm")) {
+        if (value != 1 && value != 2) return GAMMA_ERR_INVALID_ARG;
+        h->shell_minblocks = (int)value;
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "timing")) {

@@ -42,8 +42,8 @@ namespace gk {
 
 constexpr float kInf = __builtin_huge_valf();
 
-__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__host__ __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
@@ -67,7 +67,7 @@ struct MetricT {
 using Metric = MetricT<float>;
 
 template <int N, typename T>
-__device__ __forceinline__ void cell_geom(int cx, int cy, int cz, const MetricT<T>& mt,
+__host__ __device__ __forceinline__ void cell_geom(int cx, int cy, int cz, const MetricT<T>& mt,
                                           CellGeom<T>& g)
 {
     const int c[3] = {cx, cy, cz};

@@ -13,6 +13,7 @@ constexpr int kNumBuckets = 32;
 enum : uint32_t {
     kFlagNonFinite = 1u,     // a NaN or Inf dose was seen
     kFlagTailFull = 2u,      // the tail queue overflowed its capacity
+    kFlagTimeout = 4u,       // a bounded wait on a tile copy gave up
 };
 
 // One entry of the radially sorted cell table (Algorithm A1 steps 2-3):
@@ -69,6 +70,15 @@ __host__ __device__ inline float fdec(unsigned int e)
     return c.f;
 }
 
+// Constants of the 2^n key-0 cells around a voxel (lower-corner offsets
+// c in {-1, 0}^n, indexed by the mask of axes where c = -1), computed on the
+// host by the shell launcher.
+struct ShellConst {
+    CellGeom<float> g[8];
+    float far2;   // squared spatial distance from the voxel to the nearest face
+                  // of these cells that does not contain it (rounded down)
+};
+
 // Everything a launch needs about one dose pair.
 struct Problem {
     const float* ref;
@@ -96,6 +106,8 @@ struct Problem {
     unsigned char* tail_bucket;  // their cost buckets
     unsigned int* tail_sorted;   // tail voxels, most expensive bucket first
     int sort_tail;               // 0: keep discovery order (ablation)
+    int shell_minblocks;         // k_shell variant: 1 (no spills) or 2 (128 registers); 0 = 2
+    ShellConst shell;            // filled by launch_shell
 };
 
 // Launchers (gamma_kernels.cu).  All are stream-ordered and allocate nothing.

@@ -16,10 +16,15 @@
 //               early exit of A1 step 4b-ii (key >= gamma) and a per-cell
 //               lower bound sqrt(key^2 + dose gap^2)
 // No kernel waits on another block or allocates memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "gamma_internal.h"
+#include "gamma_tma.cuh"
 
 namespace gk {
 
@@ -86,120 +91,310 @@ __device__ __noinline__ float cell_redo_f64(const float* __restrict__ ev, long l
 }
 
 // --------------------------------------------------------------------------
-// k_shell: gamma0 and the key-0 cells, thread per voxel
+// k_shell: gamma0 and the key-0 cells, one block per tile of voxels
 // --------------------------------------------------------------------------
 
+// Tile of voxels per block (x fastest; a warp is one x row) and its halo box
+// in shared memory.  The box starts 4 voxels left of the tile so that the TMA
+// x coordinate stays a multiple of 4 floats (16 bytes).
 template <int N>
-__global__ void __launch_bounds__(256) k_shell(const __grid_constant__ Problem P)
+struct ShellTile {
+    static constexpr int TX = 32, TY = N == 3 ? 4 : 8, TZ = N == 3 ? 2 : 1;
+    static constexpr int BX = 40, BY = TY + 2, BZ = N == 3 ? TZ + 2 : 1;
+    static constexpr int ELEMS = BX * BY * BZ;
+};
+
+// A face owned by the cell whose lower corner sits at -S from the voxel
+// contains the voxel iff the voxel (vertex S of the cell) is on its chain.
+template <int M, int U1, int U2, int U3>
+constexpr bool face_has_vertex(int S)
 {
-    constexpr int NB = N == 3 ? 27 : 9;
+    return S == 0 || S == U1 || (M >= 2 && S == U2) || (M >= 3 && S == U3);
+}
+
+template <bool NEAR, int S, int M, int U1, int U2, int U3>
+__device__ __forceinline__ void apply_face_sel(Face<M, U1, U2, U3>, const float (&q)[8],
+                                               uint32_t ok, const CellGeom<float>& g,
+                                               const float (&kappa)[8], float tau, float& best,
+                                               bool& ill)
+{
+    if constexpr (face_has_vertex<M, U1, U2, U3>(S) == NEAR)
+        best = fminf(best, face_d2<M, U1, U2, U3, float>(q, ok, g, kappa, tau, ill));
+}
+
+template <bool NEAR, int S, typename... Fs>
+__device__ __forceinline__ void apply_sel(std::tuple<Fs...>*, const float (&q)[8], uint32_t ok,
+                                          const CellGeom<float>& g, const float (&kappa)[8],
+                                          float tau, float& best, bool& ill)
+{
+    (apply_face_sel<NEAR, S>(Fs{}, q, ok, g, kappa, tau, best, ill), ...);
+}
+
+// The faces of key-0 cell S (lower corner at -S from the voxel) that contain
+// the voxel (NEAR) or not.  S is a compile-time constant, so the face subset,
+// the shared-memory offsets and the cell constants are all resolved at compile
+// time.  A cell flagged ill-conditioned is redone in FP64 (all its faces) and
+// marked in `done64` so the other pass skips it.
+template <int N, bool NEAR, int S>
+__device__ __forceinline__ void shell_cell(const Problem& P, const float* tile, int tix,
+                                           uint32_t inm, uint32_t inp, float dr, float inv,
+                                           float dnorm, long long v, float& best, uint32_t& done64)
+{
+    using T = ShellTile<N>;
+    if (!NEAR && ((done64 >> S) & 1u)) return;
+    float q[8];
+    uint32_t ok = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        q[u] = 0.f;
+        if (u < (1 << N)) {
+            bool in = true;
+            int off = 0;
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const int d = ((u >> a) & 1) - ((S >> a) & 1);              // -1, 0, +1
+                in = in && (d < 0 ? ((inm >> a) & 1u) : d > 0 ? ((inp >> a) & 1u) : 1u);
+                off += d * (a == 0 ? 1 : a == 1 ? T::BX : T::BX * T::BY);
+            }
+            q[u] = (tile[tix + off] - dr) * inv;       // halo entries outside the grid are 0
+            ok |= (in ? 1u : 0u) << u;
+        }
+    }
+    if (!(ok & 1u)) return;
+    const CellGeom<float>& g = P.shell.g[S];
+    bool ill = false;
+    float cb = kInf;
+    // the cell's corner vertex: the voxel itself when S == 0, else a far face
+    if constexpr ((S == 0) == NEAR) cb = fmaf(q[0], q[0], g.tsum[0]);
+    apply_sel<NEAR, S>((typename FaceList<N>::type*)nullptr, q, ok, g, P.mt.kappa, P.tau, cb, ill);
+    if (ill) {
+        const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+        const double drd = dr;
+        const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
+        constexpr int cx = -(S & 1), cy = -((S >> 1) & 1), cz = -((S >> 2) & 1);
+        const long long p = v + cx + cy * sy + cz * sz;
+        cb = cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd, P.mtd,
+                              &P.ctr->fp64_cells);
+        done64 |= 1u << S;
+    }
+    best = fminf(best, cb);
+}
+
+template <int N, bool NEAR, int... Ss>
+__device__ __forceinline__ float shell_pass_seq(std::integer_sequence<int, Ss...>, const Problem& P,
+                                                const float* tile, int tix, uint32_t inm,
+                                                uint32_t inp, float dr, float inv, float dnorm,
+                                                long long v, float best, uint32_t& done64)
+{
+    (shell_cell<N, NEAR, Ss>(P, tile, tix, inm, inp, dr, inv, dnorm, v, best, done64), ...);
+    return best;
+}
+
+template <int N, bool NEAR>
+__device__ __forceinline__ float shell_pass(const Problem& P, const float* tile, int tix,
+                                            uint32_t inm, uint32_t inp, float dr, float inv,
+                                            float dnorm, long long v, float best, uint32_t& done64)
+{
+    return shell_pass_seq<N, NEAR>(std::make_integer_sequence<int, (1 << N)>{}, P, tile, tix, inm,
+                                   inp, dr, inv, dnorm, v, best, done64);
+}
+
+template <int N, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_shell(const __grid_constant__ Problem P, const __grid_constant__ CUtensorMap tmap, int use_tma,
+            int ntiles)
+{
+    using T = ShellTile<N>;
+    constexpr int NC = 1 << N;
+    __shared__ __align__(128) float tile[2][T::ELEMS];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ unsigned int sh_best[256];      // gamma^2 bits of the tile's voxels
+    __shared__ float sh_dr[256], sh_inv[256];
+    __shared__ unsigned short sh_far[256];     // voxels that still need the far faces
+    __shared__ unsigned int sh_nfar;
     __shared__ unsigned int sh_hist[kNumBuckets];
     __shared__ unsigned long long sh_eval, sh_pass;
     __shared__ unsigned int sh_rmax;
-    if (threadIdx.x < kNumBuckets) sh_hist[threadIdx.x] = 0;
-    if (threadIdx.x == 0) { sh_eval = 0; sh_pass = 0; sh_rmax = 0; }
-    __syncthreads();
 
+    const int ntx = (P.nx + T::TX - 1) / T::TX, nty = (P.ny + T::TY - 1) / T::TY;
     const int lane = threadIdx.x & 31;
+    const int lx = lane, ly = (threadIdx.x >> 5) % T::TY, lz = (threadIdx.x >> 5) / T::TY;
     const float dnorm = resolve_dnorm(P);
     const float thr = P.cutoff_frac * dnorm;
     const float k1 = P.t1 < P.ntable ? P.table[P.t1].key : kInf;
-    const float k1sq = k1 * k1;
     const float rc2 = P.r_cover * P.r_cover;
     const bool table_ends = P.t1 >= P.ntable;
     const long long sy = P.nx, sz = (long long)P.nx * P.ny;
-    unsigned int my_eval = 0, my_pass = 0;
-    float my_rmax = 0.f;
 
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < P.nvox;
-         base += stride) {
-        const long long v = base + lane;
+    if (threadIdx.x < kNumBuckets) sh_hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        sh_eval = 0;
+        sh_pass = 0;
+        sh_rmax = 0;
+        sh_nfar = 0;
+        if (use_tma) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            mbar_fence_init();
+        }
+    }
+    __syncthreads();
+
+    auto tile_origin = [&](int t, int& x0, int& y0, int& z0) {
+        x0 = (t % ntx) * T::TX;
+        y0 = ((t / ntx) % nty) * T::TY;
+        z0 = (t / ntx / nty) * T::TZ;
+    };
+    auto issue = [&](int t, int b) {
+        if (t >= ntiles) return;
+        int x0, y0, z0;
+        tile_origin(t, x0, y0, z0);
+        mbar_arrive_expect_tx(&bar[b], T::ELEMS * (uint32_t)sizeof(float));
+        if (N == 3) tma_load_3d(tile[b], &tmap, x0 - 4, y0 - 1, z0 - 1, &bar[b]);
+        else tma_load_2d(tile[b], &tmap, x0 - 4, y0 - 1, &bar[b]);
+    };
+    if (use_tma && threadIdx.x == 0) issue(blockIdx.x, 0);
+    uint32_t parity = 0;                 // bit b: phase of bar[b] to wait for
+    unsigned my_eval = 0, my_pass = 0;
+    float my_rmax = 0.f;
+    int buf = 0;
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+        int x0, y0, z0;
+        tile_origin(t, x0, y0, z0);
+        float* tl = tile[buf];
+        // ---- stage: prefetch the next tile, wait for this one ----
+        if (use_tma) {
+            if (threadIdx.x == 0) issue(t + gridDim.x, buf ^ 1);
+            const bool ok = mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+            parity ^= 1u << buf;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicOr(&P.ctr->flags, kFlagTimeout);
+                    // let this block's own copies land before it leaves
+                    mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+                    mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
+                }
+                break;
+            }
+        } else {
+            for (int i = threadIdx.x; i < T::ELEMS; i += blockDim.x) {
+                const int bx = i % T::BX, by = (i / T::BX) % T::BY, bz = i / (T::BX * T::BY);
+                const int gx = x0 - 4 + bx, gy = y0 - 1 + by, gz = (N == 3 ? z0 - 1 : 0) + bz;
+                const bool in = (unsigned)gx < (unsigned)P.nx && (unsigned)gy < (unsigned)P.ny &&
+                                (N == 2 || (unsigned)gz < (unsigned)P.nz);
+                tl[i] = in ? __ldg(P.ev + ((long long)gz * P.ny + gy) * P.nx + gx) : 0.f;
+            }
+            __syncthreads();
+        }
+
+        // ---- phase A: gamma0 and the faces that contain the voxel ----
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        const bool inside = x < P.nx && y < P.ny && z < P.nz;
+        const long long v = inside ? ((long long)z * P.ny + y) * P.nx + x : 0;
+        float dr = 0.f, inv = 0.f, best = 0.f;
+        bool act = false;
+        if (inside) {
+            dr = __ldg(P.ref + v);
+            act = is_evaluated(P, dr, thr);
+            if (!act) P.out[v] = __int_as_float(0x7fc00000);
+        }
+        const int tix = ((N == 3 ? lz + 1 : 0) * T::BY + (ly + 1)) * T::BX + (lx + 4);
+        uint32_t inm = 0, inp = 0;       // neighbours at -1 / +1 inside the grid, per axis
+        inm |= (x > 0) ? 1u : 0u;
+        inp |= (x + 1 < P.nx) ? 1u : 0u;
+        inm |= (y > 0) ? 2u : 0u;
+        inp |= (y + 1 < P.ny) ? 2u : 0u;
+        if (N == 3) {
+            inm |= (z > 0) ? 4u : 0u;
+            inp |= (z + 1 < P.nz) ? 4u : 0u;
+        }
+        if (act) {
+            const float dD = P.dd_frac * (P.local ? dr : dnorm);
+            inv = 1.0f / dD;
+            const float q0 = (tl[tix] - dr) * inv;
+            best = q0 * q0;
+            my_rmax = fmaxf(my_rmax, fabsf(q0));
+        }
+        uint32_t done64 = 0;
+        if (__any_sync(kFull, act && best > 0.f))
+            best = act ? shell_pass<N, true>(P, tl, tix, inm, inp, dr, inv, dnorm, v, best, done64)
+                       : best;
+
+        // ---- phase B: far faces, shared by the whole block ----
+        sh_best[threadIdx.x] = __float_as_uint(best);
+        sh_dr[threadIdx.x] = dr;
+        sh_inv[threadIdx.x] = inv;
+        if (act && best > P.shell.far2) sh_far[atomicAdd(&sh_nfar, 1u)] = (unsigned short)threadIdx.x;
+        __syncthreads();
+        const unsigned nitems = sh_nfar * NC;
+        for (unsigned it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int lv = sh_far[it / NC];
+            const int sc = (int)(it % NC);
+            const int vx = x0 + (lv & 31), vy = y0 + (lv >> 5) % T::TY, vz = z0 + (lv >> 5) / T::TY;
+            const int cx = -(sc & 1), cy = -((sc >> 1) & 1), cz = N == 3 ? -((sc >> 2) & 1) : 0;
+            const int px = vx + cx, py = vy + cy, pz = vz + cz;
+            if (px < 0 || py < 0 || pz < 0) continue;           // corner outside the grid
+            const bool ex = px + 1 < P.nx, ey = py + 1 < P.ny, ez = N == 3 && pz + 1 < P.nz;
+            const int lvx = lv & 31, lvy = (lv >> 5) % T::TY, lvz = (lv >> 5) / T::TY;
+            const int cix = ((N == 3 ? lvz + 1 + cz : 0) * T::BY + (lvy + 1 + cy)) * T::BX + (lvx + 4 + cx);
+            const float vdr = sh_dr[lv], vinv = sh_inv[lv];
+            float q[8];
+            uint32_t ok = 0;
+            float qmin = kInf, qmax = -kInf;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                q[u] = 0.f;
+                if (u < NC) {
+                    const bool present = (!(u & 1) || ex) && (!(u & 2) || ey) && (!(u & 4) || ez);
+                    if (present) {
+                        const int o = ((u & 1) ? 1 : 0) + ((u & 2) ? T::BX : 0) + ((u & 4) ? T::BX * T::BY : 0);
+                        q[u] = (tl[cix + o] - vdr) * vinv;
+                        qmin = fminf(qmin, q[u]);
+                        qmax = fmaxf(qmax, q[u]);
+                        ok |= 1u << u;
+                    }
+                }
+            }
+            const float vbest = __uint_as_float(((volatile unsigned int*)sh_best)[lv]);
+            const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
+            if (gap * gap >= vbest) continue;                    // dose lower bound
+            CellGeom<float> g;
+            cell_geom<N, float>(cx, cy, cz, P.mt, g);
+            bool ill = false;
+            float cb = cell_min_d2<N, float>(q, ok, g, P.mt, P.tau, kInf, ill);
+            if (ill) {
+                const double drd = vdr;
+                const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
+                const long long p = ((long long)pz * P.ny + py) * P.nx + px;
+                cb = cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd, P.mtd,
+                                      &P.ctr->fp64_cells);
+            }
+            atomicMin(&sh_best[lv], __float_as_uint(cb));
+        }
+        __syncthreads();
+        if (act) best = __uint_as_float(sh_best[threadIdx.x]);
+
+        // ---- phase C: finish or queue ----
         bool tail = false;
         int bucket = 0;
-        if (v < P.nvox) {
-            const int x = (int)(v % P.nx);
-            const long long r1 = v / P.nx;
-            const int y = (int)(r1 % P.ny);
-            const int z = (int)(r1 / P.ny);
-            const float dr = __ldg(P.ref + v);
-            if (!is_evaluated(P, dr, thr)) {
-                P.out[v] = __int_as_float(0x7fc00000);
+        if (act) {
+            tail = (best > k1 * k1) || (table_ends && best > rc2);
+            if (tail) {
+                P.out[v] = best;                       // gamma^2, finished by k_tail
+                const float gk_ = sqrtf(best);
+                int lo = P.t1, hi = P.ntable;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
+                }
+                const int cost = lo - P.t1;
+                bucket = cost <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)cost)));
             } else {
-                const float dD = P.dd_frac * (P.local ? dr : dnorm);
-                const float inv = 1.0f / dD;
-                float nb[NB];
-                uint32_t inb = 0;
-#pragma unroll
-                for (int dz = (N == 3 ? -1 : 0); dz <= (N == 3 ? 1 : 0); ++dz)
-#pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int k = (N == 3 ? (dz + 1) * 9 : 0) + (dy + 1) * 3 + (dx + 1);
-                            const bool in = (unsigned)(x + dx) < (unsigned)P.nx &&
-                                            (unsigned)(y + dy) < (unsigned)P.ny &&
-                                            (N == 2 || (unsigned)(z + dz) < (unsigned)P.nz);
-                            nb[k] = in ? (__ldg(P.ev + v + dx + dy * sy + dz * sz) - dr) * inv : 0.f;
-                            inb |= (in ? 1u : 0u) << k;
-                        }
-                constexpr int C = N == 3 ? 13 : 4;           // the voxel itself
-                float best = nb[C] * nb[C];
-                my_rmax = fmaxf(my_rmax, fabsf(nb[C]));
-                if (best > 0.f) {
-#pragma unroll
-                    for (int cz = (N == 3 ? -1 : 0); cz <= 0; ++cz)
-#pragma unroll
-                        for (int cy = -1; cy <= 0; ++cy)
-#pragma unroll
-                            for (int cx = -1; cx <= 0; ++cx) {
-                                float q[8];
-                                uint32_t ok = 0;
-#pragma unroll
-                                for (int u = 0; u < 8; ++u) {
-                                    q[u] = 0.f;
-                                    if (u < (1 << N)) {
-                                        const int ux = u & 1, uy = (u >> 1) & 1, uz = (u >> 2) & 1;
-                                        const int k = (N == 3 ? (cz + uz + 1) * 9 : 0) +
-                                                      (cy + uy + 1) * 3 + (cx + ux + 1);
-                                        q[u] = nb[k];
-                                        ok |= ((inb >> k) & 1u) << u;
-                                    }
-                                }
-                                if (!(ok & 1u)) continue;
-                                CellGeom<float> g;
-                                cell_geom<N, float>(cx, cy, cz, P.mt, g);
-                                bool ill = false;
-                                float cb = cell_min_d2<N, float>(q, ok, g, P.mt, P.tau, kInf, ill);
-                                if (ill) {
-                                    const double drd = dr;
-                                    const double invd =
-                                        1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
-                                    const long long p = v + cx + cy * sy + cz * sz;
-                                    cb = cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd,
-                                                          P.mtd, &P.ctr->fp64_cells);
-                                }
-                                best = fminf(best, cb);
-                            }
-                }
-                tail = (best > k1sq) || (table_ends && best > rc2);
-                if (tail) {
-                    P.out[v] = best;                       // gamma^2, finished by k_tail
-                    // estimated cost: table cells past the shell with key < gamma
-                    const float gk_ = sqrtf(best);
-                    int lo = P.t1, hi = P.ntable;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
-                    }
-                    const int cost = lo - P.t1;
-                    bucket = cost <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)cost)));
-                } else {
-                    const float gam = sqrtf(best);
-                    P.out[v] = gam;
-                    ++my_eval;
-                    my_pass += gam <= 1.f;             // decided on the value written
-                }
+                const float gam = sqrtf(best);
+                P.out[v] = gam;
+                ++my_eval;
+                my_pass += gam <= 1.f;                 // decided on the value written
             }
         }
         const unsigned tm = __ballot_sync(kFull, tail);
@@ -218,8 +413,10 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ Problem P
                 }
             }
         }
+        if (threadIdx.x == 0) sh_nfar = 0;
+        __syncthreads();                 // tile[buf] and the lists are free for reuse
     }
-    // block reductions
+
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         my_eval += __shfl_xor_sync(kFull, my_eval, o);
@@ -227,8 +424,8 @@ __global__ void __launch_bounds__(256) k_shell(const __grid_constant__ Problem P
         my_rmax = fmaxf(my_rmax, __shfl_xor_sync(kFull, my_rmax, o));
     }
     if (lane == 0) {
-        atomicAdd(&sh_eval, (unsigned long long)my_eval);
-        atomicAdd(&sh_pass, (unsigned long long)my_pass);
+        if (my_eval) atomicAdd(&sh_eval, (unsigned long long)my_eval);
+        if (my_pass) atomicAdd(&sh_pass, (unsigned long long)my_pass);
         atomicMax(&sh_rmax, fenc(my_rmax));
     }
     __syncthreads();
@@ -464,12 +661,186 @@ cudaError_t launch_prepare(const Problem& P, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_shell(const Problem& P, cudaStream_t s)
+// Distance from the origin to the closed simplex with vertices W[0..nv-1] in
+// R^3 (KKT enumeration over its faces), for the host-side shell constants.
+static double simplex_dist_host(const double (*W)[3], int nv)
 {
+    double best = INFINITY;
+    for (int mask = 1; mask < (1 << nv); ++mask) {
+        int idx[4], k = 0;
+        for (int i = 0; i < nv; ++i)
+            if (mask & (1 << i)) idx[k++] = i;
+        const double* w0 = W[idx[0]];
+        double E[3][3], G[3][3], r[3], mu[3] = {0, 0, 0};
+        const int m = k - 1;
+        for (int i = 0; i < m; ++i)
+            for (int a = 0; a < 3; ++a) E[i][a] = W[idx[i + 1]][a] - w0[a];
+        for (int i = 0; i < m; ++i) {
+            r[i] = 0;
+            for (int a = 0; a < 3; ++a) r[i] -= E[i][a] * w0[a];
+            for (int j = 0; j < m; ++j) {
+                G[i][j] = 0;
+                for (int a = 0; a < 3; ++a) G[i][j] += E[i][a] * E[j][a];
+            }
+        }
+        // Gaussian elimination (G is symmetric positive definite here)
+        bool okk = true;
+        for (int c = 0; c < m && okk; ++c) {
+            if (!(fabs(G[c][c]) > 1e-300)) { okk = false; break; }
+            for (int rr = c + 1; rr < m; ++rr) {
+                const double f = G[rr][c] / G[c][c];
+                for (int j = c; j < m; ++j) G[rr][j] -= f * G[c][j];
+                r[rr] -= f * r[c];
+            }
+        }
+        if (!okk) continue;
+        for (int c = m - 1; c >= 0; --c) {
+            double acc = r[c];
+            for (int j = c + 1; j < m; ++j) acc -= G[c][j] * mu[j];
+            mu[c] = acc / G[c][c];
+        }
+        double sum = 0;
+        bool valid = true;
+        for (int i = 0; i < m; ++i) {
+            sum += mu[i];
+            if (mu[i] < -1e-12) valid = false;
+        }
+        if (sum > 1 + 1e-12) valid = false;
+        if (!valid) continue;
+        double d2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            double p = w0[a];
+            for (int i = 0; i < m; ++i) p += mu[i] * E[i][a];
+            d2 += p * p;
+        }
+        best = fmin(best, sqrt(d2));
+    }
+    return best;
+}
+
+// Constants of the key-0 cells: per-cell geometry and the smallest spatial
+// distance from the voxel to a face of these cells that does not contain it.
+static void shell_constants(const Problem& P, ShellConst& sc)
+{
+    const int N = P.ndim;
+    for (int s = 0; s < 8; ++s) {
+        if (s >= (1 << N)) {
+            sc.g[s] = CellGeom<float>{};
+            continue;
+        }
+        const int cx = -(s & 1), cy = -((s >> 1) & 1), cz = -((s >> 2) & 1);
+        if (N == 3) cell_geom<3, float>(cx, cy, cz, P.mt, sc.g[s]);
+        else cell_geom<2, float>(cx, cy, 0, P.mt, sc.g[s]);
+    }
+    // every owned face is a chain 0 = u0 < u1 < ... < um of axis masks
+    const double hn[3] = {P.hn[0], P.hn[1], N == 3 ? P.hn[2] : 0.0};
+    double far = INFINITY;
+    const int full = (1 << N) - 1;
+    for (int s = 0; s < (1 << N); ++s) {
+        const int c[3] = {-(s & 1), -((s >> 1) & 1), -((s >> 2) & 1)};
+        // enumerate chains by their sequence of masks (up to N increments)
+        for (int u1 = 1; u1 <= full; ++u1)
+            for (int u2 = 0; u2 <= full; ++u2)
+                for (int u3 = 0; u3 <= full; ++u3) {
+                    int chain[4] = {0, u1, u2, u3};
+                    int m = 1;
+                    if (u2) {
+                        if ((u2 & u1) != u1 || u2 == u1) continue;
+                        m = 2;
+                        if (u3) {
+                            if ((u3 & u2) != u2 || u3 == u2) continue;
+                            m = 3;
+                        }
+                    } else if (u3) {
+                        continue;
+                    }
+                    bool has = false;
+                    for (int i = 0; i <= m; ++i) has = has || chain[i] == s;
+                    if (has) continue;
+                    double W[4][3];
+                    for (int i = 0; i <= m; ++i)
+                        for (int a = 0; a < 3; ++a)
+                            W[i][a] = (a < N) ? (c[a] + ((chain[i] >> a) & 1)) * hn[a] : 0.0;
+                    far = fmin(far, simplex_dist_host(W, m + 1));
+                }
+        if (s != 0) {           // the cell's own corner vertex, when it is not the voxel
+            double W[1][3];
+            for (int a = 0; a < 3; ++a) W[0][a] = (a < N) ? c[a] * hn[a] : 0.0;
+            far = fmin(far, simplex_dist_host(W, 1));
+        }
+    }
+    float f = (float)(far * far * (1.0 - 1e-6));
+    sc.far2 = f;
+}
+
+static bool encode_tile_map(const Problem& P, CUtensorMap* map)
+{
+    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = (EncodeFn)fn;
+    }
+    if (!encode) return false;
+    if (((uintptr_t)P.ev & 15u) != 0 || (P.nx % 4) != 0) return false;   // TMA alignment rules
+    if (P.ndim == 3) {
+        using T = ShellTile<3>;
+        const cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz};
+        const cuuint64_t strides[2] = {(cuuint64_t)P.nx * 4, (cuuint64_t)P.nx * P.ny * 4};
+        const cuuint32_t box[3] = {T::BX, T::BY, T::BZ};
+        const cuuint32_t es[3] = {1, 1, 1};
+        return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)P.ev, dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    using T = ShellTile<2>;
+    const cuuint64_t dims[2] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)P.nx * 4};
+    const cuuint32_t box[2] = {T::BX, T::BY};
+    const cuuint32_t es[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)P.ev, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
+{
+    Problem P = P0;
+    shell_constants(P, P.shell);
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    const int use_tma = encode_tile_map(P, &map) ? 1 : 0;
     const int sms = device_sm_count();
-    const int grid = grid_for(P.nvox, 256, sms * 64);
-    if (P.ndim == 3) k_shell<3><<<grid, 256, 0, s>>>(P);
-    else k_shell<2><<<grid, 256, 0, s>>>(P);
+    const int per_sm = P.shell_minblocks == 1 ? 1 : 2;
+    long long tiles;
+    if (P.ndim == 3) {
+        using T = ShellTile<3>;
+        tiles = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY) *
+                ((P.nz + T::TZ - 1) / T::TZ);
+    } else {
+        using T = ShellTile<2>;
+        tiles = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
+    }
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
+    if (P.ndim == 3) {
+        if (per_sm == 1) k_shell<3, 1><<<grid, 256, 0, s>>>(P, map, use_tma, (int)tiles);
+        else k_shell<3, 2><<<grid, 256, 0, s>>>(P, map, use_tma, (int)tiles);
+    } else {
+        if (per_sm == 1) k_shell<2, 1><<<grid, 256, 0, s>>>(P, map, use_tma, (int)tiles);
+        else k_shell<2, 2><<<grid, 256, 0, s>>>(P, map, use_tma, (int)tiles);
+    }
     return cudaGetLastError();
 }
 
