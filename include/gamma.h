@@ -166,6 +166,8 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *  "sort_tail"        0: process queued voxels in discovery order instead
  *                     of most-expensive-first (ablation)
  *  "timing"           1: record per-phase CUDA events (gamma_get_timings)
+ *  "graph"            batch handles: 0 launches directly instead of capturing
+ *                     and replaying a CUDA graph
  *  "shell_blocks_per_sm"  1 or 2: register budget of the key-0 cell kernel
  *                     (2 = 128 registers a thread, two blocks per SM)
  * Errors: INVALID_ARG (unknown key or value), TABLE_TOO_LARGE, OOM. */
@@ -174,6 +176,57 @@ int gamma_set_option(gamma_handle h, const char *key, int64_t value);
 /* Release the handle and everything it owns (synchronises its last stream).
  * NULL is allowed. */
 void gamma_destroy(gamma_handle h);
+
+/* ---------------------------------------------------------------------------
+ * Batched runs: many dose pairs of uneven size, geometry and criteria in one
+ * sequence of persistent launches (prepare, key-0 cells, cost ordering,
+ * table walk), grouped by dimension, with one queue of expensive voxels
+ * ordered by (cost bucket, pair) across all pairs of a group, captured once
+ * into a CUDA graph and replayed.  This scales the per-voxel independence of
+ * the gamma search (Section 1) from one pair to many; the paper itself runs
+ * one pair at a time (Algorithm A2).
+ */
+typedef struct {
+    const float *ref_dev;      /* device, float32, (nz, ny, nx), borrowed */
+    const float *eval_dev;     /* device, float32, same shape, borrowed */
+    float *gamma_out_dev;      /* device, float32, nz*ny*nx, caller-owned */
+    int ndim;                  /* 2 or 3 */
+    int64_t shape[3];          /* (nz, ny, nx), nz = 1 for 2D */
+    float spacing_mm[3];       /* (hz, hy, hx) */
+    gamma_criteria crit;
+} gamma_pair_desc;
+
+/* Create a batch handle over n_pairs descriptors (copied; device buffers
+ * borrowed).  Each pair gets its own cell table and scratch.  Errors:
+ * INVALID_ARG, SHAPE, OOM, TABLE_TOO_LARGE, CUDA.  Synchronous. */
+int gamma_batch_create(gamma_handle *out, int n_pairs, const gamma_pair_desc *pairs);
+
+/* Compute every pair's gamma map on `cuda_stream`.  The first call (and the
+ * first after an option change) captures the launch sequence into a CUDA
+ * graph on a private stream; later calls replay it on `cuda_stream`.
+ * Stream-ordered, no allocation after the first call.  Errors: INVALID_ARG,
+ * CUDA.  gamma_pass_rate / gamma_get_stats on a batch handle report the
+ * totals over all pairs. */
+int gamma_batch_run(gamma_handle h, void *cuda_stream);
+
+/* Pass rate and counts of one pair of the last batched run (synchronises).
+ * Errors: INVALID_ARG (pair out of range or not a batch), NOT_RUN, NAN_INPUT,
+ * QUEUE_FULL, CUDA. */
+int gamma_batch_pass_rate(gamma_handle h, int pair, double *rate, int64_t *n_eval,
+                          int64_t *n_pass);
+
+/* Counters of one pair of the last batched run (synchronises). */
+int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
+
+/* Autotuner: times the full run (single or batch handle) for every
+ * combination of lanes_per_voxel in {4, 8, 16, 32} and
+ * shell_blocks_per_sm in {1, 2} (one warm-up and `reps` timed runs each, CUDA
+ * events on `cuda_stream`), keeps the fastest as the handle's options and
+ * returns it (any output pointer may be NULL).  gamma_out_dev receives the
+ * gamma map of a single-pair handle (device, nz*ny*nx floats) and is ignored
+ * for a batch handle.  Errors as for the runs. */
+int gamma_autotune(gamma_handle h, float *gamma_out_dev, void *cuda_stream, int reps,
+                   int64_t *lanes_per_voxel, int64_t *shell_blocks_per_sm, float *best_ms);
 
 /* Static description of a status code. */
 const char *gamma_strerror(int code);

@@ -18,7 +18,8 @@ __all__ = [
     "GammaError", "gamma_criteria", "gamma_stats", "gamma_create", "gamma_set_inputs",
     "gamma_run", "gamma_run_host", "gamma_pass_rate", "gamma_get_stats", "gamma_get_timings",
     "gamma_set_option",
-    "gamma_run_noalloc", "gamma_destroy", "gamma_strerror", "gamma_version", "library_path",
+    "gamma_run_noalloc", "gamma_batch_create", "gamma_batch_run", "gamma_batch_pass_rate",
+    "gamma_batch_get_stats", "gamma_autotune", "gamma_pair_desc", "gamma_destroy", "gamma_strerror", "gamma_version", "library_path",
     "criteria",
     "GLOBAL", "LOCAL",
 ]
@@ -50,6 +51,13 @@ class gamma_timings(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class gamma_pair_desc(ctypes.Structure):
+    _fields_ = [("ref_dev", ctypes.c_void_p), ("eval_dev", ctypes.c_void_p),
+                ("gamma_out_dev", ctypes.c_void_p), ("ndim", ctypes.c_int),
+                ("shape", ctypes.c_int64 * 3), ("spacing_mm", ctypes.c_float * 3),
+                ("crit", gamma_criteria)]
 
 
 class GammaError(RuntimeError):
@@ -85,6 +93,14 @@ def _load():
     lib.gamma_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
     lib.gamma_run_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, i64p, f32p,
                                       ctypes.POINTER(gamma_criteria), vp, i64p, i64p]
+    lib.gamma_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int,
+                                       ctypes.POINTER(gamma_pair_desc)]
+    lib.gamma_batch_run.argtypes = [vp, vp]
+    lib.gamma_batch_pass_rate.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          i64p, i64p]
+    lib.gamma_batch_get_stats.argtypes = [vp, ctypes.c_int, ctypes.POINTER(gamma_stats)]
+    lib.gamma_autotune.argtypes = [vp, vp, vp, ctypes.c_int, i64p, i64p,
+                                   ctypes.POINTER(ctypes.c_float)]
     lib.gamma_destroy.argtypes = [vp]
     lib.gamma_destroy.restype = None
     lib.gamma_strerror.argtypes = [ctypes.c_int]
@@ -205,6 +221,51 @@ def gamma_run_noalloc(ref_dev, eval_dev, gamma_out_dev, ndim: int, shape: Sequen
                                   ctypes.byref(ne) if counts else None,
                                   ctypes.byref(npass) if counts else None), "gamma_run_noalloc")
     return (ne.value, npass.value) if counts else None
+
+
+def gamma_batch_create(pairs) -> int:
+    """Batch handle over a list of (ref_dev, eval_dev, gamma_out_dev, ndim, shape,
+    spacing_mm, crit) tuples; tensors are float32 CUDA tensors, shape/spacing
+    in (z, y, x) order with shape[0] = 1 for 2D."""
+    arr = (gamma_pair_desc * len(pairs))()
+    for d, (ref, ev, out, ndim, shape, spacing, crit) in zip(arr, pairs):
+        d.ref_dev, d.eval_dev, d.gamma_out_dev = _dev_ptr(ref), _dev_ptr(ev), _dev_ptr(out)
+        d.ndim = int(ndim)
+        d.shape = (ctypes.c_int64 * 3)(*[int(v) for v in shape])
+        d.spacing_mm = (ctypes.c_float * 3)(*[float(v) for v in spacing])
+        d.crit = crit
+    h = ctypes.c_void_p()
+    _check(_lib.gamma_batch_create(ctypes.byref(h), len(pairs), arr), "gamma_batch_create")
+    return h.value
+
+
+def gamma_batch_run(h: int, stream=None) -> None:
+    _check(_lib.gamma_batch_run(h, _stream_ptr(stream)), "gamma_batch_run")
+
+
+def gamma_batch_pass_rate(h: int, pair: int):
+    rate = ctypes.c_double()
+    ne, npass = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.gamma_batch_pass_rate(h, int(pair), ctypes.byref(rate), ctypes.byref(ne),
+                                      ctypes.byref(npass)), "gamma_batch_pass_rate")
+    return rate.value, ne.value, npass.value
+
+
+def gamma_batch_get_stats(h: int, pair: int) -> dict:
+    st = gamma_stats()
+    _check(_lib.gamma_batch_get_stats(h, int(pair), ctypes.byref(st)), "gamma_batch_get_stats")
+    return st.as_dict()
+
+
+def gamma_autotune(h: int, gamma_out_dev=None, stream=None, reps: int = 3):
+    """Time every (lanes_per_voxel, shell_blocks_per_sm) choice, keep the
+    fastest; returns (lanes_per_voxel, shell_blocks_per_sm, ms)."""
+    lanes, blocks = ctypes.c_int64(), ctypes.c_int64()
+    ms = ctypes.c_float()
+    _check(_lib.gamma_autotune(h, _dev_ptr(gamma_out_dev), _stream_ptr(stream), int(reps),
+                               ctypes.byref(lanes), ctypes.byref(blocks), ctypes.byref(ms)),
+           "gamma_autotune")
+    return lanes.value, blocks.value, ms.value
 
 
 def gamma_destroy(h: Optional[int]) -> None:

@@ -61,7 +61,12 @@ double axis_gap(int i) { return i >= 0 ? (double)i : (double)(-i - 1); }
 
 }  // namespace
 
+struct BatchState;
+void free_batch(BatchState* b);
+
 struct gamma_ctx {
+    BatchState* batch = nullptr;      // non-null for batch handles
+    int graph = 1;                    // batch: capture and replay a CUDA graph
     int device = 0;
     int ndim = 3;
     int64_t nz = 1, ny = 1, nx = 1, nvox = 0;
@@ -235,6 +240,7 @@ Problem make_problem(const gamma_ctx* h, float* out)
 void free_ctx(gamma_ctx* h)
 {
     if (!h) return;
+    if (h->batch) free_batch(h->batch);
     for (auto& e : h->tev)
         if (e) cudaEventDestroy(e);
     cudaFree(h->table_dev);
@@ -256,6 +262,171 @@ int check_criteria(const gamma_criteria* c)
     if (c->mode != GAMMA_GLOBAL && c->mode != GAMMA_LOCAL) return GAMMA_ERR_INVALID_ARG;
     if (!std::isfinite(c->cutoff_frac) || !std::isfinite(c->dose_norm)) return GAMMA_ERR_INVALID_ARG;
     return GAMMA_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batched runs
+// ---------------------------------------------------------------------------
+
+struct BatchState {
+    int n = 0;
+    std::vector<gamma_ctx*> pairs;     // per-pair tables and scratch
+    std::vector<float*> outs;
+    std::vector<int> members[2];       // pair indices of group 0 (2D) and 1 (3D)
+    Counters* ctrs = nullptr;          // [n], contiguous: one memset per run
+    struct Group {
+        gk::Problem* probs = nullptr;
+        CUtensorMap* maps = nullptr;
+        int* use_tma = nullptr;
+        int* tile_start = nullptr;
+        unsigned* item_start = nullptr;
+        unsigned* head = nullptr;
+        gk::BatchDesc* desc = nullptr;
+        gk::BatchGroup host{};
+    } grp[2];
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool dirty = true;                 // device problems / graph out of date
+};
+
+namespace {
+
+void free_group(BatchState::Group& g)
+{
+    cudaFree(g.probs);
+    cudaFree(g.maps);
+    cudaFree(g.use_tma);
+    cudaFree(g.tile_start);
+    cudaFree(g.item_start);
+    cudaFree(g.head);
+    cudaFree(g.desc);
+    g = BatchState::Group{};
+}
+
+}  // namespace
+
+void free_batch(BatchState* b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (auto& g : b->grp) free_group(g);
+    for (gamma_ctx* c : b->pairs) {
+        if (c) c->ctr = nullptr;           // points into b->ctrs
+        free_ctx(c);
+    }
+    cudaFree(b->ctrs);
+    delete b;
+}
+
+namespace {
+
+// (Re)build every pair's Problem with the batch handle's options and upload
+// the per-group descriptors.
+int batch_upload(gamma_ctx* h)
+{
+    BatchState* b = h->batch;
+    for (int gi = 0; gi < 2; ++gi) {
+        auto& G = b->grp[gi];
+        const auto& mem = b->members[gi];
+        const int np = (int)mem.size();
+        if (np == 0) continue;
+        std::vector<gk::Problem> probs(np);
+        std::vector<CUtensorMap> maps(np);
+        std::vector<int> use(np), tstart(np + 1, 0);
+        long long maxv = 0;
+        for (int k = 0; k < np; ++k) {
+            gamma_ctx* c = b->pairs[mem[k]];
+            c->tau = h->tau;
+            c->stats = 0;
+            c->sort_tail = 1;
+            c->shell_minblocks = h->shell_minblocks;
+            probs[k] = make_problem(c, b->outs[mem[k]]);
+            gk::fill_shell_constants(probs[k]);
+            std::memset(&maps[k], 0, sizeof(CUtensorMap));
+            use[k] = gk::encode_tile_map(probs[k], &maps[k]) ? 1 : 0;
+            const int tiles = gk::shell_tiles(probs[k]);
+            if (tiles < 0) return GAMMA_ERR_SHAPE;
+            if ((long long)tstart[k] + tiles > 0x3fffffffLL) return GAMMA_ERR_SHAPE;
+            tstart[k + 1] = tstart[k] + tiles;
+            maxv = std::max<long long>(maxv, c->nvox);
+        }
+        if (!G.probs) {
+            CK(cudaMalloc(&G.probs, sizeof(gk::Problem) * np));
+            CK(cudaMalloc(&G.maps, sizeof(CUtensorMap) * np));
+            CK(cudaMalloc(&G.use_tma, sizeof(int) * np));
+            CK(cudaMalloc(&G.tile_start, sizeof(int) * (np + 1)));
+            CK(cudaMalloc(&G.item_start, sizeof(unsigned) * (gk::kNumBuckets * np + 1)));
+            CK(cudaMalloc(&G.head, sizeof(unsigned)));
+            CK(cudaMalloc(&G.desc, sizeof(gk::BatchDesc)));
+        }
+        CK(cudaMemcpy(G.probs, probs.data(), sizeof(gk::Problem) * np, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(G.maps, maps.data(), sizeof(CUtensorMap) * np, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(G.use_tma, use.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(G.tile_start, tstart.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice));
+        gk::BatchDesc d{};
+        d.npairs = np;
+        d.probs = G.probs;
+        d.maps = G.maps;
+        d.use_tma = G.use_tma;
+        d.tile_start = G.tile_start;
+        d.item_start = G.item_start;
+        d.head = G.head;
+        CK(cudaMemcpy(G.desc, &d, sizeof(d), cudaMemcpyHostToDevice));
+        G.host.ndim = gi == 0 ? 2 : 3;
+        G.host.npairs = np;
+        G.host.max_nvox = maxv;
+        G.host.total_tiles = tstart[np];
+        G.host.desc = G.desc;
+    }
+    return GAMMA_OK;
+}
+
+// The launch sequence of one batched run, on stream s.
+int batch_enqueue(gamma_ctx* h, cudaStream_t s)
+{
+    BatchState* b = h->batch;
+    const bool tm = h->timing != 0;
+    if (tm) {
+        CK(cudaEventRecord(h->tev[0], s));
+        CK(cudaEventRecord(h->tev[1], s));
+    }
+    CK(cudaMemsetAsync(b->ctrs, 0, sizeof(Counters) * b->n, s));
+    for (auto& G : b->grp) CK(gk::launch_batch_prepare(G.host, s));
+    if (tm) CK(cudaEventRecord(h->tev[2], s));
+    for (auto& G : b->grp) CK(gk::launch_batch_shell(G.host, h->shell_minblocks, s));
+    if (tm) CK(cudaEventRecord(h->tev[3], s));
+    for (auto& G : b->grp) CK(gk::launch_batch_order(G.host, s));
+    if (tm) CK(cudaEventRecord(h->tev[4], s));
+    for (auto& G : b->grp) CK(gk::launch_batch_tail(G.host, h->lanes, s));
+    if (tm) {
+        CK(cudaEventRecord(h->tev[5], s));
+        CK(cudaEventRecord(h->tev[6], s));
+    }
+    return GAMMA_OK;
+}
+
+Counters sum_counters(const std::vector<Counters>& cs)
+{
+    Counters t;
+    std::memset(&t, 0, sizeof(t));
+    for (const Counters& c : cs) {
+        t.n_eval += c.n_eval;
+        t.n_pass += c.n_pass;
+        t.cells_visited += c.cells_visited;
+        t.cells_pruned += c.cells_pruned;
+        t.cells_keyed += c.cells_keyed;
+        t.flags |= c.flags;
+        t.tail_count += c.tail_count;
+        t.overflow_count += c.overflow_count;
+        t.fp64_cells += c.fp64_cells;
+        if (gk::fdec(c.rmax_enc) > gk::fdec(t.rmax_enc) || t.rmax_enc == 0) t.rmax_enc = c.rmax_enc;
+    }
+    return t;
 }
 
 }  // namespace
@@ -371,13 +542,19 @@ int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host
     return GAMMA_OK;
 }
 
-static int read_counters(gamma_handle h, Counters* c)
+static int read_counters(gamma_handle h, Counters* c, int pair = -1)
 {
     if (!h->ran) return GAMMA_ERR_NOT_RUN;
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     CK(cudaStreamSynchronize(h->last_stream));
-    CK(cudaMemcpy(c, h->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+    if (!h->batch) {
+        CK(cudaMemcpy(c, h->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+        return GAMMA_OK;
+    }
+    std::vector<Counters> cs(h->batch->n);
+    CK(cudaMemcpy(cs.data(), h->batch->ctrs, sizeof(Counters) * cs.size(), cudaMemcpyDeviceToHost));
+    *c = pair >= 0 ? cs[pair] : sum_counters(cs);
     return GAMMA_OK;
 }
 
@@ -401,7 +578,12 @@ int gamma_get_stats(gamma_handle h, gamma_stats* out)
     Counters c;
     if (int rc = read_counters(h, &c)) return rc;
     std::memset(out, 0, sizeof(*out));
-    out->n_voxels = h->nvox;
+    if (h->batch) {
+        out->n_voxels = 0;
+        for (gamma_ctx* c2 : h->batch->pairs) out->n_voxels += c2->nvox;
+    } else {
+        out->n_voxels = h->nvox;
+    }
     out->n_eval = (int64_t)c.n_eval;
     out->n_pass = (int64_t)c.n_pass;
     out->tail_voxels = (int64_t)c.tail_count;
@@ -441,6 +623,21 @@ int gamma_get_timings(gamma_handle h, gamma_timings* out)
 int gamma_set_option(gamma_handle h, const char* key, int64_t value)
 {
     if (!h || !key) return GAMMA_ERR_INVALID_ARG;
+    if (h->batch) {
+        h->batch->dirty = true;
+        if (!std::strcmp(key, "graph")) {
+            if (value != 0 && value != 1) return GAMMA_ERR_INVALID_ARG;
+            h->graph = (int)value;
+            return GAMMA_OK;
+        }
+        if (!std::strcmp(key, "table_cap")) {
+            for (gamma_ctx* c : h->batch->pairs)
+                if (int rc = gamma_set_option(c, key, value)) return rc;
+            return GAMMA_OK;
+        }
+        if (!std::strcmp(key, "sort_tail") || !std::strcmp(key, "stats"))
+            return value == 0 || value == 1 ? GAMMA_OK : GAMMA_ERR_INVALID_ARG;  // fixed in batches
+    }
     if (!std::strcmp(key, "lanes_per_voxel")) {
         if (value != 4 && value != 8 && value != 16 && value != 32) return GAMMA_ERR_INVALID_ARG;
         h->lanes = (int)value;
@@ -488,6 +685,160 @@ void gamma_destroy(gamma_handle h)
     DeviceGuard dg(h->device);
     if (h->ran) cudaStreamSynchronize(h->last_stream);
     free_ctx(h);
+}
+
+int gamma_batch_create(gamma_handle* out, int n_pairs, const gamma_pair_desc* pairs)
+{
+    if (!out || n_pairs <= 0 || !pairs) return GAMMA_ERR_INVALID_ARG;
+    *out = nullptr;
+    gamma_ctx* h = new (std::nothrow) gamma_ctx();
+    if (!h) return GAMMA_ERR_OOM;
+    h->batch = new (std::nothrow) BatchState();
+    if (!h->batch) { delete h; return GAMMA_ERR_OOM; }
+    BatchState* b = h->batch;
+    auto fail = [&](int code) { free_ctx(h); return code; };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(GAMMA_ERR_CUDA);
+    cudaError_t e;
+    for (auto& te : h->tev)
+        if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(cuda_fail(e));
+    b->n = n_pairs;
+    b->pairs.assign(n_pairs, nullptr);
+    b->outs.assign(n_pairs, nullptr);
+    if ((e = cudaMalloc(&b->ctrs, sizeof(Counters) * n_pairs)) != cudaSuccess)
+        return fail(cuda_fail(e));
+    for (int i = 0; i < n_pairs; ++i) {
+        const gamma_pair_desc& d = pairs[i];
+        if (!d.ref_dev || !d.eval_dev || !d.gamma_out_dev) return fail(GAMMA_ERR_INVALID_ARG);
+        gamma_ctx* c = nullptr;
+        if (int rc = gamma_create(&c, d.ref_dev, d.eval_dev, d.ndim, d.shape, d.spacing_mm, &d.crit))
+            return fail(rc);
+        cudaFree(c->ctr);                        // counters live in one shared array
+        c->ctr = b->ctrs + i;
+        b->pairs[i] = c;
+        b->outs[i] = d.gamma_out_dev;
+        b->members[d.ndim == 2 ? 0 : 1].push_back(i);
+    }
+    if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(cuda_fail(e));
+    if (int rc = batch_upload(h)) return fail(rc);
+    b->dirty = false;
+    *out = h;
+    return GAMMA_OK;
+}
+
+int gamma_batch_run(gamma_handle h, void* cuda_stream)
+{
+    if (!h || !h->batch) return GAMMA_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    BatchState* b = h->batch;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (b->dirty) {
+        if (h->ran) CK(cudaStreamSynchronize(h->last_stream));
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        if (int rc = batch_upload(h)) return rc;
+        b->dirty = false;
+    }
+    if (h->graph) {
+        if (!b->exec) {
+            CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            const int rc = batch_enqueue(h, b->cap);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (ec != cudaSuccess) return cuda_fail(ec);
+            b->graph = g;
+            CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        }
+        CK(cudaGraphLaunch(b->exec, s));
+    } else {
+        if (int rc = batch_enqueue(h, s)) return rc;
+    }
+    h->last_stream = s;
+    h->ran = true;
+    for (gamma_ctx* c : b->pairs) {
+        c->ran = true;
+        c->last_stream = s;
+    }
+    return GAMMA_OK;
+}
+
+int gamma_batch_pass_rate(gamma_handle h, int pair, double* rate, int64_t* n_eval, int64_t* n_pass)
+{
+    if (!h || !h->batch || pair < 0 || pair >= h->batch->n) return GAMMA_ERR_INVALID_ARG;
+    Counters c;
+    if (int rc = read_counters(h, &c, pair)) return rc;
+    if (c.flags & gk::kFlagNonFinite) return GAMMA_ERR_NAN_INPUT;
+    if (c.flags & gk::kFlagTimeout) return GAMMA_ERR_TIMEOUT;
+    if (c.flags & gk::kFlagTailFull) return GAMMA_ERR_QUEUE_FULL;
+    if (n_eval) *n_eval = (int64_t)c.n_eval;
+    if (n_pass) *n_pass = (int64_t)c.n_pass;
+    if (rate) *rate = c.n_eval ? (double)c.n_pass / (double)c.n_eval : 0.0;
+    return GAMMA_OK;
+}
+
+int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats* out)
+{
+    if (!h || !h->batch || !out || pair < 0 || pair >= h->batch->n) return GAMMA_ERR_INVALID_ARG;
+    gamma_ctx* c = h->batch->pairs[pair];
+    Counters k;
+    if (int rc = read_counters(h, &k, pair)) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->n_voxels = c->nvox;
+    out->n_eval = (int64_t)k.n_eval;
+    out->n_pass = (int64_t)k.n_pass;
+    out->tail_voxels = (int64_t)k.tail_count;
+    out->overflow_voxels = (int64_t)k.overflow_count;
+    out->fp64_cells = (int64_t)k.fp64_cells;
+    out->d_norm = c->crit.dose_norm > 0 ? (double)c->crit.dose_norm : (double)gk::fdec(k.dnorm_enc);
+    out->r_max = (double)gk::fdec(k.rmax_enc);
+    out->table_entries = (int64_t)c->table.size();
+    out->table_radius = c->r_cover;
+    out->flags = k.flags;
+    return GAMMA_OK;
+}
+
+int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int reps,
+                   int64_t* lanes_per_voxel, int64_t* shell_blocks_per_sm, float* best_ms)
+{
+    if (!h || reps <= 0 || (!h->batch && !gamma_out_dev)) return GAMMA_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int lanes[4] = {4, 8, 16, 32};
+    int best_l = h->lanes, best_b = h->shell_minblocks;
+    float best = INFINITY;
+    int rc = GAMMA_OK;
+    auto run = [&]() { return h->batch ? gamma_batch_run(h, s) : gamma_run(h, gamma_out_dev, s); };
+    for (int li = 0; li < 4 && rc == GAMMA_OK; ++li)
+        for (int bl = 1; bl <= 2 && rc == GAMMA_OK; ++bl) {
+            h->lanes = lanes[li];
+            h->shell_minblocks = bl;
+            if (h->batch) h->batch->dirty = true;
+            if ((rc = run())) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == GAMMA_OK; ++r) rc = run();
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GAMMA_ERR_CUDA; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < best) { best = ms; best_l = lanes[li]; best_b = bl; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->lanes = best_l;
+    h->shell_minblocks = best_b;
+    if (h->batch) h->batch->dirty = true;
+    if (rc) return rc;
+    if (lanes_per_voxel) *lanes_per_voxel = best_l;
+    if (shell_blocks_per_sm) *shell_blocks_per_sm = best_b;
+    if (best_ms) *best_ms = best;
+    return GAMMA_OK;
 }
 
 const char* gamma_strerror(int code)

@@ -1,6 +1,7 @@
 // Internal structures shared by the CUDA kernels and the C-ABI layer.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "gamma_face.cuh"
@@ -110,11 +111,45 @@ struct Problem {
     ShellConst shell;            // filled by launch_shell
 };
 
+// Device-side description of the pairs of one batched launch group (pairs of
+// the same dimension).  All arrays live in device memory.
+struct BatchDesc {
+    int npairs;
+    const Problem* probs;          // [npairs], shell constants filled in
+    const CUtensorMap* maps;       // [npairs] evaluation-dose tile maps
+    const int* use_tma;            // [npairs] 1: the map is valid for TMA loads
+    const int* tile_start;         // [npairs + 1] first global shell tile of each pair
+    unsigned* item_start;          // [kNumBuckets * npairs + 1] queued voxels ordered
+                                   // by (cost bucket descending, pair)
+    unsigned* head;                // work counter of the group's table walk
+};
+
+// Host view of one batched launch group.
+struct BatchGroup {
+    int ndim;
+    int npairs;
+    long long max_nvox;            // largest pair, for the prepare grid
+    int total_tiles;               // shell tiles over all pairs
+    const BatchDesc* desc;         // device copy of the descriptor
+};
+
 // Launchers (gamma_kernels.cu).  All are stream-ordered and allocate nothing.
 cudaError_t launch_prepare(const Problem& P, cudaStream_t s);
 cudaError_t launch_shell(const Problem& P, cudaStream_t s);
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
 cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, cudaStream_t s);
 int device_sm_count();
+
+// Host-side constants a Problem needs before it is uploaded for a batch.
+void fill_shell_constants(Problem& P);
+// Tile-load map for a Problem; false when TMA cannot be used for it.
+bool encode_tile_map(const Problem& P, CUtensorMap* map);
+int shell_tiles(const Problem& P);
+
+// Batched launches over one group: prepare, shell, ordering, table walk.
+cudaError_t launch_batch_prepare(const BatchGroup& g, cudaStream_t s);
+cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStream_t s);
+cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s);
+cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, cudaStream_t s);
 
 }  // namespace gk

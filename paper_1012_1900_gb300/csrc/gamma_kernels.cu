@@ -44,8 +44,11 @@ __device__ __forceinline__ bool is_evaluated(const Problem& P, float dr, float t
 // k_prepare: dose norm and finite check
 // --------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_prepare(const __grid_constant__ Problem P)
+template <bool BATCH>
+__global__ void __launch_bounds__(256)
+    k_prepare(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd)
 {
+    const Problem& P = BATCH ? bd->probs[blockIdx.y] : P0;
     float m = -kInf;
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -199,10 +202,10 @@ __device__ __forceinline__ float shell_pass(const Problem& P, const float* tile,
                                    inp, dr, inv, dnorm, v, best, done64);
 }
 
-template <int N, int MINB>
+template <int N, int MINB, bool BATCH>
 __global__ void __launch_bounds__(256, MINB)
-    k_shell(const __grid_constant__ Problem P, const __grid_constant__ CUtensorMap tmap, int use_tma,
-            int ntiles)
+    k_shell(const __grid_constant__ Problem P0, const __grid_constant__ CUtensorMap tmap0,
+            int use_tma0, int ntiles, const BatchDesc* __restrict__ bd)
 {
     using T = ShellTile<N>;
     constexpr int NC = 1 << N;
@@ -215,16 +218,10 @@ __global__ void __launch_bounds__(256, MINB)
     __shared__ unsigned int sh_hist[kNumBuckets];
     __shared__ unsigned long long sh_eval, sh_pass;
     __shared__ unsigned int sh_rmax;
+    __shared__ __align__(16) Problem sh_P;     // the current pair (batched launches)
 
-    const int ntx = (P.nx + T::TX - 1) / T::TX, nty = (P.ny + T::TY - 1) / T::TY;
     const int lane = threadIdx.x & 31;
     const int lx = lane, ly = (threadIdx.x >> 5) % T::TY, lz = (threadIdx.x >> 5) / T::TY;
-    const float dnorm = resolve_dnorm(P);
-    const float thr = P.cutoff_frac * dnorm;
-    const float k1 = P.t1 < P.ntable ? P.table[P.t1].key : kInf;
-    const float rc2 = P.r_cover * P.r_cover;
-    const bool table_ends = P.t1 >= P.ntable;
-    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
 
     if (threadIdx.x < kNumBuckets) sh_hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
@@ -232,40 +229,113 @@ __global__ void __launch_bounds__(256, MINB)
         sh_pass = 0;
         sh_rmax = 0;
         sh_nfar = 0;
-        if (use_tma) {
-            mbar_init(&bar[0], 1);
-            mbar_init(&bar[1], 1);
-            mbar_fence_init();
-        }
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
     }
     __syncthreads();
 
-    auto tile_origin = [&](int t, int& x0, int& y0, int& z0) {
-        x0 = (t % ntx) * T::TX;
-        y0 = ((t / ntx) % nty) * T::TY;
-        z0 = (t / ntx / nty) * T::TZ;
+    // global tile -> (pair, tile of that pair)
+    auto locate = [&](int t, int& pr, int& lt) {
+        if constexpr (!BATCH) {
+            pr = 0;
+            lt = t;
+        } else {
+            int lo = 0, hi = bd->npairs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bd->tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            pr = lo;
+            lt = t - bd->tile_start[lo];
+        }
+    };
+    auto pair_tma = [&](int pr) { return BATCH ? bd->use_tma[pr] : use_tma0; };
+    auto tile_origin = [&](int nx, int ny, int lt, int& x0, int& y0, int& z0) {
+        const int ntx = (nx + T::TX - 1) / T::TX, nty = (ny + T::TY - 1) / T::TY;
+        x0 = (lt % ntx) * T::TX;
+        y0 = ((lt / ntx) % nty) * T::TY;
+        z0 = (lt / ntx / nty) * T::TZ;
     };
     auto issue = [&](int t, int b) {
         if (t >= ntiles) return;
+        int pr, lt;
+        locate(t, pr, lt);
+        if (!pair_tma(pr)) return;
+        const Problem& Q = BATCH ? bd->probs[pr] : P0;
+        const CUtensorMap* map = BATCH ? &bd->maps[pr] : &tmap0;
         int x0, y0, z0;
-        tile_origin(t, x0, y0, z0);
+        tile_origin(Q.nx, Q.ny, lt, x0, y0, z0);
         mbar_arrive_expect_tx(&bar[b], T::ELEMS * (uint32_t)sizeof(float));
-        if (N == 3) tma_load_3d(tile[b], &tmap, x0 - 4, y0 - 1, z0 - 1, &bar[b]);
-        else tma_load_2d(tile[b], &tmap, x0 - 4, y0 - 1, &bar[b]);
+        if (N == 3) tma_load_3d(tile[b], map, x0 - 4, y0 - 1, z0 - 1, &bar[b]);
+        else tma_load_2d(tile[b], map, x0 - 4, y0 - 1, &bar[b]);
     };
-    if (use_tma && threadIdx.x == 0) issue(blockIdx.x, 0);
+    if (threadIdx.x == 0) issue(blockIdx.x, 0);
     uint32_t parity = 0;                 // bit b: phase of bar[b] to wait for
     unsigned my_eval = 0, my_pass = 0;
     float my_rmax = 0.f;
     int buf = 0;
+    int cur = -1;                        // pair whose counters my_* accumulate
+
+    // per-block counters -> the pair's global counters
+    auto flush = [&](const Problem& Q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            my_eval += __shfl_xor_sync(kFull, my_eval, o);
+            my_pass += __shfl_xor_sync(kFull, my_pass, o);
+            my_rmax = fmaxf(my_rmax, __shfl_xor_sync(kFull, my_rmax, o));
+        }
+        if (lane == 0) {
+            if (my_eval) atomicAdd(&sh_eval, (unsigned long long)my_eval);
+            if (my_pass) atomicAdd(&sh_pass, (unsigned long long)my_pass);
+            atomicMax(&sh_rmax, fenc(my_rmax));
+        }
+        my_eval = my_pass = 0;
+        my_rmax = 0.f;
+        __syncthreads();
+        if (threadIdx.x < kNumBuckets && sh_hist[threadIdx.x]) {
+            atomicAdd(&Q.ctr->hist[threadIdx.x], sh_hist[threadIdx.x]);
+            sh_hist[threadIdx.x] = 0;
+        }
+        if (threadIdx.x == 0) {
+            if (sh_eval) atomicAdd(&Q.ctr->n_eval, sh_eval);
+            if (sh_pass) atomicAdd(&Q.ctr->n_pass, sh_pass);
+            atomicMax(&Q.ctr->rmax_enc, sh_rmax);
+            sh_eval = 0;
+            sh_pass = 0;
+            sh_rmax = 0;
+        }
+        __syncthreads();
+    };
 
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+        int pr, lt;
+        locate(t, pr, lt);
+        if constexpr (BATCH) {
+            if (pr != cur) {                       // block-uniform
+                if (cur >= 0) flush(sh_P);
+                const int* src = (const int*)&bd->probs[pr];
+                int* dst = (int*)&sh_P;
+                for (int i = threadIdx.x; i < (int)(sizeof(Problem) / 4); i += blockDim.x)
+                    dst[i] = src[i];
+                __syncthreads();
+                cur = pr;
+            }
+        }
+        const Problem& P = BATCH ? sh_P : P0;
+        const bool use_tma = pair_tma(pr) != 0;
+        const float dnorm = resolve_dnorm(P);
+        const float thr = P.cutoff_frac * dnorm;
+        const float k1 = P.t1 < P.ntable ? P.table[P.t1].key : kInf;
+        const float rc2 = P.r_cover * P.r_cover;
+        const bool table_ends = P.t1 >= P.ntable;
+        const long long sy = P.nx, sz = (long long)P.nx * P.ny;
         int x0, y0, z0;
-        tile_origin(t, x0, y0, z0);
+        tile_origin(P.nx, P.ny, lt, x0, y0, z0);
         float* tl = tile[buf];
         // ---- stage: prefetch the next tile, wait for this one ----
+        if (threadIdx.x == 0) issue(t + gridDim.x, buf ^ 1);
         if (use_tma) {
-            if (threadIdx.x == 0) issue(t + gridDim.x, buf ^ 1);
             const bool ok = mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
             parity ^= 1u << buf;
             if (__syncthreads_or(!ok)) {
@@ -416,26 +486,7 @@ __global__ void __launch_bounds__(256, MINB)
         if (threadIdx.x == 0) sh_nfar = 0;
         __syncthreads();                 // tile[buf] and the lists are free for reuse
     }
-
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_eval += __shfl_xor_sync(kFull, my_eval, o);
-        my_pass += __shfl_xor_sync(kFull, my_pass, o);
-        my_rmax = fmaxf(my_rmax, __shfl_xor_sync(kFull, my_rmax, o));
-    }
-    if (lane == 0) {
-        if (my_eval) atomicAdd(&sh_eval, (unsigned long long)my_eval);
-        if (my_pass) atomicAdd(&sh_pass, (unsigned long long)my_pass);
-        atomicMax(&sh_rmax, fenc(my_rmax));
-    }
-    __syncthreads();
-    if (threadIdx.x < kNumBuckets && sh_hist[threadIdx.x])
-        atomicAdd(&P.ctr->hist[threadIdx.x], sh_hist[threadIdx.x]);
-    if (threadIdx.x == 0) {
-        if (sh_eval) atomicAdd(&P.ctr->n_eval, sh_eval);
-        if (sh_pass) atomicAdd(&P.ctr->n_pass, sh_pass);
-        atomicMax(&P.ctr->rmax_enc, sh_rmax);
-    }
+    if (!BATCH || cur >= 0) flush(BATCH ? sh_P : P0);
 }
 
 // --------------------------------------------------------------------------
@@ -455,6 +506,44 @@ __global__ void k_bucket_scan(Counters* ctr)
 
 __global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ Problem P)
 {
+    const unsigned total = min(P.ctr->tail_count, P.tail_cap);
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const unsigned pos = atomicAdd(&P.ctr->cursor[P.tail_bucket[i]], 1u);
+        P.tail_sorted[pos] = P.tail_raw[i];
+    }
+}
+
+// Batched ordering: each pair's queue sorted by its own bucket offsets, plus a
+// global item order over (bucket descending, pair) for the table walk.
+__global__ void k_bucket_scan_batch(const BatchDesc* __restrict__ bd)
+{
+    const int np = bd->npairs;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        Counters* c = bd->probs[p].ctr;
+        unsigned acc = 0;
+        for (int b = kNumBuckets - 1; b >= 0; --b) {
+            c->cursor[b] = acc;
+            acc += c->hist[b];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        int k = 0;
+        for (int b = kNumBuckets - 1; b >= 0; --b)
+            for (int p = 0; p < np; ++p) {
+                bd->item_start[k++] = acc;
+                acc += bd->probs[p].ctr->hist[b];
+            }
+        bd->item_start[k] = acc;
+        *bd->head = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scatter_batch(const BatchDesc* __restrict__ bd)
+{
+    const Problem& P = bd->probs[blockIdx.y];
     const unsigned total = min(P.ctr->tail_count, P.tail_cap);
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
@@ -525,25 +614,45 @@ __device__ __forceinline__ float group_min(float v, unsigned gmask)
     return v;
 }
 
-template <int N, int G>
-__global__ void __launch_bounds__(256) k_tail(const __grid_constant__ Problem P)
+template <int N, int G, bool BATCH>
+__global__ void __launch_bounds__(256)
+    k_tail(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd)
 {
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const int gbase = lane & ~(G - 1);
     const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
-    const float dnorm = resolve_dnorm(P);
-    const unsigned total = min(P.ctr->tail_count, P.tail_cap);
-    const float rc2 = P.r_cover * P.r_cover;
+    const unsigned total = BATCH ? bd->item_start[kNumBuckets * bd->npairs]
+                                 : min(P0.ctr->tail_count, P0.tail_cap);
+    unsigned* head = BATCH ? bd->head : &P0.ctr->head;
     unsigned int my_eval = 0, my_pass = 0, my_over = 0;
     TailStats st;
 
     for (;;) {
         unsigned item = 0;
-        if (gl == 0) item = atomicAdd(&P.ctr->head, 1u);
+        if (gl == 0) item = atomicAdd(head, 1u);
         item = __shfl_sync(gmask, item, gbase);
         if (item >= total) break;
-        const unsigned v = P.sort_tail ? P.tail_sorted[item] : P.tail_raw[item];
+        int pr = 0;
+        unsigned v;
+        if constexpr (BATCH) {
+            const int np = bd->npairs;
+            int lo = 0, hi = kNumBuckets * np - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bd->item_start[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            const int b = kNumBuckets - 1 - lo / np;
+            pr = lo % np;
+            const Problem& Q = bd->probs[pr];
+            const unsigned first = Q.ctr->cursor[b] - Q.ctr->hist[b];
+            v = Q.tail_sorted[first + (item - bd->item_start[lo])];
+        } else {
+            v = P0.sort_tail ? P0.tail_sorted[item] : P0.tail_raw[item];
+        }
+        const Problem& P = BATCH ? bd->probs[pr] : P0;
+        const float dnorm = resolve_dnorm(P);
+        const float rc2 = P.r_cover * P.r_cover;
         const int x = (int)(v % (unsigned)P.nx);
         const unsigned r1 = v / (unsigned)P.nx;
         const int y = (int)(r1 % (unsigned)P.ny);
@@ -607,29 +716,43 @@ __global__ void __launch_bounds__(256) k_tail(const __grid_constant__ Problem P)
         if (gl == 0) {
             const float gam = sqrtf(best);
             P.out[v] = gam;
-            ++my_eval;
-            my_pass += gam <= 1.f;
+            if constexpr (BATCH) {
+                atomicAdd(&P.ctr->n_eval, 1ull);
+                if (gam <= 1.f) atomicAdd(&P.ctr->n_pass, 1ull);
+            } else {
+                ++my_eval;
+                my_pass += gam <= 1.f;
+            }
+        }
+        if constexpr (BATCH) {
+            if (my_over) {
+                if (gl == 0) atomicAdd(&P.ctr->overflow_count, 1u);
+                my_over = 0;
+            }
         }
     }
+    if constexpr (!BATCH) {      // single-pair totals (batched ones went out per voxel)
+        const Problem& P = P0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_eval += __shfl_xor_sync(kFull, my_eval, o);
-        my_pass += __shfl_xor_sync(kFull, my_pass, o);
-        my_over += __shfl_xor_sync(kFull, my_over, o);
-        if (P.stats) {
-            st.visited += __shfl_xor_sync(kFull, st.visited, o);
-            st.pruned += __shfl_xor_sync(kFull, st.pruned, o);
-            st.keyed += __shfl_xor_sync(kFull, st.keyed, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            my_eval += __shfl_xor_sync(kFull, my_eval, o);
+            my_pass += __shfl_xor_sync(kFull, my_pass, o);
+            my_over += __shfl_xor_sync(kFull, my_over, o);
+            if (P.stats) {
+                st.visited += __shfl_xor_sync(kFull, st.visited, o);
+                st.pruned += __shfl_xor_sync(kFull, st.pruned, o);
+                st.keyed += __shfl_xor_sync(kFull, st.keyed, o);
+            }
         }
-    }
-    if (lane == 0) {
-        if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
-        if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
-        if (my_over) atomicAdd(&P.ctr->overflow_count, my_over / G);
-        if (P.stats) {
-            atomicAdd(&P.ctr->cells_visited, st.visited);
-            atomicAdd(&P.ctr->cells_pruned, st.pruned);
-            atomicAdd(&P.ctr->cells_keyed, st.keyed);
+        if (lane == 0) {
+            if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
+            if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
+            if (my_over) atomicAdd(&P.ctr->overflow_count, my_over / G);
+            if (P.stats) {
+                atomicAdd(&P.ctr->cells_visited, st.visited);
+                atomicAdd(&P.ctr->cells_pruned, st.pruned);
+                atomicAdd(&P.ctr->cells_keyed, st.keyed);
+            }
         }
     }
 }
@@ -657,7 +780,7 @@ static int grid_for(long long n, int threads, int cap)
 cudaError_t launch_prepare(const Problem& P, cudaStream_t s)
 {
     const int sms = device_sm_count();
-    k_prepare<<<grid_for(P.nvox, 256, sms * 8), 256, 0, s>>>(P);
+    k_prepare<false><<<grid_for(P.nvox, 256, sms * 8), 256, 0, s>>>(P, nullptr);
     return cudaGetLastError();
 }
 
@@ -720,6 +843,10 @@ static double simplex_dist_host(const double (*W)[3], int nv)
 
 // Constants of the key-0 cells: per-cell geometry and the smallest spatial
 // distance from the voxel to a face of these cells that does not contain it.
+static void shell_constants(const Problem& P, ShellConst& sc);
+
+void fill_shell_constants(Problem& P) { shell_constants(P, P.shell); }
+
 static void shell_constants(const Problem& P, ShellConst& sc)
 {
     const int N = P.ndim;
@@ -773,7 +900,7 @@ static void shell_constants(const Problem& P, ShellConst& sc)
     sc.far2 = f;
 }
 
-static bool encode_tile_map(const Problem& P, CUtensorMap* map)
+bool encode_tile_map(const Problem& P, CUtensorMap* map)
 {
     using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -814,15 +941,8 @@ static bool encode_tile_map(const Problem& P, CUtensorMap* map)
            CUDA_SUCCESS;
 }
 
-cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
+int shell_tiles(const Problem& P)
 {
-    Problem P = P0;
-    shell_constants(P, P.shell);
-    CUtensorMap map;
-    std::memset(&map, 0, sizeof(map));
-    const int use_tma = encode_tile_map(P, &map) ? 1 : 0;
-    const int sms = device_sm_count();
-    const int per_sm = P.shell_minblocks == 1 ? 1 : 2;
     long long tiles;
     if (P.ndim == 3) {
         using T = ShellTile<3>;
@@ -832,14 +952,27 @@ cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
         using T = ShellTile<2>;
         tiles = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
     }
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    return tiles > 0x3fffffffLL ? -1 : (int)tiles;
+}
+
+cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
+{
+    Problem P = P0;
+    shell_constants(P, P.shell);
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    const int use_tma = encode_tile_map(P, &map) ? 1 : 0;
+    const int sms = device_sm_count();
+    const int per_sm = P.shell_minblocks == 1 ? 1 : 2;
+    const int tiles = shell_tiles(P);
+    if (tiles < 0) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
     if (P.ndim == 3) {
-        if (per_sm == 1) k_shell<3, 1><<<grid, 256, 0, s>>>(P, map, use_tma, (int)tiles);
-        else k_shell<3, 2><<<grid, 256, 0, s>>>(P, map, use_tma, (int)tiles);
+        if (per_sm == 1) k_shell<3, 1, false><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, nullptr);
+        else k_shell<3, 2, false><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, nullptr);
     } else {
-        if (per_sm == 1) k_shell<2, 1><<<grid, 256, 0, s>>>(P, map, use_tma, (int)tiles);
-        else k_shell<2, 2><<<grid, 256, 0, s>>>(P, map, use_tma, (int)tiles);
+        if (per_sm == 1) k_shell<2, 1, false><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, nullptr);
+        else k_shell<2, 2, false><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, nullptr);
     }
     return cudaGetLastError();
 }
@@ -853,14 +986,14 @@ cudaError_t launch_order_tail(const Problem& P, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int N>
-static void launch_tail_n(const Problem& P, int G, int grid, cudaStream_t s)
+template <int N, bool BATCH>
+static void launch_tail_n(const Problem& P, const BatchDesc* bd, int G, int grid, cudaStream_t s)
 {
     switch (G) {
-    case 4: k_tail<N, 4><<<grid, 256, 0, s>>>(P); break;
-    case 8: k_tail<N, 8><<<grid, 256, 0, s>>>(P); break;
-    case 16: k_tail<N, 16><<<grid, 256, 0, s>>>(P); break;
-    default: k_tail<N, 32><<<grid, 256, 0, s>>>(P); break;
+    case 4: k_tail<N, 4, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
+    case 8: k_tail<N, 8, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
+    case 16: k_tail<N, 16, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
+    default: k_tail<N, 32, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
     }
 }
 
@@ -868,8 +1001,61 @@ cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, cudaStream_t s)
 {
     const int sms = device_sm_count();
     const int grid = sms * 8;      // persistent: enough warps to fill every SM
-    if (P.ndim == 3) launch_tail_n<3>(P, lanes_per_voxel, grid, s);
-    else launch_tail_n<2>(P, lanes_per_voxel, grid, s);
+    if (P.ndim == 3) launch_tail_n<3, false>(P, nullptr, lanes_per_voxel, grid, s);
+    else launch_tail_n<2, false>(P, nullptr, lanes_per_voxel, grid, s);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Batched launches (one group = pairs of one dimension)
+// --------------------------------------------------------------------------
+
+cudaError_t launch_batch_prepare(const BatchGroup& g, cudaStream_t s)
+{
+    if (g.npairs <= 0) return cudaSuccess;
+    const int sms = device_sm_count();
+    const int bx = grid_for(g.max_nvox, 256, std::max(1, sms * 8 / std::max(1, g.npairs)) + 1);
+    Problem dummy{};
+    k_prepare<true><<<dim3(bx, g.npairs), 256, 0, s>>>(dummy, g.desc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStream_t s)
+{
+    if (g.npairs <= 0 || g.total_tiles <= 0) return cudaSuccess;
+    const int sms = device_sm_count();
+    const int per_sm = shell_minblocks == 1 ? 1 : 2;
+    const unsigned grid = (unsigned)std::min<long long>(g.total_tiles, (long long)sms * per_sm);
+    Problem dummy{};
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    if (g.ndim == 3) {
+        if (per_sm == 1) k_shell<3, 1, true><<<grid, 256, 0, s>>>(dummy, map, 0, g.total_tiles, g.desc);
+        else k_shell<3, 2, true><<<grid, 256, 0, s>>>(dummy, map, 0, g.total_tiles, g.desc);
+    } else {
+        if (per_sm == 1) k_shell<2, 1, true><<<grid, 256, 0, s>>>(dummy, map, 0, g.total_tiles, g.desc);
+        else k_shell<2, 2, true><<<grid, 256, 0, s>>>(dummy, map, 0, g.total_tiles, g.desc);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s)
+{
+    if (g.npairs <= 0) return cudaSuccess;
+    k_bucket_scan_batch<<<1, 256, 0, s>>>(g.desc);
+    const int sms = device_sm_count();
+    const int bx = std::max(1, sms * 2 / std::max(1, g.npairs)) + 1;
+    k_scatter_batch<<<dim3(bx, g.npairs), 256, 0, s>>>(g.desc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, cudaStream_t s)
+{
+    if (g.npairs <= 0) return cudaSuccess;
+    const int sms = device_sm_count();
+    Problem dummy{};
+    if (g.ndim == 3) launch_tail_n<3, true>(dummy, g.desc, lanes_per_voxel, sms * 8, s);
+    else launch_tail_n<2, true>(dummy, g.desc, lanes_per_voxel, sms * 8, s);
     return cudaGetLastError();
 }
 
