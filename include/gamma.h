@@ -85,6 +85,8 @@ typedef struct {
     int64_t tail_voxels;     /* voxels that searched past the key-0 cells */
     int64_t overflow_voxels; /* voxels that ran past the table and scanned their box */
     int64_t fp64_cells;      /* cells recomputed in FP64 (near-singular Gram matrix) */
+    int64_t seeded;          /* queued voxels seeded by an attached model */
+    int64_t seed_improved;   /* ... whose upper bound the seed lowered */
     int64_t cells_keyed;     /* stats mode: tail cells reached before the early exit */
     int64_t cells_visited;   /* stats mode: tail cells whose faces were evaluated */
     int64_t cells_pruned;    /* stats mode: tail cells skipped by the dose lower bound */
@@ -227,6 +229,59 @@ int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
  * for a batch handle.  Errors as for the runs. */
 int gamma_autotune(gamma_handle h, float *gamma_out_dev, void *cuda_stream, int reps,
                    int64_t *lanes_per_voxel, int64_t *shell_blocks_per_sm, float *best_ms);
+
+/* ---------------------------------------------------------------------------
+ * Learned proposal (no counterpart in the paper).  A 375-128-128-4 network
+ * (ReLU; BF16 weights on the tensor cores, FP32 accumulation) reads a
+ * 5x5x5 patch of three normalised channels around a reference voxel --
+ * (D_e - D_r(v))/dD, |grad D_e| dta/dD, |grad D_r| dta/dD -- and proposes the
+ * offset of the nearest surface point (normalised units x/dta, y/dta, z/dta)
+ * and log(gamma + 1e-3).  When a model is attached to a handle, every voxel
+ * queued for the table walk gets an exact upper bound from the faces of the
+ * cells around the proposed point before the walk; the walk itself is
+ * unchanged, so results stay exact.
+ */
+typedef struct gamma_model_s *gamma_model;
+
+/* New model with He-normal weights drawn from `seed`.  Errors: OOM, CUDA. */
+int gamma_model_create(gamma_model *out, uint64_t seed);
+void gamma_model_destroy(gamma_model m);
+/* Number of FP32 parameters (fixed layout: W1[128][384], b1[128], W2[128][128],
+ * b2[128], W3[8][128], b3[8]; padding entries stay zero). */
+int64_t gamma_model_num_params(void);
+/* Copy parameters (which = 0), gradients of the last backward (1) or the Adam
+ * moments (2, 3) to host memory of n = gamma_model_num_params() floats. */
+int gamma_model_get_params(gamma_model m, float *host, int64_t n, int which);
+int gamma_model_set_params(gamma_model m, const float *host, int64_t n);
+/* Forward a batch: X_bf16_dev is M x 384 bfloat16 (device), Y_dev M x 4 float. */
+int gamma_model_forward(gamma_model m, const void *X_bf16_dev, int64_t M, float *Y_dev,
+                        void *cuda_stream);
+/* Gradients of the mean Huber loss (delta 1) against targets T_dev (M x 4
+ * float, rows with a NaN last column are ignored); loss_out optional (host). */
+int gamma_model_backward(gamma_model m, const void *X_bf16_dev, const float *T_dev, int64_t M,
+                         float *loss_out, void *cuda_stream);
+/* backward + one Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr. */
+int gamma_model_train_step(gamma_model m, const void *X_bf16_dev, const float *T_dev, int64_t M,
+                           float lr, float *loss_out, void *cuda_stream);
+/* Binary weights file (magic "GAMMAMLP", version 1, shapes, Adam state). */
+int gamma_model_save(gamma_model m, const char *path);
+int gamma_model_load(gamma_model m, const char *path);
+
+/* Features of the listed voxels of a handle's dose pair: X_bf16_dev gets
+ * n x 384 bfloat16.  Global criteria with dose_norm <= 0 use the dose norm of
+ * the handle's last run (run it first). */
+int gamma_features(gamma_handle h, const uint32_t *voxels_dev, int64_t n, void *X_bf16_dev,
+                   void *cuda_stream);
+/* Training targets of the listed voxels from a finished gamma map of the same
+ * handle: targets_dev gets n x 4 floats (nearest-point offset in normalised
+ * units, log(gamma + 1e-3)); NaN rows for voxels not evaluated or beyond the
+ * table. */
+int gamma_labels(gamma_handle h, const float *gamma_map_dev, const uint32_t *voxels_dev,
+                 int64_t n, float *targets_dev, void *cuda_stream);
+/* Attach a model to a single-pair handle (borrowed; NULL detaches) or load one
+ * from a file that the handle then owns. */
+int gamma_set_model(gamma_handle h, gamma_model m);
+int gamma_load_model(gamma_handle h, const char *path);
 
 /* Static description of a status code. */
 const char *gamma_strerror(int code);

@@ -19,7 +19,11 @@ __all__ = [
     "gamma_run", "gamma_run_host", "gamma_pass_rate", "gamma_get_stats", "gamma_get_timings",
     "gamma_set_option",
     "gamma_run_noalloc", "gamma_batch_create", "gamma_batch_run", "gamma_batch_pass_rate",
-    "gamma_batch_get_stats", "gamma_autotune", "gamma_pair_desc", "gamma_destroy", "gamma_strerror", "gamma_version", "library_path",
+    "gamma_batch_get_stats", "gamma_autotune", "gamma_pair_desc", "gamma_destroy",
+    "gamma_model_create", "gamma_model_destroy", "gamma_model_num_params", "gamma_model_get_params",
+    "gamma_model_set_params", "gamma_model_forward", "gamma_model_backward",
+    "gamma_model_train_step", "gamma_model_save", "gamma_model_load", "gamma_features",
+    "gamma_labels", "gamma_set_model", "gamma_load_model", "gamma_strerror", "gamma_version", "library_path",
     "criteria",
     "GLOBAL", "LOCAL",
 ]
@@ -36,6 +40,7 @@ class gamma_stats(ctypes.Structure):
     _fields_ = [("n_voxels", ctypes.c_int64), ("n_eval", ctypes.c_int64),
                 ("n_pass", ctypes.c_int64), ("tail_voxels", ctypes.c_int64),
                 ("overflow_voxels", ctypes.c_int64), ("fp64_cells", ctypes.c_int64),
+                ("seeded", ctypes.c_int64), ("seed_improved", ctypes.c_int64),
                 ("cells_keyed", ctypes.c_int64), ("cells_visited", ctypes.c_int64),
                 ("cells_pruned", ctypes.c_int64), ("d_norm", ctypes.c_double),
                 ("r_max", ctypes.c_double), ("table_entries", ctypes.c_int64),
@@ -101,6 +106,23 @@ def _load():
     lib.gamma_batch_get_stats.argtypes = [vp, ctypes.c_int, ctypes.POINTER(gamma_stats)]
     lib.gamma_autotune.argtypes = [vp, vp, vp, ctypes.c_int, i64p, i64p,
                                    ctypes.POINTER(ctypes.c_float)]
+    lib.gamma_model_create.argtypes = [ctypes.POINTER(vp), ctypes.c_uint64]
+    lib.gamma_model_destroy.argtypes = [vp]
+    lib.gamma_model_destroy.restype = None
+    lib.gamma_model_num_params.restype = ctypes.c_int64
+    lib.gamma_model_get_params.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int]
+    lib.gamma_model_set_params.argtypes = [vp, vp, ctypes.c_int64]
+    lib.gamma_model_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    lib.gamma_model_backward.argtypes = [vp, vp, vp, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_float), vp]
+    lib.gamma_model_train_step.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_float), vp]
+    lib.gamma_model_save.argtypes = [vp, ctypes.c_char_p]
+    lib.gamma_model_load.argtypes = [vp, ctypes.c_char_p]
+    lib.gamma_features.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    lib.gamma_labels.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp]
+    lib.gamma_set_model.argtypes = [vp, vp]
+    lib.gamma_load_model.argtypes = [vp, ctypes.c_char_p]
     lib.gamma_destroy.argtypes = [vp]
     lib.gamma_destroy.restype = None
     lib.gamma_strerror.argtypes = [ctypes.c_int]
@@ -266,6 +288,92 @@ def gamma_autotune(h: int, gamma_out_dev=None, stream=None, reps: int = 3):
                                ctypes.byref(lanes), ctypes.byref(blocks), ctypes.byref(ms)),
            "gamma_autotune")
     return lanes.value, blocks.value, ms.value
+
+
+# ---- learned proposal ----
+
+def _raw_ptr(t) -> int:
+    """Device pointer of any contiguous CUDA tensor (bf16, float32, int32...)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def gamma_model_create(seed: int = 0) -> int:
+    m = ctypes.c_void_p()
+    _check(_lib.gamma_model_create(ctypes.byref(m), int(seed)), "gamma_model_create")
+    return m.value
+
+
+def gamma_model_destroy(m: Optional[int]) -> None:
+    if m:
+        _lib.gamma_model_destroy(m)
+
+
+def gamma_model_num_params() -> int:
+    return int(_lib.gamma_model_num_params())
+
+
+def gamma_model_get_params(m: int, which: int = 0):
+    import numpy as np
+    n = gamma_model_num_params()
+    out = np.empty(n, dtype=np.float32)
+    _check(_lib.gamma_model_get_params(m, out.ctypes.data, n, int(which)), "gamma_model_get_params")
+    return out
+
+
+def gamma_model_set_params(m: int, params) -> None:
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib.gamma_model_set_params(m, p.ctypes.data, p.size), "gamma_model_set_params")
+
+
+def gamma_model_forward(m: int, X_bf16, Y, stream=None) -> None:
+    _check(_lib.gamma_model_forward(m, _raw_ptr(X_bf16), int(X_bf16.shape[0]), _raw_ptr(Y),
+                                    _stream_ptr(stream)), "gamma_model_forward")
+
+
+def gamma_model_backward(m: int, X_bf16, T, stream=None) -> float:
+    loss = ctypes.c_float()
+    _check(_lib.gamma_model_backward(m, _raw_ptr(X_bf16), _raw_ptr(T), int(X_bf16.shape[0]),
+                                     ctypes.byref(loss), _stream_ptr(stream)),
+           "gamma_model_backward")
+    return loss.value
+
+
+def gamma_model_train_step(m: int, X_bf16, T, lr: float, stream=None, want_loss: bool = True):
+    loss = ctypes.c_float()
+    _check(_lib.gamma_model_train_step(m, _raw_ptr(X_bf16), _raw_ptr(T), int(X_bf16.shape[0]),
+                                       float(lr), ctypes.byref(loss) if want_loss else None,
+                                       _stream_ptr(stream)), "gamma_model_train_step")
+    return loss.value if want_loss else None
+
+
+def gamma_model_save(m: int, path: str) -> None:
+    _check(_lib.gamma_model_save(m, str(path).encode()), "gamma_model_save")
+
+
+def gamma_model_load(m: int, path: str) -> None:
+    _check(_lib.gamma_model_load(m, str(path).encode()), "gamma_model_load")
+
+
+def gamma_features(h: int, voxels, X_bf16, stream=None) -> None:
+    _check(_lib.gamma_features(h, _raw_ptr(voxels), int(voxels.numel()), _raw_ptr(X_bf16),
+                               _stream_ptr(stream)), "gamma_features")
+
+
+def gamma_labels(h: int, gamma_map, voxels, targets, stream=None) -> None:
+    _check(_lib.gamma_labels(h, _dev_ptr(gamma_map), _raw_ptr(voxels), int(voxels.numel()),
+                             _raw_ptr(targets), _stream_ptr(stream)), "gamma_labels")
+
+
+def gamma_set_model(h: int, m: Optional[int]) -> None:
+    _check(_lib.gamma_set_model(h, m or 0), "gamma_set_model")
+
+
+def gamma_load_model(h: int, path: str) -> None:
+    _check(_lib.gamma_load_model(h, str(path).encode()), "gamma_load_model")
 
 
 def gamma_destroy(h: Optional[int]) -> None:

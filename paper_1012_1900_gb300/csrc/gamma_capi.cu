@@ -96,6 +96,8 @@ struct gamma_ctx {
     int sort_tail = 1;
     int timing = 0;
     int shell_minblocks = 2;
+    gamma_model model = nullptr;      // attached proposal network (may be null)
+    bool own_model = false;
     // per-phase events: 0 start, 1 after h2d, 2 after prepare, 3 after shell,
     // 4 after order, 5 after tail, 6 after d2h
     cudaEvent_t tev[7] = {};
@@ -241,6 +243,7 @@ void free_ctx(gamma_ctx* h)
 {
     if (!h) return;
     if (h->batch) free_batch(h->batch);
+    if (h->own_model) gamma_model_destroy(h->model);
     for (auto& e : h->tev)
         if (e) cudaEventDestroy(e);
     cudaFree(h->table_dev);
@@ -424,6 +427,8 @@ Counters sum_counters(const std::vector<Counters>& cs)
         t.tail_count += c.tail_count;
         t.overflow_count += c.overflow_count;
         t.fp64_cells += c.fp64_cells;
+        t.seeded += c.seeded;
+        t.seed_improved += c.seed_improved;
         if (gk::fdec(c.rmax_enc) > gk::fdec(t.rmax_enc) || t.rmax_enc == 0) t.rmax_enc = c.rmax_enc;
     }
     return t;
@@ -507,6 +512,12 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
     CK(gk::launch_prepare(P, s));
     if (tm) CK(cudaEventRecord(h->tev[2], s));
     CK(gk::launch_shell(P, s));
+    if (h->model) {
+        gk::MlpWeights W;
+        gk::model_weights(h->model, &W);
+        CK(cudaMemsetAsync(h->ctr->hist, 0, sizeof(h->ctr->hist), s));
+        CK(gk::launch_learned(P, W, s));
+    }
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     CK(gk::launch_order_tail(P, s));
     if (tm) CK(cudaEventRecord(h->tev[4], s));
@@ -589,6 +600,8 @@ int gamma_get_stats(gamma_handle h, gamma_stats* out)
     out->tail_voxels = (int64_t)c.tail_count;
     out->overflow_voxels = (int64_t)c.overflow_count;
     out->fp64_cells = (int64_t)c.fp64_cells;
+    out->seeded = (int64_t)c.seeded;
+    out->seed_improved = (int64_t)c.seed_improved;
     out->cells_keyed = (int64_t)c.cells_keyed;
     out->cells_visited = (int64_t)c.cells_visited;
     out->cells_pruned = (int64_t)c.cells_pruned;
@@ -838,6 +851,57 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     if (lanes_per_voxel) *lanes_per_voxel = best_l;
     if (shell_blocks_per_sm) *shell_blocks_per_sm = best_b;
     if (best_ms) *best_ms = best;
+    return GAMMA_OK;
+}
+
+int gamma_features(gamma_handle h, const uint32_t* voxels_dev, int64_t n, void* X_bf16_dev,
+                   void* cuda_stream)
+{
+    if (!h || h->batch || !voxels_dev || !X_bf16_dev || n < 0) return GAMMA_ERR_INVALID_ARG;
+    if (n == 0) return GAMMA_OK;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    const Problem P = make_problem(h, nullptr);
+    CK(gk::launch_features(P, voxels_dev, n, (__nv_bfloat16*)X_bf16_dev, (cudaStream_t)cuda_stream));
+    return GAMMA_OK;
+}
+
+int gamma_labels(gamma_handle h, const float* gamma_map_dev, const uint32_t* voxels_dev, int64_t n,
+                 float* targets_dev, void* cuda_stream)
+{
+    if (!h || h->batch || !gamma_map_dev || !voxels_dev || !targets_dev || n < 0)
+        return GAMMA_ERR_INVALID_ARG;
+    if (n == 0) return GAMMA_OK;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    const Problem P = make_problem(h, nullptr);
+    CK(gk::launch_labels(P, gamma_map_dev, voxels_dev, n, targets_dev, (cudaStream_t)cuda_stream));
+    return GAMMA_OK;
+}
+
+int gamma_set_model(gamma_handle h, gamma_model m)
+{
+    if (!h || h->batch) return GAMMA_ERR_INVALID_ARG;
+    if (h->own_model) gamma_model_destroy(h->model);
+    h->model = m;
+    h->own_model = false;
+    return GAMMA_OK;
+}
+
+int gamma_load_model(gamma_handle h, const char* path)
+{
+    if (!h || h->batch || !path) return GAMMA_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    gamma_model m = nullptr;
+    if (int rc = gamma_model_create(&m, 0)) return rc;
+    if (int rc = gamma_model_load(m, path)) {
+        gamma_model_destroy(m);
+        return rc;
+    }
+    if (h->own_model) gamma_model_destroy(h->model);
+    h->model = m;
+    h->own_model = true;
     return GAMMA_OK;
 }
 

@@ -109,13 +109,20 @@ __host__ __device__ __forceinline__ void cell_geom(int cx, int cy, int cz, const
     }
 }
 
-// Squared distance to the owned face with chain (U1[, U2[, U3]]), or +inf
-// when the projection falls outside the face or the face leaves the grid.
-// Also raises `ill` when the face's Gram matrix is near singular in the
-// normalised-determinant sense det(G) / prod(G_ii) < tau.
+// Projection of the origin onto the owned face with chain (U1[, U2[, U3]]).
+// d2 is the squared distance, or +inf when the projection falls outside the
+// face or the face leaves the grid; mu are the coefficients of the chain
+// increments (the foot point is s0 + sum_i mu_i e_i).  Raises `ill` when the
+// face's Gram matrix is near singular in the normalised-determinant sense
+// det(G) / prod(G_ii) < tau.
+template <typename T>
+struct FaceFoot {
+    T d2, mu1, mu2, mu3;
+};
+
 template <int M, int U1, int U2, int U3, typename T>
-__device__ __forceinline__ T face_d2(const T (&q)[8], uint32_t ok, const CellGeom<T>& g,
-                                     const T (&kappa)[8], T tau, bool& ill)
+__device__ __forceinline__ FaceFoot<T> face_core(const T (&q)[8], uint32_t ok, const CellGeom<T>& g,
+                                                 const T (&kappa)[8], T tau, bool& ill)
 {
     constexpr int UM = M == 1 ? U1 : (M == 2 ? U2 : U3);
     constexpr int A1 = U1, A2 = U2 ^ U1, A3 = U3 ^ U2;
@@ -140,17 +147,20 @@ __device__ __forceinline__ T face_d2(const T (&q)[8], uint32_t ok, const CellGeo
         rho2 += g.br[A3];
     }
     const T r = div_(L, D);
-    const T mu1 = fma_(-r, k1, g.beta[A1]);
-    bool valid = mu1 <= T(1);
-    T last = mu1;
+    FaceFoot<T> f;
+    f.mu1 = fma_(-r, k1, g.beta[A1]);
+    f.mu2 = T(0);
+    f.mu3 = T(0);
+    bool valid = f.mu1 <= T(1);
+    T last = f.mu1;
     if constexpr (M >= 2) {
-        const T mu2 = fma_(-r, k2, g.beta[A2]);
-        valid = valid && (mu1 >= mu2);
-        last = mu2;
+        f.mu2 = fma_(-r, k2, g.beta[A2]);
+        valid = valid && (f.mu1 >= f.mu2);
+        last = f.mu2;
         if constexpr (M >= 3) {
-            const T mu3 = fma_(-r, k3, g.beta[A3]);
-            valid = valid && (mu2 >= mu3);
-            last = mu3;
+            f.mu3 = fma_(-r, k3, g.beta[A3]);
+            valid = valid && (f.mu2 >= f.mu3);
+            last = f.mu3;
         }
         // normalised Gram determinant (1 + |g|^2) / prod(1 + g_i^2)
         T prod = fma_(d1, k1, T(1)) * fma_(d2, k2, T(1));
@@ -158,7 +168,15 @@ __device__ __forceinline__ T face_d2(const T (&q)[8], uint32_t ok, const CellGeo
         ill = ill || (D < tau * prod);
     }
     valid = valid && (last >= T(0)) && ((ok >> UM) & 1u);
-    return valid ? fma_(L, r, rho2) : T(kInf);
+    f.d2 = valid ? fma_(L, r, rho2) : T(kInf);
+    return f;
+}
+
+template <int M, int U1, int U2, int U3, typename T>
+__device__ __forceinline__ T face_d2(const T (&q)[8], uint32_t ok, const CellGeom<T>& g,
+                                     const T (&kappa)[8], T tau, bool& ill)
+{
+    return face_core<M, U1, U2, U3, T>(q, ok, g, kappa, tau, ill).d2;
 }
 
 template <int M, int U1, int U2, int U3>
@@ -216,6 +234,45 @@ __device__ __forceinline__ T cell_min_d2(const T (&q)[8], uint32_t ok, const Cel
     best = min_(best, fma_(q[0], q[0], g.tsum[0]));            // the vertex itself
     apply_all<T>((typename FaceList<N>::type*)nullptr, q, ok, g, mt.kappa, tau, best, ill);
     return best;
+}
+
+// Argmin variant: the minimum over the cell's faces of the squared distance
+// and the foot point, in voxel units relative to the cell's lower corner.
+template <typename T, int M, int U1, int U2, int U3>
+__device__ __forceinline__ void arg_face(Face<M, U1, U2, U3>, const T (&q)[8], uint32_t ok,
+                                         const CellGeom<T>& g, const T (&kappa)[8], T& best,
+                                         T (&foot)[3])
+{
+    bool ill = false;
+    const FaceFoot<T> f = face_core<M, U1, U2, U3, T>(q, ok, g, kappa, T(0), ill);
+    if (f.d2 < best) {
+        best = f.d2;
+        constexpr int A1 = U1, A2 = U2 ^ U1, A3 = U3 ^ U2;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            foot[a] = ((A1 >> a) & 1 ? f.mu1 : T(0)) + (M >= 2 && ((A2 >> a) & 1) ? f.mu2 : T(0)) +
+                      (M >= 3 && ((A3 >> a) & 1) ? f.mu3 : T(0));
+    }
+}
+
+template <typename T, typename... Fs>
+__device__ __forceinline__ void arg_all(std::tuple<Fs...>*, const T (&q)[8], uint32_t ok,
+                                        const CellGeom<T>& g, const T (&kappa)[8], T& best,
+                                        T (&foot)[3])
+{
+    (arg_face(Fs{}, q, ok, g, kappa, best, foot), ...);
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void cell_argmin(const T (&q)[8], uint32_t ok, const CellGeom<T>& g,
+                                            const MetricT<T>& mt, T& best, T (&foot)[3])
+{
+    const T dv = fma_(q[0], q[0], g.tsum[0]);
+    if (dv < best) {
+        best = dv;
+        foot[0] = foot[1] = foot[2] = T(0);
+    }
+    arg_all<T>((typename FaceList<N>::type*)nullptr, q, ok, g, mt.kappa, best, foot);
 }
 
 }  // namespace gk

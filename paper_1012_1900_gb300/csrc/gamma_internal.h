@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 
 #include "gamma_face.cuh"
+#include "gamma_mlp.cuh"
+
+struct gamma_model_s;
 
 namespace gk {
 
@@ -52,7 +55,9 @@ struct Counters {
     unsigned int head;
     unsigned int overflow_count;        // voxels that needed the box scan
     unsigned int fp64_cells;            // cells redone in FP64
-    unsigned int pad;
+    unsigned int seed_head;             // work counter of the learned seeding pass
+    unsigned int seeded;                // queued voxels the proposal network seeded
+    unsigned int seed_improved;         // ... whose bound the seed lowered
     unsigned int hist[kNumBuckets];
     unsigned int cursor[kNumBuckets];
 };
@@ -145,6 +150,14 @@ void fill_shell_constants(Problem& P);
 // Tile-load map for a Problem; false when TMA cannot be used for it.
 bool encode_tile_map(const Problem& P, CUtensorMap* map);
 int shell_tiles(const Problem& P);
+
+// Learned proposal (gamma_learned.cu).
+bool model_weights(const gamma_model_s* m, MlpWeights* w);
+cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s);
+cudaError_t launch_features(const Problem& P, const unsigned* vox, long long n, __nv_bfloat16* X,
+                            cudaStream_t s);
+cudaError_t launch_labels(const Problem& P, const float* gmap, const unsigned* vox, long long n,
+                          float* T, cudaStream_t s);
 
 // Batched launches over one group: prepare, shell, ordering, table walk.
 cudaError_t launch_batch_prepare(const BatchGroup& g, cudaStream_t s);

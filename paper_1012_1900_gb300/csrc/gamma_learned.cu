@@ -1,0 +1,974 @@
+// Learned proposal for the gamma search: patch features, labels from the exact
+// search, a 375-128-128-4 BF16 network trained and run with hand-written
+// tensor-core kernels, and the seeding pass that turns its proposal into an
+// exact upper bound before the table walk.
+//
+// None of this is in the paper.  The network never decides a result: its
+// proposed nearest point only selects cells whose faces are evaluated
+// exactly, and the distance found is a true distance to the evaluation
+// surface, hence a valid upper bound on gamma.  The exact walk (Algorithm A1
+// step 4) then runs unchanged from that bound.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gamma.h"
+#include "gamma_internal.h"
+#include "gamma_mlp.cuh"
+
+namespace gk {
+
+using bf16 = __nv_bfloat16;
+
+// --------------------------------------------------------------------------
+// Features
+// --------------------------------------------------------------------------
+
+// Gradient magnitude of dose D at grid point p, in normalised units
+// (dose / dD per length / dta): central differences inside, one-sided at the
+// grid edge.
+template <int N>
+__device__ __forceinline__ float grad_norm(const float* __restrict__ D, const Problem& P, int px,
+                                           int py, int pz, long long p)
+{
+    const int c[3] = {px, py, pz};
+    const int n[3] = {P.nx, P.ny, P.nz};
+    const long long st[3] = {1, (long long)P.nx, (long long)P.nx * P.ny};
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        float d;
+        if (c[a] > 0 && c[a] < n[a] - 1) d = (__ldg(D + p + st[a]) - __ldg(D + p - st[a])) / (2.f * P.hn[a]);
+        else if (c[a] == 0) d = (__ldg(D + p + st[a]) - __ldg(D + p)) / P.hn[a];
+        else d = (__ldg(D + p) - __ldg(D + p - st[a])) / P.hn[a];
+        s = fmaf(d, d, s);
+    }
+    return sqrtf(s);
+}
+
+// Feature f (0..kInPad-1) of reference voxel (x, y, z): channel f / 125 over
+// the 5^N patch p = v + o, o in {-2..2}^N (patch index f % 125, x fastest):
+//   0: (D_e(p) - D_r(v)) / dD          clamped to [-16, 16]
+//   1: |grad D_e(p)| * dta / dD        clamped to [0, 32]
+//   2: |grad D_r(p)| * dta / dD        clamped to [0, 32]
+// zero outside the grid and for f >= 375 (2D uses the first 25 of each 125).
+template <int N>
+__device__ __forceinline__ float voxel_feature(const Problem& P, int x, int y, int z, float dr,
+                                               float inv, int f)
+{
+    if (f >= kIn) return 0.f;
+    const int ch = f / 125, pi = f % 125;
+    const int ox = pi % 5 - 2, oy = (pi / 5) % 5 - 2, oz = pi / 25 - 2;
+    if (N == 2 && oz != -2) return 0.f;
+    const int px = x + ox, py = y + oy, pz = N == 3 ? z + oz : 0;
+    if ((unsigned)px >= (unsigned)P.nx || (unsigned)py >= (unsigned)P.ny ||
+        (N == 3 && (unsigned)pz >= (unsigned)P.nz))
+        return 0.f;
+    const long long p = ((long long)pz * P.ny + py) * P.nx + px;
+    if (ch == 0) return fminf(fmaxf((__ldg(P.ev + p) - dr) * inv, -16.f), 16.f);
+    const float gmag = grad_norm<N>(ch == 1 ? P.ev : P.ref, P, px, py, pz, p);
+    return fminf(gmag * inv, 32.f);
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_features(const __grid_constant__ Problem P,
+                                                  const unsigned* __restrict__ vox, long long n,
+                                                  bf16* __restrict__ X)
+{
+    const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
+    const long long total = n * kInPad;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / kInPad;
+        const int f = (int)(e % kInPad);
+        const unsigned v = vox[i];
+        const int x = (int)(v % (unsigned)P.nx);
+        const unsigned r1 = v / (unsigned)P.nx;
+        const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
+        const float dr = __ldg(P.ref + v);
+        const float dD = P.dd_frac * (P.local ? dr : dnorm);
+        const float inv = dD > 0.f ? 1.0f / dD : 0.f;
+        X[e] = __float2bfloat16(voxel_feature<N>(P, x, y, z, dr, inv, f));
+    }
+}
+
+// --------------------------------------------------------------------------
+// Cells around an arbitrary offset (labels and seeds)
+// --------------------------------------------------------------------------
+
+template <int N>
+__device__ __forceinline__ bool load_cell(const Problem& P, int x, int y, int z, int cx, int cy,
+                                          int cz, float dr, float inv, float (&q)[8], uint32_t& ok)
+{
+    const int px = x + cx, py = y + cy, pz = z + cz;
+    if ((unsigned)px >= (unsigned)P.nx || (unsigned)py >= (unsigned)P.ny ||
+        (N == 3 && (unsigned)pz >= (unsigned)P.nz))
+        return false;
+    const bool ex = px + 1 < P.nx, ey = py + 1 < P.ny, ez = N == 3 && pz + 1 < P.nz;
+    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+    const long long p = (long long)pz * sz + (long long)py * sy + px;
+    ok = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        q[u] = 0.f;
+        if (u < (1 << N)) {
+            const bool present = (!(u & 1) || ex) && (!(u & 2) || ey) && (!(u & 4) || ez);
+            if (present) {
+                const long long o = p + ((u & 1) ? 1 : 0) + ((u & 2) ? sy : 0) + ((u & 4) ? sz : 0);
+                q[u] = (__ldg(P.ev + o) - dr) * inv;
+                ok |= 1u << u;
+            }
+        }
+    }
+    return true;
+}
+
+// Labels: for each listed voxel, the nearest point of the evaluation surface
+// (re-walking the table up to the gamma already computed) as an offset in
+// normalised spatial units, and log(gamma + 1e-3).  Rows whose search would
+// leave the table, or whose voxel is not evaluated, get NaN.
+template <int N>
+__global__ void __launch_bounds__(128) k_labels(const __grid_constant__ Problem P,
+                                                const float* __restrict__ gmap,
+                                                const unsigned* __restrict__ vox, long long n,
+                                                float* __restrict__ T)
+{
+    const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned v = vox[i];
+        const float gs = gmap[v];
+        float* t = T + 4 * i;
+        if (!(gs >= 0.f) || gs > P.r_cover) {
+            t[0] = t[1] = t[2] = t[3] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const int x = (int)(v % (unsigned)P.nx);
+        const unsigned r1 = v / (unsigned)P.nx;
+        const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
+        const float dr = __ldg(P.ref + v);
+        const float inv = 1.0f / (P.dd_frac * (P.local ? dr : dnorm));
+        const float lim = gs * (1.f + 1e-5f) + 1e-6f;
+        float best = kInf, foot[3] = {0.f, 0.f, 0.f}, fv[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < P.ntable; ++k) {
+            const TableEntry e = P.table[k];
+            if (e.key > lim) break;
+            const int cx = unpack10(e.off, 0), cy = unpack10(e.off, 10), cz = unpack10(e.off, 20);
+            float q[8];
+            uint32_t ok;
+            if (!load_cell<N>(P, x, y, z, cx, cy, cz, dr, inv, q, ok)) continue;
+            CellGeom<float> g;
+            cell_geom<N, float>(cx, cy, cz, P.mt, g);
+            const float before = best;
+            cell_argmin<N, float>(q, ok, g, P.mt, best, foot);
+            if (best < before) {
+                fv[0] = cx + foot[0];
+                fv[1] = cy + foot[1];
+                fv[2] = cz + foot[2];
+            }
+        }
+        t[0] = fv[0] * P.hn[0];
+        t[1] = fv[1] * P.hn[1];
+        t[2] = N == 3 ? fv[2] * P.hn[2] : 0.f;
+        t[3] = logf(gs + 1e-3f);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Generic BF16 GEMM for training (mma.sync m16n8k16, FP32 accumulation)
+//   C[m][n] (+)= sum_k A'(m, k) B'(n, k)
+//   A'(m, k) = TA ? A[k * lda + m] : A[m * lda + k]
+//   B'(n, k) = TB ? B[k * ldb + n] : B[n * ldb + k]
+// 64 x 64 tiles, 4 warps of 16 rows; split-K over gridDim.z with ATOMIC.
+// --------------------------------------------------------------------------
+
+template <bool TA, bool TB, bool ATOMIC>
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16* __restrict__ A,
+                                              int lda, const bf16* __restrict__ B, int ldb,
+                                              float* __restrict__ C, int ldc)
+{
+    constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;
+    __shared__ __align__(16) bf16 As[BM * LDS];
+    __shared__ __align__(16) bf16 Bs[BN * LDS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kslice = (K + gridDim.z - 1) / gridDim.z;
+    const int kbeg = blockIdx.z * kslice, kend = min(K, kbeg + kslice);
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const bf16 zero = __float2bfloat16(0.f);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
+            int r, c;
+            if (TA) { c = e / BM; r = e % BM; } else { r = e / BK; c = e % BK; }
+            const int m = m0 + r, k = k0 + c;
+            As[r * LDS + c] = (m < M && k < kend) ? (TA ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : zero;
+        }
+        for (int e = threadIdx.x; e < BN * BK; e += blockDim.x) {
+            int r, c;
+            if (TB) { c = e / BN; r = e % BN; } else { r = e / BK; c = e % BK; }
+            const int nn = n0 + r, k = k0 + c;
+            Bs[r * LDS + c] = (nn < N && k < kend) ? (TB ? B[(long long)k * ldb + nn] : B[(long long)nn * ldb + k]) : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            uint32_t a[4];
+            load_a_frag(a, As + warp * 16 * LDS + ks, LDS, lane);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                uint32_t b[2];
+                load_b_frag(b, Bs + j * 8 * LDS + ks, LDS, lane);
+                mma_bf16_16816(acc[j], a, b);
+            }
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int m = m0 + warp * 16 + g + (h >= 2 ? 8 : 0);
+            const int nn = n0 + j * 8 + 2 * t + (h & 1);
+            if (m < M && nn < N) {
+                float* dst = C + (long long)m * ldc + nn;
+                if (ATOMIC) atomicAdd(dst, acc[j][h]);
+                else *dst = acc[j][h];
+            }
+        }
+}
+
+// Z (M x N, fp32) += bias; H = bf16(relu(Z)) (or bf16(Z) without relu).
+__global__ void k_bias_act(long long M, int N, float* __restrict__ Z, const float* __restrict__ bias,
+                           bf16* __restrict__ H, int ldh, int relu)
+{
+    const long long total = M * N;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % N);
+        const float z = Z[e] + bias[c];
+        Z[e] = z;
+        if (H) H[(e / N) * ldh + c] = __float2bfloat16(relu ? fmaxf(z, 0.f) : z);
+    }
+}
+
+// Huber loss (delta 1) per output, averaged over the rows with finite
+// targets; dY = dloss / dy.  Y: M x kOutPad, T: M x kOut.
+__global__ void k_huber(long long M, const float* __restrict__ Y, const float* __restrict__ T,
+                        float* __restrict__ dY, float* __restrict__ loss, float inv_count)
+{
+    float acc = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x) {
+        const bool valid = isfinite(T[4 * i + 3]);
+#pragma unroll
+        for (int j = 0; j < kOut; ++j) {
+            const float r = valid ? Y[i * kOutPad + j] - T[4 * i + j] : 0.f;
+            const float a = fabsf(r);
+            acc += a <= 1.f ? 0.5f * r * r : a - 0.5f;
+            dY[4 * i + j] = (a <= 1.f ? r : copysignf(1.f, r)) * inv_count;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * inv_count);
+}
+
+// Output layer backward on CUDA cores (K = 4 is too thin for the tensor
+// cores): dZ2 = (dY W3) * [Z2 > 0] (bf16), and the partial sums of
+// dW3 = dY^T H2, db3 = sum dY.
+__global__ void k_out_back(long long M, const float* __restrict__ dY, const float* __restrict__ W3,
+                           const float* __restrict__ Z2, const bf16* __restrict__ H2,
+                           bf16* __restrict__ dZ2, float* __restrict__ gW3, float* __restrict__ gb3)
+{
+    __shared__ float sW3[kOut * kH];
+    __shared__ float sg[kOut * kH + kOut];
+    for (int i = threadIdx.x; i < kOut * kH; i += blockDim.x) {
+        sW3[i] = W3[i];
+        sg[i] = 0.f;
+    }
+    if (threadIdx.x < kOut) sg[kOut * kH + threadIdx.x] = 0.f;
+    __syncthreads();
+    const int c = threadIdx.x % kH;                  // blockDim.x is a multiple of kH
+    const int rstep = blockDim.x / kH;
+    float gw[kOut] = {0.f, 0.f, 0.f, 0.f}, gb[kOut] = {0.f, 0.f, 0.f, 0.f};
+    for (long long m = (long long)blockIdx.x * rstep + threadIdx.x / kH; m < M;
+         m += (long long)gridDim.x * rstep) {
+        float d = 0.f;
+#pragma unroll
+        for (int j = 0; j < kOut; ++j) d = fmaf(dY[4 * m + j], sW3[j * kH + c], d);
+        dZ2[m * kH + c] = __float2bfloat16(Z2[m * kH + c] > 0.f ? d : 0.f);
+        const float h = __bfloat162float(H2[m * kH + c]);
+#pragma unroll
+        for (int j = 0; j < kOut; ++j) {
+            gw[j] = fmaf(dY[4 * m + j], h, gw[j]);
+            if (c == 0) gb[j] += dY[4 * m + j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kOut; ++j) {
+        atomicAdd(&sg[j * kH + c], gw[j]);
+        if (c == 0) atomicAdd(&sg[kOut * kH + j], gb[j]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOut * kH; i += blockDim.x) atomicAdd(&gW3[i], sg[i]);
+    if (threadIdx.x < kOut) atomicAdd(&gb3[threadIdx.x], sg[kOut * kH + threadIdx.x]);
+}
+
+// dZ = bf16(dH * [Z > 0]) and the column sums of dZ (bias gradient).
+__global__ void k_relu_back(long long M, int N, const float* __restrict__ dH,
+                            const float* __restrict__ Z, bf16* __restrict__ dZ,
+                            float* __restrict__ gb)
+{
+    const long long total = M * N;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float d = Z[e] > 0.f ? dH[e] : 0.f;
+        dZ[e] = __float2bfloat16(d);
+    }
+    (void)gb;
+}
+
+// Column sums of a bf16 matrix (M x N) into gb (atomic).
+__global__ void k_colsum(long long M, int N, const bf16* __restrict__ D, float* __restrict__ gb)
+{
+    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    float s = 0.f;
+    for (long long m = blockIdx.x; m < M; m += gridDim.x) s += __bfloat162float(D[m * N + c]);
+    atomicAdd(&gb[c], s);
+}
+
+// Adam on the FP32 master parameters; padded entries (mask == 0) stay zero.
+__global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, const unsigned char* __restrict__ mask,
+                       float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!mask[i]) continue;
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// bf16 copies of the weights (and W2^T for the backward GEMM).
+__global__ void k_cast_weights(const float* __restrict__ W1, const float* __restrict__ W2,
+                               const float* __restrict__ W3, bf16* __restrict__ W1h,
+                               bf16* __restrict__ W2h, bf16* __restrict__ W2Th,
+                               bf16* __restrict__ W3h)
+{
+    const int total = kH * kInPad + 2 * kH * kH + kOutPad * kH;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        if (e < kH * kInPad) {
+            W1h[e] = __float2bfloat16(W1[e]);
+        } else if (e < kH * kInPad + kH * kH) {
+            const int i = e - kH * kInPad;
+            W2h[i] = __float2bfloat16(W2[i]);
+        } else if (e < kH * kInPad + 2 * kH * kH) {
+            const int i = e - kH * kInPad - kH * kH;
+            const int r = i / kH, c = i % kH;            // W2T[r][c] = W2[c][r]
+            W2Th[i] = __float2bfloat16(W2[c * kH + r]);
+        } else {
+            const int i = e - kH * kInPad - 2 * kH * kH;
+            W3h[i] = __float2bfloat16(W3[i]);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Fused inference + seeding over the queued voxels
+// --------------------------------------------------------------------------
+
+constexpr int kRows = 128;                 // voxels per block iteration
+constexpr int kLdX = kInPad + 8;           // smem row strides (bf16), padded
+constexpr int kLdH = kH + 8;
+constexpr int kKc = 64;                    // K chunk of the streamed weights
+constexpr int kLdW = kKc + 8;
+
+struct LearnSmem {
+    bf16 X[kRows * kLdX];                  // features, later H2
+    bf16 H1[kRows * kLdH];
+    bf16 Wc[kH * kLdW];                    // streamed weight chunk
+    float Y[kRows * kOut];
+    unsigned vox[kRows];
+    unsigned item[kRows];
+    float dr[kRows], inv[kRows];
+    unsigned hist[kNumBuckets];
+    unsigned base;
+    unsigned nseed, nimp;
+};
+
+// One warp: 16 rows x 128 columns of  A (smem, [row][k]) x W^T  with W
+// streamed from global memory in K chunks through shared memory.
+__device__ __forceinline__ void layer_mma(const bf16* A, int lda, const bf16* __restrict__ W,
+                                          int K, bf16* Wc, float (&acc)[16][4], int warp, int lane)
+{
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += kKc) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kH * kKc / 8; e += blockDim.x) {     // 16-byte copies
+            const int r = e / (kKc / 8), c8 = e % (kKc / 8);
+            *(uint4*)(Wc + r * kLdW + c8 * 8) = *(const uint4*)(W + (long long)r * K + k0 + c8 * 8);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kKc; ks += 16) {
+            uint32_t a[4];
+            load_a_frag(a, A + warp * 16 * lda + k0 + ks, lda, lane);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                uint32_t b[2];
+                load_b_frag(b, Wc + j * 8 * kLdW + ks, kLdW, lane);
+                mma_bf16_16816(acc[j], a, b);
+            }
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Problem P,
+                                                    const __grid_constant__ MlpWeights W)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LearnSmem& S = *reinterpret_cast<LearnSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
+    const unsigned total = min(P.ctr->tail_count, P.tail_cap);
+    if (threadIdx.x < kNumBuckets) S.hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) { S.nseed = 0; S.nimp = 0; }
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) S.base = atomicAdd(&P.ctr->seed_head, (unsigned)kRows);
+        __syncthreads();
+        const unsigned base = S.base;
+        if (base >= total) break;
+        // ---- rows: voxel, dose, scale ----
+        if (threadIdx.x < kRows) {
+            const unsigned it = base + threadIdx.x;
+            unsigned v = 0xffffffffu;
+            float dr = 0.f, inv = 0.f;
+            if (it < total) {
+                v = P.tail_raw[it];
+                dr = __ldg(P.ref + v);
+                inv = 1.0f / (P.dd_frac * (P.local ? dr : dnorm));
+            }
+            S.vox[threadIdx.x] = v;
+            S.item[threadIdx.x] = it;
+            S.dr[threadIdx.x] = dr;
+            S.inv[threadIdx.x] = inv;
+        }
+        __syncthreads();
+        // ---- features ----
+        for (int e = threadIdx.x; e < kRows * kInPad; e += blockDim.x) {
+            const int r = e / kInPad, f = e % kInPad;
+            const unsigned v = S.vox[r];
+            float val = 0.f;
+            if (v != 0xffffffffu) {
+                const int x = (int)(v % (unsigned)P.nx);
+                const unsigned r1 = v / (unsigned)P.nx;
+                val = voxel_feature<N>(P, x, (int)(r1 % (unsigned)P.ny), (int)(r1 / (unsigned)P.ny),
+                                       S.dr[r], S.inv[r], f);
+            }
+            S.X[r * kLdX + f] = __float2bfloat16(val);
+        }
+        // ---- layer 1: H1 = relu(X W1^T + b1) ----
+        float acc[16][4];
+        layer_mma(S.X, kLdX, W.W1, kInPad, S.Wc, acc, warp, lane);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int r = warp * 16 + g + (h >= 2 ? 8 : 0), c = j * 8 + 2 * t4 + (h & 1);
+                S.H1[r * kLdH + c] = __float2bfloat16(fmaxf(acc[j][h] + W.b1[c], 0.f));
+            }
+        // ---- layer 2: H2 = relu(H1 W2^T + b2), stored over X ----
+        layer_mma(S.H1, kLdH, W.W2, kH, S.Wc, acc, warp, lane);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int r = warp * 16 + g + (h >= 2 ? 8 : 0), c = j * 8 + 2 * t4 + (h & 1);
+                S.X[r * kLdH + c] = __float2bfloat16(fmaxf(acc[j][h] + W.b2[c], 0.f));
+            }
+        __syncthreads();
+        // ---- layer 3: Y = H2 W3^T + b3 (8 padded outputs, 4 used) ----
+        {
+            for (int e = threadIdx.x; e < kOutPad * kH; e += blockDim.x)
+                S.Wc[(e / kH) * kLdH + e % kH] = W.W3[e];
+            __syncthreads();
+            float y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < kH; ks += 16) {
+                uint32_t a[4], b[2];
+                load_a_frag(a, S.X + warp * 16 * kLdH + ks, kLdH, lane);
+                load_b_frag(b, S.Wc + ks, kLdH, lane);
+                mma_bf16_16816(y, a, b);
+            }
+            if (t4 < 2)
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int r = warp * 16 + g + (h >= 2 ? 8 : 0), c = 2 * t4 + (h & 1);
+                    S.Y[r * kOut + c] = y[h] + W.b3[c];
+                }
+        }
+        __syncthreads();
+        // ---- seed: exact faces of the cells around the proposed point ----
+        {
+            const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
+            const unsigned v = S.vox[r];
+            float sd2 = kInf;
+            int x = 0, y = 0, z = 0;
+            if (v != 0xffffffffu) {
+                x = (int)(v % (unsigned)P.nx);
+                const unsigned r1 = v / (unsigned)P.nx;
+                y = (int)(r1 % (unsigned)P.ny);
+                z = (int)(r1 / (unsigned)P.ny);
+                int o[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float ov = a < N ? S.Y[r * kOut + a] / P.hn[a] : 0.f;
+                    o[a] = (int)floorf(fminf(fmaxf(ov, -256.f), 256.f));
+                }
+                constexpr int NCELL = 1 << N;
+#pragma unroll 1
+                for (int u = half; u < NCELL; u += 2) {
+                    const int cx = o[0] + (u & 1), cy = o[1] + ((u >> 1) & 1),
+                              cz = N == 3 ? o[2] + ((u >> 2) & 1) : 0;
+                    float q[8];
+                    uint32_t ok;
+                    if (!load_cell<N>(P, x, y, z, cx, cy, cz, S.dr[r], S.inv[r], q, ok)) continue;
+                    CellGeom<float> gg;
+                    cell_geom<N, float>(cx, cy, cz, P.mt, gg);
+                    bool ill = false;
+                    const float cb = cell_min_d2<N, float>(q, ok, gg, P.mt, P.tau, kInf, ill);
+                    if (!ill) sd2 = fminf(sd2, cb);        // ill-conditioned cells are not used as seeds
+                }
+            }
+            sd2 = fminf(sd2, __shfl_xor_sync(0xffffffffu, sd2, 1));
+            if (half == 0 && v != 0xffffffffu) {
+                const float cur = P.out[v];                   // gamma^2 after the key-0 cells
+                const float nb = fminf(cur, sd2);
+                atomicAdd(&S.nseed, 1u);
+                if (nb < cur) {
+                    P.out[v] = nb;
+                    atomicAdd(&S.nimp, 1u);
+                }
+                // bucket from the (possibly) tighter bound
+                const float gk_ = sqrtf(nb);
+                int lo = P.t1, hi = P.ntable;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
+                }
+                const int cost = lo - P.t1;
+                const int bucket = cost <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)cost)));
+                P.tail_bucket[S.item[r]] = (unsigned char)bucket;
+                atomicAdd(&S.hist[bucket], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBuckets && S.hist[threadIdx.x])
+        atomicAdd(&P.ctr->hist[threadIdx.x], S.hist[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        atomicAdd(&P.ctr->seeded, S.nseed);
+        atomicAdd(&P.ctr->seed_improved, S.nimp);
+    }
+}
+
+size_t learned_smem_bytes() { return sizeof(LearnSmem); }
+
+cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s)
+{
+    const size_t smem = sizeof(LearnSmem);
+    cudaError_t e;
+    if (P.ndim == 3) {
+        e = cudaFuncSetAttribute(k_learned<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_learned<3><<<device_sm_count(), 256, smem, s>>>(P, W);
+    } else {
+        e = cudaFuncSetAttribute(k_learned<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_learned<2><<<device_sm_count(), 256, smem, s>>>(P, W);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(const Problem& P, const unsigned* vox, long long n, bf16* X,
+                            cudaStream_t s)
+{
+    const long long total = n * kInPad;
+    const int grid = (int)std::min<long long>((total + 255) / 256, (long long)device_sm_count() * 32);
+    if (P.ndim == 3) k_features<3><<<std::max(grid, 1), 256, 0, s>>>(P, vox, n, X);
+    else k_features<2><<<std::max(grid, 1), 256, 0, s>>>(P, vox, n, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels(const Problem& P, const float* gmap, const unsigned* vox, long long n,
+                          float* T, cudaStream_t s)
+{
+    const int grid = (int)std::min<long long>((n + 127) / 128, (long long)device_sm_count() * 16);
+    if (P.ndim == 3) k_labels<3><<<std::max(grid, 1), 128, 0, s>>>(P, gmap, vox, n, T);
+    else k_labels<2><<<std::max(grid, 1), 128, 0, s>>>(P, gmap, vox, n, T);
+    return cudaGetLastError();
+}
+
+}  // namespace gk
+
+// ==========================================================================
+// Model object and its C ABI
+// ==========================================================================
+
+using gk::bf16;
+
+struct gamma_model_s {
+    int device = 0;
+    float* p = nullptr;           // fp32 master parameters (layout below)
+    float* gr = nullptr;          // gradients
+    float* m1 = nullptr;          // Adam first moment
+    float* m2 = nullptr;          // Adam second moment
+    unsigned char* mask = nullptr;  // 1 for trainable entries (padding stays zero)
+    bf16 *W1h = nullptr, *W2h = nullptr, *W2Th = nullptr, *W3h = nullptr;
+    long long step = 0;
+    unsigned long long seed = 0;
+    // training workspace
+    long long wsM = 0;
+    float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dY = nullptr, *dH1 = nullptr, *loss = nullptr;
+    bf16 *H1h = nullptr, *H2h = nullptr, *dZ2h = nullptr, *dZ1h = nullptr;
+};
+
+namespace {
+
+// Parameter layout (floats): W1 [128][384], b1 [128], W2 [128][128], b2 [128],
+// W3 [8][128], b3 [8].
+constexpr long long kOffW1 = 0;
+constexpr long long kOffB1 = kOffW1 + gk::kH * gk::kInPad;
+constexpr long long kOffW2 = kOffB1 + gk::kH;
+constexpr long long kOffB2 = kOffW2 + gk::kH * gk::kH;
+constexpr long long kOffW3 = kOffB2 + gk::kH;
+constexpr long long kOffB3 = kOffW3 + gk::kOutPad * gk::kH;
+constexpr long long kNParams = kOffB3 + gk::kOutPad;
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? GAMMA_OK : (e == cudaErrorMemoryAllocation ? GAMMA_ERR_OOM : GAMMA_ERR_CUDA); }
+
+#define MCK(call)                                  \
+    do {                                           \
+        int rc_ = cuda_rc(call);                   \
+        if (rc_) return rc_;                       \
+    } while (0)
+
+void free_ws(gamma_model_s* m)
+{
+    cudaFree(m->Z1); cudaFree(m->Z2); cudaFree(m->Y); cudaFree(m->dY); cudaFree(m->dH1);
+    cudaFree(m->loss); cudaFree(m->H1h); cudaFree(m->H2h); cudaFree(m->dZ2h); cudaFree(m->dZ1h);
+    m->Z1 = m->Z2 = m->Y = m->dY = m->dH1 = m->loss = nullptr;
+    m->H1h = m->H2h = m->dZ2h = m->dZ1h = nullptr;
+    m->wsM = 0;
+}
+
+int ensure_ws(gamma_model_s* m, long long M)
+{
+    if (M <= m->wsM) return GAMMA_OK;
+    free_ws(m);
+    MCK(cudaMalloc(&m->Z1, sizeof(float) * M * gk::kH));
+    MCK(cudaMalloc(&m->Z2, sizeof(float) * M * gk::kH));
+    MCK(cudaMalloc(&m->Y, sizeof(float) * M * gk::kOutPad));
+    MCK(cudaMalloc(&m->dY, sizeof(float) * M * gk::kOut));
+    MCK(cudaMalloc(&m->dH1, sizeof(float) * M * gk::kH));
+    MCK(cudaMalloc(&m->loss, sizeof(float)));
+    MCK(cudaMalloc(&m->H1h, sizeof(bf16) * M * gk::kH));
+    MCK(cudaMalloc(&m->H2h, sizeof(bf16) * M * gk::kH));
+    MCK(cudaMalloc(&m->dZ2h, sizeof(bf16) * M * gk::kH));
+    MCK(cudaMalloc(&m->dZ1h, sizeof(bf16) * M * gk::kH));
+    m->wsM = M;
+    return GAMMA_OK;
+}
+
+int grid_for_n(long long n, int threads = 256)
+{
+    long long b = (n + threads - 1) / threads;
+    return (int)std::max<long long>(1, std::min<long long>(b, (long long)gk::device_sm_count() * 16));
+}
+
+// Host-side parameter initialisation: He-normal weights from a splitmix64 /
+// Box-Muller stream, zero biases and padding.
+void init_params(std::vector<float>& h, unsigned long long seed)
+{
+    h.assign(kNParams, 0.f);
+    unsigned long long st = seed ? seed : 0x9e3779b97f4a7c15ull;
+    auto next = [&]() {
+        st += 0x9e3779b97f4a7c15ull;
+        unsigned long long z = st;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    };
+    auto unif = [&]() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+    auto normal = [&]() { return std::sqrt(-2.0 * std::log(unif())) * std::cos(6.283185307179586 * unif()); };
+    for (int r = 0; r < gk::kH; ++r)
+        for (int c = 0; c < gk::kIn; ++c) h[kOffW1 + r * gk::kInPad + c] = (float)(normal() * std::sqrt(2.0 / gk::kIn));
+    for (int i = 0; i < gk::kH * gk::kH; ++i) h[kOffW2 + i] = (float)(normal() * std::sqrt(2.0 / gk::kH));
+    for (int r = 0; r < gk::kOut; ++r)
+        for (int c = 0; c < gk::kH; ++c) h[kOffW3 + r * gk::kH + c] = (float)(normal() * std::sqrt(1.0 / gk::kH));
+}
+
+std::vector<unsigned char> param_mask()
+{
+    std::vector<unsigned char> k(kNParams, 1);
+    for (int r = 0; r < gk::kH; ++r)
+        for (int c = gk::kIn; c < gk::kInPad; ++c) k[kOffW1 + r * gk::kInPad + c] = 0;
+    for (int r = gk::kOut; r < gk::kOutPad; ++r)
+        for (int c = 0; c < gk::kH; ++c) k[kOffW3 + r * gk::kH + c] = 0;
+    for (int r = gk::kOut; r < gk::kOutPad; ++r) k[kOffB3 + r] = 0;
+    return k;
+}
+
+int refresh_bf16(gamma_model_s* m, cudaStream_t s)
+{
+    gk::k_cast_weights<<<64, 256, 0, s>>>(m->p + kOffW1, m->p + kOffW2, m->p + kOffW3, m->W1h,
+                                          m->W2h, m->W2Th, m->W3h);
+    return cuda_rc(cudaGetLastError());
+}
+
+// Forward pass of a minibatch through the training kernels (activations kept).
+int forward_train(gamma_model_s* m, const bf16* X, long long M, cudaStream_t s)
+{
+    using namespace gk;
+    const dim3 g1((kH + 63) / 64, (unsigned)((M + 63) / 64), 1);
+    k_gemm<false, false, false><<<g1, 128, 0, s>>>((int)M, kH, kInPad, X, kInPad, m->W1h, kInPad, m->Z1, kH);
+    k_bias_act<<<grid_for_n(M * kH), 256, 0, s>>>(M, kH, m->Z1, m->p + kOffB1, m->H1h, kH, 1);
+    k_gemm<false, false, false><<<g1, 128, 0, s>>>((int)M, kH, kH, m->H1h, kH, m->W2h, kH, m->Z2, kH);
+    k_bias_act<<<grid_for_n(M * kH), 256, 0, s>>>(M, kH, m->Z2, m->p + kOffB2, m->H2h, kH, 1);
+    const dim3 g3(1, (unsigned)((M + 63) / 64), 1);
+    k_gemm<false, false, false><<<g3, 128, 0, s>>>((int)M, kOutPad, kH, m->H2h, kH, m->W3h, kH, m->Y, kOutPad);
+    k_bias_act<<<grid_for_n(M * kOutPad), 256, 0, s>>>(M, kOutPad, m->Y, m->p + kOffB3, nullptr, 0, 0);
+    return cuda_rc(cudaGetLastError());
+}
+
+// Loss and gradients of a minibatch into m->gr (zeroed first).
+int backward_train(gamma_model_s* m, const bf16* X, const float* T, long long M, long long count,
+                   cudaStream_t s)
+{
+    using namespace gk;
+    MCK(cudaMemsetAsync(m->gr, 0, sizeof(float) * kNParams, s));
+    MCK(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
+    const float invc = count > 0 ? 1.f / (float)count : 0.f;
+    k_huber<<<grid_for_n(M), 256, 0, s>>>(M, m->Y, T, m->dY, m->loss, invc);
+    k_out_back<<<grid_for_n(M * kH, 256), 256, 0, s>>>(M, m->dY, m->p + kOffW3, m->Z2, m->H2h,
+                                                         m->dZ2h, m->gr + kOffW3, m->gr + kOffB3);
+    // dW2 = dZ2^T H1 (split over the batch), db2 = colsum dZ2
+    const int splits = (int)std::max<long long>(1, std::min<long long>(64, M / 256));
+    const dim3 gw2((kH + 63) / 64, (kH + 63) / 64, splits);
+    k_gemm<true, true, true><<<gw2, 128, 0, s>>>(kH, kH, (int)M, m->dZ2h, kH, m->H1h, kH, m->gr + kOffW2, kH);
+    k_colsum<<<dim3(256, (kH + 127) / 128), 128, 0, s>>>(M, kH, m->dZ2h, m->gr + kOffB2);
+    // dH1 = dZ2 W2, dZ1 = dH1 [Z1 > 0]
+    const dim3 gh((kH + 63) / 64, (unsigned)((M + 63) / 64), 1);
+    k_gemm<false, false, false><<<gh, 128, 0, s>>>((int)M, kH, kH, m->dZ2h, kH, m->W2Th, kH, m->dH1, kH);
+    k_relu_back<<<grid_for_n(M * kH), 256, 0, s>>>(M, kH, m->dH1, m->Z1, m->dZ1h, nullptr);
+    k_colsum<<<dim3(256, (kH + 127) / 128), 128, 0, s>>>(M, kH, m->dZ1h, m->gr + kOffB1);
+    // dW1 = dZ1^T X
+    const dim3 gw1((kInPad + 63) / 64, (kH + 63) / 64, splits);
+    k_gemm<true, true, true><<<gw1, 128, 0, s>>>(kH, kInPad, (int)M, m->dZ1h, kH, X, kInPad, m->gr + kOffW1, kInPad);
+    return cuda_rc(cudaGetLastError());
+}
+
+}  // namespace
+
+namespace gk {
+
+bool model_weights(const gamma_model_s* m, MlpWeights* w)
+{
+    if (!m) return false;
+    w->W1 = m->W1h;
+    w->W2 = m->W2h;
+    w->W3 = m->W3h;
+    w->b1 = m->p + kOffB1;
+    w->b2 = m->p + kOffB2;
+    w->b3 = m->p + kOffB3;
+    return true;
+}
+
+}  // namespace gk
+
+extern "C" {
+
+int gamma_model_create(gamma_model* out, uint64_t seed)
+{
+    if (!out) return GAMMA_ERR_INVALID_ARG;
+    *out = nullptr;
+    gamma_model_s* m = new (std::nothrow) gamma_model_s();
+    if (!m) return GAMMA_ERR_OOM;
+    auto fail = [&](int rc) { gamma_model_destroy(m); return rc; };
+    if (cudaGetDevice(&m->device) != cudaSuccess) return fail(GAMMA_ERR_CUDA);
+    int rc;
+    if ((rc = cuda_rc(cudaMalloc(&m->p, sizeof(float) * kNParams)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->gr, sizeof(float) * kNParams)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->m1, sizeof(float) * kNParams)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->m2, sizeof(float) * kNParams)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->mask, kNParams)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->W1h, sizeof(bf16) * gk::kH * gk::kInPad)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->W2h, sizeof(bf16) * gk::kH * gk::kH)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->W2Th, sizeof(bf16) * gk::kH * gk::kH)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->W3h, sizeof(bf16) * gk::kOutPad * gk::kH)))) return fail(rc);
+    std::vector<float> h;
+    init_params(h, seed);
+    m->seed = seed;
+    const std::vector<unsigned char> k = param_mask();
+    if ((rc = cuda_rc(cudaMemcpy(m->p, h.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMemcpy(m->mask, k.data(), kNParams, cudaMemcpyHostToDevice)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMemset(m->m1, 0, sizeof(float) * kNParams)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMemset(m->m2, 0, sizeof(float) * kNParams)))) return fail(rc);
+    if ((rc = refresh_bf16(m, 0))) return fail(rc);
+    if ((rc = cuda_rc(cudaDeviceSynchronize()))) return fail(rc);
+    *out = m;
+    return GAMMA_OK;
+}
+
+void gamma_model_destroy(gamma_model m)
+{
+    if (!m) return;
+    cudaFree(m->p); cudaFree(m->gr); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->mask);
+    cudaFree(m->W1h); cudaFree(m->W2h); cudaFree(m->W2Th); cudaFree(m->W3h);
+    free_ws(m);
+    delete m;
+}
+
+int64_t gamma_model_num_params(void) { return kNParams; }
+
+int gamma_model_get_params(gamma_model m, float* host, int64_t n, int which)
+{
+    if (!m || !host || n != kNParams || which < 0 || which > 3) return GAMMA_ERR_INVALID_ARG;
+    const float* src = which == 0 ? m->p : which == 1 ? m->gr : which == 2 ? m->m1 : m->m2;
+    MCK(cudaDeviceSynchronize());
+    MCK(cudaMemcpy(host, src, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
+    return GAMMA_OK;
+}
+
+int gamma_model_set_params(gamma_model m, const float* host, int64_t n)
+{
+    if (!m || !host || n != kNParams) return GAMMA_ERR_INVALID_ARG;
+    MCK(cudaMemcpy(m->p, host, sizeof(float) * kNParams, cudaMemcpyHostToDevice));
+    if (int rc = refresh_bf16(m, 0)) return rc;
+    MCK(cudaDeviceSynchronize());
+    return GAMMA_OK;
+}
+
+int gamma_model_forward(gamma_model m, const void* X_bf16_dev, int64_t M, float* Y_dev,
+                        void* cuda_stream)
+{
+    if (!m || !X_bf16_dev || !Y_dev || M <= 0) return GAMMA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (int rc = ensure_ws(m, M)) return rc;
+    if (int rc = forward_train(m, (const bf16*)X_bf16_dev, M, s)) return rc;
+    MCK(cudaMemcpy2DAsync(Y_dev, sizeof(float) * gk::kOut, m->Y, sizeof(float) * gk::kOutPad,
+                          sizeof(float) * gk::kOut, (size_t)M, cudaMemcpyDeviceToDevice, s));
+    return GAMMA_OK;
+}
+
+int gamma_model_backward(gamma_model m, const void* X_bf16_dev, const float* T_dev, int64_t M,
+                         float* loss_out, void* cuda_stream)
+{
+    if (!m || !X_bf16_dev || !T_dev || M <= 0) return GAMMA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (int rc = ensure_ws(m, M)) return rc;
+    if (int rc = forward_train(m, (const bf16*)X_bf16_dev, M, s)) return rc;
+    if (int rc = backward_train(m, (const bf16*)X_bf16_dev, T_dev, M, M, s)) return rc;
+    if (loss_out) {
+        MCK(cudaMemcpyAsync(loss_out, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        MCK(cudaStreamSynchronize(s));
+    }
+    return GAMMA_OK;
+}
+
+int gamma_model_train_step(gamma_model m, const void* X_bf16_dev, const float* T_dev, int64_t M,
+                           float lr, float* loss_out, void* cuda_stream)
+{
+    if (!m || !(lr >= 0.f)) return GAMMA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (int rc = gamma_model_backward(m, X_bf16_dev, T_dev, M, nullptr, cuda_stream)) return rc;
+    m->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)m->step), c2 = 1.f - std::pow(b2, (float)m->step);
+    gk::k_adam<<<grid_for_n(kNParams), 256, 0, s>>>(kNParams, m->p, m->gr, m->m1, m->m2, m->mask, lr,
+                                                   b1, b2, 1e-8f, c1, c2);
+    MCK(cudaGetLastError());
+    if (int rc = refresh_bf16(m, s)) return rc;
+    if (loss_out) {
+        MCK(cudaMemcpyAsync(loss_out, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        MCK(cudaStreamSynchronize(s));
+    }
+    return GAMMA_OK;
+}
+
+// File format: 8-byte magic "GAMMAMLP", int32 version 1, int32 kIn, kInPad,
+// kH, kOut, kOutPad, int64 Adam step, uint64 seed, then kNParams floats each of
+// parameters, Adam first and second moments (little-endian).
+int gamma_model_save(gamma_model m, const char* path)
+{
+    if (!m || !path) return GAMMA_ERR_INVALID_ARG;
+    std::vector<float> p(kNParams), a(kNParams), b(kNParams);
+    if (int rc = gamma_model_get_params(m, p.data(), kNParams, 0)) return rc;
+    if (int rc = gamma_model_get_params(m, a.data(), kNParams, 2)) return rc;
+    if (int rc = gamma_model_get_params(m, b.data(), kNParams, 3)) return rc;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return GAMMA_ERR_INVALID_ARG;
+    const int32_t hdr[7] = {1, gk::kIn, gk::kInPad, gk::kH, gk::kOut, gk::kOutPad, 0};
+    const int64_t step = m->step;
+    const uint64_t seed = m->seed;
+    bool ok = std::fwrite("GAMMAMLP", 1, 8, f) == 8 && std::fwrite(hdr, 4, 6, f) == 6 &&
+              std::fwrite(&step, 8, 1, f) == 1 && std::fwrite(&seed, 8, 1, f) == 1 &&
+              std::fwrite(p.data(), 4, kNParams, f) == (size_t)kNParams &&
+              std::fwrite(a.data(), 4, kNParams, f) == (size_t)kNParams &&
+              std::fwrite(b.data(), 4, kNParams, f) == (size_t)kNParams;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? GAMMA_OK : GAMMA_ERR_INVALID_ARG;
+}
+
+int gamma_model_load(gamma_model m, const char* path)
+{
+    if (!m || !path) return GAMMA_ERR_INVALID_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return GAMMA_ERR_MODEL;
+    char magic[8];
+    int32_t hdr[6];
+    int64_t step = 0;
+    uint64_t seed = 0;
+    std::vector<float> p(kNParams), a(kNParams), b(kNParams);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "GAMMAMLP", 8) == 0 &&
+              std::fread(hdr, 4, 6, f) == 6 && hdr[0] == 1 && hdr[1] == gk::kIn &&
+              hdr[2] == gk::kInPad && hdr[3] == gk::kH && hdr[4] == gk::kOut &&
+              hdr[5] == gk::kOutPad && std::fread(&step, 8, 1, f) == 1 &&
+              std::fread(&seed, 8, 1, f) == 1 &&
+              std::fread(p.data(), 4, kNParams, f) == (size_t)kNParams &&
+              std::fread(a.data(), 4, kNParams, f) == (size_t)kNParams &&
+              std::fread(b.data(), 4, kNParams, f) == (size_t)kNParams;
+    std::fclose(f);
+    if (!ok) return GAMMA_ERR_MODEL;
+    for (float x : p)
+        if (!std::isfinite(x)) return GAMMA_ERR_MODEL;
+    MCK(cudaMemcpy(m->p, p.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice));
+    MCK(cudaMemcpy(m->m1, a.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice));
+    MCK(cudaMemcpy(m->m2, b.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice));
+    m->step = step;
+    m->seed = seed;
+    if (int rc = refresh_bf16(m, 0)) return rc;
+    MCK(cudaDeviceSynchronize());
+    return GAMMA_OK;
+}
+
+}  // extern "C"

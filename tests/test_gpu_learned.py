@@ -1,0 +1,188 @@
+"""GPU checks of the learned proposal: the network's forward and backward
+against the FP64 reference with the same bf16 rounding points, features
+against their FP64 definition, labels as true nearest surface points,
+training that lowers the loss, and runs with a model attached that stay
+exactly equal to runs without it."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp
+from tests import _brute as brute
+from tests.test_gpu_parity import assert_parity, f32, gpu_gamma, oracle_gamma
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_forward_and_backward_match_reference():
+    import paper_1012_1900_gb300 as g
+    rng = np.random.default_rng(3)
+    m = g.gamma_model_create(7)
+    try:
+        M = 300                                     # ragged against the 64-row tiles
+        X = np.zeros((M, mlp.K_PAD), np.float32)
+        X[:, :mlp.K_IN] = rng.normal(0, 1.5, (M, mlp.K_IN))
+        Xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
+        Xq = Xb.float().cpu().numpy().astype(np.float64)
+        T = rng.normal(0, 1, (M, 4)).astype(np.float32)
+        T[::17, 3] = np.nan
+        Tt = torch.from_numpy(T).cuda()
+        p = g.gamma_model_get_params(m).astype(np.float64)
+        Y = torch.empty((M, 4), device="cuda")
+        g.gamma_model_forward(m, Xb, Y)
+        ref = mlp.forward(p, Xq)
+        assert _rel(Y.cpu().numpy(), ref["y"]) < 2e-3
+        loss = g.gamma_model_backward(m, Xb, Tt)
+        want_loss, want_g = mlp.loss_and_grads(p, Xq, T)
+        assert loss == pytest.approx(want_loss, rel=2e-3)
+        got_g = g.gamma_model_get_params(m, which=1).astype(np.float64)
+        for a, b in [(mlp.OFF_W1, mlp.OFF_B1), (mlp.OFF_B1, mlp.OFF_W2), (mlp.OFF_W2, mlp.OFF_B2),
+                     (mlp.OFF_B2, mlp.OFF_W3), (mlp.OFF_W3, mlp.OFF_B3), (mlp.OFF_B3, mlp.N_PARAMS)]:
+            assert _rel(got_g[a:b], want_g[a:b]) < 1e-2, (a, b)
+        assert np.all(got_g[~mlp.trainable_mask()] == 0)
+    finally:
+        g.gamma_model_destroy(m)
+
+
+def test_adam_step_and_save_load(tmp_path):
+    import paper_1012_1900_gb300 as g
+    rng = np.random.default_rng(4)
+    m = g.gamma_model_create(11)
+    m2 = g.gamma_model_create(12)
+    try:
+        X = torch.from_numpy(rng.normal(0, 1, (128, mlp.K_PAD)).astype(np.float32)).to(torch.bfloat16).cuda()
+        T = torch.from_numpy(rng.normal(0, 1, (128, 4)).astype(np.float32)).cuda()
+        p0 = g.gamma_model_get_params(m).astype(np.float64)
+        g.gamma_model_backward(m, X, T)
+        gr = g.gamma_model_get_params(m, which=1).astype(np.float64)
+        g.gamma_model_train_step(m, X, T, 1e-3)
+        p1 = g.gamma_model_get_params(m).astype(np.float64)
+        # first Adam step: update = lr * g / (|g| + eps) elementwise (eps = 1e-8)
+        k = mlp.trainable_mask() & (np.abs(gr) > 1e-7)
+        want = 1e-3 * gr[k] / (np.abs(gr[k]) + 1e-8)
+        np.testing.assert_allclose((p0 - p1)[k], want, rtol=2e-3, atol=1e-7)
+        assert np.all(p1[~mlp.trainable_mask()] == 0)
+        path = os.path.join(tmp_path, "m.gmlp")
+        g.gamma_model_save(m, path)
+        g.gamma_model_load(m2, path)
+        assert np.array_equal(g.gamma_model_get_params(m2), g.gamma_model_get_params(m))
+    finally:
+        g.gamma_model_destroy(m)
+        g.gamma_model_destroy(m2)
+
+
+def _handle(g, p):
+    r = torch.from_numpy(p.ref).cuda()
+    e = torch.from_numpy(p.eval).cuda()
+    c = p.criteria
+    h = g.gamma_create(r, e, 3, p.ref.shape, p.spacing,
+                       g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm))
+    return h, r, e
+
+
+def test_features_match_definition():
+    import paper_1012_1900_gb300 as g
+    p = synth.workload("imrt_small")
+    h, r, e = _handle(g, p)
+    try:
+        out = torch.empty_like(r)
+        g.gamma_run(h, out)
+        g.gamma_pass_rate(h)
+        rng = np.random.default_rng(0)
+        ok = np.nonzero(np.isfinite(out.cpu().numpy().ravel()))[0]
+        vox = rng.choice(ok, 40, replace=False).astype(np.int32)
+        X = torch.empty((vox.size, 384), dtype=torch.bfloat16, device="cuda")
+        g.gamma_features(h, torch.from_numpy(vox).cuda(), X)
+        got = X.float().cpu().numpy().astype(np.float64)
+    finally:
+        g.gamma_destroy(h)
+    c = p.criteria
+    want = mlp.bf16_round(mlp.features(p.ref.astype(np.float64), p.eval.astype(np.float64), p.spacing,
+                                       f32(c.dd_frac), f32(c.dta_mm), vox))
+    assert np.all(np.abs(got - want) <= 2 ** -7 * np.abs(want) + 1e-6)
+
+
+def test_labels_are_nearest_surface_points():
+    import paper_1012_1900_gb300 as g
+    p = synth.workload("imrt_small")
+    crit = synth.Criteria(0.01, 1.0, local=True)
+    p = synth.Pair(p.name, p.ref, p.eval, p.spacing, crit)
+    h, r, e = _handle(g, p)
+    try:
+        out = torch.empty_like(r)
+        g.gamma_run(h, out)
+        g.gamma_pass_rate(h)
+        gm = out.cpu().numpy().ravel().astype(np.float64)
+        ok = np.nonzero(np.isfinite(gm) & (gm > 0.9))[0]
+        rng = np.random.default_rng(1)
+        vox = rng.choice(ok, min(60, ok.size), replace=False).astype(np.int32)
+        T = torch.empty((vox.size, 4), device="cuda")
+        g.gamma_labels(h, out, torch.from_numpy(vox).cuda(), T)
+        T = T.cpu().numpy().astype(np.float64)
+    finally:
+        g.gamma_destroy(h)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit, idx=vox)
+    hn = np.array(p.spacing[::-1]) / crit.dta_mm                  # x, y, z
+    shape = p.ref.shape
+    for row, v in enumerate(vox):
+        z, y, x = np.unravel_index(v, shape)
+        off = T[row, :3] / hn                                        # voxel units (x, y, z)
+        pos = np.array([x, y, z]) + off
+        de = brute.freudenthal_interpolate(p.eval, pos[None, :])[0]
+        dr = float(p.ref.ravel()[v])
+        dD = f32(crit.dd_frac) * dr
+        dist = math.sqrt(float((T[row, :3] ** 2).sum()) + ((de - dr) / dD) ** 2)
+        assert dist == pytest.approx(want[row], abs=2e-4), row
+        assert T[row, 3] == pytest.approx(math.log(want[row] + 1e-3), abs=1e-4)
+
+
+def test_training_lowers_the_loss():
+    import paper_1012_1900_gb300 as g
+    from paper_1012_1900_gb300 import train
+    pairs = [synth.make_pair_3d(shape=(30, 40, 40), spacing=(2.0, 2.0, 2.0), seed=1000 + i,
+                                shift_mm=(0.0, 1.0 + i, 2.0), scale=1.0 + 0.02 * i,
+                                criteria=synth.Criteria(0.02, 2.0)) for i in range(3)]
+    X, T = train.build_dataset(pairs, 3000, seed=0)
+    assert X.shape[0] > 1000
+    m = g.gamma_model_create(5)
+    try:
+        losses = train.train(m, X, T, steps=300, batch=1024, lr=3e-3)
+    finally:
+        g.gamma_model_destroy(m)
+    first = float(np.mean(losses[:10]))
+    last = float(np.mean(losses[-10:]))
+    assert last < 0.5 * first, (first, last)
+
+
+@pytest.mark.parametrize("crit", [synth.Criteria(0.02, 2.0), synth.Criteria(0.01, 1.0, local=True)],
+                         ids=["2pct2mm", "1pct1mm_local"])
+def test_runs_with_a_model_stay_exact(crit):
+    import paper_1012_1900_gb300 as g
+    p = synth.make_pair_3d(shape=(24, 36, 32), spacing=(2.0, 2.0, 2.0), seed=2001,
+                           shift_mm=(0.5, 1.5, 2.5), scale=1.04, criteria=crit)
+    plain, pc, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit)
+    m = g.gamma_model_create(9)                 # untrained: any proposal must be safe
+    h, r, e = _handle(g, p)
+    try:
+        g.gamma_set_model(h, m)
+        out = torch.empty_like(r)
+        g.gamma_run(h, out)
+        counts = g.gamma_pass_rate(h)
+        st = g.gamma_get_stats(h)
+        got = out.cpu().numpy().astype(np.float64)
+    finally:
+        g.gamma_destroy(h)
+        g.gamma_model_destroy(m)
+    assert st["seeded"] == st["tail_voxels"] > 0
+    np.testing.assert_allclose(got, plain, rtol=0, atol=1e-6, equal_nan=True)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
