@@ -42,7 +42,7 @@ WORKLOAD_DESC = ("synthetic IMRT pair 160x160x120 at 2.5 mm (7 coplanar beams, 1
                  "3%/3mm global, 10% cutoff")
 # Algorithmic FP32 work per cell of the face formulation (FMA = 2 FLOP); the
 # count is derived in the design doc from cell_min_d2 (26 faces in 3D, 6 in 2D).
-FLOP_PER_CELL = {3: 651, 2: 115}
+FLOP_PER_CELL = {3: 615, 2: 103}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 KERNELS_PER_RUN = 5          # prepare, shell, bucket scan, scatter, tail
@@ -60,6 +60,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
+    ap.add_argument("--experiment", choices=["learned", "batch"], default=None,
+                    help="learned: train + evaluate the proposal network (200x200x150 pairs, "
+                         "2%%/2mm); batch: 64 uneven pairs batched vs one by one")
+    ap.add_argument("--train-pairs", type=int, default=200)
+    ap.add_argument("--test-pairs", type=int, default=20)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--model-out", default="")
+    ap.add_argument("--model-in", default="")
     return ap.parse_args()
 
 
@@ -222,6 +230,31 @@ def run_reference(args, pair, rank, world):
 # our arm
 # --------------------------------------------------------------------------
 
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_pairs(costs, world: int, rank: int):
+    """Indices of the pairs rank `rank` runs: greedy longest-processing-time
+    assignment of the pairs' estimated costs (voxel counts) to `world` ranks.
+    Pairs are independent problems, so ranks exchange no data."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    loads = [0.0] * world
+    owner = [0] * len(costs)
+    for i in order:
+        r = min(range(world), key=lambda k: (loads[k], k))
+        owner[i] = r
+        loads[r] += costs[i]
+    return [i for i in range(len(costs)) if owner[i] == rank]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -284,11 +317,7 @@ def run_ours(args, pair, rank, world, local_rank):
         barrier()
         clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
     value = world * pair.nvox * args.steps / (total_ms / 1000.0)
 
@@ -309,11 +338,7 @@ def run_ours(args, pair, rank, world, local_rank):
             for _ in range(args.steps):
                 g.gamma_run_host(hh, rh, eh, oh, stream)
                 g.gamma_pass_rate(hh)                      # device->host read of the result
-            e2e_s = time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                e2e_s = float(t.item())
+            e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
             nbytes = pair.nvox * 4
             e2e = {"value": world * pair.nvox * args.steps / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes + 24}
@@ -377,8 +402,224 @@ def run_ours(args, pair, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# experiments (not the headline line)
+# --------------------------------------------------------------------------
+
+def _gen(job):
+    kind, i, shape = job
+    if kind == "train":
+        return synth.training_pair(i, shape=shape)
+    if kind == "test":
+        return synth.test_pair(i, shape=shape)
+    return synth.batch_pair(i)
+
+
+def _pool(workers=8):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(workers)
+
+
+def _chunks(pool, jobs, size=16):
+    """Generate pairs chunk by chunk (bounded host memory)."""
+    for i in range(0, len(jobs), size):
+        yield pool.map(_gen, jobs[i:i + size])
+
+
+def _timed_runs(g, h, out, reps=5):
+    import torch
+    ts = []
+    for _ in range(reps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        g.gamma_run(h, out)
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    return statistics.median(ts)
+
+
+def experiment_learned(args):
+    """Train the proposal network on the learned-config recipe and compare
+    seeded against plain runs on held-out pairs (exactness, cells, time)."""
+    shape = (150, 200, 200)
+    pool = _pool()
+    import torch
+    import paper_1012_1900_gb300 as g
+    from paper_1012_1900_gb300 import train
+    t0 = time.perf_counter()
+    m = g.gamma_model_create(1234)
+    if args.model_in:
+        g.gamma_model_load(m, args.model_in)
+        losses = []
+    else:
+        xs, ts_ = [], []
+        for k, chunk in enumerate(_chunks(pool, [("train", i, shape) for i in range(args.train_pairs)])):
+            X, T = train.build_dataset(chunk, 4096, seed=k)
+            xs.append(X)
+            ts_.append(T)
+        X, T = torch.cat(xs), torch.cat(ts_)
+        del xs, ts_
+        losses = train.train(m, X, T, steps=args.train_steps, batch=8192, lr=2e-3)
+        if args.model_out:
+            g.gamma_model_save(m, args.model_out)
+    t_train = time.perf_counter() - t0
+    rows = []
+    test_iter = (p for chunk in _chunks(pool, [("test", i, shape) for i in range(args.test_pairs)])
+                 for p in chunk)
+    for p in test_iter:
+        ref = torch.from_numpy(p.ref).cuda()
+        ev = torch.from_numpy(p.eval).cuda()
+        c = p.criteria
+        crit = g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)
+        res = {}
+        for mode in ("plain", "learned"):
+            h = g.gamma_create(ref, ev, 3, p.ref.shape, p.spacing, crit)
+            try:
+                if mode == "learned":
+                    g.gamma_set_model(h, m)
+                out = torch.empty_like(ref)
+                g.gamma_run(h, out)
+                g.gamma_pass_rate(h)
+                ms = _timed_runs(g, h, out)
+                g.gamma_set_option(h, "stats", 1)
+                g.gamma_run(h, out)
+                g.gamma_pass_rate(h)
+                st = g.gamma_get_stats(h)
+                res[mode] = (out.cpu().numpy(), ms, st)
+            finally:
+                g.gamma_destroy(h)
+        a, b = res["plain"][0], res["learned"][0]
+        ok = np.isfinite(a)
+        sp, sl = res["plain"][2], res["learned"][2]
+        tv = max(1, sp["tail_voxels"])
+        rows.append({
+            "pair": p.name, "voxels": p.nvox, "evaluated": int(ok.sum()),
+            "tail_voxels": sp["tail_voxels"],
+            "max_abs_diff": float(np.max(np.abs(a[ok] - b[ok]))) if ok.any() else 0.0,
+            "identical": bool(np.array_equal(a, b, equal_nan=True)),
+            "ms_plain": res["plain"][1], "ms_learned": res["learned"][1],
+            "cells_keyed_per_tail_voxel": [sp["cells_keyed"] / tv, sl["cells_keyed"] / tv],
+            "cells_visited_per_tail_voxel": [sp["cells_visited"] / tv, sl["cells_visited"] / tv],
+            "cells_pruned_per_tail_voxel": [sp["cells_pruned"] / tv, sl["cells_pruned"] / tv],
+            "seed_improved_frac": sl["seed_improved"] / max(1, sl["seeded"]),
+        })
+    g.gamma_model_destroy(m)
+    pool.close()
+    tot_p = sum(r["ms_plain"] for r in rows)
+    tot_l = sum(r["ms_learned"] for r in rows)
+    vox = sum(r["voxels"] for r in rows)
+    summary = {
+        "experiment": "learned", "criteria": "2%/2mm global, 10% cutoff",
+        "train_pairs": args.train_pairs, "test_pairs": len(rows),
+        "train_steps": args.train_steps, "final_loss": float(np.mean(losses[-50:])) if losses else None,
+        "first_loss": float(np.mean(losses[:10])) if losses else None,
+        "train_seconds": t_train,
+        "plain_voxels_per_s": vox / (tot_p / 1000.0), "learned_voxels_per_s": vox / (tot_l / 1000.0),
+        "speedup": tot_p / tot_l,
+        "all_identical": all(r["identical"] for r in rows),
+        "max_abs_diff": max(r["max_abs_diff"] for r in rows),
+        "cells_keyed_per_tail_voxel": [float(np.mean([r["cells_keyed_per_tail_voxel"][k] for r in rows])) for k in (0, 1)],
+        "cells_visited_per_tail_voxel": [float(np.mean([r["cells_visited_per_tail_voxel"][k] for r in rows])) for k in (0, 1)],
+        "cells_pruned_per_tail_voxel": [float(np.mean([r["cells_pruned_per_tail_voxel"][k] for r in rows])) for k in (0, 1)],
+        "seed_improved_frac": float(np.mean([r["seed_improved_frac"] for r in rows])),
+        "fallback_frac": 1.0 - float(np.mean([r["seed_improved_frac"] for r in rows])),
+        "pairs": rows,
+    }
+    print(json.dumps(summary), flush=True)
+
+
+def experiment_batch(args):
+    """64 uneven pairs: one batched graph launch against one run per pair, and
+    the per-pair error against the oracle on sampled voxels."""
+    pool = _pool()
+    pairs = [p for chunk in _chunks(pool, [("batch", i, None) for i in range(64)]) for p in chunk]
+    pool.close()
+    import torch
+    import oracle
+    import paper_1012_1900_gb300 as g
+    oracle.build()
+    descs, outs, keep = [], [], []
+    for p in pairs:
+        nd = p.ref.ndim
+        r = torch.from_numpy(p.ref).cuda()
+        e = torch.from_numpy(p.eval).cuda()
+        o = torch.empty_like(r)
+        keep += [r, e, o]
+        outs.append(o)
+        c = p.criteria
+        descs.append((r, e, o, nd, p.ref.shape if nd == 3 else (1,) + p.ref.shape,
+                      p.spacing if nd == 3 else (1.0,) + p.spacing,
+                      g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)))
+    vox = sum(p.nvox for p in pairs)
+    # batched
+    hb = g.gamma_batch_create(descs)
+    lanes, blocks, tune_ms = g.gamma_autotune(hb, reps=2)
+    for _ in range(3):
+        g.gamma_batch_run(hb)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        g.gamma_batch_run(hb)
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    batched_ms = statistics.median(ts)
+    maps = [o.cpu().numpy() for o in outs]
+    g.gamma_destroy(hb)
+    # one handle per pair, run one after another
+    hs = [g.gamma_create(d[0], d[1], d[3], d[4], d[5], d[6]) for d in descs]
+    for _ in range(3):
+        for h, d in zip(hs, descs):
+            g.gamma_run(h, d[2])
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        for h, d in zip(hs, descs):
+            g.gamma_run(h, d[2])
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    seq_ms = statistics.median(ts)
+    for h in hs:
+        g.gamma_destroy(h)
+    # per-pair error against the oracle on sampled voxels
+    rng = np.random.default_rng(0)
+    errs = []
+    f32 = lambda x: float(np.float32(x))
+    for p, gm in zip(pairs, maps):
+        ok = np.nonzero(np.isfinite(gm.ravel()))[0]
+        idx = rng.choice(ok, min(2000, ok.size), replace=False) if ok.size else ok
+        c = p.criteria
+        want = oracle.gamma(p.ref, p.eval, p.spacing, f32(c.dd_frac), f32(c.dta_mm),
+                            cutoff_frac=f32(c.cutoff_frac), idx=idx)
+        errs.append(float(np.max(np.abs(gm.ravel()[idx] - want))) if idx.size else 0.0)
+    print(json.dumps({
+        "experiment": "batch", "pairs": len(pairs), "voxels": vox,
+        "batched_ms": batched_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batched_ms,
+        "batched_voxels_per_s": vox / (batched_ms / 1000.0),
+        "sequential_voxels_per_s": vox / (seq_ms / 1000.0),
+        "autotune": {"lanes_per_voxel": lanes, "shell_blocks_per_sm": blocks, "ms": tune_ms},
+        "max_abs_err_vs_oracle": max(errs), "per_pair_max_abs_err": errs,
+        "names": [p.name for p in pairs],
+    }), flush=True)
+
+
 def main():
     args = parse()
+    if args.experiment == "learned":
+        experiment_learned(args)
+        return
+    if args.experiment == "batch":
+        experiment_batch(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

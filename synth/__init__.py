@@ -27,7 +27,7 @@ from scipy import ndimage, special
 
 __all__ = [
     "Criteria", "Pair", "blob_phantom_2d", "beam_phantom_3d", "make_pair_2d",
-    "make_pair_3d", "workload", "batch_pairs", "training_pair", "test_pair",
+    "make_pair_3d", "workload", "batch_pair", "batch_pairs", "training_pair", "test_pair",
     "random_field",
 ]
 
@@ -255,35 +255,35 @@ def workload(name: str, criteria: Criteria | None = None) -> Pair:
 _CRIT_SET = (Criteria(0.01, 1.0), Criteria(0.02, 2.0), Criteria(0.03, 3.0))
 
 
-def batch_pairs(n2d: int = 32, n3d: int = 32, base_seed: int = 3000,
-                max_shape=(150, 200, 200), min_shape=(64, 64, 64)) -> List[Pair]:
-    """Uneven batch: n2d planes 256x256 at 1 mm plus n3d volumes at 2 mm with
-    shapes log-uniform between min_shape and max_shape; per pair a shift
-    U[0, 3] mm in a random direction, scale U[0.97, 1.05] and criteria drawn
-    from {1%/1 mm, 2%/2 mm, 3%/3 mm} (global, 10 % cutoff)."""
-    pairs: List[Pair] = []
-    for i in range(n2d + n3d):
-        seed = base_seed + i
-        rng = np.random.default_rng(seed + 55555)
-        crit = _CRIT_SET[int(rng.integers(0, 3))]
-        mag = rng.uniform(0.0, 3.0)
-        scale = float(rng.uniform(0.97, 1.05))
-        if i < n2d:
-            ang = rng.uniform(0, 2 * math.pi)
-            shift = (mag * math.sin(ang), mag * math.cos(ang))
-            pairs.append(make_pair_2d(shape=(256, 256), spacing=(1.0, 1.0), seed=seed,
-                                      shift_mm=shift, scale=scale, criteria=crit,
-                                      name=f"batch{i:02d}_2d"))
-        else:
-            v = rng.normal(size=3)
-            v /= np.linalg.norm(v)
-            t = rng.uniform(0.0, 1.0)
-            shp = tuple(int(round(math.exp(math.log(a) + t * (math.log(b) - math.log(a)))))
-                        for a, b in zip(min_shape, max_shape))
-            pairs.append(make_pair_3d(shape=shp, spacing=(2.0, 2.0, 2.0), seed=seed,
-                                      shift_mm=tuple(mag * v), scale=scale, criteria=crit,
-                                      name=f"batch{i:02d}_3d"))
-    return pairs
+def batch_pair(i: int, n2d: int = 32, base_seed: int = 3000,
+               max_shape=(150, 200, 200), min_shape=(64, 64, 64)) -> Pair:
+    """Pair i of the uneven batch: pairs 0..n2d-1 are planes 256x256 at 1 mm,
+    the others volumes at 2 mm with shapes log-uniform between min_shape and
+    max_shape; per pair a shift U[0, 3] mm in a random direction, scale
+    U[0.97, 1.05] and criteria drawn from {1%/1 mm, 2%/2 mm, 3%/3 mm}
+    (global, 10 % cutoff)."""
+    seed = base_seed + i
+    rng = np.random.default_rng(seed + 55555)
+    crit = _CRIT_SET[int(rng.integers(0, 3))]
+    mag = rng.uniform(0.0, 3.0)
+    scale = float(rng.uniform(0.97, 1.05))
+    if i < n2d:
+        ang = rng.uniform(0, 2 * math.pi)
+        shift = (mag * math.sin(ang), mag * math.cos(ang))
+        return make_pair_2d(shape=(256, 256), spacing=(1.0, 1.0), seed=seed, shift_mm=shift,
+                            scale=scale, criteria=crit, name=f"batch{i:02d}_2d")
+    v = rng.normal(size=3)
+    v /= np.linalg.norm(v)
+    t = rng.uniform(0.0, 1.0)
+    shp = tuple(int(round(math.exp(math.log(a) + t * (math.log(b) - math.log(a)))))
+                for a, b in zip(min_shape, max_shape))
+    return make_pair_3d(shape=shp, spacing=(2.0, 2.0, 2.0), seed=seed, shift_mm=tuple(mag * v),
+                        scale=scale, criteria=crit, name=f"batch{i:02d}_3d")
+
+
+def batch_pairs(n2d: int = 32, n3d: int = 32, base_seed: int = 3000) -> List[Pair]:
+    """The uneven batch: n2d planes and n3d volumes (see batch_pair)."""
+    return [batch_pair(i, n2d=n2d, base_seed=base_seed) for i in range(n2d + n3d)]
 
 
 def training_pair(i: int, shape=(150, 200, 200), crit: Criteria = Criteria(0.02, 2.0)) -> Pair:
