@@ -105,6 +105,9 @@ struct ShellTile {
     static constexpr int TX = 32, TY = N == 3 ? 4 : 8, TZ = N == 3 ? 2 : 1;
     static constexpr int BX = 40, BY = TY + 2, BZ = N == 3 ? TZ + 2 : 1;
     static constexpr int ELEMS = BX * BY * BZ;
+    // each staging buffer starts on a 128-byte boundary (TMA destination rule)
+    static constexpr int STRIDE = (ELEMS + 31) / 32 * 32;
+    static_assert(STRIDE * 4 % 128 == 0, "TMA destination must stay 128-byte aligned");
 };
 
 // A face owned by the cell whose lower corner sits at -S from the voxel
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(256, MINB)
 {
     using T = ShellTile<N>;
     constexpr int NC = 1 << N;
-    __shared__ __align__(128) float tile[2][T::ELEMS];
+    __shared__ __align__(128) float tile[2][T::STRIDE];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ unsigned int sh_best[256];      // gamma^2 bits of the tile's voxels
     __shared__ float sh_dr[256], sh_inv[256];

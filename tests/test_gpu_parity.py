@@ -91,6 +91,19 @@ def test_plane_128_full():
     assert st["n_eval"] > 1000
 
 
+@pytest.mark.parametrize("blocks", [1, 2])
+def test_plane_larger_than_one_tile_per_block(blocks):
+    # More 32x8 tiles than persistent blocks: every block stages tiles into
+    # both of its shared-memory buffers (the second one must stay aligned for
+    # the tensor copy).
+    p = synth.make_pair_2d(shape=(512, 640), spacing=(1.0, 1.0), seed=13, shift_mm=(0.5, 1.2),
+                           scale=1.03)
+    crit = synth.Criteria(0.02, 2.0)
+    got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"shell_blocks_per_sm": blocks})
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
 @pytest.mark.parametrize("local", [False, True])
 def test_plane_ragged(local):
     p = synth.make_pair_2d(shape=(37, 53), spacing=(1.25, 0.8), seed=11, shift_mm=(0.4, -1.1),
