@@ -45,7 +45,7 @@ WORKLOAD_DESC = ("synthetic IMRT pair 160x160x120 at 2.5 mm (7 coplanar beams, 1
 FLOP_PER_CELL = {3: 615, 2: 103}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
-KERNELS_PER_RUN = 5          # prepare, shell, bucket scan, scatter, tail
+KERNELS_PER_RUN = 4          # prepare, shell, scatter, tail
 
 
 def parse():
@@ -280,11 +280,16 @@ def run_ours(args, pair, rank, world, local_rank):
     out = torch.empty_like(ref)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     h = g.gamma_create(ref, ev, ndim, shape, spacing, crit)
+    tuned = None
+    if args.lanes or args.shell_blocks:
+        if args.lanes:
+            g.gamma_set_option(h, "lanes_per_voxel", args.lanes)
+        if args.shell_blocks:
+            g.gamma_set_option(h, "shell_blocks_per_sm", args.shell_blocks)
+    else:
+        lanes, blocks, _ = g.gamma_autotune(h, out, stream, reps=3)   # setup, not timed
+        tuned = {"lanes_per_voxel": lanes, "shell_blocks_per_sm": blocks}
     g.gamma_set_option(h, "timing", 1)
-    if args.lanes:
-        g.gamma_set_option(h, "lanes_per_voxel", args.lanes)
-    if args.shell_blocks:
-        g.gamma_set_option(h, "shell_blocks_per_sm", args.shell_blocks)
 
     def barrier():
         if world > 1:
@@ -390,6 +395,7 @@ def run_ours(args, pair, rank, world, local_rank):
                    "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "phases_ms": mean_ph,
+        "autotuned": tuned,
         "search": {"tail_voxels": stats["tail_voxels"], "overflow_voxels": stats["overflow_voxels"],
                    "fp64_cells": stats["fp64_cells"], "table_entries": stats["table_entries"],
                    "r_max": stats["r_max"], "shell_cells": shell_cells, "tail_cells": tail_cells},

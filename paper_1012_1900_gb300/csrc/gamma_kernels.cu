@@ -1,6 +1,6 @@
 // CUDA kernels of the gamma search (sm_103a).
 //
-// One run over a dose pair is five stream-ordered launches:
+// One run over a dose pair is four stream-ordered launches:
 //   k_prepare   max of the reference dose (the global dose norm) and a
 //               finite-input check                       (Algorithm A2 step 2)
 //   k_shell     per reference voxel: criteria, low-dose cutoff, gamma0 =
@@ -8,8 +8,7 @@
 //               around the voxel, from its 3^n neighbourhood held in
 //               registers; voxels whose running gamma still exceeds the next
 //               table key are queued with a cost bucket
-//   k_bucket_scan / k_scatter
-//               order the queue by estimated cost, most expensive first (the
+//   k_scatter   order the queue by estimated cost, most expensive first (the
 //               role the paper's DD sort plays, Section 2.2 and Table 2)
 //   k_tail      persistent: a group of G lanes takes one queued voxel and
 //               walks the sorted cell table G cells at a time, with the exact
@@ -52,7 +51,21 @@ __global__ void __launch_bounds__(256)
     float m = -kInf;
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.nvox; i += stride) {
+    const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long done = 0;
+    if ((((uintptr_t)P.ref | (uintptr_t)P.ev) & 15u) == 0) {      // 16-byte vector reads
+        const long long n4 = P.nvox / 4;
+        const float4* r4 = (const float4*)P.ref;
+        const float4* e4 = (const float4*)P.ev;
+        for (long long i = first; i < n4; i += stride) {
+            const float4 r = __ldg(r4 + i), e = __ldg(e4 + i);
+            bad |= !(isfinite(r.x) && isfinite(r.y) && isfinite(r.z) && isfinite(r.w) &&
+                     isfinite(e.x) && isfinite(e.y) && isfinite(e.z) && isfinite(e.w));
+            m = fmaxf(m, fmaxf(fmaxf(r.x, r.y), fmaxf(r.z, r.w)));
+        }
+        done = n4 * 4;
+    }
+    for (long long i = done + first; i < P.nvox; i += stride) {
         const float r = __ldg(P.ref + i), e = __ldg(P.ev + i);
         bad |= !(isfinite(r) && isfinite(e));
         m = fmaxf(m, r);
@@ -496,24 +509,36 @@ __global__ void __launch_bounds__(256, MINB)
 // Queue ordering: bucket offsets (most expensive first) and scatter
 // --------------------------------------------------------------------------
 
-__global__ void k_bucket_scan(Counters* ctr)
+// Scatter queued voxels into bucket order.  Every block derives the bucket
+// starts from the histogram itself (32 values), then reserves one range per
+// bucket per block-chunk with a single atomic on a per-bucket cursor.
+__global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ Problem P)
 {
+    __shared__ unsigned start[kNumBuckets], cnt[kNumBuckets], base[kNumBuckets];
     if (threadIdx.x == 0) {
         unsigned acc = 0;
         for (int b = kNumBuckets - 1; b >= 0; --b) {
-            ctr->cursor[b] = acc;
-            acc += ctr->hist[b];
+            start[b] = acc;
+            acc += P.ctr->hist[b];
         }
     }
-}
-
-__global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ Problem P)
-{
     const unsigned total = min(P.ctr->tail_count, P.tail_cap);
-    const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const unsigned pos = atomicAdd(&P.ctr->cursor[P.tail_bucket[i]], 1u);
-        P.tail_sorted[pos] = P.tail_raw[i];
+    for (unsigned c0 = blockIdx.x * blockDim.x; c0 < total; c0 += gridDim.x * blockDim.x) {
+        if (threadIdx.x < kNumBuckets) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned i = c0 + threadIdx.x;
+        int b = -1;
+        unsigned rank = 0;
+        if (i < total) {
+            b = P.tail_bucket[i];
+            rank = atomicAdd(&cnt[b], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumBuckets && cnt[threadIdx.x])
+            base[threadIdx.x] = start[threadIdx.x] + atomicAdd(&P.ctr->cursor[threadIdx.x], cnt[threadIdx.x]);
+        __syncthreads();
+        if (b >= 0) P.tail_sorted[base[b] + rank] = P.tail_raw[i];
+        __syncthreads();
     }
 }
 
@@ -783,7 +808,7 @@ static int grid_for(long long n, int threads, int cap)
 cudaError_t launch_prepare(const Problem& P, cudaStream_t s)
 {
     const int sms = device_sm_count();
-    k_prepare<false><<<grid_for(P.nvox, 256, sms * 8), 256, 0, s>>>(P, nullptr);
+    k_prepare<false><<<grid_for((P.nvox + 3) / 4, 256, sms * 4), 256, 0, s>>>(P, nullptr);
     return cudaGetLastError();
 }
 
@@ -983,7 +1008,6 @@ cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s)
 {
     if (!P.sort_tail) return cudaSuccess;
-    k_bucket_scan<<<1, 32, 0, s>>>(P.ctr);
     const int sms = device_sm_count();
     k_scatter<<<sms * 2, 256, 0, s>>>(P);
     return cudaGetLastError();
