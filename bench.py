@@ -255,6 +255,32 @@ def shard_pairs(costs, world: int, rank: int):
     return [i for i in range(len(costs)) if owner[i] == rank]
 
 
+def shell_source_hash() -> str:
+    """Hash of the key-0 cell kernel's source, to tell whether recorded ncu
+    counters still describe it."""
+    import hashlib
+    base = os.path.join(ROOT, "paper_1012_1900_gb300", "csrc")
+    s = open(os.path.join(base, "gamma_kernels.cu")).read()
+    a, b = s.index("// k_shell: gamma0 and the key-0 cells"), s.index("// Queue ordering")
+    face = open(os.path.join(base, "gamma_face.cuh")).read()
+    return hashlib.sha256((s[a:b] + face).encode()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel changed since the capture or none was taken for this workload."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("workload") != workload:
+        return None
+    if kernel == "k_shell" and rec.get("source_sha256_16") != shell_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -371,7 +397,7 @@ def run_ours(args, pair, rank, world, local_rank):
         achieved = flops / t_k / 1e12 if t_k > 0 else 0.0
         roofline = {"bound": "alu", "kernel": f"k_{kernel}", "achieved": achieved,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                    "traffic": None,
+                    "traffic": recorded_traffic(f"k_{kernel}", args.workload),
                     "peak_basis": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                   f"{sm_max:.0f} MHz",
                     "work": f"{cells} cells x {FLOP_PER_CELL[ndim]} FLOP"}
