@@ -112,9 +112,15 @@ __host__ __device__ __forceinline__ void cell_geom(int cx, int cy, int cz, const
 // Projection of the origin onto the owned face with chain (U1[, U2[, U3]]).
 // d2 is the squared distance, or +inf when the projection falls outside the
 // face or the face leaves the grid; mu are the coefficients of the chain
-// increments (the foot point is s0 + sum_i mu_i e_i).  Raises `ill` when the
-// face's Gram matrix is near singular in the normalised-determinant sense
-// det(G) / prod(G_ii) < tau.
+// increments (the foot point is s0 + sum_i mu_i e_i).
+//
+// Near-singular Gram matrices.  With the increments scaled to unit spatial
+// length the Gram matrix is I + g g^T, whose normalised determinant
+// det(G) / prod(G_ii) = D / prod_i (1 + g_i^2) with D = 1 + |g|^2.  Since
+// every factor 1 + g_i^2 <= D, the ratio is >= D^(1 - M), so it can only fall
+// below tau when D > tau^(-1/2) (M = 3) or tau^(-1) (M = 2).  The face
+// therefore only raises `ill` when D > dmax = tau^(-1/2); the caller then
+// applies the exact test (cell_gram_ill) before redoing the cell in FP64.
 template <typename T>
 struct FaceFoot {
     T d2, mu1, mu2, mu3;
@@ -122,7 +128,7 @@ struct FaceFoot {
 
 template <int M, int U1, int U2, int U3, typename T>
 __device__ __forceinline__ FaceFoot<T> face_core(const T (&q)[8], uint32_t ok, const CellGeom<T>& g,
-                                                 const T (&kappa)[8], T tau, bool& ill)
+                                                 const T (&kappa)[8], T dmax, bool& ill)
 {
     constexpr int UM = M == 1 ? U1 : (M == 2 ? U2 : U3);
     constexpr int A1 = U1, A2 = U2 ^ U1, A3 = U3 ^ U2;
@@ -162,10 +168,7 @@ __device__ __forceinline__ FaceFoot<T> face_core(const T (&q)[8], uint32_t ok, c
             valid = valid && (f.mu2 >= f.mu3);
             last = f.mu3;
         }
-        // normalised Gram determinant (1 + |g|^2) / prod(1 + g_i^2)
-        T prod = fma_(d1, k1, T(1)) * fma_(d2, k2, T(1));
-        if constexpr (M >= 3) prod *= fma_(d3, k3, T(1));
-        ill = ill || (D < tau * prod);
+        ill = ill || (D > dmax);
     }
     valid = valid && (last >= T(0)) && ((ok >> UM) & 1u);
     f.d2 = valid ? fma_(L, r, rho2) : T(kInf);
@@ -174,9 +177,9 @@ __device__ __forceinline__ FaceFoot<T> face_core(const T (&q)[8], uint32_t ok, c
 
 template <int M, int U1, int U2, int U3, typename T>
 __device__ __forceinline__ T face_d2(const T (&q)[8], uint32_t ok, const CellGeom<T>& g,
-                                     const T (&kappa)[8], T tau, bool& ill)
+                                     const T (&kappa)[8], T dmax, bool& ill)
 {
-    return face_core<M, U1, U2, U3, T>(q, ok, g, kappa, tau, ill).d2;
+    return face_core<M, U1, U2, U3, T>(q, ok, g, kappa, dmax, ill).d2;
 }
 
 template <int M, int U1, int U2, int U3>
@@ -209,18 +212,18 @@ constexpr int kFacesPerCell = N == 3 ? 26 : 6;
 
 template <typename T, int M, int U1, int U2, int U3>
 __device__ __forceinline__ void apply_face(Face<M, U1, U2, U3>, const T (&q)[8], uint32_t ok,
-                                           const CellGeom<T>& g, const T (&kappa)[8], T tau,
+                                           const CellGeom<T>& g, const T (&kappa)[8], T dmax,
                                            T& best, bool& ill)
 {
-    best = min_(best, face_d2<M, U1, U2, U3, T>(q, ok, g, kappa, tau, ill));
+    best = min_(best, face_d2<M, U1, U2, U3, T>(q, ok, g, kappa, dmax, ill));
 }
 
 template <typename T, typename... Fs>
 __device__ __forceinline__ void apply_all(std::tuple<Fs...>*, const T (&q)[8], uint32_t ok,
-                                          const CellGeom<T>& g, const T (&kappa)[8], T tau,
+                                          const CellGeom<T>& g, const T (&kappa)[8], T dmax,
                                           T& best, bool& ill)
 {
-    (apply_face(Fs{}, q, ok, g, kappa, tau, best, ill), ...);
+    (apply_face(Fs{}, q, ok, g, kappa, dmax, best, ill), ...);
 }
 
 // Minimum squared distance over all faces owned by one cell.  q holds the
@@ -229,11 +232,49 @@ __device__ __forceinline__ void apply_all(std::tuple<Fs...>*, const T (&q)[8], u
 // vertex u lies inside the grid (bit 0 must be set).
 template <int N, typename T>
 __device__ __forceinline__ T cell_min_d2(const T (&q)[8], uint32_t ok, const CellGeom<T>& g,
-                                         const MetricT<T>& mt, T tau, T best, bool& ill)
+                                         const MetricT<T>& mt, T dmax, T best, bool& ill)
 {
     best = min_(best, fma_(q[0], q[0], g.tsum[0]));            // the vertex itself
-    apply_all<T>((typename FaceList<N>::type*)nullptr, q, ok, g, mt.kappa, tau, best, ill);
+    apply_all<T>((typename FaceList<N>::type*)nullptr, q, ok, g, mt.kappa, dmax, best, ill);
     return best;
+}
+
+// Exact near-singularity test of the cell's faces: det(G)/prod(G_ii) < tau.
+template <int M, int U1, int U2, int U3>
+__device__ __forceinline__ bool gram_ill_face(Face<M, U1, U2, U3>, const float (&q)[8], uint32_t ok,
+                                              const float (&kappa)[8], float tau)
+{
+    if constexpr (M < 2) {
+        return false;
+    } else {
+        constexpr int UM = M == 2 ? U2 : U3;
+        constexpr int A1 = U1, A2 = U2 ^ U1, A3 = U3 ^ U2;
+        if (!((ok >> UM) & 1u)) return false;
+        const float d1 = q[U1] - q[0], d2 = q[U2] - q[U1];
+        const float e1 = fmaf(d1 * kappa[A1], d1, 1.f), e2 = fmaf(d2 * kappa[A2], d2, 1.f);
+        float D = e1 + e2 - 1.f, prod = e1 * e2;
+        if constexpr (M >= 3) {
+            const float d3 = q[U3] - q[U2];
+            const float e3 = fmaf(d3 * kappa[A3], d3, 1.f);
+            D += e3 - 1.f;
+            prod *= e3;
+        }
+        return D < tau * prod;
+    }
+}
+
+template <typename... Fs>
+__device__ __forceinline__ bool gram_ill_all(std::tuple<Fs...>*, const float (&q)[8], uint32_t ok,
+                                             const float (&kappa)[8], float tau)
+{
+    return (gram_ill_face(Fs{}, q, ok, kappa, tau) || ...);
+}
+
+template <int N>
+__device__ __forceinline__ bool cell_gram_ill(const float (&q)[8], uint32_t ok, const float (&kappa)[8],
+                                           float tau)
+{
+    return gram_ill_all((typename FaceList<N>::type*)nullptr, q, ok, kappa, tau);
 }
 
 // Argmin variant: the minimum over the cell's faces of the squared distance
@@ -244,7 +285,7 @@ __device__ __forceinline__ void arg_face(Face<M, U1, U2, U3>, const T (&q)[8], u
                                          T (&foot)[3])
 {
     bool ill = false;
-    const FaceFoot<T> f = face_core<M, U1, U2, U3, T>(q, ok, g, kappa, T(0), ill);
+    const FaceFoot<T> f = face_core<M, U1, U2, U3, T>(q, ok, g, kappa, T(kInf), ill);
     if (f.d2 < best) {
         best = f.d2;
         constexpr int A1 = U1, A2 = U2 ^ U1, A3 = U3 ^ U2;

@@ -34,6 +34,12 @@ __device__ __forceinline__ float resolve_dnorm(const Problem& P)
     return P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
 }
 
+// Pre-filter threshold on D for the near-singular Gram test (see face_core).
+__device__ __forceinline__ float ill_dmax(const Problem& P)
+{
+    return P.tau > 0.f ? 0.99f * rsqrtf(P.tau) : kInf;
+}
+
 __device__ __forceinline__ bool is_evaluated(const Problem& P, float dr, float thr)
 {
     return dr >= thr && (!P.local || dr > 0.f);
@@ -101,7 +107,7 @@ __device__ __noinline__ float cell_redo_f64(const float* __restrict__ ev, long l
     CellGeom<double> g;
     cell_geom<N, double>(cx, cy, cz, mtd, g);
     bool ill = false;
-    const double b = cell_min_d2<N, double>(q, ok, g, mtd, 0.0, (double)kInf, ill);
+    const double b = cell_min_d2<N, double>(q, ok, g, mtd, (double)kInf, (double)kInf, ill);
     atomicAdd(fp64_counter, 1u);
     return (float)b;
 }
@@ -185,7 +191,9 @@ __device__ __forceinline__ void shell_cell(const Problem& P, const float* tile, 
     float cb = kInf;
     // the cell's corner vertex: the voxel itself when S == 0, else a far face
     if constexpr ((S == 0) == NEAR) cb = fmaf(q[0], q[0], g.tsum[0]);
-    apply_sel<NEAR, S>((typename FaceList<N>::type*)nullptr, q, ok, g, P.mt.kappa, P.tau, cb, ill);
+    apply_sel<NEAR, S>((typename FaceList<N>::type*)nullptr, q, ok, g, P.mt.kappa, ill_dmax(P), cb,
+                       ill);
+    if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
     if (ill) {
         const long long sy = P.nx, sz = (long long)P.nx * P.ny;
         const double drd = dr;
@@ -448,7 +456,8 @@ __global__ void __launch_bounds__(256, MINB)
             CellGeom<float> g;
             cell_geom<N, float>(cx, cy, cz, P.mt, g);
             bool ill = false;
-            float cb = cell_min_d2<N, float>(q, ok, g, P.mt, P.tau, kInf, ill);
+            float cb = cell_min_d2<N, float>(q, ok, g, P.mt, ill_dmax(P), kInf, ill);
+            if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
             if (ill) {
                 const double drd = vdr;
                 const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
@@ -628,7 +637,8 @@ __device__ __forceinline__ float visit_cell(const Problem& P, int x, int y, int 
     CellGeom<float> g;
     cell_geom<N, float>(cx, cy, cz, P.mt, g);
     bool ill = false;
-    float cb = cell_min_d2<N, float>(q, ok, g, P.mt, P.tau, kInf, ill);
+    float cb = cell_min_d2<N, float>(q, ok, g, P.mt, ill_dmax(P), kInf, ill);
+    if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
     if (ill)
         cb = cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd, P.mtd, &P.ctr->fp64_cells);
     return fminf(best, cb);

@@ -555,7 +555,10 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
                     CellGeom<float> gg;
                     cell_geom<N, float>(cx, cy, cz, P.mt, gg);
                     bool ill = false;
-                    const float cb = cell_min_d2<N, float>(q, ok, gg, P.mt, P.tau, kInf, ill);
+                    const float cb = cell_min_d2<N, float>(q, ok, gg, P.mt,
+                                                           P.tau > 0.f ? 0.99f * rsqrtf(P.tau) : kInf,
+                                                           kInf, ill);
+                    if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
                     if (!ill) sd2 = fminf(sd2, cb);        // ill-conditioned cells are not used as seeds
                 }
             }
