@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
-    ap.add_argument("--experiment", choices=["learned", "batch"], default=None,
+    ap.add_argument("--experiment", choices=["learned", "batch", "studies"], default=None,
                     help="learned: train + evaluate the proposal network (200x200x150 pairs, "
                          "2%%/2mm); batch: 64 uneven pairs batched vs one by one")
     ap.add_argument("--train-pairs", type=int, default=200)
@@ -644,8 +644,91 @@ def experiment_batch(args):
     }), flush=True)
 
 
+def experiment_studies(args):
+    """Synthetic re-runs of the paper's timing studies on one GPU:
+    Fig. 1(b) (evaluation dose shifted -10 %..+10 % inside the 10 % isodose,
+    time against sum gamma^3), Fig. 2 (resolution sweep, power-law exponent),
+    Table 3 (DD x DTA grid), and the ablation of the cost-ordered queue."""
+    import torch
+    import paper_1012_1900_gb300 as g
+
+    def run(ref_np, ev_np, spacing, crit, opts=None, reps=5):
+        ref = torch.from_numpy(np.ascontiguousarray(ref_np)).cuda()
+        ev = torch.from_numpy(np.ascontiguousarray(ev_np)).cuda()
+        out = torch.empty_like(ref)
+        h = g.gamma_create(ref, ev, 3, ref_np.shape, spacing,
+                           g.criteria(crit[0], crit[1], False, 0.10, 0.0))
+        try:
+            for k, v in (opts or {}).items():
+                g.gamma_set_option(h, k, v)
+            g.gamma_run(h, out)
+            g.gamma_pass_rate(h)
+            ms = _timed_runs(g, h, out, reps)
+            st = g.gamma_get_stats(h)
+            gm = out.cpu().numpy().astype(np.float64)
+        finally:
+            g.gamma_destroy(h)
+        ok = np.isfinite(gm)
+        return ms, float(np.sum(gm[ok] ** 3)), st, float(np.mean(gm[ok] <= 1.0)) if ok.any() else 0.0
+
+    res = {"experiment": "studies"}
+    # ---- Fig. 1(b): additive shifts of the evaluation dose inside the 10 % isodose ----
+    base = synth.make_pair_3d(shape=(144, 256, 256), spacing=(2.5, 1.5625, 1.5625), seed=2,
+                              shift_mm=(0.0, 0.0, 1.5), scale=1.0, criteria=synth.Criteria(0.03, 3.0))
+    inside = base.ref >= 0.1 * base.ref.max()
+    shifts = []
+    for k in range(-10, 11):
+        ev = base.eval + np.where(inside, np.float32(k / 100.0), np.float32(0.0))
+        ms, s3, st, pr = run(base.ref, ev.astype(np.float32), base.spacing, (0.03, 3.0))
+        shifts.append({"shift_pct": k, "ms": ms, "sum_gamma3": s3, "tail_voxels": st["tail_voxels"],
+                       "pass_rate": pr})
+    t = np.array([r["ms"] for r in shifts])
+    s3 = np.array([r["sum_gamma3"] for r in shifts])
+    res["fig1b"] = {"workload": "256x256x144 (1.5625 x 1.5625 x 2.5 mm), 3%/3mm global",
+                    "points": shifts, "corr_time_vs_sum_gamma3": float(np.corrcoef(t, s3)[0, 1])}
+    del base, ev
+    # ---- Fig. 2: resolution sweep over the same physical box ----
+    box = (360.0, 400.0, 400.0)
+    sweep = []
+    for shp in [(144, 128, 128), (72, 256, 256), (144, 256, 256), (72, 512, 512)]:
+        sp = tuple(b / n for b, n in zip(box, shp))
+        p = synth.make_pair_3d(shape=shp, spacing=sp, seed=2, shift_mm=(0.0, 0.0, 1.5), scale=1.03)
+        ms, s3_, st, pr = run(p.ref, p.eval, p.spacing, (0.03, 3.0))
+        sweep.append({"shape": list(shp[::-1]), "voxels": p.nvox, "ms": ms, "sum_gamma3": s3_})
+        del p
+    nv = np.log([r["voxels"] for r in sweep])
+    lt = np.log([r["ms"] for r in sweep])
+    res["fig2"] = {"workload": "400x400x360 mm box, 3%/3mm global", "points": sweep,
+                   "exponent_time_vs_voxels": float(np.polyfit(nv, lt, 1)[0])}
+    # ---- Table 3: DD x DTA grid on the 256^2 x 144 case ----
+    p = synth.make_pair_3d(shape=(144, 256, 256), spacing=(2.5, 1.5625, 1.5625), seed=2,
+                           shift_mm=(0.0, 0.0, 1.5), scale=1.03)
+    grid = []
+    for dd in (0.01, 0.02, 0.03):
+        for dta in (1.0, 2.0, 3.0):
+            ms, s3_, st, pr = run(p.ref, p.eval, p.spacing, (dd, dta))
+            grid.append({"dd_pct": dd * 100, "dta_mm": dta, "ms": ms, "sum_gamma3": s3_,
+                         "pass_rate": pr, "tail_voxels": st["tail_voxels"]})
+    res["table3"] = {"workload": "256x256x144, eval 1.03*D(x-1.5mm)+noise", "points": grid}
+    # ---- NEXT #2: cost-ordered queue against discovery order ----
+    abl = []
+    for crit in [(0.01, 3.0), (0.01, 1.0), (0.03, 3.0)]:
+        row = {"dd_pct": crit[0] * 100, "dta_mm": crit[1]}
+        for lanes in (4, 32):
+            for srt in (1, 0):
+                ms, _, st, _ = run(p.ref, p.eval, p.spacing, crit,
+                                   {"sort_tail": srt, "lanes_per_voxel": lanes, "timing": 1})
+                row[f"ms_lanes{lanes}_{'sorted' if srt else 'unsorted'}"] = ms
+        abl.append(row)
+    res["queue_ablation"] = abl
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
+    if args.experiment == "studies":
+        experiment_studies(args)
+        return
     if args.experiment == "learned":
         experiment_learned(args)
         return
