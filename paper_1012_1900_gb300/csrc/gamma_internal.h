@@ -76,11 +76,9 @@ __host__ __device__ inline float fdec(unsigned int e)
     return c.f;
 }
 
-// Constants of the 2^n key-0 cells around a voxel (lower-corner offsets
-// c in {-1, 0}^n, indexed by the mask of axes where c = -1), computed on the
-// host by the shell launcher.
+// Constant of the 2^n key-0 cells around a voxel (lower-corner offsets
+// c in {-1, 0}^n), computed on the host by the shell launcher.
 struct ShellConst {
-    CellGeom<float> g[8];
     float far2;   // squared spatial distance from the voxel to the nearest face
                   // of these cells that does not contain it (rounded down)
 };

@@ -23,6 +23,7 @@
 #include <cstring>
 
 #include "gamma_internal.h"
+#include "gamma_near.cuh"
 #include "gamma_tma.cuh"
 
 namespace gk {
@@ -128,103 +129,6 @@ struct ShellTile {
     static constexpr int STRIDE = (ELEMS + 31) / 32 * 32;
     static_assert(STRIDE * 4 % 128 == 0, "TMA destination must stay 128-byte aligned");
 };
-
-// A face owned by the cell whose lower corner sits at -S from the voxel
-// contains the voxel iff the voxel (vertex S of the cell) is on its chain.
-template <int M, int U1, int U2, int U3>
-constexpr bool face_has_vertex(int S)
-{
-    return S == 0 || S == U1 || (M >= 2 && S == U2) || (M >= 3 && S == U3);
-}
-
-template <bool NEAR, int S, int M, int U1, int U2, int U3>
-__device__ __forceinline__ void apply_face_sel(Face<M, U1, U2, U3>, const float (&q)[8],
-                                               uint32_t ok, const CellGeom<float>& g,
-                                               const float (&kappa)[8], float tau, float& best,
-                                               bool& ill)
-{
-    if constexpr (face_has_vertex<M, U1, U2, U3>(S) == NEAR)
-        best = fminf(best, face_d2<M, U1, U2, U3, float>(q, ok, g, kappa, tau, ill));
-}
-
-template <bool NEAR, int S, typename... Fs>
-__device__ __forceinline__ void apply_sel(std::tuple<Fs...>*, const float (&q)[8], uint32_t ok,
-                                          const CellGeom<float>& g, const float (&kappa)[8],
-                                          float tau, float& best, bool& ill)
-{
-    (apply_face_sel<NEAR, S>(Fs{}, q, ok, g, kappa, tau, best, ill), ...);
-}
-
-// The faces of key-0 cell S (lower corner at -S from the voxel) that contain
-// the voxel (NEAR) or not.  S is a compile-time constant, so the face subset,
-// the shared-memory offsets and the cell constants are all resolved at compile
-// time.  A cell flagged ill-conditioned is redone in FP64 (all its faces) and
-// marked in `done64` so the other pass skips it.
-template <int N, bool NEAR, int S>
-__device__ __forceinline__ void shell_cell(const Problem& P, const float* tile, int tix,
-                                           uint32_t inm, uint32_t inp, float dr, float inv,
-                                           float dnorm, long long v, float& best, uint32_t& done64)
-{
-    using T = ShellTile<N>;
-    if (!NEAR && ((done64 >> S) & 1u)) return;
-    float q[8];
-    uint32_t ok = 0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        q[u] = 0.f;
-        if (u < (1 << N)) {
-            bool in = true;
-            int off = 0;
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                const int d = ((u >> a) & 1) - ((S >> a) & 1);              // -1, 0, +1
-                in = in && (d < 0 ? ((inm >> a) & 1u) : d > 0 ? ((inp >> a) & 1u) : 1u);
-                off += d * (a == 0 ? 1 : a == 1 ? T::BX : T::BX * T::BY);
-            }
-            q[u] = (tile[tix + off] - dr) * inv;       // halo entries outside the grid are 0
-            ok |= (in ? 1u : 0u) << u;
-        }
-    }
-    if (!(ok & 1u)) return;
-    const CellGeom<float>& g = P.shell.g[S];
-    bool ill = false;
-    float cb = kInf;
-    // the cell's corner vertex: the voxel itself when S == 0, else a far face
-    if constexpr ((S == 0) == NEAR) cb = fmaf(q[0], q[0], g.tsum[0]);
-    apply_sel<NEAR, S>((typename FaceList<N>::type*)nullptr, q, ok, g, P.mt.kappa, ill_dmax(P), cb,
-                       ill);
-    if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
-    if (ill) {
-        const long long sy = P.nx, sz = (long long)P.nx * P.ny;
-        const double drd = dr;
-        const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
-        constexpr int cx = -(S & 1), cy = -((S >> 1) & 1), cz = -((S >> 2) & 1);
-        const long long p = v + cx + cy * sy + cz * sz;
-        cb = cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd, P.mtd,
-                              &P.ctr->fp64_cells);
-        done64 |= 1u << S;
-    }
-    best = fminf(best, cb);
-}
-
-template <int N, bool NEAR, int... Ss>
-__device__ __forceinline__ float shell_pass_seq(std::integer_sequence<int, Ss...>, const Problem& P,
-                                                const float* tile, int tix, uint32_t inm,
-                                                uint32_t inp, float dr, float inv, float dnorm,
-                                                long long v, float best, uint32_t& done64)
-{
-    (shell_cell<N, NEAR, Ss>(P, tile, tix, inm, inp, dr, inv, dnorm, v, best, done64), ...);
-    return best;
-}
-
-template <int N, bool NEAR>
-__device__ __forceinline__ float shell_pass(const Problem& P, const float* tile, int tix,
-                                            uint32_t inm, uint32_t inp, float dr, float inv,
-                                            float dnorm, long long v, float best, uint32_t& done64)
-{
-    return shell_pass_seq<N, NEAR>(std::make_integer_sequence<int, (1 << N)>{}, P, tile, tix, inm,
-                                   inp, dr, inv, dnorm, v, best, done64);
-}
 
 template <int N, int MINB, bool BATCH>
 __global__ void __launch_bounds__(256, MINB)
@@ -403,17 +307,16 @@ __global__ void __launch_bounds__(256, MINB)
             inm |= (z > 0) ? 4u : 0u;
             inp |= (z + 1 < P.nz) ? 4u : 0u;
         }
+        float dD = 0.f;
         if (act) {
-            const float dD = P.dd_frac * (P.local ? dr : dnorm);
+            dD = P.dd_frac * (P.local ? dr : dnorm);
             inv = 1.0f / dD;
             const float q0 = (tl[tix] - dr) * inv;
             best = q0 * q0;
             my_rmax = fmaxf(my_rmax, fabsf(q0));
         }
-        uint32_t done64 = 0;
-        if (__any_sync(kFull, act && best > 0.f))
-            best = act ? shell_pass<N, true>(P, tl, tix, inm, inp, dr, inv, dnorm, v, best, done64)
-                       : best;
+        if (act && best > 0.f)
+            best = near_gamma2<N, T::BX, T::BX * T::BY>(tl, tix, inm, inp, dr, dD, P.mt.kappa);
 
         // ---- phase B: far faces, shared by the whole block ----
         sh_best[threadIdx.x] = __float_as_uint(best);
@@ -879,8 +782,8 @@ static double simplex_dist_host(const double (*W)[3], int nv)
     return best;
 }
 
-// Constants of the key-0 cells: per-cell geometry and the smallest spatial
-// distance from the voxel to a face of these cells that does not contain it.
+// Constant of the key-0 cells: the smallest spatial distance from the voxel
+// to a face of these cells that does not contain it.
 static void shell_constants(const Problem& P, ShellConst& sc);
 
 void fill_shell_constants(Problem& P) { shell_constants(P, P.shell); }
@@ -888,15 +791,6 @@ void fill_shell_constants(Problem& P) { shell_constants(P, P.shell); }
 static void shell_constants(const Problem& P, ShellConst& sc)
 {
     const int N = P.ndim;
-    for (int s = 0; s < 8; ++s) {
-        if (s >= (1 << N)) {
-            sc.g[s] = CellGeom<float>{};
-            continue;
-        }
-        const int cx = -(s & 1), cy = -((s >> 1) & 1), cz = -((s >> 2) & 1);
-        if (N == 3) cell_geom<3, float>(cx, cy, cz, P.mt, sc.g[s]);
-        else cell_geom<2, float>(cx, cy, 0, P.mt, sc.g[s]);
-    }
     // every owned face is a chain 0 = u0 < u1 < ... < um of axis masks
     const double hn[3] = {P.hn[0], P.hn[1], N == 3 ? P.hn[2] : 0.0};
     double far = INFINITY;
