@@ -170,8 +170,8 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *  "timing"           1: record per-phase CUDA events (gamma_get_timings)
  *  "graph"            batch handles: 0 launches directly instead of capturing
  *                     and replaying a CUDA graph
- *  "shell_blocks_per_sm"  1 or 2: register budget of the key-0 cell kernel
- *                     (2 = 128 registers a thread, two blocks per SM)
+ *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell
+ *                     kernel's register budget is sized for (default 2)
  * Errors: INVALID_ARG (unknown key or value), TABLE_TOO_LARGE, OOM. */
 int gamma_set_option(gamma_handle h, const char *key, int64_t value);
 
@@ -222,7 +222,7 @@ int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
 
 /* Autotuner: times the full run (single or batch handle) for every
  * combination of lanes_per_voxel in {4, 8, 16, 32} and
- * shell_blocks_per_sm in {1, 2} (one warm-up and `reps` timed runs each, CUDA
+ * shell_blocks_per_sm in {1, 2, 3, 4} (one warm-up and `reps` timed runs each, CUDA
  * events on `cuda_stream`), keeps the fastest as the handle's options and
  * returns it (any output pointer may be NULL).  gamma_out_dev receives the
  * gamma map of a single-pair handle (device, nz*ny*nx floats) and is ignored

@@ -110,7 +110,7 @@ struct Problem {
     unsigned char* tail_bucket;  // their cost buckets
     unsigned int* tail_sorted;   // tail voxels, most expensive bucket first
     int sort_tail;               // 0: keep discovery order (ablation)
-    int shell_minblocks;         // k_shell variant: 1 (no spills) or 2 (128 registers); 0 = 2
+    int shell_minblocks;         // k_shell register budget: resident blocks per SM, 1..4
     ShellConst shell;            // filled by launch_shell
 };
 

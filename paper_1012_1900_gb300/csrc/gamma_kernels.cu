@@ -4,10 +4,10 @@
 //   k_prepare   max of the reference dose (the global dose norm) and a
 //               finite-input check                       (Algorithm A2 step 2)
 //   k_shell     per reference voxel: criteria, low-dose cutoff, gamma0 =
-//               DD/dD (A1 step 4a) and every face of the 2^n key-0 cells
-//               around the voxel, from its 3^n neighbourhood held in
-//               registers; voxels whose running gamma still exceeds the next
-//               table key are queued with a cost bucket
+//               DD/dD (A1 step 4a) and every face through the voxel's node
+//               (reduced closed form), from a TMA-staged tile; voxels whose
+//               running gamma still exceeds the distance to any other face
+//               are queued with a cost bucket
 //   k_scatter   order the queue by estimated cost, most expensive first (the
 //               role the paper's DD sort plays, Section 2.2 and Table 2)
 //   k_tail      persistent: a group of G lanes takes one queued voxel and
@@ -136,13 +136,8 @@ __global__ void __launch_bounds__(256, MINB)
             int use_tma0, int ntiles, const BatchDesc* __restrict__ bd)
 {
     using T = ShellTile<N>;
-    constexpr int NC = 1 << N;
     __shared__ __align__(128) float tile[2][T::STRIDE];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ unsigned int sh_best[256];      // gamma^2 bits of the tile's voxels
-    __shared__ float sh_dr[256], sh_inv[256];
-    __shared__ unsigned short sh_far[256];     // voxels that still need the far faces
-    __shared__ unsigned int sh_nfar;
     __shared__ unsigned int sh_hist[kNumBuckets];
     __shared__ unsigned long long sh_eval, sh_pass;
     __shared__ unsigned int sh_rmax;
@@ -156,7 +151,6 @@ __global__ void __launch_bounds__(256, MINB)
         sh_eval = 0;
         sh_pass = 0;
         sh_rmax = 0;
-        sh_nfar = 0;
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
@@ -256,25 +250,20 @@ __global__ void __launch_bounds__(256, MINB)
         const float thr = P.cutoff_frac * dnorm;
         const float k1 = P.t1 < P.ntable ? P.table[P.t1].key : kInf;
         const float rc2 = P.r_cover * P.r_cover;
+        const float qlim = fminf(P.shell.far2, k1 * k1);
         const bool table_ends = P.t1 >= P.ntable;
-        const long long sy = P.nx, sz = (long long)P.nx * P.ny;
         int x0, y0, z0;
         tile_origin(P.nx, P.ny, lt, x0, y0, z0);
         float* tl = tile[buf];
         // ---- stage: prefetch the next tile, wait for this one ----
+        // Every thread waits on the tile's mbarrier itself; a wait that gives
+        // up is reported at the end-of-tile barrier, where the block leaves
+        // together (the smem reads in between stay in bounds).
         if (threadIdx.x == 0) issue(t + gridDim.x, buf ^ 1);
+        bool timed_out = false;
         if (use_tma) {
-            const bool ok = mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+            timed_out = !mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
             parity ^= 1u << buf;
-            if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) {
-                    atomicOr(&P.ctr->flags, kFlagTimeout);
-                    // let this block's own copies land before it leaves
-                    mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
-                    mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
-                }
-                break;
-            }
         } else {
             for (int i = threadIdx.x; i < T::ELEMS; i += blockDim.x) {
                 const int bx = i % T::BX, by = (i / T::BX) % T::BY, bz = i / (T::BX * T::BY);
@@ -286,11 +275,11 @@ __global__ void __launch_bounds__(256, MINB)
             __syncthreads();
         }
 
-        // ---- phase A: gamma0 and the faces that contain the voxel ----
+        // ---- gamma0 and the faces that contain the voxel ----
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         const bool inside = x < P.nx && y < P.ny && z < P.nz;
         const long long v = inside ? ((long long)z * P.ny + y) * P.nx + x : 0;
-        float dr = 0.f, inv = 0.f, best = 0.f;
+        float dr = 0.f, best = 0.f;
         bool act = false;
         if (inside) {
             dr = __ldg(P.ref + v);
@@ -307,86 +296,30 @@ __global__ void __launch_bounds__(256, MINB)
             inm |= (z > 0) ? 4u : 0u;
             inp |= (z + 1 < P.nz) ? 4u : 0u;
         }
-        float dD = 0.f;
         if (act) {
-            dD = P.dd_frac * (P.local ? dr : dnorm);
-            inv = 1.0f / dD;
-            const float q0 = (tl[tix] - dr) * inv;
+            const float dD = P.dd_frac * (P.local ? dr : dnorm);
+            const float q0 = (tl[tix] - dr) / dD;
             best = q0 * q0;
             my_rmax = fmaxf(my_rmax, fabsf(q0));
+            if (best > 0.f) best = near_gamma2<N, T::BX, T::BX * T::BY>(tl, tix, inm, inp, dr, dD, P.mt.kappa);
         }
-        if (act && best > 0.f)
-            best = near_gamma2<N, T::BX, T::BX * T::BY>(tl, tix, inm, inp, dr, dD, P.mt.kappa);
 
-        // ---- phase B: far faces, shared by the whole block ----
-        sh_best[threadIdx.x] = __float_as_uint(best);
-        sh_dr[threadIdx.x] = dr;
-        sh_inv[threadIdx.x] = inv;
-        if (act && best > P.shell.far2) sh_far[atomicAdd(&sh_nfar, 1u)] = (unsigned short)threadIdx.x;
-        __syncthreads();
-        const unsigned nitems = sh_nfar * NC;
-        for (unsigned it = threadIdx.x; it < nitems; it += blockDim.x) {
-            const int lv = sh_far[it / NC];
-            const int sc = (int)(it % NC);
-            const int vx = x0 + (lv & 31), vy = y0 + (lv >> 5) % T::TY, vz = z0 + (lv >> 5) / T::TY;
-            const int cx = -(sc & 1), cy = -((sc >> 1) & 1), cz = N == 3 ? -((sc >> 2) & 1) : 0;
-            const int px = vx + cx, py = vy + cy, pz = vz + cz;
-            if (px < 0 || py < 0 || pz < 0) continue;           // corner outside the grid
-            const bool ex = px + 1 < P.nx, ey = py + 1 < P.ny, ez = N == 3 && pz + 1 < P.nz;
-            const int lvx = lv & 31, lvy = (lv >> 5) % T::TY, lvz = (lv >> 5) / T::TY;
-            const int cix = ((N == 3 ? lvz + 1 + cz : 0) * T::BY + (lvy + 1 + cy)) * T::BX + (lvx + 4 + cx);
-            const float vdr = sh_dr[lv], vinv = sh_inv[lv];
-            float q[8];
-            uint32_t ok = 0;
-            float qmin = kInf, qmax = -kInf;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                q[u] = 0.f;
-                if (u < NC) {
-                    const bool present = (!(u & 1) || ex) && (!(u & 2) || ey) && (!(u & 4) || ez);
-                    if (present) {
-                        const int o = ((u & 1) ? 1 : 0) + ((u & 2) ? T::BX : 0) + ((u & 4) ? T::BX * T::BY : 0);
-                        q[u] = (tl[cix + o] - vdr) * vinv;
-                        qmin = fminf(qmin, q[u]);
-                        qmax = fmaxf(qmax, q[u]);
-                        ok |= 1u << u;
-                    }
-                }
-            }
-            const float vbest = __uint_as_float(((volatile unsigned int*)sh_best)[lv]);
-            const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
-            if (gap * gap >= vbest) continue;                    // dose lower bound
-            CellGeom<float> g;
-            cell_geom<N, float>(cx, cy, cz, P.mt, g);
-            bool ill = false;
-            float cb = cell_min_d2<N, float>(q, ok, g, P.mt, ill_dmax(P), kInf, ill);
-            if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
-            if (ill) {
-                const double drd = vdr;
-                const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
-                const long long p = ((long long)pz * P.ny + py) * P.nx + px;
-                cb = cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd, P.mtd,
-                                      &P.ctr->fp64_cells);
-            }
-            atomicMin(&sh_best[lv], __float_as_uint(cb));
-        }
-        __syncthreads();
-        if (act) best = __uint_as_float(sh_best[threadIdx.x]);
-
-        // ---- phase C: finish or queue ----
+        // ---- finish or queue ----
+        // The other faces of the key-0 cells are at squared spatial distance
+        // >= far2 and every other cell at >= k1^2, so gamma^2 <= both is final.
         bool tail = false;
         int bucket = 0;
         if (act) {
-            tail = (best > k1 * k1) || (table_ends && best > rc2);
+            tail = (best > qlim) || (table_ends && best > rc2);
             if (tail) {
                 P.out[v] = best;                       // gamma^2, finished by k_tail
                 const float gk_ = sqrtf(best);
-                int lo = P.t1, hi = P.ntable;
+                int lo = 0, hi = P.ntable;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
                 }
-                const int cost = lo - P.t1;
+                const int cost = lo;
                 bucket = cost <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)cost)));
             } else {
                 const float gam = sqrtf(best);
@@ -411,8 +344,16 @@ __global__ void __launch_bounds__(256, MINB)
                 }
             }
         }
-        if (threadIdx.x == 0) sh_nfar = 0;
-        __syncthreads();                 // tile[buf] and the lists are free for reuse
+        // tile[buf] is free for reuse once every thread has passed this point
+        if (__syncthreads_or(timed_out)) {
+            if (threadIdx.x == 0) {
+                atomicOr(&P.ctr->flags, kFlagTimeout);
+                // let this block's own copies land before it leaves
+                mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+                mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
+            }
+            break;
+        }
     }
     if (!BATCH || cur >= 0) flush(BATCH ? sh_P : P0);
 }
@@ -603,8 +544,8 @@ __global__ void __launch_bounds__(256)
         const float inv = 1.0f / dD;
         const double drd = dr;
         const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
-        float best = P.out[v];                       // gamma^2 after the key-0 cells
-        int t = P.t1;
+        float best = P.out[v];                       // gamma^2 over the faces through v
+        int t = 0;                                   // from the key-0 cells' other faces on
         while (t < P.ntable) {
             const int idx = t + gl;
             float key = kInf;
@@ -887,6 +828,19 @@ int shell_tiles(const Problem& P)
     return tiles > 0x3fffffffLL ? -1 : (int)tiles;
 }
 
+// k_shell with its register budget chosen for `per_sm` resident blocks.
+template <int N, bool BATCH>
+static void launch_shell_k(int per_sm, unsigned grid, cudaStream_t s, const Problem& P,
+                           const CUtensorMap& map, int use_tma, int tiles, const BatchDesc* bd)
+{
+    switch (per_sm) {
+    case 1: k_shell<N, 1, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, bd); break;
+    case 2: k_shell<N, 2, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, bd); break;
+    case 3: k_shell<N, 3, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, bd); break;
+    default: k_shell<N, 4, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, bd); break;
+    }
+}
+
 cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
 {
     Problem P = P0;
@@ -895,17 +849,12 @@ cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
     std::memset(&map, 0, sizeof(map));
     const int use_tma = encode_tile_map(P, &map) ? 1 : 0;
     const int sms = device_sm_count();
-    const int per_sm = P.shell_minblocks == 1 ? 1 : 2;
+    const int per_sm = std::min(4, std::max(1, P.shell_minblocks));
     const int tiles = shell_tiles(P);
     if (tiles < 0) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
-    if (P.ndim == 3) {
-        if (per_sm == 1) k_shell<3, 1, false><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, nullptr);
-        else k_shell<3, 2, false><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, nullptr);
-    } else {
-        if (per_sm == 1) k_shell<2, 1, false><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, nullptr);
-        else k_shell<2, 2, false><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, nullptr);
-    }
+    if (P.ndim == 3) launch_shell_k<3, false>(per_sm, grid, s, P, map, use_tma, tiles, nullptr);
+    else launch_shell_k<2, false>(per_sm, grid, s, P, map, use_tma, tiles, nullptr);
     return cudaGetLastError();
 }
 
@@ -955,18 +904,13 @@ cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStr
 {
     if (g.npairs <= 0 || g.total_tiles <= 0) return cudaSuccess;
     const int sms = device_sm_count();
-    const int per_sm = shell_minblocks == 1 ? 1 : 2;
+    const int per_sm = std::min(4, std::max(1, shell_minblocks));
     const unsigned grid = (unsigned)std::min<long long>(g.total_tiles, (long long)sms * per_sm);
     Problem dummy{};
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
-    if (g.ndim == 3) {
-        if (per_sm == 1) k_shell<3, 1, true><<<grid, 256, 0, s>>>(dummy, map, 0, g.total_tiles, g.desc);
-        else k_shell<3, 2, true><<<grid, 256, 0, s>>>(dummy, map, 0, g.total_tiles, g.desc);
-    } else {
-        if (per_sm == 1) k_shell<2, 1, true><<<grid, 256, 0, s>>>(dummy, map, 0, g.total_tiles, g.desc);
-        else k_shell<2, 2, true><<<grid, 256, 0, s>>>(dummy, map, 0, g.total_tiles, g.desc);
-    }
+    if (g.ndim == 3) launch_shell_k<3, true>(per_sm, grid, s, dummy, map, 0, g.total_tiles, g.desc);
+    else launch_shell_k<2, true>(per_sm, grid, s, dummy, map, 0, g.total_tiles, g.desc);
     return cudaGetLastError();
 }
 

@@ -91,13 +91,25 @@ def test_plane_128_full():
     assert st["n_eval"] > 1000
 
 
-@pytest.mark.parametrize("blocks", [1, 2])
+@pytest.mark.parametrize("blocks", [1, 2, 3, 4])
 def test_plane_larger_than_one_tile_per_block(blocks):
     # More 32x8 tiles than persistent blocks: every block stages tiles into
     # both of its shared-memory buffers (the second one must stay aligned for
     # the tensor copy).
     p = synth.make_pair_2d(shape=(512, 640), spacing=(1.0, 1.0), seed=13, shift_mm=(0.5, 1.2),
                            scale=1.03)
+    crit = synth.Criteria(0.02, 2.0)
+    got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"shell_blocks_per_sm": blocks})
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
+@pytest.mark.parametrize("blocks", [1, 2, 3, 4])
+def test_volume_every_shell_register_budget(blocks):
+    # 3D, 768 tiles of 32x4x2 voxels: more tiles than persistent blocks at
+    # every budget (the 3- and 4-block variants run with register spills).
+    p = synth.make_pair_3d(shape=(48, 64, 64), spacing=(2.5, 2.0, 2.0), seed=17,
+                           shift_mm=(0.5, -1.0, 1.5), scale=1.02)
     crit = synth.Criteria(0.02, 2.0)
     got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"shell_blocks_per_sm": blocks})
     want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
