@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per queued voxel (0: library default)")
     ap.add_argument("--shell-blocks", type=int, default=0, help="key-0 kernel blocks per SM (1-4)")
+    ap.add_argument("--tail-blocks", type=int, default=0, help="table-walk kernel blocks per SM (1-2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
@@ -307,14 +308,16 @@ def run_ours(args, pair, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     h = g.gamma_create(ref, ev, ndim, shape, spacing, crit)
     tuned = None
-    if args.lanes or args.shell_blocks:
+    if args.lanes or args.shell_blocks or args.tail_blocks:
         if args.lanes:
             g.gamma_set_option(h, "lanes_per_voxel", args.lanes)
         if args.shell_blocks:
             g.gamma_set_option(h, "shell_blocks_per_sm", args.shell_blocks)
+        if args.tail_blocks:
+            g.gamma_set_option(h, "tail_blocks_per_sm", args.tail_blocks)
     else:
-        lanes, blocks, _ = g.gamma_autotune(h, out, stream, reps=3)   # setup, not timed
-        tuned = {"lanes_per_voxel": lanes, "shell_blocks_per_sm": blocks}
+        tuned = g.gamma_autotune(h, out, stream, reps=3)   # setup, not timed
+        tuned.pop("ms")
     g.gamma_set_option(h, "timing", 1)
 
     def barrier():
@@ -587,7 +590,7 @@ def experiment_batch(args):
     vox = sum(p.nvox for p in pairs)
     # batched
     hb = g.gamma_batch_create(descs)
-    lanes, blocks, tune_ms = g.gamma_autotune(hb, reps=2)
+    tuned = g.gamma_autotune(hb, reps=2)
     for _ in range(3):
         g.gamma_batch_run(hb)
     torch.cuda.synchronize()
@@ -638,7 +641,7 @@ def experiment_batch(args):
         "batched_ms": batched_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batched_ms,
         "batched_voxels_per_s": vox / (batched_ms / 1000.0),
         "sequential_voxels_per_s": vox / (seq_ms / 1000.0),
-        "autotune": {"lanes_per_voxel": lanes, "shell_blocks_per_sm": blocks, "ms": tune_ms},
+        "autotune": tuned,
         "max_abs_err_vs_oracle": max(errs), "per_pair_max_abs_err": errs,
         "names": [p.name for p in pairs],
     }), flush=True)

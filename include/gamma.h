@@ -172,6 +172,8 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     and replaying a CUDA graph
  *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell
  *                     kernel's register budget is sized for (default 2)
+ *  "tail_blocks_per_sm"   1 or 2: the same for the table-walk kernel
+ *                     (default 2)
  * Errors: INVALID_ARG (unknown key or value), TABLE_TOO_LARGE, OOM. */
 int gamma_set_option(gamma_handle h, const char *key, int64_t value);
 
@@ -221,14 +223,15 @@ int gamma_batch_pass_rate(gamma_handle h, int pair, double *rate, int64_t *n_eva
 int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
 
 /* Autotuner: times the full run (single or batch handle) for every
- * combination of lanes_per_voxel in {4, 8, 16, 32} and
- * shell_blocks_per_sm in {1, 2, 3, 4} (one warm-up and `reps` timed runs each, CUDA
- * events on `cuda_stream`), keeps the fastest as the handle's options and
- * returns it (any output pointer may be NULL).  gamma_out_dev receives the
+ * combination of lanes_per_voxel in {4, 8, 16, 32}, shell_blocks_per_sm in
+ * {1, 2, 3, 4} and tail_blocks_per_sm in {1, 2} (one warm-up and `reps` timed
+ * runs each, CUDA events on `cuda_stream`), keeps the fastest as the handle's
+ * options and returns it (any output pointer may be NULL).  gamma_out_dev receives the
  * gamma map of a single-pair handle (device, nz*ny*nx floats) and is ignored
  * for a batch handle.  Errors as for the runs. */
 int gamma_autotune(gamma_handle h, float *gamma_out_dev, void *cuda_stream, int reps,
-                   int64_t *lanes_per_voxel, int64_t *shell_blocks_per_sm, float *best_ms);
+                   int64_t *lanes_per_voxel, int64_t *shell_blocks_per_sm,
+                   int64_t *tail_blocks_per_sm, float *best_ms);
 
 /* ---------------------------------------------------------------------------
  * Learned proposal (no counterpart in the paper).  A 375-128-128-4 network

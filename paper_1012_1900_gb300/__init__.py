@@ -104,7 +104,7 @@ def _load():
     lib.gamma_batch_pass_rate.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           i64p, i64p]
     lib.gamma_batch_get_stats.argtypes = [vp, ctypes.c_int, ctypes.POINTER(gamma_stats)]
-    lib.gamma_autotune.argtypes = [vp, vp, vp, ctypes.c_int, i64p, i64p,
+    lib.gamma_autotune.argtypes = [vp, vp, vp, ctypes.c_int, i64p, i64p, i64p,
                                    ctypes.POINTER(ctypes.c_float)]
     lib.gamma_model_create.argtypes = [ctypes.POINTER(vp), ctypes.c_uint64]
     lib.gamma_model_destroy.argtypes = [vp]
@@ -280,14 +280,16 @@ def gamma_batch_get_stats(h: int, pair: int) -> dict:
 
 
 def gamma_autotune(h: int, gamma_out_dev=None, stream=None, reps: int = 3):
-    """Time every (lanes_per_voxel, shell_blocks_per_sm) choice, keep the
-    fastest; returns (lanes_per_voxel, shell_blocks_per_sm, ms)."""
-    lanes, blocks = ctypes.c_int64(), ctypes.c_int64()
+    """Time every (lanes_per_voxel, shell_blocks_per_sm, tail_blocks_per_sm)
+    choice, keep the fastest; returns a dict of the three and the time (ms)."""
+    lanes, blocks, tblocks = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     ms = ctypes.c_float()
     _check(_lib.gamma_autotune(h, _dev_ptr(gamma_out_dev), _stream_ptr(stream), int(reps),
-                               ctypes.byref(lanes), ctypes.byref(blocks), ctypes.byref(ms)),
+                               ctypes.byref(lanes), ctypes.byref(blocks), ctypes.byref(tblocks),
+                               ctypes.byref(ms)),
            "gamma_autotune")
-    return lanes.value, blocks.value, ms.value
+    return {"lanes_per_voxel": lanes.value, "shell_blocks_per_sm": blocks.value,
+            "tail_blocks_per_sm": tblocks.value, "ms": ms.value}
 
 
 # ---- learned proposal ----

@@ -80,7 +80,7 @@ struct gamma_ctx {
     // cell table
     std::vector<TableEntry> table;
     TableEntry* table_dev = nullptr;
-    int t1 = 0;
+    float key0_far2[8] = {};
     double r_cover = 0;
     int64_t table_cap = 1 << 17;
     // scratch
@@ -96,6 +96,7 @@ struct gamma_ctx {
     int sort_tail = 1;
     int timing = 0;
     int shell_minblocks = 2;
+    int tail_minblocks = 2;
     gamma_model model = nullptr;      // attached proposal network (may be null)
     bool own_model = false;
     // per-phase events: 0 start, 1 after h2d, 2 after prepare, 3 after shell,
@@ -112,7 +113,8 @@ namespace {
 // Algorithm A1 steps 2-3 for the cells of the Freudenthal triangulation: every
 // lower-corner offset c whose cell can hold faces for some voxel, keyed by the
 // distance from the reference voxel to the closed cell box [c, c + 1] divided
-// by the DTA, sorted ascending (ties by z, y, x), cut to `cap` entries.
+// by the DTA (for the key-0 cells: to their faces off the voxel), sorted
+// ascending (ties by z, y, x), cut to `cap` entries.
 int build_table(gamma_ctx* h)
 {
     const double dta = h->crit.dta_mm;
@@ -140,6 +142,14 @@ int build_table(gamma_ctx* h)
         if (lo[a] < -511) { lo[a] = -511; packing_limited = true; }
         if (hi[a] > 511) { hi[a] = 511; packing_limited = true; }
     }
+    double far[8];
+    gk::key0_far(hn, nd, far);
+    for (int s = 0; s < 8; ++s) {
+        const double f2 = far[s] * far[s];
+        float r = (float)f2;
+        if ((double)r > f2) r = std::nextafterf(r, -INFINITY);
+        h->key0_far2[s] = r;
+    }
     struct Tmp { double key; int x, y, z; };
     std::vector<Tmp> all;
     try {
@@ -149,6 +159,7 @@ int build_table(gamma_ctx* h)
                     double ax = axis_gap((int)x) * hn[0], ay = axis_gap((int)y) * hn[1];
                     double az = nd == 3 ? axis_gap((int)z) * hn[2] : 0.0;
                     double key = std::sqrt(ax * ax + ay * ay + az * az);
+                    if (key == 0.0) key = far[(x & 1) | ((y & 1) << 1) | ((z & 1) << 2)];
                     if (key < R) all.push_back({key, (int)x, (int)y, (int)z});
                 }
     } catch (const std::bad_alloc&) {
@@ -172,14 +183,10 @@ int build_table(gamma_ctx* h)
         cover = std::min(cover, all[keep].key);
     }
     h->table.resize(keep);
-    int t1 = 0;
     for (size_t i = 0; i < keep; ++i) {
         h->table[i].off = gk::pack10(all[i].x, all[i].y, all[i].z);
         h->table[i].key = round_down(all[i].key);
-        if (all[i].key == 0.0) ++t1;
     }
-    if (keep > 0 && t1 != (1 << nd)) return GAMMA_ERR_TABLE_TOO_LARGE;  // cannot happen for n >= 2
-    h->t1 = t1;
     h->r_cover = cover;
     if (h->table_dev) { cudaFree(h->table_dev); h->table_dev = nullptr; }
     if (keep) {
@@ -227,7 +234,7 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.stats = h->stats;
     P.table = h->table_dev;
     P.ntable = (int)h->table.size();
-    P.t1 = h->t1;
+    for (int s = 0; s < 8; ++s) P.key0_far2[s] = h->key0_far2[s];
     P.r_cover = std::isinf(h->r_cover) ? INFINITY : round_down(h->r_cover);
     P.tail_cap = h->tail_cap;
     P.ctr = h->ctr;
@@ -349,7 +356,6 @@ int batch_upload(gamma_ctx* h)
             c->sort_tail = 1;
             c->shell_minblocks = h->shell_minblocks;
             probs[k] = make_problem(c, b->outs[mem[k]]);
-            gk::fill_shell_constants(probs[k]);
             std::memset(&maps[k], 0, sizeof(CUtensorMap));
             use[k] = gk::encode_tile_map(probs[k], &maps[k]) ? 1 : 0;
             const int tiles = gk::shell_tiles(probs[k]);
@@ -405,7 +411,7 @@ int batch_enqueue(gamma_ctx* h, cudaStream_t s)
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     for (auto& G : b->grp) CK(gk::launch_batch_order(G.host, s));
     if (tm) CK(cudaEventRecord(h->tev[4], s));
-    for (auto& G : b->grp) CK(gk::launch_batch_tail(G.host, h->lanes, s));
+    for (auto& G : b->grp) CK(gk::launch_batch_tail(G.host, h->lanes, h->tail_minblocks, s));
     if (tm) {
         CK(cudaEventRecord(h->tev[5], s));
         CK(cudaEventRecord(h->tev[6], s));
@@ -521,7 +527,7 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     CK(gk::launch_order_tail(P, s));
     if (tm) CK(cudaEventRecord(h->tev[4], s));
-    CK(gk::launch_tail(P, h->lanes, s));
+    CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, s));
     if (tm) {
         CK(cudaEventRecord(h->tev[5], s));
         if (!h->ev_h2d) CK(cudaEventRecord(h->tev[6], s));
@@ -674,6 +680,11 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         h->stats = (int)value;
         return GAMMA_OK;
     }
+    if (!std::strcmp(key, "tail_blocks_per_sm")) {
+        if (value < 1 || value > 2) return GAMMA_ERR_INVALID_ARG;
+        h->tail_minblocks = (int)value;
+        return GAMMA_OK;
+    }
     if (!std::strcmp(key, "shell_blocks_per_sm")) {
         if (value < 1 || value > 4) return GAMMA_ERR_INVALID_ARG;
         h->shell_minblocks = (int)value;
@@ -813,7 +824,8 @@ int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats* out)
 }
 
 int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int reps,
-                   int64_t* lanes_per_voxel, int64_t* shell_blocks_per_sm, float* best_ms)
+                   int64_t* lanes_per_voxel, int64_t* shell_blocks_per_sm,
+                   int64_t* tail_blocks_per_sm, float* best_ms)
 {
     if (!h || reps <= 0 || (!h->batch && !gamma_out_dev)) return GAMMA_ERR_INVALID_ARG;
     DeviceGuard dg(h->device);
@@ -823,33 +835,37 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int lanes[4] = {4, 8, 16, 32};
-    int best_l = h->lanes, best_b = h->shell_minblocks;
+    int best_l = h->lanes, best_b = h->shell_minblocks, best_t = h->tail_minblocks;
     float best = INFINITY;
     int rc = GAMMA_OK;
     auto run = [&]() { return h->batch ? gamma_batch_run(h, s) : gamma_run(h, gamma_out_dev, s); };
     for (int li = 0; li < 4 && rc == GAMMA_OK; ++li)
-        for (int bl = 1; bl <= 4 && rc == GAMMA_OK; ++bl) {
-            h->lanes = lanes[li];
-            h->shell_minblocks = bl;
-            if (h->batch) h->batch->dirty = true;
-            if ((rc = run())) break;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && rc == GAMMA_OK; ++r) rc = run();
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GAMMA_ERR_CUDA; break; }
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= reps;
-            if (ms < best) { best = ms; best_l = lanes[li]; best_b = bl; }
-        }
+        for (int bl = 1; bl <= 4 && rc == GAMMA_OK; ++bl)
+            for (int tb = 1; tb <= 2 && rc == GAMMA_OK; ++tb) {
+                h->lanes = lanes[li];
+                h->shell_minblocks = bl;
+                h->tail_minblocks = tb;
+                if (h->batch) h->batch->dirty = true;
+                if ((rc = run())) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && rc == GAMMA_OK; ++r) rc = run();
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GAMMA_ERR_CUDA; break; }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+                if (ms < best) { best = ms; best_l = lanes[li]; best_b = bl; best_t = tb; }
+            }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->lanes = best_l;
     h->shell_minblocks = best_b;
+    h->tail_minblocks = best_t;
     if (h->batch) h->batch->dirty = true;
     if (rc) return rc;
     if (lanes_per_voxel) *lanes_per_voxel = best_l;
     if (shell_blocks_per_sm) *shell_blocks_per_sm = best_b;
+    if (tail_blocks_per_sm) *tail_blocks_per_sm = best_t;
     if (best_ms) *best_ms = best;
     return GAMMA_OK;
 }

@@ -22,9 +22,14 @@ enum : uint32_t {
 
 // One entry of the radially sorted cell table (Algorithm A1 steps 2-3):
 // the cell's lower-corner offset relative to the reference voxel, packed as
-// three signed 10-bit fields (x | y << 10 | z << 20), and the key: the
-// distance from the reference voxel to the cell box, divided by the DTA,
-// rounded down to float so that it stays a lower bound.
+// three signed 10-bit fields (x | y << 10 | z << 20), and the key: a lower
+// bound, divided by the DTA and rounded down to float, on the spatial
+// distance from the voxel to every face of the cell the table walk still has
+// to evaluate.  That is the distance to the cell box, except for the cells
+// whose box contains the voxel (key-0 cells): their faces through the voxel
+// are done before the walk, so their key is the distance to their other
+// faces, and the cell whose corner is the voxel (all its faces contain it) is
+// not in the table.
 struct TableEntry {
     uint32_t off;
     float key;
@@ -76,13 +81,6 @@ __host__ __device__ inline float fdec(unsigned int e)
     return c.f;
 }
 
-// Constant of the 2^n key-0 cells around a voxel (lower-corner offsets
-// c in {-1, 0}^n), computed on the host by the shell launcher.
-struct ShellConst {
-    float far2;   // squared spatial distance from the voxel to the nearest face
-                  // of these cells that does not contain it (rounded down)
-};
-
 // Everything a launch needs about one dose pair.
 struct Problem {
     const float* ref;
@@ -102,7 +100,6 @@ struct Problem {
     int stats;               // count cells in the tail search
     const TableEntry* table;
     int ntable;
-    int t1;                  // first table index past the key-0 shell
     float r_cover;           // every cell with key < r_cover is in the table
     unsigned int tail_cap;
     Counters* ctr;
@@ -111,7 +108,9 @@ struct Problem {
     unsigned int* tail_sorted;   // tail voxels, most expensive bucket first
     int sort_tail;               // 0: keep discovery order (ablation)
     int shell_minblocks;         // k_shell register budget: resident blocks per SM, 1..4
-    ShellConst shell;            // filled by launch_shell
+    // squared spatial distance from the voxel to the faces of key-0 cell S
+    // (lower corner at -S) that do not contain it, rounded down; +inf for S = 0
+    float key0_far2[8];
 };
 
 // Device-side description of the pairs of one batched launch group (pairs of
@@ -140,11 +139,13 @@ struct BatchGroup {
 cudaError_t launch_prepare(const Problem& P, cudaStream_t s);
 cudaError_t launch_shell(const Problem& P, cudaStream_t s);
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
-cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, cudaStream_t s);
+cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblocks, cudaStream_t s);
 int device_sm_count();
 
 // Host-side constants a Problem needs before it is uploaded for a batch.
-void fill_shell_constants(Problem& P);
+// Spatial distance (DTA units, rounded down) from the voxel to the faces of
+// key-0 cell S that do not contain it, for S = 1 .. 2^nd - 1; far[0] = +inf.
+void key0_far(const double hn[3], int nd, double far[8]);
 // Tile-load map for a Problem; false when TMA cannot be used for it.
 bool encode_tile_map(const Problem& P, CUtensorMap* map);
 int shell_tiles(const Problem& P);
@@ -161,6 +162,7 @@ cudaError_t launch_labels(const Problem& P, const float* gmap, const unsigned* v
 cudaError_t launch_batch_prepare(const BatchGroup& g, cudaStream_t s);
 cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStream_t s);
 cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s);
-cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, cudaStream_t s);
+cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, int tail_minblocks,
+                              cudaStream_t s);
 
 }  // namespace gk

@@ -248,10 +248,10 @@ __global__ void __launch_bounds__(256, MINB)
         const bool use_tma = pair_tma(pr) != 0;
         const float dnorm = resolve_dnorm(P);
         const float thr = P.cutoff_frac * dnorm;
-        const float k1 = P.t1 < P.ntable ? P.table[P.t1].key : kInf;
-        const float rc2 = P.r_cover * P.r_cover;
-        const float qlim = fminf(P.shell.far2, k1 * k1);
-        const bool table_ends = P.t1 >= P.ntable;
+        // every face not through the voxel is at spatial distance >= the
+        // first table key, or >= the cover radius when the table was cut
+        const float k0 = P.ntable > 0 ? P.table[0].key : kInf;
+        const float qlim = fminf(k0 * k0, P.r_cover * P.r_cover);
         int x0, y0, z0;
         tile_origin(P.nx, P.ny, lt, x0, y0, z0);
         float* tl = tile[buf];
@@ -305,12 +305,10 @@ __global__ void __launch_bounds__(256, MINB)
         }
 
         // ---- finish or queue ----
-        // The other faces of the key-0 cells are at squared spatial distance
-        // >= far2 and every other cell at >= k1^2, so gamma^2 <= both is final.
         bool tail = false;
         int bucket = 0;
         if (act) {
-            tail = (best > qlim) || (table_ends && best > rc2);
+            tail = best > qlim;
             if (tail) {
                 P.out[v] = best;                       // gamma^2, finished by k_tail
                 const float gk_ = sqrtf(best);
@@ -441,10 +439,35 @@ struct TailStats {
     unsigned long long visited = 0, pruned = 0, keyed = 0;
 };
 
+// Every face of the cell with lower corner (x+cx, y+cy, z+cz) as squared
+// gamma, with the FP64 redo when a face's Gram matrix is near singular.  Out
+// of line: the table walk and the box scan share one copy, and the walk keeps
+// its own registers few.
+template <int N>
+__device__ __noinline__ float cell_all_faces(const Problem& P, float q0, float q1, float q2,
+                                             float q3, float q4, float q5, float q6, float q7,
+                                             uint32_t ok, int cx, int cy, int cz, long long p,
+                                             float dr, float dnorm)
+{
+    const float q[8] = {q0, q1, q2, q3, q4, q5, q6, q7};
+    CellGeom<float> g;
+    cell_geom<N, float>(cx, cy, cz, P.mt, g);
+    bool ill = false;
+    float cb = cell_min_d2<N, float>(q, ok, g, P.mt, ill_dmax(P), kInf, ill);
+    if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
+    if (ill) {
+        const double drd = dr;
+        const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
+        const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+        cb = cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd, P.mtd, &P.ctr->fp64_cells);
+    }
+    return cb;
+}
+
 template <int N>
 __device__ __forceinline__ float visit_cell(const Problem& P, int x, int y, int z, int cx, int cy,
-                                            int cz, float key, float dr, float inv, double drd,
-                                            double invd, float best, TailStats& st)
+                                            int cz, float key, float dr, float inv, float dnorm,
+                                            float best, TailStats& st)
 {
     const int px = x + cx, py = y + cy, pz = z + cz;
     if ((unsigned)px >= (unsigned)P.nx || (unsigned)py >= (unsigned)P.ny ||
@@ -478,13 +501,8 @@ __device__ __forceinline__ float visit_cell(const Problem& P, int x, int y, int 
         return best;
     }
     if (P.stats) ++st.visited;
-    CellGeom<float> g;
-    cell_geom<N, float>(cx, cy, cz, P.mt, g);
-    bool ill = false;
-    float cb = cell_min_d2<N, float>(q, ok, g, P.mt, ill_dmax(P), kInf, ill);
-    if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
-    if (ill)
-        cb = cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd, P.mtd, &P.ctr->fp64_cells);
+    const float cb = cell_all_faces<N>(P, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], ok, cx, cy,
+                                       cz, p, dr, dnorm);
     return fminf(best, cb);
 }
 
@@ -496,8 +514,8 @@ __device__ __forceinline__ float group_min(float v, unsigned gmask)
     return v;
 }
 
-template <int N, int G, bool BATCH>
-__global__ void __launch_bounds__(256)
+template <int N, int G, int MINB, bool BATCH>
+__global__ void __launch_bounds__(256, MINB)
     k_tail(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd)
 {
     const int lane = threadIdx.x & 31;
@@ -542,10 +560,8 @@ __global__ void __launch_bounds__(256)
         const float dr = __ldg(P.ref + v);
         const float dD = P.dd_frac * (P.local ? dr : dnorm);
         const float inv = 1.0f / dD;
-        const double drd = dr;
-        const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
         float best = P.out[v];                       // gamma^2 over the faces through v
-        int t = 0;                                   // from the key-0 cells' other faces on
+        int t = 0;
         while (t < P.ntable) {
             const int idx = t + gl;
             float key = kInf;
@@ -561,7 +577,7 @@ __global__ void __launch_bounds__(256)
             if (key * key < best) {
                 if (P.stats) ++st.keyed;
                 cb = visit_cell<N>(P, x, y, z, unpack10(off, 0), unpack10(off, 10),
-                                   unpack10(off, 20), key, dr, inv, drd, invd, best, st);
+                                   unpack10(off, 20), key, dr, inv, dnorm, best, st);
             }
             best = group_min<G>(cb, gmask);
             t += G;
@@ -589,9 +605,11 @@ __global__ void __launch_bounds__(256)
                 const float axd = (float)max(max(cx, -cx - 1), 0) * P.hn[0];
                 const float ayd = (float)max(max(cy, -cy - 1), 0) * P.hn[1];
                 const float azd = N == 3 ? (float)max(max(cz, -cz - 1), 0) * P.hn[2] : 0.f;
-                const float k2 = axd * axd + ayd * ayd + azd * azd;
+                float k2 = axd * axd + ayd * ayd + azd * azd;
+                if (k2 == 0.f)       // key-0 cell: only its faces off the voxel remain
+                    k2 = P.key0_far2[(cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2)];
                 if (k2 < lim || k2 >= lb) continue;
-                lb = visit_cell<N>(P, x, y, z, cx, cy, cz, sqrtf(k2), dr, inv, drd, invd, lb, st);
+                lb = visit_cell<N>(P, x, y, z, cx, cy, cz, sqrtf(k2), dr, inv, dnorm, lb, st);
             }
             best = group_min<G>(lb, gmask);
         }
@@ -723,22 +741,15 @@ static double simplex_dist_host(const double (*W)[3], int nv)
     return best;
 }
 
-// Constant of the key-0 cells: the smallest spatial distance from the voxel
-// to a face of these cells that does not contain it.
-static void shell_constants(const Problem& P, ShellConst& sc);
-
-void fill_shell_constants(Problem& P) { shell_constants(P, P.shell); }
-
-static void shell_constants(const Problem& P, ShellConst& sc)
+void key0_far(const double hn_in[3], int nd, double far[8])
 {
-    const int N = P.ndim;
-    // every owned face is a chain 0 = u0 < u1 < ... < um of axis masks
-    const double hn[3] = {P.hn[0], P.hn[1], N == 3 ? P.hn[2] : 0.0};
-    double far = INFINITY;
-    const int full = (1 << N) - 1;
-    for (int s = 0; s < (1 << N); ++s) {
+    const double hn[3] = {hn_in[0], hn_in[1], nd == 3 ? hn_in[2] : 0.0};
+    const int full = (1 << nd) - 1;
+    for (int s = 0; s < 8; ++s) far[s] = INFINITY;
+    for (int s = 1; s <= full; ++s) {
         const int c[3] = {-(s & 1), -((s >> 1) & 1), -((s >> 2) & 1)};
-        // enumerate chains by their sequence of masks (up to N increments)
+        double f = INFINITY;
+        // every owned face is a chain 0 = u0 < u1 < ... < um of axis masks
         for (int u1 = 1; u1 <= full; ++u1)
             for (int u2 = 0; u2 <= full; ++u2)
                 for (int u3 = 0; u3 <= full; ++u3) {
@@ -760,17 +771,14 @@ static void shell_constants(const Problem& P, ShellConst& sc)
                     double W[4][3];
                     for (int i = 0; i <= m; ++i)
                         for (int a = 0; a < 3; ++a)
-                            W[i][a] = (a < N) ? (c[a] + ((chain[i] >> a) & 1)) * hn[a] : 0.0;
-                    far = fmin(far, simplex_dist_host(W, m + 1));
+                            W[i][a] = (a < nd) ? (c[a] + ((chain[i] >> a) & 1)) * hn[a] : 0.0;
+                    f = fmin(f, simplex_dist_host(W, m + 1));
                 }
-        if (s != 0) {           // the cell's own corner vertex, when it is not the voxel
-            double W[1][3];
-            for (int a = 0; a < 3; ++a) W[0][a] = (a < N) ? c[a] * hn[a] : 0.0;
-            far = fmin(far, simplex_dist_host(W, 1));
-        }
+        double W[1][3];                       // the cell's own corner vertex
+        for (int a = 0; a < 3; ++a) W[0][a] = (a < nd) ? c[a] * hn[a] : 0.0;
+        f = fmin(f, simplex_dist_host(W, 1));
+        far[s] = f * (1.0 - 1e-6);            // absorbs the rounding of the projection
     }
-    float f = (float)(far * far * (1.0 - 1e-6));
-    sc.far2 = f;
 }
 
 bool encode_tile_map(const Problem& P, CUtensorMap* map)
@@ -843,8 +851,7 @@ static void launch_shell_k(int per_sm, unsigned grid, cudaStream_t s, const Prob
 
 cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
 {
-    Problem P = P0;
-    shell_constants(P, P.shell);
+    const Problem& P = P0;
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     const int use_tma = encode_tile_map(P, &map) ? 1 : 0;
@@ -866,23 +873,33 @@ cudaError_t launch_order_tail(const Problem& P, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int N, bool BATCH>
-static void launch_tail_n(const Problem& P, const BatchDesc* bd, int G, int grid, cudaStream_t s)
+template <int N, int MINB, bool BATCH>
+static void launch_tail_g(const Problem& P, const BatchDesc* bd, int G, int grid, cudaStream_t s)
 {
     switch (G) {
-    case 4: k_tail<N, 4, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
-    case 8: k_tail<N, 8, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
-    case 16: k_tail<N, 16, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
-    default: k_tail<N, 32, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
+    case 4: k_tail<N, 4, MINB, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
+    case 8: k_tail<N, 8, MINB, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
+    case 16: k_tail<N, 16, MINB, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
+    default: k_tail<N, 32, MINB, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
     }
 }
 
-cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, cudaStream_t s)
+// k_tail with G lanes per queued voxel and its register budget sized for
+// `per_sm` resident blocks (1 or 2).
+template <int N, bool BATCH>
+static void launch_tail_n(const Problem& P, const BatchDesc* bd, int G, int per_sm, int grid,
+                          cudaStream_t s)
+{
+    if (per_sm >= 2) launch_tail_g<N, 2, BATCH>(P, bd, G, grid, s);
+    else launch_tail_g<N, 1, BATCH>(P, bd, G, grid, s);
+}
+
+cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblocks, cudaStream_t s)
 {
     const int sms = device_sm_count();
     const int grid = sms * 8;      // persistent: enough warps to fill every SM
-    if (P.ndim == 3) launch_tail_n<3, false>(P, nullptr, lanes_per_voxel, grid, s);
-    else launch_tail_n<2, false>(P, nullptr, lanes_per_voxel, grid, s);
+    if (P.ndim == 3) launch_tail_n<3, false>(P, nullptr, lanes_per_voxel, tail_minblocks, grid, s);
+    else launch_tail_n<2, false>(P, nullptr, lanes_per_voxel, tail_minblocks, grid, s);
     return cudaGetLastError();
 }
 
@@ -924,13 +941,14 @@ cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, cudaStream_t s)
+cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, int tail_minblocks,
+                              cudaStream_t s)
 {
     if (g.npairs <= 0) return cudaSuccess;
     const int sms = device_sm_count();
     Problem dummy{};
-    if (g.ndim == 3) launch_tail_n<3, true>(dummy, g.desc, lanes_per_voxel, sms * 8, s);
-    else launch_tail_n<2, true>(dummy, g.desc, lanes_per_voxel, sms * 8, s);
+    if (g.ndim == 3) launch_tail_n<3, true>(dummy, g.desc, lanes_per_voxel, tail_minblocks, sms * 8, s);
+    else launch_tail_n<2, true>(dummy, g.desc, lanes_per_voxel, tail_minblocks, sms * 8, s);
     return cudaGetLastError();
 }
 

@@ -156,10 +156,23 @@ __global__ void __launch_bounds__(128) k_labels(const __grid_constant__ Problem 
         const float inv = 1.0f / (P.dd_frac * (P.local ? dr : dnorm));
         const float lim = gs * (1.f + 1e-5f) + 1e-6f;
         float best = kInf, foot[3] = {0.f, 0.f, 0.f}, fv[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < P.ntable; ++k) {
-            const TableEntry e = P.table[k];
-            if (e.key > lim) break;
-            const int cx = unpack10(e.off, 0), cy = unpack10(e.off, 10), cz = unpack10(e.off, 20);
+        // the 2^N cells whose box contains the voxel first (the table keys
+        // them by their faces off the voxel only), then the table
+        for (int k = -(1 << N); k < P.ntable; ++k) {
+            int cx, cy, cz;
+            if (k < 0) {
+                const int s = k + (1 << N);
+                cx = -(s & 1);
+                cy = -((s >> 1) & 1);
+                cz = N == 3 ? -((s >> 2) & 1) : 0;
+            } else {
+                const TableEntry e = P.table[k];
+                if (e.key > lim) break;
+                cx = unpack10(e.off, 0);
+                cy = unpack10(e.off, 10);
+                cz = unpack10(e.off, 20);
+                if (cx >= -1 && cx <= 0 && cy >= -1 && cy <= 0 && cz >= -1 && cz <= 0) continue;
+            }
             float q[8];
             uint32_t ok;
             if (!load_cell<N>(P, x, y, z, cx, cy, cz, dr, inv, q, ok)) continue;
@@ -564,7 +577,7 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
             }
             sd2 = fminf(sd2, __shfl_xor_sync(0xffffffffu, sd2, 1));
             if (half == 0 && v != 0xffffffffu) {
-                const float cur = P.out[v];                   // gamma^2 after the key-0 cells
+                const float cur = P.out[v];                   // gamma^2 after the faces through v
                 const float nb = fminf(cur, sd2);
                 atomicAdd(&S.nseed, 1u);
                 if (nb < cur) {
@@ -573,12 +586,12 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
                 }
                 // bucket from the (possibly) tighter bound
                 const float gk_ = sqrtf(nb);
-                int lo = P.t1, hi = P.ntable;
+                int lo = 0, hi = P.ntable;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
                 }
-                const int cost = lo - P.t1;
+                const int cost = lo;
                 const int bucket = cost <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)cost)));
                 P.tail_bucket[S.item[r]] = (unsigned char)bucket;
                 atomicAdd(&S.hist[bucket], 1u);

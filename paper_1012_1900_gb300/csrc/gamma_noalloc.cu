@@ -72,11 +72,16 @@ float round_down_f(double x)
 
 double gap1(int i) { return i >= 0 ? (double)i : (double)(-i - 1); }
 
-// The radially sorted cell table (Algorithm A1 steps 2-3) in static storage.
-// Returns the entry count; *t1 gets the number of key-0 cells, *cover the
-// radius below which the table is complete.
-int build_static_table(int nd, const int64_t n[3], const double hn[3], int* t1, double* cover)
+// The radially sorted cell table (Algorithm A1 steps 2-3) in static storage,
+// keyed as the allocating handle's table is (key-0 cells by the distance to
+// their faces off the voxel).  Returns the entry count; *cover gets the radius
+// below which the table is complete, far2 the squared key-0 distances.
+int build_static_table(int nd, const int64_t n[3], const double hn[3], double* cover,
+                       float far2[8])
 {
+    double far[8];
+    gk::key0_far(hn, nd, far);
+    for (int s = 0; s < 8; ++s) far2[s] = round_down_f(far[s] * far[s]);
     double cellvol = hn[0] * hn[1] * (nd == 3 ? hn[2] : 1.0);
     double R = nd == 3 ? std::cbrt(1.5 * kMaxTable * cellvol * 3.0 / (4.0 * M_PI))
                        : std::sqrt(1.5 * kMaxTable * cellvol / M_PI);
@@ -100,7 +105,8 @@ int build_static_table(int nd, const int64_t n[3], const double hn[3], int* t1, 
                 for (int64_t x = lo[0]; x <= hi[0]; ++x) {
                     const double ax = gap1((int)x) * hn[0], ay = gap1((int)y) * hn[1];
                     const double az = nd == 3 ? gap1((int)z) * hn[2] : 0.0;
-                    const double key = std::sqrt(ax * ax + ay * ay + az * az);
+                    double key = std::sqrt(ax * ax + ay * ay + az * az);
+                    if (key == 0.0) key = far[(x & 1) | ((y & 1) << 1) | ((z & 1) << 2)];
                     if (!(key < R)) continue;
                     if (cnt == kMaxEnum) { full = true; break; }
                     g_enum[cnt++] = {key, (int)x, (int)y, (int)z};
@@ -123,13 +129,10 @@ int build_static_table(int nd, const int64_t n[3], const double hn[3], int* t1, 
         cov = std::min(cov, g_enum[kMaxTable].key);
         cnt = kMaxTable;
     }
-    int zeros = 0;
     for (int i = 0; i < cnt; ++i) {
         g_table_host[i].off = gk::pack10(g_enum[i].x, g_enum[i].y, g_enum[i].z);
         g_table_host[i].key = round_down_f(g_enum[i].key);
-        if (g_enum[i].key == 0.0) ++zeros;
     }
-    *t1 = zeros;
     *cover = cov;
     return cnt;
 }
@@ -173,10 +176,9 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
     const double h[3] = {spacing_mm[2], spacing_mm[1], ndim == 3 ? spacing_mm[0] : 1.0};
     const double hn[3] = {h[0] / dta, h[1] / dta, h[2] / dta};
     const int64_t n[3] = {nx, ny, nz};
-    int t1 = 0;
     double cover = 0;
-    const int ntable = build_static_table(ndim, n, hn, &t1, &cover);
-    if (ntable > 0 && t1 != (1 << ndim)) return GAMMA_ERR_TABLE_TOO_LARGE;
+    float far2[8];
+    const int ntable = build_static_table(ndim, n, hn, &cover, far2);
 
     gk::Problem P{};
     P.ref = ref_dev;
@@ -209,7 +211,7 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
     P.stats = 0;
     P.table = (const gk::TableEntry*)(base + kOffTable);
     P.ntable = ntable;
-    P.t1 = t1;
+    for (int s = 0; s < 8; ++s) P.key0_far2[s] = far2[s];
     P.r_cover = std::isinf(cover) ? INFINITY : round_down_f(cover);
     P.tail_cap = (unsigned)kMaxVoxels;
     P.ctr = (gk::Counters*)(base + kOffCounters);
@@ -227,7 +229,7 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
         return GAMMA_ERR_CUDA;
     if (gk::launch_prepare(P, s) != cudaSuccess) return GAMMA_ERR_CUDA;
     if (gk::launch_shell(P, s) != cudaSuccess) return GAMMA_ERR_CUDA;
-    if (gk::launch_tail(P, 8, s) != cudaSuccess) return GAMMA_ERR_CUDA;
+    if (gk::launch_tail(P, 8, 2, s) != cudaSuccess) return GAMMA_ERR_CUDA;
 
     if (n_eval || n_pass) {
         gk::Counters c;

@@ -148,12 +148,13 @@ def test_volume_ragged_anisotropic():
 
 
 @pytest.mark.parametrize("lanes", [4, 8, 16, 32])
-@pytest.mark.parametrize("sort_tail", [0, 1])
-def test_launch_shapes_agree(lanes, sort_tail):
+@pytest.mark.parametrize("sort_tail,tail_blocks", [(0, 1), (1, 2), (1, 1)])
+def test_launch_shapes_agree(lanes, sort_tail, tail_blocks):
     p = synth.workload("imrt_small")
     crit = synth.Criteria(0.01, 1.0, local=True)
     got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit,
-                               {"lanes_per_voxel": lanes, "sort_tail": sort_tail})
+                               {"lanes_per_voxel": lanes, "sort_tail": sort_tail,
+                                "tail_blocks_per_sm": tail_blocks})
     want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
     assert_parity(got, want, counts)
 
