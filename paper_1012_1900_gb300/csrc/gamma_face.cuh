@@ -196,14 +196,17 @@ struct FaceList<2> {
 
 template <>
 struct FaceList<3> {
+    // depth-first over the chain tree 0 -> u1 -> u2 -> u3, so that the
+    // prefix terms of a chain are consumed by its extensions right away
     using type = std::tuple<
-        Face<1, 1, 0, 0>, Face<1, 2, 0, 0>, Face<1, 3, 0, 0>, Face<1, 4, 0, 0>,
-        Face<1, 5, 0, 0>, Face<1, 6, 0, 0>, Face<1, 7, 0, 0>,
-        Face<2, 1, 3, 0>, Face<2, 2, 3, 0>, Face<2, 1, 5, 0>, Face<2, 4, 5, 0>,
-        Face<2, 2, 6, 0>, Face<2, 4, 6, 0>, Face<2, 1, 7, 0>, Face<2, 2, 7, 0>,
-        Face<2, 4, 7, 0>, Face<2, 3, 7, 0>, Face<2, 5, 7, 0>, Face<2, 6, 7, 0>,
-        Face<3, 1, 3, 7>, Face<3, 2, 3, 7>, Face<3, 1, 5, 7>, Face<3, 4, 5, 7>,
-        Face<3, 2, 6, 7>, Face<3, 4, 6, 7>>;
+        Face<1, 1, 0, 0>, Face<2, 1, 3, 0>, Face<3, 1, 3, 7>, Face<2, 1, 5, 0>, Face<3, 1, 5, 7>,
+        Face<2, 1, 7, 0>,
+        Face<1, 2, 0, 0>, Face<2, 2, 3, 0>, Face<3, 2, 3, 7>, Face<2, 2, 6, 0>, Face<3, 2, 6, 7>,
+        Face<2, 2, 7, 0>,
+        Face<1, 4, 0, 0>, Face<2, 4, 5, 0>, Face<3, 4, 5, 7>, Face<2, 4, 6, 0>, Face<3, 4, 6, 7>,
+        Face<2, 4, 7, 0>,
+        Face<1, 3, 0, 0>, Face<2, 3, 7, 0>, Face<1, 5, 0, 0>, Face<2, 5, 7, 0>,
+        Face<1, 6, 0, 0>, Face<2, 6, 7, 0>, Face<1, 7, 0, 0>>;
 };
 
 // Number of owned faces per cell (including the vertex).
