@@ -415,11 +415,11 @@ def run_ours(args, pair, rank, world, local_rank):
         peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         f = FLOP_PER_CELL[ndim]
 
-        def rate(cells, ms):
+        def tflops(cells, ms):
             return cells * f / (ms / 1000.0) / 1e12 if ms > 0 else 0.0
 
         t_search = mean_ph["shell_ms"] + mean_ph["tail_ms"]
-        achieved = rate(shell_cells + tail_cells, t_search)
+        achieved = tflops(shell_cells + tail_cells, t_search)
         traffic = [recorded_traffic(k, args.workload) for k in ("k_shell", "k_tail")]
         roofline = {"bound": "alu", "kernel": "k_shell+k_tail", "achieved": achieved,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
@@ -429,10 +429,10 @@ def run_ours(args, pair, rank, world, local_rank):
                     "work": f"{shell_cells + tail_cells} cells x {f} FLOP",
                     "per_kernel": {
                         "k_shell": {"ms": mean_ph["shell_ms"], "cells": shell_cells,
-                                    "achieved": rate(shell_cells, mean_ph["shell_ms"]),
+                                    "achieved": tflops(shell_cells, mean_ph["shell_ms"]),
                                     "traffic": traffic[0]},
                         "k_tail": {"ms": mean_ph["tail_ms"], "cells": tail_cells,
-                                   "achieved": rate(tail_cells, mean_ph["tail_ms"]),
+                                   "achieved": tflops(tail_cells, mean_ph["tail_ms"]),
                                    "traffic": traffic[1]}}}
 
     cpu = None
