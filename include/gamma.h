@@ -259,6 +259,14 @@ int gamma_model_set_params(gamma_model m, const float *host, int64_t n);
 /* Forward a batch: X_bf16_dev is M x 384 bfloat16 (device), Y_dev M x 4 float. */
 int gamma_model_forward(gamma_model m, const void *X_bf16_dev, int64_t M, float *Y_dev,
                         void *cuda_stream);
+/* Inference with the kernel the search uses: the three layers on the
+ * fifth-generation tensor cores (tcgen05.mma, BF16 operands, FP32
+ * accumulation in tensor memory), 128 rows per tile.  X_bf16_dev is M x 384
+ * bfloat16 (device, 16-byte aligned, row-major), Y_dev M x 4 float (device).
+ * Synchronises the stream.  Errors: INVALID_ARG, CUDA, TIMEOUT (a bounded
+ * wait for the tensor cores gave up). */
+int gamma_model_infer(gamma_model m, const void *X_bf16_dev, int64_t M, float *Y_dev,
+                      void *cuda_stream);
 /* Gradients of the mean Huber loss (delta 1) against targets T_dev (M x 4
  * float, rows with a NaN last column are ignored); loss_out optional (host). */
 int gamma_model_backward(gamma_model m, const void *X_bf16_dev, const float *T_dev, int64_t M,

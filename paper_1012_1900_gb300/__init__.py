@@ -21,7 +21,7 @@ __all__ = [
     "gamma_run_noalloc", "gamma_batch_create", "gamma_batch_run", "gamma_batch_pass_rate",
     "gamma_batch_get_stats", "gamma_autotune", "gamma_pair_desc", "gamma_destroy",
     "gamma_model_create", "gamma_model_destroy", "gamma_model_num_params", "gamma_model_get_params",
-    "gamma_model_set_params", "gamma_model_forward", "gamma_model_backward",
+    "gamma_model_set_params", "gamma_model_forward", "gamma_model_infer", "gamma_model_backward",
     "gamma_model_train_step", "gamma_model_save", "gamma_model_load", "gamma_features",
     "gamma_labels", "gamma_set_model", "gamma_load_model", "gamma_strerror", "gamma_version", "library_path",
     "criteria",
@@ -113,6 +113,7 @@ def _load():
     lib.gamma_model_get_params.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int]
     lib.gamma_model_set_params.argtypes = [vp, vp, ctypes.c_int64]
     lib.gamma_model_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    lib.gamma_model_infer.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     lib.gamma_model_backward.argtypes = [vp, vp, vp, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_float), vp]
     lib.gamma_model_train_step.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float,
@@ -334,6 +335,12 @@ def gamma_model_set_params(m: int, params) -> None:
 def gamma_model_forward(m: int, X_bf16, Y, stream=None) -> None:
     _check(_lib.gamma_model_forward(m, _raw_ptr(X_bf16), int(X_bf16.shape[0]), _raw_ptr(Y),
                                     _stream_ptr(stream)), "gamma_model_forward")
+
+
+def gamma_model_infer(m: int, X_bf16, Y, stream=None) -> None:
+    """Network outputs with the tensor-core inference kernel of the search."""
+    _check(_lib.gamma_model_infer(m, _raw_ptr(X_bf16), int(X_bf16.shape[0]), _raw_ptr(Y),
+                                  _stream_ptr(stream)), "gamma_model_infer")
 
 
 def gamma_model_backward(m: int, X_bf16, T, stream=None) -> float:

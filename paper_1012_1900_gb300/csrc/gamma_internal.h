@@ -153,6 +153,8 @@ int shell_tiles(const Problem& P);
 // Learned proposal (gamma_learned.cu).
 bool model_weights(const gamma_model_s* m, MlpWeights* w);
 cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s);
+cudaError_t launch_mlp_infer(const MlpWeights& W, const __nv_bfloat16* X, long long M, float* Y,
+                             unsigned* flags, cudaStream_t s);
 cudaError_t launch_features(const Problem& P, const unsigned* vox, long long n, __nv_bfloat16* X,
                             cudaStream_t s);
 cudaError_t launch_labels(const Problem& P, const float* gmap, const unsigned* vox, long long n,

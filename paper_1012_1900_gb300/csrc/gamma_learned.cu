@@ -21,6 +21,7 @@
 #include "../../include/gamma.h"
 #include "gamma_internal.h"
 #include "gamma_mlp.cuh"
+#include "gamma_tc.cuh"
 
 namespace gk {
 
@@ -402,74 +403,280 @@ __global__ void k_cast_weights(const float* __restrict__ W1, const float* __rest
 }
 
 // --------------------------------------------------------------------------
-// Fused inference + seeding over the queued voxels
+// Fused inference on the fifth-generation tensor cores (tcgen05)
+//
+// One block of 256 threads per SM keeps the three weight matrices resident in
+// shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16
+// bytes per core matrix; core matrices adjacent in K are LBO = rows/8 * 128
+// bytes apart, adjacent 8-row groups SBO = 128 bytes apart) and runs 128 rows
+// (voxels) at a time: layer 1 streams the 384 input features in six 64-wide
+// chunks through two buffers (one mbarrier each, so that every commit is
+// waited for exactly once and in order), accumulating X W1^T in TMEM columns
+// 0..127; layer 2 puts H1 W2^T in columns 128..255; layer 3 (N padded to 16)
+// reuses columns 0..15.  One thread issues the MMAs; the epilogues read TMEM
+// with tcgen05.ld (warp w reads lanes 32 (w % 4) .. +31), add the bias, apply
+// the ReLU and write the next layer's BF16 operand.  Every wait is bounded.
 // --------------------------------------------------------------------------
 
-constexpr int kRows = 128;                 // voxels per block iteration
-constexpr int kLdX = kInPad + 8;           // smem row strides (bf16), padded
-constexpr int kLdH = kH + 8;
-constexpr int kKc = 64;                    // K chunk of the streamed weights
-constexpr int kLdW = kKc + 8;
+constexpr int kRows = 128;                 // rows per tile (MMA M)
+constexpr int kKc = 64;                    // K chunk of the streamed features
+constexpr int kN3 = 16;                    // layer-3 N (4 outputs, padded)
+constexpr int kTmemCols = 256;
 
-struct LearnSmem {
-    bf16 X[kRows * kLdX];                  // features, later H2
-    bf16 H1[kRows * kLdH];
-    bf16 Wc[kH * kLdW];                    // streamed weight chunk
+struct __align__(1024) TcSmem {
+    bf16 W2[kH * kH];                      // rows 128, K 128 (core-matrix layout)
+    bf16 W1[kH * kInPad];                  // rows 128, K 384
+    bf16 H1[kRows * kH];
+    bf16 Xc[2][kRows * kKc];               // feature chunks; later H2 (rows 128, K 128)
+    bf16 W3[kN3 * kH];                     // rows 16, K 128 (rows >= kOut zero)
+    float b1[kH], b2[kH], b3[kOutPad];
     float Y[kRows * kOut];
-    unsigned vox[kRows];
-    unsigned item[kRows];
+    unsigned vox[kRows], item[kRows];
     float dr[kRows], inv[kRows];
     unsigned hist[kNumBuckets];
-    unsigned base;
-    unsigned nseed, nimp;
+    unsigned base, nseed, nimp;
+    uint32_t tmem;
+    uint64_t bar[3];
 };
 
-// One warp: 16 rows x 128 columns of  A (smem, [row][k]) x W^T  with W
-// streamed from global memory in K chunks through shared memory.
-__device__ __forceinline__ void layer_mma(const bf16* A, int lda, const bf16* __restrict__ W,
-                                          int K, bf16* Wc, float (&acc)[16][4], int warp, int lane)
+// Element index of (row, k) in a core-matrix tile with `rows` rows.
+__device__ __forceinline__ int core_idx(int row, int k, int rows)
 {
+    return (((k >> 3) * (rows >> 3) + (row >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+}
+
+// Descriptor of the K = 16 slice starting at column k0 of a core-matrix tile.
+__device__ __forceinline__ uint64_t tile_desc(const bf16* base, int rows, int k0)
+{
+    const uint32_t lbo = (uint32_t)(rows >> 3) * 128u;
+    return smem_desc(smem_addr(base) + (uint32_t)(k0 >> 3) * lbo, lbo, 128u);
+}
+
+// Row-major [rows][K] BF16 weights (global) -> core-matrix tile (shared).
+__device__ __forceinline__ void stage_weights(bf16* dst, const bf16* __restrict__ src, int rows,
+                                              int src_rows, int K)
+{
+    const int n = rows * (K / 8);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int r = e / (K / 8), j = e % (K / 8);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r < src_rows) v = *reinterpret_cast<const uint4*>(src + (long long)r * K + j * 8);
+        *reinterpret_cast<uint4*>(dst + core_idx(r, j * 8, rows)) = v;
+    }
+}
+
+// Weights, biases, barriers and the TMEM accumulators of one block.
+__device__ void tc_setup(TcSmem& S, const MlpWeights& W)
+{
+    stage_weights(S.W1, W.W1, kH, kH, kInPad);
+    stage_weights(S.W2, W.W2, kH, kH, kH);
+    stage_weights(S.W3, W.W3, kN3, kOutPad, kH);
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        S.b1[i] = W.b1[i];
+        S.b2[i] = W.b2[i];
+    }
+    if (threadIdx.x < kOutPad) S.b3[threadIdx.x] = W.b3[threadIdx.x];
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 3; ++b) mbar_init(&S.bar[b], 1);
+        mbar_fence_init();
+    }
+    if ((threadIdx.x >> 5) == 0) {
+        tmem_alloc(&S.tmem, kTmemCols);
+        tmem_relinquish();
+    }
+    fence_async_shared();
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+}
+
+__device__ void tc_teardown(TcSmem& S)
+{
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(S.tmem, kTmemCols);
+}
+
+// D (TMEM, 128 lanes x 128 columns from column `col`) + bias, ReLU -> BF16
+// core-matrix tile `dst` (rows 128, K 128).
+__device__ __forceinline__ void epilogue_relu(const TcSmem& S, uint32_t col, const float* bias,
+                                              bf16* dst)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+        const int c0 = half * 64 + j * 16;
+        float v[16];
+        tmem_ld16(S.tmem + ((uint32_t)(32 * q) << 16) + col + (uint32_t)c0, v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += kKc) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < kH * kKc / 8; e += blockDim.x) {     // 16-byte copies
-            const int r = e / (kKc / 8), c8 = e % (kKc / 8);
-            *(uint4*)(Wc + r * kLdW + c8 * 8) = *(const uint4*)(W + (long long)r * K + k0 + c8 * 8);
-        }
-        __syncthreads();
+        for (int h = 0; h < 2; ++h) {
+            uint32_t w[4];
 #pragma unroll
-        for (int ks = 0; ks < kKc; ks += 16) {
-            uint32_t a[4];
-            load_a_frag(a, A + warp * 16 * lda + k0 + ks, lda, lane);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                uint32_t b[2];
-                load_b_frag(b, Wc + j * 8 * kLdW + ks, kLdW, lane);
-                mma_bf16_16816(acc[j], a, b);
+            for (int i = 0; i < 4; ++i) {
+                const int c = c0 + 8 * h + 2 * i;
+                const __nv_bfloat162 pr = __floats2bfloat162_rn(fmaxf(v[8 * h + 2 * i] + bias[c], 0.f),
+                                                                fmaxf(v[8 * h + 2 * i + 1] + bias[c + 1], 0.f));
+                w[i] = *reinterpret_cast<const uint32_t*>(&pr);
             }
+            *reinterpret_cast<uint4*>(dst + core_idx(row, c0 + 8 * h, kRows)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
+
+// One tile of 128 rows: fill(c, dst) writes feature chunk c (columns 64c ..
+// 64c + 63 of every row) into dst in core-matrix layout; on return S.Y holds
+// the 4 outputs of every row.  nc counts the waited phases of each barrier.
+// Returns false (block-uniformly) if a wait gave up.
+template <typename Fill>
+__device__ bool mlp_tile(TcSmem& S, uint32_t (&nc)[3], Fill fill)
+{
+    constexpr uint32_t kId128 = idesc_bf16_f32(kRows, kH), kId16 = idesc_bf16_f32(kRows, kN3);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tm = S.tmem;
+    bool ok = true;
+    // ---- layer 1: D1 = X W1^T over six chunks ----
+#pragma unroll 1
+    for (int c = 0; c < kInPad / kKc; ++c) {
+        const int b = c & 1;
+        if (c >= 2) {                                   // MMAs of chunk c - 2 have read the buffer
+            ok = mbar_wait_bounded(&S.bar[b], nc[b] & 1u) && ok;
+            ++nc[b];
+        }
+        fill(c, S.Xc[b]);
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after_sync();
+#pragma unroll
+            for (int kk = 0; kk < kKc; kk += 16)
+                tc_mma_bf16(tm, tile_desc(S.Xc[b], kRows, kk), tile_desc(S.W1, kH, c * kKc + kk),
+                            kId128, (c | kk) != 0);
+            tc_commit(&S.bar[b]);
+        }
+    }
+    for (int b = 0; b < 2; ++b) {
+        ok = mbar_wait_bounded(&S.bar[b], nc[b] & 1u) && ok;
+        ++nc[b];
+    }
+    tc_fence_after_sync();
+    epilogue_relu(S, 0u, S.b1, S.H1);
+    fence_async_shared();
+    tc_fence_before_sync();
+    __syncthreads();
+    // ---- layer 2: D2 (columns 128..255) = H1 W2^T ----
+    if (tid == 0) {
+        tc_fence_after_sync();
+#pragma unroll
+        for (int kk = 0; kk < kH; kk += 16)
+            tc_mma_bf16(tm + kH, tile_desc(S.H1, kRows, kk), tile_desc(S.W2, kH, kk), kId128, kk != 0);
+        tc_commit(&S.bar[2]);
+    }
+    ok = mbar_wait_bounded(&S.bar[2], nc[2] & 1u) && ok;
+    ++nc[2];
+    tc_fence_after_sync();
+    bf16* H2 = &S.Xc[0][0];                             // both chunk buffers, 128 x 128
+    epilogue_relu(S, (uint32_t)kH, S.b2, H2);
+    fence_async_shared();
+    tc_fence_before_sync();
+    __syncthreads();
+    // ---- layer 3: D3 (columns 0..15) = H2 W3^T ----
+    if (tid == 0) {
+        tc_fence_after_sync();
+#pragma unroll
+        for (int kk = 0; kk < kH; kk += 16)
+            tc_mma_bf16(tm, tile_desc(H2, kRows, kk), tile_desc(S.W3, kN3, kk), kId16, kk != 0);
+        tc_commit(&S.bar[2]);
+    }
+    ok = mbar_wait_bounded(&S.bar[2], nc[2] & 1u) && ok;
+    ++nc[2];
+    tc_fence_after_sync();
+    if (warp < 4) {
+        float v[16];
+        tmem_ld16(tm + ((uint32_t)(32 * warp) << 16), v);
+        const int row = 32 * warp + lane;
+#pragma unroll
+        for (int o = 0; o < kOut; ++o) S.Y[row * kOut + o] = v[o] + S.b3[o];
+    }
+    tc_fence_before_sync();
+    return __syncthreads_and(ok) != 0;
+}
+
+// The blocks of both inference kernels take the whole 227 KB of shared memory
+// (one block per SM; the TMEM allocation can then never wait).
+constexpr size_t kTcSmemBytes = 232448;
+static_assert(sizeof(TcSmem) <= kTcSmemBytes, "tensor-core tile does not fit in shared memory");
+
+size_t learned_smem_bytes() { return kTcSmemBytes; }
+
+// Network outputs for M given feature rows (row-major [M][384] BF16).
+__global__ void __launch_bounds__(256, 1) k_mlp_infer(const __grid_constant__ MlpWeights W,
+                                                      const bf16* __restrict__ X, long long M,
+                                                      float* __restrict__ Y, unsigned* flags)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+    tc_setup(S, W);
+    uint32_t nc[3] = {0u, 0u, 0u};
+    bool ok = true;
+    for (long long t = blockIdx.x; ok && t * kRows < M; t += gridDim.x) {
+        const long long row0 = t * kRows;
+        auto fill = [&](int c, bf16* dst) {
+            for (int e = threadIdx.x; e < kRows * (kKc / 8); e += blockDim.x) {
+                const int r = e >> 3, j = e & 7;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (row0 + r < M)
+                    v = *reinterpret_cast<const uint4*>(X + (row0 + r) * kInPad + c * kKc + j * 8);
+                *reinterpret_cast<uint4*>(dst + core_idx(r, j * 8, kRows)) = v;
+            }
+        };
+        ok = mlp_tile(S, nc, fill);
+        if (threadIdx.x < kRows && row0 + threadIdx.x < M)
+#pragma unroll
+            for (int o = 0; o < kOut; ++o) Y[(row0 + threadIdx.x) * kOut + o] = S.Y[threadIdx.x * kOut + o];
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
+    tc_teardown(S);
+}
+
+cudaError_t launch_mlp_infer(const MlpWeights& W, const bf16* X, long long M, float* Y,
+                             unsigned* flags, cudaStream_t s)
+{
+    const size_t smem = kTcSmemBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (M + kRows - 1) / kRows;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, device_sm_count()));
+    k_mlp_infer<<<grid, 256, smem, s>>>(W, X, M, Y, flags);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Fused inference + seeding over the queued voxels
+// --------------------------------------------------------------------------
 
 template <int N>
 __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Problem P,
                                                     const __grid_constant__ MlpWeights W)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    LearnSmem& S = *reinterpret_cast<LearnSmem*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t4 = lane & 3;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
     const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
     const unsigned total = min(P.ctr->tail_count, P.tail_cap);
     if (threadIdx.x < kNumBuckets) S.hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) { S.nseed = 0; S.nimp = 0; }
+    tc_setup(S, W);
+    uint32_t nc[3] = {0u, 0u, 0u};
+    bool ok = true;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) S.base = atomicAdd(&P.ctr->seed_head, (unsigned)kRows);
         __syncthreads();
         const unsigned base = S.base;
-        if (base >= total) break;
+        if (base >= total || !ok) break;
         // ---- rows: voxel, dose, scale ----
         if (threadIdx.x < kRows) {
             const unsigned it = base + threadIdx.x;
@@ -486,60 +693,22 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
             S.inv[threadIdx.x] = inv;
         }
         __syncthreads();
-        // ---- features ----
-        for (int e = threadIdx.x; e < kRows * kInPad; e += blockDim.x) {
-            const int r = e / kInPad, f = e % kInPad;
-            const unsigned v = S.vox[r];
-            float val = 0.f;
-            if (v != 0xffffffffu) {
-                const int x = (int)(v % (unsigned)P.nx);
-                const unsigned r1 = v / (unsigned)P.nx;
-                val = voxel_feature<N>(P, x, (int)(r1 % (unsigned)P.ny), (int)(r1 / (unsigned)P.ny),
-                                       S.dr[r], S.inv[r], f);
-            }
-            S.X[r * kLdX + f] = __float2bfloat16(val);
-        }
-        // ---- layer 1: H1 = relu(X W1^T + b1) ----
-        float acc[16][4];
-        layer_mma(S.X, kLdX, W.W1, kInPad, S.Wc, acc, warp, lane);
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int r = warp * 16 + g + (h >= 2 ? 8 : 0), c = j * 8 + 2 * t4 + (h & 1);
-                S.H1[r * kLdH + c] = __float2bfloat16(fmaxf(acc[j][h] + W.b1[c], 0.f));
-            }
-        // ---- layer 2: H2 = relu(H1 W2^T + b2), stored over X ----
-        layer_mma(S.H1, kLdH, W.W2, kH, S.Wc, acc, warp, lane);
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int r = warp * 16 + g + (h >= 2 ? 8 : 0), c = j * 8 + 2 * t4 + (h & 1);
-                S.X[r * kLdH + c] = __float2bfloat16(fmaxf(acc[j][h] + W.b2[c], 0.f));
-            }
-        __syncthreads();
-        // ---- layer 3: Y = H2 W3^T + b3 (8 padded outputs, 4 used) ----
-        {
-            for (int e = threadIdx.x; e < kOutPad * kH; e += blockDim.x)
-                S.Wc[(e / kH) * kLdH + e % kH] = W.W3[e];
-            __syncthreads();
-            float y[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int ks = 0; ks < kH; ks += 16) {
-                uint32_t a[4], b[2];
-                load_a_frag(a, S.X + warp * 16 * kLdH + ks, kLdH, lane);
-                load_b_frag(b, S.Wc + ks, kLdH, lane);
-                mma_bf16_16816(y, a, b);
-            }
-            if (t4 < 2)
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int r = warp * 16 + g + (h >= 2 ? 8 : 0), c = 2 * t4 + (h & 1);
-                    S.Y[r * kOut + c] = y[h] + W.b3[c];
+        // ---- features (chunk by chunk) and the three layers ----
+        auto fill = [&](int c, bf16* dst) {
+            for (int e = threadIdx.x; e < kRows * kKc; e += blockDim.x) {
+                const int r = e / kKc, fl = e % kKc;
+                const unsigned v = S.vox[r];
+                float val = 0.f;
+                if (v != 0xffffffffu) {
+                    const int x = (int)(v % (unsigned)P.nx);
+                    const unsigned r1 = v / (unsigned)P.nx;
+                    val = voxel_feature<N>(P, x, (int)(r1 % (unsigned)P.ny), (int)(r1 / (unsigned)P.ny),
+                                           S.dr[r], S.inv[r], c * kKc + fl);
                 }
-        }
-        __syncthreads();
+                dst[core_idx(r, fl, kRows)] = __float2bfloat16(val);
+            }
+        };
+        ok = mlp_tile(S, nc, fill);
         // ---- seed: exact faces of the cells around the proposed point ----
         {
             const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
@@ -604,14 +773,14 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
     if (threadIdx.x == 0) {
         atomicAdd(&P.ctr->seeded, S.nseed);
         atomicAdd(&P.ctr->seed_improved, S.nimp);
+        if (!ok) atomicOr(&P.ctr->flags, kFlagTimeout);
     }
+    tc_teardown(S);
 }
-
-size_t learned_smem_bytes() { return sizeof(LearnSmem); }
 
 cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s)
 {
-    const size_t smem = sizeof(LearnSmem);
+    const size_t smem = kTcSmemBytes;
     cudaError_t e;
     if (P.ndim == 3) {
         e = cudaFuncSetAttribute(k_learned<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -666,6 +835,7 @@ struct gamma_model_s {
     long long wsM = 0;
     float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dY = nullptr, *dH1 = nullptr, *loss = nullptr;
     bf16 *H1h = nullptr, *H2h = nullptr, *dZ2h = nullptr, *dZ1h = nullptr;
+    unsigned* dflags = nullptr;   // error flags of the inference kernel
 };
 
 namespace {
@@ -841,6 +1011,8 @@ int gamma_model_create(gamma_model* out, uint64_t seed)
     if ((rc = cuda_rc(cudaMalloc(&m->W2h, sizeof(bf16) * gk::kH * gk::kH)))) return fail(rc);
     if ((rc = cuda_rc(cudaMalloc(&m->W2Th, sizeof(bf16) * gk::kH * gk::kH)))) return fail(rc);
     if ((rc = cuda_rc(cudaMalloc(&m->W3h, sizeof(bf16) * gk::kOutPad * gk::kH)))) return fail(rc);
+    if ((rc = cuda_rc(cudaMalloc(&m->dflags, sizeof(unsigned))))) return fail(rc);
+    if ((rc = cuda_rc(cudaMemset(m->dflags, 0, sizeof(unsigned))))) return fail(rc);
     std::vector<float> h;
     init_params(h, seed);
     m->seed = seed;
@@ -860,6 +1032,7 @@ void gamma_model_destroy(gamma_model m)
     if (!m) return;
     cudaFree(m->p); cudaFree(m->gr); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->mask);
     cudaFree(m->W1h); cudaFree(m->W2h); cudaFree(m->W2Th); cudaFree(m->W3h);
+    cudaFree(m->dflags);
     free_ws(m);
     delete m;
 }
@@ -894,6 +1067,22 @@ int gamma_model_forward(gamma_model m, const void* X_bf16_dev, int64_t M, float*
     MCK(cudaMemcpy2DAsync(Y_dev, sizeof(float) * gk::kOut, m->Y, sizeof(float) * gk::kOutPad,
                           sizeof(float) * gk::kOut, (size_t)M, cudaMemcpyDeviceToDevice, s));
     return GAMMA_OK;
+}
+
+int gamma_model_infer(gamma_model m, const void* X_bf16_dev, int64_t M, float* Y_dev,
+                      void* cuda_stream)
+{
+    if (!m || !X_bf16_dev || !Y_dev || M <= 0) return GAMMA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(X_bf16_dev) % 16 != 0) return GAMMA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    gk::MlpWeights W;
+    gk::model_weights(m, &W);
+    MCK(cudaMemsetAsync(m->dflags, 0, sizeof(unsigned), s));
+    MCK(gk::launch_mlp_infer(W, (const bf16*)X_bf16_dev, M, Y_dev, m->dflags, s));
+    unsigned flags = 0;
+    MCK(cudaMemcpyAsync(&flags, m->dflags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MCK(cudaStreamSynchronize(s));
+    return (flags & gk::kFlagTimeout) ? GAMMA_ERR_TIMEOUT : GAMMA_OK;
 }
 
 int gamma_model_backward(gamma_model m, const void* X_bf16_dev, const float* T_dev, int64_t M,

@@ -53,6 +53,34 @@ def test_forward_and_backward_match_reference():
         g.gamma_model_destroy(m)
 
 
+@pytest.mark.parametrize("M", [1, 300, 40000])
+def test_tensor_core_inference_matches_reference(M):
+    # The search's inference kernel (tcgen05 MMAs, TMEM accumulators) against
+    # the FP64 network with the same BF16 rounding points.  300 rows leave a
+    # ragged last tile; 40,000 rows give every block several tiles, so the
+    # barrier phases carry over between tiles.
+    import paper_1012_1900_gb300 as g
+    rng = np.random.default_rng(5 + M)
+    m = g.gamma_model_create(21)
+    try:
+        X = np.zeros((M, mlp.K_PAD), np.float32)
+        X[:, :mlp.K_IN] = rng.normal(0, 1.5, (M, mlp.K_IN))
+        Xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
+        Xq = Xb.float().cpu().numpy().astype(np.float64)
+        p = g.gamma_model_get_params(m).astype(np.float64)
+        Y = torch.full((M, 4), float("nan"), device="cuda")
+        g.gamma_model_infer(m, Xb, Y)
+        got = Y.cpu().numpy().astype(np.float64)
+        ref = mlp.forward(p, Xq)["y"]
+        assert np.all(np.isfinite(got))
+        assert _rel(got, ref) < 2e-3
+        Y2 = torch.empty((M, 4), device="cuda")
+        g.gamma_model_forward(m, Xb, Y2)                 # the training kernels agree
+        assert _rel(got, Y2.cpu().numpy().astype(np.float64)) < 2e-3
+    finally:
+        g.gamma_model_destroy(m)
+
+
 def test_adam_step_and_save_load(tmp_path):
     import paper_1012_1900_gb300 as g
     rng = np.random.default_rng(4)
