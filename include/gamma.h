@@ -200,9 +200,10 @@ typedef struct {
     gamma_criteria crit;
 } gamma_pair_desc;
 
-/* Create a batch handle over n_pairs descriptors (copied; device buffers
- * borrowed).  Each pair gets its own cell table and scratch.  Errors:
- * INVALID_ARG, SHAPE, OOM, TABLE_TOO_LARGE, CUDA.  Synchronous. */
+/* Create a batch handle over 1 <= n_pairs <= 65535 descriptors (copied;
+ * device buffers borrowed).  Each pair gets its own cell table and scratch;
+ * the handle adds 6 bytes per voxel of all pairs for the shared work order.
+ * Errors: INVALID_ARG, SHAPE, OOM, TABLE_TOO_LARGE, CUDA.  Synchronous. */
 int gamma_batch_create(gamma_handle *out, int n_pairs, const gamma_pair_desc *pairs);
 
 /* Compute every pair's gamma map on `cuda_stream`.  The first call (and the

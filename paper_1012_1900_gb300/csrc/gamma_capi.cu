@@ -292,6 +292,8 @@ struct BatchState {
         int* use_tma = nullptr;
         int* tile_start = nullptr;
         unsigned* item_start = nullptr;
+        unsigned* items_v = nullptr;
+        unsigned short* items_p = nullptr;
         unsigned* head = nullptr;
         gk::BatchDesc* desc = nullptr;
         gk::BatchGroup host{};
@@ -311,6 +313,8 @@ void free_group(BatchState::Group& g)
     cudaFree(g.use_tma);
     cudaFree(g.tile_start);
     cudaFree(g.item_start);
+    cudaFree(g.items_v);
+    cudaFree(g.items_p);
     cudaFree(g.head);
     cudaFree(g.desc);
     g = BatchState::Group{};
@@ -370,6 +374,10 @@ int batch_upload(gamma_ctx* h)
             CK(cudaMalloc(&G.use_tma, sizeof(int) * np));
             CK(cudaMalloc(&G.tile_start, sizeof(int) * (np + 1)));
             CK(cudaMalloc(&G.item_start, sizeof(unsigned) * (gk::kNumBuckets * np + 1)));
+            size_t cap = 0;
+            for (int k = 0; k < np; ++k) cap += b->pairs[mem[k]]->tail_cap;
+            CK(cudaMalloc(&G.items_v, sizeof(unsigned) * std::max<size_t>(cap, 1)));
+            CK(cudaMalloc(&G.items_p, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
             CK(cudaMalloc(&G.head, sizeof(unsigned)));
             CK(cudaMalloc(&G.desc, sizeof(gk::BatchDesc)));
         }
@@ -384,6 +392,8 @@ int batch_upload(gamma_ctx* h)
         d.use_tma = G.use_tma;
         d.tile_start = G.tile_start;
         d.item_start = G.item_start;
+        d.items_v = G.items_v;
+        d.items_p = G.items_p;
         d.head = G.head;
         CK(cudaMemcpy(G.desc, &d, sizeof(d), cudaMemcpyHostToDevice));
         G.host.ndim = gi == 0 ? 2 : 3;
@@ -713,7 +723,7 @@ void gamma_destroy(gamma_handle h)
 
 int gamma_batch_create(gamma_handle* out, int n_pairs, const gamma_pair_desc* pairs)
 {
-    if (!out || n_pairs <= 0 || !pairs) return GAMMA_ERR_INVALID_ARG;
+    if (!out || n_pairs <= 0 || n_pairs > 65535 || !pairs) return GAMMA_ERR_INVALID_ARG;
     *out = nullptr;
     gamma_ctx* h = new (std::nothrow) gamma_ctx();
     if (!h) return GAMMA_ERR_OOM;

@@ -121,8 +121,10 @@ struct BatchDesc {
     const CUtensorMap* maps;       // [npairs] evaluation-dose tile maps
     const int* use_tma;            // [npairs] 1: the map is valid for TMA loads
     const int* tile_start;         // [npairs + 1] first global shell tile of each pair
-    unsigned* item_start;          // [kNumBuckets * npairs + 1] queued voxels ordered
-                                   // by (cost bucket descending, pair)
+    unsigned* item_start;          // [npairs * kNumBuckets + 1] queued voxels ordered
+                                   // by (pair, cost bucket descending)
+    unsigned* items_v;             // [sum of tail_cap] queued voxels in that order
+    unsigned short* items_p;       // [sum of tail_cap] their pair
     unsigned* head;                // work counter of the group's table walk
 };
 

@@ -393,30 +393,27 @@ __global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ Problem
     }
 }
 
-// Batched ordering: each pair's queue sorted by its own bucket offsets, plus a
-// global item order over (bucket descending, pair) for the table walk.
+// Global order of a batch group's queued voxels: pair by pair (so that the
+// walks in flight share one pair's doses in L2), most expensive bucket first
+// within a pair; each pair's cursor[b] starts at its range in that order.
 __global__ void k_bucket_scan_batch(const BatchDesc* __restrict__ bd)
 {
     const int np = bd->npairs;
-    for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        Counters* c = bd->probs[p].ctr;
-        unsigned acc = 0;
-        for (int b = kNumBuckets - 1; b >= 0; --b) {
-            c->cursor[b] = acc;
-            acc += c->hist[b];
-        }
-    }
-    __syncthreads();
     if (threadIdx.x == 0) {
         unsigned acc = 0;
         int k = 0;
-        for (int b = kNumBuckets - 1; b >= 0; --b)
-            for (int p = 0; p < np; ++p) {
+        for (int p = 0; p < np; ++p)
+            for (int b = kNumBuckets - 1; b >= 0; --b) {
                 bd->item_start[k++] = acc;
                 acc += bd->probs[p].ctr->hist[b];
             }
         bd->item_start[k] = acc;
         *bd->head = 0;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        Counters* c = bd->probs[p].ctr;
+        for (int b = 0; b < kNumBuckets; ++b) c->cursor[b] = bd->item_start[p * kNumBuckets + (kNumBuckets - 1 - b)];
     }
 }
 
@@ -427,7 +424,8 @@ __global__ void __launch_bounds__(256) k_scatter_batch(const BatchDesc* __restri
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
         const unsigned pos = atomicAdd(&P.ctr->cursor[P.tail_bucket[i]], 1u);
-        P.tail_sorted[pos] = P.tail_raw[i];
+        bd->items_v[pos] = P.tail_raw[i];
+        bd->items_p[pos] = (unsigned short)blockIdx.y;
     }
 }
 
@@ -526,7 +524,18 @@ __global__ void __launch_bounds__(256, MINB)
                                  : min(P0.ctr->tail_count, P0.tail_cap);
     unsigned* head = BATCH ? bd->head : &P0.ctr->head;
     unsigned int my_eval = 0, my_pass = 0, my_over = 0;
+    int my_pair = -1;          // batched: pair whose counts my_* hold
     TailStats st;
+    // batched launches: hand this lane's counts to their pair
+    auto flush_pair = [&]() {
+        if (my_pair >= 0 && gl == 0) {
+            Counters* c = bd->probs[my_pair].ctr;
+            if (my_eval) atomicAdd(&c->n_eval, (unsigned long long)my_eval);
+            if (my_pass) atomicAdd(&c->n_pass, (unsigned long long)my_pass);
+            if (my_over) atomicAdd(&c->overflow_count, my_over);
+        }
+        my_eval = my_pass = my_over = 0;
+    };
 
     for (;;) {
         unsigned item = 0;
@@ -536,17 +545,12 @@ __global__ void __launch_bounds__(256, MINB)
         int pr = 0;
         unsigned v;
         if constexpr (BATCH) {
-            const int np = bd->npairs;
-            int lo = 0, hi = kNumBuckets * np - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (bd->item_start[mid] <= item) lo = mid; else hi = mid - 1;
+            v = bd->items_v[item];
+            pr = bd->items_p[item];
+            if (pr != my_pair) {                 // uniform over the group
+                flush_pair();
+                my_pair = pr;
             }
-            const int b = kNumBuckets - 1 - lo / np;
-            pr = lo % np;
-            const Problem& Q = bd->probs[pr];
-            const unsigned first = Q.ctr->cursor[b] - Q.ctr->hist[b];
-            v = Q.tail_sorted[first + (item - bd->item_start[lo])];
         } else {
             v = P0.sort_tail ? P0.tail_sorted[item] : P0.tail_raw[item];
         }
@@ -585,7 +589,7 @@ __global__ void __launch_bounds__(256, MINB)
         if (t >= P.ntable && best > rc2) {
             // The walk ran past a truncated table: scan every cell of the
             // remaining search box (rare; keeps the result exact).
-            ++my_over;
+            if (gl == 0) ++my_over;
             const float g = sqrtf(best);
             const int ax = (int)ceilf(g / P.hn[0]) + 1;
             const int ay = (int)ceilf(g / P.hn[1]) + 1;
@@ -616,22 +620,12 @@ __global__ void __launch_bounds__(256, MINB)
         if (gl == 0) {
             const float gam = sqrtf(best);
             P.out[v] = gam;
-            if constexpr (BATCH) {
-                atomicAdd(&P.ctr->n_eval, 1ull);
-                if (gam <= 1.f) atomicAdd(&P.ctr->n_pass, 1ull);
-            } else {
-                ++my_eval;
-                my_pass += gam <= 1.f;
-            }
-        }
-        if constexpr (BATCH) {
-            if (my_over) {
-                if (gl == 0) atomicAdd(&P.ctr->overflow_count, 1u);
-                my_over = 0;
-            }
+            ++my_eval;
+            my_pass += gam <= 1.f;
         }
     }
-    if constexpr (!BATCH) {      // single-pair totals (batched ones went out per voxel)
+    if constexpr (BATCH) flush_pair();
+    if constexpr (!BATCH) {      // single-pair totals (batched ones went out per pair run)
         const Problem& P = P0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -647,7 +641,7 @@ __global__ void __launch_bounds__(256, MINB)
         if (lane == 0) {
             if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
             if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
-            if (my_over) atomicAdd(&P.ctr->overflow_count, my_over / G);
+            if (my_over) atomicAdd(&P.ctr->overflow_count, my_over);
             if (P.stats) {
                 atomicAdd(&P.ctr->cells_visited, st.visited);
                 atomicAdd(&P.ctr->cells_pruned, st.pruned);
