@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
-    ap.add_argument("--experiment", choices=["learned", "batch", "studies"], default=None,
+    ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation"], default=None,
                     help="learned: train + evaluate the proposal network (200x200x150 pairs, "
                          "2%%/2mm); batch: 64 uneven pairs batched vs one by one")
     ap.add_argument("--train-pairs", type=int, default=200)
@@ -758,8 +758,55 @@ def experiment_studies(args):
     print(json.dumps(res), flush=True)
 
 
+def experiment_ablation(args):
+    """The paper's own GPU design (Algorithm A2) against this library's
+    two-phase search on the same GPU: one thread per voxel with and without
+    the DD sort (Table 2), and every face in closed form against Ju's
+    recursion on the full simplices (Section 2.1 vs 2.2).  All variants give
+    the same map; the max |difference| to the two-phase map is reported."""
+    import torch
+    import paper_1012_1900_gb300 as g
+    rows = []
+    for name in ("imrt_160", "imrt_160_2mm2pct", "imrt_320_global"):
+        pair = synth.workload(name)
+        c = pair.criteria
+        ref = torch.from_numpy(pair.ref).cuda()
+        ev = torch.from_numpy(pair.eval).cuda()
+        out = torch.empty_like(ref)
+        h = g.gamma_create(ref, ev, 3, pair.ref.shape, pair.spacing,
+                           g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm))
+        try:
+            tuned = g.gamma_autotune(h, out, reps=2)
+            g.gamma_run(h, out)
+            g.gamma_pass_rate(h)
+            base = out.cpu().numpy()
+            row = {"workload": name, "two_phase_ms": _timed_runs(g, h, out), "autotuned": tuned}
+            for design, dname in ((1, "dd_sorted"), (2, "unsorted")):
+                for fe, fname in ((0, "all_faces"), (1, "ju")):
+                    g.gamma_set_option(h, "design", design)
+                    g.gamma_set_option(h, "face_eval", fe)
+                    g.gamma_run(h, out)
+                    g.gamma_pass_rate(h)
+                    got = out.cpu().numpy()
+                    ok = np.isfinite(base)
+                    row[f"paper_{dname}_{fname}_ms"] = _timed_runs(g, h, out, reps=3)
+                    row[f"paper_{dname}_{fname}_maxdiff"] = float(np.max(np.abs(got[ok] - base[ok])))
+            g.gamma_set_option(h, "design", 0)
+        finally:
+            g.gamma_destroy(h)
+        row["speedup_vs_paper_design"] = row["paper_dd_sorted_all_faces_ms"] / row["two_phase_ms"]
+        row["dd_sort_speedup"] = row["paper_unsorted_all_faces_ms"] / row["paper_dd_sorted_all_faces_ms"]
+        row["ju_over_all_faces"] = row["paper_dd_sorted_ju_ms"] / row["paper_dd_sorted_all_faces_ms"]
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"experiment": "ablation", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.experiment == "ablation":
+        experiment_ablation(args)
+        return
     if args.experiment == "studies":
         experiment_studies(args)
         return

@@ -174,6 +174,15 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     kernel's register budget is sized for (default 2)
  *  "tail_blocks_per_sm"   1 or 2: the same for the table-walk kernel
  *                     (default 2)
+ *  "design"           ablation of the paper's GPU design (Algorithm A2;
+ *                     single-pair handles): 0 this library's two-phase search
+ *                     (default); 1 one thread per voxel in the order of a
+ *                     radix sort by DD, walking the whole cell table with
+ *                     every simplex of every cell; 2 the same without the
+ *                     sort.  Same results; allocates 16 bytes per voxel.
+ *  "face_eval"        design 1 / 2 only: 0 every face in closed form (the
+ *                     paper's choice, Section 2.2); 1 the full simplices by
+ *                     Ju's recursion (Section 2.1)
  * Errors: INVALID_ARG (unknown key or value), TABLE_TOO_LARGE, OOM. */
 int gamma_set_option(gamma_handle h, const char *key, int64_t value);
 

@@ -97,6 +97,9 @@ struct gamma_ctx {
     int timing = 0;
     int shell_minblocks = 2;
     int tail_minblocks = 2;
+    int design = 0;          // 0: two-phase search; 1 / 2: the paper's A2 with / without DD sort
+    int face_eval = 0;       // design 1 / 2: 0 closed-form faces, 1 Ju's recursion
+    gk::PaperScratch paper;
     gamma_model model = nullptr;      // attached proposal network (may be null)
     bool own_model = false;
     // per-phase events: 0 start, 1 after h2d, 2 after prepare, 3 after shell,
@@ -261,6 +264,11 @@ void free_ctx(gamma_ctx* h)
     cudaFree(h->own_ref);
     cudaFree(h->own_ev);
     cudaFree(h->own_out);
+    cudaFree(h->paper.keys);
+    cudaFree(h->paper.ids);
+    cudaFree(h->paper.keys_alt);
+    cudaFree(h->paper.ids_alt);
+    cudaFree(h->paper.temp);
     delete h;
 }
 
@@ -527,6 +535,18 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), s));
     CK(gk::launch_prepare(P, s));
     if (tm) CK(cudaEventRecord(h->tev[2], s));
+    if (h->design != 0) {
+        // the paper's design: DD keys and sort ("shell" phase), then the walk ("tail")
+        CK(gk::launch_paper(P, h->paper, h->design == 1, h->face_eval == 1, tm ? h->tev[3] : nullptr, s));
+        if (tm) {
+            CK(cudaEventRecord(h->tev[4], s));
+            CK(cudaEventRecord(h->tev[5], s));
+            if (!h->ev_h2d) CK(cudaEventRecord(h->tev[6], s));
+        }
+        h->last_stream = s;
+        h->ran = true;
+        return GAMMA_OK;
+    }
     CK(gk::launch_shell(P, s));
     if (h->model) {
         gk::MlpWeights W;
@@ -688,6 +708,29 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
     if (!std::strcmp(key, "stats")) {
         if (value != 0 && value != 1) return GAMMA_ERR_INVALID_ARG;
         h->stats = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "design")) {
+        if (h->batch || value < 0 || value > 2) return GAMMA_ERR_INVALID_ARG;
+        if (value != 0 && !h->paper.keys) {
+            DeviceGuard dg(h->device);
+            if (!dg.ok) return GAMMA_ERR_CUDA;
+            if (h->ran) { CK(cudaStreamSynchronize(h->last_stream)); }
+            const size_t n = (size_t)h->nvox;
+            gk::PaperScratch& w = h->paper;
+            w.temp_bytes = gk::paper_sort_bytes(h->nvox);
+            CK(cudaMalloc(&w.keys, sizeof(unsigned) * n));
+            CK(cudaMalloc(&w.ids, sizeof(unsigned) * n));
+            CK(cudaMalloc(&w.keys_alt, sizeof(unsigned) * n));
+            CK(cudaMalloc(&w.ids_alt, sizeof(unsigned) * n));
+            CK(cudaMalloc(&w.temp, std::max<size_t>(w.temp_bytes, 16)));
+        }
+        h->design = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "face_eval")) {
+        if (h->batch || value < 0 || value > 1) return GAMMA_ERR_INVALID_ARG;
+        h->face_eval = (int)value;
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "tail_blocks_per_sm")) {

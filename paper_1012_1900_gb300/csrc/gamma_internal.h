@@ -155,6 +155,17 @@ int shell_tiles(const Problem& P);
 // Learned proposal (gamma_learned.cu).
 bool model_weights(const gamma_model_s* m, MlpWeights* w);
 cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s);
+
+// Paper-design ablation (gamma_paper.cu): one thread per voxel, optionally in
+// DD order, all simplices of every cell reached (closed form or Ju's recursion).
+struct PaperScratch {
+    unsigned *keys = nullptr, *ids = nullptr, *keys_alt = nullptr, *ids_alt = nullptr;
+    void* temp = nullptr;
+    size_t temp_bytes = 0;
+};
+size_t paper_sort_bytes(long long nvox);
+cudaError_t launch_paper(const Problem& P, const PaperScratch& w, bool sorted, bool ju,
+                         cudaEvent_t after_sort, cudaStream_t s);
 cudaError_t launch_mlp_infer(const MlpWeights& W, const __nv_bfloat16* X, long long M, float* Y,
                              unsigned* flags, cudaStream_t s);
 cudaError_t launch_features(const Problem& P, const unsigned* vox, long long n, __nv_bfloat16* X,

@@ -174,6 +174,36 @@ def test_truncated_table_box_scan(ndim):
     assert_parity(got, want, counts)
 
 
+@pytest.mark.parametrize("design", [1, 2])
+@pytest.mark.parametrize("face_eval", [0, 1])
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_paper_design_ablation(design, face_eval, ndim):
+    # The paper's own GPU design (one thread per voxel, DD-sorted or not; all
+    # faces in closed form or Ju's recursion) must give the same map.
+    if ndim == 2:
+        p = synth.make_pair_2d(shape=(61, 47), spacing=(1.0, 1.25), seed=21, shift_mm=(0.9, -1.3),
+                               scale=1.03, noise_sd=0.01)
+        crit = synth.Criteria(0.02, 2.0)
+    else:
+        p = synth.workload("imrt_small")
+        crit = synth.Criteria(0.01, 1.0, local=True)
+    got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"design": design, "face_eval": face_eval})
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
+@pytest.mark.parametrize("face_eval", [0, 1])
+def test_paper_design_truncated_table(face_eval):
+    p = synth.make_pair_3d(shape=(14, 18, 16), spacing=(2.0, 2.0, 2.0), seed=6,
+                           shift_mm=(1.0, 2.0, 2.5), scale=1.06)
+    crit = synth.Criteria(0.01, 1.0, local=True)
+    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, crit,
+                                {"table_cap": 16, "design": 1, "face_eval": face_eval})
+    assert st["overflow_voxels"] > 0
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    assert_parity(got, want, counts)
+
+
 def test_fp64_redo_paths():
     p = synth.workload("imrt_small")
     crit = synth.Criteria(0.01, 1.0, local=True)
