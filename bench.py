@@ -71,7 +71,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
-    ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation"], default=None,
+    ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation", "mlp_infer"],
+                    default=None,
                     help="learned: train + evaluate the proposal network (200x200x150 pairs, "
                          "2%%/2mm); batch: 64 uneven pairs batched vs one by one")
     ap.add_argument("--train-pairs", type=int, default=200)
@@ -802,8 +803,47 @@ def experiment_ablation(args):
     print(json.dumps({"experiment": "ablation", "rows": rows}), flush=True)
 
 
+def experiment_mlp_infer(args):
+    """The proposal network's tensor-core inference kernel alone: 262,144 random
+    feature rows (201 MB, more than L2), median of timed calls."""
+    import torch
+    import paper_1012_1900_gb300 as g
+    M = 262144
+    m = g.gamma_model_create(3)
+    try:
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        X = (torch.randn(M, 384, device="cuda", generator=gen) * 1.5).to(torch.bfloat16)
+        X[:, 375:] = 0
+        Y = torch.empty((M, 4), device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            g.gamma_model_infer(m, X, Y)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record()
+            g.gamma_model_infer(m, X, Y)
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        ms = statistics.median(ts)
+        flop = 2.0 * M * (384 * 128 + 128 * 128 + 128 * 4)
+        peaks = load_peaks()
+        print(json.dumps({"experiment": "mlp_infer", "rows": M, "ms": ms,
+                          "tflops": flop / (ms / 1000.0) / 1e12,
+                          "bf16_peak_tflops": peaks.get("bf16_tflops"),
+                          "input_gbs": X.numel() * 2 / (ms / 1000.0) / 1e9,
+                          "hbm_peak_gbs": peaks.get("hbm_gbs")}), flush=True)
+    finally:
+        g.gamma_model_destroy(m)
+
+
 def main():
     args = parse()
+    if args.experiment == "mlp_infer":
+        experiment_mlp_infer(args)
+        return
     if args.experiment == "ablation":
         experiment_ablation(args)
         return
