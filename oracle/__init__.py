@@ -56,6 +56,11 @@ def _load():
                                               ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                               f64p, ctypes.c_int64]
             lib.oracle_max_threads.restype = ctypes.c_int
+            lib.oracle_gamma_grids.restype = ctypes.c_int
+            lib.oracle_gamma_grids.argtypes = [f32p, i64p, f64p, f64p, f32p, i64p, f64p, f64p,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               i64p, ctypes.c_int64, f64p, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -118,6 +123,49 @@ def gamma(ref: np.ndarray, ev: np.ndarray, spacing: Sequence[float], dd_frac: fl
     if return_cells:
         return out, cells.reshape(out_shape), rmax.value
     return out
+
+
+def _grid3(a: np.ndarray, spacing: Sequence[float], origin: Sequence[float]):
+    if a.ndim == 2:
+        return (np.array([1, a.shape[0], a.shape[1]], dtype=np.int64),
+                np.array([1.0, spacing[0], spacing[1]], dtype=np.float64),
+                np.array([0.0, origin[0], origin[1]], dtype=np.float64))
+    return (np.array(a.shape, dtype=np.int64), np.array(spacing, dtype=np.float64),
+            np.array(origin, dtype=np.float64))
+
+
+def gamma_grids(ref: np.ndarray, ref_spacing: Sequence[float], ref_origin: Sequence[float],
+                ev: np.ndarray, ev_spacing: Sequence[float], ev_origin: Sequence[float],
+                dd_frac: float, dta_mm: float, local: bool = False, cutoff_frac: float = 0.0,
+                dose_norm: float = 0.0, idx: Optional[np.ndarray] = None, threads: int = 0):
+    """Gamma of every reference voxel (or of the flat indices ``idx``) when the
+    reference and evaluation doses sit on different grids: each grid with its
+    own shape, spacing and origin (mm, array order).  FP64; NaN where not
+    evaluated; shaped like ref (or idx)."""
+    lib = _load()
+    ref = np.ascontiguousarray(ref, dtype=np.float32)
+    ev = np.ascontiguousarray(ev, dtype=np.float32)
+    if ref.ndim != ev.ndim or ref.ndim not in (2, 3):
+        raise ValueError("both grids must be 2D or both 3D")
+    rs, rsp, ro = _grid3(ref, ref_spacing, ref_origin)
+    es, esp, eo = _grid3(ev, ev_spacing, ev_origin)
+    if idx is None:
+        n, idx_arr, out_shape = ref.size, None, ref.shape
+    else:
+        idx_arr = np.ascontiguousarray(idx, dtype=np.int64).ravel()
+        n, out_shape = idx_arr.size, np.shape(idx)
+    out = np.empty(n, dtype=np.float64)
+    rc = lib.oracle_gamma_grids(_ptr(ref, ctypes.c_float), _ptr(rs, ctypes.c_int64),
+                                _ptr(rsp, ctypes.c_double), _ptr(ro, ctypes.c_double),
+                                _ptr(ev, ctypes.c_float), _ptr(es, ctypes.c_int64),
+                                _ptr(esp, ctypes.c_double), _ptr(eo, ctypes.c_double),
+                                ref.ndim, float(dd_frac), float(dta_mm), int(bool(local)),
+                                float(cutoff_frac), float(dose_norm),
+                                _ptr(idx_arr, ctypes.c_int64) if idx_arr is not None else None,
+                                int(n), _ptr(out, ctypes.c_double), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_gamma_grids failed: {_ERRORS.get(rc, rc)}")
+    return out.reshape(out_shape)
 
 
 def gamma_pair(pair, idx=None, **kw):

@@ -483,3 +483,160 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reference and evaluation on different grids.                              */
+/* ------------------------------------------------------------------------ */
+/* Each grid has its own shape, spacing and origin (mm, same axes).  Eq. 1 is
+ * taken literally: for a reference voxel at position x_r with dose D_r,
+ *     gamma = min over the evaluation surface (the Freudenthal interpolant of
+ *             the evaluation grid, cubes wholly inside it) of
+ *             |(x - x_r)/dta, (D_e(x) - D_r)/dD|.
+ * The nearest evaluation node is a point of the surface, so its distance
+ * g_ub bounds gamma; every cube whose box lies within the running minimum of
+ * x_r (in dta units) is searched, by the same simplex distance as above, and
+ * no other cube can hold a closer point.  D_norm (global mode) and the
+ * cutoff use the reference grid's doses, as for coincident grids. */
+
+typedef struct {
+    int ndim;
+    int64_t n[3];            /* evaluation grid (x, y, z) */
+    double h[3], o[3];       /* evaluation spacing and origin (x, y, z) */
+    const float *ev;
+    double dta;
+} or_egrid;
+
+static double or_grid_cube(const or_egrid *e, const int perms[6][3], int nperm, const int64_t p[3],
+                           double inv_dd, const double *P, double best)
+{
+    const int n = e->ndim, K = n + 1;
+    for (int s = 0; s < nperm; ++s) {
+        double W[4 * OR_MAXD];
+        int64_t q[3] = {p[0], p[1], p[2]};
+        for (int v = 0; v <= n; ++v) {
+            if (v > 0) q[perms[s][v - 1]] += 1;
+            const int64_t lin = (q[2] * e->n[1] + q[1]) * e->n[0] + q[0];
+            double *w = W + (size_t)v * K;
+            for (int a = 0; a < n; ++a) w[a] = (e->o[a] + (double)q[a] * e->h[a]) / e->dta;
+            w[n] = (double)e->ev[lin] * inv_dd;
+        }
+        double d = oracle_simplex_distance(K, n + 1, W, P);
+        if (d < best) best = d;
+    }
+    return best;
+}
+
+/* gamma for the reference voxels listed in idx (all when idx == NULL).
+ * ref: float32 (z, y, x) with ref_shape, ref_spacing, ref_origin in (z, y, x)
+ * order; likewise ev.  2D: the z entries are ignored.  Returns 0 or a
+ * negative code as oracle_gamma. */
+int oracle_gamma_grids(const float *ref, const int64_t ref_shape[3], const double ref_spacing[3],
+                       const double ref_origin[3], const float *ev, const int64_t ev_shape[3],
+                       const double ev_spacing[3], const double ev_origin[3], int ndim,
+                       double dd_frac, double dta_mm, int local, double cutoff_frac,
+                       double dose_norm, const int64_t *idx, int64_t nidx, double *gamma_out,
+                       int threads)
+{
+    if (ndim != 2 && ndim != 3) return -1;
+    if (!(dta_mm > 0) || !(dd_frac > 0)) return -1;
+    int64_t rn[3] = {ref_shape[2], ref_shape[1], ndim == 3 ? ref_shape[0] : 1};
+    or_egrid e;
+    memset(&e, 0, sizeof(e));
+    e.ndim = ndim;
+    e.ev = ev;
+    e.dta = dta_mm;
+    e.n[0] = ev_shape[2]; e.n[1] = ev_shape[1]; e.n[2] = ndim == 3 ? ev_shape[0] : 1;
+    double rh[3], ro[3];
+    for (int a = 0; a < 3; ++a) {
+        const int src = 2 - a;                 /* (z, y, x) -> (x, y, z) */
+        rh[a] = ref_spacing[src];
+        ro[a] = ref_origin[src];
+        e.h[a] = ev_spacing[src];
+        e.o[a] = ev_origin[src];
+    }
+    for (int a = 0; a < ndim; ++a) {
+        if (rn[a] < 1 || e.n[a] < 2) return -2;
+        if (!(rh[a] > 0) || !(e.h[a] > 0)) return -1;
+    }
+    const int64_t NR = rn[0] * rn[1] * rn[2], NE = e.n[0] * e.n[1] * e.n[2];
+    double m = -INFINITY;
+    for (int64_t v = 0; v < NR; ++v) {
+        if (!isfinite(ref[v])) return -3;
+        if (ref[v] > m) m = ref[v];
+    }
+    for (int64_t v = 0; v < NE; ++v)
+        if (!isfinite(ev[v])) return -3;
+    or_ctx c;                                  /* criteria helpers only */
+    memset(&c, 0, sizeof(c));
+    c.ndim = ndim;
+    c.dd_frac = dd_frac;
+    c.local = local;
+    c.cutoff_frac = cutoff_frac;
+    c.d_norm = dose_norm > 0 ? dose_norm : m;
+    if (!local && !(c.d_norm > 0)) return -1;
+    or_make_perms(&c);
+    const int64_t n = idx ? nidx : NR;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t v = idx ? idx[t] : t;
+        if (v < 0 || v >= NR) { bad |= 1; gamma_out[t] = NAN; continue; }
+        const double dr = (double)ref[v];
+        if (!or_evaluated(&c, dr)) { gamma_out[t] = NAN; continue; }
+        const double inv_dd = 1.0 / or_delta_dose(&c, dr);
+        const int64_t ix[3] = {v % rn[0], (v / rn[0]) % rn[1], v / (rn[0] * rn[1])};
+        double x[3] = {0, 0, 0}, P[OR_MAXD];
+        for (int a = 0; a < ndim; ++a) {
+            x[a] = ro[a] + (double)ix[a] * rh[a];
+            P[a] = x[a] / dta_mm;
+        }
+        P[ndim] = dr * inv_dd;
+        /* upper bound: the nearest evaluation node */
+        int64_t nn[3] = {0, 0, 0};
+        for (int a = 0; a < ndim; ++a) {
+            double u = floor((x[a] - e.o[a]) / e.h[a] + 0.5);
+            if (u < 0) u = 0;
+            if (u > (double)(e.n[a] - 1)) u = (double)(e.n[a] - 1);
+            nn[a] = (int64_t)u;
+        }
+        double g2 = 0;
+        for (int a = 0; a < ndim; ++a) {
+            const double d = (e.o[a] + (double)nn[a] * e.h[a] - x[a]) / dta_mm;
+            g2 += d * d;
+        }
+        {
+            const double dd = ((double)ev[(nn[2] * e.n[1] + nn[1]) * e.n[0] + nn[0]] - dr) * inv_dd;
+            g2 += dd * dd;
+        }
+        double g = sqrt(g2);
+        /* every cube whose box is within g of x_r */
+        int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int a = 0; a < ndim; ++a) {
+            const double r = g * dta_mm;
+            int64_t l = (int64_t)floor((x[a] - r - e.o[a]) / e.h[a]) - 1;
+            int64_t u = (int64_t)ceil((x[a] + r - e.o[a]) / e.h[a]) + 1;
+            lo[a] = l < 0 ? 0 : l;
+            hi[a] = u > e.n[a] - 2 ? e.n[a] - 2 : u;
+        }
+        for (int64_t pz = lo[2]; pz <= hi[2]; ++pz)
+            for (int64_t py = lo[1]; py <= hi[1]; ++py)
+                for (int64_t px = lo[0]; px <= hi[0]; ++px) {
+                    const int64_t p[3] = {px, py, pz};
+                    double key2 = 0;
+                    for (int a = 0; a < ndim; ++a) {
+                        const double b0 = e.o[a] + (double)p[a] * e.h[a], b1 = b0 + e.h[a];
+                        const double d = x[a] < b0 ? b0 - x[a] : (x[a] > b1 ? x[a] - b1 : 0.0);
+                        key2 += (d / dta_mm) * (d / dta_mm);
+                    }
+                    if (!(sqrt(key2) < g)) continue;
+                    g = or_grid_cube(&e, c.perms, c.nperm, p, inv_dd, P, g);
+                }
+        gamma_out[t] = g;
+    }
+    return bad ? -1 : 0;
+}
