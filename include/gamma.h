@@ -125,6 +125,24 @@ typedef struct {
 int gamma_create(gamma_handle *out, const float *ref_dev, const float *eval_dev, int ndim,
                  const int64_t shape[3], const float spacing_mm[3], const gamma_criteria *crit);
 
+/* Create a handle for reference and evaluation doses on different grids
+ * (NEXT to Section 3.5: doses interpolated to other resolutions).  Each grid
+ * has its own shape (nz, ny, nx), spacing (hz, hy, hx) and origin (z, y, x) of
+ * its first node, in mm, on the same axes; nz = 1 for 2D.  The evaluation
+ * surface is the Freudenthal interpolant of the evaluation grid (at least 2
+ * nodes per axis); gamma is computed for every reference voxel from its own
+ * position, wherever it falls (inside the evaluation grid or not).  The
+ * dose norm (global mode) and the cutoff use the reference doses.  Both
+ * buffers are borrowed device float32 arrays; gamma_run writes nz*ny*nx
+ * reference-grid values.  Identical geometries give an ordinary handle (the
+ * coincident-grid search).  Options: "timing", "fp64_tau_exp10", "table_cap".
+ * Errors: INVALID_ARG, SHAPE, OOM, CUDA.  Synchronous. */
+int gamma_create_grids(gamma_handle *out, const float *ref_dev, const float *eval_dev, int ndim,
+                       const int64_t ref_shape[3], const float ref_spacing_mm[3],
+                       const float ref_origin_mm[3], const int64_t eval_shape[3],
+                       const float eval_spacing_mm[3], const float eval_origin_mm[3],
+                       const gamma_criteria *crit);
+
 /* Point an existing handle at a new dose pair of the same geometry (device,
  * borrowed).  Errors: INVALID_ARG. */
 int gamma_set_inputs(gamma_handle h, const float *ref_dev, const float *eval_dev);

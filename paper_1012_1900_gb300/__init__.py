@@ -19,7 +19,7 @@ __all__ = [
     "gamma_run", "gamma_run_host", "gamma_pass_rate", "gamma_get_stats", "gamma_get_timings",
     "gamma_set_option",
     "gamma_run_noalloc", "gamma_batch_create", "gamma_batch_run", "gamma_batch_pass_rate",
-    "gamma_batch_get_stats", "gamma_autotune", "gamma_pair_desc", "gamma_destroy",
+    "gamma_batch_get_stats", "gamma_create_grids", "gamma_autotune", "gamma_pair_desc", "gamma_destroy",
     "gamma_model_create", "gamma_model_destroy", "gamma_model_num_params", "gamma_model_get_params",
     "gamma_model_set_params", "gamma_model_forward", "gamma_model_infer", "gamma_model_backward",
     "gamma_model_train_step", "gamma_model_save", "gamma_model_load", "gamma_features",
@@ -89,6 +89,8 @@ def _load():
     f32p = ctypes.POINTER(ctypes.c_float)
     lib.gamma_create.argtypes = [ctypes.POINTER(vp), vp, vp, ctypes.c_int, i64p, f32p,
                                  ctypes.POINTER(gamma_criteria)]
+    lib.gamma_create_grids.argtypes = [ctypes.POINTER(vp), vp, vp, ctypes.c_int, i64p, f32p, f32p,
+                                       i64p, f32p, f32p, ctypes.POINTER(gamma_criteria)]
     lib.gamma_set_inputs.argtypes = [vp, vp, vp]
     lib.gamma_run.argtypes = [vp, vp, vp]
     lib.gamma_run_host.argtypes = [vp, vp, vp, vp, vp]
@@ -179,6 +181,22 @@ def gamma_create(ref_dev, eval_dev, ndim: int, shape: Sequence[int], spacing_mm:
     sp = (ctypes.c_float * 3)(*[float(s) for s in spacing_mm])
     _check(_lib.gamma_create(ctypes.byref(h), _dev_ptr(ref_dev), _dev_ptr(eval_dev), int(ndim),
                              shp, sp, ctypes.byref(crit)), "gamma_create")
+    return h.value
+
+
+def gamma_create_grids(ref_dev, eval_dev, ndim: int, ref_shape: Sequence[int],
+                       ref_spacing_mm: Sequence[float], ref_origin_mm: Sequence[float],
+                       eval_shape: Sequence[int], eval_spacing_mm: Sequence[float],
+                       eval_origin_mm: Sequence[float], crit: gamma_criteria) -> int:
+    """Handle for doses on two different grids (float32 CUDA tensors); every
+    shape / spacing / origin in (z, y, x) order, 1 / 1.0 / 0.0 first for 2D."""
+    h = ctypes.c_void_p()
+    i3 = lambda v: (ctypes.c_int64 * 3)(*[int(s) for s in v])
+    f3 = lambda v: (ctypes.c_float * 3)(*[float(s) for s in v])
+    _check(_lib.gamma_create_grids(ctypes.byref(h), _dev_ptr(ref_dev), _dev_ptr(eval_dev),
+                                   int(ndim), i3(ref_shape), f3(ref_spacing_mm),
+                                   f3(ref_origin_mm), i3(eval_shape), f3(eval_spacing_mm),
+                                   f3(eval_origin_mm), ctypes.byref(crit)), "gamma_create_grids")
     return h.value
 
 

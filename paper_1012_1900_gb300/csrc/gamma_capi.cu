@@ -64,8 +64,16 @@ double axis_gap(int i) { return i >= 0 ? (double)i : (double)(-i - 1); }
 struct BatchState;
 void free_batch(BatchState* b);
 
+// Reference and evaluation on different grids: the launch description and
+// its cell table (device).
+struct GridState {
+    gk::GridProblem G{};
+    TableEntry* table_dev = nullptr;
+};
+
 struct gamma_ctx {
     BatchState* batch = nullptr;      // non-null for batch handles
+    GridState* grids = nullptr;       // non-null for handles over two different grids
     int graph = 1;                    // batch: capture and replay a CUDA graph
     int device = 0;
     int ndim = 3;
@@ -253,6 +261,10 @@ void free_ctx(gamma_ctx* h)
 {
     if (!h) return;
     if (h->batch) free_batch(h->batch);
+    if (h->grids) {
+        cudaFree(h->grids->table_dev);
+        delete h->grids;
+    }
     if (h->own_model) gamma_model_destroy(h->model);
     for (auto& e : h->tev)
         if (e) cudaEventDestroy(e);
@@ -512,6 +524,105 @@ int gamma_create(gamma_handle* out, const float* ref_dev, const float* eval_dev,
     return GAMMA_OK;
 }
 
+int gamma_create_grids(gamma_handle* out, const float* ref_dev, const float* eval_dev, int ndim,
+                       const int64_t ref_shape[3], const float ref_spacing_mm[3],
+                       const float ref_origin_mm[3], const int64_t eval_shape[3],
+                       const float eval_spacing_mm[3], const float eval_origin_mm[3],
+                       const gamma_criteria* crit)
+{
+    if (!out || !ref_dev || !eval_dev || !ref_shape || !ref_spacing_mm || !ref_origin_mm ||
+        !eval_shape || !eval_spacing_mm || !eval_origin_mm)
+        return GAMMA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (int rc = check_criteria(crit)) return rc;
+    if (ndim != 2 && ndim != 3) return GAMMA_ERR_SHAPE;
+    if (ndim == 2 && (ref_shape[0] != 1 || eval_shape[0] != 1)) return GAMMA_ERR_SHAPE;
+    const int first = ndim == 3 ? 0 : 1;
+    bool same = true;
+    for (int a = first; a < 3; ++a) {
+        if (ref_shape[a] < 1 || eval_shape[a] < 2) return GAMMA_ERR_SHAPE;
+        if (ref_shape[a] > (1 << 30) || eval_shape[a] > (1 << 30)) return GAMMA_ERR_SHAPE;
+        if (!(ref_spacing_mm[a] > 0.f) || !std::isfinite(ref_spacing_mm[a]) ||
+            !(eval_spacing_mm[a] > 0.f) || !std::isfinite(eval_spacing_mm[a]) ||
+            !std::isfinite(ref_origin_mm[a]) || !std::isfinite(eval_origin_mm[a]))
+            return GAMMA_ERR_INVALID_ARG;
+        same = same && ref_shape[a] == eval_shape[a] && ref_spacing_mm[a] == eval_spacing_mm[a] &&
+               ref_origin_mm[a] == eval_origin_mm[a];
+    }
+    int64_t nref = 1, neval = 1;
+    for (int a = first; a < 3; ++a) {
+        nref *= ref_shape[a];
+        neval *= eval_shape[a];
+    }
+    if (nref >= (int64_t(1) << 31) || neval >= (int64_t(1) << 31)) return GAMMA_ERR_SHAPE;
+    if (same) return gamma_create(out, ref_dev, eval_dev, ndim, ref_shape, ref_spacing_mm, crit);
+
+    gamma_ctx* h = new (std::nothrow) gamma_ctx();
+    if (!h) return GAMMA_ERR_OOM;
+    auto fail = [&](int code) { free_ctx(h); return code; };
+    h->grids = new (std::nothrow) GridState();
+    if (!h->grids) return fail(GAMMA_ERR_OOM);
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(GAMMA_ERR_CUDA);
+    h->ndim = ndim;
+    h->nz = ndim == 3 ? ref_shape[0] : 1;
+    h->ny = ref_shape[1];
+    h->nx = ref_shape[2];
+    h->nvox = nref;
+    h->crit = *crit;
+    h->ref = ref_dev;
+    h->ev = eval_dev;
+    gk::GridProblem& G = h->grids->G;
+    const double dta = crit->dta_mm;
+    G.ndim = ndim;
+    G.nref = nref;
+    G.neval = neval;
+    for (int a = 0; a < 3; ++a) {
+        const int src = 2 - a;                          // (z, y, x) -> (x, y, z)
+        const bool used = a < ndim;
+        G.rn[a] = used ? (int)ref_shape[src] : 1;
+        G.en[a] = used ? (int)eval_shape[src] : 1;
+        G.rh[a] = used ? ref_spacing_mm[src] / dta : 1.0;
+        G.ro[a] = used ? ref_origin_mm[src] / dta : 0.0;
+        G.eh[a] = used ? eval_spacing_mm[src] / dta : 1.0;
+        G.eo[a] = used ? eval_origin_mm[src] / dta : 0.0;
+        G.mt.hn2[a] = (float)(G.eh[a] * G.eh[a]);
+        G.mtd.hn2[a] = G.eh[a] * G.eh[a];
+    }
+    G.mt.kappa[0] = 0.f;
+    G.mtd.kappa[0] = 0.0;
+    for (int A = 1; A < 8; ++A) {
+        double s = 0;
+        for (int a = 0; a < 3; ++a)
+            if (A & (1 << a)) s += G.mtd.hn2[a];
+        G.mt.kappa[A] = (float)(1.0 / s);
+        G.mtd.kappa[A] = 1.0 / s;
+    }
+    G.dd_frac = crit->dd_frac;
+    G.cutoff_frac = crit->cutoff_frac;
+    G.dose_norm = crit->dose_norm;
+    G.local = crit->mode == GAMMA_LOCAL;
+    std::vector<TableEntry> table;
+    double cover = 0;
+    const double hn[3] = {G.eh[0], G.eh[1], G.eh[2]};
+    if (int rc = gk::build_grid_table(ndim, hn, G.en, h->table_cap, table, cover)) return fail(rc);
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->grids->table_dev, sizeof(TableEntry) * std::max<size_t>(table.size(), 1))) !=
+        cudaSuccess)
+        return fail(cuda_fail(e));
+    if (!table.empty() &&
+        (e = cudaMemcpy(h->grids->table_dev, table.data(), sizeof(TableEntry) * table.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(cuda_fail(e));
+    G.table = h->grids->table_dev;
+    G.ntable = (int)table.size();
+    G.r_cover = std::isinf(cover) ? INFINITY : round_down(cover);
+    for (auto& te : h->tev)
+        if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = cudaMalloc(&h->ctr, sizeof(Counters))) != cudaSuccess) return fail(cuda_fail(e));
+    *out = h;
+    return GAMMA_OK;
+}
+
 int gamma_set_inputs(gamma_handle h, const float* ref_dev, const float* eval_dev)
 {
     if (!h || !ref_dev || !eval_dev || h->own_ref) return GAMMA_ERR_INVALID_ARG;
@@ -526,8 +637,32 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const Problem P = make_problem(h, gamma_out_dev);
     const bool tm = h->timing != 0;
+    if (h->grids) {
+        gk::GridProblem G = h->grids->G;
+        G.ref = h->ref;
+        G.ev = h->ev;
+        G.out = gamma_out_dev;
+        G.ctr = h->ctr;
+        G.tau = (float)h->tau;
+        if (tm) {
+            CK(cudaEventRecord(h->tev[0], s));
+            CK(cudaEventRecord(h->tev[1], s));
+            CK(cudaEventRecord(h->tev[2], s));
+            CK(cudaEventRecord(h->tev[3], s));
+            CK(cudaEventRecord(h->tev[4], s));
+        }
+        CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), s));
+        CK(gk::launch_grids(G, s));
+        if (tm) {
+            CK(cudaEventRecord(h->tev[5], s));
+            CK(cudaEventRecord(h->tev[6], s));
+        }
+        h->last_stream = s;
+        h->ran = true;
+        return GAMMA_OK;
+    }
+    const Problem P = make_problem(h, gamma_out_dev);
     if (tm && !h->ev_h2d) {
         CK(cudaEventRecord(h->tev[0], s));
         CK(cudaEventRecord(h->tev[1], s));
@@ -672,6 +807,31 @@ int gamma_get_timings(gamma_handle h, gamma_timings* out)
 int gamma_set_option(gamma_handle h, const char* key, int64_t value)
 {
     if (!h || !key) return GAMMA_ERR_INVALID_ARG;
+    if (h->grids && !std::strcmp(key, "table_cap")) {
+        // every cell next to the voxel's own (3^n of them) must be in the table
+        if (value < 27 || value > (int64_t(1) << 26)) return GAMMA_ERR_INVALID_ARG;
+        DeviceGuard dg(h->device);
+        if (!dg.ok) return GAMMA_ERR_CUDA;
+        if (h->ran) { CK(cudaStreamSynchronize(h->last_stream)); }
+        gk::GridProblem& G = h->grids->G;
+        std::vector<TableEntry> table;
+        double cover = 0;
+        const double hn[3] = {G.eh[0], G.eh[1], G.eh[2]};
+        if (int rc = gk::build_grid_table(G.ndim, hn, G.en, value, table, cover)) return rc;
+        cudaFree(h->grids->table_dev);
+        h->grids->table_dev = nullptr;
+        CK(cudaMalloc(&h->grids->table_dev, sizeof(TableEntry) * std::max<size_t>(table.size(), 1)));
+        if (!table.empty())
+            CK(cudaMemcpy(h->grids->table_dev, table.data(), sizeof(TableEntry) * table.size(),
+                          cudaMemcpyHostToDevice));
+        G.table = h->grids->table_dev;
+        G.ntable = (int)table.size();
+        G.r_cover = std::isinf(cover) ? INFINITY : round_down(cover);
+        h->table_cap = value;
+        return GAMMA_OK;
+    }
+    if (h->grids && std::strcmp(key, "timing") && std::strcmp(key, "fp64_tau_exp10"))
+        return GAMMA_ERR_INVALID_ARG;                   // the other options tune the coincident-grid search
     if (h->batch) {
         h->batch->dirty = true;
         if (!std::strcmp(key, "graph")) {

@@ -32,9 +32,9 @@ __device__ __forceinline__ bool is_evaluated(const Problem& P, float dr, float t
 // FP64 redo of one cell whose Gram matrices are near singular
 // --------------------------------------------------------------------------
 
-template <int N>
+template <int N, typename C = int>
 __device__ __noinline__ float cell_redo_f64(const float* __restrict__ ev, long long p, long long sy,
-                                            long long sz, uint32_t ok, int cx, int cy, int cz,
+                                            long long sz, uint32_t ok, C cx, C cy, C cz,
                                             double drd, double invd, MetricT<double> mtd,
                                             unsigned int* fp64_counter)
 {

@@ -66,14 +66,16 @@ struct MetricT {
 };
 using Metric = MetricT<float>;
 
-template <int N, typename T>
-__host__ __device__ __forceinline__ void cell_geom(int cx, int cy, int cz, const MetricT<T>& mt,
+// Cell constants for the lower-corner offset c (voxel units from the
+// reference point; integer on a coincident grid, real otherwise).
+template <int N, typename T, typename C>
+__host__ __device__ __forceinline__ void cell_geom(C cx, C cy, C cz, const MetricT<T>& mt,
                                           CellGeom<T>& g)
 {
-    const int c[3] = {cx, cy, cz};
+    const T c[3] = {T(cx), T(cy), T(cz)};
     T t[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int a = 0; a < N; ++a) t[a] = mt.hn2[a] * T(c[a]) * T(c[a]);
+    for (int a = 0; a < N; ++a) t[a] = mt.hn2[a] * c[a] * c[a];
 #pragma unroll
     for (int A = 0; A < 8; ++A) { g.beta[A] = T(0); g.br[A] = T(0); g.tsum[A] = T(0); }
 #pragma unroll
@@ -81,7 +83,7 @@ __host__ __device__ __forceinline__ void cell_geom(int cx, int cy, int cz, const
         T s = T(0);
 #pragma unroll
         for (int a = 0; a < N; ++a)
-            if (A & (1 << a)) s = fma_(mt.hn2[a], T(c[a]), s);
+            if (A & (1 << a)) s = fma_(mt.hn2[a], c[a], s);
         g.beta[A] = -s * mt.kappa[A];
     }
 #pragma unroll
@@ -97,11 +99,11 @@ __host__ __device__ __forceinline__ void cell_geom(int cx, int cy, int cz, const
     for (int a = 0; a < N; ++a)
 #pragma unroll
         for (int b = a + 1; b < N; ++b) {
-            const T dc = T(c[a] - c[b]);
+            const T dc = c[a] - c[b];
             g.br[(1 << a) | (1 << b)] = mt.hn2[a] * mt.hn2[b] * dc * dc * mt.kappa[(1 << a) | (1 << b)];
         }
     if constexpr (N == 3) {
-        const T dxy = T(cx - cy), dxz = T(cx - cz), dyz = T(cy - cz);
+        const T dxy = c[0] - c[1], dxz = c[0] - c[2], dyz = c[1] - c[2];
         T s = mt.hn2[0] * mt.hn2[1] * dxy * dxy;
         s = fma_(mt.hn2[0] * mt.hn2[2], dxz * dxz, s);
         s = fma_(mt.hn2[1] * mt.hn2[2], dyz * dyz, s);

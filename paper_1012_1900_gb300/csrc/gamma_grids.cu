@@ -1,0 +1,274 @@
+// Reference and evaluation doses on different grids (each grid with its own
+// shape, spacing and origin; same axes).  Eq. 1 as for coincident grids: the
+// evaluation surface is the Freudenthal interpolant of the evaluation grid,
+// and each reference voxel searches it from its own position, which is in
+// general not an evaluation node.
+//
+//   k_grid_prepare  max of the reference dose (the global dose norm) and a
+//                   finite check of both grids
+//   k_grid_walk     one thread per reference voxel: the evaluation cell that
+//                   contains the voxel (clamped to the grid), then the cell
+//                   table in key order with the exact stop of A1 step 4b-ii,
+//                   every face of every cell reached (real-valued cell
+//                   offsets; FP64 redo when a Gram matrix is near singular)
+//
+// The table is keyed by the distance between the box of the voxel's cell and
+// the box of the other cell, divided by the DTA: a lower bound on the distance
+// from any point of the first box to any face of the second.  It stays a
+// lower bound for a voxel outside the evaluation grid, whose clamped cell is
+// the grid cell nearest to it: per axis, its distance to any cell is at least
+// that cell's gap to the clamped one.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/gamma.h"
+#include "gamma_cell.cuh"
+#include "gamma_internal.h"
+
+namespace gk {
+
+// --------------------------------------------------------------------------
+// Prepare: dose norm over the reference grid, finite checks
+// --------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_grid_prepare(const __grid_constant__ GridProblem G)
+{
+    float m = -kInf;
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long i = first; i < G.nref; i += stride) {
+        const float r = __ldg(G.ref + i);
+        bad |= !isfinite(r);
+        m = fmaxf(m, r);
+    }
+    for (long long i = first; i < G.neval; i += stride) bad |= !isfinite(__ldg(G.ev + i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    bad = __any_sync(kFull, bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&G.ctr->dnorm_enc, fenc(m));
+        if (bad) atomicOr(&G.ctr->flags, kFlagNonFinite);
+    }
+}
+
+// --------------------------------------------------------------------------
+// The walk
+// --------------------------------------------------------------------------
+
+// Every face of evaluation cell p (its lower corner, grid coordinates) for a
+// reference point at u (evaluation voxel units, real).
+template <int N>
+__device__ __forceinline__ float grid_cell(const GridProblem& G, const int (&p)[3],
+                                           const double (&u)[3], float dr, float inv, float dnorm,
+                                           float best)
+{
+    const long long sy = G.en[0], sz = (long long)G.en[0] * G.en[1];
+    const long long pidx = (long long)p[2] * sz + (long long)p[1] * sy + p[0];
+    const bool ex = p[0] + 1 < G.en[0], ey = p[1] + 1 < G.en[1], ez = N == 3 && p[2] + 1 < G.en[2];
+    float q[8];
+    uint32_t ok = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        q[w] = 0.f;
+        if (w < (1 << N)) {
+            const bool present = (!(w & 1) || ex) && (!(w & 2) || ey) && (!(w & 4) || ez);
+            if (present) {
+                const long long o = pidx + ((w & 1) ? 1 : 0) + ((w & 2) ? sy : 0) + ((w & 4) ? sz : 0);
+                q[w] = (__ldg(G.ev + o) - dr) * inv;
+                ok |= 1u << w;
+            }
+        }
+    }
+    const float cx = (float)((double)p[0] - u[0]), cy = (float)((double)p[1] - u[1]);
+    const float cz = N == 3 ? (float)((double)p[2] - u[2]) : 0.f;
+    CellGeom<float> g;
+    cell_geom<N, float>(cx, cy, cz, G.mt, g);
+    bool ill = false;
+    const float dmax = G.tau > 0.f ? 0.99f * rsqrtf(G.tau) : kInf;
+    float cb = cell_min_d2<N, float>(q, ok, g, G.mt, dmax, kInf, ill);
+    if (ill) ill = cell_gram_ill<N>(q, ok, G.mt.kappa, G.tau);
+    if (ill) {
+        const double drd = dr;
+        const double invd = 1.0 / ((double)G.dd_frac * (G.local ? drd : (double)dnorm));
+        cb = cell_redo_f64<N, double>(G.ev, pidx, sy, sz, ok, (double)p[0] - u[0],
+                                      (double)p[1] - u[1], N == 3 ? (double)p[2] - u[2] : 0.0,
+                                      drd, invd, G.mtd, &G.ctr->fp64_cells);
+    }
+    return fminf(best, cb);
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridProblem G)
+{
+    const float dnorm = G.dose_norm > 0.f ? G.dose_norm : fdec(G.ctr->dnorm_enc);
+    const float thr = G.cutoff_frac * dnorm;
+    const float rc2 = G.r_cover * G.r_cover;
+    unsigned my_eval = 0, my_pass = 0, my_over = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < G.nref; v += stride) {
+        const float dr = __ldg(G.ref + v);
+        if (!(dr >= thr && (!G.local || dr > 0.f))) {
+            G.out[v] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const long long ix[3] = {v % G.rn[0], (v / G.rn[0]) % G.rn[1], v / ((long long)G.rn[0] * G.rn[1])};
+        double u[3] = {0.0, 0.0, 0.0};
+        int c0[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            u[a] = (G.ro[a] + (double)ix[a] * G.rh[a] - G.eo[a]) / G.eh[a];
+            const double f = floor(u[a]);
+            c0[a] = (int)fmin(fmax(f, 0.0), (double)(G.en[a] - 2));
+        }
+        const float dD = G.dd_frac * (G.local ? dr : dnorm);
+        const float inv = 1.0f / dD;
+        float best = kInf;
+        int t = 0;
+        for (; t < G.ntable; ++t) {
+            const TableEntry e = G.table[t];
+            if (e.key * e.key >= best) break;                 // A1 step 4b-ii, exact
+            const int p[3] = {c0[0] + unpack10(e.off, 0), c0[1] + unpack10(e.off, 10),
+                              N == 3 ? c0[2] + unpack10(e.off, 20) : 0};
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < N; ++a) in = in && p[a] >= 0 && p[a] < G.en[a];
+            if (!in) continue;
+            best = grid_cell<N>(G, p, u, dr, inv, dnorm, best);
+        }
+        if (t >= G.ntable && best > rc2) {
+            // past a truncated table: every remaining cell of the search box
+            ++my_over;
+            // the search box, clipped to the grid (so bounded for any best)
+            const float gm = sqrtf(best);
+            int dlo[3] = {0, 0, 0}, dhi[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const float l = gm / (float)G.eh[a] + 2.f;
+                const int lim = l < (float)G.en[a] ? (int)ceilf(l) : G.en[a];
+                dlo[a] = max(-lim, -c0[a]);
+                dhi[a] = min(lim, G.en[a] - 1 - c0[a]);
+            }
+            const float cut = rc2 * 0.99999f;
+            for (int dz = dlo[2]; dz <= dhi[2]; ++dz)
+                for (int dy = dlo[1]; dy <= dhi[1]; ++dy)
+                    for (int dx = dlo[0]; dx <= dhi[0]; ++dx) {
+                        const int d[3] = {dx, dy, dz};
+                        const int p[3] = {c0[0] + dx, c0[1] + dy, c0[2] + dz};
+                        bool in = true;
+                        float k2 = 0.f;
+#pragma unroll
+                        for (int a = 0; a < N; ++a) {
+                            in = in && p[a] >= 0 && p[a] < G.en[a];
+                            const float gap = (float)max(abs(d[a]) - 1, 0) * (float)G.eh[a];
+                            k2 = fmaf(gap, gap, k2);
+                        }
+                        if (!in || k2 < cut || k2 >= best) continue;
+                        best = grid_cell<N>(G, p, u, dr, inv, dnorm, best);
+                    }
+        }
+        const float gam = sqrtf(best);
+        G.out[v] = gam;
+        ++my_eval;
+        my_pass += gam <= 1.f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_eval += __shfl_xor_sync(kFull, my_eval, o);
+        my_pass += __shfl_xor_sync(kFull, my_pass, o);
+        my_over += __shfl_xor_sync(kFull, my_over, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (my_eval) atomicAdd(&G.ctr->n_eval, (unsigned long long)my_eval);
+        if (my_pass) atomicAdd(&G.ctr->n_pass, (unsigned long long)my_pass);
+        if (my_over) atomicAdd(&G.ctr->overflow_count, my_over);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+
+int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
+                     std::vector<TableEntry>& table, double& r_cover)
+{
+    // radius from a ball-volume estimate of about 2 * cap cells
+    const double cellvol = hn[0] * hn[1] * (nd == 3 ? hn[2] : 1.0);
+    double R = nd == 3 ? std::cbrt(2.0 * (double)cap * cellvol * 3.0 / (4.0 * M_PI))
+                       : std::sqrt(2.0 * (double)cap * cellvol / M_PI);
+    bool whole = false, packing = false;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    double diag = 0;
+    for (int a = 0; a < nd; ++a) diag += (double)en[a] * en[a] * hn[a] * hn[a];
+    diag = std::sqrt(diag) + 1.0;
+    if (R > diag) { R = diag; whole = true; }
+    for (int a = 0; a < nd; ++a) {
+        long long l = (long long)std::ceil(R / hn[a]) + 2;
+        l = std::min<long long>(l, en[a]);
+        if (l > 511) { l = 511; packing = true; }
+        lo[a] = -(int)l;
+        hi[a] = (int)l;
+    }
+    struct Tmp { double key; int x, y, z; };
+    std::vector<Tmp> all;
+    try {
+        for (int z = lo[2]; z <= hi[2]; ++z)
+            for (int y = lo[1]; y <= hi[1]; ++y)
+                for (int x = lo[0]; x <= hi[0]; ++x) {
+                    const int c[3] = {x, y, z};
+                    double k2 = 0;
+                    for (int a = 0; a < nd; ++a) {
+                        const double gap = std::max(std::abs(c[a]) - 1, 0) * hn[a];
+                        k2 += gap * gap;
+                    }
+                    const double key = std::sqrt(k2);
+                    if (key < R) all.push_back({key, x, y, z});
+                }
+    } catch (const std::bad_alloc&) {
+        return GAMMA_ERR_OOM;
+    }
+    std::sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
+        if (a.key != b.key) return a.key < b.key;
+        if (a.z != b.z) return a.z < b.z;
+        if (a.y != b.y) return a.y < b.y;
+        return a.x < b.x;
+    });
+    double cover = whole ? INFINITY : R;
+    if (packing) {
+        double m = INFINITY;
+        for (int a = 0; a < nd; ++a) m = std::min(m, 509.0 * hn[a]);
+        cover = std::min(cover, m);
+    }
+    size_t keep = all.size();
+    if ((long long)keep > cap) {
+        keep = (size_t)cap;
+        cover = std::min(cover, all[keep].key);
+    }
+    table.resize(keep);
+    for (size_t i = 0; i < keep; ++i) {
+        table[i].off = pack10(all[i].x, all[i].y, all[i].z);
+        float f = (float)all[i].key;
+        if ((double)f > all[i].key) f = std::nextafterf(f, -INFINITY);
+        table[i].key = f;
+    }
+    r_cover = cover;
+    return GAMMA_OK;
+}
+
+cudaError_t launch_grids(const GridProblem& G, cudaStream_t s)
+{
+    const int sms = device_sm_count();
+    const long long nmax = std::max(G.nref, G.neval);
+    const int gp = (int)std::max<long long>(1, std::min<long long>((nmax + 255) / 256, (long long)sms * 8));
+    k_grid_prepare<<<gp, 256, 0, s>>>(G);
+    const int gw = (int)std::max<long long>(1, (G.nref + 255) / 256);
+    if (G.ndim == 3) k_grid_walk<3><<<gw, 256, 0, s>>>(G);
+    else k_grid_walk<2><<<gw, 256, 0, s>>>(G);
+    return cudaGetLastError();
+}
+
+}  // namespace gk

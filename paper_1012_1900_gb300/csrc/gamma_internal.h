@@ -1,6 +1,7 @@
 // Internal structures shared by the CUDA kernels and the C-ABI layer.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -155,6 +156,31 @@ int shell_tiles(const Problem& P);
 // Learned proposal (gamma_learned.cu).
 bool model_weights(const gamma_model_s* m, MlpWeights* w);
 cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s);
+
+// Reference and evaluation doses on different grids (gamma_grids.cu).
+// Positions and spacings are in DTA units, axes (x, y, z).
+struct GridProblem {
+    const float* ref;
+    const float* ev;
+    float* out;
+    int ndim;
+    int rn[3], en[3];            // reference / evaluation grid sizes (z = 1 in 2D)
+    double ro[3], rh[3];         // reference origin and spacing
+    double eo[3], eh[3];         // evaluation origin and spacing
+    long long nref, neval;
+    Metric mt;                   // evaluation-grid metric (hn = eh)
+    MetricT<double> mtd;
+    float dd_frac, cutoff_frac, dose_norm;
+    int local;
+    float tau;
+    const TableEntry* table;     // keyed by the gap between cell boxes
+    int ntable;
+    float r_cover;
+    Counters* ctr;
+};
+int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
+                     std::vector<TableEntry>& table, double& r_cover);
+cudaError_t launch_grids(const GridProblem& G, cudaStream_t s);
 
 // Paper-design ablation (gamma_paper.cu): one thread per voxel, optionally in
 // DD order, all simplices of every cell reached (closed form or Ju's recursion).
