@@ -71,7 +71,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
-    ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation", "mlp_infer"],
+    ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation", "mlp_infer",
+                                             "grids"],
                     default=None,
                     help="learned: train + evaluate the proposal network (200x200x150 pairs, "
                          "2%%/2mm); batch: 64 uneven pairs batched vs one by one")
@@ -839,8 +840,55 @@ def experiment_mlp_infer(args):
         g.gamma_model_destroy(m)
 
 
+def experiment_grids(args):
+    """Reference and evaluation on different grids (Section 3.5's doses at
+    another resolution): the imrt_160 reference (2.5 mm) against the same
+    phantom sampled at 1.25 mm, then the same evaluation grid shifted by half
+    a fine voxel; voxels/s of the two-grid search, and its error against the
+    oracle on a random sample of reference voxels."""
+    import torch
+    import oracle
+    import paper_1012_1900_gb300 as g
+    oracle.build()
+    ref_pair = synth.workload("imrt_160")
+    fine = synth.make_pair_3d(shape=(240, 320, 320), spacing=(1.25, 1.25, 1.25), seed=0)
+    c = ref_pair.criteria
+    ref = torch.from_numpy(ref_pair.ref).cuda()
+    ev = torch.from_numpy(fine.eval).cuda()
+    out = torch.empty_like(ref)
+    rng = np.random.default_rng(1)
+    rows = []
+    for eo in ((0.0, 0.0, 0.0), (0.625, 0.625, 0.625)):
+        h = g.gamma_create_grids(ref, ev, 3, ref_pair.ref.shape, ref_pair.spacing, (0.0, 0.0, 0.0),
+                                 fine.eval.shape, (1.25, 1.25, 1.25), eo,
+                                 g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm))
+        try:
+            g.gamma_run(h, out)
+            _, n_eval, n_pass = g.gamma_pass_rate(h)
+            ms = _timed_runs(g, h, out, reps=max(args.steps, 3))
+        finally:
+            g.gamma_destroy(h)
+        got = out.cpu().numpy().ravel()
+        ok = np.nonzero(np.isfinite(got))[0]
+        sample = rng.choice(ok, min(2000, ok.size), replace=False)
+        want = oracle.gamma_grids(ref_pair.ref, ref_pair.spacing, (0.0, 0.0, 0.0), fine.eval,
+                                  (1.25, 1.25, 1.25), eo, float(np.float32(c.dd_frac)),
+                                  float(np.float32(c.dta_mm)), cutoff_frac=float(np.float32(c.cutoff_frac)),
+                                  idx=sample)
+        rows.append({"eval_origin_mm": eo, "ms": ms, "voxels_per_s": ref_pair.nvox / (ms / 1000.0),
+                     "evaluated": n_eval, "pass_rate": n_pass / max(n_eval, 1),
+                     "sample": int(sample.size),
+                     "max_abs_err_vs_oracle": float(np.max(np.abs(got[sample] - want)))})
+    print(json.dumps({"experiment": "grids", "reference": "imrt_160 (160x160x120 at 2.5 mm)",
+                      "evaluation": "the same phantom at 1.25 mm (320x320x240)", "rows": rows}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.experiment == "grids":
+        experiment_grids(args)
+        return
     if args.experiment == "mlp_infer":
         experiment_mlp_infer(args)
         return

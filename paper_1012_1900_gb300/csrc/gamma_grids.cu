@@ -61,11 +61,12 @@ __global__ void __launch_bounds__(256) k_grid_prepare(const __grid_constant__ Gr
 // --------------------------------------------------------------------------
 
 // Every face of evaluation cell p (its lower corner, grid coordinates) for a
-// reference point at u (evaluation voxel units, real).
+// reference point at u (evaluation voxel units, real), unless the cell's
+// key and dose range already keep it at least sqrt(best) away.
 template <int N>
 __device__ __forceinline__ float grid_cell(const GridProblem& G, const int (&p)[3],
-                                           const double (&u)[3], float dr, float inv, float dnorm,
-                                           float best)
+                                           const double (&u)[3], float key, float dr, float inv,
+                                           float dnorm, float best)
 {
     const long long sy = G.en[0], sz = (long long)G.en[0] * G.en[1];
     const long long pidx = (long long)p[2] * sz + (long long)p[1] * sy + p[0];
@@ -84,6 +85,15 @@ __device__ __forceinline__ float grid_cell(const GridProblem& G, const int (&p)[
             }
         }
     }
+    float qmin = kInf, qmax = -kInf;
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+        if ((ok >> w) & 1u) {
+            qmin = fminf(qmin, q[w]);
+            qmax = fmaxf(qmax, q[w]);
+        }
+    const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
+    if (fmaf(gap, gap, key * key) >= best) return best;
     const float cx = (float)((double)p[0] - u[0]), cy = (float)((double)p[1] - u[1]);
     const float cz = N == 3 ? (float)((double)p[2] - u[2]) : 0.f;
     CellGeom<float> g;
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
 #pragma unroll
             for (int a = 0; a < N; ++a) in = in && p[a] >= 0 && p[a] < G.en[a];
             if (!in) continue;
-            best = grid_cell<N>(G, p, u, dr, inv, dnorm, best);
+            best = grid_cell<N>(G, p, u, e.key, dr, inv, dnorm, best);
         }
         if (t >= G.ntable && best > rc2) {
             // past a truncated table: every remaining cell of the search box
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
                             k2 = fmaf(gap, gap, k2);
                         }
                         if (!in || k2 < cut || k2 >= best) continue;
-                        best = grid_cell<N>(G, p, u, dr, inv, dnorm, best);
+                        best = grid_cell<N>(G, p, u, sqrtf(k2), dr, inv, dnorm, best);
                     }
         }
         const float gam = sqrtf(best);
