@@ -436,6 +436,16 @@ def run_ours(args, pair, rank, world, local_rank):
                         "k_tail": {"ms": mean_ph["tail_ms"], "cells": tail_cells,
                                    "achieved": tflops(tail_cells, mean_ph["tail_ms"]),
                                    "traffic": traffic[1]}}}
+        # the derived peak, confirmed by a measured FMA loop (outside the timed
+        # region) and restated at the SM clock seen under load
+        probe = g.gamma_measure_fp32_peak()
+        sm_load = clocks.get("sm_mhz")
+        roofline["peak_check"] = {
+            "measured_fma_tflops": probe["tflops"],
+            "measured_over_derived": probe["tflops"] / peak_tflops,
+            "derived_at_load_clock": (n_sm * FP32_LANES_PER_SM * 2 * sm_load * 1e6 / 1e12
+                                      if sm_load else None),
+            "load_clock_mhz": sm_load}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -322,6 +322,16 @@ int gamma_labels(gamma_handle h, const float *gamma_map_dev, const uint32_t *vox
 int gamma_set_model(gamma_handle h, gamma_model m);
 int gamma_load_model(gamma_handle h, const char *path);
 
+/* Measured FP32 fused multiply-add throughput of the current device, the
+ * confirmation of the FP32 peak the search's roofline is quoted against
+ * (SMs x 128 FP32 lanes x 2 FLOP x SM clock).  Every SM runs 2048 threads of
+ * eight independent multiply-add chains; one launch of about a millisecond is
+ * timed with CUDA events on `cuda_stream` after a warm-up launch, best of three.
+ * tflops gets 2 FLOP per FMA over that time, ms (may be NULL) the time of the
+ * best launch.  Allocates nothing; syncs the stream.  Returns
+ * GAMMA_ERR_INVALID_ARG for a NULL tflops, GAMMA_ERR_CUDA on a CUDA failure. */
+int gamma_measure_fp32_peak(double *tflops, double *ms, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *gamma_strerror(int code);
 

@@ -23,7 +23,8 @@ __all__ = [
     "gamma_model_create", "gamma_model_destroy", "gamma_model_num_params", "gamma_model_get_params",
     "gamma_model_set_params", "gamma_model_forward", "gamma_model_infer", "gamma_model_backward",
     "gamma_model_train_step", "gamma_model_save", "gamma_model_load", "gamma_features",
-    "gamma_labels", "gamma_set_model", "gamma_load_model", "gamma_strerror", "gamma_version", "library_path",
+    "gamma_labels", "gamma_set_model", "gamma_load_model", "gamma_measure_fp32_peak", "gamma_strerror",
+    "gamma_version", "library_path",
     "criteria",
     "GLOBAL", "LOCAL",
 ]
@@ -128,6 +129,8 @@ def _load():
     lib.gamma_load_model.argtypes = [vp, ctypes.c_char_p]
     lib.gamma_destroy.argtypes = [vp]
     lib.gamma_destroy.restype = None
+    lib.gamma_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), vp]
     lib.gamma_strerror.argtypes = [ctypes.c_int]
     lib.gamma_strerror.restype = ctypes.c_char_p
     lib.gamma_last_cuda_error.restype = ctypes.c_char_p
@@ -221,6 +224,15 @@ def gamma_run_host(h: int, ref_host, eval_host, gamma_out_host, stream=None) -> 
         return a.ctypes.data
     _check(_lib.gamma_run_host(h, hp(ref_host), hp(eval_host), hp(gamma_out_host),
                                _stream_ptr(stream)), "gamma_run_host")
+
+
+def gamma_measure_fp32_peak(stream=None) -> dict:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s) and the
+    time of the timed launch (ms)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.gamma_measure_fp32_peak(ctypes.byref(t), ctypes.byref(ms), _stream_ptr(stream)),
+           "gamma_measure_fp32_peak")
+    return {"tflops": t.value, "ms": ms.value}
 
 
 def gamma_pass_rate(h: int):

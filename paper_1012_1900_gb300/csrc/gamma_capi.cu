@@ -1153,6 +1153,72 @@ const char* gamma_strerror(int code)
     }
 }
 
+namespace {
+
+__device__ float g_fma_sink;
+
+// FP32 FMA throughput probe: eight independent multiply-add chains per
+// thread, 128 FMAs per chain and round.  With 0 < b < 1 and c > 0 every chain
+// stays positive, so the sum is never stored; the store keeps the chains live.
+__global__ void __launch_bounds__(256) k_fma_probe(float b, float c, int rounds)
+{
+    float a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (float)threadIdx.x * 1e-3f + (float)i;
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = fmaf(a[i], b, c);
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sum += a[i];
+    if (sum < 0.f) g_fma_sink = sum;
+}
+
+struct EventPair {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~EventPair()
+    {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+}  // namespace
+
+int gamma_measure_fp32_peak(double* tflops, double* ms, void* cuda_stream)
+{
+    if (!tflops) return GAMMA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256, rounds = 1000;
+    EventPair ev;
+    CK(cudaEventCreate(&ev.e[0]));
+    CK(cudaEventCreate(&ev.e[1]));
+    k_fma_probe<<<blocks, threads, 0, s>>>(0.999f, 1e-3f, rounds / 10);
+    CK(cudaGetLastError());
+    float best = INFINITY;
+    for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(ev.e[0], s));
+        k_fma_probe<<<blocks, threads, 0, s>>>(0.999f, 1e-3f, rounds);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ev.e[1], s));
+        CK(cudaEventSynchronize(ev.e[1]));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ev.e[0], ev.e[1]));
+        best = std::min(best, t);
+    }
+    const double flop = (double)blocks * threads * rounds * 16.0 * 8.0 * 2.0;
+    *tflops = best > 0.f ? flop / (best * 1e-3) / 1e12 : 0.0;
+    if (ms) *ms = best;
+    return GAMMA_OK;
+}
+
 const char* gamma_last_cuda_error(void) { return g_last_cuda.c_str(); }
 
 const char* gamma_version(void) { return "gamma_gb300 0.1 (sm_103a)"; }

@@ -47,12 +47,19 @@ __global__ void __launch_bounds__(256)
         const long long n4 = P.nvox / 4;
         const float4* r4 = (const float4*)P.ref;
         const float4* e4 = (const float4*)P.ev;
-        for (long long i = first; i < n4; i += stride) {
-            const float4 r = __ldg(r4 + i), e = __ldg(e4 + i);
+        auto take = [&](const float4 r, const float4 e) {
             bad |= !(isfinite(r.x) && isfinite(r.y) && isfinite(r.z) && isfinite(r.w) &&
                      isfinite(e.x) && isfinite(e.y) && isfinite(e.z) && isfinite(e.w));
             m = fmaxf(m, fmaxf(fmaxf(r.x, r.y), fmaxf(r.z, r.w)));
+        };
+        long long i = first;
+        for (; i + stride < n4; i += 2 * stride) {          // four 16-byte reads in flight
+            const float4 ra = __ldg(r4 + i), ea = __ldg(e4 + i);
+            const float4 rb = __ldg(r4 + i + stride), eb = __ldg(e4 + i + stride);
+            take(ra, ea);
+            take(rb, eb);
         }
+        if (i < n4) take(__ldg(r4 + i), __ldg(e4 + i));
         done = n4 * 4;
     }
     for (long long i = done + first; i < P.nvox; i += stride) {
@@ -605,7 +612,7 @@ static int grid_for(long long n, int threads, int cap)
 cudaError_t launch_prepare(const Problem& P, cudaStream_t s)
 {
     const int sms = device_sm_count();
-    k_prepare<false><<<grid_for((P.nvox + 3) / 4, 256, sms * 4), 256, 0, s>>>(P, nullptr);
+    k_prepare<false><<<grid_for((P.nvox + 3) / 4, 256, sms * 8), 256, 0, s>>>(P, nullptr);
     return cudaGetLastError();
 }
 

@@ -353,3 +353,15 @@ def test_imrt_160_2pct2mm_sampled():
 def test_imrt_320_local_sampled():
     p = synth.workload("imrt_320_local")
     _full_size_check(p, p.criteria, 4000, table_cap=1 << 20)
+
+
+def test_fp32_peak_probe_confirms_the_derived_peak():
+    # The search's roofline is quoted against SMs x 128 FP32 lanes x 2 FLOP x
+    # clock; a measured FMA loop must land below that at the 2070 MHz maximum
+    # clock (it cannot beat the lanes) and not far below it.
+    import paper_1012_1900_gb300 as g
+    r = g.gamma_measure_fp32_peak()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = n_sm * 128 * 2 * 2070e6 / 1e12
+    assert 0.5 * derived < r["tflops"] < 1.02 * derived, (r, derived)
+    assert r["ms"] > 0.1
