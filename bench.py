@@ -268,8 +268,8 @@ def shard_pairs(costs, world: int, rank: int):
     return [i for i in range(len(costs)) if owner[i] == rank]
 
 
-SEARCH_SOURCES = ("gamma_kernels.cu", "gamma_face.cuh", "gamma_near.cuh", "gamma_tma.cuh",
-                  "gamma_internal.h")
+SEARCH_SOURCES = ("gamma_kernels.cu", "gamma_cell.cuh", "gamma_face.cuh", "gamma_near.cuh",
+                  "gamma_tma.cuh", "gamma_internal.h")
 
 
 def search_source_hash() -> str:

@@ -47,10 +47,13 @@ __global__ void __launch_bounds__(256) k_grid_prepare(const __grid_constant__ Gr
         m = fmaxf(m, r);
     }
     for (long long i = first; i < G.neval; i += stride) bad |= !isfinite(__ldg(G.ev + i));
+    __shared__ float sh_m[8];                  // one atomic per block
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
-    bad = __any_sync(kFull, bad);
-    if ((threadIdx.x & 31) == 0) {
+    if ((threadIdx.x & 31) == 0) sh_m[threadIdx.x >> 5] = m;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh_m[w]);
         atomicMax(&G.ctr->dnorm_enc, fenc(m));
         if (bad) atomicOr(&G.ctr->flags, kFlagNonFinite);
     }

@@ -67,10 +67,14 @@ __global__ void __launch_bounds__(256)
         bad |= !(isfinite(r) && isfinite(e));
         m = fmaxf(m, r);
     }
+    // one atomic per block: same-address atomics serialise in L2
+    __shared__ float sh_m[8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
-    bad = __any_sync(kFull, bad);
-    if ((threadIdx.x & 31) == 0) {
+    if ((threadIdx.x & 31) == 0) sh_m[threadIdx.x >> 5] = m;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh_m[w]);
         atomicMax(&P.ctr->dnorm_enc, fenc(m));
         if (bad) atomicOr(&P.ctr->flags, kFlagNonFinite);
     }
