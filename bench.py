@@ -756,7 +756,7 @@ def experiment_studies(args):
             grid.append({"dd_pct": dd * 100, "dta_mm": dta, "ms": ms, "sum_gamma3": s3_,
                          "pass_rate": pr, "tail_voxels": st["tail_voxels"]})
     res["table3"] = {"workload": "256x256x144, eval 1.03*D(x-1.5mm)+noise", "points": grid}
-    # ---- NEXT #2: cost-ordered queue against discovery order ----
+    # ---- cost-ordered queue against discovery order ----
     abl = []
     for crit in [(0.01, 3.0), (0.01, 1.0), (0.03, 3.0)]:
         row = {"dd_pct": crit[0] * 100, "dta_mm": crit[1]}

@@ -126,7 +126,7 @@ int gamma_create(gamma_handle *out, const float *ref_dev, const float *eval_dev,
                  const int64_t shape[3], const float spacing_mm[3], const gamma_criteria *crit);
 
 /* Create a handle for reference and evaluation doses on different grids
- * (NEXT to Section 3.5: doses interpolated to other resolutions).  Each grid
+ * (the paper interpolates doses to other resolutions, Section 3).  Each grid
  * has its own shape (nz, ny, nx), spacing (hz, hy, hx) and origin (z, y, x) of
  * its first node, in mm, on the same axes; nz = 1 for 2D.  The evaluation
  * surface is the Freudenthal interpolant of the evaluation grid (at least 2
@@ -156,10 +156,21 @@ int gamma_run(gamma_handle h, float *gamma_out_dev, void *cuda_stream);
 
 /* gamma_run on host buffers: copies ref_host and eval_host (float32, nz*ny*nx
  * each) to the handle's own device buffers, runs, and copies the gamma map
- * back into gamma_out_host, all on `cuda_stream`.  Only for handles created
- * with NULL device inputs.  Stream-ordered like gamma_run: the host buffers
- * must stay valid until the stream reaches the end of the copy (for example
- * until gamma_pass_rate returns).  Errors: INVALID_ARG, CUDA. */
+ * back into gamma_out_host.  Only for handles created with NULL device inputs.
+ * Stream-ordered like gamma_run: the host buffers must stay valid until
+ * `cuda_stream` reaches the end of the run (for example until gamma_pass_rate
+ * returns).
+ * When all three buffers are page-locked and mapped (cudaHostAlloc /
+ * cudaMallocHost / pinned tensors) and option "pipeline" is 1 (default), the
+ * copies overlap the search: the reference dose is copied first and reduced
+ * while the evaluation dose follows in z slabs; the shell runs on each slab as
+ * soon as the slab after it has landed; the map is copied out while the
+ * queued voxels are searched, and a kernel then writes their final values
+ * into gamma_out_host through its mapped address.  That work runs on two
+ * streams the handle owns, ordered after all earlier work on `cuda_stream`,
+ * which in turn waits for it.  Otherwise (pageable buffers, option "timing",
+ * "design" or an attached model) every step runs in order on `cuda_stream`.
+ * Errors: INVALID_ARG, CUDA. */
 int gamma_run_host(gamma_handle h, const float *ref_host, const float *eval_host,
                    float *gamma_out_host, void *cuda_stream);
 
@@ -186,6 +197,8 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *  "sort_tail"        0: process queued voxels in discovery order instead
  *                     of most-expensive-first (ablation)
  *  "timing"           1: record per-phase CUDA events (gamma_get_timings)
+ *  "pipeline"         gamma_run_host on page-locked buffers: 1 overlaps the
+ *                     copies with the search (default), 0 runs in order
  *  "graph"            batch handles: 0 launches directly instead of capturing
  *                     and replaying a CUDA graph
  *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell

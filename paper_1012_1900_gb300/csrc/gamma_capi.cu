@@ -71,6 +71,10 @@ struct GridState {
     TableEntry* table_dev = nullptr;
 };
 
+// Evaluation-dose z slabs of a host-buffer run: the shell starts on a slab
+// while the next ones are still being copied.
+constexpr int kPipeChunks = 8;
+
 struct gamma_ctx {
     BatchState* batch = nullptr;      // non-null for batch handles
     GridState* grids = nullptr;       // non-null for handles over two different grids
@@ -105,6 +109,7 @@ struct gamma_ctx {
     int timing = 0;
     int shell_minblocks = 2;
     int tail_minblocks = 2;
+    int pipeline = 1;        // gamma_run_host: overlap copies and search when the buffers allow
     int design = 0;          // 0: two-phase search; 1 / 2: the paper's A2 with / without DD sort
     int face_eval = 0;       // design 1 / 2: 0 closed-form faces, 1 Ju's recursion
     gk::PaperScratch paper;
@@ -114,6 +119,10 @@ struct gamma_ctx {
     // 4 after order, 5 after tail, 6 after d2h
     cudaEvent_t tev[7] = {};
     bool ev_h2d = false;     // the last run copied inputs from the host
+    // host-buffer pipeline (gamma_run_host): compute and copy-out streams and
+    // the events that order them against the caller's stream
+    cudaStream_t pipe_s[2] = {};
+    cudaEvent_t pipe_ev[kPipeChunks + 5] = {};
     // state
     cudaStream_t last_stream = nullptr;
     bool ran = false;
@@ -268,6 +277,10 @@ void free_ctx(gamma_ctx* h)
     if (h->own_model) gamma_model_destroy(h->model);
     for (auto& e : h->tev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : h->pipe_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto& st : h->pipe_s)
+        if (st) cudaStreamDestroy(st);
     cudaFree(h->table_dev);
     cudaFree(h->ctr);
     cudaFree(h->tail_raw);
@@ -702,6 +715,85 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
     return GAMMA_OK;
 }
 
+namespace {
+
+// Device address of a page-locked, mapped host buffer of `bytes` bytes, or
+// null when either end of it is not such memory.
+void* mapped_host(const void* p, size_t bytes)
+{
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+        cudaPointerGetAttributes(&b, (const char*)p + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer ||
+        (const char*)b.devicePointer != (const char*)a.devicePointer + bytes - 1)
+        return nullptr;
+    return a.devicePointer;
+}
+
+// Host-buffer run with the copies overlapped: the reference dose goes first
+// and its norm is taken while the evaluation dose follows in z slabs; the
+// shell runs on each slab once the slab after it (its halo) has landed; the
+// map is copied out while the queued voxels are searched, and their final
+// values are then written into the host map directly.
+int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_host,
+                       float* gamma_out_host, float* out_mapped, cudaStream_t s)
+{
+    for (auto& st : h->pipe_s)
+        if (!st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto& e : h->pipe_ev)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaStream_t c = h->pipe_s[0], o = h->pipe_s[1];
+    cudaEvent_t* E = h->pipe_ev;     // 0 start, 1 reference in, 2.. slabs in, then shell, out, done
+    cudaEvent_t e_shell = E[2 + kPipeChunks], e_out = E[3 + kPipeChunks], e_done = E[4 + kPipeChunks];
+    const Problem P = make_problem(h, h->own_out);
+    int per_layer = 0, layers = 0, depth = 0;
+    gk::shell_layers(P, &per_layer, &layers, &depth);
+    const int K = std::max(1, std::min(kPipeChunks, layers / 2));
+    const size_t slice = sizeof(float) * (size_t)h->nx * (size_t)h->ny;
+    const size_t bytes = sizeof(float) * (size_t)h->nvox;
+
+    CK(cudaEventRecord(E[0], s));
+    CK(cudaStreamWaitEvent(c, E[0], 0));
+    CK(cudaStreamWaitEvent(o, E[0], 0));
+    CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), c));
+    CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(E[1], s));
+    std::vector<int> l0(K + 1);
+    for (int k = 0; k <= K; ++k) l0[k] = (int)((long long)layers * k / K);
+    for (int k = 0; k < K; ++k) {
+        const int64_t za = (int64_t)l0[k] * depth, zb = std::min<int64_t>((int64_t)l0[k + 1] * depth, h->nz);
+        if (zb > za)
+            CK(cudaMemcpyAsync(h->own_ev + za * (int64_t)h->nx * h->ny, eval_host + za * (int64_t)h->nx * h->ny,
+                               slice * (size_t)(zb - za), cudaMemcpyHostToDevice, s));
+        CK(cudaEventRecord(E[2 + k], s));
+    }
+    CK(cudaStreamWaitEvent(c, E[1], 0));
+    CK(gk::launch_prepare(P, c, 1));
+    for (int k = 0; k < K; ++k) {
+        CK(cudaStreamWaitEvent(c, E[2 + std::min(k + 1, K - 1)], 0));
+        CK(gk::launch_shell_range(P, l0[k] * per_layer, l0[k + 1] * per_layer, c));
+    }
+    CK(gk::launch_prepare(P, c, 2));
+    CK(cudaEventRecord(e_shell, c));
+    CK(cudaStreamWaitEvent(o, e_shell, 0));
+    CK(cudaMemcpyAsync(gamma_out_host, h->own_out, bytes, cudaMemcpyDeviceToHost, o));
+    CK(cudaEventRecord(e_out, o));
+    CK(gk::launch_order_tail(P, c));
+    CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, c));
+    CK(cudaStreamWaitEvent(c, e_out, 0));
+    CK(gk::launch_patch_host(P, out_mapped, c));
+    CK(cudaEventRecord(e_done, c));
+    CK(cudaStreamWaitEvent(s, e_done, 0));
+    h->last_stream = s;
+    h->ran = true;
+    return GAMMA_OK;
+}
+
+}  // namespace
+
 int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host,
                    float* gamma_out_host, void* cuda_stream)
 {
@@ -709,6 +801,14 @@ int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    {
+        const size_t nb = sizeof(float) * (size_t)h->nvox;
+        float* out_mapped = nullptr;
+        if (!h->grids && !h->batch && h->design == 0 && !h->model && !h->timing && h->pipeline &&
+            mapped_host(ref_host, nb) && mapped_host(eval_host, nb) &&
+            (out_mapped = (float*)mapped_host(gamma_out_host, nb)) != nullptr)
+            return run_host_pipelined(h, ref_host, eval_host, gamma_out_host, out_mapped, s);
+    }
     const size_t bytes = sizeof(float) * (size_t)h->nvox;
     const bool tm = h->timing != 0;
     if (tm) CK(cudaEventRecord(h->tev[0], s));
@@ -886,6 +986,11 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
             CK(cudaMalloc(&w.temp, std::max<size_t>(w.temp_bytes, 16)));
         }
         h->design = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "pipeline")) {
+        if (h->batch || value < 0 || value > 1) return GAMMA_ERR_INVALID_ARG;
+        h->pipeline = (int)value;
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "face_eval")) {

@@ -139,8 +139,18 @@ struct BatchGroup {
 };
 
 // Launchers (gamma_kernels.cu).  All are stream-ordered and allocate nothing.
-cudaError_t launch_prepare(const Problem& P, cudaStream_t s);
+// part: 1 = reference dose only (norm, finite check), 2 = evaluation dose only
+// (finite check), 3 = both.
+cudaError_t launch_prepare(const Problem& P, cudaStream_t s, int part = 3);
 cudaError_t launch_shell(const Problem& P, cudaStream_t s);
+// Shell over tiles [tile_first, tile_end).  Tiles run x fastest, then y, then
+// z: shell_layers gives the tiles of one z layer, the number of layers and the
+// voxel depth of a layer, so that a z slab of layers is one tile range.
+cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, cudaStream_t s);
+void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* layer_depth);
+// Final gamma of every queued voxel into a host map, through its
+// device-mapped pointer.
+cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, cudaStream_t s);
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
 cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblocks, cudaStream_t s);
 int device_sm_count();

@@ -33,20 +33,27 @@ namespace gk {
 // k_prepare: dose norm and finite check
 // --------------------------------------------------------------------------
 
+// part: bit 0 = maximum and finite check of the reference dose, bit 1 =
+// finite check of the evaluation dose (a part left out reads as zeros).
 template <bool BATCH>
 __global__ void __launch_bounds__(256)
-    k_prepare(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd)
+    k_prepare(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd, int part)
 {
     const Problem& P = BATCH ? bd->probs[blockIdx.y] : P0;
     float m = -kInf;
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const float* ref = (part & 1) ? P.ref : nullptr;
+    const float* ev = (part & 2) ? P.ev : nullptr;
     long long done = 0;
     if ((((uintptr_t)P.ref | (uintptr_t)P.ev) & 15u) == 0) {      // 16-byte vector reads
         const long long n4 = P.nvox / 4;
-        const float4* r4 = (const float4*)P.ref;
-        const float4* e4 = (const float4*)P.ev;
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4* r4p = (const float4*)ref;
+        const float4* e4p = (const float4*)ev;
+        auto r4 = [&](long long i) { return r4p ? __ldg(r4p + i) : zero4; };
+        auto e4 = [&](long long i) { return e4p ? __ldg(e4p + i) : zero4; };
         auto take = [&](const float4 r, const float4 e) {
             bad |= !(isfinite(r.x) && isfinite(r.y) && isfinite(r.z) && isfinite(r.w) &&
                      isfinite(e.x) && isfinite(e.y) && isfinite(e.z) && isfinite(e.w));
@@ -54,16 +61,16 @@ __global__ void __launch_bounds__(256)
         };
         long long i = first;
         for (; i + stride < n4; i += 2 * stride) {          // four 16-byte reads in flight
-            const float4 ra = __ldg(r4 + i), ea = __ldg(e4 + i);
-            const float4 rb = __ldg(r4 + i + stride), eb = __ldg(e4 + i + stride);
+            const float4 ra = r4(i), ea = e4(i);
+            const float4 rb = r4(i + stride), eb = e4(i + stride);
             take(ra, ea);
             take(rb, eb);
         }
-        if (i < n4) take(__ldg(r4 + i), __ldg(e4 + i));
+        if (i < n4) take(r4(i), e4(i));
         done = n4 * 4;
     }
     for (long long i = done + first; i < P.nvox; i += stride) {
-        const float r = __ldg(P.ref + i), e = __ldg(P.ev + i);
+        const float r = ref ? __ldg(ref + i) : 0.f, e = ev ? __ldg(ev + i) : 0.f;
         bad |= !(isfinite(r) && isfinite(e));
         m = fmaxf(m, r);
     }
@@ -75,7 +82,7 @@ __global__ void __launch_bounds__(256)
     bad = __syncthreads_or(bad);
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh_m[w]);
-        atomicMax(&P.ctr->dnorm_enc, fenc(m));
+        if (part & 1) atomicMax(&P.ctr->dnorm_enc, fenc(m));
         if (bad) atomicOr(&P.ctr->flags, kFlagNonFinite);
     }
 }
@@ -100,7 +107,7 @@ struct ShellTile {
 template <int N, int MINB, bool BATCH>
 __global__ void __launch_bounds__(256, MINB)
     k_shell(const __grid_constant__ Problem P0, const __grid_constant__ CUtensorMap tmap0,
-            int use_tma0, int ntiles, const BatchDesc* __restrict__ bd)
+            int use_tma0, int t_first, int ntiles, const BatchDesc* __restrict__ bd)
 {
     using T = ShellTile<N>;
     __shared__ __align__(128) float tile[2][T::STRIDE];
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(256, MINB)
         if (N == 3) tma_load_3d(tile[b], map, x0 - 4, y0 - 1, z0 - 1, &bar[b]);
         else tma_load_2d(tile[b], map, x0 - 4, y0 - 1, &bar[b]);
     };
-    if (threadIdx.x == 0) issue(blockIdx.x, 0);
+    if (threadIdx.x == 0) issue(t_first + blockIdx.x, 0);
     uint32_t parity = 0;                 // bit b: phase of bar[b] to wait for
     unsigned my_eval = 0, my_pass = 0;
     float my_rmax = 0.f;
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(256, MINB)
         __syncthreads();
     };
 
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    for (int t = t_first + blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
         int pr, lt;
         locate(t, pr, lt);
         if constexpr (BATCH) {
@@ -613,10 +620,10 @@ static int grid_for(long long n, int threads, int cap)
     return (int)b;
 }
 
-cudaError_t launch_prepare(const Problem& P, cudaStream_t s)
+cudaError_t launch_prepare(const Problem& P, cudaStream_t s, int part)
 {
     const int sms = device_sm_count();
-    k_prepare<false><<<grid_for((P.nvox + 3) / 4, 256, sms * 8), 256, 0, s>>>(P, nullptr);
+    k_prepare<false><<<grid_for((P.nvox + 3) / 4, 256, sms * 8), 256, 0, s>>>(P, nullptr, part);
     return cudaGetLastError();
 }
 
@@ -775,29 +782,74 @@ int shell_tiles(const Problem& P)
 // k_shell with its register budget chosen for `per_sm` resident blocks.
 template <int N, bool BATCH>
 static void launch_shell_k(int per_sm, unsigned grid, cudaStream_t s, const Problem& P,
-                           const CUtensorMap& map, int use_tma, int tiles, const BatchDesc* bd)
+                           const CUtensorMap& map, int use_tma, int t_first, int tiles,
+                           const BatchDesc* bd)
 {
     switch (per_sm) {
-    case 1: k_shell<N, 1, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, bd); break;
-    case 2: k_shell<N, 2, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, bd); break;
-    case 3: k_shell<N, 3, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, bd); break;
-    default: k_shell<N, 4, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, tiles, bd); break;
+    case 1: k_shell<N, 1, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, bd); break;
+    case 2: k_shell<N, 2, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, bd); break;
+    case 3: k_shell<N, 3, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, bd); break;
+    default: k_shell<N, 4, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, bd); break;
     }
 }
 
-cudaError_t launch_shell(const Problem& P0, cudaStream_t s)
+void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* layer_depth)
 {
-    const Problem& P = P0;
+    if (P.ndim == 3) {
+        using T = ShellTile<3>;
+        *tiles_per_layer = ((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
+        *layers = (P.nz + T::TZ - 1) / T::TZ;
+        *layer_depth = T::TZ;
+    } else {
+        using T = ShellTile<2>;
+        *tiles_per_layer = ((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
+        *layers = 1;
+        *layer_depth = 1;
+    }
+}
+
+cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, cudaStream_t s)
+{
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     const int use_tma = encode_tile_map(P, &map) ? 1 : 0;
     const int sms = device_sm_count();
     const int per_sm = std::min(4, std::max(1, P.shell_minblocks));
     const int tiles = shell_tiles(P);
+    if (tiles < 0 || tile_first < 0 || tile_end > tiles || tile_first > tile_end)
+        return cudaErrorInvalidValue;
+    if (tile_first == tile_end) return cudaSuccess;
+    const unsigned grid =
+        (unsigned)std::min<long long>(tile_end - tile_first, (long long)sms * per_sm);
+    if (P.ndim == 3)
+        launch_shell_k<3, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, nullptr);
+    else
+        launch_shell_k<2, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shell(const Problem& P, cudaStream_t s)
+{
+    const int tiles = shell_tiles(P);
     if (tiles < 0) return cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
-    if (P.ndim == 3) launch_shell_k<3, false>(per_sm, grid, s, P, map, use_tma, tiles, nullptr);
-    else launch_shell_k<2, false>(per_sm, grid, s, P, map, use_tma, tiles, nullptr);
+    return launch_shell_range(P, 0, tiles, s);
+}
+
+// Copy the final gamma of every queued voxel from the device map into a
+// host map (through its device-mapped pointer) that already holds the rest.
+__global__ void __launch_bounds__(256) k_patch_host(const __grid_constant__ Problem P, float* host_out)
+{
+    const unsigned n = min(P.ctr->tail_count, P.tail_cap);
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned v = P.tail_raw[i];
+        host_out[v] = P.out[v];
+    }
+}
+
+cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, cudaStream_t s)
+{
+    k_patch_host<<<device_sm_count() * 4, 256, 0, s>>>(P, host_out_mapped);
     return cudaGetLastError();
 }
 
@@ -849,7 +901,7 @@ cudaError_t launch_batch_prepare(const BatchGroup& g, cudaStream_t s)
     const int sms = device_sm_count();
     const int bx = grid_for(g.max_nvox, 256, std::max(1, sms * 8 / std::max(1, g.npairs)) + 1);
     Problem dummy{};
-    k_prepare<true><<<dim3(bx, g.npairs), 256, 0, s>>>(dummy, g.desc);
+    k_prepare<true><<<dim3(bx, g.npairs), 256, 0, s>>>(dummy, g.desc, 3);
     return cudaGetLastError();
 }
 
@@ -862,8 +914,8 @@ cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStr
     Problem dummy{};
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
-    if (g.ndim == 3) launch_shell_k<3, true>(per_sm, grid, s, dummy, map, 0, g.total_tiles, g.desc);
-    else launch_shell_k<2, true>(per_sm, grid, s, dummy, map, 0, g.total_tiles, g.desc);
+    if (g.ndim == 3) launch_shell_k<3, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.desc);
+    else launch_shell_k<2, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.desc);
     return cudaGetLastError();
 }
 

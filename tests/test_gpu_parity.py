@@ -273,23 +273,41 @@ def test_repeat_runs_identical_and_counters_reset():
     assert counts[1] == int((~np.isnan(outs[2])).sum())
 
 
-def test_run_host_matches_device_run():
+@pytest.mark.parametrize("name", ["imrt_small", "plane_128"])
+@pytest.mark.parametrize("mode", ["pipelined", "in_order", "pageable"])
+def test_run_host_matches_device_run(name, mode):
+    # Pinned buffers take the overlapped path (z slabs of the evaluation dose,
+    # map copied out during the table walk, queued voxels patched through the
+    # mapped address); option "pipeline" = 0 and pageable arrays run in order.
+    # Every path must give the device run's map bit for bit, on every run.
     import paper_1012_1900_gb300 as g
-    p = synth.workload("imrt_small")
+    p = synth.workload(name)
     crit = synth.Criteria(0.03, 3.0)
     dev_out, dev_counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit)
-    h = g.gamma_create(None, None, 3, p.ref.shape, p.spacing,
+    ndim, shape, sp = _geom(p.ref, p.spacing)
+    h = g.gamma_create(None, None, ndim, shape, sp,
                        g.criteria(crit.dd_frac, crit.dta_mm, cutoff_frac=crit.cutoff_frac))
     try:
-        ref = torch.from_numpy(p.ref).pin_memory()
-        ev = torch.from_numpy(p.eval).pin_memory()
-        out = torch.empty_like(ref).pin_memory()
-        g.gamma_run_host(h, ref, ev, out)
-        counts = g.gamma_pass_rate(h)
+        if mode == "in_order":
+            g.gamma_set_option(h, "pipeline", 0)
+        if mode == "pageable":
+            ref, ev = np.ascontiguousarray(p.ref), np.ascontiguousarray(p.eval)
+            out = np.empty_like(ref)
+            view = lambda: out
+        else:
+            ref = torch.from_numpy(p.ref).pin_memory()
+            ev = torch.from_numpy(p.eval).pin_memory()
+            out = torch.empty_like(ref).pin_memory()
+            view = lambda: out.numpy()
+        for _ in range(3):
+            view()[...] = -7.0
+            g.gamma_run_host(h, ref, ev, out)
+            counts = g.gamma_pass_rate(h)
+            assert np.array_equal(view().astype(np.float64).reshape(dev_out.shape), dev_out,
+                                  equal_nan=True)
+            assert counts == dev_counts
     finally:
         g.gamma_destroy(h)
-    assert np.array_equal(out.numpy().astype(np.float64), dev_out, equal_nan=True)
-    assert counts == dev_counts
 
 
 def test_stats_mode_counts_cells():
