@@ -326,15 +326,15 @@ def run_ours(args, pair, rank, world, local_rank):
     h = g.gamma_create(ref, ev, ndim, shape, spacing, crit)
     tuned = None
     if args.lanes or args.shell_blocks or args.tail_blocks:
-        if args.lanes:
-            g.gamma_set_option(h, "lanes_per_voxel", args.lanes)
-        if args.shell_blocks:
-            g.gamma_set_option(h, "shell_blocks_per_sm", args.shell_blocks)
-        if args.tail_blocks:
-            g.gamma_set_option(h, "tail_blocks_per_sm", args.tail_blocks)
+        launch = {k: v for k, v in (("lanes_per_voxel", args.lanes),
+                                    ("shell_blocks_per_sm", args.shell_blocks),
+                                    ("tail_blocks_per_sm", args.tail_blocks)) if v}
+        for k, v in launch.items():
+            g.gamma_set_option(h, k, v)
     else:
         tuned = g.gamma_autotune(h, out, stream, reps=3)   # setup, not timed
         tuned.pop("ms")
+        launch = dict(tuned)
     g.gamma_set_option(h, "timing", 1)
 
     def barrier():
@@ -376,6 +376,8 @@ def run_ours(args, pair, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         hh = g.gamma_create(None, None, ndim, shape, spacing, crit)
+        for k, v in launch.items():                  # the launch shapes tuned above
+            g.gamma_set_option(hh, k, v)
         try:
             rh = torch.from_numpy(pair.ref).pin_memory()
             eh = torch.from_numpy(pair.eval).pin_memory()

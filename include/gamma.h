@@ -109,6 +109,12 @@ typedef struct {
     float tail_ms;      /* table walk of the queued voxels */
     float d2h_ms;       /* device-to-host copy of the gamma map (gamma_run_host) */
     float total_ms;     /* first to last event */
+    int overlapped;     /* 1: an overlapped gamma_run_host run, whose phases run
+                         * concurrently: every field is then the time from the
+                         * start of the run to the END of that phase (h2d: the
+                         * last input copy; prepare: the reference reduction;
+                         * shell: the last z slab; d2h: the map copy-out;
+                         * total: the final patch of the queued voxels) */
 } gamma_timings;
 
 /* Create a handle for one dose-pair geometry (Algorithm A1 steps 2-3: builds
@@ -161,15 +167,17 @@ int gamma_run(gamma_handle h, float *gamma_out_dev, void *cuda_stream);
  * `cuda_stream` reaches the end of the run (for example until gamma_pass_rate
  * returns).
  * When all three buffers are page-locked and mapped (cudaHostAlloc /
- * cudaMallocHost / pinned tensors) and option "pipeline" is 1 (default), the
+ * cudaMallocHost / pinned tensors) and option "pipeline" is not 0, the
  * copies overlap the search: the reference dose is copied first and reduced
- * while the evaluation dose follows in z slabs; the shell runs on each slab as
- * soon as the slab after it has landed; the map is copied out while the
- * queued voxels are searched, and a kernel then writes their final values
- * into gamma_out_host through its mapped address.  That work runs on two
- * streams the handle owns, ordered after all earlier work on `cuda_stream`,
- * which in turn waits for it.  Otherwise (pageable buffers, option "timing",
- * "design" or an attached model) every step runs in order on `cuda_stream`.
+ * while the evaluation dose follows in z slabs; the shell starts as soon as
+ * the dose norm is known, each of its tiles waiting (bounded) for the slab
+ * that holds the last slice it reads, which a stream write after the slab's
+ * copy announces; the map is copied out while the queued voxels are
+ * searched, and a kernel then writes their final values into gamma_out_host
+ * through its mapped address.  That work runs on two streams the handle
+ * owns, ordered after all earlier work on `cuda_stream`, which in turn waits
+ * for it.  Otherwise (pageable buffers, option "design"
+ * or an attached model) every step runs in order on `cuda_stream`.
  * Errors: INVALID_ARG, CUDA. */
 int gamma_run_host(gamma_handle h, const float *ref_host, const float *eval_host,
                    float *gamma_out_host, void *cuda_stream);
@@ -197,8 +205,10 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *  "sort_tail"        0: process queued voxels in discovery order instead
  *                     of most-expensive-first (ablation)
  *  "timing"           1: record per-phase CUDA events (gamma_get_timings)
- *  "pipeline"         gamma_run_host on page-locked buffers: 1 overlaps the
- *                     copies with the search (default), 0 runs in order
+ *  "pipeline"         gamma_run_host on page-locked buffers: 1 to 8 overlaps
+ *                     the copies with the search, the evaluation dose in that
+ *                     many z slabs (default 4; 1: the shell waits for the
+ *                     whole dose); 0 runs in order
  *  "graph"            batch handles: 0 launches directly instead of capturing
  *                     and replaying a CUDA graph
  *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell

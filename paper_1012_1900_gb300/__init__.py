@@ -53,7 +53,8 @@ class gamma_stats(ctypes.Structure):
 
 class gamma_timings(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in ("h2d_ms", "prepare_ms", "shell_ms", "order_ms",
-                                              "tail_ms", "d2h_ms", "total_ms")]
+                                              "tail_ms", "d2h_ms", "total_ms")] + \
+        [("overlapped", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -73,7 +73,7 @@ struct GridState {
 
 // Evaluation-dose z slabs of a host-buffer run: the shell starts on a slab
 // while the next ones are still being copied.
-constexpr int kPipeChunks = 8;
+constexpr int kPipeChunks = gk::kShellSlots;
 
 struct gamma_ctx {
     BatchState* batch = nullptr;      // non-null for batch handles
@@ -109,7 +109,7 @@ struct gamma_ctx {
     int timing = 0;
     int shell_minblocks = 2;
     int tail_minblocks = 2;
-    int pipeline = 1;        // gamma_run_host: overlap copies and search when the buffers allow
+    int pipeline = 4;        // gamma_run_host: z slabs of the overlapped path (0: run in order)
     int design = 0;          // 0: two-phase search; 1 / 2: the paper's A2 with / without DD sort
     int face_eval = 0;       // design 1 / 2: 0 closed-form faces, 1 Ju's recursion
     gk::PaperScratch paper;
@@ -122,7 +122,11 @@ struct gamma_ctx {
     // host-buffer pipeline (gamma_run_host): compute and copy-out streams and
     // the events that order them against the caller's stream
     cudaStream_t pipe_s[2] = {};
-    cudaEvent_t pipe_ev[kPipeChunks + 5] = {};
+    cudaEvent_t pipe_ev[6] = {};
+    unsigned* slab_flags = nullptr;   // device, kPipeChunks: last run whose slab k landed
+    unsigned epoch = 0;               // number of the current overlapped run
+    cudaEvent_t tev_out = nullptr;    // timing: end of the overlapped map copy-out
+    bool overlapped = false;          // the last run was an overlapped host-buffer run
     // state
     cudaStream_t last_stream = nullptr;
     bool ran = false;
@@ -279,6 +283,8 @@ void free_ctx(gamma_ctx* h)
         if (e) cudaEventDestroy(e);
     for (auto& e : h->pipe_ev)
         if (e) cudaEventDestroy(e);
+    if (h->tev_out) cudaEventDestroy(h->tev_out);
+    cudaFree(h->slab_flags);
     for (auto& st : h->pipe_s)
         if (st) cudaStreamDestroy(st);
     cudaFree(h->table_dev);
@@ -647,6 +653,7 @@ int gamma_set_inputs(gamma_handle h, const float* ref_dev, const float* eval_dev
 int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
 {
     if (!h || !gamma_out_dev) return GAMMA_ERR_INVALID_ARG;
+    h->overlapped = false;
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -733,11 +740,34 @@ void* mapped_host(const void* p, size_t bytes)
     return a.devicePointer;
 }
 
-// Host-buffer run with the copies overlapped: the reference dose goes first
-// and its norm is taken while the evaluation dose follows in z slabs; the
-// shell runs on each slab once the slab after it (its halo) has landed; the
-// map is copied out while the queued voxels are searched, and their final
-// values are then written into the host map directly.
+// Stream write of a 32-bit value into device memory, ordered after the
+// stream's earlier work with a memory fence (driver entry point; null when
+// the driver does not offer it).
+using WriteValueFn = CUresult (*)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+WriteValueFn write_value_fn()
+{
+    static WriteValueFn fn = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (WriteValueFn)p;
+    }
+    return fn;
+}
+
+// Host-buffer run with the copies overlapped.  The reference dose goes first
+// and its norm is taken while the evaluation dose follows in z slabs.  The
+// shell is one launch over every tile that starts once the norm is known: a
+// stream write after each slab's copy raises that slab's flag, and each tile
+// waits (bounded) for the slab holding the last slice its box reads.  The map
+// is copied out while the queued voxels are searched, and their final values
+// are then written into the host map directly.  Without TMA tile loads or
+// the stream write, the shell waits for the whole dose instead.
 int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_host,
                        float* gamma_out_host, float* out_mapped, cudaStream_t s)
 {
@@ -745,50 +775,74 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
         if (!st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     for (auto& e : h->pipe_ev)
         if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (!h->slab_flags) {
+        CK(cudaMalloc(&h->slab_flags, sizeof(unsigned) * kPipeChunks));
+        CK(cudaMemset(h->slab_flags, 0, sizeof(unsigned) * kPipeChunks));
+    }
+    const bool tm = h->timing != 0;
+    if (tm && !h->tev_out) CK(cudaEventCreate(&h->tev_out));
     cudaStream_t c = h->pipe_s[0], o = h->pipe_s[1];
-    cudaEvent_t* E = h->pipe_ev;     // 0 start, 1 reference in, 2.. slabs in, then shell, out, done
-    cudaEvent_t e_shell = E[2 + kPipeChunks], e_out = E[3 + kPipeChunks], e_done = E[4 + kPipeChunks];
+    cudaEvent_t* E = h->pipe_ev;     // start, reference in, evaluation in, shell done, map out, done
     const Problem P = make_problem(h, h->own_out);
     int per_layer = 0, layers = 0, depth = 0;
     gk::shell_layers(P, &per_layer, &layers, &depth);
-    const int K = std::max(1, std::min(kPipeChunks, layers / 2));
+    WriteValueFn wv = write_value_fn();
+    bool gated = h->pipeline > 1 && P.ndim == 3 && layers > 1 && wv && gk::shell_gate_ok(P);
+    const int want = gated ? std::min(h->pipeline, layers) : 1;
+    const int slab_layers = (layers + want - 1) / want;
+    const int64_t slab_depth = (int64_t)slab_layers * depth;           // voxel slices per slab
+    const int K = (int)((h->nz + slab_depth - 1) / slab_depth);
     const size_t slice = sizeof(float) * (size_t)h->nx * (size_t)h->ny;
     const size_t bytes = sizeof(float) * (size_t)h->nvox;
+    const unsigned epoch = ++h->epoch == 0 ? ++h->epoch : h->epoch;    // 0 is the flags' initial value
 
+    if (tm) CK(cudaEventRecord(h->tev[0], s));
     CK(cudaEventRecord(E[0], s));
     CK(cudaStreamWaitEvent(c, E[0], 0));
     CK(cudaStreamWaitEvent(o, E[0], 0));
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), c));
     CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(E[1], s));
-    std::vector<int> l0(K + 1);
-    for (int k = 0; k <= K; ++k) l0[k] = (int)((long long)layers * k / K);
     for (int k = 0; k < K; ++k) {
-        const int64_t za = (int64_t)l0[k] * depth, zb = std::min<int64_t>((int64_t)l0[k + 1] * depth, h->nz);
-        if (zb > za)
-            CK(cudaMemcpyAsync(h->own_ev + za * (int64_t)h->nx * h->ny, eval_host + za * (int64_t)h->nx * h->ny,
-                               slice * (size_t)(zb - za), cudaMemcpyHostToDevice, s));
-        CK(cudaEventRecord(E[2 + k], s));
+        const int64_t za = k * slab_depth, zb = std::min<int64_t>(za + slab_depth, h->nz);
+        const int64_t off = za * h->nx * h->ny;
+        CK(cudaMemcpyAsync(h->own_ev + off, eval_host + off, slice * (size_t)(zb - za),
+                           cudaMemcpyHostToDevice, s));
+        if (gated && wv(s, (CUdeviceptr)(h->slab_flags + k), epoch, 0) != CUDA_SUCCESS)
+            gated = false;           // not offered here: the shell waits for the whole dose
     }
+    CK(cudaEventRecord(E[2], s));
+    if (tm) CK(cudaEventRecord(h->tev[1], s));
     CK(cudaStreamWaitEvent(c, E[1], 0));
     CK(gk::launch_prepare(P, c, 1));
-    for (int k = 0; k < K; ++k) {
-        CK(cudaStreamWaitEvent(c, E[2 + std::min(k + 1, K - 1)], 0));
-        CK(gk::launch_shell_range(P, l0[k] * per_layer, l0[k + 1] * per_layer, c));
+    if (tm) CK(cudaEventRecord(h->tev[2], c));
+    const int tiles = gk::shell_tiles(P);
+    if (gated) {
+        CK(gk::launch_shell_range(P, 0, tiles, 0, gk::SlabGate{h->slab_flags, epoch, (int)slab_depth}, c));
+        CK(cudaStreamWaitEvent(c, E[2], 0));
+    } else {
+        CK(cudaStreamWaitEvent(c, E[2], 0));
+        CK(gk::launch_shell_range(P, 0, tiles, 0, gk::SlabGate{nullptr, 0u, 0}, c));
     }
     CK(gk::launch_prepare(P, c, 2));
-    CK(cudaEventRecord(e_shell, c));
-    CK(cudaStreamWaitEvent(o, e_shell, 0));
+    if (tm) CK(cudaEventRecord(h->tev[3], c));
+    CK(cudaEventRecord(E[3], c));
+    CK(cudaStreamWaitEvent(o, E[3], 0));
     CK(cudaMemcpyAsync(gamma_out_host, h->own_out, bytes, cudaMemcpyDeviceToHost, o));
-    CK(cudaEventRecord(e_out, o));
+    if (tm) CK(cudaEventRecord(h->tev_out, o));
+    CK(cudaEventRecord(E[4], o));
     CK(gk::launch_order_tail(P, c));
+    if (tm) CK(cudaEventRecord(h->tev[4], c));
     CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, c));
-    CK(cudaStreamWaitEvent(c, e_out, 0));
+    if (tm) CK(cudaEventRecord(h->tev[5], c));
+    CK(cudaStreamWaitEvent(c, E[4], 0));
     CK(gk::launch_patch_host(P, out_mapped, c));
-    CK(cudaEventRecord(e_done, c));
-    CK(cudaStreamWaitEvent(s, e_done, 0));
+    if (tm) CK(cudaEventRecord(h->tev[6], c));
+    CK(cudaEventRecord(E[5], c));
+    CK(cudaStreamWaitEvent(s, E[5], 0));
     h->last_stream = s;
     h->ran = true;
+    h->overlapped = true;
     return GAMMA_OK;
 }
 
@@ -804,7 +858,7 @@ int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host
     {
         const size_t nb = sizeof(float) * (size_t)h->nvox;
         float* out_mapped = nullptr;
-        if (!h->grids && !h->batch && h->design == 0 && !h->model && !h->timing && h->pipeline &&
+        if (!h->grids && !h->batch && h->design == 0 && !h->model && h->pipeline &&
             mapped_host(ref_host, nb) && mapped_host(eval_host, nb) &&
             (out_mapped = (float*)mapped_host(gamma_out_host, nb)) != nullptr)
             return run_host_pipelined(h, ref_host, eval_host, gamma_out_host, out_mapped, s);
@@ -892,6 +946,14 @@ int gamma_get_timings(gamma_handle h, gamma_timings* out)
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     CK(cudaStreamSynchronize(h->last_stream));
+    out->overlapped = h->overlapped ? 1 : 0;
+    if (h->overlapped) {             // phase end times from the start of the run
+        float* f[6] = {&out->h2d_ms, &out->prepare_ms, &out->shell_ms, &out->order_ms,
+                       &out->tail_ms, &out->total_ms};
+        for (int i = 0; i < 6; ++i) CK(cudaEventElapsedTime(f[i], h->tev[0], h->tev[i + 1]));
+        CK(cudaEventElapsedTime(&out->d2h_ms, h->tev[0], h->tev_out));
+        return GAMMA_OK;
+    }
     float t[6];
     for (int i = 0; i < 6; ++i) CK(cudaEventElapsedTime(&t[i], h->tev[i], h->tev[i + 1]));
     out->h2d_ms = t[0];
@@ -989,7 +1051,7 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "pipeline")) {
-        if (h->batch || value < 0 || value > 1) return GAMMA_ERR_INVALID_ARG;
+        if (h->batch || value < 0 || value > kPipeChunks) return GAMMA_ERR_INVALID_ARG;
         h->pipeline = (int)value;
         return GAMMA_OK;
     }

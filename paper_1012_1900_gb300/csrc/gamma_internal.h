@@ -13,6 +13,7 @@ struct gamma_model_s;
 namespace gk {
 
 constexpr int kNumBuckets = 32;
+constexpr int kShellSlots = 8;       // shell launches of one run with their own tile counter
 
 // Flags raised by kernels (Counters::flags).
 enum : uint32_t {
@@ -64,6 +65,7 @@ struct Counters {
     unsigned int seed_head;             // work counter of the learned seeding pass
     unsigned int seeded;                // queued voxels the proposal network seeded
     unsigned int seed_improved;         // ... whose bound the seed lowered
+    unsigned int shell_next[kShellSlots];   // tile work counters of the shell launches
     unsigned int hist[kNumBuckets];
     unsigned int cursor[kNumBuckets];
 };
@@ -114,6 +116,16 @@ struct Problem {
     float key0_far2[8];
 };
 
+// Readiness of the evaluation dose by z slab, for a shell launch that starts
+// while the dose is still being copied in: slab k (voxel slices
+// [k * depth, (k + 1) * depth)) has landed once flag[k] has reached epoch.
+// flag == nullptr: the whole dose is present.
+struct SlabGate {
+    const unsigned* flag;
+    unsigned epoch;
+    int depth;
+};
+
 // Device-side description of the pairs of one batched launch group (pairs of
 // the same dimension).  All arrays live in device memory.
 struct BatchDesc {
@@ -146,7 +158,12 @@ cudaError_t launch_shell(const Problem& P, cudaStream_t s);
 // Shell over tiles [tile_first, tile_end).  Tiles run x fastest, then y, then
 // z: shell_layers gives the tiles of one z layer, the number of layers and the
 // voxel depth of a layer, so that a z slab of layers is one tile range.
-cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, cudaStream_t s);
+// Each launch of one run takes its own tile counter, slot 0 .. kShellSlots - 1.
+// A gate makes the launch wait, tile by tile, for the z slabs its tiles read
+// (only with TMA tile loads; false from shell_gate_ok otherwise).
+cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, int slot,
+                               const SlabGate& gate, cudaStream_t s);
+bool shell_gate_ok(const Problem& P);
 void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* layer_depth);
 // Final gamma of every queued voxel into a host map, through its
 // device-mapped pointer.

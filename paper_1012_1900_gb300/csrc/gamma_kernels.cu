@@ -107,7 +107,8 @@ struct ShellTile {
 template <int N, int MINB, bool BATCH>
 __global__ void __launch_bounds__(256, MINB)
     k_shell(const __grid_constant__ Problem P0, const __grid_constant__ CUtensorMap tmap0,
-            int use_tma0, int t_first, int ntiles, const BatchDesc* __restrict__ bd)
+            int use_tma0, int t_first, int ntiles, unsigned* tile_next,
+            const __grid_constant__ SlabGate gate, const BatchDesc* __restrict__ bd)
 {
     using T = ShellTile<N>;
     __shared__ __align__(128) float tile[2][T::STRIDE];
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(256, MINB)
     __shared__ unsigned long long sh_eval, sh_pass;
     __shared__ unsigned int sh_rmax;
     __shared__ __align__(16) Problem sh_P;     // the current pair (batched launches)
+    __shared__ int sh_next[2];                 // the block's next tile, per staging buffer
 
     const int lane = threadIdx.x & 31;
     const int lx = lane, ly = (threadIdx.x >> 5) % T::TY, lz = (threadIdx.x >> 5) / T::TY;
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(256, MINB)
         y0 = ((lt / ntx) % nty) * T::TY;
         z0 = (lt / ntx / nty) * T::TZ;
     };
+    bool gate_failed = false;            // thread 0: a slab wait gave up
     auto issue = [&](int t, int b) {
         if (t >= ntiles) return;
         int pr, lt;
@@ -162,6 +165,15 @@ __global__ void __launch_bounds__(256, MINB)
         const CUtensorMap* map = BATCH ? &bd->maps[pr] : &tmap0;
         int x0, y0, z0;
         tile_origin(Q.nx, Q.ny, lt, x0, y0, z0);
+        if (!BATCH && gate.flag && !gate_failed) {
+            // the box reads slices up to z0 + TZ; slabs land in order
+            const int zlast = min(z0 + T::TZ, Q.nz - 1);
+            if (!flag_wait_bounded(gate.flag + zlast / gate.depth, gate.epoch)) {
+                atomicOr(&Q.ctr->flags, kFlagTimeout);     // the run reports a timeout
+                gate_failed = true;                        // and this block waits no more
+            }
+            fence_async_global();
+        }
         mbar_arrive_expect_tx(&bar[b], T::ELEMS * (uint32_t)sizeof(float));
         if (N == 3) tma_load_3d(tile[b], map, x0 - 4, y0 - 1, z0 - 1, &bar[b]);
         else tma_load_2d(tile[b], map, x0 - 4, y0 - 1, &bar[b]);
@@ -204,7 +216,9 @@ __global__ void __launch_bounds__(256, MINB)
         __syncthreads();
     };
 
-    for (int t = t_first + blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    // Tiles after the first come from a work counter when one is given (the
+    // block that finishes first takes the next tile), else in grid stride.
+    for (int t = t_first + blockIdx.x; t < ntiles; buf ^= 1) {
         int pr, lt;
         locate(t, pr, lt);
         if constexpr (BATCH) {
@@ -233,7 +247,12 @@ __global__ void __launch_bounds__(256, MINB)
         // Every thread waits on the tile's mbarrier itself; a wait that gives
         // up is reported at the end-of-tile barrier, where the block leaves
         // together (the smem reads in between stay in bounds).
-        if (threadIdx.x == 0) issue(t + gridDim.x, buf ^ 1);
+        if (threadIdx.x == 0) {
+            const int nt = tile_next ? t_first + (int)gridDim.x + (int)atomicAdd(tile_next, 1u)
+                                     : t + (int)gridDim.x;
+            sh_next[buf] = nt;                 // read by every thread after this tile's barrier
+            issue(nt, buf ^ 1);
+        }
         bool timed_out = false;
         if (use_tma) {
             timed_out = !mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
@@ -326,6 +345,7 @@ __global__ void __launch_bounds__(256, MINB)
             }
             break;
         }
+        t = sh_next[buf];
     }
     if (!BATCH || cur >= 0) flush(BATCH ? sh_P : P0);
 }
@@ -783,14 +803,20 @@ int shell_tiles(const Problem& P)
 template <int N, bool BATCH>
 static void launch_shell_k(int per_sm, unsigned grid, cudaStream_t s, const Problem& P,
                            const CUtensorMap& map, int use_tma, int t_first, int tiles,
-                           const BatchDesc* bd)
+                           unsigned* next, const SlabGate& gate, const BatchDesc* bd)
 {
     switch (per_sm) {
-    case 1: k_shell<N, 1, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, bd); break;
-    case 2: k_shell<N, 2, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, bd); break;
-    case 3: k_shell<N, 3, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, bd); break;
-    default: k_shell<N, 4, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, bd); break;
+    case 1: k_shell<N, 1, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, next, gate, bd); break;
+    case 2: k_shell<N, 2, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, next, gate, bd); break;
+    case 3: k_shell<N, 3, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, next, gate, bd); break;
+    default: k_shell<N, 4, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, next, gate, bd); break;
     }
+}
+
+bool shell_gate_ok(const Problem& P)
+{
+    CUtensorMap map;
+    return encode_tile_map(P, &map);
 }
 
 void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* layer_depth)
@@ -808,11 +834,14 @@ void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* laye
     }
 }
 
-cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, cudaStream_t s)
+cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, int slot,
+                               const SlabGate& gate, cudaStream_t s)
 {
+    if (slot < 0 || slot >= kShellSlots) return cudaErrorInvalidValue;
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     const int use_tma = encode_tile_map(P, &map) ? 1 : 0;
+    if (gate.flag && (!use_tma || gate.depth <= 0)) return cudaErrorInvalidValue;
     const int sms = device_sm_count();
     const int per_sm = std::min(4, std::max(1, P.shell_minblocks));
     const int tiles = shell_tiles(P);
@@ -821,10 +850,13 @@ cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, c
     if (tile_first == tile_end) return cudaSuccess;
     const unsigned grid =
         (unsigned)std::min<long long>(tile_end - tile_first, (long long)sms * per_sm);
+    unsigned* next = &P.ctr->shell_next[slot];
     if (P.ndim == 3)
-        launch_shell_k<3, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, nullptr);
+        launch_shell_k<3, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, next, gate,
+                                 nullptr);
     else
-        launch_shell_k<2, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, nullptr);
+        launch_shell_k<2, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, next, gate,
+                                 nullptr);
     return cudaGetLastError();
 }
 
@@ -832,7 +864,7 @@ cudaError_t launch_shell(const Problem& P, cudaStream_t s)
 {
     const int tiles = shell_tiles(P);
     if (tiles < 0) return cudaErrorInvalidValue;
-    return launch_shell_range(P, 0, tiles, s);
+    return launch_shell_range(P, 0, tiles, 0, SlabGate{nullptr, 0u, 0}, s);
 }
 
 // Copy the final gamma of every queued voxel from the device map into a
@@ -914,8 +946,10 @@ cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStr
     Problem dummy{};
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
-    if (g.ndim == 3) launch_shell_k<3, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.desc);
-    else launch_shell_k<2, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.desc);
+    if (g.ndim == 3) launch_shell_k<3, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, nullptr,
+                                        SlabGate{nullptr, 0u, 0}, g.desc);
+    else launch_shell_k<2, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, nullptr,
+                                        SlabGate{nullptr, 0u, 0}, g.desc);
     return cudaGetLastError();
 }
 

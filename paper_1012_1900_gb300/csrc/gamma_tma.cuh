@@ -57,6 +57,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// Bounded wait until the 32-bit flag at `f` reaches `epoch` (wrap-around
+// order), read with acquire semantics; false on timeout.  The caller then
+// issues TMA loads of data written before the flag: fence_async_global()
+// orders those async-proxy reads after this acquire.
+__device__ __forceinline__ bool flag_wait_bounded(const unsigned* f, unsigned epoch)
+{
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+        if ((int)(v - epoch) >= 0) return true;
+        __nanosleep(128);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // 2D / 3D tiled TMA loads into shared memory, completing on `bar`.  The
 // innermost coordinate x must be a multiple of 4 (16 bytes of float32).
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,

@@ -274,7 +274,7 @@ def test_repeat_runs_identical_and_counters_reset():
 
 
 @pytest.mark.parametrize("name", ["imrt_small", "plane_128"])
-@pytest.mark.parametrize("mode", ["pipelined", "in_order", "pageable"])
+@pytest.mark.parametrize("mode", ["pipelined", "one_slab", "eight_slabs", "in_order", "pageable"])
 def test_run_host_matches_device_run(name, mode):
     # Pinned buffers take the overlapped path (z slabs of the evaluation dose,
     # map copied out during the table walk, queued voxels patched through the
@@ -288,8 +288,9 @@ def test_run_host_matches_device_run(name, mode):
     h = g.gamma_create(None, None, ndim, shape, sp,
                        g.criteria(crit.dd_frac, crit.dta_mm, cutoff_frac=crit.cutoff_frac))
     try:
-        if mode == "in_order":
-            g.gamma_set_option(h, "pipeline", 0)
+        slabs = {"in_order": 0, "one_slab": 1, "eight_slabs": 8}
+        if mode in slabs:
+            g.gamma_set_option(h, "pipeline", slabs[mode])
         if mode == "pageable":
             ref, ev = np.ascontiguousarray(p.ref), np.ascontiguousarray(p.eval)
             out = np.empty_like(ref)
