@@ -122,7 +122,7 @@ struct gamma_ctx {
     // host-buffer pipeline (gamma_run_host): compute and copy-out streams and
     // the events that order them against the caller's stream
     cudaStream_t pipe_s[2] = {};
-    cudaEvent_t pipe_ev[6] = {};
+    cudaEvent_t pipe_ev[7] = {};
     unsigned* slab_flags = nullptr;   // device, kPipeChunks: last run whose slab k landed
     unsigned epoch = 0;               // number of the current overlapped run
     cudaEvent_t tev_out = nullptr;    // timing: end of the overlapped map copy-out
@@ -760,16 +760,20 @@ WriteValueFn write_value_fn()
     return fn;
 }
 
-// Host-buffer run with the copies overlapped.  The reference dose goes first
-// and its norm is taken while the evaluation dose follows in z slabs.  The
-// shell is one launch over every tile that starts once the norm is known: a
-// stream write after each slab's copy raises that slab's flag, and each tile
-// waits (bounded) for the slab holding the last slice its box reads.  The map
-// is copied out while the queued voxels are searched, and their final values
-// are then written into the host map directly.  Without TMA tile loads or
-// the stream write, the shell waits for the whole dose instead.
-int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_host,
-                       float* gamma_out_host, float* out_mapped, cudaStream_t s)
+// Host-buffer run with the copies overlapped.  The reference dose comes in
+// first: read by a kernel through its mapped address, which takes the dose
+// norm on the way (or, when the buffer is not 16-byte aligned, by the copy
+// engine followed by the norm pass).  The evaluation dose follows in z slabs,
+// alternating between two copy streams.  The shell is one launch that
+// starts once the norm is known: a stream write after each slab's copy
+// raises that slab's flag, and each tile waits (bounded) for the slabs its
+// box reads.  The map is copied out while the queued voxels are searched,
+// and their final values are then written into the host map directly.
+// Without TMA tile loads or the stream write, the shell waits for the whole
+// dose instead.
+int run_host_pipelined(gamma_handle h, const float* ref_host, const float* ref_mapped,
+                       const float* eval_host, float* gamma_out_host, float* out_mapped,
+                       cudaStream_t s)
 {
     for (auto& st : h->pipe_s)
         if (!st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -782,12 +786,14 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
     const bool tm = h->timing != 0;
     if (tm && !h->tev_out) CK(cudaEventCreate(&h->tev_out));
     cudaStream_t c = h->pipe_s[0], o = h->pipe_s[1];
-    cudaEvent_t* E = h->pipe_ev;     // start, reference in, evaluation in, shell done, map out, done
+    // start, reference in, evaluation in (s / o), shell done, map out, done
+    cudaEvent_t* E = h->pipe_ev;
     const Problem P = make_problem(h, h->own_out);
     int per_layer = 0, layers = 0, depth = 0;
     gk::shell_layers(P, &per_layer, &layers, &depth);
     WriteValueFn wv = write_value_fn();
     bool gated = h->pipeline > 1 && P.ndim == 3 && layers > 1 && wv && gk::shell_gate_ok(P);
+    const bool ingest = (((uintptr_t)ref_mapped) & 15u) == 0;
     const int want = gated ? std::min(h->pipeline, layers) : 1;
     const int slab_layers = (layers + want - 1) / want;
     const int64_t slab_depth = (int64_t)slab_layers * depth;           // voxel slices per slab
@@ -801,45 +807,59 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
     CK(cudaStreamWaitEvent(c, E[0], 0));
     CK(cudaStreamWaitEvent(o, E[0], 0));
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), c));
-    CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
-    CK(cudaEventRecord(E[1], s));
+    if (ingest) {
+        CK(gk::launch_ingest_ref(P, ref_mapped, c));
+        CK(cudaEventRecord(E[1], c));
+        CK(cudaStreamWaitEvent(s, E[1], 0));
+    } else {
+        CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
+        CK(cudaEventRecord(E[1], s));
+        CK(cudaStreamWaitEvent(c, E[1], 0));
+        CK(gk::launch_prepare(P, c, 1));
+    }
+    CK(cudaStreamWaitEvent(o, E[1], 0));
     for (int k = 0; k < K; ++k) {
+        cudaStream_t cs = (k & 1) ? o : s;
         const int64_t za = k * slab_depth, zb = std::min<int64_t>(za + slab_depth, h->nz);
         const int64_t off = za * h->nx * h->ny;
         CK(cudaMemcpyAsync(h->own_ev + off, eval_host + off, slice * (size_t)(zb - za),
-                           cudaMemcpyHostToDevice, s));
-        if (gated && wv(s, (CUdeviceptr)(h->slab_flags + k), epoch, 0) != CUDA_SUCCESS)
+                           cudaMemcpyHostToDevice, cs));
+        if (gated && wv(cs, (CUdeviceptr)(h->slab_flags + k), epoch, 0) != CUDA_SUCCESS)
             gated = false;           // not offered here: the shell waits for the whole dose
     }
     CK(cudaEventRecord(E[2], s));
-    if (tm) CK(cudaEventRecord(h->tev[1], s));
-    CK(cudaStreamWaitEvent(c, E[1], 0));
-    CK(gk::launch_prepare(P, c, 1));
+    CK(cudaEventRecord(E[3], o));
+    if (tm) {
+        CK(cudaStreamWaitEvent(s, E[3], 0));
+        CK(cudaEventRecord(h->tev[1], s));
+    }
     if (tm) CK(cudaEventRecord(h->tev[2], c));
     const int tiles = gk::shell_tiles(P);
     if (gated) {
         CK(gk::launch_shell_range(P, 0, tiles, 0, gk::SlabGate{h->slab_flags, epoch, (int)slab_depth}, c));
         CK(cudaStreamWaitEvent(c, E[2], 0));
+        CK(cudaStreamWaitEvent(c, E[3], 0));
     } else {
         CK(cudaStreamWaitEvent(c, E[2], 0));
+        CK(cudaStreamWaitEvent(c, E[3], 0));
         CK(gk::launch_shell_range(P, 0, tiles, 0, gk::SlabGate{nullptr, 0u, 0}, c));
     }
     CK(gk::launch_prepare(P, c, 2));
     if (tm) CK(cudaEventRecord(h->tev[3], c));
-    CK(cudaEventRecord(E[3], c));
-    CK(cudaStreamWaitEvent(o, E[3], 0));
+    CK(cudaEventRecord(E[4], c));
+    CK(cudaStreamWaitEvent(o, E[4], 0));
     CK(cudaMemcpyAsync(gamma_out_host, h->own_out, bytes, cudaMemcpyDeviceToHost, o));
     if (tm) CK(cudaEventRecord(h->tev_out, o));
-    CK(cudaEventRecord(E[4], o));
+    CK(cudaEventRecord(E[5], o));
     CK(gk::launch_order_tail(P, c));
     if (tm) CK(cudaEventRecord(h->tev[4], c));
     CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, c));
     if (tm) CK(cudaEventRecord(h->tev[5], c));
-    CK(cudaStreamWaitEvent(c, E[4], 0));
+    CK(cudaStreamWaitEvent(c, E[5], 0));
     CK(gk::launch_patch_host(P, out_mapped, c));
     if (tm) CK(cudaEventRecord(h->tev[6], c));
-    CK(cudaEventRecord(E[5], c));
-    CK(cudaStreamWaitEvent(s, E[5], 0));
+    CK(cudaEventRecord(E[6], c));
+    CK(cudaStreamWaitEvent(s, E[6], 0));
     h->last_stream = s;
     h->ran = true;
     h->overlapped = true;
@@ -858,10 +878,13 @@ int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host
     {
         const size_t nb = sizeof(float) * (size_t)h->nvox;
         float* out_mapped = nullptr;
+        const float* ref_mapped = nullptr;
         if (!h->grids && !h->batch && h->design == 0 && !h->model && h->pipeline &&
-            mapped_host(ref_host, nb) && mapped_host(eval_host, nb) &&
+            (ref_mapped = (const float*)mapped_host(ref_host, nb)) != nullptr &&
+            mapped_host(eval_host, nb) &&
             (out_mapped = (float*)mapped_host(gamma_out_host, nb)) != nullptr)
-            return run_host_pipelined(h, ref_host, eval_host, gamma_out_host, out_mapped, s);
+            return run_host_pipelined(h, ref_host, ref_mapped, eval_host, gamma_out_host,
+                                      out_mapped, s);
     }
     const size_t bytes = sizeof(float) * (size_t)h->nvox;
     const bool tm = h->timing != 0;
