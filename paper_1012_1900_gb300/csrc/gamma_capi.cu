@@ -123,6 +123,7 @@ struct gamma_ctx {
     // the events that order them against the caller's stream
     cudaStream_t pipe_s[2] = {};
     cudaEvent_t pipe_ev[7] = {};
+    cudaEvent_t slab_ev[kPipeChunks] = {};
     unsigned* slab_flags = nullptr;   // device, kPipeChunks: last run whose slab k landed
     unsigned epoch = 0;               // number of the current overlapped run
     cudaEvent_t tev_out = nullptr;    // timing: end of the overlapped map copy-out
@@ -282,6 +283,8 @@ void free_ctx(gamma_ctx* h)
     for (auto& e : h->tev)
         if (e) cudaEventDestroy(e);
     for (auto& e : h->pipe_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto& e : h->slab_ev)
         if (e) cudaEventDestroy(e);
     if (h->tev_out) cudaEventDestroy(h->tev_out);
     cudaFree(h->slab_flags);
@@ -760,24 +763,23 @@ WriteValueFn write_value_fn()
     return fn;
 }
 
-// Host-buffer run with the copies overlapped.  The reference dose comes in
-// first: read by a kernel through its mapped address, which takes the dose
-// norm on the way (or, when the buffer is not 16-byte aligned, by the copy
-// engine followed by the norm pass).  The evaluation dose follows in z slabs,
-// alternating between two copy streams.  The shell is one launch that
-// starts once the norm is known: a stream write after each slab's copy
-// raises that slab's flag, and each tile waits (bounded) for the slabs its
-// box reads.  The map is copied out while the queued voxels are searched,
+// Host-buffer run with the copies overlapped.  The reference dose is copied
+// first and its norm taken on the compute stream while the evaluation dose
+// follows in z slabs on the same copy stream.  The shell is one launch that
+// starts once the norm is known: once a slab's copy has completed, a stream
+// write on a second stream raises that slab's flag, and each tile waits
+// (bounded) for the slabs its box reads.  The map is copied out while the queued voxels are searched,
 // and their final values are then written into the host map directly.
 // Without TMA tile loads or the stream write, the shell waits for the whole
 // dose instead.
-int run_host_pipelined(gamma_handle h, const float* ref_host, const float* ref_mapped,
-                       const float* eval_host, float* gamma_out_host, float* out_mapped,
-                       cudaStream_t s)
+int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_host,
+                       float* gamma_out_host, float* out_mapped, cudaStream_t s)
 {
     for (auto& st : h->pipe_s)
         if (!st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     for (auto& e : h->pipe_ev)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : h->slab_ev)
         if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (!h->slab_flags) {
         CK(cudaMalloc(&h->slab_flags, sizeof(unsigned) * kPipeChunks));
@@ -793,7 +795,6 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* ref_m
     gk::shell_layers(P, &per_layer, &layers, &depth);
     WriteValueFn wv = write_value_fn();
     bool gated = h->pipeline > 1 && P.ndim == 3 && layers > 1 && wv && gk::shell_gate_ok(P);
-    const bool ingest = (((uintptr_t)ref_mapped) & 15u) == 0;
     const int want = gated ? std::min(h->pipeline, layers) : 1;
     const int slab_layers = (layers + want - 1) / want;
     const int64_t slab_depth = (int64_t)slab_layers * depth;           // voxel slices per slab
@@ -807,32 +808,27 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* ref_m
     CK(cudaStreamWaitEvent(c, E[0], 0));
     CK(cudaStreamWaitEvent(o, E[0], 0));
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), c));
-    if (ingest) {
-        CK(gk::launch_ingest_ref(P, ref_mapped, c));
-        CK(cudaEventRecord(E[1], c));
-        CK(cudaStreamWaitEvent(s, E[1], 0));
-    } else {
-        CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
-        CK(cudaEventRecord(E[1], s));
-        CK(cudaStreamWaitEvent(c, E[1], 0));
-        CK(gk::launch_prepare(P, c, 1));
-    }
-    CK(cudaStreamWaitEvent(o, E[1], 0));
+    CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(E[1], s));
+    CK(cudaStreamWaitEvent(c, E[1], 0));
+    CK(gk::launch_prepare(P, c, 1));
+    // slabs back to back on s; each slab's flag is written on o once the
+    // slab's event has fired, so the copies see no fence between them
     for (int k = 0; k < K; ++k) {
-        cudaStream_t cs = (k & 1) ? o : s;
         const int64_t za = k * slab_depth, zb = std::min<int64_t>(za + slab_depth, h->nz);
         const int64_t off = za * h->nx * h->ny;
         CK(cudaMemcpyAsync(h->own_ev + off, eval_host + off, slice * (size_t)(zb - za),
-                           cudaMemcpyHostToDevice, cs));
-        if (gated && wv(cs, (CUdeviceptr)(h->slab_flags + k), epoch, 0) != CUDA_SUCCESS)
-            gated = false;           // not offered here: the shell waits for the whole dose
+                           cudaMemcpyHostToDevice, s));
+        if (gated) {
+            CK(cudaEventRecord(h->slab_ev[k], s));
+            CK(cudaStreamWaitEvent(o, h->slab_ev[k], 0));
+            if (wv(o, (CUdeviceptr)(h->slab_flags + k), epoch, 0) != CUDA_SUCCESS)
+                gated = false;       // not offered here: the shell waits for the whole dose
+        }
     }
     CK(cudaEventRecord(E[2], s));
     CK(cudaEventRecord(E[3], o));
-    if (tm) {
-        CK(cudaStreamWaitEvent(s, E[3], 0));
-        CK(cudaEventRecord(h->tev[1], s));
-    }
+    if (tm) CK(cudaEventRecord(h->tev[1], s));
     if (tm) CK(cudaEventRecord(h->tev[2], c));
     const int tiles = gk::shell_tiles(P);
     if (gated) {
@@ -878,13 +874,10 @@ int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host
     {
         const size_t nb = sizeof(float) * (size_t)h->nvox;
         float* out_mapped = nullptr;
-        const float* ref_mapped = nullptr;
         if (!h->grids && !h->batch && h->design == 0 && !h->model && h->pipeline &&
-            (ref_mapped = (const float*)mapped_host(ref_host, nb)) != nullptr &&
-            mapped_host(eval_host, nb) &&
+            mapped_host(ref_host, nb) && mapped_host(eval_host, nb) &&
             (out_mapped = (float*)mapped_host(gamma_out_host, nb)) != nullptr)
-            return run_host_pipelined(h, ref_host, ref_mapped, eval_host, gamma_out_host,
-                                      out_mapped, s);
+            return run_host_pipelined(h, ref_host, eval_host, gamma_out_host, out_mapped, s);
     }
     const size_t bytes = sizeof(float) * (size_t)h->nvox;
     const bool tm = h->timing != 0;

@@ -168,9 +168,6 @@ void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* laye
 // Final gamma of every queued voxel into a host map, through its
 // device-mapped pointer.
 cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, cudaStream_t s);
-// Reference dose from a mapped host buffer into P.ref, with the dose norm and
-// the finite check of launch_prepare part 1 (both pointers 16-byte aligned).
-cudaError_t launch_ingest_ref(const Problem& P, const float* ref_host_mapped, cudaStream_t s);
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
 cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblocks, cudaStream_t s);
 int device_sm_count();

@@ -886,63 +886,6 @@ cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, cudaStre
     return cudaGetLastError();
 }
 
-// The reference dose read from a host buffer (through its device-mapped
-// address) into the device buffer P.ref, with its maximum and finite check
-// taken on the way: the copy and the dose-norm pass in one.  Both buffers
-// are 16-byte aligned; nvox need not be a multiple of 4.
-__global__ void __launch_bounds__(256)
-    k_ingest_ref(const __grid_constant__ Problem P, const float* __restrict__ src)
-{
-    float* dst = const_cast<float*>(P.ref);
-    float m = -kInf;
-    bool bad = false;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n4 = P.nvox / 4;
-    const float4* s4 = (const float4*)src;
-    float4* d4 = (float4*)dst;
-    long long i = first;
-    for (; i + stride < n4; i += 2 * stride) {              // two 16-byte reads in flight
-        const float4 a = s4[i], b = s4[i + stride];
-        d4[i] = a;
-        d4[i + stride] = b;
-        bad |= !(isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(a.w) &&
-                 isfinite(b.x) && isfinite(b.y) && isfinite(b.z) && isfinite(b.w));
-        m = fmaxf(m, fmaxf(fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)),
-                           fmaxf(fmaxf(b.x, b.y), fmaxf(b.z, b.w))));
-    }
-    if (i < n4) {
-        const float4 a = s4[i];
-        d4[i] = a;
-        bad |= !(isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(a.w));
-        m = fmaxf(m, fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)));
-    }
-    for (long long j = n4 * 4 + first; j < P.nvox; j += stride) {
-        const float r = src[j];
-        dst[j] = r;
-        bad |= !isfinite(r);
-        m = fmaxf(m, r);
-    }
-    __shared__ float sh_m[8];                  // one atomic per block
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
-    if ((threadIdx.x & 31) == 0) sh_m[threadIdx.x >> 5] = m;
-    bad = __syncthreads_or(bad);
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh_m[w]);
-        atomicMax(&P.ctr->dnorm_enc, fenc(m));
-        if (bad) atomicOr(&P.ctr->flags, kFlagNonFinite);
-    }
-}
-
-cudaError_t launch_ingest_ref(const Problem& P, const float* ref_host_mapped, cudaStream_t s)
-{
-    if (((uintptr_t)P.ref | (uintptr_t)ref_host_mapped) & 15u) return cudaErrorInvalidValue;
-    const int sms = device_sm_count();
-    k_ingest_ref<<<grid_for((P.nvox + 3) / 4, 256, sms * 8), 256, 0, s>>>(P, ref_host_mapped);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s)
 {
     if (!P.sort_tail) return cudaSuccess;
