@@ -114,7 +114,8 @@ typedef struct {
                          * start of the run to the END of that phase (h2d: the
                          * last input copy; prepare: the reference reduction;
                          * shell: the last z slab; d2h: the map copy-out;
-                         * total: the final patch of the queued voxels) */
+                         * total: the final patch of the queued voxels);
+                         * 2: the same, with the shell gated per z slab */
 } gamma_timings;
 
 /* Create a handle for one dose-pair geometry (Algorithm A1 steps 2-3: builds
@@ -221,6 +222,9 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     radix sort by DD, walking the whole cell table with
  *                     every simplex of every cell; 2 the same without the
  *                     sort.  Same results; allocates 16 bytes per voxel.
+ *  "drop_slab_flag"   failure test: k + 1 leaves slab k's readiness flag
+ *                     unwritten in overlapped runs, so that the gated shell's
+ *                     bounded wait gives up (GAMMA_ERR_TIMEOUT); 0 (default)
  *  "face_eval"        design 1 / 2 only: 0 every face in closed form (the
  *                     paper's choice, Section 2.2); 1 the full simplices by
  *                     Ju's recursion (Section 2.1)

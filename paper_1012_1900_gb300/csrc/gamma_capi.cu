@@ -127,7 +127,8 @@ struct gamma_ctx {
     unsigned* slab_flags = nullptr;   // device, kPipeChunks: last run whose slab k landed
     unsigned epoch = 0;               // number of the current overlapped run
     cudaEvent_t tev_out = nullptr;    // timing: end of the overlapped map copy-out
-    bool overlapped = false;          // the last run was an overlapped host-buffer run
+    int overlapped = 0;               // last run: 0 in order, 1 overlapped, 2 overlapped + slab gate
+    int drop_slab_flag = 0;           // test hook: k + 1 leaves slab k's flag unwritten
     // state
     cudaStream_t last_stream = nullptr;
     bool ran = false;
@@ -656,7 +657,7 @@ int gamma_set_inputs(gamma_handle h, const float* ref_dev, const float* eval_dev
 int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
 {
     if (!h || !gamma_out_dev) return GAMMA_ERR_INVALID_ARG;
-    h->overlapped = false;
+    h->overlapped = 0;
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -822,7 +823,8 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
         if (gated) {
             CK(cudaEventRecord(h->slab_ev[k], s));
             CK(cudaStreamWaitEvent(o, h->slab_ev[k], 0));
-            if (wv(o, (CUdeviceptr)(h->slab_flags + k), epoch, 0) != CUDA_SUCCESS)
+            if (h->drop_slab_flag != k + 1 &&
+                wv(o, (CUdeviceptr)(h->slab_flags + k), epoch, 0) != CUDA_SUCCESS)
                 gated = false;       // not offered here: the shell waits for the whole dose
         }
     }
@@ -858,7 +860,7 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
     CK(cudaStreamWaitEvent(s, E[6], 0));
     h->last_stream = s;
     h->ran = true;
-    h->overlapped = true;
+    h->overlapped = gated ? 2 : 1;
     return GAMMA_OK;
 }
 
@@ -962,7 +964,7 @@ int gamma_get_timings(gamma_handle h, gamma_timings* out)
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     CK(cudaStreamSynchronize(h->last_stream));
-    out->overlapped = h->overlapped ? 1 : 0;
+    out->overlapped = h->overlapped;
     if (h->overlapped) {             // phase end times from the start of the run
         float* f[6] = {&out->h2d_ms, &out->prepare_ms, &out->shell_ms, &out->order_ms,
                        &out->tail_ms, &out->total_ms};
@@ -1069,6 +1071,11 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
     if (!std::strcmp(key, "pipeline")) {
         if (h->batch || value < 0 || value > kPipeChunks) return GAMMA_ERR_INVALID_ARG;
         h->pipeline = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "drop_slab_flag")) {
+        if (h->batch || value < 0 || value > kPipeChunks) return GAMMA_ERR_INVALID_ARG;
+        h->drop_slab_flag = (int)value;
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "face_eval")) {

@@ -61,9 +61,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // order), read with acquire semantics; false on timeout.  The caller then
 // issues TMA loads of data written before the flag: fence_async_global()
 // orders those async-proxy reads after this acquire.
+constexpr uint32_t kFlagWaitLimit = 1u << 20;     // about a second of polling
+
 __device__ __forceinline__ bool flag_wait_bounded(const unsigned* f, unsigned epoch)
 {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    for (uint32_t i = 0; i < kFlagWaitLimit; ++i) {
         unsigned v;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
         if ((int)(v - epoch) >= 0) return true;

@@ -384,3 +384,38 @@ def test_fp32_peak_probe_confirms_the_derived_peak():
     derived = n_sm * 128 * 2 * 2070e6 / 1e12
     assert 0.5 * derived < r["tflops"] < 1.02 * derived, (r, derived)
     assert r["ms"] > 0.1
+
+
+def test_slab_gate_timeout_is_reported_and_the_next_run_recovers():
+    # Failure made on the host: the readiness flag of one evaluation-dose slab
+    # is never written, so the gated shell's bounded wait gives up.  The run
+    # must report GAMMA_ERR_TIMEOUT (not hang or fault), and the same handle's
+    # next run must be exact again.
+    import paper_1012_1900_gb300 as g
+    p = synth.workload("imrt_small")
+    crit = synth.Criteria(0.03, 3.0)
+    dev_out, dev_counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit)
+    h = g.gamma_create(None, None, 3, p.ref.shape, p.spacing,
+                       g.criteria(crit.dd_frac, crit.dta_mm, cutoff_frac=crit.cutoff_frac))
+    try:
+        ref = torch.from_numpy(p.ref).pin_memory()
+        ev = torch.from_numpy(p.eval).pin_memory()
+        out = torch.empty_like(ref).pin_memory()
+        g.gamma_set_option(h, "timing", 1)
+        g.gamma_set_option(h, "pipeline", 4)
+        g.gamma_run_host(h, ref, ev, out)
+        g.gamma_pass_rate(h)
+        if g.gamma_get_timings(h)["overlapped"] != 2:
+            pytest.skip("the slab gate is not available on this device")
+        g.gamma_set_option(h, "drop_slab_flag", 2)
+        g.gamma_run_host(h, ref, ev, out)
+        with pytest.raises(g.GammaError) as err:
+            g.gamma_pass_rate(h)
+        assert err.value.code == -6                      # GAMMA_ERR_TIMEOUT
+        g.gamma_set_option(h, "drop_slab_flag", 0)
+        out.numpy()[...] = -7.0
+        g.gamma_run_host(h, ref, ev, out)
+        assert g.gamma_pass_rate(h) == dev_counts
+        assert np.array_equal(out.numpy().astype(np.float64), dev_out, equal_nan=True)
+    finally:
+        g.gamma_destroy(h)
