@@ -222,15 +222,6 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     radix sort by DD, walking the whole cell table with
  *                     every simplex of every cell; 2 the same without the
  *                     sort.  Same results; allocates 16 bytes per voxel.
- *  "tail_mode"        table walk of the queued voxels: 1 (default) a
- *                     screening walk lists the cells that pass the key and
- *                     dose-gap bounds, lowering each voxel's bound by the
- *                     cells' vertex distances, then one thread evaluates each
- *                     listed cell; 0 the lanes that reach a cell evaluate it
- *                     (also what batches use).  Same results.
- *  "walk_candidates"  tail_mode 1: cells the list may hold, 1 up to twice
- *                     the voxels (at least 2^16, at most 2^24; the default);
- *                     voxels whose cells do not fit take the mode-0 walk
  *  "drop_slab_flag"   failure test: k + 1 leaves slab k's readiness flag
  *                     unwritten in overlapped runs, so that the gated shell's
  *                     bounded wait gives up (GAMMA_ERR_TIMEOUT); 0 (default)

@@ -101,12 +101,6 @@ struct gamma_ctx {
     unsigned char* tail_bucket = nullptr;
     unsigned* tail_sorted = nullptr;
     unsigned tail_cap = 0;
-    // screen-and-evaluate walk: candidate cells, voxels left to the full walk
-    uint2* cand = nullptr;
-    unsigned cand_cap = 0;            // allocated entries
-    unsigned cand_limit = 0;          // entries a run may use (<= cand_cap; option "walk_candidates")
-    unsigned* retry_list = nullptr;
-    unsigned* retry_mark = nullptr;
     // options
     int lanes = 8;
     double tau = 1e-6;
@@ -116,7 +110,6 @@ struct gamma_ctx {
     int shell_minblocks = 2;
     int tail_minblocks = 2;
     int pipeline = 4;        // gamma_run_host: z slabs of the overlapped path (0: run in order)
-    int tail_mode = 1;       // table walk: 0 walk and evaluate; 1 screen, then evaluate per cell
     int design = 0;          // 0: two-phase search; 1 / 2: the paper's A2 with / without DD sort
     int face_eval = 0;       // design 1 / 2: 0 closed-form faces, 1 Ju's recursion
     gk::PaperScratch paper;
@@ -276,10 +269,6 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.tail_sorted = h->tail_sorted;
     P.sort_tail = h->sort_tail;
     P.shell_minblocks = h->shell_minblocks;
-    P.cand = h->cand;
-    P.cand_cap = h->cand_limit;
-    P.retry_list = h->retry_list;
-    P.retry_mark = h->retry_mark;
     return P;
 }
 
@@ -307,9 +296,6 @@ void free_ctx(gamma_ctx* h)
     cudaFree(h->tail_raw);
     cudaFree(h->tail_bucket);
     cudaFree(h->tail_sorted);
-    cudaFree(h->cand);
-    cudaFree(h->retry_list);
-    cudaFree(h->retry_mark);
     cudaFree(h->own_ref);
     cudaFree(h->own_ev);
     cudaFree(h->own_out);
@@ -550,12 +536,6 @@ int gamma_create(gamma_handle* out, const float* ref_dev, const float* eval_dev,
     if ((e = cudaMalloc(&h->tail_raw, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = cudaMalloc(&h->tail_sorted, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = cudaMalloc(&h->tail_bucket, nvox)) != cudaSuccess) return fail(cuda_fail(e));
-    // candidate cells of the screening walk: twice the voxels, within [2^16, 2^24]
-    h->cand_cap = (unsigned)std::min<int64_t>(std::max<int64_t>(2 * nvox, 1 << 16), 1 << 24);
-    if ((e = cudaMalloc(&h->cand, sizeof(uint2) * h->cand_cap)) != cudaSuccess) return fail(cuda_fail(e));
-    h->cand_limit = h->cand_cap;
-    if ((e = cudaMalloc(&h->retry_list, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
-    if ((e = cudaMalloc(&h->retry_mark, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     if (!ref_dev) {
         if ((e = cudaMalloc(&h->own_ref, sizeof(float) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
         if ((e = cudaMalloc(&h->own_ev, sizeof(float) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
@@ -736,7 +716,7 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     CK(gk::launch_order_tail(P, s));
     if (tm) CK(cudaEventRecord(h->tev[4], s));
-    CK(gk::launch_walk(P, h->tail_mode, h->lanes, h->tail_minblocks, s));
+    CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, s));
     if (tm) {
         CK(cudaEventRecord(h->tev[5], s));
         if (!h->ev_h2d) CK(cudaEventRecord(h->tev[6], s));
@@ -871,7 +851,7 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
     CK(cudaEventRecord(E[5], o));
     CK(gk::launch_order_tail(P, c));
     if (tm) CK(cudaEventRecord(h->tev[4], c));
-    CK(gk::launch_walk(P, h->tail_mode, h->lanes, h->tail_minblocks, c));
+    CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, c));
     if (tm) CK(cudaEventRecord(h->tev[5], c));
     CK(cudaStreamWaitEvent(c, E[5], 0));
     CK(gk::launch_patch_host(P, out_mapped, c));
@@ -1093,16 +1073,6 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         h->pipeline = (int)value;
         return GAMMA_OK;
     }
-    if (!std::strcmp(key, "tail_mode")) {
-        if (h->batch || value < 0 || value > 1 || (value == 1 && !h->cand)) return GAMMA_ERR_INVALID_ARG;
-        h->tail_mode = (int)value;
-        return GAMMA_OK;
-    }
-    if (!std::strcmp(key, "walk_candidates")) {
-        if (h->batch || !h->cand || value < 1 || value > (int64_t)h->cand_cap) return GAMMA_ERR_INVALID_ARG;
-        h->cand_limit = (unsigned)value;
-        return GAMMA_OK;
-    }
     if (!std::strcmp(key, "drop_slab_flag")) {
         if (h->batch || value < 0 || value > kPipeChunks) return GAMMA_ERR_INVALID_ARG;
         h->drop_slab_flag = (int)value;
@@ -1171,13 +1141,6 @@ int gamma_batch_create(gamma_handle* out, int n_pairs, const gamma_pair_desc* pa
             return fail(rc);
         cudaFree(c->ctr);                        // counters live in one shared array
         c->ctr = b->ctrs + i;
-        cudaFree(c->cand);                       // batches walk with k_tail
-        cudaFree(c->retry_list);
-        cudaFree(c->retry_mark);
-        c->cand = nullptr;
-        c->retry_list = c->retry_mark = nullptr;
-        c->cand_cap = 0;
-        c->tail_mode = 0;
         b->pairs[i] = c;
         b->outs[i] = d.gamma_out_dev;
         b->members[d.ndim == 2 ? 0 : 1].push_back(i);

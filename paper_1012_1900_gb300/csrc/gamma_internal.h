@@ -66,10 +66,6 @@ struct Counters {
     unsigned int seeded;                // queued voxels the proposal network seeded
     unsigned int seed_improved;         // ... whose bound the seed lowered
     unsigned int shell_next[kShellSlots];   // tile work counters of the shell launches
-    unsigned int screen_head;           // work counter of the screening walk
-    unsigned int cand_count;            // candidate cells the screening walk found
-    unsigned int retry_count;           // queued voxels left to the full walk
-    unsigned int retry_head;            // work counter of that walk
     unsigned int hist[kNumBuckets];
     unsigned int cursor[kNumBuckets];
 };
@@ -118,18 +114,6 @@ struct Problem {
     // squared spatial distance from the voxel to the faces of key-0 cell S
     // (lower corner at -S) that do not contain it, rounded down; +inf for S = 0
     float key0_far2[8];
-    // screen-and-evaluate walk (launch_walk mode 1): candidate (queue item,
-    // table index) pairs, and the queued voxels left to the full walk (the
-    // candidate list ran full, or the walk ran past a truncated table)
-    uint2* cand;
-    unsigned cand_cap;
-    unsigned* retry_list;        // [tail_cap] voxels
-    unsigned* retry_mark;        // [tail_cap] per queue item: 1 = left to the full walk
-    // full walk over another list (k_tail, single pair): the list, its length
-    // and its work counter; null: the cost-ordered queue
-    const unsigned* walk_list;
-    const unsigned* walk_count;
-    unsigned* walk_head;
 };
 
 // Readiness of the evaluation dose by z slab, for a shell launch that starts
@@ -186,14 +170,6 @@ void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* laye
 cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, cudaStream_t s);
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
 cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblocks, cudaStream_t s);
-// The table walk of the queued voxels.  mode 0: k_tail, G lanes walk a voxel
-// and evaluate the cells they reach.  mode 1: a screening walk (G lanes per
-// voxel, cell bounds and vertex distances only) lists the candidate cells,
-// one thread per candidate evaluates it, a pass writes gamma, and k_tail
-// finishes the voxels left over.  Mode 1 needs P.cand, P.retry_list and
-// P.retry_mark.
-cudaError_t launch_walk(const Problem& P, int mode, int lanes_per_voxel, int tail_minblocks,
-                        cudaStream_t s);
 int device_sm_count();
 
 // Host-side constants a Problem needs before it is uploaded for a batch.

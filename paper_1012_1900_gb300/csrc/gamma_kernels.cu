@@ -490,10 +490,9 @@ __global__ void __launch_bounds__(256, MINB)
     const int gl = lane & (G - 1);
     const int gbase = lane & ~(G - 1);
     const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
-    const unsigned total =
-        BATCH ? bd->item_start[kNumBuckets * bd->npairs]
-              : min(P0.walk_count ? *P0.walk_count : P0.ctr->tail_count, P0.tail_cap);
-    unsigned* head = BATCH ? bd->head : (P0.walk_head ? P0.walk_head : &P0.ctr->head);
+    const unsigned total = BATCH ? bd->item_start[kNumBuckets * bd->npairs]
+                                 : min(P0.ctr->tail_count, P0.tail_cap);
+    unsigned* head = BATCH ? bd->head : &P0.ctr->head;
     unsigned int my_eval = 0, my_pass = 0, my_over = 0;
     int my_pair = -1;          // batched: pair whose counts my_* hold
     TailStats st;
@@ -523,8 +522,7 @@ __global__ void __launch_bounds__(256, MINB)
                 my_pair = pr;
             }
         } else {
-            v = P0.walk_list ? P0.walk_list[item]
-                             : (P0.sort_tail ? P0.tail_sorted[item] : P0.tail_raw[item]);
+            v = P0.sort_tail ? P0.tail_sorted[item] : P0.tail_raw[item];
         }
         const Problem& P = BATCH ? bd->probs[pr] : P0;
         const float dnorm = resolve_dnorm(P);
@@ -620,219 +618,6 @@ __global__ void __launch_bounds__(256, MINB)
                 atomicAdd(&P.ctr->cells_keyed, st.keyed);
             }
         }
-    }
-}
-
-// --------------------------------------------------------------------------
-// Screen-and-evaluate table walk (launch_walk mode 1)
-// --------------------------------------------------------------------------
-//
-// The walk of k_tail evaluates a cell in the lanes that reach it, so a warp
-// runs the evaluation whenever any of its lanes holds a cell that passed the
-// dose-gap bound (about half its lanes on the benchmark workload).  Mode 1
-// splits it.  k_screen walks the table per queued voxel exactly like k_tail
-// (same keys, same exact stop, same dose-gap bound), but instead of
-// evaluating a surviving cell it lists it as a candidate and lowers the
-// voxel's bound by the cell's vertex distances (vertices are points of the
-// surface, so the bound stays an upper bound of gamma^2 that some surface
-// point attains).  k_eval then evaluates one candidate per thread and lowers
-// the voxel's gamma^2 with an atomic minimum.  Every cell that could hold a
-// face closer than the final value was listed: its key^2 + gap^2 lies below
-// that value, which is at most the bound at the time the cell was reached.
-
-constexpr int kStageCells = 32;          // candidates a lane group stages before a flush
-
-template <int N, int G>
-__global__ void __launch_bounds__(256)
-    k_screen(const __grid_constant__ Problem P)
-{
-    __shared__ uint2 stage[256 / G][kStageCells];
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (G - 1);
-    const int gbase = lane & ~(G - 1);
-    const int grp = threadIdx.x / G;
-    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
-    const unsigned total = min(P.ctr->tail_count, P.tail_cap);
-    const unsigned* list = P.sort_tail ? P.tail_sorted : P.tail_raw;
-    const float dnorm = resolve_dnorm(P);
-    const float rc2 = P.r_cover * P.r_cover;
-    unsigned staged = 0;                  // uniform over the group
-    unsigned long long keyed = 0, pruned = 0;
-
-    // hand the group's staged candidates to the global list
-    auto flush = [&]() {
-        __syncwarp(gmask);
-        unsigned base = 0;
-        if (gl == 0) base = atomicAdd(&P.ctr->cand_count, staged);
-        base = __shfl_sync(gmask, base, gbase);
-        for (unsigned i = gl; i < staged; i += G) {
-            const uint2 c = stage[grp][i];
-            if (base + i < P.cand_cap) {
-                P.cand[base + i] = c;
-            } else if (atomicExch(&P.retry_mark[c.x], 1u) == 0u) {
-                P.retry_list[atomicAdd(&P.ctr->retry_count, 1u)] = list[c.x];
-            }
-        }
-        __syncwarp(gmask);
-        staged = 0;
-    };
-
-    for (;;) {
-        unsigned item = 0;
-        if (gl == 0) item = atomicAdd(&P.ctr->screen_head, 1u);
-        item = __shfl_sync(gmask, item, gbase);
-        if (item >= total) break;
-        const unsigned v = list[item];
-        if (gl == 0) P.retry_mark[item] = 0u;
-        const int x = (int)(v % (unsigned)P.nx);
-        const unsigned r1 = v / (unsigned)P.nx;
-        const int y = (int)(r1 % (unsigned)P.ny);
-        const int z = (int)(r1 / (unsigned)P.ny);
-        const float dr = __ldg(P.ref + v);
-        const float dD = P.dd_frac * (P.local ? dr : dnorm);
-        const float inv = 1.0f / dD;
-        float ub = P.out[v];                          // gamma^2 over the faces through v
-        int t = 0;
-        while (t < P.ntable) {
-            const int idx = t + gl;
-            float key = kInf;
-            uint32_t off = 0;
-            if (idx < P.ntable) {
-                const TableEntry e = P.table[idx];
-                key = e.key;
-                off = e.off;
-            }
-            const float k0 = __shfl_sync(gmask, key, gbase);
-            if (k0 * k0 >= ub) break;                 // A1 step 4b-ii, exact
-            float lub = ub;
-            bool cand = false;
-            if (key * key < ub) {
-                ++keyed;
-                const int cx = unpack10(off, 0), cy = unpack10(off, 10), cz = unpack10(off, 20);
-                const int px = x + cx, py = y + cy, pz = z + cz;
-                if ((unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny &&
-                    (N == 2 || (unsigned)pz < (unsigned)P.nz)) {
-                    const bool ex = px + 1 < P.nx, ey = py + 1 < P.ny, ez = N == 3 && pz + 1 < P.nz;
-                    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
-                    const long long pp = (long long)pz * sz + (long long)py * sy + px;
-                    float qmin = kInf, qmax = -kInf, vmin = kInf;
-#pragma unroll
-                    for (int u = 0; u < (1 << N); ++u) {
-                        const bool present = (!(u & 1) || ex) && (!(u & 2) || ey) && (!(u & 4) || ez);
-                        if (present) {
-                            const long long o = pp + ((u & 1) ? 1 : 0) + ((u & 2) ? sy : 0) +
-                                                ((u & 4) ? sz : 0);
-                            const float q = (__ldg(P.ev + o) - dr) * inv;
-                            qmin = fminf(qmin, q);
-                            qmax = fmaxf(qmax, q);
-                            const float ax = (float)(cx + (u & 1)) * P.hn[0];
-                            const float ay = (float)(cy + ((u >> 1) & 1)) * P.hn[1];
-                            const float az = N == 3 ? (float)(cz + ((u >> 2) & 1)) * P.hn[2] : 0.f;
-                            vmin = fminf(vmin, fmaf(q, q, fmaf(ax, ax, fmaf(ay, ay, az * az))));
-                        }
-                    }
-                    const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
-                    if (fmaf(gap, gap, key * key) < ub) {
-                        cand = true;
-                        lub = fminf(ub, vmin);
-                    } else {
-                        ++pruned;
-                    }
-                }
-            }
-            // stage this round's candidates (at most G), flushing first if needed
-            const unsigned bits = (__ballot_sync(gmask, cand) >> gbase) & (G == 32 ? kFull : ((1u << G) - 1u));
-            if (staged + G > kStageCells) flush();
-            if (cand) stage[grp][staged + __popc(bits & ((1u << gl) - 1u))] = make_uint2(item, (unsigned)idx);
-            staged += __popc(bits);
-            ub = group_min<G>(lub, gmask);
-            t += G;
-        }
-        if (gl == 0) {
-            P.out[v] = ub;                            // an attained gamma^2: an upper bound
-            // past a truncated table the box beyond it must be scanned: the full walk does it
-            if (t >= P.ntable && ub > rc2 && atomicExch(&P.retry_mark[item], 1u) == 0u)
-                P.retry_list[atomicAdd(&P.ctr->retry_count, 1u)] = v;
-        }
-    }
-    if (staged) flush();
-    if (P.stats) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            keyed += __shfl_xor_sync(kFull, keyed, o);
-            pruned += __shfl_xor_sync(kFull, pruned, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&P.ctr->cells_keyed, keyed);
-            atomicAdd(&P.ctr->cells_pruned, pruned);
-        }
-    }
-}
-
-// One thread per candidate cell: evaluate its faces and lower the voxel's
-// gamma^2 (an atomic minimum on the float's bits, valid for values >= 0).
-template <int N>
-__global__ void __launch_bounds__(256, 2) k_eval(const __grid_constant__ Problem P)
-{
-    const unsigned n = min(P.ctr->cand_count, P.cand_cap);
-    const unsigned* list = P.sort_tail ? P.tail_sorted : P.tail_raw;
-    const float dnorm = resolve_dnorm(P);
-    TailStats st;
-    const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint2 c = P.cand[i];
-        const unsigned v = list[c.x];
-        const TableEntry e = P.table[c.y];
-        const float cur = __ldcg(P.out + v);          // from L2: other threads' minima
-        if (e.key * e.key >= cur) continue;
-        const int x = (int)(v % (unsigned)P.nx);
-        const unsigned r1 = v / (unsigned)P.nx;
-        const int y = (int)(r1 % (unsigned)P.ny);
-        const int z = (int)(r1 / (unsigned)P.ny);
-        const float dr = __ldg(P.ref + v);
-        const float dD = P.dd_frac * (P.local ? dr : dnorm);
-        const float cb = visit_cell<N>(P, x, y, z, unpack10(e.off, 0), unpack10(e.off, 10),
-                                       unpack10(e.off, 20), e.key, dr, 1.0f / dD, dnorm, cur, st);
-        if (cb < cur) atomicMin((int*)(P.out + v), max(__float_as_int(cb), 0));
-    }
-    if (P.stats) {
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            st.visited += __shfl_xor_sync(kFull, st.visited, o);
-            st.pruned += __shfl_xor_sync(kFull, st.pruned, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&P.ctr->cells_visited, st.visited);
-            atomicAdd(&P.ctr->cells_pruned, st.pruned);
-        }
-    }
-}
-
-// gamma = sqrt(gamma^2) for every queued voxel not left to the full walk,
-// with the evaluated and passing counts.
-__global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ Problem P)
-{
-    const unsigned total = min(P.ctr->tail_count, P.tail_cap);
-    const unsigned* list = P.sort_tail ? P.tail_sorted : P.tail_raw;
-    unsigned my_eval = 0, my_pass = 0;
-    const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-        if (P.retry_mark[item]) continue;
-        const unsigned v = list[item];
-        const float gam = sqrtf(P.out[v]);
-        P.out[v] = gam;
-        ++my_eval;
-        my_pass += gam <= 1.f;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_eval += __shfl_xor_sync(kFull, my_eval, o);
-        my_pass += __shfl_xor_sync(kFull, my_pass, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
-        if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
     }
 }
 
@@ -1137,40 +922,6 @@ cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblock
     if (P.ndim == 3) launch_tail_n<3, false>(P, nullptr, lanes_per_voxel, tail_minblocks, grid, s);
     else launch_tail_n<2, false>(P, nullptr, lanes_per_voxel, tail_minblocks, grid, s);
     return cudaGetLastError();
-}
-
-template <int N>
-static void launch_screen_n(const Problem& P, int G, int grid, cudaStream_t s)
-{
-    switch (G) {
-    case 4: k_screen<N, 4><<<grid, 256, 0, s>>>(P); break;
-    case 8: k_screen<N, 8><<<grid, 256, 0, s>>>(P); break;
-    case 16: k_screen<N, 16><<<grid, 256, 0, s>>>(P); break;
-    default: k_screen<N, 32><<<grid, 256, 0, s>>>(P); break;
-    }
-}
-
-cudaError_t launch_walk(const Problem& P, int mode, int lanes_per_voxel, int tail_minblocks,
-                        cudaStream_t s)
-{
-    if (mode == 0) return launch_tail(P, lanes_per_voxel, tail_minblocks, s);
-    if (!P.cand || !P.retry_list || !P.retry_mark || P.cand_cap == 0) return cudaErrorInvalidValue;
-    const int sms = device_sm_count();
-    if (P.ndim == 3) {
-        launch_screen_n<3>(P, lanes_per_voxel, sms * 8, s);
-        k_eval<3><<<sms * 2, 256, 0, s>>>(P);
-    } else {
-        launch_screen_n<2>(P, lanes_per_voxel, sms * 8, s);
-        k_eval<2><<<sms * 2, 256, 0, s>>>(P);
-    }
-    k_finalize<<<sms * 2, 256, 0, s>>>(P);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    Problem R = P;                         // the voxels left over: the full walk
-    R.walk_list = P.retry_list;
-    R.walk_count = &P.ctr->retry_count;
-    R.walk_head = &P.ctr->retry_head;
-    return launch_tail(R, lanes_per_voxel, tail_minblocks, s);
 }
 
 // --------------------------------------------------------------------------

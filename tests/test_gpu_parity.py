@@ -147,15 +147,14 @@ def test_volume_ragged_anisotropic():
     assert_parity(got, want, counts)
 
 
-@pytest.mark.parametrize("tail_mode", [0, 1])
 @pytest.mark.parametrize("lanes", [4, 8, 16, 32])
 @pytest.mark.parametrize("sort_tail,tail_blocks", [(0, 1), (1, 2), (1, 1)])
-def test_launch_shapes_agree(lanes, sort_tail, tail_blocks, tail_mode):
+def test_launch_shapes_agree(lanes, sort_tail, tail_blocks):
     p = synth.workload("imrt_small")
     crit = synth.Criteria(0.01, 1.0, local=True)
     got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit,
                                {"lanes_per_voxel": lanes, "sort_tail": sort_tail,
-                                "tail_blocks_per_sm": tail_blocks, "tail_mode": tail_mode})
+                                "tail_blocks_per_sm": tail_blocks})
     want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
     assert_parity(got, want, counts)
 
@@ -420,15 +419,3 @@ def test_slab_gate_timeout_is_reported_and_the_next_run_recovers():
         assert np.array_equal(out.numpy().astype(np.float64), dev_out, equal_nan=True)
     finally:
         g.gamma_destroy(h)
-
-
-@pytest.mark.parametrize("limit", [1, 37, 1000])
-def test_screen_walk_candidate_list_overflow(limit):
-    # A candidate list far too short: the voxels whose cells do not fit are
-    # left to the full walk, and the map stays exact.
-    p = synth.workload("imrt_small")
-    crit = synth.Criteria(0.01, 1.0, local=True)
-    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, crit,
-                                {"tail_mode": 1, "walk_candidates": limit, "lanes_per_voxel": 8})
-    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
-    assert_parity(got, want, counts)
