@@ -692,7 +692,8 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
         CK(cudaEventRecord(h->tev[1], s));
     }
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), s));
-    CK(gk::launch_prepare(P, s));
+    // the search's shell checks the evaluation dose itself; the paper's design does not
+    CK(gk::launch_prepare(P, s, h->design != 0 ? 3 : 1));
     if (tm) CK(cudaEventRecord(h->tev[2], s));
     if (h->design != 0) {
         // the paper's design: DD keys and sort ("shell" phase), then the walk ("tail")
@@ -842,7 +843,6 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
         CK(cudaStreamWaitEvent(c, E[3], 0));
         CK(gk::launch_shell_range(P, 0, tiles, 0, gk::SlabGate{nullptr, 0u, 0}, c));
     }
-    CK(gk::launch_prepare(P, c, 2));
     if (tm) CK(cudaEventRecord(h->tev[3], c));
     CK(cudaEventRecord(E[4], c));
     CK(cudaStreamWaitEvent(o, E[4], 0));

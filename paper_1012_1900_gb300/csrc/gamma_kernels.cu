@@ -1,8 +1,9 @@
 // CUDA kernels of the gamma search (sm_103a).
 //
 // One run over a dose pair is four stream-ordered launches:
-//   k_prepare   max of the reference dose (the global dose norm) and a
-//               finite-input check                       (Algorithm A2 step 2)
+//   k_prepare   max of the reference dose (the global dose norm) and its
+//               finite check (k_shell checks the evaluation dose, every value
+//               of which is the centre of one tile voxel)  (Algorithm A2 step 2)
 //   k_shell     per reference voxel: criteria, low-dose cutoff, gamma0 =
 //               DD/dD (A1 step 4a) and every face through the voxel's node
 //               (reduced closed form), from a TMA-staged tile; voxels whose
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(256, MINB)
     uint32_t parity = 0;                 // bit b: phase of bar[b] to wait for
     unsigned my_eval = 0, my_pass = 0;
     float my_rmax = 0.f;
+    bool bad_ev = false;                 // a non-finite evaluation dose was seen
     int buf = 0;
     int cur = -1;                        // pair whose counters my_* accumulate
 
@@ -194,6 +196,8 @@ __global__ void __launch_bounds__(256, MINB)
             my_pass += __shfl_xor_sync(kFull, my_pass, o);
             my_rmax = fmaxf(my_rmax, __shfl_xor_sync(kFull, my_rmax, o));
         }
+        if (__any_sync(kFull, bad_ev) && lane == 0) atomicOr(&Q.ctr->flags, kFlagNonFinite);
+        bad_ev = false;
         if (lane == 0) {
             if (my_eval) atomicAdd(&sh_eval, (unsigned long long)my_eval);
             if (my_pass) atomicAdd(&sh_pass, (unsigned long long)my_pass);
@@ -273,14 +277,16 @@ __global__ void __launch_bounds__(256, MINB)
         const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
         const bool inside = x < P.nx && y < P.ny && z < P.nz;
         const long long v = inside ? ((long long)z * P.ny + y) * P.nx + x : 0;
+        const int tix0 = ((N == 3 ? lz + 1 : 0) * T::BY + (ly + 1)) * T::BX + (lx + 4);
         float dr = 0.f, best = 0.f;
         bool act = false;
         if (inside) {
             dr = __ldg(P.ref + v);
             act = is_evaluated(P, dr, thr);
             if (!act) P.out[v] = __int_as_float(0x7fc00000);
+            bad_ev |= !isfinite(tl[tix0]);           // every evaluation dose is some tile's centre
         }
-        const int tix = ((N == 3 ? lz + 1 : 0) * T::BY + (ly + 1)) * T::BX + (lx + 4);
+        const int tix = tix0;
         uint32_t inm = 0, inp = 0;       // neighbours at -1 / +1 inside the grid, per axis
         inm |= (x > 0) ? 1u : 0u;
         inp |= (x + 1 < P.nx) ? 1u : 0u;
@@ -934,7 +940,7 @@ cudaError_t launch_batch_prepare(const BatchGroup& g, cudaStream_t s)
     const int sms = device_sm_count();
     const int bx = grid_for(g.max_nvox, 256, std::max(1, sms * 8 / std::max(1, g.npairs)) + 1);
     Problem dummy{};
-    k_prepare<true><<<dim3(bx, g.npairs), 256, 0, s>>>(dummy, g.desc, 3);
+    k_prepare<true><<<dim3(bx, g.npairs), 256, 0, s>>>(dummy, g.desc, 1);   // k_shell checks the evaluation dose
     return cudaGetLastError();
 }
 

@@ -227,7 +227,7 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
     // the counters must start at zero; the rest is written before it is read
     if (cudaMemsetAsync(base + kOffCounters, 0, sizeof(gk::Counters), s) != cudaSuccess)
         return GAMMA_ERR_CUDA;
-    if (gk::launch_prepare(P, s) != cudaSuccess) return GAMMA_ERR_CUDA;
+    if (gk::launch_prepare(P, s, 1) != cudaSuccess) return GAMMA_ERR_CUDA;
     if (gk::launch_shell(P, s) != cudaSuccess) return GAMMA_ERR_CUDA;
     if (gk::launch_tail(P, 8, 2, s) != cudaSuccess) return GAMMA_ERR_CUDA;
 

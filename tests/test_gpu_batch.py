@@ -113,3 +113,35 @@ def test_autotune_single_and_batch():
         g.gamma_destroy(h)
     want = oracle_gamma(p.ref, p.eval, p.spacing, p.criteria)
     assert_parity(o.cpu().numpy().astype(np.float64), want)
+
+
+@pytest.mark.parametrize("which", ["eval", "ref"])
+def test_non_finite_input_reported_per_pair(which):
+    # A NaN in one pair's dose (a corner voxel) is reported for that pair only.
+    import paper_1012_1900_gb300 as g
+    ps = _pairs()[3:7]
+    bad = 2
+    arr = ps[bad].eval if which == "eval" else ps[bad].ref
+    arr[(-1,) * arr.ndim] = np.nan
+    tensors, descs = [], []
+    for p in ps:
+        r, e = torch.from_numpy(p.ref).cuda(), torch.from_numpy(p.eval).cuda()
+        o = torch.empty_like(r)
+        tensors += [r, e, o]
+        nd = p.ref.ndim
+        c = p.criteria
+        descs.append((r, e, o, nd, p.ref.shape if nd == 3 else (1,) + p.ref.shape,
+                      p.spacing if nd == 3 else (1.0,) + p.spacing,
+                      g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)))
+    h = g.gamma_batch_create(descs)
+    try:
+        g.gamma_batch_run(h)
+        for i in range(len(ps)):
+            if i == bad:
+                with pytest.raises(g.GammaError) as err:
+                    g.gamma_batch_pass_rate(h, i)
+                assert err.value.code == -3
+            else:
+                g.gamma_batch_pass_rate(h, i)
+    finally:
+        g.gamma_destroy(h)

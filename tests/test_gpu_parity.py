@@ -255,14 +255,42 @@ def test_tiny_golden_grids(name):
         assert abs(got.ravel()[flat] - value) <= 1e-6, expr
 
 
-def test_non_finite_input_reported():
+@pytest.mark.parametrize("where", [(3, 4, 5), (0, 0, 0), (-1, -1, -1), (-1, 0, -1)])
+@pytest.mark.parametrize("which,value", [("eval", np.nan), ("eval", np.inf), ("ref", np.nan),
+                                         ("ref", -np.inf)])
+def test_non_finite_input_reported(where, which, value):
+    # The reference dose is checked by the dose-norm pass, the evaluation dose
+    # by the shell (every value is the centre of one tile voxel), corners too.
     import paper_1012_1900_gb300 as g
     p = synth.workload("imrt_small")
-    ev = p.eval.copy()
-    ev[3, 4, 5] = np.nan
+    ref, ev = p.ref.copy(), p.eval.copy()
+    (ev if which == "eval" else ref)[where] = value
     with pytest.raises(g.GammaError) as e:
-        gpu_gamma(p.ref, ev, p.spacing, p.criteria)
+        gpu_gamma(ref, ev, p.spacing, p.criteria)
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("which", ["eval", "ref"])
+def test_non_finite_input_reported_on_host_runs(which):
+    import paper_1012_1900_gb300 as g
+    p = synth.workload("imrt_small")
+    ref, ev = p.ref.copy(), p.eval.copy()
+    (ev if which == "eval" else ref)[-1, 7, 0] = np.nan
+    crit = p.criteria
+    h = g.gamma_create(None, None, 3, p.ref.shape, p.spacing,
+                       g.criteria(crit.dd_frac, crit.dta_mm, cutoff_frac=crit.cutoff_frac))
+    try:
+        for pipe in (4, 0):
+            g.gamma_set_option(h, "pipeline", pipe)
+            r = torch.from_numpy(ref).pin_memory()
+            e = torch.from_numpy(ev).pin_memory()
+            o = torch.empty_like(r).pin_memory()
+            g.gamma_run_host(h, r, e, o)
+            with pytest.raises(g.GammaError) as err:
+                g.gamma_pass_rate(h)
+            assert err.value.code == -3
+    finally:
+        g.gamma_destroy(h)
 
 
 def test_repeat_runs_identical_and_counters_reset():
