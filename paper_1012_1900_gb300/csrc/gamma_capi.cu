@@ -421,7 +421,7 @@ int batch_upload(gamma_ctx* h)
             for (int k = 0; k < np; ++k) cap += b->pairs[mem[k]]->tail_cap;
             CK(cudaMalloc(&G.items_v, sizeof(unsigned) * std::max<size_t>(cap, 1)));
             CK(cudaMalloc(&G.items_p, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
-            CK(cudaMalloc(&G.head, sizeof(unsigned)));
+            CK(cudaMalloc(&G.head, 2 * sizeof(unsigned)));   // walk, shell tiles
             CK(cudaMalloc(&G.desc, sizeof(gk::BatchDesc)));
         }
         CK(cudaMemcpy(G.probs, probs.data(), sizeof(gk::Problem) * np, cudaMemcpyHostToDevice));
@@ -438,12 +438,14 @@ int batch_upload(gamma_ctx* h)
         d.items_v = G.items_v;
         d.items_p = G.items_p;
         d.head = G.head;
+        d.shell_next = G.head + 1;
         CK(cudaMemcpy(G.desc, &d, sizeof(d), cudaMemcpyHostToDevice));
         G.host.ndim = gi == 0 ? 2 : 3;
         G.host.npairs = np;
         G.host.max_nvox = maxv;
         G.host.total_tiles = tstart[np];
         G.host.desc = G.desc;
+        G.host.shell_next = G.head + 1;
     }
     return GAMMA_OK;
 }

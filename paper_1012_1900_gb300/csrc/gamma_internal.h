@@ -139,6 +139,7 @@ struct BatchDesc {
     unsigned* items_v;             // [sum of tail_cap] queued voxels in that order
     unsigned short* items_p;       // [sum of tail_cap] their pair
     unsigned* head;                // work counter of the group's table walk
+    unsigned* shell_next;          // tile counter of the group's shell (zeroed by its prepare)
 };
 
 // Host view of one batched launch group.
@@ -148,6 +149,7 @@ struct BatchGroup {
     long long max_nvox;            // largest pair, for the prepare grid
     int total_tiles;               // shell tiles over all pairs
     const BatchDesc* desc;         // device copy of the descriptor
+    unsigned* shell_next;          // device: the descriptor's shell tile counter
 };
 
 // Launchers (gamma_kernels.cu).  All are stream-ordered and allocate nothing.

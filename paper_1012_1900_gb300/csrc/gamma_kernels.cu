@@ -41,6 +41,9 @@ __global__ void __launch_bounds__(256)
     k_prepare(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd, int part)
 {
     const Problem& P = BATCH ? bd->probs[blockIdx.y] : P0;
+    if constexpr (BATCH) {
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *bd->shell_next = 0u;
+    }
     float m = -kInf;
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -953,9 +956,9 @@ cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStr
     Problem dummy{};
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
-    if (g.ndim == 3) launch_shell_k<3, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, nullptr,
+    if (g.ndim == 3) launch_shell_k<3, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.shell_next,
                                         SlabGate{nullptr, 0u, 0}, g.desc);
-    else launch_shell_k<2, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, nullptr,
+    else launch_shell_k<2, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.shell_next,
                                         SlabGate{nullptr, 0u, 0}, g.desc);
     return cudaGetLastError();
 }
