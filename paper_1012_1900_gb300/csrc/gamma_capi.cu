@@ -128,6 +128,8 @@ struct gamma_ctx {
     unsigned epoch = 0;               // number of the current overlapped run
     cudaEvent_t tev_out = nullptr;    // timing: end of the overlapped map copy-out
     int overlapped = 0;               // last run: 0 in order, 1 overlapped, 2 overlapped + slab gate
+    Counters* host_ctr = nullptr;     // page-locked, mapped: counters an overlapped run leaves
+    Counters* host_ctr_dev = nullptr; // its device address
     int drop_slab_flag = 0;           // test hook: k + 1 leaves slab k's flag unwritten
     // state
     cudaStream_t last_stream = nullptr;
@@ -288,6 +290,7 @@ void free_ctx(gamma_ctx* h)
     for (auto& e : h->slab_ev)
         if (e) cudaEventDestroy(e);
     if (h->tev_out) cudaEventDestroy(h->tev_out);
+    if (h->host_ctr) cudaFreeHost(h->host_ctr);
     cudaFree(h->slab_flags);
     for (auto& st : h->pipe_s)
         if (st) cudaStreamDestroy(st);
@@ -785,6 +788,10 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
         if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : h->slab_ev)
         if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (!h->host_ctr) {
+        CK(cudaHostAlloc(&h->host_ctr, sizeof(Counters), cudaHostAllocMapped));
+        CK(cudaHostGetDevicePointer((void**)&h->host_ctr_dev, h->host_ctr, 0));
+    }
     if (!h->slab_flags) {
         CK(cudaMalloc(&h->slab_flags, sizeof(unsigned) * kPipeChunks));
         CK(cudaMemset(h->slab_flags, 0, sizeof(unsigned) * kPipeChunks));
@@ -856,7 +863,7 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
     CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, c));
     if (tm) CK(cudaEventRecord(h->tev[5], c));
     CK(cudaStreamWaitEvent(c, E[5], 0));
-    CK(gk::launch_patch_host(P, out_mapped, c));
+    CK(gk::launch_patch_host(P, out_mapped, h->host_ctr_dev, c));
     if (tm) CK(cudaEventRecord(h->tev[6], c));
     CK(cudaEventRecord(E[6], c));
     CK(cudaStreamWaitEvent(s, E[6], 0));
@@ -904,6 +911,10 @@ static int read_counters(gamma_handle h, Counters* c, int pair = -1)
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     CK(cudaStreamSynchronize(h->last_stream));
+    if (!h->batch && h->overlapped) {            // the final patch left them in host memory
+        std::memcpy(c, h->host_ctr, sizeof(Counters));
+        return GAMMA_OK;
+    }
     if (!h->batch) {
         CK(cudaMemcpy(c, h->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
         return GAMMA_OK;

@@ -168,8 +168,10 @@ cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, i
 bool shell_gate_ok(const Problem& P);
 void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* layer_depth);
 // Final gamma of every queued voxel into a host map, through its
-// device-mapped pointer.
-cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, cudaStream_t s);
+// device-mapped pointer, and (when given) the run's counters into mapped
+// host memory.
+cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, Counters* host_ctr_mapped,
+                              cudaStream_t s);
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
 cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblocks, cudaStream_t s);
 int device_sm_count();

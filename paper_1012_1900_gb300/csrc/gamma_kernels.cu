@@ -879,8 +879,16 @@ cudaError_t launch_shell(const Problem& P, cudaStream_t s)
 
 // Copy the final gamma of every queued voxel from the device map into a
 // host map (through its device-mapped pointer) that already holds the rest.
-__global__ void __launch_bounds__(256) k_patch_host(const __grid_constant__ Problem P, float* host_out)
+// Block 0 also copies the run's final counters into `host_ctr` (mapped), so
+// that reading them needs no copy of its own.
+__global__ void __launch_bounds__(256) k_patch_host(const __grid_constant__ Problem P, float* host_out,
+                                                    Counters* host_ctr)
 {
+    if (blockIdx.x == 0 && host_ctr) {
+        const unsigned* src = (const unsigned*)P.ctr;
+        unsigned* dst = (unsigned*)host_ctr;
+        for (unsigned i = threadIdx.x; i < sizeof(Counters) / 4; i += blockDim.x) dst[i] = src[i];
+    }
     const unsigned n = min(P.ctr->tail_count, P.tail_cap);
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -889,9 +897,10 @@ __global__ void __launch_bounds__(256) k_patch_host(const __grid_constant__ Prob
     }
 }
 
-cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, cudaStream_t s)
+cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, Counters* host_ctr_mapped,
+                              cudaStream_t s)
 {
-    k_patch_host<<<device_sm_count() * 4, 256, 0, s>>>(P, host_out_mapped);
+    k_patch_host<<<device_sm_count() * 4, 256, 0, s>>>(P, host_out_mapped, host_ctr_mapped);
     return cudaGetLastError();
 }
 
