@@ -908,7 +908,7 @@ cudaError_t launch_order_tail(const Problem& P, cudaStream_t s)
 {
     if (!P.sort_tail) return cudaSuccess;
     const int sms = device_sm_count();
-    k_scatter<<<sms * 2, 256, 0, s>>>(P);
+    k_scatter<<<sms * 8, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
