@@ -470,8 +470,12 @@ def test_graph_replay_matches_direct_launches():
         want_counts = g.gamma_pass_rate(h0)
         out = torch.empty_like(r)
         for k in range(6):
-            if k == 3:
-                g.gamma_set_option(h, "lanes_per_voxel", 16)   # drops the captured graph
+            if k == 3:                                  # drops the captured graph
+                for hh in (h, h0):
+                    g.gamma_set_option(hh, "lanes_per_voxel", 16)
+                g.gamma_run(h0, ref_out)
+                want = ref_out.cpu().numpy()
+                want_counts = g.gamma_pass_rate(h0)
             out.fill_(-7.0)
             g.gamma_run(h, out)
             assert g.gamma_pass_rate(h) == want_counts
