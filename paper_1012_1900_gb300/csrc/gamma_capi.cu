@@ -1324,8 +1324,10 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
                 h->lanes = lanes[li];
                 h->shell_minblocks = bl;
                 h->tail_minblocks = tb;
+                h->sg_dirty = true;                    // a captured graph holds the old shapes
                 if (h->batch) h->batch->dirty = true;
-                if ((rc = run())) break;
+                if ((rc = run()) || (rc = run())) break; // direct run, then graph capture
+
                 cudaEventRecord(e0, s);
                 for (int r = 0; r < reps && rc == GAMMA_OK; ++r) rc = run();
                 cudaEventRecord(e1, s);
@@ -1340,6 +1342,7 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     h->lanes = best_l;
     h->shell_minblocks = best_b;
     h->tail_minblocks = best_t;
+    h->sg_dirty = true;
     if (h->batch) h->batch->dirty = true;
     if (rc) return rc;
     if (lanes_per_voxel) *lanes_per_voxel = best_l;
