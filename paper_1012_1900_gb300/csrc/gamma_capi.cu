@@ -114,6 +114,9 @@ struct gamma_ctx {
     int face_eval = 0;       // design 1 / 2: 0 closed-form faces, 1 Ju's recursion
     gk::PaperScratch paper;
     gamma_model model = nullptr;      // attached proposal network (may be null)
+    float* gnorm = nullptr;           // with a model: gradient magnitudes of both doses (2 x nvox)
+    unsigned* seed_list = nullptr;    // with a model: queue items past the cost gate (tail_cap)
+    int seed_min_bucket = 9;          // cost gate of the seeding pass (bucket of >= 16 cells)
     bool own_model = false;
     // per-phase events: 0 start, 1 after h2d, 2 after prepare, 3 after shell,
     // 4 after order, 5 after tail, 6 after d2h
@@ -310,6 +313,8 @@ void free_ctx(gamma_ctx* h)
     cudaFree(h->tail_raw);
     cudaFree(h->tail_bucket);
     cudaFree(h->tail_sorted);
+    cudaFree(h->gnorm);
+    cudaFree(h->seed_list);
     cudaFree(h->own_ref);
     cudaFree(h->own_ev);
     cudaFree(h->own_out);
@@ -773,8 +778,13 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
     if (h->model) {
         gk::MlpWeights W;
         gk::model_weights(h->model, &W);
-        CK(cudaMemsetAsync(h->ctr->hist, 0, sizeof(h->ctr->hist), s));
-        CK(gk::launch_learned(P, W, s));
+        Problem Q = P;
+        Q.gnorm_e = h->gnorm;
+        Q.gnorm_r = h->gnorm + h->nvox;
+        Q.seed_list = h->seed_list;
+        CK(gk::launch_grad_norms(Q, h->gnorm, h->gnorm + h->nvox, s));
+        CK(gk::launch_seed_select(Q, h->seed_min_bucket, s));
+        CK(gk::launch_learned(Q, W, s));
     }
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     CK(gk::launch_order_tail(P, s));
@@ -1159,6 +1169,11 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         h->face_eval = (int)value;
         return GAMMA_OK;
     }
+    if (!std::strcmp(key, "seed_min_bucket")) {
+        if (value < 0 || value >= gk::kNumBuckets) return GAMMA_ERR_INVALID_ARG;
+        h->seed_min_bucket = (int)value;
+        return GAMMA_OK;
+    }
     if (!std::strcmp(key, "tail_blocks_per_sm")) {
         if (value < 1 || value > 2) return GAMMA_ERR_INVALID_ARG;
         h->tail_minblocks = (int)value;
@@ -1377,9 +1392,21 @@ int gamma_labels(gamma_handle h, const float* gamma_map_dev, const uint32_t* vox
     return GAMMA_OK;
 }
 
+// Buffers the seeding pass needs once a model is attached.
+static int seed_buffers(gamma_handle h)
+{
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    if (!h->gnorm) CK(cudaMalloc(&h->gnorm, sizeof(float) * 2 * (size_t)h->nvox));
+    if (!h->seed_list) CK(cudaMalloc(&h->seed_list, sizeof(unsigned) * (size_t)h->tail_cap));
+    return GAMMA_OK;
+}
+
 int gamma_set_model(gamma_handle h, gamma_model m)
 {
-    if (!h || h->batch) return GAMMA_ERR_INVALID_ARG;
+    if (!h || h->batch || h->grids) return GAMMA_ERR_INVALID_ARG;
+    if (m)
+        if (int rc = seed_buffers(h)) return rc;
     if (h->own_model) gamma_model_destroy(h->model);
     h->sg_dirty = true;
     h->model = m;
@@ -1392,6 +1419,8 @@ int gamma_load_model(gamma_handle h, const char* path)
     if (!h || h->batch || !path) return GAMMA_ERR_INVALID_ARG;
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
+    if (h->grids) return GAMMA_ERR_INVALID_ARG;
+    if (int rc = seed_buffers(h)) return rc;
     gamma_model m = nullptr;
     if (int rc = gamma_model_create(&m, 0)) return rc;
     if (int rc = gamma_model_load(m, path)) {
@@ -1399,6 +1428,7 @@ int gamma_load_model(gamma_handle h, const char* path)
         return rc;
     }
     if (h->own_model) gamma_model_destroy(h->model);
+    h->sg_dirty = true;
     h->model = m;
     h->own_model = true;
     return GAMMA_OK;

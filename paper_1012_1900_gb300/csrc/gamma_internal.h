@@ -65,6 +65,7 @@ struct Counters {
     unsigned int seed_head;             // work counter of the learned seeding pass
     unsigned int seeded;                // queued voxels the proposal network seeded
     unsigned int seed_improved;         // ... whose bound the seed lowered
+    unsigned int seed_count;            // queued voxels past the seeding cost gate
     unsigned int shell_next[kShellSlots];   // tile work counters of the shell launches
     unsigned int hist[kNumBuckets];
     unsigned int cursor[kNumBuckets];
@@ -114,6 +115,12 @@ struct Problem {
     // squared spatial distance from the voxel to the faces of key-0 cell S
     // (lower corner at -S) that do not contain it, rounded down; +inf for S = 0
     float key0_far2[8];
+    // learned seeding: gradient-magnitude volumes of the evaluation and the
+    // reference dose (null: computed where needed), and the queue items past
+    // the cost gate
+    const float* gnorm_e;
+    const float* gnorm_r;
+    unsigned* seed_list;
 };
 
 // Readiness of the evaluation dose by z slab, for a shell launch that starts
@@ -187,6 +194,11 @@ int shell_tiles(const Problem& P);
 // Learned proposal (gamma_learned.cu).
 bool model_weights(const gamma_model_s* m, MlpWeights* w);
 cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s);
+// Gradient magnitudes of both doses at every grid point (the feature
+// channels 1 and 2 before their per-voxel scale), into ge and gr.
+cudaError_t launch_grad_norms(const Problem& P, float* ge, float* gr, cudaStream_t s);
+// Queue items whose cost bucket is at least min_bucket, into P.seed_list.
+cudaError_t launch_seed_select(const Problem& P, int min_bucket, cudaStream_t s);
 
 // Reference and evaluation doses on different grids (gamma_grids.cu).
 // Positions and spacings are in DTA units, axes (x, y, z).

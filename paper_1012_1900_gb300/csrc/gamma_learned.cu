@@ -73,8 +73,43 @@ __device__ __forceinline__ float voxel_feature(const Problem& P, int x, int y, i
         return 0.f;
     const long long p = ((long long)pz * P.ny + py) * P.nx + px;
     if (ch == 0) return fminf(fmaxf((__ldg(P.ev + p) - dr) * inv, -16.f), 16.f);
-    const float gmag = grad_norm<N>(ch == 1 ? P.ev : P.ref, P, px, py, pz, p);
+    const float* pre = ch == 1 ? P.gnorm_e : P.gnorm_r;
+    const float gmag = pre ? __ldg(pre + p) : grad_norm<N>(ch == 1 ? P.ev : P.ref, P, px, py, pz, p);
     return fminf(gmag * inv, 32.f);
+}
+
+// The gradient magnitudes of both doses at every grid point, computed once
+// per run for the seeding pass (the same function the features evaluate
+// point by point, so the features do not change).
+template <int N>
+__global__ void __launch_bounds__(256) k_grad_norms(const __grid_constant__ Problem P,
+                                                    float* __restrict__ ge, float* __restrict__ gr)
+{
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P.nvox;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % P.nx);
+        const long long r1 = p / P.nx;
+        const int y = (int)(r1 % P.ny), z = (int)(r1 / P.ny);
+        ge[p] = grad_norm<N>(P.ev, P, x, y, z, p);
+        gr[p] = grad_norm<N>(P.ref, P, x, y, z, p);
+    }
+}
+
+// Queue items past the cost gate (bucket >= min_bucket), into P.seed_list.
+__global__ void __launch_bounds__(256) k_seed_select(const __grid_constant__ Problem P, int min_bucket)
+{
+    const unsigned total = min(P.ctr->tail_count, P.tail_cap);
+    const int lane = threadIdx.x & 31;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned c0 = blockIdx.x * blockDim.x; c0 < total; c0 += stride) {
+        const unsigned i = c0 + threadIdx.x;
+        const bool take = i < total && (int)P.tail_bucket[i] >= min_bucket;
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        unsigned base = 0;
+        if (lane == 0 && m) base = atomicAdd(&P.ctr->seed_count, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) P.seed_list[base + __popc(m & ((1u << lane) - 1u))] = i;
+    }
 }
 
 template <int N>
@@ -665,7 +700,7 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
     const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
-    const unsigned total = min(P.ctr->tail_count, P.tail_cap);
+    const unsigned total = min(P.ctr->seed_count, P.tail_cap);
     if (threadIdx.x < kNumBuckets) S.hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) { S.nseed = 0; S.nimp = 0; }
     tc_setup(S, W);
@@ -683,12 +718,12 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
             unsigned v = 0xffffffffu;
             float dr = 0.f, inv = 0.f;
             if (it < total) {
-                v = P.tail_raw[it];
+                v = P.tail_raw[P.seed_list[it]];
                 dr = __ldg(P.ref + v);
                 inv = 1.0f / (P.dd_frac * (P.local ? dr : dnorm));
             }
             S.vox[threadIdx.x] = v;
-            S.item[threadIdx.x] = it;
+            S.item[threadIdx.x] = it < total ? P.seed_list[it] : 0u;
             S.dr[threadIdx.x] = dr;
             S.inv[threadIdx.x] = inv;
         }
@@ -762,8 +797,12 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
                 }
                 const int cost = lo;
                 const int bucket = cost <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)cost)));
-                P.tail_bucket[S.item[r]] = (unsigned char)bucket;
-                atomicAdd(&S.hist[bucket], 1u);
+                const int was = P.tail_bucket[S.item[r]];
+                if (bucket != was) {                    // move the voxel between histogram bins
+                    P.tail_bucket[S.item[r]] = (unsigned char)bucket;
+                    atomicAdd(&S.hist[bucket], 1u);
+                    atomicSub(&S.hist[was], 1u);        // wraps; the sum over the block is exact
+                }
             }
         }
     }
@@ -791,6 +830,21 @@ cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s
         if (e != cudaSuccess) return e;
         k_learned<2><<<device_sm_count(), 256, smem, s>>>(P, W);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_norms(const Problem& P, float* ge, float* gr, cudaStream_t s)
+{
+    const int grid = (int)std::min<long long>((P.nvox + 255) / 256, (long long)device_sm_count() * 8);
+    if (P.ndim == 3) k_grad_norms<3><<<std::max(grid, 1), 256, 0, s>>>(P, ge, gr);
+    else k_grad_norms<2><<<std::max(grid, 1), 256, 0, s>>>(P, ge, gr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_select(const Problem& P, int min_bucket, cudaStream_t s)
+{
+    if (!P.seed_list) return cudaErrorInvalidValue;
+    k_seed_select<<<device_sm_count() * 4, 256, 0, s>>>(P, min_bucket);
     return cudaGetLastError();
 }
 

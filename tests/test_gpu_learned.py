@@ -191,9 +191,12 @@ def test_training_lowers_the_loss():
     assert last < 0.5 * first, (first, last)
 
 
+@pytest.mark.parametrize("gate", [0, 9, 31])
 @pytest.mark.parametrize("crit", [synth.Criteria(0.02, 2.0), synth.Criteria(0.01, 1.0, local=True)],
                          ids=["2pct2mm", "1pct1mm_local"])
-def test_runs_with_a_model_stay_exact(crit):
+def test_runs_with_a_model_stay_exact(crit, gate):
+    # gate: the seeding pass takes only queued voxels of cost bucket >= gate
+    # (0: all of them); the search stays exact whichever voxels are seeded.
     import paper_1012_1900_gb300 as g
     p = synth.make_pair_3d(shape=(24, 36, 32), spacing=(2.0, 2.0, 2.0), seed=2001,
                            shift_mm=(0.5, 1.5, 2.5), scale=1.04, criteria=crit)
@@ -202,6 +205,7 @@ def test_runs_with_a_model_stay_exact(crit):
     h, r, e = _handle(g, p)
     try:
         g.gamma_set_model(h, m)
+        g.gamma_set_option(h, "seed_min_bucket", gate)
         out = torch.empty_like(r)
         g.gamma_run(h, out)
         counts = g.gamma_pass_rate(h)
@@ -210,7 +214,10 @@ def test_runs_with_a_model_stay_exact(crit):
     finally:
         g.gamma_destroy(h)
         g.gamma_model_destroy(m)
-    assert st["seeded"] == st["tail_voxels"] > 0
+    if gate == 0:
+        assert st["seeded"] == st["tail_voxels"] > 0
+    else:
+        assert st["seeded"] < st["tail_voxels"]
     np.testing.assert_allclose(got, plain, rtol=0, atol=1e-6, equal_nan=True)
     want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
     assert_parity(got, want, counts)
