@@ -1374,8 +1374,14 @@ int gamma_features(gamma_handle h, const uint32_t* voxels_dev, int64_t n, void* 
     if (n == 0) return GAMMA_OK;
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
-    const Problem P = make_problem(h, nullptr);
-    CK(gk::launch_features(P, voxels_dev, n, (__nv_bfloat16*)X_bf16_dev, (cudaStream_t)cuda_stream));
+    Problem P = make_problem(h, nullptr);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (h->gnorm) {                  // a model is attached: the gradient volumes the seeding pass reads
+        P.gnorm_e = h->gnorm;
+        P.gnorm_r = h->gnorm + h->nvox;
+        CK(gk::launch_grad_norms(P, h->gnorm, h->gnorm + h->nvox, s));
+    }
+    CK(gk::launch_features(P, voxels_dev, n, (__nv_bfloat16*)X_bf16_dev, s));
     return GAMMA_OK;
 }
 

@@ -112,25 +112,75 @@ __global__ void __launch_bounds__(256) k_seed_select(const __grid_constant__ Pro
     }
 }
 
+// Features f0 .. f0 + 7 of reference voxel v (f0 a multiple of 8), the same
+// values voxel_feature gives one by one, with their eight loads issued before
+// any is used.  v = 0xffffffff: zeros.
+template <int N>
+__device__ __forceinline__ void features8(const Problem& P, unsigned v, float dr, float inv, int f0,
+                                          float (&val)[8])
+{
+#pragma unroll
+    for (int u = 0; u < 8; ++u) val[u] = 0.f;
+    if (v == 0xffffffffu || f0 >= kIn) return;
+    if (!P.gnorm_e || !P.gnorm_r) {
+        const int x = (int)(v % (unsigned)P.nx);
+        const unsigned r1 = v / (unsigned)P.nx;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            val[u] = voxel_feature<N>(P, x, (int)(r1 % (unsigned)P.ny), (int)(r1 / (unsigned)P.ny), dr,
+                                      inv, f0 + u);
+        return;
+    }
+    const int x = (int)(v % (unsigned)P.nx);
+    const unsigned r1 = v / (unsigned)P.nx;
+    const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
+    int ch = f0 / 125;
+    const int pi = f0 % 125;
+    int ox = pi % 5 - 2, oy = (pi / 5) % 5 - 2, oz = pi / 25 - 2;
+    float raw[8];
+    int chs[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int px = x + ox, py = y + oy, pz = N == 3 ? z + oz : 0;
+        const bool ok = f0 + u < kIn && (N == 3 || oz == -2) && (unsigned)px < (unsigned)P.nx &&
+                        (unsigned)py < (unsigned)P.ny && (N == 2 || (unsigned)pz < (unsigned)P.nz);
+        const float* src = ch == 0 ? P.ev : (ch == 1 ? P.gnorm_e : P.gnorm_r);
+        raw[u] = ok ? __ldg(src + ((long long)pz * P.ny + py) * P.nx + px) : __int_as_float(0x7fc00000);
+        chs[u] = ch;
+        if (++ox > 2) {                            // next patch point (x fastest), then channel
+            ox = -2;
+            if (++oy > 2) {
+                oy = -2;
+                if (++oz > 2) { oz = -2; ++ch; }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        if (isnan(raw[u])) continue;               // outside the grid or past the last feature: 0
+        val[u] = chs[u] == 0 ? fminf(fmaxf((raw[u] - dr) * inv, -16.f), 16.f) : fminf(raw[u] * inv, 32.f);
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) k_features(const __grid_constant__ Problem P,
                                                   const unsigned* __restrict__ vox, long long n,
                                                   bf16* __restrict__ X)
 {
     const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
-    const long long total = n * kInPad;
+    const long long total = n * (kInPad / 8);
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const long long i = e / kInPad;
-        const int f = (int)(e % kInPad);
+        const long long i = e / (kInPad / 8);
+        const int f0 = (int)(e % (kInPad / 8)) * 8;
         const unsigned v = vox[i];
-        const int x = (int)(v % (unsigned)P.nx);
-        const unsigned r1 = v / (unsigned)P.nx;
-        const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
         const float dr = __ldg(P.ref + v);
         const float dD = P.dd_frac * (P.local ? dr : dnorm);
         const float inv = dD > 0.f ? 1.0f / dD : 0.f;
-        X[e] = __float2bfloat16(voxel_feature<N>(P, x, y, z, dr, inv, f));
+        float val[8];
+        features8<N>(P, v, dr, inv, f0, val);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) X[i * kInPad + f0 + u] = __float2bfloat16(val[u]);
     }
 }
 
@@ -730,17 +780,20 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
         __syncthreads();
         // ---- features (chunk by chunk) and the three layers ----
         auto fill = [&](int c, bf16* dst) {
-            for (int e = threadIdx.x; e < kRows * kKc; e += blockDim.x) {
-                const int r = e / kKc, fl = e % kKc;
-                const unsigned v = S.vox[r];
-                float val = 0.f;
-                if (v != 0xffffffffu) {
-                    const int x = (int)(v % (unsigned)P.nx);
-                    const unsigned r1 = v / (unsigned)P.nx;
-                    val = voxel_feature<N>(P, x, (int)(r1 % (unsigned)P.ny), (int)(r1 / (unsigned)P.ny),
-                                           S.dr[r], S.inv[r], c * kKc + fl);
+            // eight consecutive features of one row per step: their loads are
+            // independent, so each thread keeps eight in flight
+            for (int e = threadIdx.x; e < kRows * (kKc / 8); e += blockDim.x) {
+                const int r = e / (kKc / 8), j = e % (kKc / 8);
+                float val[8];
+                features8<N>(P, S.vox[r], S.dr[r], S.inv[r], c * kKc + j * 8, val);
+                uint4 pk;
+                uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(val[2 * u], val[2 * u + 1]);
+                    w[u] = *reinterpret_cast<const uint32_t*>(&b2);
                 }
-                dst[core_idx(r, fl, kRows)] = __float2bfloat16(val);
+                *reinterpret_cast<uint4*>(dst + core_idx(r, j * 8, kRows)) = pk;
             }
         };
         ok = mlp_tile(S, nc, fill);
@@ -851,7 +904,7 @@ cudaError_t launch_seed_select(const Problem& P, int min_bucket, cudaStream_t s)
 cudaError_t launch_features(const Problem& P, const unsigned* vox, long long n, bf16* X,
                             cudaStream_t s)
 {
-    const long long total = n * kInPad;
+    const long long total = n * (kInPad / 8);
     const int grid = (int)std::min<long long>((total + 255) / 256, (long long)device_sm_count() * 32);
     if (P.ndim == 3) k_features<3><<<std::max(grid, 1), 256, 0, s>>>(P, vox, n, X);
     else k_features<2><<<std::max(grid, 1), 256, 0, s>>>(P, vox, n, X);

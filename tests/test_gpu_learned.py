@@ -117,11 +117,17 @@ def _handle(g, p):
     return h, r, e
 
 
-def test_features_match_definition():
+@pytest.mark.parametrize("volumes", [False, True], ids=["pointwise", "gradient_volumes"])
+def test_features_match_definition(volumes):
+    # With a model attached the features read the gradient-magnitude volumes
+    # the seeding pass uses; without, they take the gradients point by point.
     import paper_1012_1900_gb300 as g
     p = synth.workload("imrt_small")
     h, r, e = _handle(g, p)
+    m = g.gamma_model_create(3) if volumes else None
     try:
+        if volumes:
+            g.gamma_set_model(h, m)
         out = torch.empty_like(r)
         g.gamma_run(h, out)
         g.gamma_pass_rate(h)
@@ -133,6 +139,7 @@ def test_features_match_definition():
         got = X.float().cpu().numpy().astype(np.float64)
     finally:
         g.gamma_destroy(h)
+        g.gamma_model_destroy(m)
     c = p.criteria
     want = mlp.bf16_round(mlp.features(p.ref.astype(np.float64), p.eval.astype(np.float64), p.spacing,
                                        f32(c.dd_frac), f32(c.dta_mm), vox))
