@@ -50,6 +50,8 @@ WORKLOAD_DESCS = {
     "imrt_small": f"synthetic IMRT pair 36x40x24 at 2.5 mm ({_BEAMS}); 3%/3mm global",
     "plane_128": "synthetic 2D pair 128x128 at 1 mm (6 Gaussian blobs); 3%/3mm global",
 }
+# Cost gates of the learned seeding compared by --experiment learned
+SEED_GATES = (0, 9, 11, 13)
 # Algorithmic FP32 work per cell of the all-faces formulation (FMA = 2 FLOP),
 # counted from the face projection of cell_min_d2 (26 faces in 3D, 6 in 2D).
 FLOP_PER_CELL = {3: 615, 2: 103}
@@ -559,11 +561,12 @@ def experiment_learned(args):
         c = p.criteria
         crit = g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)
         res = {}
-        for mode in ("plain", "learned"):
+        for mode in ["plain"] + [f"learned{b}" for b in SEED_GATES]:
             h = g.gamma_create(ref, ev, 3, p.ref.shape, p.spacing, crit)
             try:
-                if mode == "learned":
+                if mode != "plain":
                     g.gamma_set_model(h, m)
+                    g.gamma_set_option(h, "seed_min_bucket", int(mode[len("learned"):]))
                 out = torch.empty_like(ref)
                 g.gamma_run(h, out)
                 g.gamma_pass_rate(h)
@@ -575,41 +578,50 @@ def experiment_learned(args):
                 res[mode] = (out.cpu().numpy(), ms, st)
             finally:
                 g.gamma_destroy(h)
-        a, b = res["plain"][0], res["learned"][0]
+        a = res["plain"][0]
         ok = np.isfinite(a)
-        sp, sl = res["plain"][2], res["learned"][2]
+        sp = res["plain"][2]
         tv = max(1, sp["tail_voxels"])
-        rows.append({
-            "pair": p.name, "voxels": p.nvox, "evaluated": int(ok.sum()),
-            "tail_voxels": sp["tail_voxels"],
-            "max_abs_diff": float(np.max(np.abs(a[ok] - b[ok]))) if ok.any() else 0.0,
-            "identical": bool(np.array_equal(a, b, equal_nan=True)),
-            "ms_plain": res["plain"][1], "ms_learned": res["learned"][1],
-            "cells_keyed_per_tail_voxel": [sp["cells_keyed"] / tv, sl["cells_keyed"] / tv],
-            "cells_visited_per_tail_voxel": [sp["cells_visited"] / tv, sl["cells_visited"] / tv],
-            "cells_pruned_per_tail_voxel": [sp["cells_pruned"] / tv, sl["cells_pruned"] / tv],
-            "seed_improved_frac": sl["seed_improved"] / max(1, sl["seeded"]),
-        })
+        row = {"pair": p.name, "voxels": p.nvox, "evaluated": int(ok.sum()),
+               "tail_voxels": sp["tail_voxels"], "ms_plain": res["plain"][1]}
+        for b_ in SEED_GATES:
+            b, _, sl = res[f"learned{b_}"]
+            row[f"gate{b_}"] = {
+                "ms": res[f"learned{b_}"][1], "seeded": sl["seeded"],
+                "max_abs_diff": float(np.max(np.abs(a[ok] - b[ok]))) if ok.any() else 0.0,
+                "identical": bool(np.array_equal(a, b, equal_nan=True)),
+                "cells_keyed_per_tail_voxel": [sp["cells_keyed"] / tv, sl["cells_keyed"] / tv],
+                "cells_visited_per_tail_voxel": [sp["cells_visited"] / tv, sl["cells_visited"] / tv],
+                "cells_pruned_per_tail_voxel": [sp["cells_pruned"] / tv, sl["cells_pruned"] / tv],
+                "seed_improved_frac": sl["seed_improved"] / max(1, sl["seeded"])}
+        rows.append(row)
     g.gamma_model_destroy(m)
     pool.close()
     tot_p = sum(r["ms_plain"] for r in rows)
-    tot_l = sum(r["ms_learned"] for r in rows)
     vox = sum(r["voxels"] for r in rows)
+    gates = {}
+    for b_ in SEED_GATES:
+        k = f"gate{b_}"
+        tot_l = sum(r[k]["ms"] for r in rows)
+        mean = lambda key, i: float(np.mean([r[k][key][i] for r in rows]))
+        gates[k] = {
+            "seed_min_bucket": b_, "learned_voxels_per_s": vox / (tot_l / 1000.0), "speedup": tot_p / tot_l,
+            "seeded_per_tail_voxel": float(np.mean([r[k]["seeded"] / max(1, r["tail_voxels"]) for r in rows])),
+            "all_identical": all(r[k]["identical"] for r in rows),
+            "max_abs_diff": max(r[k]["max_abs_diff"] for r in rows),
+            "cells_keyed_per_tail_voxel": [mean("cells_keyed_per_tail_voxel", i) for i in (0, 1)],
+            "cells_visited_per_tail_voxel": [mean("cells_visited_per_tail_voxel", i) for i in (0, 1)],
+            "cells_pruned_per_tail_voxel": [mean("cells_pruned_per_tail_voxel", i) for i in (0, 1)],
+            "seed_improved_frac": float(np.mean([r[k]["seed_improved_frac"] for r in rows])),
+        }
     summary = {
         "experiment": "learned", "criteria": "2%/2mm global, 10% cutoff",
         "train_pairs": args.train_pairs, "test_pairs": len(rows),
         "train_steps": args.train_steps, "final_loss": float(np.mean(losses[-50:])) if losses else None,
         "first_loss": float(np.mean(losses[:10])) if losses else None,
         "train_seconds": t_train,
-        "plain_voxels_per_s": vox / (tot_p / 1000.0), "learned_voxels_per_s": vox / (tot_l / 1000.0),
-        "speedup": tot_p / tot_l,
-        "all_identical": all(r["identical"] for r in rows),
-        "max_abs_diff": max(r["max_abs_diff"] for r in rows),
-        "cells_keyed_per_tail_voxel": [float(np.mean([r["cells_keyed_per_tail_voxel"][k] for r in rows])) for k in (0, 1)],
-        "cells_visited_per_tail_voxel": [float(np.mean([r["cells_visited_per_tail_voxel"][k] for r in rows])) for k in (0, 1)],
-        "cells_pruned_per_tail_voxel": [float(np.mean([r["cells_pruned_per_tail_voxel"][k] for r in rows])) for k in (0, 1)],
-        "seed_improved_frac": float(np.mean([r["seed_improved_frac"] for r in rows])),
-        "fallback_frac": 1.0 - float(np.mean([r["seed_improved_frac"] for r in rows])),
+        "plain_voxels_per_s": vox / (tot_p / 1000.0),
+        "gates": gates,
         "pairs": rows,
     }
     print(json.dumps(summary), flush=True)
