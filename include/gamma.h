@@ -227,7 +227,7 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     sort.  Same results; allocates 16 bytes per voxel.
  *  "seed_min_bucket"  with a model attached: only queued voxels whose cost
  *                     bucket (1 + floor(2 log2 cells with key < gamma0)) is
- *                     at least this get a proposal (default 9: >= 16 cells);
+ *                     at least this get a proposal (default 13: >= 64 cells);
  *                     0 seeds every queued voxel
  *  "drop_slab_flag"   failure test: k + 1 leaves slab k's readiness flag
  *                     unwritten in overlapped runs, so that the gated shell's

@@ -116,7 +116,7 @@ struct gamma_ctx {
     gamma_model model = nullptr;      // attached proposal network (may be null)
     float* gnorm = nullptr;           // with a model: gradient magnitudes of both doses (2 x nvox)
     unsigned* seed_list = nullptr;    // with a model: queue items past the cost gate (tail_cap)
-    int seed_min_bucket = 9;          // cost gate of the seeding pass (bucket of >= 16 cells)
+    int seed_min_bucket = 13;         // cost gate of the seeding pass (bucket of >= 64 cells)
     bool own_model = false;
     // per-phase events: 0 start, 1 after h2d, 2 after prepare, 3 after shell,
     // 4 after order, 5 after tail, 6 after d2h
