@@ -456,6 +456,14 @@ def run_ours(args, pair, rank, world, local_rank):
                                       if sm_load else None),
             "load_clock_mhz": sm_load}
 
+    # the cost law of the paper's timing studies: time follows sum gamma^3 (Fig. 1b)
+    gm = out.double()
+    gm = gm[torch.isfinite(gm)].cpu().numpy()
+    edges = [0.0, 1e-3, 1e-2, 0.1, 0.3, 1.0, 3.0, 10.0, float("inf")]
+    hist, _ = np.histogram(gm ** 3, bins=edges)
+    gamma3 = {"sum": float(np.sum(gm ** 3)), "bin_edges": edges[:-1] + ["inf"],
+              "counts": [int(c) for c in hist]}
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         import oracle
@@ -479,7 +487,11 @@ def run_ours(args, pair, rank, world, local_rank):
         "autotuned": tuned,
         "search": {"tail_voxels": stats["tail_voxels"], "overflow_voxels": stats["overflow_voxels"],
                    "fp64_cells": stats["fp64_cells"], "table_entries": stats["table_entries"],
-                   "r_max": stats["r_max"], "shell_cells": shell_cells, "tail_cells": tail_cells},
+                   "r_max": stats["r_max"], "shell_cells": shell_cells, "tail_cells": tail_cells,
+                   "evaluated_voxels_per_s": value * n_eval / pair.nvox,
+                   "cells_per_evaluated_voxel": ((shell_cells + tail_cells) / max(1, n_eval)
+                                                 if shell_cells is not None else None),
+                   "gamma3": gamma3},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
