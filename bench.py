@@ -457,8 +457,8 @@ def run_ours(args, pair, rank, world, local_rank):
             "load_clock_mhz": sm_load}
 
     # the cost law of the paper's timing studies: time follows sum gamma^3 (Fig. 1b)
-    gm = out.double()
-    gm = gm[torch.isfinite(gm)].cpu().numpy()
+    gm = out.cpu().numpy().astype(np.float64)
+    gm = gm[np.isfinite(gm)]
     edges = [0.0, 1e-3, 1e-2, 0.1, 0.3, 1.0, 3.0, 10.0, float("inf")]
     hist, _ = np.histogram(gm ** 3, bins=edges)
     gamma3 = {"sum": float(np.sum(gm ** 3)), "bin_edges": edges[:-1] + ["inf"],
