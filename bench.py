@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per queued voxel (0: library default)")
     ap.add_argument("--shell-blocks", type=int, default=0, help="key-0 kernel blocks per SM (1-4)")
-    ap.add_argument("--tail-blocks", type=int, default=0, help="table-walk kernel blocks per SM (1-2)")
+    ap.add_argument("--tail-blocks", type=int, default=0, help="table-walk kernel blocks per SM (1-3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")

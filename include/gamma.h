@@ -217,7 +217,7 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     change between (not with "timing", a model or "design")
  *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell
  *                     kernel's register budget is sized for (default 2)
- *  "tail_blocks_per_sm"   1 or 2: the same for the table-walk kernel
+ *  "tail_blocks_per_sm"   1 to 3: the same for the table-walk kernel
  *                     (default 2)
  *  "design"           ablation of the paper's GPU design (Algorithm A2;
  *                     single-pair handles): 0 this library's two-phase search
@@ -286,7 +286,7 @@ int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
 
 /* Autotuner: times the full run (single or batch handle) for every
  * combination of lanes_per_voxel in {4, 8, 16, 32}, shell_blocks_per_sm in
- * {1, 2, 3, 4} and tail_blocks_per_sm in {1, 2} (one warm-up and `reps` timed
+ * {1, 2, 3, 4} and tail_blocks_per_sm in {1, 2, 3} (two warm-ups and `reps` timed
  * runs each, CUDA events on `cuda_stream`), keeps the fastest as the handle's
  * options and returns it (any output pointer may be NULL).  gamma_out_dev receives the
  * gamma map of a single-pair handle (device, nz*ny*nx floats) and is ignored

@@ -1175,7 +1175,7 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "tail_blocks_per_sm")) {
-        if (value < 1 || value > 2) return GAMMA_ERR_INVALID_ARG;
+        if (value < 1 || value > 3) return GAMMA_ERR_INVALID_ARG;
         h->tail_minblocks = (int)value;
         return GAMMA_OK;
     }
@@ -1335,7 +1335,7 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     auto run = [&]() { return h->batch ? gamma_batch_run(h, s) : gamma_run(h, gamma_out_dev, s); };
     for (int li = 0; li < 4 && rc == GAMMA_OK; ++li)
         for (int bl = 1; bl <= 4 && rc == GAMMA_OK; ++bl)
-            for (int tb = 1; tb <= 2 && rc == GAMMA_OK; ++tb) {
+            for (int tb = 1; tb <= 3 && rc == GAMMA_OK; ++tb) {
                 h->lanes = lanes[li];
                 h->shell_minblocks = bl;
                 h->tail_minblocks = tb;

@@ -924,12 +924,14 @@ static void launch_tail_g(const Problem& P, const BatchDesc* bd, int G, int grid
 }
 
 // k_tail with G lanes per queued voxel and its register budget sized for
-// `per_sm` resident blocks (1 or 2).
+// `per_sm` resident blocks (1 to 3; 3 spills a little and is still the
+// fastest on the benchmark workload).
 template <int N, bool BATCH>
 static void launch_tail_n(const Problem& P, const BatchDesc* bd, int G, int per_sm, int grid,
                           cudaStream_t s)
 {
-    if (per_sm >= 2) launch_tail_g<N, 2, BATCH>(P, bd, G, grid, s);
+    if (per_sm >= 3) launch_tail_g<N, 3, BATCH>(P, bd, G, grid, s);
+    else if (per_sm == 2) launch_tail_g<N, 2, BATCH>(P, bd, G, grid, s);
     else launch_tail_g<N, 1, BATCH>(P, bd, G, grid, s);
 }
 
