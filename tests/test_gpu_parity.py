@@ -487,3 +487,28 @@ def test_graph_replay_matches_direct_launches():
     finally:
         g.gamma_destroy(h0)
         g.gamma_destroy(h)
+
+
+def test_imrt_320_global_sampled():
+    p = synth.workload("imrt_320_global")
+    _full_size_check(p, p.criteria, 6000)
+
+
+def test_plane_128_host_run_matches_oracle():
+    # The 2D workload through the overlapped host-buffer path, in full.
+    import paper_1012_1900_gb300 as g
+    p = synth.workload("plane_128")
+    c = p.criteria
+    ndim, shape, sp = _geom(p.ref, p.spacing)
+    h = g.gamma_create(None, None, ndim, shape, sp,
+                       g.criteria(c.dd_frac, c.dta_mm, cutoff_frac=c.cutoff_frac))
+    try:
+        r = torch.from_numpy(p.ref).pin_memory()
+        e = torch.from_numpy(p.eval).pin_memory()
+        o = torch.empty_like(r).pin_memory()
+        g.gamma_run_host(h, r, e, o)
+        counts = g.gamma_pass_rate(h)
+    finally:
+        g.gamma_destroy(h)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, c)
+    assert_parity(o.numpy().astype(np.float64), want, counts)
