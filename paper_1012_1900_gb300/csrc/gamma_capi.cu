@@ -846,8 +846,8 @@ WriteValueFn write_value_fn()
 // and their final values are then written into the host map directly.
 // Without TMA tile loads or the stream write, the shell waits for the whole
 // dose instead.
-int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_host,
-                       float* gamma_out_host, float* out_mapped, cudaStream_t s)
+int run_host_pipelined(gamma_handle h, const float* eval_host, float* gamma_out_host,
+                       float* out_mapped, cudaStream_t s)
 {
     for (auto& st : h->pipe_s)
         if (!st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -881,12 +881,11 @@ int run_host_pipelined(gamma_handle h, const float* ref_host, const float* eval_
     const size_t bytes = sizeof(float) * (size_t)h->nvox;
     const unsigned epoch = ++h->epoch == 0 ? ++h->epoch : h->epoch;    // 0 is the flags' initial value
 
-    if (tm) CK(cudaEventRecord(h->tev[0], s));
+    // the caller has already queued the reference dose's copy on s
     CK(cudaEventRecord(E[0], s));
     CK(cudaStreamWaitEvent(c, E[0], 0));
     CK(cudaStreamWaitEvent(o, E[0], 0));
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), c));
-    CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(E[1], s));
     CK(cudaStreamWaitEvent(c, E[1], 0));
     CK(gk::launch_prepare(P, c, 1));
@@ -949,18 +948,18 @@ int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    {
-        const size_t nb = sizeof(float) * (size_t)h->nvox;
-        float* out_mapped = nullptr;
-        if (!h->grids && !h->batch && h->design == 0 && !h->model && h->pipeline &&
-            mapped_host(ref_host, nb) && mapped_host(eval_host, nb) &&
-            (out_mapped = (float*)mapped_host(gamma_out_host, nb)) != nullptr)
-            return run_host_pipelined(h, ref_host, eval_host, gamma_out_host, out_mapped, s);
-    }
     const size_t bytes = sizeof(float) * (size_t)h->nvox;
     const bool tm = h->timing != 0;
+    // both paths start with the reference dose: queue it before choosing one
     if (tm) CK(cudaEventRecord(h->tev[0], s));
     CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
+    {
+        float* out_mapped = nullptr;
+        if (!h->grids && !h->batch && h->design == 0 && !h->model && h->pipeline &&
+            mapped_host(ref_host, bytes) && mapped_host(eval_host, bytes) &&
+            (out_mapped = (float*)mapped_host(gamma_out_host, bytes)) != nullptr)
+            return run_host_pipelined(h, eval_host, gamma_out_host, out_mapped, s);
+    }
     CK(cudaMemcpyAsync(h->own_ev, eval_host, bytes, cudaMemcpyHostToDevice, s));
     if (tm) CK(cudaEventRecord(h->tev[1], s));
     h->ev_h2d = true;
