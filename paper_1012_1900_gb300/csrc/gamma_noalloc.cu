@@ -219,6 +219,7 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
     P.tail_bucket = base + kOffBucket;
     P.tail_sorted = nullptr;
     P.sort_tail = 0;
+    P.shell_minblocks = 4;               // the launch shapes the autotuner picks on the benchmark workload
 
     if (ntable > 0 &&
         cudaMemcpyAsync(base + kOffTable, g_table_host, sizeof(gk::TableEntry) * ntable,
@@ -229,7 +230,7 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
         return GAMMA_ERR_CUDA;
     if (gk::launch_prepare(P, s, 1) != cudaSuccess) return GAMMA_ERR_CUDA;
     if (gk::launch_shell(P, s) != cudaSuccess) return GAMMA_ERR_CUDA;
-    if (gk::launch_tail(P, 8, 2, s) != cudaSuccess) return GAMMA_ERR_CUDA;
+    if (gk::launch_tail(P, 4, 3, s) != cudaSuccess) return GAMMA_ERR_CUDA;
 
     if (n_eval || n_pass) {
         gk::Counters c;
