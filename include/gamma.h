@@ -198,7 +198,7 @@ int gamma_get_stats(gamma_handle h, gamma_stats *out);
 int gamma_get_timings(gamma_handle h, gamma_timings *out);
 
 /* Tuning and diagnostic options (take effect at the next run):
- *  "lanes_per_voxel"  4, 8, 16 or 32 lanes search one queued voxel together
+ *  "lanes_per_voxel"  2, 4, 8, 16 or 32 lanes search one queued voxel together
  *  "table_cap"        maximum cell-table length (rebuilds the table)
  *  "fp64_tau_exp10"   FP64 redo when the normalised Gram determinant
  *                     det(G)/prod(G_ii) < 10^-value; value <= 0 disables it
@@ -285,7 +285,7 @@ int gamma_batch_pass_rate(gamma_handle h, int pair, double *rate, int64_t *n_eva
 int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
 
 /* Autotuner: times the full run (single or batch handle) for every
- * combination of lanes_per_voxel in {4, 8, 16, 32}, shell_blocks_per_sm in
+ * combination of lanes_per_voxel in {2, 4, 8, 16, 32}, shell_blocks_per_sm in
  * {1, 2, 3, 4} and tail_blocks_per_sm in {1, 2, 3} (two warm-ups and `reps` timed
  * runs each, CUDA events on `cuda_stream`), keeps the fastest as the handle's
  * options and returns it (any output pointer may be NULL).  gamma_out_dev receives the

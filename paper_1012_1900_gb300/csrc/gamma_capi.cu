@@ -1113,7 +1113,7 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "lanes_per_voxel")) {
-        if (value != 4 && value != 8 && value != 16 && value != 32) return GAMMA_ERR_INVALID_ARG;
+        if (value != 2 && value != 4 && value != 8 && value != 16 && value != 32) return GAMMA_ERR_INVALID_ARG;
         h->lanes = (int)value;
         return GAMMA_OK;
     }
@@ -1327,12 +1327,12 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int lanes[4] = {4, 8, 16, 32};
+    const int lanes[5] = {2, 4, 8, 16, 32};
     int best_l = h->lanes, best_b = h->shell_minblocks, best_t = h->tail_minblocks;
     float best = INFINITY;
     int rc = GAMMA_OK;
     auto run = [&]() { return h->batch ? gamma_batch_run(h, s) : gamma_run(h, gamma_out_dev, s); };
-    for (int li = 0; li < 4 && rc == GAMMA_OK; ++li)
+    for (int li = 0; li < 5 && rc == GAMMA_OK; ++li)
         for (int bl = 1; bl <= 4 && rc == GAMMA_OK; ++bl)
             for (int tb = 1; tb <= 3 && rc == GAMMA_OK; ++tb) {
                 h->lanes = lanes[li];

@@ -916,6 +916,7 @@ template <int N, int MINB, bool BATCH>
 static void launch_tail_g(const Problem& P, const BatchDesc* bd, int G, int grid, cudaStream_t s)
 {
     switch (G) {
+    case 2: k_tail<N, 2, MINB, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
     case 4: k_tail<N, 4, MINB, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
     case 8: k_tail<N, 8, MINB, BATCH><<<grid, 256, 0, s>>>(P, bd); break;
     case 16: k_tail<N, 16, MINB, BATCH><<<grid, 256, 0, s>>>(P, bd); break;

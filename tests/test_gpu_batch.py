@@ -105,7 +105,7 @@ def test_autotune_single_and_batch():
     h = g.gamma_create(r, e, 3, p.ref.shape, p.spacing, g.criteria(c.dd_frac, c.dta_mm))
     try:
         t = g.gamma_autotune(h, o, reps=2)
-        assert t["lanes_per_voxel"] in (4, 8, 16, 32) and t["shell_blocks_per_sm"] in (1, 2, 3, 4)
+        assert t["lanes_per_voxel"] in (2, 4, 8, 16, 32) and t["shell_blocks_per_sm"] in (1, 2, 3, 4)
         assert t["tail_blocks_per_sm"] in (1, 2, 3) and t["ms"] > 0
         g.gamma_run(h, o)
         g.gamma_pass_rate(h)

@@ -147,7 +147,7 @@ def test_volume_ragged_anisotropic():
     assert_parity(got, want, counts)
 
 
-@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
 @pytest.mark.parametrize("sort_tail,tail_blocks", [(0, 1), (1, 2), (1, 1), (1, 3), (0, 3)])
 def test_launch_shapes_agree(lanes, sort_tail, tail_blocks):
     p = synth.workload("imrt_small")
