@@ -171,9 +171,9 @@ int gamma_run(gamma_handle h, float *gamma_out_dev, void *cuda_stream);
  * cudaMallocHost / pinned tensors) and option "pipeline" is not 0, the
  * copies overlap the search: the reference dose is copied first and reduced
  * while the evaluation dose follows in z slabs; the shell starts as soon as
- * the dose norm is known, each of its tiles waiting (bounded) for the slab
- * that holds the last slice it reads, which a stream write after the slab's
- * copy announces; the map is copied out while the queued voxels are
+ * the dose norm is known, each of its tiles waiting (bounded) for the slabs
+ * that hold the slices it reads, which a stream write after each slab's copy
+ * announces; the map is copied out while the queued voxels are
  * searched, and a kernel then writes their final values into gamma_out_host
  * through its mapped address.  That work runs on two streams the handle
  * owns, ordered after all earlier work on `cuda_stream`, which in turn waits
