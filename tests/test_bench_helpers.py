@@ -1,0 +1,57 @@
+"""CPU checks of the benchmark's measurement helpers: the cell census that the
+roofline's algorithmic work is counted from, against a brute-force count."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import bench
+
+
+def _brute_census(gamma, spacing, dta):
+    """For every evaluated voxel v and every cell whose lower corner v + c lies
+    inside the grid: count it when its box distance / dta is below gamma(v),
+    split into the cells whose box contains v (distance 0) and the others."""
+    nd = gamma.ndim
+    shape = gamma.shape                                  # (z, y, x) or (y, x)
+    hn = np.array(spacing[::-1], dtype=np.float64) / dta  # x, y[, z]
+    dims = shape[::-1]
+    shell = tail = 0
+    for idx in itertools.product(*[range(n) for n in shape]):
+        g = gamma[idx]
+        if not np.isfinite(g):
+            continue
+        v = idx[::-1]                                    # x, y[, z]
+        lim = [int(math.ceil(g / h)) + 1 for h in hn]
+        for c in itertools.product(*[range(-l - 1, l + 1) for l in lim]):
+            if any(not (0 <= v[a] + c[a] <= dims[a] - 1) for a in range(nd)):
+                continue
+            gap = [max(c[a], -c[a] - 1, 0) * hn[a] for a in range(nd)]
+            key = math.sqrt(sum(x * x for x in gap))
+            if key < g:
+                if key == 0.0:
+                    shell += 1
+                else:
+                    tail += 1
+    return shell, tail
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_cell_census_matches_brute_force(nd):
+    rng = np.random.default_rng(5 + nd)
+    shape = (9, 11) if nd == 2 else (5, 6, 7)
+    spacing = (1.0, 1.5) if nd == 2 else (2.0, 1.5, 1.25)
+    gamma = rng.uniform(0.0, 2.5, shape)
+    gamma[rng.uniform(size=shape) < 0.3] = np.nan       # voxels below the cutoff
+    gamma[(0,) * nd] = 0.0                               # gamma = 0 certifies nothing
+    want = _brute_census(gamma, spacing, 2.0)
+    got = bench.cell_census(torch.from_numpy(gamma), spacing, 2.0)
+    assert tuple(int(x) for x in got) == want
+
+
+def test_cell_census_empty_map():
+    gamma = np.full((4, 5, 6), np.nan)
+    assert tuple(bench.cell_census(torch.from_numpy(gamma), (1.0, 1.0, 1.0), 3.0)) == (0, 0)
