@@ -849,10 +849,6 @@ WriteValueFn write_value_fn()
 int run_host_pipelined(gamma_handle h, const float* eval_host, float* gamma_out_host,
                        float* out_mapped, cudaStream_t s)
 {
-    for (auto& st : h->pipe_s)
-        if (!st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    for (auto& e : h->pipe_ev)
-        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : h->slab_ev)
         if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (!h->host_ctr) {
@@ -881,8 +877,8 @@ int run_host_pipelined(gamma_handle h, const float* eval_host, float* gamma_out_
     const size_t bytes = sizeof(float) * (size_t)h->nvox;
     const unsigned epoch = ++h->epoch == 0 ? ++h->epoch : h->epoch;    // 0 is the flags' initial value
 
-    // the caller has already queued the reference dose's copy on s
-    CK(cudaEventRecord(E[0], s));
+    // the caller has already recorded E[0] (earlier work on s) and queued the
+    // reference dose's copy after it
     CK(cudaStreamWaitEvent(c, E[0], 0));
     CK(cudaStreamWaitEvent(o, E[0], 0));
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), c));
@@ -950,13 +946,22 @@ int gamma_run_host(gamma_handle h, const float* ref_host, const float* eval_host
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const size_t bytes = sizeof(float) * (size_t)h->nvox;
     const bool tm = h->timing != 0;
-    // both paths start with the reference dose: queue it before choosing one
+    // both paths start with the reference dose: queue it before choosing one;
+    // E[0] marks the work already on s, which the overlapped path's own
+    // streams wait for (not for this copy)
     if (tm) CK(cudaEventRecord(h->tev[0], s));
+    const bool may_overlap = !h->grids && !h->batch && h->design == 0 && !h->model && h->pipeline;
+    if (may_overlap) {
+        for (auto& st : h->pipe_s)
+            if (!st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        for (auto& e : h->pipe_ev)
+            if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CK(cudaEventRecord(h->pipe_ev[0], s));
+    }
     CK(cudaMemcpyAsync(h->own_ref, ref_host, bytes, cudaMemcpyHostToDevice, s));
     {
         float* out_mapped = nullptr;
-        if (!h->grids && !h->batch && h->design == 0 && !h->model && h->pipeline &&
-            mapped_host(ref_host, bytes) && mapped_host(eval_host, bytes) &&
+        if (may_overlap && mapped_host(ref_host, bytes) && mapped_host(eval_host, bytes) &&
             (out_mapped = (float*)mapped_host(gamma_out_host, bytes)) != nullptr)
             return run_host_pipelined(h, eval_host, gamma_out_host, out_mapped, s);
     }
