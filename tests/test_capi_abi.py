@@ -89,3 +89,17 @@ def test_product_and_oracle_are_independent():
     for f in glob.glob(os.path.join(ROOT, "oracle", "*.c")):
         incs = re.findall(r'#include\s+[<"]([^>"]+)', open(f).read())
         assert all(i in ("math.h", "stdint.h", "stdlib.h", "string.h", "omp.h") for i in incs), incs
+
+
+def test_more_argument_validation_without_gpu(lib):
+    # Entry points that must reject bad arguments before touching a device.
+    import ctypes
+    INVALID = -1
+    assert lib.gamma_measure_fp32_peak(None, None, None) == INVALID
+    assert lib.gamma_set_option(None, b"pipeline", 1) == INVALID
+    assert lib.gamma_run_host(None, None, None, None, None) == INVALID
+    assert lib.gamma_run(None, None, None) == INVALID
+    assert lib.gamma_pass_rate(None, None, None, None) == INVALID
+    out = ctypes.c_void_p()
+    assert lib.gamma_batch_create(ctypes.byref(out), 0, None) == INVALID
+    assert lib.gamma_batch_create(ctypes.byref(out), 70000, None) == INVALID
