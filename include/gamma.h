@@ -208,7 +208,7 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *  "timing"           1: record per-phase CUDA events (gamma_get_timings)
  *  "pipeline"         gamma_run_host on page-locked buffers: 1 to 8 overlaps
  *                     the copies with the search, the evaluation dose in that
- *                     many z slabs (default 4; 1: the shell waits for the
+ *                     many z slabs (default 8; 1: the shell waits for the
  *                     whole dose); 0 runs in order
  *  "graph"            0 launches directly instead of capturing and replaying
  *                     a CUDA graph (default 1).  Batch handles capture at

@@ -109,7 +109,7 @@ struct gamma_ctx {
     int timing = 0;
     int shell_minblocks = 2;
     int tail_minblocks = 2;
-    int pipeline = 4;        // gamma_run_host: z slabs of the overlapped path (0: run in order)
+    int pipeline = 8;        // gamma_run_host: z slabs of the overlapped path (0: run in order)
     int design = 0;          // 0: two-phase search; 1 / 2: the paper's A2 with / without DD sort
     int face_eval = 0;       // design 1 / 2: 0 closed-form faces, 1 Ju's recursion
     gk::PaperScratch paper;
