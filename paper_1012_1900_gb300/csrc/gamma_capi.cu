@@ -838,14 +838,14 @@ WriteValueFn write_value_fn()
 }
 
 // Host-buffer run with the copies overlapped.  The reference dose is copied
-// first and its norm taken on the compute stream while the evaluation dose
-// follows in z slabs on the same copy stream.  The shell is one launch that
-// starts once the norm is known: once a slab's copy has completed, a stream
-// write on a second stream raises that slab's flag, and each tile waits
-// (bounded) for the slabs its box reads.  The map is copied out while the queued voxels are searched,
-// and their final values are then written into the host map directly.
-// Without TMA tile loads or the stream write, the shell waits for the whole
-// dose instead.
+// first (the caller has queued it) and its norm taken on the compute stream
+// while the evaluation dose follows in z slabs on the same copy stream.  The
+// shell is one launch that starts once the norm is known: once a slab's copy
+// has completed, a stream write on a second stream raises that slab's flag,
+// and each tile waits (bounded) for the slabs its box reads.  The map is
+// copied out while the queued voxels are searched, and their final values are
+// then written into the host map directly, with the run's counters.  Without
+// TMA tile loads or the stream write, the shell waits for the whole dose.
 int run_host_pipelined(gamma_handle h, const float* eval_host, float* gamma_out_host,
                        float* out_mapped, cudaStream_t s)
 {
