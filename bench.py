@@ -58,6 +58,9 @@ FLOP_PER_CELL = {3: 615, 2: 103}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 KERNELS_PER_RUN = 4          # prepare, shell, scatter, tail
+LOAD_S = 1.5                 # back-to-back maps before the timed steps (clock samples)
+# gamma within this distance of 1 may pass on one side and fail on the other
+TIE_BAND = 1e-4
 
 
 def parse():
@@ -91,14 +94,18 @@ def parse():
 # --------------------------------------------------------------------------
 
 class ClockSampler:
+    """nvidia-smi samples (every 100 ms) with their arrival times, so that the
+    clock record can be restricted to a window of back-to-back GPU work."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []            # (monotonic time, line)
+        self.window = None
 
     def start(self):
         try:
@@ -113,34 +120,46 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark_window(self, t0: float, t1: float):
+        """The interval (monotonic seconds) of back-to-back GPU work."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)                    # the sample taken at the window's end
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = []
+        for t, ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
+                rows.append((t, float(parts[0]), float(parts[1]), float(parts[2]), parts[4:8]))
             except ValueError:
                 continue
-            for name, val in zip(names, parts[4:8]):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = rows
+        if self.window:
+            # a line arrives up to one period after its sample
+            load = [r for r in rows if self.window[0] + 0.1 <= r[0] <= self.window[1] + 0.1] or rows
+        reasons = set()
+        for r in load:
+            for name, val in zip(self.NAMES, r[4]):
                 if val.lower() == "active":
                     reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in load),
+                "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load),
+                "power_w_max_under_load": max(r[3] for r in load),
+                "load_window_s": (self.window[1] - self.window[0]) if self.window else None}
 
 
 # --------------------------------------------------------------------------
@@ -148,11 +167,12 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 
 def cell_census(gamma, spacing, dta: float):
-    """Cells the exact search must certify: for every evaluated voxel, the cells
-    (lower corner p = v + c inside the grid) whose box distance / dta is below
-    gamma*.  gamma: the gamma map as a torch tensor (NaN = not evaluated).
-    Returns (key-0 cells, other cells) summed over voxels.  A measurement
-    helper: it only counts, from the finished map."""
+    """Cells the exact search must certify: for every evaluated voxel, the grid
+    cubes (lower corner p = v + c with the whole cube inside the grid) whose
+    box distance / dta is below gamma*, plus one for the voxel's final stop
+    test.  gamma: the gamma map as a torch tensor (NaN = not evaluated).
+    Returns (key-0 cubes + one per voxel, other cubes) summed over voxels.  A
+    measurement helper: it only counts, from the finished map."""
     import torch
     nd = gamma.dim()
     shape = tuple(gamma.shape)
@@ -170,9 +190,11 @@ def cell_census(gamma, spacing, dta: float):
     offs, keys = offs[keep], keys[keep]
     dims = shape[::-1]                                   # n_x, n_y[, n_z]
     ar = [torch.arange(n, device=g.device) for n in dims]
-    shell = tail = 0
+    shell = int(torch.count_nonzero(g >= 0.0))          # the +1 per evaluated voxel
+    tail = 0
     for off, key in zip(offs, keys):
-        masks = [((a + int(o)) >= 0) & ((a + int(o)) <= n - 1) for a, o, n in zip(ar, off, dims)]
+        # a whole cube: its lower corner at 0 .. n - 2 on every axis
+        masks = [((a + int(o)) >= 0) & ((a + int(o)) <= n - 2) for a, o, n in zip(ar, off, dims)]
         if nd == 3:
             inside = masks[2][:, None, None] & masks[1][None, :, None] & masks[0][None, None, :]
         else:
@@ -189,25 +211,70 @@ def cell_census(gamma, spacing, dta: float):
 # CPU oracle timing (cpu_baseline and the reference arm)
 # --------------------------------------------------------------------------
 
-def time_oracle(pair, target_s: float, seed: int = 0):
-    """Time the FP64 oracle on a uniform random sample of grid voxels sized to
-    about target_s seconds; returns (voxels/s, sample size, seconds, threads)."""
+def sample_text(n: int, nvox: int, dt: float) -> str:
+    if n >= nvox:
+        return f"full grid of {nvox} voxels x {n / nvox:.3g} passes, {dt:.1f} s"
+    return f"{n} of {nvox} grid voxels (uniform random), {dt:.1f} s"
+
+
+def time_oracle(pair, target_s: float, seed: int = 0, threads: int = 0, keep: bool = False):
+    """Time the FP64 oracle on about target_s seconds of work: a uniform random
+    sample of grid voxels, or whole-grid passes repeated when one pass takes
+    less.  Returns (voxels/s, voxels, seconds, threads, gamma of the first
+    whole-grid pass or None)."""
     import oracle
     c = pair.criteria
     f32 = lambda x: float(np.float32(x))
+
+    def run(idx):
+        return oracle.gamma(pair.ref, pair.eval, pair.spacing, f32(c.dd_frac), f32(c.dta_mm),
+                            local=c.local, cutoff_frac=f32(c.cutoff_frac),
+                            dose_norm=f32(c.dose_norm), idx=idx, threads=threads)
+
     rng = np.random.default_rng(seed)
     probe = rng.choice(pair.nvox, min(pair.nvox, 50000), replace=False)
     t0 = time.perf_counter()
-    oracle.gamma(pair.ref, pair.eval, pair.spacing, f32(c.dd_frac), f32(c.dta_mm), local=c.local,
-                 cutoff_frac=f32(c.cutoff_frac), dose_norm=f32(c.dose_norm), idx=probe)
+    run(probe)
     dt = max(time.perf_counter() - t0, 1e-3)
-    n = int(min(pair.nvox, max(probe.size, probe.size * target_s / dt)))
-    idx = None if n >= pair.nvox else rng.choice(pair.nvox, n, replace=False)
-    t0 = time.perf_counter()
-    oracle.gamma(pair.ref, pair.eval, pair.spacing, f32(c.dd_frac), f32(c.dta_mm), local=c.local,
-                 cutoff_frac=f32(c.cutoff_frac), dose_norm=f32(c.dose_norm), idx=idx)
-    dt = time.perf_counter() - t0
-    return n / dt, n, dt, oracle.max_threads()
+    n = int(max(probe.size, probe.size * target_s / dt))
+    kept = None
+    if n < pair.nvox and not keep:
+        idx = rng.choice(pair.nvox, n, replace=False)
+        t0 = time.perf_counter()
+        run(idx)
+        dt = time.perf_counter() - t0
+    else:
+        n, dt = 0, 0.0
+        while dt < target_s or n == 0:          # whole-grid passes
+            t0 = time.perf_counter()
+            out = run(None)
+            dt += time.perf_counter() - t0
+            n += pair.nvox
+            if kept is None:
+                kept = out
+    used = threads if threads > 0 else oracle.max_threads()
+    return n / dt, n, dt, used, kept
+
+
+def parity_report(want, got, got_fp32, stats):
+    """max |dgamma| and pass/fail mismatches of the GPU maps against the
+    oracle's full-grid gamma (float64, NaN = not evaluated)."""
+    def one(m):
+        same_mask = bool(np.array_equal(np.isnan(m), np.isnan(want)))
+        ok = np.isfinite(want) & np.isfinite(m)
+        err = np.abs(m[ok] - want[ok])
+        band = np.abs(want[ok] - 1.0) < TIE_BAND
+        flips = int(np.count_nonzero(((m[ok] <= 1.0) != (want[ok] <= 1.0)) & ~band))
+        return {"max_abs_dgamma": float(err.max()) if err.size else 0.0,
+                "mean_abs_dgamma": float(err.mean()) if err.size else 0.0,
+                "pass_fail_mismatches_outside_tie_band": flips, "masks_identical": same_mask}
+    rep = {"oracle_sample": f"every grid voxel ({want.size}, {int(np.isfinite(want).sum())} "
+                            f"evaluated), FP64 oracle", "tolerance": 1e-4, "tie_band": TIE_BAND}
+    rep.update(one(got))
+    rep["fp32_only"] = one(got_fp32)
+    rep["fp32_only"]["note"] = "option fp64_tau_exp10 = 0: no FP64 redo of near-singular cells"
+    rep["fp64_redo_cells"] = stats.get("fp64_cells")
+    return rep
 
 
 def run_reference(args, pair, rank, world):
@@ -221,13 +288,11 @@ def run_reference(args, pair, rank, world):
     times, voxels = [], []
     threads = 0
     for k in range(args.steps):
-        rate, n, dt, threads = time_oracle(pair, per_step_s, seed=k + 1)
+        rate, n, dt, threads, _ = time_oracle(pair, per_step_s, seed=k + 1)
         times.append(dt)
         voxels.append(n)
     value = sum(voxels) / sum(times)
-    sample = (f"uniform random sample of {voxels[0]} of {pair.nvox} grid voxels per step "
-              f"(full grid)" if voxels[0] >= pair.nvox else
-              f"uniform random sample of ~{int(statistics.mean(voxels))} of {pair.nvox} grid voxels per step")
+    sample = "per step: " + sample_text(voxels[0], pair.nvox, times[0])
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
@@ -354,6 +419,14 @@ def run_ours(args, pair, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         sampler.start()
         time.sleep(0.3)
+        # back-to-back maps for about LOAD_S seconds right before the timed
+        # steps, so that the clock samples describe the GPU under this load
+        t_load = time.monotonic()
+        while time.monotonic() - t_load < LOAD_S:
+            for _ in range(50):
+                flush.zero_()
+                g.gamma_run(h, out, stream)
+            torch.cuda.synchronize(dev)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         for k in range(args.steps):
@@ -362,6 +435,7 @@ def run_ours(args, pair, rank, world, local_rank):
             g.gamma_run(h, out, stream)
             ends[k].record(stream)
         torch.cuda.synchronize(dev)
+        sampler.mark_window(t_load, time.monotonic())
         barrier()
         clocks = sampler.stop()
         # per-phase split from as many further runs, with the library's own
@@ -413,6 +487,16 @@ def run_ours(args, pair, rank, world, local_rank):
             e2e["timeline_ms"] = {k: statistics.median([t[k] for t in tl]) for k in tl[0]}
         finally:
             g.gamma_destroy(hh)
+    # the same map with the FP64 redo of near-singular cells switched off
+    # (FP32 only), for the parity report; outside every timed region
+    gmap = out.cpu().numpy().astype(np.float64)
+    g.gamma_set_option(h, "fp64_tau_exp10", 0)
+    g.gamma_run(h, out, stream)
+    g.gamma_pass_rate(h)
+    gmap_fp32 = out.cpu().numpy().astype(np.float64)
+    g.gamma_set_option(h, "fp64_tau_exp10", 6)
+    g.gamma_run(h, out, stream)
+    g.gamma_pass_rate(h)
     g.gamma_destroy(h)
 
     if rank != 0:
@@ -474,14 +558,18 @@ def run_ours(args, pair, rank, world, local_rank):
               "counts": [int(c) for c in hist]}
 
     cpu = None
+    parity = None
     if not args.no_cpu_baseline and world == 1:
         import oracle
         oracle.build()
-        v, n, dt, threads = time_oracle(pair, 15.0)
+        v, n, dt, threads, want = time_oracle(pair, 12.0, keep=True)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": (f"{n} of {pair.nvox} grid voxels" +
-                          (" (full grid)" if n >= pair.nvox else ", uniform random") +
-                          f", {dt:.1f} s")}
+               "sample": sample_text(n, pair.nvox, dt)}
+        v1, n1, dt1, _, _ = time_oracle(pair, 8.0, threads=1)
+        cpu["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                "sample": sample_text(n1, pair.nvox, dt1)}
+        # the timed oracle's gamma values against the GPU maps (parity)
+        parity = parity_report(want, gmap, gmap_fp32, stats)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -503,6 +591,7 @@ def run_ours(args, pair, rank, world, local_rank):
                    "gamma3": gamma3},
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "parity": parity,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": KERNELS_PER_RUN * args.steps,

@@ -218,7 +218,7 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell
  *                     kernel's register budget is sized for (default 2)
  *  "tail_blocks_per_sm"   1 to 3: the same for the table-walk kernel
- *                     (default 2)
+ *                     (default 2; lanes_per_voxel defaults to 8)
  *  "design"           ablation of the paper's GPU design (Algorithm A2;
  *                     single-pair handles): 0 this library's two-phase search
  *                     (default); 1 one thread per voxel in the order of a
@@ -399,10 +399,14 @@ const char *gamma_version(void);
  * calls whose GPU work overlaps (different streams, several host threads)
  * race on it and give wrong results, so serialise them.  The first call on
  * each device looks up the array's device address with that device current;
- * make it before any stream capture begins.  Voxels whose search runs past the
- * GAMMA_NOALLOC_MAX_TABLE-entry table finish with the exact box scan.
- * Errors: INVALID_ARG, SHAPE, TOO_LARGE, TABLE_TOO_LARGE, NAN_INPUT (only when
- * counts are requested), CUDA. */
+ * make it before any stream capture begins.  The cell table is built on the
+ * host during the call and reaches the device inside the parameters of the
+ * call's own launches, so nothing the call enqueues reads host memory after
+ * it returns.  Voxels whose search runs past the GAMMA_NOALLOC_MAX_TABLE-entry
+ * table finish with the exact box scan.  The launch shapes are the defaults
+ * of a new handle.
+ * Errors: INVALID_ARG, SHAPE, TOO_LARGE, NAN_INPUT (only when counts are
+ * requested), CUDA. */
 #define GAMMA_NOALLOC_MAX_VOXELS 4194304
 #define GAMMA_NOALLOC_MAX_TABLE 32768
 int gamma_run_noalloc(const float *ref_dev, const float *eval_dev, float *gamma_out_dev, int ndim,

@@ -102,13 +102,13 @@ struct gamma_ctx {
     unsigned* tail_sorted = nullptr;
     unsigned tail_cap = 0;
     // options
-    int lanes = 8;
+    int lanes = gk::kDefaultLanesPerVoxel;
     double tau = 1e-6;
     int stats = 0;
     int sort_tail = 1;
     int timing = 0;
-    int shell_minblocks = 2;
-    int tail_minblocks = 2;
+    int shell_minblocks = gk::kDefaultShellBlocksPerSm;
+    int tail_minblocks = gk::kDefaultTailBlocksPerSm;
     int pipeline = 8;        // gamma_run_host: z slabs of the overlapped path (0: run in order)
     int design = 0;          // 0: two-phase search; 1 / 2: the paper's A2 with / without DD sort
     int face_eval = 0;       // design 1 / 2: 0 closed-form faces, 1 Ju's recursion

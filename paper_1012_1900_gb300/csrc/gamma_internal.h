@@ -15,6 +15,13 @@ namespace gk {
 constexpr int kNumBuckets = 32;
 constexpr int kShellSlots = 8;       // shell launches of one run with their own tile counter
 
+// Launch shapes a new handle starts with (options "lanes_per_voxel",
+// "shell_blocks_per_sm", "tail_blocks_per_sm"); gamma_run_noalloc, which has
+// no options, always uses them.
+constexpr int kDefaultLanesPerVoxel = 8;
+constexpr int kDefaultShellBlocksPerSm = 2;
+constexpr int kDefaultTailBlocksPerSm = 2;
+
 // Flags raised by kernels (Counters::flags).
 enum : uint32_t {
     kFlagNonFinite = 1u,     // a NaN or Inf dose was seen

@@ -23,7 +23,12 @@
 //    (cudaGetSymbolAddress) with that device current; make that first call
 //    before any stream capture starts.
 // The table is built on the host in static storage (no heap), guarded by a
-// mutex, and copied to the device array on the caller's stream.
+// mutex.  It reaches the device array as the by-value parameters of small
+// copy kernels (at most kChunk entries per launch): a launch takes its own
+// copy of its parameters when it is issued, so no device work reads the host
+// table after the call has returned, and a later call that rebuilds it for
+// another geometry cannot change what an earlier call's work writes.  The
+// launch shapes are the defaults a new handle starts with.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -137,6 +142,24 @@ int build_static_table(int nd, const int64_t n[3], const double hn[3], double* c
     return cnt;
 }
 
+// Table entries carried to the device by value: kChunk entries keep the
+// parameter block under the 32,764-byte kernel parameter limit.
+constexpr int kChunk = 4000;
+struct TableChunk {
+    int first;                 // index of e[0] in the table
+    int count;                 // entries used
+    gk::TableEntry e[kChunk];
+};
+static_assert(sizeof(TableChunk) + sizeof(void*) <= 32764,
+              "table chunk exceeds the kernel parameter limit");
+
+__global__ void __launch_bounds__(256) k_table_fill(gk::TableEntry* __restrict__ dst,
+                                                    const __grid_constant__ TableChunk c)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.count; i += gridDim.x * blockDim.x)
+        dst[c.first + i] = c.e[i];
+}
+
 }  // namespace
 
 extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, float* gamma_out_dev,
@@ -219,18 +242,26 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
     P.tail_bucket = base + kOffBucket;
     P.tail_sorted = nullptr;
     P.sort_tail = 0;
-    P.shell_minblocks = 4;               // the launch shapes the autotuner picks on the benchmark workload
+    P.shell_minblocks = gk::kDefaultShellBlocksPerSm;
 
-    if (ntable > 0 &&
-        cudaMemcpyAsync(base + kOffTable, g_table_host, sizeof(gk::TableEntry) * ntable,
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return GAMMA_ERR_CUDA;
+    // the table, kChunk entries per launch, each chunk copied into its
+    // launch's parameters (static storage: the struct is 32 KB)
+    static TableChunk chunk;
+    for (int first = 0; first < ntable; first += kChunk) {
+        chunk.first = first;
+        chunk.count = std::min(kChunk, ntable - first);
+        std::copy(g_table_host + first, g_table_host + first + chunk.count, chunk.e);
+        k_table_fill<<<(chunk.count + 255) / 256, 256, 0, s>>>(
+            (gk::TableEntry*)(base + kOffTable), chunk);
+        if (cudaGetLastError() != cudaSuccess) return GAMMA_ERR_CUDA;
+    }
     // the counters must start at zero; the rest is written before it is read
     if (cudaMemsetAsync(base + kOffCounters, 0, sizeof(gk::Counters), s) != cudaSuccess)
         return GAMMA_ERR_CUDA;
     if (gk::launch_prepare(P, s, 1) != cudaSuccess) return GAMMA_ERR_CUDA;
     if (gk::launch_shell(P, s) != cudaSuccess) return GAMMA_ERR_CUDA;
-    if (gk::launch_tail(P, 4, 3, s) != cudaSuccess) return GAMMA_ERR_CUDA;
+    if (gk::launch_tail(P, gk::kDefaultLanesPerVoxel, gk::kDefaultTailBlocksPerSm, s) != cudaSuccess)
+        return GAMMA_ERR_CUDA;
 
     if (n_eval || n_pass) {
         gk::Counters c;

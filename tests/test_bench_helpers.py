@@ -12,9 +12,11 @@ import bench
 
 
 def _brute_census(gamma, spacing, dta):
-    """For every evaluated voxel v and every cell whose lower corner v + c lies
-    inside the grid: count it when its box distance / dta is below gamma(v),
-    split into the cells whose box contains v (distance 0) and the others."""
+    """For every evaluated voxel v and every grid cube (lower corner v + c at
+    0 .. n - 2 on each axis, so the whole cube lies inside the grid): count it
+    when its box distance / dta is below gamma(v), split into the cubes whose
+    box contains v (distance 0) and the others; each evaluated voxel adds one
+    to the first count (its final stop test)."""
     nd = gamma.ndim
     shape = gamma.shape                                  # (z, y, x) or (y, x)
     hn = np.array(spacing[::-1], dtype=np.float64) / dta  # x, y[, z]
@@ -25,9 +27,10 @@ def _brute_census(gamma, spacing, dta):
         if not np.isfinite(g):
             continue
         v = idx[::-1]                                    # x, y[, z]
+        shell += 1
         lim = [int(math.ceil(g / h)) + 1 for h in hn]
         for c in itertools.product(*[range(-l - 1, l + 1) for l in lim]):
-            if any(not (0 <= v[a] + c[a] <= dims[a] - 1) for a in range(nd)):
+            if any(not (0 <= v[a] + c[a] <= dims[a] - 2) for a in range(nd)):
                 continue
             gap = [max(c[a], -c[a] - 1, 0) * hn[a] for a in range(nd)]
             key = math.sqrt(sum(x * x for x in gap))

@@ -13,41 +13,44 @@ import oracle
 import synth
 from oracle import mlp
 from tests import _brute as brute
+from tests import _nnbound as nb
 from tests.test_gpu_parity import assert_parity, f32, gpu_gamma, oracle_gamma
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+def _bf16_rows(rng, M):
+    X = np.zeros((M, mlp.K_PAD), np.float32)
+    X[:, :mlp.K_IN] = rng.normal(0, 1.5, (M, mlp.K_IN))
+    Xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    return Xb, Xb.float().cpu().numpy().astype(np.float64)
 
 
 def test_forward_and_backward_match_reference():
+    # Element by element: every output and every gradient entry within the
+    # bound propagated from the bf16 rounding points and FP32 sums
+    # (tests/_nnbound.py), and every row and column of each gradient block
+    # within 2 % of its own norm.
     import paper_1012_1900_gb300 as g
     rng = np.random.default_rng(3)
     m = g.gamma_model_create(7)
     try:
         M = 300                                     # ragged against the 64-row tiles
-        X = np.zeros((M, mlp.K_PAD), np.float32)
-        X[:, :mlp.K_IN] = rng.normal(0, 1.5, (M, mlp.K_IN))
-        Xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
-        Xq = Xb.float().cpu().numpy().astype(np.float64)
+        Xb, Xq = _bf16_rows(rng, M)
         T = rng.normal(0, 1, (M, 4)).astype(np.float32)
         T[::17, 3] = np.nan
         Tt = torch.from_numpy(T).cuda()
         p = g.gamma_model_get_params(m).astype(np.float64)
         Y = torch.empty((M, 4), device="cuda")
         g.gamma_model_forward(m, Xb, Y)
-        ref = mlp.forward(p, Xq)
-        assert _rel(Y.cpu().numpy(), ref["y"]) < 2e-3
+        f, e = nb.forward_bounds(p, Xq)
+        nb.check(Y.cpu().numpy(), f["y"], e["y"], "forward")
         loss = g.gamma_model_backward(m, Xb, Tt)
-        want_loss, want_g = mlp.loss_and_grads(p, Xq, T)
-        assert loss == pytest.approx(want_loss, rel=2e-3)
+        want_loss, want_g, e_loss, e_g = nb.backward_bounds(p, Xq, T)
+        assert abs(loss - want_loss) <= e_loss + 1e-7
         got_g = g.gamma_model_get_params(m, which=1).astype(np.float64)
-        for a, b in [(mlp.OFF_W1, mlp.OFF_B1), (mlp.OFF_B1, mlp.OFF_W2), (mlp.OFF_W2, mlp.OFF_B2),
-                     (mlp.OFF_B2, mlp.OFF_W3), (mlp.OFF_W3, mlp.OFF_B3), (mlp.OFF_B3, mlp.N_PARAMS)]:
-            assert _rel(got_g[a:b], want_g[a:b]) < 1e-2, (a, b)
+        nb.check_grads(got_g, want_g, e_g)
         assert np.all(got_g[~mlp.trainable_mask()] == 0)
     finally:
         g.gamma_model_destroy(m)
@@ -56,27 +59,24 @@ def test_forward_and_backward_match_reference():
 @pytest.mark.parametrize("M", [1, 300, 40000])
 def test_tensor_core_inference_matches_reference(M):
     # The search's inference kernel (tcgen05 MMAs, TMEM accumulators) against
-    # the FP64 network with the same BF16 rounding points.  300 rows leave a
-    # ragged last tile; 40,000 rows give every block several tiles, so the
-    # barrier phases carry over between tiles.
+    # the FP64 network with the same BF16 rounding points, element by element.
+    # 300 rows leave a ragged last tile; 40,000 rows give every block several
+    # tiles, so the barrier phases carry over between tiles.
     import paper_1012_1900_gb300 as g
     rng = np.random.default_rng(5 + M)
     m = g.gamma_model_create(21)
     try:
-        X = np.zeros((M, mlp.K_PAD), np.float32)
-        X[:, :mlp.K_IN] = rng.normal(0, 1.5, (M, mlp.K_IN))
-        Xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
-        Xq = Xb.float().cpu().numpy().astype(np.float64)
+        Xb, Xq = _bf16_rows(rng, M)
         p = g.gamma_model_get_params(m).astype(np.float64)
         Y = torch.full((M, 4), float("nan"), device="cuda")
         g.gamma_model_infer(m, Xb, Y)
         got = Y.cpu().numpy().astype(np.float64)
-        ref = mlp.forward(p, Xq)["y"]
+        f, e = nb.forward_bounds(p, Xq)
         assert np.all(np.isfinite(got))
-        assert _rel(got, ref) < 2e-3
+        nb.check(got, f["y"], e["y"], "tensor-core inference")
         Y2 = torch.empty((M, 4), device="cuda")
         g.gamma_model_forward(m, Xb, Y2)                 # the training kernels agree
-        assert _rel(got, Y2.cpu().numpy().astype(np.float64)) < 2e-3
+        nb.check(Y2.cpu().numpy(), f["y"], e["y"], "training forward")
     finally:
         g.gamma_model_destroy(m)
 
@@ -144,6 +144,39 @@ def test_features_match_definition(volumes):
     want = mlp.bf16_round(mlp.features(p.ref.astype(np.float64), p.eval.astype(np.float64), p.spacing,
                                        f32(c.dd_frac), f32(c.dta_mm), vox))
     assert np.all(np.abs(got - want) <= 2 ** -7 * np.abs(want) + 1e-6)
+
+
+def test_features_at_grid_edges_and_saturation():
+    # The corners, edges and faces of the grid (patches that leave it, one-
+    # sided gradients) and a steep pair whose features saturate (dose channel
+    # at +-16, gradient channels at 32), element by element against the FP64
+    # definition with the same bf16 rounding.
+    import paper_1012_1900_gb300 as g
+    base = synth.workload("imrt_small")
+    steep = synth.Pair("steep", base.ref, (1.25 * base.ref).astype(np.float32), base.spacing,
+                       synth.Criteria(0.003, 3.0, cutoff_frac=0.0))
+    for p in (synth.Pair(base.name, base.ref, base.eval, base.spacing,
+                         synth.Criteria(0.03, 3.0, cutoff_frac=0.0)), steep):
+        nz, ny, nx = p.ref.shape
+        pts = [(z, y, x) for z in (0, 1, nz - 1) for y in (0, ny - 2, ny - 1) for x in (0, 1, nx - 1)]
+        pts += [(nz // 2, ny // 2, x) for x in range(nx)]
+        vox = np.array([np.ravel_multi_index(q, p.ref.shape) for q in pts], dtype=np.int32)
+        h, r, e = _handle(g, p)
+        try:
+            out = torch.empty_like(r)
+            g.gamma_run(h, out)                       # the dose norm the features use
+            g.gamma_pass_rate(h)
+            X = torch.empty((vox.size, 384), dtype=torch.bfloat16, device="cuda")
+            g.gamma_features(h, torch.from_numpy(vox).cuda(), X)
+            got = X.float().cpu().numpy().astype(np.float64)
+        finally:
+            g.gamma_destroy(h)
+        c = p.criteria
+        want = mlp.bf16_round(mlp.features(p.ref.astype(np.float64), p.eval.astype(np.float64),
+                                           p.spacing, f32(c.dd_frac), f32(c.dta_mm), vox))
+        assert np.all(np.abs(got - want) <= 2 ** -7 * np.abs(want) + 1e-6), p.name
+        if p.name == "steep":
+            assert (np.abs(want[:, :125]) == 16.0).any() and (want[:, 125:375] == 32.0).any()
 
 
 def test_labels_are_nearest_surface_points():
