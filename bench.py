@@ -34,7 +34,9 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-METRIC = "3D gamma voxels/s at 3%/3mm"
+# BASELINE's headline metric; `value` is the plain search on the clinical-size
+# pair, and the line's vs_plain object holds the learned + batched comparison
+METRIC = "3D gamma voxels/s at 3%/3mm: learned+batched vs plain, same GB300, |\u0394\u03b3|\u22641e-4"
 UNIT = "voxels/s"
 WORKLOAD = "imrt_160"
 _BEAMS = "7 coplanar beams, 10x10 beamlets, 3 mm penumbra"
@@ -61,6 +63,9 @@ KERNELS_PER_RUN = 4          # prepare, shell, scatter, tail
 LOAD_S = 1.5                 # back-to-back maps before the timed steps (clock samples)
 # gamma within this distance of 1 may pass on one side and fail on the other
 TIE_BAND = 1e-4
+# proposal network trained by the committed training command
+MODEL_PATH = os.path.join(ROOT, "paper_1012_1900_gb300", "proposal_2pct2mm.gmlp")
+VS_PLAIN_TEST_PAIRS = 4      # held-out 200x200x150 pairs timed plain against learned
 
 
 def parse():
@@ -76,6 +81,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
+    ap.add_argument("--no-vs-plain", action="store_true",
+                    help="skip the learned + batched against plain comparison")
     ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation", "mlp_infer",
                                              "grids"],
                     default=None,
@@ -374,6 +381,141 @@ def load_peaks():
         return {}
 
 
+def _event_ms(torch, stream, fn, reps, flush=None):
+    """Median device time of fn() over reps calls (CUDA events on stream)."""
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+    return statistics.median(ts)
+
+
+def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
+    """The learned + batched form against the plain search on one GPU, each map
+    kept equal to the plain one: the 64 uneven batch pairs run one by one
+    (plain), as one batched graph, and batched with the trained proposal
+    network seeding every pair; and held-out 200x200x150 pairs at 2 %/2 mm run
+    plain against a single-pair handle with the network attached."""
+    if not os.path.exists(MODEL_PATH):
+        return {"unavailable": f"no trained proposal network at {os.path.relpath(MODEL_PATH, ROOT)}"}
+    t0 = time.perf_counter()
+    pool = _pool(min(16, os.cpu_count() or 1))
+    pairs = [p for chunk in _chunks(pool, [("batch", i, None) for i in range(64)]) for p in chunk]
+    tests = pool.map(_gen, [("test", i, (150, 200, 200)) for i in range(VS_PLAIN_TEST_PAIRS)])
+    pool.close()
+    gen_s = time.perf_counter() - t0
+    res = {"model": os.path.relpath(MODEL_PATH, ROOT), "generation_s": gen_s}
+    with torch.cuda.stream(stream):
+        descs, keep = [], []
+        for p in pairs:
+            nd = p.ref.ndim
+            r = torch.from_numpy(p.ref).to(dev)
+            e = torch.from_numpy(p.eval).to(dev)
+            o = torch.empty_like(r)
+            keep += [r, e, o]
+            c = p.criteria
+            descs.append((r, e, o, nd, p.ref.shape if nd == 3 else (1,) + p.ref.shape,
+                          p.spacing if nd == 3 else (1.0,) + p.spacing,
+                          g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)))
+        vox = sum(p.nvox for p in pairs)
+        reps = max(5, min(args.steps, 10))
+        hs = [g.gamma_create(d[0], d[1], d[3], d[4], d[5], d[6]) for d in descs]
+        for h in hs:
+            for k, v in launch.items():
+                g.gamma_set_option(h, k, v)
+
+        def run_plain():
+            for h, d in zip(hs, descs):
+                g.gamma_run(h, d[2], stream)
+        for _ in range(3):
+            run_plain()
+        plain_ms = _event_ms(torch, stream, run_plain, reps)
+        plain_maps = [d[2].cpu().numpy() for d in descs]
+        for h in hs:
+            g.gamma_destroy(h)
+        hb = g.gamma_batch_create([d for d in descs])
+        try:
+            for k, v in launch.items():
+                g.gamma_set_option(hb, k, v)
+            for _ in range(3):
+                g.gamma_batch_run(hb, stream)
+            batched_ms = _event_ms(torch, stream, lambda: g.gamma_batch_run(hb, stream), reps)
+            diff_b = max(float(np.nanmax(np.abs(d[2].cpu().numpy() - m))) if np.isfinite(m).any() else 0.0
+                         for d, m in zip(descs, plain_maps))
+            g.gamma_load_model(hb, MODEL_PATH)
+            for _ in range(3):
+                g.gamma_batch_run(hb, stream)
+            learned_ms = _event_ms(torch, stream, lambda: g.gamma_batch_run(hb, stream), reps)
+            g.gamma_batch_pass_rate(hb, 0)
+            seeded = sum(g.gamma_batch_get_stats(hb, i)["seeded"] for i in range(len(pairs)))
+            queued = sum(g.gamma_batch_get_stats(hb, i)["tail_voxels"] for i in range(len(pairs)))
+            diff_l = max(float(np.nanmax(np.abs(d[2].cpu().numpy() - m))) if np.isfinite(m).any() else 0.0
+                         for d, m in zip(descs, plain_maps))
+        finally:
+            g.gamma_destroy(hb)
+        del keep, descs, plain_maps
+        res["batch_64_pairs"] = {
+            "workload": "32 planes 256x256 at 1 mm + 32 volumes 64^3..200x200x150 at 2 mm, "
+                        "criteria from {1/1, 2/2, 3/3}, seeds 3000+i",
+            "voxels": vox, "reps": reps,
+            "plain_one_by_one": {"ms": plain_ms, "voxels_per_s": vox / (plain_ms / 1e3)},
+            "batched": {"ms": batched_ms, "voxels_per_s": vox / (batched_ms / 1e3),
+                        "max_abs_diff_vs_plain": diff_b},
+            "learned_batched": {"ms": learned_ms, "voxels_per_s": vox / (learned_ms / 1e3),
+                                "max_abs_diff_vs_plain": diff_l, "seeded": seeded,
+                                "queued": queued},
+            "speedup_batched_vs_plain": plain_ms / batched_ms,
+            "speedup_learned_batched_vs_plain": plain_ms / learned_ms,
+            "speedup_learned_batched_vs_batched": batched_ms / learned_ms}
+        # held-out single pairs: plain against the network attached
+        rows = []
+        for p in tests:
+            c = p.criteria
+            crit = g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)
+            r = torch.from_numpy(p.ref).to(dev)
+            e = torch.from_numpy(p.eval).to(dev)
+            o = torch.empty_like(r)
+            row = {"pair": p.name}
+            for mode in ("plain", "learned"):
+                h = g.gamma_create(r, e, 3, p.ref.shape, p.spacing, crit)
+                try:
+                    for k, v in launch.items():
+                        g.gamma_set_option(h, k, v)
+                    if mode == "learned":
+                        g.gamma_load_model(h, MODEL_PATH)
+                    for _ in range(3):
+                        g.gamma_run(h, o, stream)
+                    row[f"{mode}_ms"] = _event_ms(torch, stream, lambda: g.gamma_run(h, o, stream),
+                                                  reps, flush)
+                    g.gamma_pass_rate(h)
+                    st = g.gamma_get_stats(h)
+                    row[f"{mode}_map"] = o.cpu().numpy()
+                    if mode == "learned":
+                        row["seeded"] = st["seeded"]
+                        row["seed_improved"] = st["seed_improved"]
+                        row["queued"] = st["tail_voxels"]
+                finally:
+                    g.gamma_destroy(h)
+            a, b = row.pop("plain_map"), row.pop("learned_map")
+            row["max_abs_diff_vs_plain"] = float(np.nanmax(np.abs(a - b)))
+            rows.append(row)
+        tp = sum(r["plain_ms"] for r in rows)
+        tl = sum(r["learned_ms"] for r in rows)
+        nv = sum(p.nvox for p in tests)
+        res["held_out_200x200x150_2pct2mm"] = {
+            "pairs": rows, "plain_voxels_per_s": nv / (tp / 1e3),
+            "learned_voxels_per_s": nv / (tl / 1e3), "speedup_learned_vs_plain": tp / tl}
+    res["seconds"] = time.perf_counter() - t0
+    return res
+
+
 def run_ours(args, pair, rank, world, local_rank):
     import torch
     import paper_1012_1900_gb300 as g
@@ -571,6 +713,10 @@ def run_ours(args, pair, rank, world, local_rank):
         # the timed oracle's gamma values against the GPU maps (parity)
         parity = parity_report(want, gmap, gmap_fp32, stats)
 
+    vs_plain = None
+    if world == 1 and not args.no_vs_plain:
+        vs_plain = measure_vs_plain(args, g, torch, dev, stream, launch, flush)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -592,6 +738,7 @@ def run_ours(args, pair, rank, world, local_rank):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "parity": parity,
+        "vs_plain": vs_plain,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": KERNELS_PER_RUN * args.steps,

@@ -356,7 +356,9 @@ struct BatchState {
         unsigned* item_start = nullptr;
         unsigned* items_v = nullptr;
         unsigned short* items_p = nullptr;
-        unsigned* head = nullptr;
+        unsigned* head = nullptr;          // walk, shell tiles, seed rows, seeding work
+        unsigned* seed_item = nullptr;     // with a model: (pair, item) rows past the gate
+        unsigned short* seed_pair = nullptr;
         gk::BatchDesc* desc = nullptr;
         gk::BatchGroup host{};
     } grp[2];
@@ -378,6 +380,8 @@ void free_group(BatchState::Group& g)
     cudaFree(g.items_v);
     cudaFree(g.items_p);
     cudaFree(g.head);
+    cudaFree(g.seed_item);
+    cudaFree(g.seed_pair);
     cudaFree(g.desc);
     g = BatchState::Group{};
 }
@@ -440,8 +444,14 @@ int batch_upload(gamma_ctx* h)
             for (int k = 0; k < np; ++k) cap += b->pairs[mem[k]]->tail_cap;
             CK(cudaMalloc(&G.items_v, sizeof(unsigned) * std::max<size_t>(cap, 1)));
             CK(cudaMalloc(&G.items_p, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
-            CK(cudaMalloc(&G.head, 2 * sizeof(unsigned)));   // walk, shell tiles
+            CK(cudaMalloc(&G.head, 4 * sizeof(unsigned)));   // walk, shell tiles, seeding
             CK(cudaMalloc(&G.desc, sizeof(gk::BatchDesc)));
+        }
+        if (h->model && !G.seed_item) {
+            size_t cap = 0;
+            for (int k = 0; k < np; ++k) cap += b->pairs[mem[k]]->tail_cap;
+            CK(cudaMalloc(&G.seed_item, sizeof(unsigned) * std::max<size_t>(cap, 1)));
+            CK(cudaMalloc(&G.seed_pair, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
         }
         CK(cudaMemcpy(G.probs, probs.data(), sizeof(gk::Problem) * np, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(G.maps, maps.data(), sizeof(CUtensorMap) * np, cudaMemcpyHostToDevice));
@@ -458,6 +468,12 @@ int batch_upload(gamma_ctx* h)
         d.items_p = G.items_p;
         d.head = G.head;
         d.shell_next = G.head + 1;
+        if (h->model) {
+            d.seed_item = G.seed_item;
+            d.seed_pair = G.seed_pair;
+            d.seed_count = G.head + 2;
+            d.seed_head = G.head + 3;
+        }
         CK(cudaMemcpy(G.desc, &d, sizeof(d), cudaMemcpyHostToDevice));
         G.host.ndim = gi == 0 ? 2 : 3;
         G.host.npairs = np;
@@ -482,6 +498,15 @@ int batch_enqueue(gamma_ctx* h, cudaStream_t s)
     for (auto& G : b->grp) CK(gk::launch_batch_prepare(G.host, s));
     if (tm) CK(cudaEventRecord(h->tev[2], s));
     for (auto& G : b->grp) CK(gk::launch_batch_shell(G.host, h->shell_minblocks, s));
+    if (h->model) {
+        // learned seeding of every pair's queued voxels past the cost gate
+        gk::MlpWeights W;
+        gk::model_weights(h->model, &W);
+        for (auto& G : b->grp) {
+            CK(gk::launch_batch_seed_select(G.host, h->seed_min_bucket, s));
+            CK(gk::launch_batch_learned(G.host, W, s));
+        }
+    }
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     for (auto& G : b->grp) CK(gk::launch_batch_order(G.host, s));
     if (tm) CK(cudaEventRecord(h->tev[4], s));
@@ -1313,6 +1338,8 @@ int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats* out)
     out->tail_voxels = (int64_t)k.tail_count;
     out->overflow_voxels = (int64_t)k.overflow_count;
     out->fp64_cells = (int64_t)k.fp64_cells;
+    out->seeded = (int64_t)k.seeded;
+    out->seed_improved = (int64_t)k.seed_improved;
     out->d_norm = c->crit.dose_norm > 0 ? (double)c->crit.dose_norm : (double)gk::fdec(k.dnorm_enc);
     out->r_max = (double)gk::fdec(k.rmax_enc);
     out->table_entries = (int64_t)c->table.size();
@@ -1412,11 +1439,26 @@ static int seed_buffers(gamma_handle h)
     return GAMMA_OK;
 }
 
+// A model attached to (or detached from) a batch handle changes its launch
+// sequence: the descriptors are uploaded again (with the seeding rows) and the
+// graph is captured again at the next run.
+static int batch_model_changed(gamma_handle h)
+{
+    BatchState* b = h->batch;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return GAMMA_ERR_CUDA;
+    if (h->ran) CK(cudaStreamSynchronize(h->last_stream));
+    b->dirty = true;
+    return GAMMA_OK;
+}
+
 int gamma_set_model(gamma_handle h, gamma_model m)
 {
-    if (!h || h->batch || h->grids) return GAMMA_ERR_INVALID_ARG;
-    if (m)
+    if (!h || h->grids) return GAMMA_ERR_INVALID_ARG;
+    if (m && !h->batch)
         if (int rc = seed_buffers(h)) return rc;
+    if (h->batch)
+        if (int rc = batch_model_changed(h)) return rc;
     if (h->own_model) gamma_model_destroy(h->model);
     h->sg_dirty = true;
     h->model = m;
@@ -1426,11 +1468,15 @@ int gamma_set_model(gamma_handle h, gamma_model m)
 
 int gamma_load_model(gamma_handle h, const char* path)
 {
-    if (!h || h->batch || !path) return GAMMA_ERR_INVALID_ARG;
+    if (!h || !path) return GAMMA_ERR_INVALID_ARG;
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
     if (h->grids) return GAMMA_ERR_INVALID_ARG;
-    if (int rc = seed_buffers(h)) return rc;
+    if (h->batch) {
+        if (int rc = batch_model_changed(h)) return rc;
+    } else if (int rc = seed_buffers(h)) {
+        return rc;
+    }
     gamma_model m = nullptr;
     if (int rc = gamma_model_create(&m, 0)) return rc;
     if (int rc = gamma_model_load(m, path)) {

@@ -154,6 +154,13 @@ struct BatchDesc {
     unsigned short* items_p;       // [sum of tail_cap] their pair
     unsigned* head;                // work counter of the group's table walk
     unsigned* shell_next;          // tile counter of the group's shell (zeroed by its prepare)
+    // learned seeding (null without a model): queue items of every pair past
+    // the cost gate, as (pair, item) rows, their count and the work counter of
+    // the seeding pass (both zeroed by the group's prepare)
+    unsigned* seed_item;           // [sum of tail_cap]
+    unsigned short* seed_pair;     // [sum of tail_cap]
+    unsigned* seed_count;
+    unsigned* seed_head;
 };
 
 // Host view of one batched launch group.
@@ -255,5 +262,10 @@ cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStr
 cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s);
 cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, int tail_minblocks,
                               cudaStream_t s);
+// Learned seeding of a batch group (gamma_learned.cu): the queue items of every
+// pair whose cost bucket is at least min_bucket, then the fused features,
+// network and exact seeds over all of them in one persistent launch.
+cudaError_t launch_batch_seed_select(const BatchGroup& g, int min_bucket, cudaStream_t s);
+cudaError_t launch_batch_learned(const BatchGroup& g, const MlpWeights& W, cudaStream_t s);
 
 }  // namespace gk

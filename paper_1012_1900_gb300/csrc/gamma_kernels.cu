@@ -42,7 +42,13 @@ __global__ void __launch_bounds__(256)
 {
     const Problem& P = BATCH ? bd->probs[blockIdx.y] : P0;
     if constexpr (BATCH) {
-        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *bd->shell_next = 0u;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+            *bd->shell_next = 0u;
+            if (bd->seed_count) {
+                *bd->seed_count = 0u;
+                *bd->seed_head = 0u;
+            }
+        }
     }
     float m = -kInf;
     bool bad = false;

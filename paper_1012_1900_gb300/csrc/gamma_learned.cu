@@ -518,6 +518,7 @@ struct __align__(1024) TcSmem {
     float Y[kRows * kOut];
     unsigned vox[kRows], item[kRows];
     float dr[kRows], inv[kRows];
+    unsigned short pair[kRows];
     unsigned hist[kNumBuckets];
     unsigned base, nseed, nimp;
     uint32_t tmem;
@@ -743,14 +744,33 @@ cudaError_t launch_mlp_infer(const MlpWeights& W, const bf16* X, long long M, fl
 // Fused inference + seeding over the queued voxels
 // --------------------------------------------------------------------------
 
-template <int N>
-__global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Problem P,
+// Cost bucket of a queued voxel whose running squared gamma is g2: 1 + floor(2
+// log2 of the table cells with key < gamma) (0 when there are none), the
+// bucket k_shell gives.
+__device__ __forceinline__ int cost_bucket(const Problem& P, float g2)
+{
+    const float gk_ = sqrtf(g2);
+    int lo = 0, hi = P.ntable;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
+    }
+    return lo <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)lo)));
+}
+
+// One launch seeds the queued voxels past the cost gate: of one pair
+// (BATCH = false: P0.seed_list) or of every pair of a batch group (BATCH =
+// true: the (pair, item) rows of bd), 128 rows per tile.
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Problem P0,
+                                                    const BatchDesc* __restrict__ bd,
                                                     const __grid_constant__ MlpWeights W)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
-    const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
-    const unsigned total = min(P.ctr->seed_count, P.tail_cap);
+    const unsigned total = BATCH ? *bd->seed_count : min(P0.ctr->seed_count, P0.tail_cap);
+    unsigned* head = BATCH ? bd->seed_head : &P0.ctr->seed_head;
+    auto prob = [&](int r) -> const Problem& { return BATCH ? bd->probs[S.pair[r]] : P0; };
     if (threadIdx.x < kNumBuckets) S.hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) { S.nseed = 0; S.nimp = 0; }
     tc_setup(S, W);
@@ -758,22 +778,32 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
     bool ok = true;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) S.base = atomicAdd(&P.ctr->seed_head, (unsigned)kRows);
+        if (threadIdx.x == 0) S.base = atomicAdd(head, (unsigned)kRows);
         __syncthreads();
         const unsigned base = S.base;
         if (base >= total || !ok) break;
-        // ---- rows: voxel, dose, scale ----
+        // ---- rows: pair, queue item, voxel, dose, scale ----
         if (threadIdx.x < kRows) {
             const unsigned it = base + threadIdx.x;
-            unsigned v = 0xffffffffu;
+            unsigned v = 0xffffffffu, item = 0u;
+            unsigned short pr = 0;
             float dr = 0.f, inv = 0.f;
             if (it < total) {
-                v = P.tail_raw[P.seed_list[it]];
+                if constexpr (BATCH) {
+                    pr = bd->seed_pair[it];
+                    item = bd->seed_item[it];
+                } else {
+                    item = P0.seed_list[it];
+                }
+                const Problem& P = BATCH ? bd->probs[pr] : P0;
+                v = P.tail_raw[item];
                 dr = __ldg(P.ref + v);
+                const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
                 inv = 1.0f / (P.dd_frac * (P.local ? dr : dnorm));
             }
+            S.pair[threadIdx.x] = pr;
             S.vox[threadIdx.x] = v;
-            S.item[threadIdx.x] = it < total ? P.seed_list[it] : 0u;
+            S.item[threadIdx.x] = item;
             S.dr[threadIdx.x] = dr;
             S.inv[threadIdx.x] = inv;
         }
@@ -785,7 +815,7 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
             for (int e = threadIdx.x; e < kRows * (kKc / 8); e += blockDim.x) {
                 const int r = e / (kKc / 8), j = e % (kKc / 8);
                 float val[8];
-                features8<N>(P, S.vox[r], S.dr[r], S.inv[r], c * kKc + j * 8, val);
+                features8<N>(prob(r), S.vox[r], S.dr[r], S.inv[r], c * kKc + j * 8, val);
                 uint4 pk;
                 uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
 #pragma unroll
@@ -801,6 +831,7 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
         {
             const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
             const unsigned v = S.vox[r];
+            const Problem& P = prob(r);
             float sd2 = kInf;
             int x = 0, y = 0, z = 0;
             if (v != 0xffffffffu) {
@@ -820,15 +851,15 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
                     const int cx = o[0] + (u & 1), cy = o[1] + ((u >> 1) & 1),
                               cz = N == 3 ? o[2] + ((u >> 2) & 1) : 0;
                     float q[8];
-                    uint32_t ok;
-                    if (!load_cell<N>(P, x, y, z, cx, cy, cz, S.dr[r], S.inv[r], q, ok)) continue;
+                    uint32_t okc;
+                    if (!load_cell<N>(P, x, y, z, cx, cy, cz, S.dr[r], S.inv[r], q, okc)) continue;
                     CellGeom<float> gg;
                     cell_geom<N, float>(cx, cy, cz, P.mt, gg);
                     bool ill = false;
-                    const float cb = cell_min_d2<N, float>(q, ok, gg, P.mt,
+                    const float cb = cell_min_d2<N, float>(q, okc, gg, P.mt,
                                                            P.tau > 0.f ? 0.99f * rsqrtf(P.tau) : kInf,
                                                            kInf, ill);
-                    if (ill) ill = cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau);
+                    if (ill) ill = cell_gram_ill<N>(q, okc, P.mt.kappa, P.tau);
                     if (!ill) sd2 = fminf(sd2, cb);        // ill-conditioned cells are not used as seeds
                 }
             }
@@ -836,53 +867,105 @@ __global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Prob
             if (half == 0 && v != 0xffffffffu) {
                 const float cur = P.out[v];                   // gamma^2 after the faces through v
                 const float nb = fminf(cur, sd2);
-                atomicAdd(&S.nseed, 1u);
-                if (nb < cur) {
-                    P.out[v] = nb;
-                    atomicAdd(&S.nimp, 1u);
-                }
+                const bool better = nb < cur;
+                if (better) P.out[v] = nb;
                 // bucket from the (possibly) tighter bound
-                const float gk_ = sqrtf(nb);
-                int lo = 0, hi = P.ntable;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
-                }
-                const int cost = lo;
-                const int bucket = cost <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)cost)));
+                const int bucket = cost_bucket(P, nb);
                 const int was = P.tail_bucket[S.item[r]];
-                if (bucket != was) {                    // move the voxel between histogram bins
-                    P.tail_bucket[S.item[r]] = (unsigned char)bucket;
-                    atomicAdd(&S.hist[bucket], 1u);
-                    atomicSub(&S.hist[was], 1u);        // wraps; the sum over the block is exact
+                if constexpr (BATCH) {
+                    atomicAdd(&P.ctr->seeded, 1u);
+                    if (better) atomicAdd(&P.ctr->seed_improved, 1u);
+                    if (bucket != was) {                 // move the voxel between its pair's bins
+                        P.tail_bucket[S.item[r]] = (unsigned char)bucket;
+                        atomicAdd(&P.ctr->hist[bucket], 1u);
+                        atomicSub(&P.ctr->hist[was], 1u);
+                    }
+                } else {
+                    atomicAdd(&S.nseed, 1u);
+                    if (better) atomicAdd(&S.nimp, 1u);
+                    if (bucket != was) {                 // move the voxel between histogram bins
+                        P.tail_bucket[S.item[r]] = (unsigned char)bucket;
+                        atomicAdd(&S.hist[bucket], 1u);
+                        atomicSub(&S.hist[was], 1u);     // wraps; the sum over the block is exact
+                    }
                 }
             }
         }
     }
     __syncthreads();
-    if (threadIdx.x < kNumBuckets && S.hist[threadIdx.x])
-        atomicAdd(&P.ctr->hist[threadIdx.x], S.hist[threadIdx.x]);
-    if (threadIdx.x == 0) {
-        atomicAdd(&P.ctr->seeded, S.nseed);
-        atomicAdd(&P.ctr->seed_improved, S.nimp);
-        if (!ok) atomicOr(&P.ctr->flags, kFlagTimeout);
+    if constexpr (!BATCH) {
+        if (threadIdx.x < kNumBuckets && S.hist[threadIdx.x])
+            atomicAdd(&P0.ctr->hist[threadIdx.x], S.hist[threadIdx.x]);
+        if (threadIdx.x == 0) {
+            atomicAdd(&P0.ctr->seeded, S.nseed);
+            atomicAdd(&P0.ctr->seed_improved, S.nimp);
+        }
+    }
+    if (threadIdx.x == 0 && !ok) {
+        if constexpr (BATCH) {
+            for (int p = 0; p < bd->npairs; ++p) atomicOr(&bd->probs[p].ctr->flags, kFlagTimeout);
+        } else {
+            atomicOr(&P0.ctr->flags, kFlagTimeout);
+        }
     }
     tc_teardown(S);
 }
 
-cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s)
+template <int N, bool BATCH>
+static cudaError_t launch_learned_k(const Problem& P, const BatchDesc* bd, const MlpWeights& W,
+                                    cudaStream_t s)
 {
     const size_t smem = kTcSmemBytes;
-    cudaError_t e;
-    if (P.ndim == 3) {
-        e = cudaFuncSetAttribute(k_learned<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_learned<3><<<device_sm_count(), 256, smem, s>>>(P, W);
-    } else {
-        e = cudaFuncSetAttribute(k_learned<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_learned<2><<<device_sm_count(), 256, smem, s>>>(P, W);
+    cudaError_t e = cudaFuncSetAttribute(k_learned<N, BATCH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_learned<N, BATCH><<<device_sm_count(), 256, smem, s>>>(P, bd, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s)
+{
+    return P.ndim == 3 ? launch_learned_k<3, false>(P, nullptr, W, s)
+                       : launch_learned_k<2, false>(P, nullptr, W, s);
+}
+
+cudaError_t launch_batch_learned(const BatchGroup& g, const MlpWeights& W, cudaStream_t s)
+{
+    if (g.npairs <= 0) return cudaSuccess;
+    Problem dummy{};
+    return g.ndim == 3 ? launch_learned_k<3, true>(dummy, g.desc, W, s)
+                       : launch_learned_k<2, true>(dummy, g.desc, W, s);
+}
+
+// Queue items of every pair of a batch group past the cost gate, as (pair,
+// item) rows (blockIdx.y = pair).
+__global__ void __launch_bounds__(256) k_seed_select_batch(const BatchDesc* __restrict__ bd,
+                                                           int min_bucket)
+{
+    const Problem& P = bd->probs[blockIdx.y];
+    const unsigned total = min(P.ctr->tail_count, P.tail_cap);
+    const int lane = threadIdx.x & 31;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned c0 = blockIdx.x * blockDim.x; c0 < total; c0 += stride) {
+        const unsigned i = c0 + threadIdx.x;
+        const bool take = i < total && (int)P.tail_bucket[i] >= min_bucket;
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        unsigned base = 0;
+        if (lane == 0 && m) base = atomicAdd(bd->seed_count, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) {
+            const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
+            bd->seed_item[pos] = i;
+            bd->seed_pair[pos] = (unsigned short)blockIdx.y;
+        }
     }
+}
+
+cudaError_t launch_batch_seed_select(const BatchGroup& g, int min_bucket, cudaStream_t s)
+{
+    if (g.npairs <= 0) return cudaSuccess;
+    const int bx = std::max(1, device_sm_count() * 2 / std::max(1, g.npairs)) + 1;
+    k_seed_select_batch<<<dim3(bx, g.npairs), 256, 0, s>>>(g.desc, min_bucket);
     return cudaGetLastError();
 }
 

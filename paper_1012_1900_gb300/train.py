@@ -90,3 +90,61 @@ def train(model: int, X, T, steps: int, batch: int = 8192, lr: float = 2e-3, see
         if log_every and s % log_every == 0:
             print(f"step {s}: loss {loss:.4f}", flush=True)
     return losses
+
+
+def _gen_training_pair(args):
+    import synth
+    i, shape = args
+    return synth.training_pair(i, shape=shape)
+
+
+def main(argv=None) -> None:
+    """Train the proposal network on the learned-proposal recipe (synthetic
+    3D pairs at 2 mm, 2 %/2 mm global, shift U[0, 4] mm, scale U[0.95, 1.05],
+    labelled by the exact GPU search) and save it:
+
+        python -m paper_1012_1900_gb300.train --pairs 200 --steps 3000 --out model.gmlp
+    """
+    import argparse
+    import multiprocessing as mp
+    import os
+    import sys
+    import time
+
+    import torch
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--pairs", type=int, default=200)
+    ap.add_argument("--shape", type=int, nargs=3, default=(150, 200, 200), metavar=("NZ", "NY", "NX"))
+    ap.add_argument("--per-pair", type=int, default=4096, help="training rows drawn per pair")
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--seed", type=int, default=1234)
+    ap.add_argument("--out", required=True)
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    t0 = time.perf_counter()
+    m = g.gamma_model_create(a.seed)
+    try:
+        xs, ts = [], []
+        jobs = [(i, tuple(a.shape)) for i in range(a.pairs)]
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            for k in range(0, len(jobs), 16):
+                chunk = pool.map(_gen_training_pair, jobs[k:k + 16])
+                X, T = build_dataset(chunk, a.per_pair, seed=k)
+                xs.append(X)
+                ts.append(T)
+        X, T = torch.cat(xs), torch.cat(ts)
+        losses = train(m, X, T, steps=a.steps, batch=a.batch, lr=a.lr)
+        g.gamma_model_save(m, a.out)
+    finally:
+        g.gamma_model_destroy(m)
+    print(f"trained on {X.shape[0]} rows from {a.pairs} pairs in {time.perf_counter() - t0:.1f} s; "
+          f"loss {np.mean(losses[:10]):.4f} -> {np.mean(losses[-50:]):.4f}; saved {a.out}", flush=True)
+
+
+if __name__ == "__main__":
+    main()

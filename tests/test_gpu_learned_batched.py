@@ -1,0 +1,156 @@
+"""GPU parity of the batched and the learned + batched forms at the scale of
+the uneven batch (64 pairs of 2D planes 256x256 and 3D volumes up to
+148x196x196) and of the learned-proposal workload (held-out 200x200x150 pairs
+at 2 %/2 mm), and what a trained proposal network gains.
+
+- A subset of the 64-pair batch (the largest volume, a 4.5 M-voxel volume at
+  1 %/1 mm, small volumes and 256^2 planes at 1 %/1 mm) runs as one batched
+  handle, then batched with a proposal network attached: every pair's map
+  equals the map of its own single-pair handle, and the oracle agrees on
+  sampled voxels (the largest gammas included).
+- A network trained in the test on small pairs of the learned-proposal
+  recipe seeds a held-out 200x200x150 pair at 2 %/2 mm: seeded, plain and
+  oracle agree, and with the trained network the walk keys and visits fewer
+  cells per queued voxel than without it and than with an untrained one.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests.test_gpu_parity import assert_parity, oracle_gamma
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# batch pairs: 50 = 148x196x196 (3 %/3 mm), 46 = 139x181x181 (1 %/1 mm),
+# 37 = 69x70x70 (1 %/1 mm), 55 = 72x75x75 (1 %/1 mm), planes 2 and 3 (1 %/1 mm)
+# and 0
+C4_SUBSET = (50, 46, 37, 55, 2, 3, 0)
+
+
+def _geom(p):
+    if p.ref.ndim == 2:
+        return 2, (1,) + p.ref.shape, (1.0,) + tuple(p.spacing)
+    return 3, p.ref.shape, tuple(p.spacing)
+
+
+def _crit(g, c):
+    return g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)
+
+
+def _sample(gm, rng, n=2500, top=100):
+    flat = gm.ravel()
+    ok = np.nonzero(np.isfinite(flat))[0]
+    if ok.size == 0:
+        return ok
+    order = ok[np.argsort(-flat[ok])]
+    return np.unique(np.concatenate([order[:top], rng.choice(ok, min(n, ok.size), replace=False)]))
+
+
+def _single(g, p):
+    nd, shape, sp = _geom(p)
+    r = torch.from_numpy(p.ref).cuda()
+    e = torch.from_numpy(p.eval).cuda()
+    o = torch.empty_like(r)
+    h = g.gamma_create(r, e, nd, shape, sp, _crit(g, p.criteria))
+    try:
+        g.gamma_run(h, o)
+        counts = g.gamma_pass_rate(h)
+    finally:
+        g.gamma_destroy(h)
+    return o.cpu().numpy().astype(np.float64), counts
+
+
+def test_batch_subset_and_learned_batch_match_single_pairs_and_oracle():
+    import paper_1012_1900_gb300 as g
+    pairs = [synth.batch_pair(i) for i in C4_SUBSET]
+    descs, outs, keep = [], [], []
+    for p in pairs:
+        nd, shape, sp = _geom(p)
+        r = torch.from_numpy(p.ref).cuda()
+        e = torch.from_numpy(p.eval).cuda()
+        o = torch.full_like(r, -7.0)
+        keep += [r, e]
+        outs.append(o)
+        descs.append((r, e, o, nd, shape, sp, _crit(g, p.criteria)))
+    singles = [_single(g, p) for p in pairs]
+    hb = g.gamma_batch_create(descs)
+    m = g.gamma_model_create(17)
+    rng = np.random.default_rng(4)
+    try:
+        g.gamma_batch_run(hb)
+        batched = [o.cpu().numpy().astype(np.float64) for o in outs]
+        counts_b = [g.gamma_batch_pass_rate(hb, i) for i in range(len(pairs))]
+        g.gamma_set_model(hb, m)
+        g.gamma_set_option(hb, "seed_min_bucket", 0)      # every queued voxel of every pair
+        for o in outs:
+            o.fill_(-7.0)
+        g.gamma_batch_run(hb)
+        g.gamma_batch_run(hb)                             # the captured graph's replay
+        learned = [o.cpu().numpy().astype(np.float64) for o in outs]
+        counts_l = [g.gamma_batch_pass_rate(hb, i) for i in range(len(pairs))]
+        stats_l = [g.gamma_batch_get_stats(hb, i) for i in range(len(pairs))]
+    finally:
+        g.gamma_destroy(hb)
+        g.gamma_model_destroy(m)
+    for p, (single, c1), b, cb, l_, cl, st in zip(pairs, singles, batched, counts_b, learned,
+                                                  counts_l, stats_l):
+        np.testing.assert_allclose(b, single, rtol=0, atol=1e-6, equal_nan=True, err_msg=p.name)
+        np.testing.assert_allclose(l_, single, rtol=0, atol=1e-6, equal_nan=True, err_msg=p.name)
+        assert cb[1:] == c1[1:] and cl[1:] == c1[1:], p.name
+        assert st["seeded"] == st["tail_voxels"], p.name
+        idx = _sample(l_, rng)
+        want = oracle_gamma(p.ref, p.eval, p.spacing, p.criteria, idx=idx)
+        assert_parity(l_.ravel()[idx], want)
+
+
+def _small_training_pairs(n, shape=(40, 56, 56)):
+    return [synth.training_pair(i, shape=shape) for i in range(n)]
+
+
+def test_trained_network_on_a_held_out_pair_stays_exact_and_saves_cells():
+    import paper_1012_1900_gb300 as g
+    from paper_1012_1900_gb300 import train
+    X, T = train.build_dataset(_small_training_pairs(8), 6000, seed=0)
+    trained = g.gamma_model_create(5)
+    untrained = g.gamma_model_create(6)
+    p = synth.test_pair(0)                                # 200x200x150 at 2 %/2 mm
+    r = torch.from_numpy(p.ref).cuda()
+    e = torch.from_numpy(p.eval).cuda()
+    o = torch.empty_like(r)
+    res = {}
+    try:
+        losses = train.train(trained, X, T, steps=600, batch=4096, lr=3e-3)
+        assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:10])
+        for name, model in (("plain", None), ("untrained", untrained), ("trained", trained)):
+            h = g.gamma_create(r, e, 3, p.ref.shape, p.spacing, _crit(g, p.criteria))
+            try:
+                if model is not None:
+                    g.gamma_set_model(h, model)
+                    g.gamma_set_option(h, "seed_min_bucket", 0)
+                g.gamma_set_option(h, "stats", 1)
+                g.gamma_run(h, o)
+                counts = g.gamma_pass_rate(h)
+                res[name] = (o.cpu().numpy().astype(np.float64), counts, g.gamma_get_stats(h))
+            finally:
+                g.gamma_destroy(h)
+    finally:
+        g.gamma_model_destroy(trained)
+        g.gamma_model_destroy(untrained)
+    plain, c_plain, s_plain = res["plain"]
+    for name in ("untrained", "trained"):
+        got, c, st = res[name]
+        np.testing.assert_allclose(got, plain, rtol=0, atol=1e-6, equal_nan=True)
+        assert c[1:] == c_plain[1:]
+        assert st["seeded"] == st["tail_voxels"] == s_plain["tail_voxels"] > 0
+    idx = _sample(res["trained"][0], np.random.default_rng(9), n=3000)
+    want = oracle_gamma(p.ref, p.eval, p.spacing, p.criteria, idx=idx)
+    assert_parity(res["trained"][0].ravel()[idx], want)
+    # what the trained proposal gains: a tighter starting bound on more of the
+    # queued voxels, hence fewer table cells keyed and visited by the walk
+    tv = s_plain["tail_voxels"]
+    s_tr, s_un = res["trained"][2], res["untrained"][2]
+    assert s_tr["seed_improved"] > s_un["seed_improved"]
+    assert s_tr["cells_keyed"] < s_plain["cells_keyed"]
+    assert s_tr["cells_visited"] < s_plain["cells_visited"]
+    assert s_tr["cells_keyed"] / tv < s_un["cells_keyed"] / tv
