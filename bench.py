@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
+    ap.add_argument("--walk", type=int, default=-1,
+                    help="1: tile-staged walk, 0: voxel-queue walk (-1: library default)")
     ap.add_argument("--no-vs-plain", action="store_true",
                     help="skip the learned + batched against plain comparison")
     ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation", "mlp_infer",
@@ -533,6 +535,8 @@ def run_ours(args, pair, rank, world, local_rank):
     out = torch.empty_like(ref)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     h = g.gamma_create(ref, ev, ndim, shape, spacing, crit)
+    if args.walk >= 0:
+        g.gamma_set_option(h, "walk", args.walk)
     tuned = None
     if args.lanes or args.shell_blocks or args.tail_blocks:
         launch = {k: v for k, v in (("lanes_per_voxel", args.lanes),
@@ -599,6 +603,8 @@ def run_ours(args, pair, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         hh = g.gamma_create(None, None, ndim, shape, spacing, crit)
+        if args.walk >= 0:
+            g.gamma_set_option(hh, "walk", args.walk)
         for k, v in launch.items():                  # the launch shapes tuned above
             g.gamma_set_option(hh, k, v)
         try:

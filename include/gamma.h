@@ -198,7 +198,15 @@ int gamma_get_stats(gamma_handle h, gamma_stats *out);
 int gamma_get_timings(gamma_handle h, gamma_timings *out);
 
 /* Tuning and diagnostic options (take effect at the next run):
+ *  "walk"             1 (default): the queued voxels are walked tile by tile:
+ *                     each block stages the evaluation doses around one
+ *                     256-voxel tile in shared memory (one TMA copy) and walks
+ *                     the table for that tile's queued voxels, the lanes per
+ *                     voxel chosen per tile; 0: voxel by voxel from a queue
+ *                     ordered by cost, "lanes_per_voxel" lanes each (batch
+ *                     handles and gamma_run_noalloc always walk this way)
  *  "lanes_per_voxel"  2, 4, 8, 16 or 32 lanes search one queued voxel together
+ *                     (the voxel-by-voxel walk)
  *  "table_cap"        maximum cell-table length (rebuilds the table)
  *  "fp64_tau_exp10"   FP64 redo when the normalised Gram determinant
  *                     det(G)/prod(G_ii) < 10^-value; value <= 0 disables it
@@ -217,7 +225,7 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     change between (not with "timing", a model or "design")
  *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell
  *                     kernel's register budget is sized for (default 2)
- *  "tail_blocks_per_sm"   1 to 3: the same for the table-walk kernel
+ *  "tail_blocks_per_sm"   1 to 3: the same for the table-walk kernels
  *                     (default 2; lanes_per_voxel defaults to 8)
  *  "design"           ablation of the paper's GPU design (Algorithm A2;
  *                     single-pair handles): 0 this library's two-phase search
@@ -285,7 +293,8 @@ int gamma_batch_pass_rate(gamma_handle h, int pair, double *rate, int64_t *n_eva
 int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
 
 /* Autotuner: times the full run (single or batch handle) for every
- * combination of lanes_per_voxel in {2, 4, 8, 16, 32}, shell_blocks_per_sm in
+ * combination of lanes_per_voxel in {2, 4, 8, 16, 32} (not varied for the
+ * tile-staged walk, which picks its own), shell_blocks_per_sm in
  * {1, 2, 3, 4} and tail_blocks_per_sm in {1, 2, 3} (two warm-ups and `reps` timed
  * runs each, CUDA events on `cuda_stream`), keeps the fastest as the handle's
  * options and returns it (any output pointer may be NULL).  gamma_out_dev receives the

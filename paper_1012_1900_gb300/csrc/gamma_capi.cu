@@ -101,6 +101,12 @@ struct gamma_ctx {
     unsigned char* tail_bucket = nullptr;
     unsigned* tail_sorted = nullptr;
     unsigned tail_cap = 0;
+    // tile-staged walk: queue bit masks per shell tile, tiles with queued voxels
+    unsigned* tile_mask = nullptr;
+    unsigned* tile_list = nullptr;
+    unsigned char* tile_bkt = nullptr;
+    unsigned* tile_sorted = nullptr;
+    int walk = 1;                     // 1: tile-staged walk (k_walk); 0: voxel queue walk (k_tail)
     // options
     int lanes = gk::kDefaultLanesPerVoxel;
     double tau = 1e-6;
@@ -282,6 +288,12 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.tail_sorted = h->tail_sorted;
     P.sort_tail = h->sort_tail;
     P.shell_minblocks = h->shell_minblocks;
+    if (h->walk && h->tile_mask) {
+        P.tile_mask = h->tile_mask;
+        P.tile_list = h->tile_list;
+        P.tile_bkt = h->tile_bkt;
+        P.tile_sorted = h->tile_sorted;
+    }
     return P;
 }
 
@@ -313,6 +325,10 @@ void free_ctx(gamma_ctx* h)
     cudaFree(h->tail_raw);
     cudaFree(h->tail_bucket);
     cudaFree(h->tail_sorted);
+    cudaFree(h->tile_mask);
+    cudaFree(h->tile_list);
+    cudaFree(h->tile_bkt);
+    cudaFree(h->tile_sorted);
     cudaFree(h->gnorm);
     cudaFree(h->seed_list);
     cudaFree(h->own_ref);
@@ -584,6 +600,17 @@ int gamma_create(gamma_handle* out, const float* ref_dev, const float* eval_dev,
     if ((e = cudaMalloc(&h->tail_raw, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = cudaMalloc(&h->tail_sorted, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = cudaMalloc(&h->tail_bucket, nvox)) != cudaSuccess) return fail(cuda_fail(e));
+    {
+        Problem P0 = make_problem(h, nullptr);
+        const int tiles = gk::shell_tiles(P0);
+        if (tiles < 0) return fail(GAMMA_ERR_SHAPE);
+        const size_t nt = (size_t)std::max(tiles, 1);
+        if ((e = cudaMalloc(&h->tile_mask, sizeof(unsigned) * 8 * nt)) != cudaSuccess ||
+            (e = cudaMalloc(&h->tile_list, sizeof(unsigned) * nt)) != cudaSuccess ||
+            (e = cudaMalloc(&h->tile_bkt, nt)) != cudaSuccess ||
+            (e = cudaMalloc(&h->tile_sorted, sizeof(unsigned) * nt)) != cudaSuccess)
+            return fail(cuda_fail(e));
+    }
     if (!ref_dev) {
         if ((e = cudaMalloc(&h->own_ref, sizeof(float) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
         if ((e = cudaMalloc(&h->own_ev, sizeof(float) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
@@ -703,6 +730,22 @@ int gamma_set_inputs(gamma_handle h, const float* ref_dev, const float* eval_dev
     return GAMMA_OK;
 }
 
+// Order and walk the queued voxels: tile by tile from staged halo boxes
+// (k_walk) or voxel by voxel (k_tail).  tm: record the "order" event between.
+static int enqueue_walk(gamma_handle h, const Problem& P, cudaStream_t s, bool tm)
+{
+    if (P.tile_mask) {
+        CK(gk::launch_order_tiles(P, s));
+        if (tm) CK(cudaEventRecord(h->tev[4], s));
+        CK(gk::launch_walk(P, h->tail_minblocks, s));
+    } else {
+        CK(gk::launch_order_tail(P, s));
+        if (tm) CK(cudaEventRecord(h->tev[4], s));
+        CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, s));
+    }
+    return GAMMA_OK;
+}
+
 // The search of one run with no timing events, model or paper design: what
 // the graph replay captures.
 static int enqueue_search(gamma_handle h, const Problem& P, cudaStream_t s)
@@ -710,9 +753,7 @@ static int enqueue_search(gamma_handle h, const Problem& P, cudaStream_t s)
     CK(cudaMemsetAsync(h->ctr, 0, sizeof(Counters), s));
     CK(gk::launch_prepare(P, s, 1));
     CK(gk::launch_shell(P, s));
-    CK(gk::launch_order_tail(P, s));
-    CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, s));
-    return GAMMA_OK;
+    return enqueue_walk(h, P, s, false);
 }
 
 int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
@@ -812,9 +853,7 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
         CK(gk::launch_learned(Q, W, s));
     }
     if (tm) CK(cudaEventRecord(h->tev[3], s));
-    CK(gk::launch_order_tail(P, s));
-    if (tm) CK(cudaEventRecord(h->tev[4], s));
-    CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, s));
+    if (int rc = enqueue_walk(h, P, s, tm)) return rc;
     if (tm) {
         CK(cudaEventRecord(h->tev[5], s));
         if (!h->ev_h2d) CK(cudaEventRecord(h->tev[6], s));
@@ -945,9 +984,7 @@ int run_host_pipelined(gamma_handle h, const float* eval_host, float* gamma_out_
     CK(cudaMemcpyAsync(gamma_out_host, h->own_out, bytes, cudaMemcpyDeviceToHost, o));
     if (tm) CK(cudaEventRecord(h->tev_out, o));
     CK(cudaEventRecord(E[5], o));
-    CK(gk::launch_order_tail(P, c));
-    if (tm) CK(cudaEventRecord(h->tev[4], c));
-    CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, c));
+    if (int rc = enqueue_walk(h, P, c, tm)) return rc;
     if (tm) CK(cudaEventRecord(h->tev[5], c));
     CK(cudaStreamWaitEvent(c, E[5], 0));
     CK(gk::launch_patch_host(P, out_mapped, h->host_ctr_dev, c));
@@ -1140,6 +1177,11 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
     if (!std::strcmp(key, "graph")) {                  // single-pair handles
         if (value != 0 && value != 1) return GAMMA_ERR_INVALID_ARG;
         h->graph = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "walk")) {
+        if (h->batch || value < 0 || value > 1) return GAMMA_ERR_INVALID_ARG;
+        h->walk = (int)value;
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "lanes_per_voxel")) {
@@ -1364,10 +1406,13 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     float best = INFINITY;
     int rc = GAMMA_OK;
     auto run = [&]() { return h->batch ? gamma_batch_run(h, s) : gamma_run(h, gamma_out_dev, s); };
-    for (int li = 0; li < 5 && rc == GAMMA_OK; ++li)
+    // the tile-staged walk picks its lanes per tile: only the block budgets vary
+    const bool tile_walk = !h->batch && !h->grids && h->walk && h->tile_mask;
+    const int nl = tile_walk ? 1 : 5;
+    for (int li = 0; li < nl && rc == GAMMA_OK; ++li)
         for (int bl = 1; bl <= 4 && rc == GAMMA_OK; ++bl)
             for (int tb = 1; tb <= 3 && rc == GAMMA_OK; ++tb) {
-                h->lanes = lanes[li];
+                h->lanes = tile_walk ? best_l : lanes[li];
                 h->shell_minblocks = bl;
                 h->tail_minblocks = tb;
                 h->sg_dirty = true;                    // a captured graph holds the old shapes
@@ -1381,7 +1426,7 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
                 float ms = 0;
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms /= reps;
-                if (ms < best) { best = ms; best_l = lanes[li]; best_b = bl; best_t = tb; }
+                if (ms < best) { best = ms; best_l = h->lanes; best_b = bl; best_t = tb; }
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -76,6 +76,10 @@ struct Counters {
     unsigned int shell_next[kShellSlots];   // tile work counters of the shell launches
     unsigned int hist[kNumBuckets];
     unsigned int cursor[kNumBuckets];
+    unsigned int tile_count;            // shell tiles with at least one queued voxel
+    unsigned int tile_head;             // work counter of the tile-staged walk
+    unsigned int tile_hist[kNumBuckets];    // those tiles by their largest cost bucket
+    unsigned int tile_cursor[kNumBuckets];
 };
 
 // Order-preserving encoding of a float into an unsigned int (for atomicMax).
@@ -128,6 +132,15 @@ struct Problem {
     const float* gnorm_e;
     const float* gnorm_r;
     unsigned* seed_list;
+    // tile-staged walk (null: the queue is walked voxel by voxel, k_tail):
+    // per shell tile one bit per voxel of the tile that is queued (8 words,
+    // word = warp of the tile, bit = lane), the tiles with any queued voxel
+    // (unordered, with their largest cost bucket) and the same tiles ordered
+    // by that bucket, most expensive first
+    unsigned* tile_mask;
+    unsigned* tile_list;
+    unsigned char* tile_bkt;
+    unsigned* tile_sorted;
 };
 
 // Readiness of the evaluation dose by z slab, for a shell launch that starts
@@ -195,6 +208,11 @@ cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, Counters
                               cudaStream_t s);
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
 cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblocks, cudaStream_t s);
+// Tile-staged walk (P.tile_mask set): order the tiles with queued voxels by
+// cost, then one block per tile stages the tile's evaluation-dose halo box in
+// shared memory and walks the table for the tile's queued voxels.
+cudaError_t launch_order_tiles(const Problem& P, cudaStream_t s);
+cudaError_t launch_walk(const Problem& P, int walk_minblocks, cudaStream_t s);
 int device_sm_count();
 
 // Host-side constants a Problem needs before it is uploaded for a batch.

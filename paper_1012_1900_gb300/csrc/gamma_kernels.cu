@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(256, MINB)
     __shared__ unsigned int sh_rmax;
     __shared__ __align__(16) Problem sh_P;     // the current pair (batched launches)
     __shared__ int sh_next[2];                 // the block's next tile, per staging buffer
+    __shared__ unsigned sh_tb[2];              // 1 + largest cost bucket queued in the tile (0: none)
 
     const int lane = threadIdx.x & 31;
     const int lx = lane, ly = (threadIdx.x >> 5) % T::TY, lz = (threadIdx.x >> 5) / T::TY;
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(256, MINB)
         sh_eval = 0;
         sh_pass = 0;
         sh_rmax = 0;
+        sh_tb[0] = sh_tb[1] = 0;
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
@@ -336,6 +338,16 @@ __global__ void __launch_bounds__(256, MINB)
             }
         }
         const unsigned tm = __ballot_sync(kFull, tail);
+        if (!BATCH && P.tile_mask) {
+            // the tile's queue for the tile-staged walk: one bit per voxel
+            if (lane == 0) P.tile_mask[(size_t)lt * 8 + (threadIdx.x >> 5)] = tm;
+            if (tm) {
+                unsigned bm = tail ? (unsigned)bucket + 1u : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(kFull, bm, o));
+                if (lane == 0) atomicMax(&sh_tb[buf], bm);
+            }
+        }
         if (tm) {
             unsigned pos0 = 0;
             if (lane == 0) pos0 = atomicAdd(&P.ctr->tail_count, (unsigned)__popc(tm));
@@ -360,6 +372,16 @@ __global__ void __launch_bounds__(256, MINB)
                 mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
             }
             break;
+        }
+        if (!BATCH && P.tile_mask && threadIdx.x == 0) {
+            const unsigned b1 = sh_tb[buf];
+            if (b1) {
+                const unsigned pos = atomicAdd(&P.ctr->tile_count, 1u);
+                P.tile_list[pos] = (unsigned)lt;
+                P.tile_bkt[pos] = (unsigned char)(b1 - 1u);
+                atomicAdd(&P.ctr->tile_hist[b1 - 1u], 1u);
+            }
+            sh_tb[buf] = 0;            // the next tile of this buffer comes after the next barrier
         }
         t = sh_next[buf];
     }
@@ -399,6 +421,38 @@ __global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ Problem
             base[threadIdx.x] = start[threadIdx.x] + atomicAdd(&P.ctr->cursor[threadIdx.x], cnt[threadIdx.x]);
         __syncthreads();
         if (b >= 0) P.tail_sorted[base[b] + rank] = P.tail_raw[i];
+        __syncthreads();
+    }
+}
+
+// The tiles with queued voxels in order of their largest cost bucket, most
+// expensive first (same scheme as k_scatter).
+__global__ void __launch_bounds__(256) k_scatter_tiles(const __grid_constant__ Problem P)
+{
+    __shared__ unsigned start[kNumBuckets], cnt[kNumBuckets], base[kNumBuckets];
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        for (int b = kNumBuckets - 1; b >= 0; --b) {
+            start[b] = acc;
+            acc += P.ctr->tile_hist[b];
+        }
+    }
+    const unsigned total = P.ctr->tile_count;
+    for (unsigned c0 = blockIdx.x * blockDim.x; c0 < total; c0 += gridDim.x * blockDim.x) {
+        if (threadIdx.x < kNumBuckets) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned i = c0 + threadIdx.x;
+        int b = -1;
+        unsigned rank = 0;
+        if (i < total) {
+            b = P.tile_bkt[i];
+            rank = atomicAdd(&cnt[b], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumBuckets && cnt[threadIdx.x])
+            base[threadIdx.x] = start[threadIdx.x] + atomicAdd(&P.ctr->tile_cursor[threadIdx.x], cnt[threadIdx.x]);
+        __syncthreads();
+        if (b >= 0) P.tile_sorted[base[b] + rank] = P.tile_list[i];
         __syncthreads();
     }
 }
@@ -637,6 +691,287 @@ __global__ void __launch_bounds__(256, MINB)
 }
 
 // --------------------------------------------------------------------------
+// k_walk: tile-staged walk of the queued voxels, one shell tile per block
+// --------------------------------------------------------------------------
+
+// Halo box of a walk tile in shared memory: the shell tile plus H voxels on
+// every side (the x start stays a multiple of 4 floats for the TMA copy).
+// Every cell whose corner lies within H - 1 voxels of a tile voxel (cells
+// with box distance up to (H - 1) h) reads its eight doses from the box;
+// cells further out read global memory.
+template <int N>
+struct WalkBox {
+    using T = ShellTile<N>;
+    static constexpr int H = 4;
+    static constexpr int BX = T::TX + 2 * H, BY = T::TY + 2 * H, BZ = N == 3 ? T::TZ + 2 * H : 1;
+    static constexpr int ELEMS = BX * BY * BZ;
+    static constexpr int STRIDE = (ELEMS + 31) / 32 * 32;
+    static_assert(STRIDE * 4 % 128 == 0, "TMA destination must stay 128-byte aligned");
+    static_assert(H % 4 == 0, "the box's x start must stay 16-byte aligned");
+};
+
+constexpr int kWalkTableCache = 1024;        // first table entries kept in shared memory
+
+// visit_cell with the eight doses from the staged box when the whole cell
+// lies inside it (b0x, b0y, b0z: grid coordinates of the box's first element).
+template <int N>
+__device__ __forceinline__ float visit_cell_box(const Problem& P, const float* __restrict__ bx,
+                                                int b0x, int b0y, int b0z, int x, int y, int z,
+                                                int cx, int cy, int cz, float key, float dr,
+                                                float inv, float dnorm, float best, TailStats& st)
+{
+    using B = WalkBox<N>;
+    const int px = x + cx, py = y + cy, pz = z + cz;
+    if ((unsigned)px >= (unsigned)P.nx || (unsigned)py >= (unsigned)P.ny ||
+        (N == 3 && (unsigned)pz >= (unsigned)P.nz))
+        return best;
+    const bool ex = px + 1 < P.nx, ey = py + 1 < P.ny, ez = N == 3 && pz + 1 < P.nz;
+    const int lx = px - b0x, ly = py - b0y, lz = N == 3 ? pz - b0z : 0;
+    const bool inbox = (unsigned)lx <= (unsigned)(B::BX - 2) && (unsigned)ly <= (unsigned)(B::BY - 2) &&
+                       (N == 2 || (unsigned)lz <= (unsigned)(B::BZ - 2));
+    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+    const long long p = (long long)pz * sz + (long long)py * sy + px;
+    const int lp = (lz * B::BY + ly) * B::BX + lx;
+    float q[8];
+    uint32_t ok = 0;
+    float qmin = kInf, qmax = -kInf;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        q[u] = 0.f;
+        if (u < (1 << N)) {
+            const bool present = (!(u & 1) || ex) && (!(u & 2) || ey) && (!(u & 4) || ez);
+            if (present) {
+                const int lo = ((u & 1) ? 1 : 0) + ((u & 2) ? B::BX : 0) + ((u & 4) ? B::BX * B::BY : 0);
+                const long long o = p + ((u & 1) ? 1 : 0) + ((u & 2) ? sy : 0) + ((u & 4) ? sz : 0);
+                const float d = inbox ? bx[lp + lo] : __ldg(P.ev + o);
+                q[u] = (d - dr) * inv;
+                qmin = fminf(qmin, q[u]);
+                qmax = fmaxf(qmax, q[u]);
+                ok |= 1u << u;
+            }
+        }
+    }
+    const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
+    if (fmaf(gap, gap, key * key) >= best) {
+        if (P.stats) ++st.pruned;
+        return best;
+    }
+    if (P.stats) ++st.visited;
+    const float cb = cell_all_faces<N>(P, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], ok, cx, cy,
+                                       cz, p, dr, dnorm);
+    return fminf(best, cb);
+}
+
+// Minimum over the G lanes of a group (G a power of two <= 32, lanes gbase ..
+// gbase + G - 1 of the warp, mask gmask).
+__device__ __forceinline__ float group_min_rt(float v, int G, unsigned gmask)
+{
+    for (int o = G >> 1; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(gmask, v, o));
+    return v;
+}
+
+// One block per tile with queued voxels, in cost order: the halo box of the
+// tile arrives by TMA (double-buffered, the next tile's copy in flight while
+// this one is walked); the tile's queued voxels are read from its bit mask;
+// G lanes per voxel (G chosen per tile from the number of queued voxels so
+// that the block's 256 threads are used) walk the sorted cell table G cells
+// at a time with the exact stop of Algorithm A1 step 4b-ii and the dose-gap
+// bound, reading cell doses from the box.
+template <int N, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_walk(const __grid_constant__ Problem P, const __grid_constant__ CUtensorMap wmap, int use_tma)
+{
+    using T = ShellTile<N>;
+    using B = WalkBox<N>;
+    __shared__ __align__(128) float box[2][B::STRIDE];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ TableEntry sh_table[kWalkTableCache];
+    __shared__ unsigned short sh_q[T::TX * T::TY * T::TZ];
+    __shared__ int sh_nq;
+    __shared__ int sh_next[2];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned ntiles = P.ctr->tile_count;
+    const unsigned* order = P.sort_tail ? P.tile_sorted : P.tile_list;
+    const int ncache = min(P.ntable, kWalkTableCache);
+    for (int i = tid; i < ncache; i += blockDim.x) sh_table[i] = P.table[i];
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const float dnorm = resolve_dnorm(P);
+    const float rc2 = P.r_cover * P.r_cover;
+    const int ntx = (P.nx + T::TX - 1) / T::TX, nty = (P.ny + T::TY - 1) / T::TY;
+    auto origin = [&](unsigned lt, int& x0, int& y0, int& z0) {
+        x0 = (int)(lt % (unsigned)ntx) * T::TX;
+        y0 = (int)((lt / (unsigned)ntx) % (unsigned)nty) * T::TY;
+        z0 = N == 3 ? (int)(lt / (unsigned)ntx / (unsigned)nty) * T::TZ : 0;
+    };
+    auto issue = [&](unsigned i, int b) {
+        if (i >= ntiles || !use_tma) return;
+        int x0, y0, z0;
+        origin(order[i], x0, y0, z0);
+        mbar_arrive_expect_tx(&bar[b], B::ELEMS * (uint32_t)sizeof(float));
+        if (N == 3) tma_load_3d(box[b], &wmap, x0 - B::H, y0 - B::H, z0 - B::H, &bar[b]);
+        else tma_load_2d(box[b], &wmap, x0 - B::H, y0 - B::H, &bar[b]);
+    };
+    unsigned my_eval = 0, my_pass = 0, my_over = 0;
+    TailStats st;
+    uint32_t parity = 0;
+    int buf = 0;
+    unsigned i = blockIdx.x;
+    if (tid == 0) issue(i, 0);
+    for (; i < ntiles; buf ^= 1) {
+        const unsigned lt = order[i];
+        int x0, y0, z0;
+        origin(lt, x0, y0, z0);
+        const int b0x = x0 - B::H, b0y = y0 - B::H, b0z = N == 3 ? z0 - B::H : 0;
+        if (tid == 0) {
+            const unsigned nt = gridDim.x + atomicAdd(&P.ctr->tile_head, 1u);
+            sh_next[buf] = (int)min(nt, ntiles);
+            issue(nt, buf ^ 1);
+        }
+        // the tile's queued voxels, in voxel order (warp 0)
+        if (warp == 0) {
+            const unsigned w = lane < 8 ? P.tile_mask[(size_t)lt * 8 + lane] : 0u;
+            const int c = __popc(w);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            int pos = incl - c;
+            for (unsigned m = w; m; m &= m - 1) sh_q[pos++] = (unsigned short)(lane * 32 + __ffs(m) - 1);
+            if (lane == 7) sh_nq = incl;
+        }
+        float* bx = box[buf];
+        bool timed_out = false;
+        if (use_tma) {
+            timed_out = !mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+            parity ^= 1u << buf;
+        } else {
+            for (int e = tid; e < B::ELEMS; e += blockDim.x) {
+                const int ex_ = e % B::BX, ey_ = (e / B::BX) % B::BY, ez_ = e / (B::BX * B::BY);
+                const int gx = b0x + ex_, gy = b0y + ey_, gz = b0z + ez_;
+                const bool in = (unsigned)gx < (unsigned)P.nx && (unsigned)gy < (unsigned)P.ny &&
+                                (N == 2 || (unsigned)gz < (unsigned)P.nz);
+                bx[e] = in ? __ldg(P.ev + ((long long)gz * P.ny + gy) * P.nx + gx) : 0.f;
+            }
+        }
+        __syncthreads();
+        const int nq = sh_nq;
+        int G = 32;
+        while (G > 2 && nq * G > (int)blockDim.x) G >>= 1;
+        const int slots = (int)blockDim.x / G;
+        const int gl = tid & (G - 1);
+        const int gbase = lane & ~(G - 1);
+        const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
+        for (int k = tid / G; k < nq && !timed_out; k += slots) {
+            const int q = sh_q[k];
+            const int x = x0 + (q & 31), y = y0 + (q >> 5) % T::TY, z = z0 + (q >> 5) / T::TY;
+            const unsigned v = (unsigned)(((long long)z * P.ny + y) * P.nx + x);
+            const float dr = __ldg(P.ref + v);
+            const float dD = P.dd_frac * (P.local ? dr : dnorm);
+            const float inv = 1.0f / dD;
+            float best = P.out[v];                       // gamma^2 over the faces through v
+            int t = 0;
+            while (t < P.ntable) {
+                const int idx = t + gl;
+                float key = kInf;
+                uint32_t off = 0;
+                if (idx < P.ntable) {
+                    const TableEntry e = idx < kWalkTableCache ? sh_table[idx] : P.table[idx];
+                    key = e.key;
+                    off = e.off;
+                }
+                const float k0 = __shfl_sync(gmask, key, gbase);
+                if (k0 * k0 >= best) break;               // A1 step 4b-ii, exact
+                float cb = best;
+                if (key * key < best) {
+                    if (P.stats) ++st.keyed;
+                    cb = visit_cell_box<N>(P, bx, b0x, b0y, b0z, x, y, z, unpack10(off, 0),
+                                           unpack10(off, 10), unpack10(off, 20), key, dr, inv, dnorm,
+                                           best, st);
+                }
+                best = group_min_rt(cb, G, gmask);
+                t += G;
+            }
+            if (t >= P.ntable && best > rc2) {
+                // past a truncated table: the exact scan of the remaining box
+                if (gl == 0) ++my_over;
+                const float g = sqrtf(best);
+                const int ax = (int)ceilf(g / P.hn[0]) + 1;
+                const int ay = (int)ceilf(g / P.hn[1]) + 1;
+                const int az = N == 3 ? (int)ceilf(g / P.hn[2]) + 1 : 0;
+                const int xa = max(-ax - 1, -x), xb = min(ax, P.nx - 1 - x);
+                const int ya = max(-ay - 1, -y), yb = min(ay, P.ny - 1 - y);
+                const int za = N == 3 ? max(-az - 1, -z) : 0, zb = N == 3 ? min(az, P.nz - 1 - z) : 0;
+                const long long wx = xb - xa + 1, wy = yb - ya + 1, wz = zb - za + 1;
+                const long long tot = wx * wy * wz;
+                const float lim = rc2 * 0.99999f;
+                float lb = best;
+                for (long long b = gl; b < tot; b += G) {
+                    const int cx = xa + (int)(b % wx);
+                    const long long rr = b / wx;
+                    const int cy = ya + (int)(rr % wy);
+                    const int cz = za + (int)(rr / wy);
+                    const float axd = (float)max(max(cx, -cx - 1), 0) * P.hn[0];
+                    const float ayd = (float)max(max(cy, -cy - 1), 0) * P.hn[1];
+                    const float azd = N == 3 ? (float)max(max(cz, -cz - 1), 0) * P.hn[2] : 0.f;
+                    float k2 = axd * axd + ayd * ayd + azd * azd;
+                    if (k2 == 0.f)
+                        k2 = P.key0_far2[(cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2)];
+                    if (k2 < lim || k2 >= lb) continue;
+                    lb = visit_cell_box<N>(P, bx, b0x, b0y, b0z, x, y, z, cx, cy, cz, sqrtf(k2), dr,
+                                           inv, dnorm, lb, st);
+                }
+                best = group_min_rt(lb, G, gmask);
+            }
+            if (gl == 0) {
+                const float gam = sqrtf(best);
+                P.out[v] = gam;
+                ++my_eval;
+                my_pass += gam <= 1.f;
+            }
+        }
+        // box[buf] and sh_q are free for reuse once every thread is here
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0) {
+                atomicOr(&P.ctr->flags, kFlagTimeout);
+                mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+                mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
+            }
+            break;
+        }
+        i = (unsigned)sh_next[buf];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_eval += __shfl_xor_sync(kFull, my_eval, o);
+        my_pass += __shfl_xor_sync(kFull, my_pass, o);
+        my_over += __shfl_xor_sync(kFull, my_over, o);
+        if (P.stats) {
+            st.visited += __shfl_xor_sync(kFull, st.visited, o);
+            st.pruned += __shfl_xor_sync(kFull, st.pruned, o);
+            st.keyed += __shfl_xor_sync(kFull, st.keyed, o);
+        }
+    }
+    if (lane == 0) {
+        if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
+        if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
+        if (my_over) atomicAdd(&P.ctr->overflow_count, my_over);
+        if (P.stats) {
+            atomicAdd(&P.ctr->cells_visited, st.visited);
+            atomicAdd(&P.ctr->cells_pruned, st.pruned);
+            atomicAdd(&P.ctr->cells_keyed, st.keyed);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // Launchers
 // --------------------------------------------------------------------------
 
@@ -760,7 +1095,9 @@ void key0_far(const double hn_in[3], int nd, double far[8])
     }
 }
 
-bool encode_tile_map(const Problem& P, CUtensorMap* map)
+// Tensor map of the evaluation dose with a tile box of (bx, by, bz) floats;
+// false when TMA cannot be used for it.
+static bool encode_box_map(const Problem& P, CUtensorMap* map, int bx, int by, int bz)
 {
     using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -780,25 +1117,29 @@ bool encode_tile_map(const Problem& P, CUtensorMap* map)
     if (!encode) return false;
     if (((uintptr_t)P.ev & 15u) != 0 || (P.nx % 4) != 0) return false;   // TMA alignment rules
     if (P.ndim == 3) {
-        using T = ShellTile<3>;
         const cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz};
         const cuuint64_t strides[2] = {(cuuint64_t)P.nx * 4, (cuuint64_t)P.nx * P.ny * 4};
-        const cuuint32_t box[3] = {T::BX, T::BY, T::BZ};
+        const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
         const cuuint32_t es[3] = {1, 1, 1};
         return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)P.ev, dims, strides, box, es,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
-    using T = ShellTile<2>;
     const cuuint64_t dims[2] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny};
     const cuuint64_t strides[1] = {(cuuint64_t)P.nx * 4};
-    const cuuint32_t box[2] = {T::BX, T::BY};
+    const cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
     const cuuint32_t es[2] = {1, 1};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)P.ev, dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
+}
+
+bool encode_tile_map(const Problem& P, CUtensorMap* map)
+{
+    return P.ndim == 3 ? encode_box_map(P, map, ShellTile<3>::BX, ShellTile<3>::BY, ShellTile<3>::BZ)
+                       : encode_box_map(P, map, ShellTile<2>::BX, ShellTile<2>::BY, 1);
 }
 
 int shell_tiles(const Problem& P)
@@ -948,6 +1289,37 @@ cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblock
     const int grid = sms * 8;      // persistent: enough warps to fill every SM
     if (P.ndim == 3) launch_tail_n<3, false>(P, nullptr, lanes_per_voxel, tail_minblocks, grid, s);
     else launch_tail_n<2, false>(P, nullptr, lanes_per_voxel, tail_minblocks, grid, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_tiles(const Problem& P, cudaStream_t s)
+{
+    if (!P.sort_tail) return cudaSuccess;
+    k_scatter_tiles<<<device_sm_count() * 2, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <int N>
+static void launch_walk_n(const Problem& P, const CUtensorMap& map, int use_tma, int per_sm,
+                          int grid, cudaStream_t s)
+{
+    if (per_sm >= 3) k_walk<N, 3><<<grid, 256, 0, s>>>(P, map, use_tma);
+    else if (per_sm == 2) k_walk<N, 2><<<grid, 256, 0, s>>>(P, map, use_tma);
+    else k_walk<N, 1><<<grid, 256, 0, s>>>(P, map, use_tma);
+}
+
+cudaError_t launch_walk(const Problem& P, int walk_minblocks, cudaStream_t s)
+{
+    if (!P.tile_mask) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    int use_tma;
+    if (P.ndim == 3) use_tma = encode_box_map(P, &map, WalkBox<3>::BX, WalkBox<3>::BY, WalkBox<3>::BZ);
+    else use_tma = encode_box_map(P, &map, WalkBox<2>::BX, WalkBox<2>::BY, 1);
+    const int per_sm = std::min(3, std::max(1, walk_minblocks));
+    const int grid = device_sm_count() * per_sm;     // persistent; blocks past the tile list exit
+    if (P.ndim == 3) launch_walk_n<3>(P, map, use_tma, per_sm, grid, s);
+    else launch_walk_n<2>(P, map, use_tma, per_sm, grid, s);
     return cudaGetLastError();
 }
 
