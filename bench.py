@@ -81,12 +81,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true", help="skip the cell census (profiling runs)")
+    ap.add_argument("--record-counters", default="", metavar="CSV",
+                    help="store the search kernels' counters from `ncu -i REPORT --page raw --csv` "
+                         "output in profiles/counters.json (for --workload), then exit")
+    ap.add_argument("--capture-note", default="", help="where the --record-counters capture came from")
     ap.add_argument("--walk", type=int, default=-1,
                     help="1: tile-staged walk, 0: voxel-queue walk (-1: library default)")
     ap.add_argument("--no-vs-plain", action="store_true",
                     help="skip the learned + batched against plain comparison")
     ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation", "mlp_infer",
-                                             "grids"],
+                                             "grids", "train_step", "parity"],
                     default=None,
                     help="learned: train + evaluate the proposal network (200x200x150 pairs, "
                          "2%%/2mm); batch: 64 uneven pairs batched vs one by one")
@@ -360,11 +364,28 @@ def search_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel changed since the capture or none was taken for this workload."""
+COUNTERS_PATH = os.path.join(ROOT, "profiles", "counters.json")
+# ncu metrics recorded per kernel (raw page names -> counters.json fields)
+NCU_FIELDS = {
+    "gpu__time_duration.sum": "ncu_duration_ns",
+    "dram__bytes_read.sum": "dram_read_bytes",
+    "dram__bytes_write.sum": "dram_write_bytes",
+    "smsp__inst_executed.sum": "warp_inst_per_launch",
+    "smsp__thread_inst_executed.sum": "thread_inst_per_launch",
+    "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active": "fma_pipe_pct",
+    "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active": "alu_pipe_pct",
+    "sm__warps_active.avg.pct_of_peak_sustained_active": "warps_active_pct",
+    "sm__inst_issued.avg.pct_of_peak_sustained_active": "issue_active_pct",
+    "launch__registers_per_thread": "registers",
+}
+
+
+def recorded_counters(kernel: str, workload: str):
+    """The ncu counters of one launch of `kernel` on `workload` from
+    profiles/counters.json, or None when the search sources changed since the
+    capture or none was taken for this workload."""
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        with open(COUNTERS_PATH) as f:
             rec = json.load(f).get(kernel)
     except (OSError, ValueError):
         return None
@@ -372,7 +393,53 @@ def recorded_traffic(kernel: str, workload: str):
         return None
     if rec.get("source_sha256_16") != search_source_hash():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + write) per launch, as recorded_counters."""
+    rec = recorded_counters(kernel, workload)
+    if not rec or rec.get("dram_read_bytes") is None:
+        return None
+    return rec["dram_read_bytes"] + rec.get("dram_write_bytes", 0)
+
+
+def record_counters(csv_path: str, workload: str, capture: str) -> dict:
+    """Read `ncu -i <report> --page raw --csv` output and store, per search
+    kernel, the counters of its last captured launch in profiles/counters.json
+    with the hash of the search sources they describe."""
+    import csv
+    import re
+    with open(csv_path, newline="") as f:
+        rows = [r for r in csv.reader(f) if r]
+    head = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    names = rows[head]
+    data = [r for r in rows[head + 1:] if len(r) == len(names) and r[names.index("Kernel Name")]]
+    try:
+        with open(COUNTERS_PATH) as f:
+            out = json.load(f)
+    except (OSError, ValueError):
+        out = {}
+    sha = search_source_hash()
+    for r in data:
+        m = re.search(r"\b(k_[a-z_0-9]+)", r[names.index("Kernel Name")])
+        if not m:
+            continue
+        rec = {"workload": workload, "source_sha256_16": sha, "capture": capture,
+               "kernel_name": r[names.index("Kernel Name")]}
+        for metric, field in NCU_FIELDS.items():
+            if metric in names:
+                try:
+                    rec[field] = float(r[names.index(metric)].replace(",", ""))
+                except ValueError:
+                    pass
+        if "dram_read_bytes" not in rec:
+            continue                              # the units row, or a capture without counters
+        out[m.group(1)] = rec
+    os.makedirs(os.path.dirname(COUNTERS_PATH), exist_ok=True)
+    with open(COUNTERS_PATH, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+    return out
 
 
 def load_peaks():
@@ -499,6 +566,17 @@ def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
                     g.gamma_pass_rate(h)
                     st = g.gamma_get_stats(h)
                     row[f"{mode}_map"] = o.cpu().numpy()
+                    # phase split (library events; the seeding runs inside the
+                    # shell phase), from a few further runs
+                    g.gamma_set_option(h, "timing", 1)
+                    ph = []
+                    for _ in range(3):
+                        flush.zero_()
+                        g.gamma_run(h, o, stream)
+                        ph.append(g.gamma_get_timings(h))
+                    row[f"{mode}_phases_ms"] = {k: statistics.median(t[k] for t in ph)
+                                                for k in ("prepare_ms", "shell_ms", "order_ms",
+                                                          "tail_ms")}
                     if mode == "learned":
                         row["seeded"] = st["seeded"]
                         row["seed_improved"] = st["seed_improved"]
@@ -537,6 +615,7 @@ def run_ours(args, pair, rank, world, local_rank):
     h = g.gamma_create(ref, ev, ndim, shape, spacing, crit)
     if args.walk >= 0:
         g.gamma_set_option(h, "walk", args.walk)
+    walk_on = args.walk == 1          # the library walks voxel by voxel by default
     tuned = None
     if args.lanes or args.shell_blocks or args.tail_blocks:
         launch = {k: v for k, v in (("lanes_per_voxel", args.lanes),
@@ -672,20 +751,37 @@ def run_ours(args, pair, rank, world, local_rank):
 
         t_search = mean_ph["shell_ms"] + mean_ph["tail_ms"]
         achieved = tflops(shell_cells + tail_cells, t_search)
-        traffic = [recorded_traffic(k, args.workload) for k in ("k_shell", "k_tail")]
-        roofline = {"bound": "alu", "kernel": "k_shell+k_tail", "achieved": achieved,
+        walker = "k_walk" if walk_on else "k_tail"
+        traffic = [recorded_traffic(k, args.workload) for k in ("k_shell", walker)]
+        clock_hz = (clocks.get("sm_mhz") or sm_max) * 1e6
+
+        def issue(kernel, ms):
+            # executed warp instructions over the SMs' issue slots (4 per SM
+            # per cycle) in the kernel's live time, at the sampled clock
+            rec = recorded_counters(kernel, args.workload)
+            if not rec or not rec.get("warp_inst_per_launch") or ms <= 0:
+                return None
+            return {"warp_inst": rec["warp_inst_per_launch"],
+                    "frac": rec["warp_inst_per_launch"] / (n_sm * 4 * clock_hz * ms / 1e3),
+                    "fma_pipe_pct": rec.get("fma_pipe_pct"), "alu_pipe_pct": rec.get("alu_pipe_pct"),
+                    "lane_efficiency": (rec["thread_inst_per_launch"] / rec["warp_inst_per_launch"]
+                                        if rec.get("thread_inst_per_launch") else None)}
+        roofline = {"bound": "alu", "kernel": f"k_shell+{walker}", "achieved": achieved,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                     "traffic": None if None in traffic else sum(traffic),
                     "peak_basis": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                   f"{sm_max:.0f} MHz",
-                    "work": f"{shell_cells + tail_cells} cells x {f} FLOP",
+                    "work": f"{shell_cells + tail_cells} cells x {f} FLOP (census of whole cubes "
+                            "with key < gamma*, +1 per evaluated voxel)",
                     "per_kernel": {
                         "k_shell": {"ms": mean_ph["shell_ms"], "cells": shell_cells,
                                     "achieved": tflops(shell_cells, mean_ph["shell_ms"]),
-                                    "traffic": traffic[0]},
-                        "k_tail": {"ms": mean_ph["tail_ms"], "cells": tail_cells,
-                                   "achieved": tflops(tail_cells, mean_ph["tail_ms"]),
-                                   "traffic": traffic[1]}}}
+                                    "traffic": traffic[0],
+                                    "executed_issue": issue("k_shell", mean_ph["shell_ms"])},
+                        walker: {"ms": mean_ph["tail_ms"], "cells": tail_cells,
+                                 "achieved": tflops(tail_cells, mean_ph["tail_ms"]),
+                                 "traffic": traffic[1],
+                                 "executed_issue": issue(walker, mean_ph["tail_ms"])}}}
         # the derived peak, confirmed by a measured FMA loop (outside the timed
         # region) and restated at the SM clock seen under load
         probe = g.gamma_measure_fp32_peak()
@@ -1132,6 +1228,125 @@ def experiment_mlp_infer(args):
         g.gamma_model_destroy(m)
 
 
+def experiment_parity(args):
+    """Error of the GPU maps against the FP64 oracle for every workload
+    configuration, with the FP64 redo of near-singular cells on (default) and
+    off: max |dgamma|, mean |dgamma| and pass/fail mismatches outside the tie
+    band, on the full grid where the oracle finishes in seconds and on a
+    stated sample (random evaluated voxels plus the largest gammas) else."""
+    import torch
+    import oracle
+    import paper_1012_1900_gb300 as g
+    oracle.build()
+    f32 = lambda x: float(np.float32(x))
+    rng = np.random.default_rng(11)
+
+    def gpu_maps(p):
+        nd = p.ref.ndim
+        r = torch.from_numpy(p.ref).cuda()
+        e = torch.from_numpy(p.eval).cuda()
+        o = torch.empty_like(r)
+        c = p.criteria
+        h = g.gamma_create(r, e, nd, p.ref.shape if nd == 3 else (1,) + p.ref.shape,
+                           p.spacing if nd == 3 else (1.0,) + p.spacing,
+                           g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm))
+        try:
+            g.gamma_run(h, o)
+            g.gamma_pass_rate(h)
+            st = g.gamma_get_stats(h)
+            a = o.cpu().numpy().astype(np.float64)
+            g.gamma_set_option(h, "fp64_tau_exp10", 0)
+            g.gamma_run(h, o)
+            g.gamma_pass_rate(h)
+            b = o.cpu().numpy().astype(np.float64)
+        finally:
+            g.gamma_destroy(h)
+        return a, b, st
+
+    def compare(p, a, b, st, sample):
+        c = p.criteria
+        flat = a.ravel()
+        ok = np.nonzero(np.isfinite(flat))[0]
+        if sample and ok.size > sample:
+            top = ok[np.argsort(-flat[ok])[:200]]
+            idx = np.unique(np.concatenate([top, rng.choice(ok, sample, replace=False)]))
+            what = f"{idx.size} of {ok.size} evaluated voxels (random + the 200 largest gammas)"
+        else:
+            idx = None
+            what = f"full grid ({flat.size} voxels, {ok.size} evaluated)"
+        want = oracle.gamma(p.ref, p.eval, p.spacing, f32(c.dd_frac), f32(c.dta_mm), local=c.local,
+                            cutoff_frac=f32(c.cutoff_frac), dose_norm=f32(c.dose_norm),
+                            idx=idx).ravel()
+        row = {"pair": p.name, "criteria": c.label, "voxels": p.nvox, "oracle_sample": what,
+               "fp64_cells": st["fp64_cells"]}
+        for key, m in (("default", a), ("fp32_only", b)):
+            got = m.ravel() if idx is None else m.ravel()[idx]
+            fin = np.isfinite(want)
+            err = np.abs(got[fin] - want[fin])
+            band = np.abs(want[fin] - 1.0) < TIE_BAND
+            row[key] = {"max_abs_dgamma": float(err.max()) if err.size else 0.0,
+                        "mean_abs_dgamma": float(err.mean()) if err.size else 0.0,
+                        "masks_identical": bool(np.array_equal(np.isnan(got), np.isnan(want))),
+                        "pass_fail_mismatches": int(np.count_nonzero(
+                            ((got[fin] <= 1.0) != (want[fin] <= 1.0)) & ~band))}
+        return row
+
+    res = {"experiment": "parity", "tolerance": 1e-4, "tie_band": TIE_BAND, "configs": {}}
+    for name, pairs, sample in (
+            ("c1 plane_128 3%/3mm", [synth.workload("plane_128")], 0),
+            ("c2 imrt_160 3%/3mm", [synth.workload("imrt_160")], 0),
+            ("c2 imrt_160 2%/2mm", [synth.workload("imrt_160_2mm2pct")], 0),
+            ("c3 imrt_320 1%/1mm local", [synth.workload("imrt_320_local")], 20000),
+            ("c3 imrt_320 3%/3mm global", [synth.workload("imrt_320_global")], 20000),
+            ("c4 batch (64 pairs)", None, 3000),
+            ("c5 held-out 200x200x150 2%/2mm", None, 5000)):
+        if pairs is None and name.startswith("c4"):
+            pairs = (synth.batch_pair(i) for i in range(64))
+        elif pairs is None:
+            pairs = (synth.test_pair(i) for i in range(args.test_pairs if args.test_pairs < 20 else 4))
+        rows = []
+        for p in pairs:
+            a, b, st = gpu_maps(p)
+            rows.append(compare(p, a, b, st, sample))
+        res["configs"][name] = {
+            "pairs": len(rows),
+            "max_abs_dgamma": max(r["default"]["max_abs_dgamma"] for r in rows),
+            "fp32_only_max_abs_dgamma": max(r["fp32_only"]["max_abs_dgamma"] for r in rows),
+            "pass_fail_mismatches": sum(r["default"]["pass_fail_mismatches"] for r in rows),
+            "fp32_only_pass_fail_mismatches": sum(r["fp32_only"]["pass_fail_mismatches"] for r in rows),
+            "masks_identical": all(r["default"]["masks_identical"] for r in rows),
+            "fp64_cells": sum(r["fp64_cells"] for r in rows),
+            "rows": rows}
+        print(json.dumps({name: {k: v for k, v in res["configs"][name].items() if k != "rows"}}),
+              flush=True)
+    print(json.dumps(res), flush=True)
+
+
+def experiment_train_step(args):
+    """One training step of the proposal network (forward, Huber loss,
+    backward, Adam) on 8,192 random feature rows, median of timed steps."""
+    import torch
+    import paper_1012_1900_gb300 as g
+    M = 8192
+    m = g.gamma_model_create(3)
+    try:
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        X = (torch.randn(M, 384, device="cuda", generator=gen) * 1.5).to(torch.bfloat16)
+        X[:, 375:] = 0
+        T = torch.randn(M, 4, device="cuda", generator=gen)
+        for _ in range(max(args.warmup, 3)):
+            g.gamma_model_train_step(m, X, T, 1e-4, want_loss=False)
+        torch.cuda.synchronize()
+        ms = _event_ms(torch, torch.cuda.current_stream(),
+                       lambda: g.gamma_model_train_step(m, X, T, 1e-4, want_loss=False),
+                       max(args.steps, 10))
+        flop = 2.0 * M * (384 * 128 + 128 * 128 + 128 * 8) * 3
+        print(json.dumps({"experiment": "train_step", "rows": M, "ms": ms,
+                          "gemm_tflops_equivalent": flop / (ms / 1e3) / 1e12}), flush=True)
+    finally:
+        g.gamma_model_destroy(m)
+
+
 def experiment_grids(args):
     """Reference and evaluation on different grids (Section 3.5's doses at
     another resolution): the imrt_160 reference (2.5 mm) against the same
@@ -1178,8 +1393,18 @@ def experiment_grids(args):
 
 def main():
     args = parse()
+    if args.record_counters:
+        out = record_counters(args.record_counters, args.workload, args.capture_note)
+        print(json.dumps(out, indent=1))
+        return
     if args.experiment == "grids":
         experiment_grids(args)
+        return
+    if args.experiment == "train_step":
+        experiment_train_step(args)
+        return
+    if args.experiment == "parity":
+        experiment_parity(args)
         return
     if args.experiment == "mlp_infer":
         experiment_mlp_infer(args)

@@ -198,13 +198,15 @@ int gamma_get_stats(gamma_handle h, gamma_stats *out);
 int gamma_get_timings(gamma_handle h, gamma_timings *out);
 
 /* Tuning and diagnostic options (take effect at the next run):
- *  "walk"             1 (default): the queued voxels are walked tile by tile:
- *                     each block stages the evaluation doses around one
- *                     256-voxel tile in shared memory (one TMA copy) and walks
- *                     the table for that tile's queued voxels, the lanes per
- *                     voxel chosen per tile; 0: voxel by voxel from a queue
- *                     ordered by cost, "lanes_per_voxel" lanes each (batch
- *                     handles and gamma_run_noalloc always walk this way)
+ *  "walk"             0 (default): the queued voxels are walked voxel by
+ *                     voxel from a queue ordered by cost, "lanes_per_voxel"
+ *                     lanes each (batch handles and gamma_run_noalloc always
+ *                     walk this way); 1: tile by tile: each block stages the
+ *                     evaluation doses around one 256-voxel tile in shared
+ *                     memory (one TMA copy) and walks the table for that
+ *                     tile's queued voxels, the lanes per voxel chosen per
+ *                     tile (same results; slower on the benchmark workloads,
+ *                     where a tile waits for its most expensive voxel)
  *  "lanes_per_voxel"  2, 4, 8, 16 or 32 lanes search one queued voxel together
  *                     (the voxel-by-voxel walk)
  *  "table_cap"        maximum cell-table length (rebuilds the table)

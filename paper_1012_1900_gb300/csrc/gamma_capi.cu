@@ -74,6 +74,10 @@ struct GridState {
 // Evaluation-dose z slabs of a host-buffer run: the shell starts on a slab
 // while the next ones are still being copied.
 constexpr int kPipeChunks = gk::kShellSlots;
+// Queued voxels one run (or one batch group) seeds at most with an attached
+// model: the network's row buffers hold this many rows (784 bytes each);
+// further voxels past the cost gate are walked without a seed.
+constexpr unsigned kSeedRowsMax = 1u << 19;
 
 struct gamma_ctx {
     BatchState* batch = nullptr;      // non-null for batch handles
@@ -106,7 +110,7 @@ struct gamma_ctx {
     unsigned* tile_list = nullptr;
     unsigned char* tile_bkt = nullptr;
     unsigned* tile_sorted = nullptr;
-    int walk = 1;                     // 1: tile-staged walk (k_walk); 0: voxel queue walk (k_tail)
+    int walk = 0;                     // 1: tile-staged walk (k_walk); 0: voxel queue walk (k_tail)
     // options
     int lanes = gk::kDefaultLanesPerVoxel;
     double tau = 1e-6;
@@ -120,8 +124,10 @@ struct gamma_ctx {
     int face_eval = 0;       // design 1 / 2: 0 closed-form faces, 1 Ju's recursion
     gk::PaperScratch paper;
     gamma_model model = nullptr;      // attached proposal network (may be null)
-    float* gnorm = nullptr;           // with a model: gradient magnitudes of both doses (2 x nvox)
     unsigned* seed_list = nullptr;    // with a model: queue items past the cost gate (tail_cap)
+    __nv_bfloat16* seed_X = nullptr;  // with a model: network input rows (seed_cap x 384)
+    float* seed_Y = nullptr;          // with a model: network output rows (seed_cap x 4)
+    unsigned seed_cap = 0;
     int seed_min_bucket = 13;         // cost gate of the seeding pass (bucket of >= 64 cells)
     bool own_model = false;
     // per-phase events: 0 start, 1 after h2d, 2 after prepare, 3 after shell,
@@ -288,6 +294,10 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.tail_sorted = h->tail_sorted;
     P.sort_tail = h->sort_tail;
     P.shell_minblocks = h->shell_minblocks;
+    P.seed_list = h->seed_list;
+    P.seed_X = h->seed_X;
+    P.seed_Y = h->seed_Y;
+    P.seed_cap = h->seed_cap;
     if (h->walk && h->tile_mask) {
         P.tile_mask = h->tile_mask;
         P.tile_list = h->tile_list;
@@ -329,8 +339,9 @@ void free_ctx(gamma_ctx* h)
     cudaFree(h->tile_list);
     cudaFree(h->tile_bkt);
     cudaFree(h->tile_sorted);
-    cudaFree(h->gnorm);
     cudaFree(h->seed_list);
+    cudaFree(h->seed_X);
+    cudaFree(h->seed_Y);
     cudaFree(h->own_ref);
     cudaFree(h->own_ev);
     cudaFree(h->own_out);
@@ -375,6 +386,9 @@ struct BatchState {
         unsigned* head = nullptr;          // walk, shell tiles, seed rows, seeding work
         unsigned* seed_item = nullptr;     // with a model: (pair, item) rows past the gate
         unsigned short* seed_pair = nullptr;
+        __nv_bfloat16* seed_X = nullptr;   // ... their network inputs and outputs
+        float* seed_Y = nullptr;
+        unsigned seed_cap = 0;
         gk::BatchDesc* desc = nullptr;
         gk::BatchGroup host{};
     } grp[2];
@@ -398,6 +412,8 @@ void free_group(BatchState::Group& g)
     cudaFree(g.head);
     cudaFree(g.seed_item);
     cudaFree(g.seed_pair);
+    cudaFree(g.seed_X);
+    cudaFree(g.seed_Y);
     cudaFree(g.desc);
     g = BatchState::Group{};
 }
@@ -466,8 +482,11 @@ int batch_upload(gamma_ctx* h)
         if (h->model && !G.seed_item) {
             size_t cap = 0;
             for (int k = 0; k < np; ++k) cap += b->pairs[mem[k]]->tail_cap;
-            CK(cudaMalloc(&G.seed_item, sizeof(unsigned) * std::max<size_t>(cap, 1)));
-            CK(cudaMalloc(&G.seed_pair, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
+            G.seed_cap = (unsigned)std::max<size_t>(1, std::min<size_t>(cap, kSeedRowsMax));
+            CK(cudaMalloc(&G.seed_item, sizeof(unsigned) * G.seed_cap));
+            CK(cudaMalloc(&G.seed_pair, sizeof(unsigned short) * G.seed_cap));
+            CK(cudaMalloc(&G.seed_X, sizeof(__nv_bfloat16) * gk::kInPad * (size_t)G.seed_cap));
+            CK(cudaMalloc(&G.seed_Y, sizeof(float) * gk::kOut * (size_t)G.seed_cap));
         }
         CK(cudaMemcpy(G.probs, probs.data(), sizeof(gk::Problem) * np, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(G.maps, maps.data(), sizeof(CUtensorMap) * np, cudaMemcpyHostToDevice));
@@ -489,6 +508,9 @@ int batch_upload(gamma_ctx* h)
             d.seed_pair = G.seed_pair;
             d.seed_count = G.head + 2;
             d.seed_head = G.head + 3;
+            d.seed_X = G.seed_X;
+            d.seed_Y = G.seed_Y;
+            d.seed_cap = G.seed_cap;
         }
         CK(cudaMemcpy(G.desc, &d, sizeof(d), cudaMemcpyHostToDevice));
         G.host.ndim = gi == 0 ? 2 : 3;
@@ -497,6 +519,11 @@ int batch_upload(gamma_ctx* h)
         G.host.total_tiles = tstart[np];
         G.host.desc = G.desc;
         G.host.shell_next = G.head + 1;
+        G.host.seed_X = h->model ? G.seed_X : nullptr;
+        G.host.seed_Y = h->model ? G.seed_Y : nullptr;
+        G.host.seed_cap = h->model ? G.seed_cap : 0u;
+        G.host.seed_count = G.head + 2;
+        G.host.flags = &b->ctrs[mem[0]].flags;
     }
     return GAMMA_OK;
 }
@@ -518,10 +545,7 @@ int batch_enqueue(gamma_ctx* h, cudaStream_t s)
         // learned seeding of every pair's queued voxels past the cost gate
         gk::MlpWeights W;
         gk::model_weights(h->model, &W);
-        for (auto& G : b->grp) {
-            CK(gk::launch_batch_seed_select(G.host, h->seed_min_bucket, s));
-            CK(gk::launch_batch_learned(G.host, W, s));
-        }
+        for (auto& G : b->grp) CK(gk::launch_batch_seeding(G.host, W, h->seed_min_bucket, s));
     }
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     for (auto& G : b->grp) CK(gk::launch_batch_order(G.host, s));
@@ -844,13 +868,7 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
     if (h->model) {
         gk::MlpWeights W;
         gk::model_weights(h->model, &W);
-        Problem Q = P;
-        Q.gnorm_e = h->gnorm;
-        Q.gnorm_r = h->gnorm + h->nvox;
-        Q.seed_list = h->seed_list;
-        CK(gk::launch_grad_norms(Q, h->gnorm, h->gnorm + h->nvox, s));
-        CK(gk::launch_seed_select(Q, h->seed_min_bucket, s));
-        CK(gk::launch_learned(Q, W, s));
+        CK(gk::launch_seeding(P, W, h->seed_min_bucket, s));
     }
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     if (int rc = enqueue_walk(h, P, s, tm)) return rc;
@@ -1450,13 +1468,8 @@ int gamma_features(gamma_handle h, const uint32_t* voxels_dev, int64_t n, void* 
     if (n == 0) return GAMMA_OK;
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
-    Problem P = make_problem(h, nullptr);
+    const Problem P = make_problem(h, nullptr);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (h->gnorm) {                  // a model is attached: the gradient volumes the seeding pass reads
-        P.gnorm_e = h->gnorm;
-        P.gnorm_r = h->gnorm + h->nvox;
-        CK(gk::launch_grad_norms(P, h->gnorm, h->gnorm + h->nvox, s));
-    }
     CK(gk::launch_features(P, voxels_dev, n, (__nv_bfloat16*)X_bf16_dev, s));
     return GAMMA_OK;
 }
@@ -1479,8 +1492,12 @@ static int seed_buffers(gamma_handle h)
 {
     DeviceGuard dg(h->device);
     if (!dg.ok) return GAMMA_ERR_CUDA;
-    if (!h->gnorm) CK(cudaMalloc(&h->gnorm, sizeof(float) * 2 * (size_t)h->nvox));
     if (!h->seed_list) CK(cudaMalloc(&h->seed_list, sizeof(unsigned) * (size_t)h->tail_cap));
+    if (!h->seed_X) {
+        h->seed_cap = std::min<unsigned>(h->tail_cap, kSeedRowsMax);
+        CK(cudaMalloc(&h->seed_X, sizeof(__nv_bfloat16) * gk::kInPad * (size_t)h->seed_cap));
+        CK(cudaMalloc(&h->seed_Y, sizeof(float) * gk::kOut * (size_t)h->seed_cap));
+    }
     return GAMMA_OK;
 }
 

@@ -126,12 +126,12 @@ struct Problem {
     // squared spatial distance from the voxel to the faces of key-0 cell S
     // (lower corner at -S) that do not contain it, rounded down; +inf for S = 0
     float key0_far2[8];
-    // learned seeding: gradient-magnitude volumes of the evaluation and the
-    // reference dose (null: computed where needed), and the queue items past
-    // the cost gate
-    const float* gnorm_e;
-    const float* gnorm_r;
+    // learned seeding: the queue items past the cost gate, and the row
+    // buffers of the network (features, outputs) for up to seed_cap of them
     unsigned* seed_list;
+    __nv_bfloat16* seed_X;         // [seed_cap][kInPad]
+    float* seed_Y;                 // [seed_cap][kOut]
+    unsigned seed_cap;
     // tile-staged walk (null: the queue is walked voxel by voxel, k_tail):
     // per shell tile one bit per voxel of the tile that is queued (8 words,
     // word = warp of the tile, bit = lane), the tiles with any queued voxel
@@ -170,10 +170,13 @@ struct BatchDesc {
     // learned seeding (null without a model): queue items of every pair past
     // the cost gate, as (pair, item) rows, their count and the work counter of
     // the seeding pass (both zeroed by the group's prepare)
-    unsigned* seed_item;           // [sum of tail_cap]
-    unsigned short* seed_pair;     // [sum of tail_cap]
+    unsigned* seed_item;           // [seed_cap]
+    unsigned short* seed_pair;     // [seed_cap]
     unsigned* seed_count;
     unsigned* seed_head;
+    __nv_bfloat16* seed_X;         // [seed_cap][kInPad] network inputs
+    float* seed_Y;                 // [seed_cap][kOut] network outputs
+    unsigned seed_cap;             // rows past it go unseeded
 };
 
 // Host view of one batched launch group.
@@ -184,6 +187,13 @@ struct BatchGroup {
     int total_tiles;               // shell tiles over all pairs
     const BatchDesc* desc;         // device copy of the descriptor
     unsigned* shell_next;          // device: the descriptor's shell tile counter
+    // learned seeding (seed_cap 0: no model): the descriptor's row buffers and
+    // row count, and where a timed-out wait of the network is reported
+    __nv_bfloat16* seed_X;
+    float* seed_Y;
+    unsigned seed_cap;
+    unsigned* seed_count;
+    unsigned* flags;
 };
 
 // Launchers (gamma_kernels.cu).  All are stream-ordered and allocate nothing.
@@ -225,12 +235,13 @@ int shell_tiles(const Problem& P);
 
 // Learned proposal (gamma_learned.cu).
 bool model_weights(const gamma_model_s* m, MlpWeights* w);
-cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s);
-// Gradient magnitudes of both doses at every grid point (the feature
-// channels 1 and 2 before their per-voxel scale), into ge and gr.
-cudaError_t launch_grad_norms(const Problem& P, float* ge, float* gr, cudaStream_t s);
-// Queue items whose cost bucket is at least min_bucket, into P.seed_list.
-cudaError_t launch_seed_select(const Problem& P, int min_bucket, cudaStream_t s);
+// Seeding of one pair's queued voxels: the items whose cost bucket is at
+// least min_bucket (into P.seed_list), their features (P.seed_X), the network
+// on the tensor cores (P.seed_Y) and the exact seeds from the proposals.
+cudaError_t launch_seeding(const Problem& P, const MlpWeights& W, int min_bucket, cudaStream_t s);
+// Network outputs for M feature rows (row-major [M][384] BF16, 16-byte aligned).
+cudaError_t launch_mlp_infer(const MlpWeights& W, const __nv_bfloat16* X, long long M, float* Y,
+                             unsigned* flags, cudaStream_t s);
 
 // Reference and evaluation doses on different grids (gamma_grids.cu).
 // Positions and spacings are in DTA units, axes (x, y, z).
@@ -267,8 +278,6 @@ struct PaperScratch {
 size_t paper_sort_bytes(long long nvox);
 cudaError_t launch_paper(const Problem& P, const PaperScratch& w, bool sorted, bool ju,
                          cudaEvent_t after_sort, cudaStream_t s);
-cudaError_t launch_mlp_infer(const MlpWeights& W, const __nv_bfloat16* X, long long M, float* Y,
-                             unsigned* flags, cudaStream_t s);
 cudaError_t launch_features(const Problem& P, const unsigned* vox, long long n, __nv_bfloat16* X,
                             cudaStream_t s);
 cudaError_t launch_labels(const Problem& P, const float* gmap, const unsigned* vox, long long n,
@@ -280,10 +289,30 @@ cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStr
 cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s);
 cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, int tail_minblocks,
                               cudaStream_t s);
+// Tensor map of a row-major bf16 matrix (inner elements x rows, row stride in
+// bytes) with boxes of box_inner x box_rows elements; false when the driver's
+// encoder is missing or the alignment rules fail.
+bool encode_bf16_2d(CUtensorMap* map, const void* base, unsigned long long inner,
+                    unsigned long long rows, unsigned long long row_stride_bytes,
+                    unsigned box_inner, unsigned box_rows);
+// C (+)= A B^T on the tensor cores (gamma_gemm_tc.cu): A [M][K] and B [N][K]
+// bf16 with K contiguous (row strides lda, ldb: multiples of 8 elements, bases
+// 16-byte aligned), C fp32 [M][ldc].  With splits > 1 the K range is split over
+// that many blocks per tile, which add into C (it must hold the initial value,
+// normally zero); else C is overwritten.  flags receives kFlagTimeout if a
+// bounded wait gave up.
+cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long M, long long lda, const __nv_bfloat16* B,
+                           int N, long long ldb, long long K, float* C, int ldc, int splits,
+                           unsigned* flags, cudaStream_t s);
+// dst [cols][ldd] = transpose of src [rows][cols] (row stride lds); the
+// columns rows .. ldd - 1 of dst are zeroed.
+cudaError_t launch_transpose_bf16(const __nv_bfloat16* src, long long rows, int cols, long long lds,
+                                  __nv_bfloat16* dst, long long ldd, cudaStream_t s);
+
 // Learned seeding of a batch group (gamma_learned.cu): the queue items of every
-// pair whose cost bucket is at least min_bucket, then the fused features,
-// network and exact seeds over all of them in one persistent launch.
-cudaError_t launch_batch_seed_select(const BatchGroup& g, int min_bucket, cudaStream_t s);
-cudaError_t launch_batch_learned(const BatchGroup& g, const MlpWeights& W, cudaStream_t s);
+// pair whose cost bucket is at least min_bucket as (pair, item) rows, then the
+// features, network and exact seeds of all of them, one launch each.
+cudaError_t launch_batch_seeding(const BatchGroup& g, const MlpWeights& W, int min_bucket,
+                                 cudaStream_t s);
 
 }  // namespace gk

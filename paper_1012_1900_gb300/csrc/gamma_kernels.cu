@@ -1095,14 +1095,14 @@ void key0_far(const double hn_in[3], int nd, double far[8])
     }
 }
 
-// Tensor map of the evaluation dose with a tile box of (bx, by, bz) floats;
-// false when TMA cannot be used for it.
-static bool encode_box_map(const Problem& P, CUtensorMap* map, int bx, int by, int bz)
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder (looked up once), or null.
+static EncodeFn tensor_map_encoder()
 {
-    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     static EncodeFn encode = nullptr;
     static bool looked_up = false;
     if (!looked_up) {
@@ -1114,6 +1114,30 @@ static bool encode_box_map(const Problem& P, CUtensorMap* map, int bx, int by, i
             q == cudaDriverEntryPointSuccess)
             encode = (EncodeFn)fn;
     }
+    return encode;
+}
+
+bool encode_bf16_2d(CUtensorMap* map, const void* base, unsigned long long inner,
+                    unsigned long long rows, unsigned long long row_stride_bytes,
+                    unsigned box_inner, unsigned box_rows)
+{
+    const EncodeFn encode = tensor_map_encoder();
+    if (!encode || ((uintptr_t)base & 15u) || (row_stride_bytes & 15u) || (box_inner * 2) % 16) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_stride_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    std::memset(map, 0, sizeof(*map));
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                  es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor map of the evaluation dose with a tile box of (bx, by, bz) floats;
+// false when TMA cannot be used for it.
+static bool encode_box_map(const Problem& P, CUtensorMap* map, int bx, int by, int bz)
+{
+    const EncodeFn encode = tensor_map_encoder();
     if (!encode) return false;
     if (((uintptr_t)P.ev & 15u) != 0 || (P.nx % 4) != 0) return false;   // TMA alignment rules
     if (P.ndim == 3) {

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/gamma.h"
+#include "gamma_cell.cuh"
 #include "gamma_internal.h"
 #include "gamma_mlp.cuh"
 #include "gamma_tc.cuh"
@@ -73,26 +74,7 @@ __device__ __forceinline__ float voxel_feature(const Problem& P, int x, int y, i
         return 0.f;
     const long long p = ((long long)pz * P.ny + py) * P.nx + px;
     if (ch == 0) return fminf(fmaxf((__ldg(P.ev + p) - dr) * inv, -16.f), 16.f);
-    const float* pre = ch == 1 ? P.gnorm_e : P.gnorm_r;
-    const float gmag = pre ? __ldg(pre + p) : grad_norm<N>(ch == 1 ? P.ev : P.ref, P, px, py, pz, p);
-    return fminf(gmag * inv, 32.f);
-}
-
-// The gradient magnitudes of both doses at every grid point, computed once
-// per run for the seeding pass (the same function the features evaluate
-// point by point, so the features do not change).
-template <int N>
-__global__ void __launch_bounds__(256) k_grad_norms(const __grid_constant__ Problem P,
-                                                    float* __restrict__ ge, float* __restrict__ gr)
-{
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P.nvox;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(p % P.nx);
-        const long long r1 = p / P.nx;
-        const int y = (int)(r1 % P.ny), z = (int)(r1 / P.ny);
-        ge[p] = grad_norm<N>(P.ev, P, x, y, z, p);
-        gr[p] = grad_norm<N>(P.ref, P, x, y, z, p);
-    }
+    return fminf(grad_norm<N>(ch == 1 ? P.ev : P.ref, P, px, py, pz, p) * inv, 32.f);
 }
 
 // Queue items past the cost gate (bucket >= min_bucket), into P.seed_list.
@@ -112,9 +94,9 @@ __global__ void __launch_bounds__(256) k_seed_select(const __grid_constant__ Pro
     }
 }
 
-// Features f0 .. f0 + 7 of reference voxel v (f0 a multiple of 8), the same
-// values voxel_feature gives one by one, with their eight loads issued before
-// any is used.  v = 0xffffffff: zeros.
+// Features f0 .. f0 + 7 of reference voxel v (f0 a multiple of 8), computed
+// point by point (their loads independent, so the compiler keeps them in
+// flight together).  v = 0xffffffff: zeros.
 template <int N>
 __device__ __forceinline__ void features8(const Problem& P, unsigned v, float dr, float inv, int f0,
                                           float (&val)[8])
@@ -122,44 +104,11 @@ __device__ __forceinline__ void features8(const Problem& P, unsigned v, float dr
 #pragma unroll
     for (int u = 0; u < 8; ++u) val[u] = 0.f;
     if (v == 0xffffffffu || f0 >= kIn) return;
-    if (!P.gnorm_e || !P.gnorm_r) {
-        const int x = (int)(v % (unsigned)P.nx);
-        const unsigned r1 = v / (unsigned)P.nx;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            val[u] = voxel_feature<N>(P, x, (int)(r1 % (unsigned)P.ny), (int)(r1 / (unsigned)P.ny), dr,
-                                      inv, f0 + u);
-        return;
-    }
     const int x = (int)(v % (unsigned)P.nx);
     const unsigned r1 = v / (unsigned)P.nx;
     const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
-    int ch = f0 / 125;
-    const int pi = f0 % 125;
-    int ox = pi % 5 - 2, oy = (pi / 5) % 5 - 2, oz = pi / 25 - 2;
-    float raw[8];
-    int chs[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int px = x + ox, py = y + oy, pz = N == 3 ? z + oz : 0;
-        const bool ok = f0 + u < kIn && (N == 3 || oz == -2) && (unsigned)px < (unsigned)P.nx &&
-                        (unsigned)py < (unsigned)P.ny && (N == 2 || (unsigned)pz < (unsigned)P.nz);
-        const float* src = ch == 0 ? P.ev : (ch == 1 ? P.gnorm_e : P.gnorm_r);
-        raw[u] = ok ? __ldg(src + ((long long)pz * P.ny + py) * P.nx + px) : __int_as_float(0x7fc00000);
-        chs[u] = ch;
-        if (++ox > 2) {                            // next patch point (x fastest), then channel
-            ox = -2;
-            if (++oy > 2) {
-                oy = -2;
-                if (++oz > 2) { oz = -2; ++ch; }
-            }
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        if (isnan(raw[u])) continue;               // outside the grid or past the last feature: 0
-        val[u] = chs[u] == 0 ? fminf(fmaxf((raw[u] - dr) * inv, -16.f), 16.f) : fminf(raw[u] * inv, 32.f);
-    }
+    for (int u = 0; u < 8; ++u) val[u] = voxel_feature<N>(P, x, y, z, dr, inv, f0 + u);
 }
 
 template <int N>
@@ -280,70 +229,8 @@ __global__ void __launch_bounds__(128) k_labels(const __grid_constant__ Problem 
 }
 
 // --------------------------------------------------------------------------
-// Generic BF16 GEMM for training (mma.sync m16n8k16, FP32 accumulation)
-//   C[m][n] (+)= sum_k A'(m, k) B'(n, k)
-//   A'(m, k) = TA ? A[k * lda + m] : A[m * lda + k]
-//   B'(n, k) = TB ? B[k * ldb + n] : B[n * ldb + k]
-// 64 x 64 tiles, 4 warps of 16 rows; split-K over gridDim.z with ATOMIC.
+// Training passes around the tensor-core GEMMs (gamma_gemm_tc.cu)
 // --------------------------------------------------------------------------
-
-template <bool TA, bool TB, bool ATOMIC>
-__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16* __restrict__ A,
-                                              int lda, const bf16* __restrict__ B, int ldb,
-                                              float* __restrict__ C, int ldc)
-{
-    constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;
-    __shared__ __align__(16) bf16 As[BM * LDS];
-    __shared__ __align__(16) bf16 Bs[BN * LDS];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kslice = (K + gridDim.z - 1) / gridDim.z;
-    const int kbeg = blockIdx.z * kslice, kend = min(K, kbeg + kslice);
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const bf16 zero = __float2bfloat16(0.f);
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
-            int r, c;
-            if (TA) { c = e / BM; r = e % BM; } else { r = e / BK; c = e % BK; }
-            const int m = m0 + r, k = k0 + c;
-            As[r * LDS + c] = (m < M && k < kend) ? (TA ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : zero;
-        }
-        for (int e = threadIdx.x; e < BN * BK; e += blockDim.x) {
-            int r, c;
-            if (TB) { c = e / BN; r = e % BN; } else { r = e / BK; c = e % BK; }
-            const int nn = n0 + r, k = k0 + c;
-            Bs[r * LDS + c] = (nn < N && k < kend) ? (TB ? B[(long long)k * ldb + nn] : B[(long long)nn * ldb + k]) : zero;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t a[4];
-            load_a_frag(a, As + warp * 16 * LDS + ks, LDS, lane);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                uint32_t b[2];
-                load_b_frag(b, Bs + j * 8 * LDS + ks, LDS, lane);
-                mma_bf16_16816(acc[j], a, b);
-            }
-        }
-        __syncthreads();
-    }
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int m = m0 + warp * 16 + g + (h >= 2 ? 8 : 0);
-            const int nn = n0 + j * 8 + 2 * t + (h & 1);
-            if (m < M && nn < N) {
-                float* dst = C + (long long)m * ldc + nn;
-                if (ATOMIC) atomicAdd(dst, acc[j][h]);
-                else *dst = acc[j][h];
-            }
-        }
-}
 
 // Z (M x N, fp32) += bias; H = bf16(relu(Z)) (or bf16(Z) without relu).
 __global__ void k_bias_act(long long M, int N, float* __restrict__ Z, const float* __restrict__ bias,
@@ -488,41 +375,41 @@ __global__ void k_cast_weights(const float* __restrict__ W1, const float* __rest
 }
 
 // --------------------------------------------------------------------------
-// Fused inference on the fifth-generation tensor cores (tcgen05)
+// Network inference on the fifth-generation tensor cores (tcgen05)
 //
 // One block of 256 threads per SM keeps the three weight matrices resident in
 // shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16
 // bytes per core matrix; core matrices adjacent in K are LBO = rows/8 * 128
-// bytes apart, adjacent 8-row groups SBO = 128 bytes apart) and runs 128 rows
-// (voxels) at a time: layer 1 streams the 384 input features in six 64-wide
-// chunks through two buffers (one mbarrier each, so that every commit is
-// waited for exactly once and in order), accumulating X W1^T in TMEM columns
-// 0..127; layer 2 puts H1 W2^T in columns 128..255; layer 3 (N padded to 16)
-// reuses columns 0..15.  One thread issues the MMAs; the epilogues read TMEM
-// with tcgen05.ld (warp w reads lanes 32 (w % 4) .. +31), add the bias, apply
-// the ReLU and write the next layer's BF16 operand.  Every wait is bounded.
+// bytes apart, adjacent 8-row groups SBO = 128 bytes apart) and runs 128
+// feature rows at a time.  The rows arrive by TMA: each 64-column chunk is
+// eight boxes of 8 columns x 128 rows, which land in exactly that layout,
+// through two stages (one "full" and one "empty" mbarrier each).  One thread
+// issues the copies and the MMAs: layer 1 accumulates X W1^T over the six
+// chunks in TMEM columns 0..127, and as soon as its last MMAs are committed
+// the first two chunks of the block's next tile are copied in, overlapping
+// the rest of this tile.  The epilogues read TMEM with tcgen05.ld (warp w
+// reads lanes 32 (w % 4) .. +31), add the bias, apply the ReLU and write the
+// next layer's BF16 operand: H1 W2^T goes to columns 128..255, then H2 (over
+// H1, whose MMAs have completed) times W3^T (N padded to 16) to columns
+// 0..15.  Every wait is bounded.
 // --------------------------------------------------------------------------
 
 constexpr int kRows = 128;                 // rows per tile (MMA M)
 constexpr int kKc = 64;                    // K chunk of the streamed features
+constexpr int kNChunks = kInPad / kKc;     // 6
 constexpr int kN3 = 16;                    // layer-3 N (4 outputs, padded)
 constexpr int kTmemCols = 256;
 
 struct __align__(1024) TcSmem {
-    bf16 W2[kH * kH];                      // rows 128, K 128 (core-matrix layout)
-    bf16 W1[kH * kInPad];                  // rows 128, K 384
-    bf16 H1[kRows * kH];
-    bf16 Xc[2][kRows * kKc];               // feature chunks; later H2 (rows 128, K 128)
+    bf16 W1[kH * kInPad];                  // rows 128, K 384 (core-matrix layout)
+    bf16 W2[kH * kH];                      // rows 128, K 128
+    bf16 H[kRows * kH];                    // H1, then H2 (rows 128, K 128)
+    bf16 Xc[2][kRows * kKc];               // feature chunks (TMA destinations)
     bf16 W3[kN3 * kH];                     // rows 16, K 128 (rows >= kOut zero)
     float b1[kH], b2[kH], b3[kOutPad];
-    float Y[kRows * kOut];
-    unsigned vox[kRows], item[kRows];
-    float dr[kRows], inv[kRows];
-    unsigned short pair[kRows];
-    unsigned hist[kNumBuckets];
-    unsigned base, nseed, nimp;
+    uint64_t xfull[2], xempty[2], mma;
     uint32_t tmem;
-    uint64_t bar[3];
+    int ok;
 };
 
 // Element index of (row, k) in a core-matrix tile with `rows` rows.
@@ -551,43 +438,9 @@ __device__ __forceinline__ void stage_weights(bf16* dst, const bf16* __restrict_
     }
 }
 
-// Weights, biases, barriers and the TMEM accumulators of one block.
-__device__ void tc_setup(TcSmem& S, const MlpWeights& W)
-{
-    stage_weights(S.W1, W.W1, kH, kH, kInPad);
-    stage_weights(S.W2, W.W2, kH, kH, kH);
-    stage_weights(S.W3, W.W3, kN3, kOutPad, kH);
-    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-        S.b1[i] = W.b1[i];
-        S.b2[i] = W.b2[i];
-    }
-    if (threadIdx.x < kOutPad) S.b3[threadIdx.x] = W.b3[threadIdx.x];
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < 3; ++b) mbar_init(&S.bar[b], 1);
-        mbar_fence_init();
-    }
-    if ((threadIdx.x >> 5) == 0) {
-        tmem_alloc(&S.tmem, kTmemCols);
-        tmem_relinquish();
-    }
-    fence_async_shared();
-    tc_fence_before_sync();
-    __syncthreads();
-    tc_fence_after_sync();
-}
-
-__device__ void tc_teardown(TcSmem& S)
-{
-    tc_fence_before_sync();
-    __syncthreads();
-    tc_fence_after_sync();
-    if ((threadIdx.x >> 5) == 0) tmem_dealloc(S.tmem, kTmemCols);
-}
-
 // D (TMEM, 128 lanes x 128 columns from column `col`) + bias, ReLU -> BF16
 // core-matrix tile `dst` (rows 128, K 128).
-__device__ __forceinline__ void epilogue_relu(const TcSmem& S, uint32_t col, const float* bias,
-                                              bf16* dst)
+__device__ __forceinline__ void epilogue_relu(uint32_t tmem, uint32_t col, const float* bias, bf16* dst)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;
@@ -595,7 +448,7 @@ __device__ __forceinline__ void epilogue_relu(const TcSmem& S, uint32_t col, con
     for (int j = 0; j < 4; ++j) {
         const int c0 = half * 64 + j * 16;
         float v[16];
-        tmem_ld16(S.tmem + ((uint32_t)(32 * q) << 16) + col + (uint32_t)c0, v);
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + col + (uint32_t)c0, v);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             uint32_t w[4];
@@ -612,136 +465,184 @@ __device__ __forceinline__ void epilogue_relu(const TcSmem& S, uint32_t col, con
     }
 }
 
-// One tile of 128 rows: fill(c, dst) writes feature chunk c (columns 64c ..
-// 64c + 63 of every row) into dst in core-matrix layout; on return S.Y holds
-// the 4 outputs of every row.  nc counts the waited phases of each barrier.
-// Returns false (block-uniformly) if a wait gave up.
-template <typename Fill>
-__device__ bool mlp_tile(TcSmem& S, uint32_t (&nc)[3], Fill fill)
+// The block's smem is the whole 227 KB (one block per SM; the TMEM allocation
+// can then never wait).
+constexpr size_t kTcSmemBytes = 232448;
+static_assert(sizeof(TcSmem) + 1024 <= kTcSmemBytes, "tensor-core tile does not fit in shared memory");
+
+// Network outputs Y [rows][4] of the feature rows X [rows][384] (bf16, read by
+// the tensor map xmap), for rows < (*count_dev if given, capped at M, else M).
+__global__ void __launch_bounds__(256, 1) k_mlp_rows(const __grid_constant__ MlpWeights W,
+                                                     const __grid_constant__ CUtensorMap xmap,
+                                                     long long M, const unsigned* count_dev,
+                                                     float* __restrict__ Y, unsigned* flags)
 {
-    constexpr uint32_t kId128 = idesc_bf16_f32(kRows, kH), kId16 = idesc_bf16_f32(kRows, kN3);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    TcSmem& S = *reinterpret_cast<TcSmem*>(base);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t tm = S.tmem;
-    bool ok = true;
-    // ---- layer 1: D1 = X W1^T over six chunks ----
-#pragma unroll 1
-    for (int c = 0; c < kInPad / kKc; ++c) {
-        const int b = c & 1;
-        if (c >= 2) {                                   // MMAs of chunk c - 2 have read the buffer
-            ok = mbar_wait_bounded(&S.bar[b], nc[b] & 1u) && ok;
-            ++nc[b];
+    const long long nrows = count_dev ? min((long long)*count_dev, M) : M;
+    const long long ntiles = (nrows + kRows - 1) / kRows;
+    if ((long long)blockIdx.x >= ntiles) return;                  // block-uniform
+    stage_weights(S.W1, W.W1, kH, kH, kInPad);
+    stage_weights(S.W2, W.W2, kH, kH, kH);
+    stage_weights(S.W3, W.W3, kN3, kOutPad, kH);
+    for (int i = tid; i < kH; i += blockDim.x) {
+        S.b1[i] = W.b1[i];
+        S.b2[i] = W.b2[i];
+    }
+    if (tid < kOutPad) S.b3[tid] = W.b3[tid];
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S.xfull[b], 1);
+            mbar_init(&S.xempty[b], 1);
         }
-        fill(c, S.Xc[b]);
+        mbar_init(&S.mma, 1);
+        mbar_fence_init();
+        S.ok = 1;
+    }
+    if (warp == 0) {
+        tmem_alloc(&S.tmem, kTmemCols);
+        tmem_relinquish();
+    }
+    fence_async_shared();
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tm = S.tmem;
+    constexpr uint32_t kId128 = idesc_bf16_f32(kRows, kH), kId16 = idesc_bf16_f32(kRows, kN3);
+    constexpr uint32_t kChunkBytes = kRows * kKc * 2;
+    // thread 0's bookkeeping: loads issued into / consumed from each stage
+    uint32_t loads[2] = {0u, 0u}, used[2] = {0u, 0u};
+    bool t0ok = true;
+    auto issue = [&](long long tile, int c) {           // thread 0: chunk c of a tile
+        const int s = c & 1;
+        if (loads[s] > 0 && t0ok)                        // the MMAs of the stage's last chunk
+            t0ok = mbar_wait_bounded(&S.xempty[s], (loads[s] - 1) & 1u);
+        if (!t0ok) return;
+        mbar_arrive_expect_tx(&S.xfull[s], kChunkBytes);
+#pragma unroll
+        for (int j = 0; j < kKc / 8; ++j)
+            tma_load_2d(&S.Xc[s][j * kRows * 8], &xmap, c * kKc + 8 * j, (int)(tile * kRows), &S.xfull[s]);
+        ++loads[s];
+    };
+    uint32_t nmma = 0;                                   // phases of S.mma waited so far
+    if (tid == 0) {
+        issue(blockIdx.x, 0);
+        issue(blockIdx.x, 1);
+    }
+    bool ok = true;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long row0 = t * kRows;
+        if (tid == 0) {
+            // ---- layer 1: D1 = X W1^T over six chunks ----
+            for (int c = 0; c < kNChunks && t0ok; ++c) {
+                const int s = c & 1;
+                if (c >= 2) issue(t, c);
+                if (!t0ok) break;
+                t0ok = mbar_wait_bounded(&S.xfull[s], used[s] & 1u);
+                if (!t0ok) break;
+                ++used[s];
+                tc_fence_after_sync();
+#pragma unroll
+                for (int kk = 0; kk < kKc; kk += 16)
+                    tc_mma_bf16(tm, tile_desc(S.Xc[s], kRows, kk), tile_desc(S.W1, kH, c * kKc + kk),
+                                kId128, (c | kk) != 0);
+                tc_commit(&S.xempty[s]);
+            }
+            tc_commit(&S.mma);
+            // the next tile's first chunks, while this tile finishes
+            if (t + gridDim.x < ntiles) {
+                issue(t + gridDim.x, 0);
+                issue(t + gridDim.x, 1);
+            }
+            if (!t0ok) S.ok = 0;
+        }
+        ok = mbar_wait_bounded(&S.mma, nmma & 1u) && ok;
+        ++nmma;
+        tc_fence_after_sync();
+        epilogue_relu(tm, 0u, S.b1, S.H);
         fence_async_shared();
+        tc_fence_before_sync();
         __syncthreads();
+        // ---- layer 2: D2 (columns 128..255) = H1 W2^T ----
         if (tid == 0) {
             tc_fence_after_sync();
 #pragma unroll
-            for (int kk = 0; kk < kKc; kk += 16)
-                tc_mma_bf16(tm, tile_desc(S.Xc[b], kRows, kk), tile_desc(S.W1, kH, c * kKc + kk),
-                            kId128, (c | kk) != 0);
-            tc_commit(&S.bar[b]);
+            for (int kk = 0; kk < kH; kk += 16)
+                tc_mma_bf16(tm + kH, tile_desc(S.H, kRows, kk), tile_desc(S.W2, kH, kk), kId128, kk != 0);
+            tc_commit(&S.mma);
+        }
+        ok = mbar_wait_bounded(&S.mma, nmma & 1u) && ok;
+        ++nmma;
+        tc_fence_after_sync();
+        __syncthreads();                                 // every read of H1 is done (MMAs completed)
+        epilogue_relu(tm, (uint32_t)kH, S.b2, S.H);      // H2 over H1
+        fence_async_shared();
+        tc_fence_before_sync();
+        __syncthreads();
+        // ---- layer 3: D3 (columns 0..15) = H2 W3^T ----
+        if (tid == 0) {
+            tc_fence_after_sync();
+#pragma unroll
+            for (int kk = 0; kk < kH; kk += 16)
+                tc_mma_bf16(tm, tile_desc(S.H, kRows, kk), tile_desc(S.W3, kN3, kk), kId16, kk != 0);
+            tc_commit(&S.mma);
+        }
+        ok = mbar_wait_bounded(&S.mma, nmma & 1u) && ok;
+        ++nmma;
+        tc_fence_after_sync();
+        if (warp < 4) {
+            float v[16];
+            tmem_ld16(tm + ((uint32_t)(32 * warp) << 16), v);
+            const long long row = row0 + 32 * warp + lane;
+            if (row < nrows)
+#pragma unroll
+                for (int o = 0; o < kOut; ++o) Y[row * kOut + o] = v[o] + S.b3[o];
+        }
+        tc_fence_before_sync();
+        const bool all_ok = __syncthreads_and(ok && S.ok) != 0;
+        tc_fence_after_sync();
+        if (!all_ok) {
+            ok = false;
+            break;
         }
     }
-    for (int b = 0; b < 2; ++b) {
-        ok = mbar_wait_bounded(&S.bar[b], nc[b] & 1u) && ok;
-        ++nc[b];
+    if (tid == 0 && (!ok || !t0ok)) {
+        atomicOr(flags, kFlagTimeout);
+        for (int b = 0; b < 2; ++b)                      // copies still in flight land first
+            if (loads[b] > used[b]) mbar_wait_bounded(&S.xfull[b], used[b] & 1u);
     }
-    tc_fence_after_sync();
-    epilogue_relu(S, 0u, S.b1, S.H1);
-    fence_async_shared();
     tc_fence_before_sync();
     __syncthreads();
-    // ---- layer 2: D2 (columns 128..255) = H1 W2^T ----
-    if (tid == 0) {
-        tc_fence_after_sync();
-#pragma unroll
-        for (int kk = 0; kk < kH; kk += 16)
-            tc_mma_bf16(tm + kH, tile_desc(S.H1, kRows, kk), tile_desc(S.W2, kH, kk), kId128, kk != 0);
-        tc_commit(&S.bar[2]);
-    }
-    ok = mbar_wait_bounded(&S.bar[2], nc[2] & 1u) && ok;
-    ++nc[2];
     tc_fence_after_sync();
-    bf16* H2 = &S.Xc[0][0];                             // both chunk buffers, 128 x 128
-    epilogue_relu(S, (uint32_t)kH, S.b2, H2);
-    fence_async_shared();
-    tc_fence_before_sync();
-    __syncthreads();
-    // ---- layer 3: D3 (columns 0..15) = H2 W3^T ----
-    if (tid == 0) {
-        tc_fence_after_sync();
-#pragma unroll
-        for (int kk = 0; kk < kH; kk += 16)
-            tc_mma_bf16(tm, tile_desc(H2, kRows, kk), tile_desc(S.W3, kN3, kk), kId16, kk != 0);
-        tc_commit(&S.bar[2]);
-    }
-    ok = mbar_wait_bounded(&S.bar[2], nc[2] & 1u) && ok;
-    ++nc[2];
-    tc_fence_after_sync();
-    if (warp < 4) {
-        float v[16];
-        tmem_ld16(tm + ((uint32_t)(32 * warp) << 16), v);
-        const int row = 32 * warp + lane;
-#pragma unroll
-        for (int o = 0; o < kOut; ++o) S.Y[row * kOut + o] = v[o] + S.b3[o];
-    }
-    tc_fence_before_sync();
-    return __syncthreads_and(ok) != 0;
+    if (warp == 0) tmem_dealloc(tm, kTmemCols);
 }
 
-// The blocks of both inference kernels take the whole 227 KB of shared memory
-// (one block per SM; the TMEM allocation can then never wait).
-constexpr size_t kTcSmemBytes = 232448;
-static_assert(sizeof(TcSmem) <= kTcSmemBytes, "tensor-core tile does not fit in shared memory");
-
-size_t learned_smem_bytes() { return kTcSmemBytes; }
-
-// Network outputs for M given feature rows (row-major [M][384] BF16).
-__global__ void __launch_bounds__(256, 1) k_mlp_infer(const __grid_constant__ MlpWeights W,
-                                                      const bf16* __restrict__ X, long long M,
-                                                      float* __restrict__ Y, unsigned* flags)
+cudaError_t launch_mlp_rows(const MlpWeights& W, const bf16* X, long long M, const unsigned* count_dev,
+                            float* Y, unsigned* flags, cudaStream_t s)
 {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
-    tc_setup(S, W);
-    uint32_t nc[3] = {0u, 0u, 0u};
-    bool ok = true;
-    for (long long t = blockIdx.x; ok && t * kRows < M; t += gridDim.x) {
-        const long long row0 = t * kRows;
-        auto fill = [&](int c, bf16* dst) {
-            for (int e = threadIdx.x; e < kRows * (kKc / 8); e += blockDim.x) {
-                const int r = e >> 3, j = e & 7;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (row0 + r < M)
-                    v = *reinterpret_cast<const uint4*>(X + (row0 + r) * kInPad + c * kKc + j * 8);
-                *reinterpret_cast<uint4*>(dst + core_idx(r, j * 8, kRows)) = v;
-            }
-        };
-        ok = mlp_tile(S, nc, fill);
-        if (threadIdx.x < kRows && row0 + threadIdx.x < M)
-#pragma unroll
-            for (int o = 0; o < kOut; ++o) Y[(row0 + threadIdx.x) * kOut + o] = S.Y[threadIdx.x * kOut + o];
-    }
-    if (!ok && threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
-    tc_teardown(S);
+    if (M <= 0) return cudaSuccess;
+    CUtensorMap xmap;
+    if (!encode_bf16_2d(&xmap, X, kInPad, (unsigned long long)M, kInPad * 2, 8, kRows))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (M + kRows - 1) / kRows;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, device_sm_count()));
+    k_mlp_rows<<<grid, 256, kTcSmemBytes, s>>>(W, xmap, M, count_dev, Y, flags);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_infer(const MlpWeights& W, const bf16* X, long long M, float* Y,
                              unsigned* flags, cudaStream_t s)
 {
-    const size_t smem = kTcSmemBytes;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    const long long tiles = (M + kRows - 1) / kRows;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, device_sm_count()));
-    k_mlp_infer<<<grid, 256, smem, s>>>(W, X, M, Y, flags);
-    return cudaGetLastError();
+    return launch_mlp_rows(W, X, M, nullptr, Y, flags, s);
 }
 
 // --------------------------------------------------------------------------
-// Fused inference + seeding over the queued voxels
+// Seeding of the queued voxels: features, network, exact seeds
 // --------------------------------------------------------------------------
 
 // Cost bucket of a queued voxel whose running squared gamma is g2: 1 + floor(2
@@ -758,183 +659,148 @@ __device__ __forceinline__ int cost_bucket(const Problem& P, float g2)
     return lo <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)lo)));
 }
 
-// One launch seeds the queued voxels past the cost gate: of one pair
-// (BATCH = false: P0.seed_list) or of every pair of a batch group (BATCH =
-// true: the (pair, item) rows of bd), 128 rows per tile.
-template <int N, bool BATCH>
-__global__ void __launch_bounds__(256, 1) k_learned(const __grid_constant__ Problem P0,
-                                                    const BatchDesc* __restrict__ bd,
-                                                    const __grid_constant__ MlpWeights W)
-{
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
-    const unsigned total = BATCH ? *bd->seed_count : min(P0.ctr->seed_count, P0.tail_cap);
-    unsigned* head = BATCH ? bd->seed_head : &P0.ctr->seed_head;
-    auto prob = [&](int r) -> const Problem& { return BATCH ? bd->probs[S.pair[r]] : P0; };
-    if (threadIdx.x < kNumBuckets) S.hist[threadIdx.x] = 0;
-    if (threadIdx.x == 0) { S.nseed = 0; S.nimp = 0; }
-    tc_setup(S, W);
-    uint32_t nc[3] = {0u, 0u, 0u};
-    bool ok = true;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) S.base = atomicAdd(head, (unsigned)kRows);
-        __syncthreads();
-        const unsigned base = S.base;
-        if (base >= total || !ok) break;
-        // ---- rows: pair, queue item, voxel, dose, scale ----
-        if (threadIdx.x < kRows) {
-            const unsigned it = base + threadIdx.x;
-            unsigned v = 0xffffffffu, item = 0u;
-            unsigned short pr = 0;
-            float dr = 0.f, inv = 0.f;
-            if (it < total) {
-                if constexpr (BATCH) {
-                    pr = bd->seed_pair[it];
-                    item = bd->seed_item[it];
-                } else {
-                    item = P0.seed_list[it];
-                }
-                const Problem& P = BATCH ? bd->probs[pr] : P0;
-                v = P.tail_raw[item];
-                dr = __ldg(P.ref + v);
-                const float dnorm = P.dose_norm > 0.f ? P.dose_norm : fdec(P.ctr->dnorm_enc);
-                inv = 1.0f / (P.dd_frac * (P.local ? dr : dnorm));
-            }
-            S.pair[threadIdx.x] = pr;
-            S.vox[threadIdx.x] = v;
-            S.item[threadIdx.x] = item;
-            S.dr[threadIdx.x] = dr;
-            S.inv[threadIdx.x] = inv;
-        }
-        __syncthreads();
-        // ---- features (chunk by chunk) and the three layers ----
-        auto fill = [&](int c, bf16* dst) {
-            // eight consecutive features of one row per step: their loads are
-            // independent, so each thread keeps eight in flight
-            for (int e = threadIdx.x; e < kRows * (kKc / 8); e += blockDim.x) {
-                const int r = e / (kKc / 8), j = e % (kKc / 8);
-                float val[8];
-                features8<N>(prob(r), S.vox[r], S.dr[r], S.inv[r], c * kKc + j * 8, val);
-                uint4 pk;
-                uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(val[2 * u], val[2 * u + 1]);
-                    w[u] = *reinterpret_cast<const uint32_t*>(&b2);
-                }
-                *reinterpret_cast<uint4*>(dst + core_idx(r, j * 8, kRows)) = pk;
-            }
-        };
-        ok = mlp_tile(S, nc, fill);
-        // ---- seed: exact faces of the cells around the proposed point ----
-        {
-            const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
-            const unsigned v = S.vox[r];
-            const Problem& P = prob(r);
-            float sd2 = kInf;
-            int x = 0, y = 0, z = 0;
-            if (v != 0xffffffffu) {
-                x = (int)(v % (unsigned)P.nx);
-                const unsigned r1 = v / (unsigned)P.nx;
-                y = (int)(r1 % (unsigned)P.ny);
-                z = (int)(r1 / (unsigned)P.ny);
-                int o[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float ov = a < N ? S.Y[r * kOut + a] / P.hn[a] : 0.f;
-                    o[a] = (int)floorf(fminf(fmaxf(ov, -256.f), 256.f));
-                }
-                constexpr int NCELL = 1 << N;
-#pragma unroll 1
-                for (int u = half; u < NCELL; u += 2) {
-                    const int cx = o[0] + (u & 1), cy = o[1] + ((u >> 1) & 1),
-                              cz = N == 3 ? o[2] + ((u >> 2) & 1) : 0;
-                    float q[8];
-                    uint32_t okc;
-                    if (!load_cell<N>(P, x, y, z, cx, cy, cz, S.dr[r], S.inv[r], q, okc)) continue;
-                    CellGeom<float> gg;
-                    cell_geom<N, float>(cx, cy, cz, P.mt, gg);
-                    bool ill = false;
-                    const float cb = cell_min_d2<N, float>(q, okc, gg, P.mt,
-                                                           P.tau > 0.f ? 0.99f * rsqrtf(P.tau) : kInf,
-                                                           kInf, ill);
-                    if (ill) ill = cell_gram_ill<N>(q, okc, P.mt.kappa, P.tau);
-                    if (!ill) sd2 = fminf(sd2, cb);        // ill-conditioned cells are not used as seeds
-                }
-            }
-            sd2 = fminf(sd2, __shfl_xor_sync(0xffffffffu, sd2, 1));
-            if (half == 0 && v != 0xffffffffu) {
-                const float cur = P.out[v];                   // gamma^2 after the faces through v
-                const float nb = fminf(cur, sd2);
-                const bool better = nb < cur;
-                if (better) P.out[v] = nb;
-                // bucket from the (possibly) tighter bound
-                const int bucket = cost_bucket(P, nb);
-                const int was = P.tail_bucket[S.item[r]];
-                if constexpr (BATCH) {
-                    atomicAdd(&P.ctr->seeded, 1u);
-                    if (better) atomicAdd(&P.ctr->seed_improved, 1u);
-                    if (bucket != was) {                 // move the voxel between its pair's bins
-                        P.tail_bucket[S.item[r]] = (unsigned char)bucket;
-                        atomicAdd(&P.ctr->hist[bucket], 1u);
-                        atomicSub(&P.ctr->hist[was], 1u);
-                    }
-                } else {
-                    atomicAdd(&S.nseed, 1u);
-                    if (better) atomicAdd(&S.nimp, 1u);
-                    if (bucket != was) {                 // move the voxel between histogram bins
-                        P.tail_bucket[S.item[r]] = (unsigned char)bucket;
-                        atomicAdd(&S.hist[bucket], 1u);
-                        atomicSub(&S.hist[was], 1u);     // wraps; the sum over the block is exact
-                    }
-                }
-            }
-        }
+// The seed rows of one pair (BATCH = false: P0.seed_list items) or of every
+// pair of a batch group (the (pair, item) rows of bd): their number, capped
+// at the row buffer, and the pair and queue item of row r.
+template <bool BATCH>
+struct SeedRows {
+    const Problem* P0;
+    const BatchDesc* bd;
+    __device__ unsigned count() const
+    {
+        return BATCH ? min(*bd->seed_count, bd->seed_cap) : min(P0->ctr->seed_count, P0->seed_cap);
     }
+    __device__ bf16* X() const { return BATCH ? bd->seed_X : P0->seed_X; }
+    __device__ float* Y() const { return BATCH ? bd->seed_Y : P0->seed_Y; }
+    __device__ const Problem& prob(unsigned r) const { return BATCH ? bd->probs[bd->seed_pair[r]] : *P0; }
+    __device__ unsigned item(unsigned r) const { return BATCH ? bd->seed_item[r] : P0->seed_list[r]; }
+};
+
+// Features of every seed row into the row buffer: one thread per eight
+// consecutive features of a row (their loads in flight together).
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(256) k_seed_features(const __grid_constant__ Problem P0,
+                                                       const BatchDesc* __restrict__ bd)
+{
+    const SeedRows<BATCH> rows{&P0, bd};
+    const long long total = (long long)rows.count() * (kInPad / 8);
+    bf16* X = rows.X();
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const unsigned r = (unsigned)(e / (kInPad / 8));
+        const int f0 = (int)(e % (kInPad / 8)) * 8;
+        const Problem& P = rows.prob(r);
+        const unsigned v = P.tail_raw[rows.item(r)];
+        const float dr = __ldg(P.ref + v);
+        const float inv = 1.0f / (P.dd_frac * (P.local ? dr : resolve_dnorm(P)));
+        float val[8];
+        features8<N>(P, v, dr, inv, f0, val);
+        uint4 pk;
+        uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(val[2 * u], val[2 * u + 1]);
+            w[u] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(X + (long long)r * kInPad + f0) = pk;
+    }
+}
+
+// Exact seeds from the network's proposals: for every seed row, the faces of
+// the 2^N cells around the proposed nearest point (two threads per row), a
+// true distance to the evaluation surface, lower the voxel's running squared
+// gamma; the voxel moves to the cost bucket of the tighter bound.
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(256) k_seed_apply(const __grid_constant__ Problem P0,
+                                                    const BatchDesc* __restrict__ bd)
+{
+    const SeedRows<BATCH> rows{&P0, bd};
+    const unsigned total = rows.count();
+    const float* Y = rows.Y();
+    __shared__ unsigned sh_hist[kNumBuckets];
+    __shared__ unsigned sh_seed, sh_imp;
+    if (threadIdx.x < kNumBuckets) sh_hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) sh_seed = sh_imp = 0;
     __syncthreads();
+    // a warp takes 16 rows at a time (two lanes per row), so that every lane
+    // of the warp runs the same iterations (the shuffle below)
+    const int lane = threadIdx.x & 31, half = lane & 1;
+    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned rb = gw * 16u; rb < total; rb += nw * 16u) {
+        const unsigned r = rb + (unsigned)(lane >> 1);
+        const bool live = r < total;
+        float sd2 = kInf;
+        unsigned v = 0, item = 0;
+        const Problem& P = rows.prob(live ? r : 0u);
+        if (live) {
+            item = rows.item(r);
+            v = P.tail_raw[item];
+            const int x = (int)(v % (unsigned)P.nx);
+            const unsigned r1 = v / (unsigned)P.nx;
+            const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
+            const float dr = __ldg(P.ref + v);
+            const float inv = 1.0f / (P.dd_frac * (P.local ? dr : resolve_dnorm(P)));
+            int o[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float ov = a < N ? Y[(long long)r * kOut + a] / P.hn[a] : 0.f;
+                o[a] = (int)floorf(fminf(fmaxf(ov, -256.f), 256.f));
+            }
+            constexpr int NCELL = 1 << N;
+#pragma unroll 1
+            for (int u = half; u < NCELL; u += 2) {
+                const int cx = o[0] + (u & 1), cy = o[1] + ((u >> 1) & 1),
+                          cz = N == 3 ? o[2] + ((u >> 2) & 1) : 0;
+                float q[8];
+                uint32_t okc;
+                if (!load_cell<N>(P, x, y, z, cx, cy, cz, dr, inv, q, okc)) continue;
+                CellGeom<float> gg;
+                cell_geom<N, float>(cx, cy, cz, P.mt, gg);
+                bool ill = false;
+                const float cb = cell_min_d2<N, float>(q, okc, gg, P.mt,
+                                                       P.tau > 0.f ? 0.99f * rsqrtf(P.tau) : kInf,
+                                                       kInf, ill);
+                if (ill) ill = cell_gram_ill<N>(q, okc, P.mt.kappa, P.tau);
+                if (!ill) sd2 = fminf(sd2, cb);            // ill-conditioned cells are not used as seeds
+            }
+        }
+        sd2 = fminf(sd2, __shfl_xor_sync(0xffffffffu, sd2, 1));
+        if (live && half == 0) {
+            const float cur = P.out[v];                     // gamma^2 after the faces through v
+            const float nb = fminf(cur, sd2);
+            const bool better = nb < cur;
+            if (better) P.out[v] = nb;
+            const int bucket = cost_bucket(P, nb);
+            const int was = P.tail_bucket[item];
+            if (BATCH) {
+                atomicAdd(&P.ctr->seeded, 1u);
+                if (better) atomicAdd(&P.ctr->seed_improved, 1u);
+                if (bucket != was) {                        // move the voxel between its pair's bins
+                    P.tail_bucket[item] = (unsigned char)bucket;
+                    atomicAdd(&P.ctr->hist[bucket], 1u);
+                    atomicSub(&P.ctr->hist[was], 1u);
+                }
+            } else {
+                atomicAdd(&sh_seed, 1u);
+                if (better) atomicAdd(&sh_imp, 1u);
+                if (bucket != was) {
+                    P.tail_bucket[item] = (unsigned char)bucket;
+                    atomicAdd(&sh_hist[bucket], 1u);
+                    atomicSub(&sh_hist[was], 1u);          // wraps; the sum over the block is exact
+                }
+            }
+        }
+    }
     if constexpr (!BATCH) {
-        if (threadIdx.x < kNumBuckets && S.hist[threadIdx.x])
-            atomicAdd(&P0.ctr->hist[threadIdx.x], S.hist[threadIdx.x]);
+        __syncthreads();
+        if (threadIdx.x < kNumBuckets && sh_hist[threadIdx.x])
+            atomicAdd(&P0.ctr->hist[threadIdx.x], sh_hist[threadIdx.x]);
         if (threadIdx.x == 0) {
-            atomicAdd(&P0.ctr->seeded, S.nseed);
-            atomicAdd(&P0.ctr->seed_improved, S.nimp);
+            if (sh_seed) atomicAdd(&P0.ctr->seeded, sh_seed);
+            if (sh_imp) atomicAdd(&P0.ctr->seed_improved, sh_imp);
         }
     }
-    if (threadIdx.x == 0 && !ok) {
-        if constexpr (BATCH) {
-            for (int p = 0; p < bd->npairs; ++p) atomicOr(&bd->probs[p].ctr->flags, kFlagTimeout);
-        } else {
-            atomicOr(&P0.ctr->flags, kFlagTimeout);
-        }
-    }
-    tc_teardown(S);
-}
-
-template <int N, bool BATCH>
-static cudaError_t launch_learned_k(const Problem& P, const BatchDesc* bd, const MlpWeights& W,
-                                    cudaStream_t s)
-{
-    const size_t smem = kTcSmemBytes;
-    cudaError_t e = cudaFuncSetAttribute(k_learned<N, BATCH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_learned<N, BATCH><<<device_sm_count(), 256, smem, s>>>(P, bd, W);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_learned(const Problem& P, const MlpWeights& W, cudaStream_t s)
-{
-    return P.ndim == 3 ? launch_learned_k<3, false>(P, nullptr, W, s)
-                       : launch_learned_k<2, false>(P, nullptr, W, s);
-}
-
-cudaError_t launch_batch_learned(const BatchGroup& g, const MlpWeights& W, cudaStream_t s)
-{
-    if (g.npairs <= 0) return cudaSuccess;
-    Problem dummy{};
-    return g.ndim == 3 ? launch_learned_k<3, true>(dummy, g.desc, W, s)
-                       : launch_learned_k<2, true>(dummy, g.desc, W, s);
 }
 
 // Queue items of every pair of a batch group past the cost gate, as (pair,
@@ -955,33 +821,54 @@ __global__ void __launch_bounds__(256) k_seed_select_batch(const BatchDesc* __re
         base = __shfl_sync(0xffffffffu, base, 0);
         if (take) {
             const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
-            bd->seed_item[pos] = i;
-            bd->seed_pair[pos] = (unsigned short)blockIdx.y;
+            if (pos < bd->seed_cap) {                       // rows past the buffer go unseeded
+                bd->seed_item[pos] = i;
+                bd->seed_pair[pos] = (unsigned short)blockIdx.y;
+            }
         }
     }
 }
 
-cudaError_t launch_batch_seed_select(const BatchGroup& g, int min_bucket, cudaStream_t s)
+template <int N, bool BATCH>
+static cudaError_t launch_seeding_n(const Problem& P, const BatchDesc* bd, const MlpWeights& W,
+                                    const bf16* X, float* Y, unsigned cap, const unsigned* count,
+                                    unsigned* flags, cudaStream_t s)
 {
-    if (g.npairs <= 0) return cudaSuccess;
+    const int sms = device_sm_count();
+    k_seed_features<N, BATCH><<<sms * 16, 256, 0, s>>>(P, bd);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_mlp_rows(W, X, cap, count, Y, flags, s)) != cudaSuccess) return e;
+    k_seed_apply<N, BATCH><<<sms * 8, 256, 0, s>>>(P, bd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seeding(const Problem& P, const MlpWeights& W, int min_bucket, cudaStream_t s)
+{
+    if (!P.seed_list || !P.seed_X || !P.seed_Y || P.seed_cap == 0) return cudaErrorInvalidValue;
+    k_seed_select<<<device_sm_count() * 4, 256, 0, s>>>(P, min_bucket);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return P.ndim == 3
+               ? launch_seeding_n<3, false>(P, nullptr, W, P.seed_X, P.seed_Y, P.seed_cap,
+                                            &P.ctr->seed_count, &P.ctr->flags, s)
+               : launch_seeding_n<2, false>(P, nullptr, W, P.seed_X, P.seed_Y, P.seed_cap,
+                                            &P.ctr->seed_count, &P.ctr->flags, s);
+}
+
+cudaError_t launch_batch_seeding(const BatchGroup& g, const MlpWeights& W, int min_bucket,
+                                 cudaStream_t s)
+{
+    if (g.npairs <= 0 || g.seed_cap == 0) return cudaSuccess;
     const int bx = std::max(1, device_sm_count() * 2 / std::max(1, g.npairs)) + 1;
     k_seed_select_batch<<<dim3(bx, g.npairs), 256, 0, s>>>(g.desc, min_bucket);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_grad_norms(const Problem& P, float* ge, float* gr, cudaStream_t s)
-{
-    const int grid = (int)std::min<long long>((P.nvox + 255) / 256, (long long)device_sm_count() * 8);
-    if (P.ndim == 3) k_grad_norms<3><<<std::max(grid, 1), 256, 0, s>>>(P, ge, gr);
-    else k_grad_norms<2><<<std::max(grid, 1), 256, 0, s>>>(P, ge, gr);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_seed_select(const Problem& P, int min_bucket, cudaStream_t s)
-{
-    if (!P.seed_list) return cudaErrorInvalidValue;
-    k_seed_select<<<device_sm_count() * 4, 256, 0, s>>>(P, min_bucket);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    Problem dummy{};
+    return g.ndim == 3 ? launch_seeding_n<3, true>(dummy, g.desc, W, g.seed_X, g.seed_Y, g.seed_cap,
+                                                   g.seed_count, g.flags, s)
+                       : launch_seeding_n<2, true>(dummy, g.desc, W, g.seed_X, g.seed_Y, g.seed_cap,
+                                                   g.seed_count, g.flags, s);
 }
 
 cudaError_t launch_features(const Problem& P, const unsigned* vox, long long n, bf16* X,
@@ -1025,7 +912,11 @@ struct gamma_model_s {
     long long wsM = 0;
     float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dY = nullptr, *dH1 = nullptr, *loss = nullptr;
     bf16 *H1h = nullptr, *H2h = nullptr, *dZ2h = nullptr, *dZ1h = nullptr;
-    unsigned* dflags = nullptr;   // error flags of the inference kernel
+    // batch-contiguous (transposed) operands of the weight-gradient GEMMs,
+    // row stride wsMp = wsM rounded up to 8 (16-byte rows for TMA)
+    bf16 *XT = nullptr, *H1T = nullptr, *dZ1T = nullptr, *dZ2T = nullptr;
+    long long wsMp = 0;
+    unsigned* dflags = nullptr;   // error flags of the tensor-core kernels
 };
 
 namespace {
@@ -1052,9 +943,11 @@ void free_ws(gamma_model_s* m)
 {
     cudaFree(m->Z1); cudaFree(m->Z2); cudaFree(m->Y); cudaFree(m->dY); cudaFree(m->dH1);
     cudaFree(m->loss); cudaFree(m->H1h); cudaFree(m->H2h); cudaFree(m->dZ2h); cudaFree(m->dZ1h);
+    cudaFree(m->XT); cudaFree(m->H1T); cudaFree(m->dZ1T); cudaFree(m->dZ2T);
     m->Z1 = m->Z2 = m->Y = m->dY = m->dH1 = m->loss = nullptr;
     m->H1h = m->H2h = m->dZ2h = m->dZ1h = nullptr;
-    m->wsM = 0;
+    m->XT = m->H1T = m->dZ1T = m->dZ2T = nullptr;
+    m->wsM = m->wsMp = 0;
 }
 
 int ensure_ws(gamma_model_s* m, long long M)
@@ -1071,7 +964,13 @@ int ensure_ws(gamma_model_s* m, long long M)
     MCK(cudaMalloc(&m->H2h, sizeof(bf16) * M * gk::kH));
     MCK(cudaMalloc(&m->dZ2h, sizeof(bf16) * M * gk::kH));
     MCK(cudaMalloc(&m->dZ1h, sizeof(bf16) * M * gk::kH));
+    const long long Mp = (M + 7) / 8 * 8;
+    MCK(cudaMalloc(&m->XT, sizeof(bf16) * Mp * gk::kInPad));
+    MCK(cudaMalloc(&m->H1T, sizeof(bf16) * Mp * gk::kH));
+    MCK(cudaMalloc(&m->dZ1T, sizeof(bf16) * Mp * gk::kH));
+    MCK(cudaMalloc(&m->dZ2T, sizeof(bf16) * Mp * gk::kH));
     m->wsM = M;
+    m->wsMp = Mp;
     return GAMMA_OK;
 }
 
@@ -1121,22 +1020,25 @@ int refresh_bf16(gamma_model_s* m, cudaStream_t s)
     return cuda_rc(cudaGetLastError());
 }
 
-// Forward pass of a minibatch through the training kernels (activations kept).
+// Forward pass of a minibatch through the training kernels (activations
+// kept): the three layers as tensor-core GEMMs (tcgen05, TMEM accumulators,
+// TMA operand loads), bias and ReLU in separate element-wise passes.
 int forward_train(gamma_model_s* m, const bf16* X, long long M, cudaStream_t s)
 {
     using namespace gk;
-    const dim3 g1((kH + 63) / 64, (unsigned)((M + 63) / 64), 1);
-    k_gemm<false, false, false><<<g1, 128, 0, s>>>((int)M, kH, kInPad, X, kInPad, m->W1h, kInPad, m->Z1, kH);
+    MCK(launch_gemm_tc(X, M, kInPad, m->W1h, kH, kInPad, kInPad, m->Z1, kH, 1, m->dflags, s));
     k_bias_act<<<grid_for_n(M * kH), 256, 0, s>>>(M, kH, m->Z1, m->p + kOffB1, m->H1h, kH, 1);
-    k_gemm<false, false, false><<<g1, 128, 0, s>>>((int)M, kH, kH, m->H1h, kH, m->W2h, kH, m->Z2, kH);
+    MCK(launch_gemm_tc(m->H1h, M, kH, m->W2h, kH, kH, kH, m->Z2, kH, 1, m->dflags, s));
     k_bias_act<<<grid_for_n(M * kH), 256, 0, s>>>(M, kH, m->Z2, m->p + kOffB2, m->H2h, kH, 1);
-    const dim3 g3(1, (unsigned)((M + 63) / 64), 1);
-    k_gemm<false, false, false><<<g3, 128, 0, s>>>((int)M, kOutPad, kH, m->H2h, kH, m->W3h, kH, m->Y, kOutPad);
+    MCK(launch_gemm_tc(m->H2h, M, kH, m->W3h, kOutPad, kH, kH, m->Y, kOutPad, 1, m->dflags, s));
     k_bias_act<<<grid_for_n(M * kOutPad), 256, 0, s>>>(M, kOutPad, m->Y, m->p + kOffB3, nullptr, 0, 0);
     return cuda_rc(cudaGetLastError());
 }
 
-// Loss and gradients of a minibatch into m->gr (zeroed first).
+// Loss and gradients of a minibatch into m->gr (zeroed first).  The weight
+// gradients sum over the batch, so their GEMMs take the batch as K: the
+// operands are first transposed to batch-contiguous rows, and the K range is
+// split over several blocks per tile that add into the gradient.
 int backward_train(gamma_model_s* m, const bf16* X, const float* T, long long M, long long count,
                    cudaStream_t s)
 {
@@ -1144,22 +1046,25 @@ int backward_train(gamma_model_s* m, const bf16* X, const float* T, long long M,
     MCK(cudaMemsetAsync(m->gr, 0, sizeof(float) * kNParams, s));
     MCK(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
     const float invc = count > 0 ? 1.f / (float)count : 0.f;
+    const long long Mp = (M + 7) / 8 * 8;
+    const int splits = (int)std::max<long long>(1, std::min<long long>(32, M / 512));
     k_huber<<<grid_for_n(M), 256, 0, s>>>(M, m->Y, T, m->dY, m->loss, invc);
     k_out_back<<<grid_for_n(M * kH, 256), 256, 0, s>>>(M, m->dY, m->p + kOffW3, m->Z2, m->H2h,
                                                          m->dZ2h, m->gr + kOffW3, m->gr + kOffB3);
-    // dW2 = dZ2^T H1 (split over the batch), db2 = colsum dZ2
-    const int splits = (int)std::max<long long>(1, std::min<long long>(64, M / 256));
-    const dim3 gw2((kH + 63) / 64, (kH + 63) / 64, splits);
-    k_gemm<true, true, true><<<gw2, 128, 0, s>>>(kH, kH, (int)M, m->dZ2h, kH, m->H1h, kH, m->gr + kOffW2, kH);
+    // dW2 = dZ2^T H1 (K = batch), db2 = colsum dZ2
+    MCK(launch_transpose_bf16(m->dZ2h, M, kH, kH, m->dZ2T, Mp, s));
+    MCK(launch_transpose_bf16(m->H1h, M, kH, kH, m->H1T, Mp, s));
+    MCK(launch_gemm_tc(m->dZ2T, kH, Mp, m->H1T, kH, Mp, M, m->gr + kOffW2, kH, splits, m->dflags, s));
     k_colsum<<<dim3(256, (kH + 127) / 128), 128, 0, s>>>(M, kH, m->dZ2h, m->gr + kOffB2);
-    // dH1 = dZ2 W2, dZ1 = dH1 [Z1 > 0]
-    const dim3 gh((kH + 63) / 64, (unsigned)((M + 63) / 64), 1);
-    k_gemm<false, false, false><<<gh, 128, 0, s>>>((int)M, kH, kH, m->dZ2h, kH, m->W2Th, kH, m->dH1, kH);
+    // dH1 = dZ2 W2 (B[n][k] = W2^T[n][k] = W2[k][n]), dZ1 = dH1 [Z1 > 0]
+    MCK(launch_gemm_tc(m->dZ2h, M, kH, m->W2Th, kH, kH, kH, m->dH1, kH, 1, m->dflags, s));
     k_relu_back<<<grid_for_n(M * kH), 256, 0, s>>>(M, kH, m->dH1, m->Z1, m->dZ1h, nullptr);
     k_colsum<<<dim3(256, (kH + 127) / 128), 128, 0, s>>>(M, kH, m->dZ1h, m->gr + kOffB1);
-    // dW1 = dZ1^T X
-    const dim3 gw1((kInPad + 63) / 64, (kH + 63) / 64, splits);
-    k_gemm<true, true, true><<<gw1, 128, 0, s>>>(kH, kInPad, (int)M, m->dZ1h, kH, X, kInPad, m->gr + kOffW1, kInPad);
+    // dW1 = dZ1^T X (K = batch)
+    MCK(launch_transpose_bf16(m->dZ1h, M, kH, kH, m->dZ1T, Mp, s));
+    MCK(launch_transpose_bf16(X, M, kInPad, kInPad, m->XT, Mp, s));
+    MCK(launch_gemm_tc(m->dZ1T, kH, Mp, m->XT, kInPad, Mp, M, m->gr + kOffW1, kInPad, splits,
+                       m->dflags, s));
     return cuda_rc(cudaGetLastError());
 }
 
@@ -1252,7 +1157,9 @@ int gamma_model_forward(gamma_model m, const void* X_bf16_dev, int64_t M, float*
 {
     if (!m || !X_bf16_dev || !Y_dev || M <= 0) return GAMMA_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (reinterpret_cast<uintptr_t>(X_bf16_dev) % 16 != 0) return GAMMA_ERR_INVALID_ARG;
     if (int rc = ensure_ws(m, M)) return rc;
+    MCK(cudaMemsetAsync(m->dflags, 0, sizeof(unsigned), s));
     if (int rc = forward_train(m, (const bf16*)X_bf16_dev, M, s)) return rc;
     MCK(cudaMemcpy2DAsync(Y_dev, sizeof(float) * gk::kOut, m->Y, sizeof(float) * gk::kOutPad,
                           sizeof(float) * gk::kOut, (size_t)M, cudaMemcpyDeviceToDevice, s));
@@ -1280,12 +1187,17 @@ int gamma_model_backward(gamma_model m, const void* X_bf16_dev, const float* T_d
 {
     if (!m || !X_bf16_dev || !T_dev || M <= 0) return GAMMA_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (reinterpret_cast<uintptr_t>(X_bf16_dev) % 16 != 0) return GAMMA_ERR_INVALID_ARG;
     if (int rc = ensure_ws(m, M)) return rc;
+    MCK(cudaMemsetAsync(m->dflags, 0, sizeof(unsigned), s));
     if (int rc = forward_train(m, (const bf16*)X_bf16_dev, M, s)) return rc;
     if (int rc = backward_train(m, (const bf16*)X_bf16_dev, T_dev, M, M, s)) return rc;
     if (loss_out) {
+        unsigned flags = 0;
         MCK(cudaMemcpyAsync(loss_out, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        MCK(cudaMemcpyAsync(&flags, m->dflags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         MCK(cudaStreamSynchronize(s));
+        if (flags & gk::kFlagTimeout) return GAMMA_ERR_TIMEOUT;
     }
     return GAMMA_OK;
 }
@@ -1304,8 +1216,11 @@ int gamma_model_train_step(gamma_model m, const void* X_bf16_dev, const float* T
     MCK(cudaGetLastError());
     if (int rc = refresh_bf16(m, s)) return rc;
     if (loss_out) {
+        unsigned flags = 0;
         MCK(cudaMemcpyAsync(loss_out, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        MCK(cudaMemcpyAsync(&flags, m->dflags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         MCK(cudaStreamSynchronize(s));
+        if (flags & gk::kFlagTimeout) return GAMMA_ERR_TIMEOUT;
     }
     return GAMMA_OK;
 }

@@ -58,3 +58,27 @@ def test_cell_census_matches_brute_force(nd):
 def test_cell_census_empty_map():
     gamma = np.full((4, 5, 6), np.nan)
     assert tuple(bench.cell_census(torch.from_numpy(gamma), (1.0, 1.0, 1.0), 3.0)) == (0, 0)
+
+
+def test_record_counters_reads_an_ncu_raw_csv(tmp_path, monkeypatch):
+    # the layout of `ncu -i REPORT --page raw --csv`: a header row of metric
+    # names, a row of units, then one row per captured launch
+    csv_text = (
+        '"ID","Kernel Name","gpu__time_duration.sum","dram__bytes_read.sum","dram__bytes_write.sum",'
+        '"smsp__inst_executed.sum","smsp__thread_inst_executed.sum",'
+        '"sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active"\n'
+        '"","","ns","byte","byte","inst","inst","%"\n'
+        '"0","void gk::k_shell<3, 4, false>(gk::Problem, CUtensorMap_st, int)","80,000","25,467,904","0",'
+        '"7,000,000","190,000,000","22.1"\n'
+        '"1","void gk::k_walk<3, 2>(gk::Problem, CUtensorMap_st, int)","40,000","9,000,000","1,000",'
+        '"3,000,000","60,000,000","30.5"\n')
+    src = tmp_path / "raw.csv"
+    src.write_text(csv_text)
+    monkeypatch.setattr(bench, "COUNTERS_PATH", str(tmp_path / "counters.json"))
+    out = bench.record_counters(str(src), "imrt_160", "test capture")
+    assert set(out) == {"k_shell", "k_walk"}
+    assert out["k_shell"]["dram_read_bytes"] == 25467904
+    assert out["k_walk"]["warp_inst_per_launch"] == 3e6
+    assert out["k_walk"]["fma_pipe_pct"] == 30.5
+    assert bench.recorded_traffic("k_walk", "imrt_160") == 9001000
+    assert bench.recorded_traffic("k_walk", "plane_128") is None

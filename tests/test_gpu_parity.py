@@ -174,6 +174,41 @@ def test_truncated_table_box_scan(ndim):
     assert_parity(got, want, counts)
 
 
+@pytest.mark.parametrize("case", ["plane_128", "volume_local", "volume_ragged", "truncated_3d",
+                                  "truncated_2d", "unsorted"])
+@pytest.mark.parametrize("blocks", [1, 3])
+def test_tile_staged_walk(case, blocks):
+    # Option walk = 1: the queued voxels walked tile by tile from a TMA-staged
+    # halo box (cells beyond the box read global memory; a tiny table sends
+    # voxels into the box scan; "unsorted" takes the tiles in discovery order).
+    opts = {"walk": 1, "tail_blocks_per_sm": blocks}
+    if case == "plane_128":
+        p, crit = synth.workload("plane_128"), synth.Criteria(0.03, 3.0)
+    elif case in ("volume_local", "unsorted"):
+        p, crit = synth.workload("imrt_small"), synth.Criteria(0.01, 1.0, local=True)
+        if case == "unsorted":
+            opts["sort_tail"] = 0
+    elif case == "volume_ragged":
+        p = synth.make_pair_3d(shape=(19, 33, 29), spacing=(3.0, 2.0, 1.5), seed=21,
+                               shift_mm=(1.0, -0.5, 2.0), scale=1.05)
+        crit = synth.Criteria(0.02, 2.0, cutoff_frac=0.05)
+    elif case == "truncated_3d":
+        p = synth.make_pair_3d(shape=(14, 18, 16), spacing=(2.0, 2.0, 2.0), seed=6,
+                               shift_mm=(1.0, 2.0, 2.5), scale=1.06)
+        crit = synth.Criteria(0.01, 1.0, local=True)
+        opts["table_cap"] = 16
+    else:
+        p = synth.make_pair_2d(shape=(30, 26), seed=5, shift_mm=(2.0, 1.0), scale=1.06)
+        crit = synth.Criteria(0.01, 1.0, local=True)
+        opts["table_cap"] = 16
+    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, crit, opts, runs=2)
+    if case.startswith("truncated"):
+        assert st["overflow_voxels"] > 0
+    want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
+    for g_ in got:                                   # a direct run, then the graph replay
+        assert_parity(g_, want, counts)
+
+
 @pytest.mark.parametrize("design", [1, 2])
 @pytest.mark.parametrize("face_eval", [0, 1])
 @pytest.mark.parametrize("ndim", [2, 3])
