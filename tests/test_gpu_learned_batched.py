@@ -26,6 +26,7 @@ torch = pytest.importorskip("torch")
 # 37 = 69x70x70 (1 %/1 mm), 55 = 72x75x75 (1 %/1 mm), planes 2 and 3 (1 %/1 mm)
 # and 0
 C4_SUBSET = (50, 46, 37, 55, 2, 3, 0)
+SEED_ROWS = 1 << 19          # rows of the network's buffer per run or batch group
 
 
 def _geom(p):
@@ -93,12 +94,18 @@ def test_batch_subset_and_learned_batch_match_single_pairs_and_oracle():
     finally:
         g.gamma_destroy(hb)
         g.gamma_model_destroy(m)
+    # each dimension group seeds its queued voxels up to the network's row
+    # buffer (SEED_ROWS rows); the rest are walked unseeded, with equal results
+    for nd in (2, 3):
+        grp = [st for p, st in zip(pairs, stats_l) if p.ref.ndim == nd]
+        queued = sum(st["tail_voxels"] for st in grp)
+        assert sum(st["seeded"] for st in grp) == min(queued, SEED_ROWS) > 0
     for p, (single, c1), b, cb, l_, cl, st in zip(pairs, singles, batched, counts_b, learned,
                                                   counts_l, stats_l):
         np.testing.assert_allclose(b, single, rtol=0, atol=1e-6, equal_nan=True, err_msg=p.name)
         np.testing.assert_allclose(l_, single, rtol=0, atol=1e-6, equal_nan=True, err_msg=p.name)
         assert cb[1:] == c1[1:] and cl[1:] == c1[1:], p.name
-        assert st["seeded"] == st["tail_voxels"], p.name
+        assert st["seeded"] <= st["tail_voxels"], p.name
         idx = _sample(l_, rng)
         want = oracle_gamma(p.ref, p.eval, p.spacing, p.criteria, idx=idx)
         assert_parity(l_.ravel()[idx], want)
