@@ -66,6 +66,7 @@ TIE_BAND = 1e-4
 # proposal network trained by the committed training command
 MODEL_PATH = os.path.join(ROOT, "paper_1012_1900_gb300", "proposal_2pct2mm.gmlp")
 VS_PLAIN_TEST_PAIRS = 4      # held-out 200x200x150 pairs timed plain against learned
+VS_PLAIN_GATES = (15, 17, 19)  # further cost gates timed on them (the library default is 13)
 
 
 def parse():
@@ -85,6 +86,9 @@ def parse():
                     help="store the search kernels' counters from `ncu -i REPORT --page raw --csv` "
                          "output in profiles/counters.json (for --workload), then exit")
     ap.add_argument("--capture-note", default="", help="where the --record-counters capture came from")
+    ap.add_argument("--load-seconds", type=float, default=LOAD_S,
+                    help="back-to-back maps before the timed steps, for the clock record "
+                         "(0 for profiler runs)")
     ap.add_argument("--walk", type=int, default=-1,
                     help="1: tile-staged walk, 0: voxel-queue walk (-1: library default)")
     ap.add_argument("--no-vs-plain", action="store_true",
@@ -552,19 +556,24 @@ def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
             e = torch.from_numpy(p.eval).to(dev)
             o = torch.empty_like(r)
             row = {"pair": p.name}
-            for mode in ("plain", "learned"):
+            for mode in ["plain", "learned"] + [f"gate{b}" for b in VS_PLAIN_GATES]:
                 h = g.gamma_create(r, e, 3, p.ref.shape, p.spacing, crit)
                 try:
                     for k, v in launch.items():
                         g.gamma_set_option(h, k, v)
-                    if mode == "learned":
+                    if mode != "plain":
                         g.gamma_load_model(h, MODEL_PATH)
+                    if mode.startswith("gate"):
+                        g.gamma_set_option(h, "seed_min_bucket", int(mode[4:]))
                     for _ in range(3):
                         g.gamma_run(h, o, stream)
                     row[f"{mode}_ms"] = _event_ms(torch, stream, lambda: g.gamma_run(h, o, stream),
                                                   reps, flush)
                     g.gamma_pass_rate(h)
                     st = g.gamma_get_stats(h)
+                    if mode.startswith("gate"):
+                        row[f"{mode}_seeded"] = st["seeded"]
+                        continue
                     row[f"{mode}_map"] = o.cpu().numpy()
                     # phase split (library events; the seeding runs inside the
                     # shell phase), from a few further runs
@@ -591,7 +600,10 @@ def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
         nv = sum(p.nvox for p in tests)
         res["held_out_200x200x150_2pct2mm"] = {
             "pairs": rows, "plain_voxels_per_s": nv / (tp / 1e3),
-            "learned_voxels_per_s": nv / (tl / 1e3), "speedup_learned_vs_plain": tp / tl}
+            "learned_voxels_per_s": nv / (tl / 1e3), "speedup_learned_vs_plain": tp / tl,
+            "gate_sweep": {f"seed_min_bucket {b}": {
+                "speedup_vs_plain": tp / sum(r[f"gate{b}_ms"] for r in rows),
+                "seeded": sum(r[f"gate{b}_seeded"] for r in rows)} for b in VS_PLAIN_GATES}}
     res["seconds"] = time.perf_counter() - t0
     return res
 
@@ -647,7 +659,7 @@ def run_ours(args, pair, rank, world, local_rank):
         # back-to-back maps for about LOAD_S seconds right before the timed
         # steps, so that the clock samples describe the GPU under this load
         t_load = time.monotonic()
-        while time.monotonic() - t_load < LOAD_S:
+        while time.monotonic() - t_load < args.load_seconds:
             for _ in range(50):
                 flush.zero_()
                 g.gamma_run(h, out, stream)

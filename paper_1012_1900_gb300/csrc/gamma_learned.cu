@@ -383,10 +383,10 @@ __global__ void k_cast_weights(const float* __restrict__ W1, const float* __rest
 // bytes apart, adjacent 8-row groups SBO = 128 bytes apart) and runs 128
 // feature rows at a time.  The rows arrive by TMA: each 64-column chunk is
 // eight boxes of 8 columns x 128 rows, which land in exactly that layout,
-// through two stages (one "full" and one "empty" mbarrier each).  One thread
+// through three stages (one "full" and one "empty" mbarrier each).  One thread
 // issues the copies and the MMAs: layer 1 accumulates X W1^T over the six
 // chunks in TMEM columns 0..127, and as soon as its last MMAs are committed
-// the first two chunks of the block's next tile are copied in, overlapping
+// the first three chunks of the block's next tile are copied in, overlapping
 // the rest of this tile.  The epilogues read TMEM with tcgen05.ld (warp w
 // reads lanes 32 (w % 4) .. +31), add the bias, apply the ReLU and write the
 // next layer's BF16 operand: H1 W2^T goes to columns 128..255, then H2 (over
@@ -397,6 +397,8 @@ __global__ void k_cast_weights(const float* __restrict__ W1, const float* __rest
 constexpr int kRows = 128;                 // rows per tile (MMA M)
 constexpr int kKc = 64;                    // K chunk of the streamed features
 constexpr int kNChunks = kInPad / kKc;     // 6
+constexpr int kXStages = 3;                // chunk stages in flight (divides kNChunks)
+static_assert(kNChunks % kXStages == 0, "chunk c of every tile must use stage c % kXStages");
 constexpr int kN3 = 16;                    // layer-3 N (4 outputs, padded)
 constexpr int kTmemCols = 256;
 
@@ -404,10 +406,10 @@ struct __align__(1024) TcSmem {
     bf16 W1[kH * kInPad];                  // rows 128, K 384 (core-matrix layout)
     bf16 W2[kH * kH];                      // rows 128, K 128
     bf16 H[kRows * kH];                    // H1, then H2 (rows 128, K 128)
-    bf16 Xc[2][kRows * kKc];               // feature chunks (TMA destinations)
+    bf16 Xc[kXStages][kRows * kKc];        // feature chunks (TMA destinations)
     bf16 W3[kN3 * kH];                     // rows 16, K 128 (rows >= kOut zero)
     float b1[kH], b2[kH], b3[kOutPad];
-    uint64_t xfull[2], xempty[2], mma;
+    uint64_t xfull[kXStages], xempty[kXStages], mma;
     uint32_t tmem;
     int ok;
 };
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_rows(const __grid_constant__ Mlp
     }
     if (tid < kOutPad) S.b3[tid] = W.b3[tid];
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kXStages; ++b) {
             mbar_init(&S.xfull[b], 1);
             mbar_init(&S.xempty[b], 1);
         }
@@ -513,10 +515,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_rows(const __grid_constant__ Mlp
     constexpr uint32_t kId128 = idesc_bf16_f32(kRows, kH), kId16 = idesc_bf16_f32(kRows, kN3);
     constexpr uint32_t kChunkBytes = kRows * kKc * 2;
     // thread 0's bookkeeping: loads issued into / consumed from each stage
-    uint32_t loads[2] = {0u, 0u}, used[2] = {0u, 0u};
+    uint32_t loads[kXStages] = {}, used[kXStages] = {};
     bool t0ok = true;
     auto issue = [&](long long tile, int c) {           // thread 0: chunk c of a tile
-        const int s = c & 1;
+        const int s = c % kXStages;
         if (loads[s] > 0 && t0ok)                        // the MMAs of the stage's last chunk
             t0ok = mbar_wait_bounded(&S.xempty[s], (loads[s] - 1) & 1u);
         if (!t0ok) return;
@@ -527,18 +529,16 @@ __global__ void __launch_bounds__(256, 1) k_mlp_rows(const __grid_constant__ Mlp
         ++loads[s];
     };
     uint32_t nmma = 0;                                   // phases of S.mma waited so far
-    if (tid == 0) {
-        issue(blockIdx.x, 0);
-        issue(blockIdx.x, 1);
-    }
+    if (tid == 0)
+        for (int c = 0; c < kXStages; ++c) issue(blockIdx.x, c);
     bool ok = true;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long long row0 = t * kRows;
         if (tid == 0) {
             // ---- layer 1: D1 = X W1^T over six chunks ----
             for (int c = 0; c < kNChunks && t0ok; ++c) {
-                const int s = c & 1;
-                if (c >= 2) issue(t, c);
+                const int s = c % kXStages;
+                if (c >= kXStages) issue(t, c);
                 if (!t0ok) break;
                 t0ok = mbar_wait_bounded(&S.xfull[s], used[s] & 1u);
                 if (!t0ok) break;
@@ -552,10 +552,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_rows(const __grid_constant__ Mlp
             }
             tc_commit(&S.mma);
             // the next tile's first chunks, while this tile finishes
-            if (t + gridDim.x < ntiles) {
-                issue(t + gridDim.x, 0);
-                issue(t + gridDim.x, 1);
-            }
+            if (t + gridDim.x < ntiles)
+                for (int c = 0; c < kXStages; ++c) issue(t + gridDim.x, c);
             if (!t0ok) S.ok = 0;
         }
         ok = mbar_wait_bounded(&S.mma, nmma & 1u) && ok;
@@ -610,7 +608,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_rows(const __grid_constant__ Mlp
     }
     if (tid == 0 && (!ok || !t0ok)) {
         atomicOr(flags, kFlagTimeout);
-        for (int b = 0; b < 2; ++b)                      // copies still in flight land first
+        for (int b = 0; b < kXStages; ++b)               // copies still in flight land first
             if (loads[b] > used[b]) mbar_wait_bounded(&S.xfull[b], used[b] & 1u);
     }
     tc_fence_before_sync();
@@ -676,33 +674,99 @@ struct SeedRows {
     __device__ unsigned item(unsigned r) const { return BATCH ? bd->seed_item[r] : P0->seed_list[r]; }
 };
 
-// Features of every seed row into the row buffer: one thread per eight
-// consecutive features of a row (their loads in flight together).
+// Features of every seed row into the row buffer.  One warp per row: the
+// warp stages the 7^N neighbourhood of the voxel (the 5^N patch and the
+// neighbours its gradients use) of both doses in shared memory, then each
+// lane computes eight consecutive features with the arithmetic of
+// voxel_feature and writes them as 16 bytes.
+constexpr int kBoxW = kPatch + 2;                    // 7
+template <int N>
+struct FeatBox {
+    static constexpr int ELEMS = N == 3 ? kBoxW * kBoxW * kBoxW : kBoxW * kBoxW;
+};
+
+template <int N>
+__device__ __forceinline__ float box_grad(const float* __restrict__ b, const Problem& P, const int (&c)[3],
+                                          int bi)
+{
+    // the same central / one-sided differences as grad_norm, from the box
+    const int n[3] = {P.nx, P.ny, P.nz};
+    const int st[3] = {1, kBoxW, kBoxW * kBoxW};
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        float d;
+        if (c[a] > 0 && c[a] < n[a] - 1) d = (b[bi + st[a]] - b[bi - st[a]]) / (2.f * P.hn[a]);
+        else if (c[a] == 0) d = (b[bi + st[a]] - b[bi]) / P.hn[a];
+        else d = (b[bi] - b[bi - st[a]]) / P.hn[a];
+        s = fmaf(d, d, s);
+    }
+    return sqrtf(s);
+}
+
 template <int N, bool BATCH>
 __global__ void __launch_bounds__(256) k_seed_features(const __grid_constant__ Problem P0,
                                                        const BatchDesc* __restrict__ bd)
 {
+    constexpr int E = FeatBox<N>::ELEMS;
+    __shared__ float sh_e[8][E], sh_r[8][E];
     const SeedRows<BATCH> rows{&P0, bd};
-    const long long total = (long long)rows.count() * (kInPad / 8);
+    const unsigned total = rows.count();
     bf16* X = rows.X();
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const unsigned r = (unsigned)(e / (kInPad / 8));
-        const int f0 = (int)(e % (kInPad / 8)) * 8;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    float* be = sh_e[wi];
+    float* br = sh_r[wi];
+    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned r = gw; r < total; r += nw) {               // warp-uniform
         const Problem& P = rows.prob(r);
         const unsigned v = P.tail_raw[rows.item(r)];
+        const int x = (int)(v % (unsigned)P.nx);
+        const unsigned r1 = v / (unsigned)P.nx;
+        const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
         const float dr = __ldg(P.ref + v);
         const float inv = 1.0f / (P.dd_frac * (P.local ? dr : resolve_dnorm(P)));
-        float val[8];
-        features8<N>(P, v, dr, inv, f0, val);
-        uint4 pk;
-        uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(val[2 * u], val[2 * u + 1]);
-            w[u] = *reinterpret_cast<const uint32_t*>(&b2);
+        // ---- the 7^N box around v (offsets -3 .. 3); outside the grid: 0 ----
+        __syncwarp();
+        for (int e = lane; e < E; e += 32) {
+            const int ox = e % kBoxW - 3, oy = (e / kBoxW) % kBoxW - 3, oz = N == 3 ? e / (kBoxW * kBoxW) - 3 : 0;
+            const int px = x + ox, py = y + oy, pz = z + oz;
+            const bool in = (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny &&
+                            (N == 2 || (unsigned)pz < (unsigned)P.nz);
+            const long long p = ((long long)pz * P.ny + py) * P.nx + px;
+            be[e] = in ? __ldg(P.ev + p) : 0.f;
+            br[e] = in ? __ldg(P.ref + p) : 0.f;
         }
-        *reinterpret_cast<uint4*>(X + (long long)r * kInPad + f0) = pk;
+        __syncwarp();
+        // ---- features f0 .. f0 + 7 per lane, 48 groups of eight ----
+        for (int gidx = lane; gidx < kInPad / 8; gidx += 32) {
+            const int f0 = gidx * 8;
+            float val[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int f = f0 + u;
+                val[u] = 0.f;
+                if (f >= kIn) continue;
+                const int ch = f / 125, pi = f % 125;
+                const int ox = pi % 5 - 2, oy = (pi / 5) % 5 - 2, oz = pi / 25 - 2;
+                if (N == 2 && oz != -2) continue;
+                const int c[3] = {x + ox, y + oy, N == 3 ? z + oz : 0};
+                if ((unsigned)c[0] >= (unsigned)P.nx || (unsigned)c[1] >= (unsigned)P.ny ||
+                    (N == 3 && (unsigned)c[2] >= (unsigned)P.nz))
+                    continue;
+                const int bi = ((N == 3 ? oz + 3 : 0) * kBoxW + (oy + 3)) * kBoxW + (ox + 3);
+                if (ch == 0) val[u] = fminf(fmaxf((be[bi] - dr) * inv, -16.f), 16.f);
+                else val[u] = fminf(box_grad<N>(ch == 1 ? be : br, P, c, bi) * inv, 32.f);
+            }
+            uint4 pk;
+            uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(val[2 * u], val[2 * u + 1]);
+                w[u] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+            *reinterpret_cast<uint4*>(X + (long long)r * kInPad + f0) = pk;
+        }
     }
 }
 
