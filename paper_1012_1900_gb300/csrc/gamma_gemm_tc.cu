@@ -3,14 +3,17 @@
 //
 //     C[m][n] (+)= sum_k A[m][k] B[n][k]        (A: M x K, B: N x K, both K-major)
 //
-// One block of 128 threads computes a 128 x BN tile of C.  Thread 0 streams the
-// K dimension in chunks of 64 through two shared-memory stages: each chunk of A
+// One block of 128 threads computes a 128 x BN tile of C (BN 128, or 64 when
+// that gives the SMs more blocks, or 16 for the output layer).  Thread 0
+// streams the K dimension in chunks of 64 through three shared-memory stages,
+// each chunk's copy issued two chunks ahead of its MMAs: each chunk of A
 // and B arrives by TMA as eight 16-byte-wide column slices (one box of 8 x 128
 // or 8 x BN elements each), which is exactly the no-swizzle K-major core-matrix
 // layout the MMA descriptors expect (adjacent 8-row groups 128 bytes apart,
 // adjacent 8-column slices rows * 16 bytes apart).  It issues four
 // tcgen05.mma (K = 16) per chunk into one TMEM accumulator and commits them to
-// the stage's mbarrier, which frees the stage for the copy two chunks later.
+// the stage's mbarrier, which frees the stage for the copy three chunks later.
+// A product split over K runs about two blocks per SM, which add their tiles.
 // After the last commit the four warps read their 32 TMEM lanes and store (or,
 // split over K, atomically add) the FP32 tile.  Rows and columns past the
 // matrices' ends are filled with zeros by the copies and never stored.  Every
@@ -33,12 +36,13 @@ namespace {
 
 constexpr int kGemmBM = 128;             // rows per tile (MMA M)
 constexpr int kGemmBK = 64;              // K per stage
+constexpr int kGemmStages = 3;           // stages in flight
 
 template <int BN>
 struct GemmSmem {
-    bf16 A[2][kGemmBM * kGemmBK];        // per stage: 8 slices of 128 rows x 16 bytes
-    bf16 B[2][BN * kGemmBK];             // per stage: 8 slices of BN rows x 16 bytes
-    uint64_t full[2], empty[2], done;
+    bf16 A[kGemmStages][kGemmBM * kGemmBK];   // per stage: 8 slices of 128 rows x 16 bytes
+    bf16 B[kGemmStages][BN * kGemmBK];        // per stage: 8 slices of BN rows x 16 bytes
+    uint64_t full[kGemmStages], empty[kGemmStages], done;
     uint32_t tmem;
     int ok;
 };
@@ -49,7 +53,7 @@ __global__ void __launch_bounds__(128, 1)
               int M, int N, int nchunks, int chunks_per_split, float* __restrict__ C, int ldc,
               unsigned* flags)
 {
-    static_assert(BN == 16 || BN == 128, "tile width");
+    static_assert(BN == 16 || BN == 64 || BN == 128, "tile width");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the stages start on a 1 KB boundary (TMA destinations: 128 bytes)
     unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -61,7 +65,7 @@ __global__ void __launch_bounds__(128, 1)
     if (c0 >= c1) return;                                 // block-uniform: an empty K split
     constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kGemmStages; ++b) {
             mbar_init(&S.full[b], 1);
             mbar_init(&S.empty[b], 1);
         }
@@ -80,24 +84,33 @@ __global__ void __launch_bounds__(128, 1)
     if (tid == 0) {
         constexpr uint32_t kId = idesc_bf16_f32(kGemmBM, BN);
         constexpr uint32_t kBytes = (kGemmBM + BN) * kGemmBK * 2;
-        uint32_t nfull[2] = {0u, 0u}, nempty[2] = {0u, 0u};
-        bool pending[2] = {false, false};                 // a copy issued but not yet seen landed
+        uint32_t nfull[kGemmStages] = {}, nempty[kGemmStages] = {};
+        bool pending[kGemmStages] = {};                   // a copy issued but not yet seen landed
         bool ok = true;
-        for (int c = c0; c < c1 && ok; ++c) {
-            const int s = (c - c0) & 1;
-            if (c - c0 >= 2) {                            // the MMAs two chunks back read this stage
+        // chunk i (from c0) goes to stage i % kGemmStages; its copy is issued
+        // kGemmStages - 1 chunks ahead of its MMAs
+        auto load = [&](int i) {
+            const int s = i % kGemmStages;
+            if (i >= kGemmStages) {                       // the MMAs of chunk i - kGemmStages read it
                 ok = mbar_wait_bounded(&S.empty[s], nempty[s] & 1u);
                 ++nempty[s];
-                if (!ok) break;
+                if (!ok) return;
             }
             mbar_arrive_expect_tx(&S.full[s], kBytes);
             pending[s] = true;
-            const int k0 = c * kGemmBK;
+            const int k0 = (c0 + i) * kGemmBK;
 #pragma unroll
             for (int j = 0; j < kGemmBK / 8; ++j) {
                 tma_load_2d(&S.A[s][j * kGemmBM * 8], &amap, k0 + 8 * j, m0, &S.full[s]);
                 tma_load_2d(&S.B[s][j * BN * 8], &bmap, k0 + 8 * j, n0, &S.full[s]);
             }
+        };
+        const int nloc = c1 - c0;
+        for (int i = 0; i < kGemmStages - 1 && i < nloc && ok; ++i) load(i);
+        for (int c = c0; c < c1 && ok; ++c) {
+            const int i = c - c0, s = i % kGemmStages;
+            if (i + kGemmStages - 1 < nloc) load(i + kGemmStages - 1);
+            if (!ok) break;
             ok = mbar_wait_bounded(&S.full[s], nfull[s] & 1u);
             if (!ok) break;
             pending[s] = false;
@@ -116,7 +129,7 @@ __global__ void __launch_bounds__(128, 1)
         if (!ok) {
             S.ok = 0;
             // let this block's copies land before it leaves
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < kGemmStages; ++b)
                 if (pending[b]) mbar_wait_bounded(&S.full[b], nfull[b] & 1u);
         }
     }
@@ -173,7 +186,9 @@ cudaError_t launch_gemm_tc(const bf16* A, long long M, long long lda, const bf16
 {
     if (M <= 0 || N <= 0 || K <= 0 || splits < 1) return cudaErrorInvalidValue;
     if ((lda % 8) || (ldb % 8) || (((uintptr_t)A | (uintptr_t)B) & 15u)) return cudaErrorInvalidValue;
-    const int bn = N <= 16 ? 16 : 128;
+    const long long mtiles = (M + kGemmBM - 1) / kGemmBM;
+    // the widest tile that still gives every SM a block (else 64 columns)
+    const int bn = N <= 16 ? 16 : (mtiles * ((N + 127) / 128) >= device_sm_count() ? 128 : 64);
     CUtensorMap am, bm;
     // A: K x M elements (inner, rows), boxes of 8 x 128; B: K x N, boxes of 8 x bn
     if (!encode_bf16_2d(&am, A, (unsigned long long)K, (unsigned long long)M,
@@ -182,6 +197,12 @@ cudaError_t launch_gemm_tc(const bf16* A, long long M, long long lda, const bf16
                         (unsigned long long)ldb * 2, 8, (unsigned)bn))
         return cudaErrorInvalidValue;
     const int nchunks = (int)((K + kGemmBK - 1) / kGemmBK);
+    if (splits > 1) {
+        // a split-K product: about two blocks per SM
+        const long long tiles = mtiles * ((N + bn - 1) / bn);
+        splits = (int)std::max<long long>(splits, (2LL * device_sm_count() + tiles - 1) / tiles);
+        splits = std::min(splits, std::max(1, nchunks / 4));   // at least 4 chunks a block
+    }
     splits = std::min(splits, nchunks);
     const int per = (nchunks + splits - 1) / splits;
     splits = (nchunks + per - 1) / per;
@@ -189,6 +210,10 @@ cudaError_t launch_gemm_tc(const bf16* A, long long M, long long lda, const bf16
     if (bn == 16) {
         return atomic ? launch_gemm_tc_k<16, true>(am, bm, M, N, nchunks, per, splits, C, ldc, flags, s)
                       : launch_gemm_tc_k<16, false>(am, bm, M, N, nchunks, per, splits, C, ldc, flags, s);
+    }
+    if (bn == 64) {
+        return atomic ? launch_gemm_tc_k<64, true>(am, bm, M, N, nchunks, per, splits, C, ldc, flags, s)
+                      : launch_gemm_tc_k<64, false>(am, bm, M, N, nchunks, per, splits, C, ldc, flags, s);
     }
     return atomic ? launch_gemm_tc_k<128, true>(am, bm, M, N, nchunks, per, splits, C, ldc, flags, s)
                   : launch_gemm_tc_k<128, false>(am, bm, M, N, nchunks, per, splits, C, ldc, flags, s);

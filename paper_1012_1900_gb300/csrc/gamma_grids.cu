@@ -7,10 +7,13 @@
 //   k_grid_prepare  max of the reference dose (the global dose norm) and a
 //                   finite check of both grids
 //   k_grid_walk     one thread per reference voxel: the evaluation cell that
-//                   contains the voxel (clamped to the grid), then the cell
-//                   table in key order with the exact stop of A1 step 4b-ii,
-//                   every face of every cell reached (real-valued cell
-//                   offsets; FP64 redo when a Gram matrix is near singular)
+//                   contains the voxel (clamped to the grid) first, then the
+//                   cell table in key order with the exact stop of A1 step
+//                   4b-ii; a cell is skipped when the distance from the
+//                   reference point to its box, with its dose gap, already
+//                   reaches the running gamma, else every face of it is
+//                   evaluated (real-valued cell offsets; FP64 redo when a
+//                   Gram matrix is near singular)
 //
 // The table is keyed by the distance between the box of the voxel's cell and
 // the box of the other cell, divided by the DTA: a lower bound on the distance
@@ -140,18 +143,30 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
         }
         const float dD = G.dd_frac * (G.local ? dr : dnorm);
         const float inv = 1.0f / dD;
-        float best = kInf;
+        // the cell that holds the voxel (clamped to the grid) first: a finite
+        // bound from the start
+        float best = grid_cell<N>(G, c0, u, 0.f, dr, inv, dnorm, kInf);
         int t = 0;
         for (; t < G.ntable; ++t) {
             const TableEntry e = G.table[t];
             if (e.key * e.key >= best) break;                 // A1 step 4b-ii, exact
-            const int p[3] = {c0[0] + unpack10(e.off, 0), c0[1] + unpack10(e.off, 10),
-                              N == 3 ? c0[2] + unpack10(e.off, 20) : 0};
+            const int d[3] = {unpack10(e.off, 0), unpack10(e.off, 10), N == 3 ? unpack10(e.off, 20) : 0};
+            if ((d[0] | d[1] | d[2]) == 0) continue;          // done above
+            const int p[3] = {c0[0] + d[0], c0[1] + d[1], c0[2] + d[2]};
             bool in = true;
+            // the spatial distance from the reference point itself to the
+            // cell box: a tighter lower bound than the key of the table (which
+            // bounds it from any point of the voxel's cell)
+            float k2 = 0.f;
 #pragma unroll
-            for (int a = 0; a < N; ++a) in = in && p[a] >= 0 && p[a] < G.en[a];
-            if (!in) continue;
-            best = grid_cell<N>(G, p, u, e.key, dr, inv, dnorm, best);
+            for (int a = 0; a < N; ++a) {
+                in = in && p[a] >= 0 && p[a] < G.en[a];
+                const double lo = (double)p[a] - u[a], hi = u[a] - (double)(p[a] + 1);
+                const float gap = (float)(fmax(fmax(lo, hi), 0.0) * G.eh[a]);
+                k2 = fmaf(gap, gap, k2);
+            }
+            if (!in || k2 >= best) continue;
+            best = grid_cell<N>(G, p, u, sqrtf(fmaxf(k2, e.key * e.key)), dr, inv, dnorm, best);
         }
         if (t >= G.ntable && best > rc2) {
             // past a truncated table: every remaining cell of the search box
