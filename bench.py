@@ -375,13 +375,19 @@ NCU_FIELDS = {
     "dram__bytes_read.sum": "dram_read_bytes",
     "dram__bytes_write.sum": "dram_write_bytes",
     "smsp__inst_executed.sum": "warp_inst_per_launch",
-    "smsp__thread_inst_executed.sum": "thread_inst_per_launch",
+    "smsp__thread_inst_executed_per_inst_executed.ratio": "lane_efficiency",
     "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active": "fma_pipe_pct",
     "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active": "alu_pipe_pct",
     "sm__warps_active.avg.pct_of_peak_sustained_active": "warps_active_pct",
-    "sm__inst_issued.avg.pct_of_peak_sustained_active": "issue_active_pct",
+    "smsp__issue_active.avg.pct_of_peak_sustained_active": "issue_active_pct",
+    "smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio": "long_scoreboard_per_issue",
+    "l1tex__t_sector_hit_rate.pct": "l1_hit_pct",
+    "lts__t_sector_hit_rate.pct": "l2_hit_pct",
     "launch__registers_per_thread": "registers",
 }
+# units of the raw page, to bytes and nanoseconds
+NCU_UNITS = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12,
+             "ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6}
 
 
 def recorded_counters(kernel: str, workload: str):
@@ -418,6 +424,7 @@ def record_counters(csv_path: str, workload: str, capture: str) -> dict:
         rows = [r for r in csv.reader(f) if r]
     head = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     names = rows[head]
+    units = rows[head + 1] if len(rows) > head + 1 else [""] * len(names)
     data = [r for r in rows[head + 1:] if len(r) == len(names) and r[names.index("Kernel Name")]]
     try:
         with open(COUNTERS_PATH) as f:
@@ -433,8 +440,9 @@ def record_counters(csv_path: str, workload: str, capture: str) -> dict:
                "kernel_name": r[names.index("Kernel Name")]}
         for metric, field in NCU_FIELDS.items():
             if metric in names:
+                i = names.index(metric)
                 try:
-                    rec[field] = float(r[names.index(metric)].replace(",", ""))
+                    rec[field] = float(r[i].replace(",", "")) * NCU_UNITS.get(units[i].strip(), 1.0)
                 except ValueError:
                     pass
         if "dram_read_bytes" not in rec:
@@ -776,8 +784,9 @@ def run_ours(args, pair, rank, world, local_rank):
             return {"warp_inst": rec["warp_inst_per_launch"],
                     "frac": rec["warp_inst_per_launch"] / (n_sm * 4 * clock_hz * ms / 1e3),
                     "fma_pipe_pct": rec.get("fma_pipe_pct"), "alu_pipe_pct": rec.get("alu_pipe_pct"),
-                    "lane_efficiency": (rec["thread_inst_per_launch"] / rec["warp_inst_per_launch"]
-                                        if rec.get("thread_inst_per_launch") else None)}
+                    "lane_efficiency": rec.get("lane_efficiency"),
+                    "issue_active_pct_ncu": rec.get("issue_active_pct"),
+                    "warps_active_pct": rec.get("warps_active_pct")}
         roofline = {"bound": "alu", "kernel": f"k_shell+{walker}", "achieved": achieved,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                     "traffic": None if None in traffic else sum(traffic),

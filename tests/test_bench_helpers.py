@@ -65,13 +65,13 @@ def test_record_counters_reads_an_ncu_raw_csv(tmp_path, monkeypatch):
     # names, a row of units, then one row per captured launch
     csv_text = (
         '"ID","Kernel Name","gpu__time_duration.sum","dram__bytes_read.sum","dram__bytes_write.sum",'
-        '"smsp__inst_executed.sum","smsp__thread_inst_executed.sum",'
+        '"smsp__inst_executed.sum","smsp__thread_inst_executed_per_inst_executed.ratio",'
         '"sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active"\n'
-        '"","","ns","byte","byte","inst","inst","%"\n'
-        '"0","void gk::k_shell<3, 4, false>(gk::Problem, CUtensorMap_st, int)","80,000","25,467,904","0",'
-        '"7,000,000","190,000,000","22.1"\n'
-        '"1","void gk::k_walk<3, 2>(gk::Problem, CUtensorMap_st, int)","40,000","9,000,000","1,000",'
-        '"3,000,000","60,000,000","30.5"\n')
+        '"","","us","Mbyte","Kbyte","inst","","%"\n'
+        '"0","void gk::k_shell<3, 4, false>(gk::Problem, CUtensorMap_st, int)","80","25.467904","0",'
+        '"7,000,000","27.1","22.1"\n'
+        '"1","void gk::k_walk<3, 2>(gk::Problem, CUtensorMap_st, int)","40","9","1",'
+        '"3,000,000","20","30.5"\n')
     src = tmp_path / "raw.csv"
     src.write_text(csv_text)
     monkeypatch.setattr(bench, "COUNTERS_PATH", str(tmp_path / "counters.json"))
@@ -80,5 +80,7 @@ def test_record_counters_reads_an_ncu_raw_csv(tmp_path, monkeypatch):
     assert out["k_shell"]["dram_read_bytes"] == 25467904
     assert out["k_walk"]["warp_inst_per_launch"] == 3e6
     assert out["k_walk"]["fma_pipe_pct"] == 30.5
+    assert out["k_walk"]["lane_efficiency"] == 20.0
+    assert out["k_shell"]["ncu_duration_ns"] == 80000
     assert bench.recorded_traffic("k_walk", "imrt_160") == 9001000
     assert bench.recorded_traffic("k_walk", "plane_128") is None
