@@ -146,6 +146,14 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
         // the cell that holds the voxel (clamped to the grid) first: a finite
         // bound from the start
         float best = grid_cell<N>(G, c0, u, 0.f, dr, inv, dnorm, kInf);
+        // the point's position in its cell (voxel units; outside [0, 1) when
+        // the voxel lies beyond the evaluation grid), for the distance bound
+        float fr[3] = {0.f, 0.f, 0.f}, ehf[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            fr[a] = (float)(u[a] - (double)c0[a]);
+            ehf[a] = (float)G.eh[a];
+        }
         int t = 0;
         for (; t < G.ntable; ++t) {
             const TableEntry e = G.table[t];
@@ -156,15 +164,20 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
             bool in = true;
             // the spatial distance from the reference point itself to the
             // cell box: a tighter lower bound than the key of the table (which
-            // bounds it from any point of the voxel's cell)
+            // bounds it from any point of the voxel's cell); in FP32 from the
+            // integer offset and the point's fraction, each axis lowered by
+            // the rounding of that arithmetic (4 ulp of its operands) and the
+            // sum by 1e-5, so that it stays a lower bound
             float k2 = 0.f;
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 in = in && p[a] >= 0 && p[a] < G.en[a];
-                const double lo = (double)p[a] - u[a], hi = u[a] - (double)(p[a] + 1);
-                const float gap = (float)(fmax(fmax(lo, hi), 0.0) * G.eh[a]);
+                const float lo = (float)d[a] - fr[a], hi = fr[a] - (float)(d[a] + 1);
+                const float slack = 4.8e-7f * (fabsf(fr[a]) + fabsf((float)d[a]) + 2.f);
+                const float gap = fmaxf(fmaxf(lo, hi) - slack, 0.f) * ehf[a];
                 k2 = fmaf(gap, gap, k2);
             }
+            k2 *= 0.99999f;
             if (!in || k2 >= best) continue;
             best = grid_cell<N>(G, p, u, sqrtf(fmaxf(k2, e.key * e.key)), dr, inv, dnorm, best);
         }

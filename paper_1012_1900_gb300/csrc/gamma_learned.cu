@@ -45,10 +45,11 @@ __device__ __forceinline__ float grad_norm(const float* __restrict__ D, const Pr
     float s = 0.f;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
+        // the same arithmetic as the seeding pass's features (box_grad2)
         float d;
-        if (c[a] > 0 && c[a] < n[a] - 1) d = (__ldg(D + p + st[a]) - __ldg(D + p - st[a])) / (2.f * P.hn[a]);
-        else if (c[a] == 0) d = (__ldg(D + p + st[a]) - __ldg(D + p)) / P.hn[a];
-        else d = (__ldg(D + p) - __ldg(D + p - st[a])) / P.hn[a];
+        if (c[a] > 0 && c[a] < n[a] - 1) d = (__ldg(D + p + st[a]) - __ldg(D + p - st[a])) * (0.5f / P.hn[a]);
+        else if (c[a] == 0) d = (__ldg(D + p + st[a]) - __ldg(D + p)) * (1.f / P.hn[a]);
+        else d = (__ldg(D + p) - __ldg(D + p - st[a])) * (1.f / P.hn[a]);
         s = fmaf(d, d, s);
     }
     return sqrtf(s);
@@ -677,38 +678,20 @@ struct SeedRows {
 // Features of every seed row into the row buffer.  One warp per row: the
 // warp stages the 7^N neighbourhood of the voxel (the 5^N patch and the
 // neighbours its gradients use) of both doses in shared memory, then each
-// lane computes eight consecutive features with the arithmetic of
-// voxel_feature and writes them as 16 bytes.
+// lane takes patch points and computes their three channels together, with
+// the arithmetic of voxel_feature (so the features equal gamma_features').
 constexpr int kBoxW = kPatch + 2;                    // 7
 template <int N>
 struct FeatBox {
     static constexpr int ELEMS = N == 3 ? kBoxW * kBoxW * kBoxW : kBoxW * kBoxW;
 };
 
-template <int N>
-__device__ __forceinline__ float box_grad(const float* __restrict__ b, const Problem& P, const int (&c)[3],
-                                          int bi)
-{
-    // the same central / one-sided differences as grad_norm, from the box
-    const int n[3] = {P.nx, P.ny, P.nz};
-    const int st[3] = {1, kBoxW, kBoxW * kBoxW};
-    float s = 0.f;
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-        float d;
-        if (c[a] > 0 && c[a] < n[a] - 1) d = (b[bi + st[a]] - b[bi - st[a]]) / (2.f * P.hn[a]);
-        else if (c[a] == 0) d = (b[bi + st[a]] - b[bi]) / P.hn[a];
-        else d = (b[bi] - b[bi - st[a]]) / P.hn[a];
-        s = fmaf(d, d, s);
-    }
-    return sqrtf(s);
-}
-
 template <int N, bool BATCH>
 __global__ void __launch_bounds__(256) k_seed_features(const __grid_constant__ Problem P0,
                                                        const BatchDesc* __restrict__ bd)
 {
     constexpr int E = FeatBox<N>::ELEMS;
+    constexpr int NP = N == 3 ? 125 : 25;            // patch points used
     __shared__ float sh_e[8][E], sh_r[8][E];
     const SeedRows<BATCH> rows{&P0, bd};
     const unsigned total = rows.count();
@@ -718,6 +701,7 @@ __global__ void __launch_bounds__(256) k_seed_features(const __grid_constant__ P
     float* br = sh_r[wi];
     const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    const int bst[3] = {1, kBoxW, kBoxW * kBoxW};
     for (unsigned r = gw; r < total; r += nw) {               // warp-uniform
         const Problem& P = rows.prob(r);
         const unsigned v = P.tail_raw[rows.item(r)];
@@ -726,8 +710,16 @@ __global__ void __launch_bounds__(256) k_seed_features(const __grid_constant__ P
         const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
         const float dr = __ldg(P.ref + v);
         const float inv = 1.0f / (P.dd_frac * (P.local ? dr : resolve_dnorm(P)));
+        const int n[3] = {P.nx, P.ny, P.nz};
+        float c1[3], c2[3];                                   // one-sided and central factors
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            c1[a] = 1.f / P.hn[a];
+            c2[a] = 0.5f / P.hn[a];
+        }
         // ---- the 7^N box around v (offsets -3 .. 3); outside the grid: 0 ----
         __syncwarp();
+#pragma unroll 4
         for (int e = lane; e < E; e += 32) {
             const int ox = e % kBoxW - 3, oy = (e / kBoxW) % kBoxW - 3, oz = N == 3 ? e / (kBoxW * kBoxW) - 3 : 0;
             const int px = x + ox, py = y + oy, pz = z + oz;
@@ -738,35 +730,45 @@ __global__ void __launch_bounds__(256) k_seed_features(const __grid_constant__ P
             br[e] = in ? __ldg(P.ref + p) : 0.f;
         }
         __syncwarp();
-        // ---- features f0 .. f0 + 7 per lane, 48 groups of eight ----
-        for (int gidx = lane; gidx < kInPad / 8; gidx += 32) {
-            const int f0 = gidx * 8;
-            float val[8];
+        // ---- the three channels of one patch point per lane ----
+        bf16* xr = X + (long long)r * kInPad;
+        for (int pi = lane; pi < 125; pi += 32) {
+            float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+            if (pi < NP) {
+                const int o[3] = {pi % 5 - 2, (pi / 5) % 5 - 2, N == 3 ? pi / 25 - 2 : 0};
+                const int c[3] = {x + o[0], y + o[1], z + o[2]};
+                if ((unsigned)c[0] < (unsigned)P.nx && (unsigned)c[1] < (unsigned)P.ny &&
+                    (N == 2 || (unsigned)c[2] < (unsigned)P.nz)) {
+                    const int bi = ((o[2] + (N == 3 ? 3 : 0)) * kBoxW + (o[1] + 3)) * kBoxW + (o[0] + 3);
+                    f0 = fminf(fmaxf((be[bi] - dr) * inv, -16.f), 16.f);
+                    // the gradients of both doses (central differences inside,
+                    // one-sided at the grid edge), as grad_norm takes them
+                    float se = 0.f, sr = 0.f;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int f = f0 + u;
-                val[u] = 0.f;
-                if (f >= kIn) continue;
-                const int ch = f / 125, pi = f % 125;
-                const int ox = pi % 5 - 2, oy = (pi / 5) % 5 - 2, oz = pi / 25 - 2;
-                if (N == 2 && oz != -2) continue;
-                const int c[3] = {x + ox, y + oy, N == 3 ? z + oz : 0};
-                if ((unsigned)c[0] >= (unsigned)P.nx || (unsigned)c[1] >= (unsigned)P.ny ||
-                    (N == 3 && (unsigned)c[2] >= (unsigned)P.nz))
-                    continue;
-                const int bi = ((N == 3 ? oz + 3 : 0) * kBoxW + (oy + 3)) * kBoxW + (ox + 3);
-                if (ch == 0) val[u] = fminf(fmaxf((be[bi] - dr) * inv, -16.f), 16.f);
-                else val[u] = fminf(box_grad<N>(ch == 1 ? be : br, P, c, bi) * inv, 32.f);
+                    for (int a = 0; a < N; ++a) {
+                        float de, dq;
+                        if (c[a] > 0 && c[a] < n[a] - 1) {
+                            de = (be[bi + bst[a]] - be[bi - bst[a]]) * c2[a];
+                            dq = (br[bi + bst[a]] - br[bi - bst[a]]) * c2[a];
+                        } else if (c[a] == 0) {
+                            de = (be[bi + bst[a]] - be[bi]) * c1[a];
+                            dq = (br[bi + bst[a]] - br[bi]) * c1[a];
+                        } else {
+                            de = (be[bi] - be[bi - bst[a]]) * c1[a];
+                            dq = (br[bi] - br[bi - bst[a]]) * c1[a];
+                        }
+                        se = fmaf(de, de, se);
+                        sr = fmaf(dq, dq, sr);
+                    }
+                    f1 = fminf(sqrtf(se) * inv, 32.f);
+                    f2 = fminf(sqrtf(sr) * inv, 32.f);
+                }
             }
-            uint4 pk;
-            uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn(val[2 * u], val[2 * u + 1]);
-                w[u] = *reinterpret_cast<const uint32_t*>(&b2);
-            }
-            *reinterpret_cast<uint4*>(X + (long long)r * kInPad + f0) = pk;
+            xr[pi] = __float2bfloat16(f0);
+            xr[125 + pi] = __float2bfloat16(f1);
+            xr[250 + pi] = __float2bfloat16(f2);
         }
+        if (lane < kInPad - kIn) xr[kIn + lane] = __float2bfloat16(0.f);
     }
 }
 
