@@ -206,7 +206,11 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     memory (one TMA copy) and walks the table for that
  *                     tile's queued voxels, the lanes per voxel chosen per
  *                     tile (same results; slower on the benchmark workloads,
- *                     where a tile waits for its most expensive voxel)
+ *                     where a tile waits for its most expensive voxel); 2: row
+ *                     by row: each warp independently takes one 32-voxel row
+ *                     of a shell tile with queued voxels, stages the doses
+ *                     around it in shared memory (one TMA copy) and walks the
+ *                     table for the row's queued voxels (same results)
  *  "lanes_per_voxel"  2, 4, 8, 16 or 32 lanes search one queued voxel together
  *                     (the voxel-by-voxel walk)
  *  "table_cap"        maximum cell-table length (rebuilds the table)

@@ -110,7 +110,12 @@ struct gamma_ctx {
     unsigned* tile_list = nullptr;
     unsigned char* tile_bkt = nullptr;
     unsigned* tile_sorted = nullptr;
-    int walk = 0;                     // 1: tile-staged walk (k_walk); 0: voxel queue walk (k_tail)
+    // row-staged walk: one item per shell warp row with queued voxels
+    unsigned long long* row_items = nullptr;
+    unsigned char* row_bkt = nullptr;
+    unsigned long long* row_sorted = nullptr;
+    int walk = 0;                     // 0: voxel queue walk (k_tail); 1: tile-staged (k_walk);
+                                      // 2: row-staged (k_walk_rows)
     // options
     int lanes = gk::kDefaultLanesPerVoxel;
     double tau = 1e-6;
@@ -298,11 +303,16 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.seed_X = h->seed_X;
     P.seed_Y = h->seed_Y;
     P.seed_cap = h->seed_cap;
-    if (h->walk && h->tile_mask) {
+    if (h->walk == 1 && h->tile_mask) {
         P.tile_mask = h->tile_mask;
         P.tile_list = h->tile_list;
         P.tile_bkt = h->tile_bkt;
         P.tile_sorted = h->tile_sorted;
+    }
+    if (h->walk == 2 && h->row_items) {
+        P.row_items = h->row_items;
+        P.row_bkt = h->row_bkt;
+        P.row_sorted = h->row_sorted;
     }
     return P;
 }
@@ -339,6 +349,9 @@ void free_ctx(gamma_ctx* h)
     cudaFree(h->tile_list);
     cudaFree(h->tile_bkt);
     cudaFree(h->tile_sorted);
+    cudaFree(h->row_items);
+    cudaFree(h->row_bkt);
+    cudaFree(h->row_sorted);
     cudaFree(h->seed_list);
     cudaFree(h->seed_X);
     cudaFree(h->seed_Y);
@@ -632,7 +645,10 @@ int gamma_create(gamma_handle* out, const float* ref_dev, const float* eval_dev,
         if ((e = cudaMalloc(&h->tile_mask, sizeof(unsigned) * 8 * nt)) != cudaSuccess ||
             (e = cudaMalloc(&h->tile_list, sizeof(unsigned) * nt)) != cudaSuccess ||
             (e = cudaMalloc(&h->tile_bkt, nt)) != cudaSuccess ||
-            (e = cudaMalloc(&h->tile_sorted, sizeof(unsigned) * nt)) != cudaSuccess)
+            (e = cudaMalloc(&h->tile_sorted, sizeof(unsigned) * nt)) != cudaSuccess ||
+            (e = cudaMalloc(&h->row_items, sizeof(unsigned long long) * 8 * nt)) != cudaSuccess ||
+            (e = cudaMalloc(&h->row_bkt, 8 * nt)) != cudaSuccess ||
+            (e = cudaMalloc(&h->row_sorted, sizeof(unsigned long long) * 8 * nt)) != cudaSuccess)
             return fail(cuda_fail(e));
     }
     if (!ref_dev) {
@@ -758,7 +774,11 @@ int gamma_set_inputs(gamma_handle h, const float* ref_dev, const float* eval_dev
 // (k_walk) or voxel by voxel (k_tail).  tm: record the "order" event between.
 static int enqueue_walk(gamma_handle h, const Problem& P, cudaStream_t s, bool tm)
 {
-    if (P.tile_mask) {
+    if (P.row_items) {
+        CK(gk::launch_order_rows(P, s));
+        if (tm) CK(cudaEventRecord(h->tev[4], s));
+        CK(gk::launch_walk_rows(P, h->tail_minblocks, s));
+    } else if (P.tile_mask) {
         CK(gk::launch_order_tiles(P, s));
         if (tm) CK(cudaEventRecord(h->tev[4], s));
         CK(gk::launch_walk(P, h->tail_minblocks, s));
@@ -1198,7 +1218,7 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "walk")) {
-        if (h->batch || value < 0 || value > 1) return GAMMA_ERR_INVALID_ARG;
+        if (h->batch || value < 0 || value > 2) return GAMMA_ERR_INVALID_ARG;
         h->walk = (int)value;
         return GAMMA_OK;
     }
@@ -1425,7 +1445,7 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     int rc = GAMMA_OK;
     auto run = [&]() { return h->batch ? gamma_batch_run(h, s) : gamma_run(h, gamma_out_dev, s); };
     // the tile-staged walk picks its lanes per tile: only the block budgets vary
-    const bool tile_walk = !h->batch && !h->grids && h->walk && h->tile_mask;
+    const bool tile_walk = !h->batch && !h->grids && h->walk != 0 && h->tile_mask;
     const int nl = tile_walk ? 1 : 5;
     for (int li = 0; li < nl && rc == GAMMA_OK; ++li)
         for (int bl = 1; bl <= 4 && rc == GAMMA_OK; ++bl)

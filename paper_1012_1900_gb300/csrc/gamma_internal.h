@@ -80,6 +80,10 @@ struct Counters {
     unsigned int tile_head;             // work counter of the tile-staged walk
     unsigned int tile_hist[kNumBuckets];    // those tiles by their largest cost bucket
     unsigned int tile_cursor[kNumBuckets];
+    unsigned int row_count;             // shell warp rows with at least one queued voxel
+    unsigned int row_head;              // work counter of the row-staged walk
+    unsigned int row_hist[kNumBuckets]; // those rows by their largest cost bucket
+    unsigned int row_cursor[kNumBuckets];
 };
 
 // Order-preserving encoding of a float into an unsigned int (for atomicMax).
@@ -141,6 +145,12 @@ struct Problem {
     unsigned* tile_list;
     unsigned char* tile_bkt;
     unsigned* tile_sorted;
+    // row-staged walk (null: not used): per shell warp row with queued voxels
+    // one item (row id = tile * 8 + warp in the high word, queue mask in the
+    // low word) with its largest cost bucket, and the items in cost order
+    unsigned long long* row_items;
+    unsigned char* row_bkt;
+    unsigned long long* row_sorted;
 };
 
 // Readiness of the evaluation dose by z slab, for a shell launch that starts
@@ -223,6 +233,12 @@ cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblock
 // shared memory and walks the table for the tile's queued voxels.
 cudaError_t launch_order_tiles(const Problem& P, cudaStream_t s);
 cudaError_t launch_walk(const Problem& P, int walk_minblocks, cudaStream_t s);
+// Row-staged walk (P.row_items set): order the shell's warp rows with queued
+// voxels by cost, then every warp takes one row at a time, stages the row's
+// evaluation-dose halo box in shared memory and walks the table for the
+// row's queued voxels.
+cudaError_t launch_order_rows(const Problem& P, cudaStream_t s);
+cudaError_t launch_walk_rows(const Problem& P, int walk_minblocks, cudaStream_t s);
 int device_sm_count();
 
 // Host-side constants a Problem needs before it is uploaded for a batch.

@@ -348,6 +348,18 @@ __global__ void __launch_bounds__(256, MINB)
                 if (lane == 0) atomicMax(&sh_tb[buf], bm);
             }
         }
+        if (!BATCH && P.row_items && tm) {
+            // this warp row's item for the row-staged walk
+            unsigned bm = tail ? (unsigned)bucket : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(kFull, bm, o));
+            if (lane == 0) {
+                const unsigned ip = atomicAdd(&P.ctr->row_count, 1u);
+                P.row_items[ip] = ((unsigned long long)((unsigned)lt * 8u + (threadIdx.x >> 5)) << 32) | tm;
+                P.row_bkt[ip] = (unsigned char)bm;
+                atomicAdd(&P.ctr->row_hist[bm], 1u);
+            }
+        }
         if (tm) {
             unsigned pos0 = 0;
             if (lane == 0) pos0 = atomicAdd(&P.ctr->tail_count, (unsigned)__popc(tm));
@@ -453,6 +465,38 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const __grid_constant__ P
             base[threadIdx.x] = start[threadIdx.x] + atomicAdd(&P.ctr->tile_cursor[threadIdx.x], cnt[threadIdx.x]);
         __syncthreads();
         if (b >= 0) P.tile_sorted[base[b] + rank] = P.tile_list[i];
+        __syncthreads();
+    }
+}
+
+// The warp rows with queued voxels in order of their largest cost bucket,
+// most expensive first (same scheme as k_scatter).
+__global__ void __launch_bounds__(256) k_scatter_rows(const __grid_constant__ Problem P)
+{
+    __shared__ unsigned start[kNumBuckets], cnt[kNumBuckets], base[kNumBuckets];
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        for (int b = kNumBuckets - 1; b >= 0; --b) {
+            start[b] = acc;
+            acc += P.ctr->row_hist[b];
+        }
+    }
+    const unsigned total = P.ctr->row_count;
+    for (unsigned c0 = blockIdx.x * blockDim.x; c0 < total; c0 += gridDim.x * blockDim.x) {
+        if (threadIdx.x < kNumBuckets) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned i = c0 + threadIdx.x;
+        int b = -1;
+        unsigned rank = 0;
+        if (i < total) {
+            b = P.row_bkt[i];
+            rank = atomicAdd(&cnt[b], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumBuckets && cnt[threadIdx.x])
+            base[threadIdx.x] = start[threadIdx.x] + atomicAdd(&P.ctr->row_cursor[threadIdx.x], cnt[threadIdx.x]);
+        __syncthreads();
+        if (b >= 0) P.row_sorted[base[b] + rank] = P.row_items[i];
         __syncthreads();
     }
 }
@@ -712,15 +756,14 @@ struct WalkBox {
 
 constexpr int kWalkTableCache = 1024;        // first table entries kept in shared memory
 
-// visit_cell with the eight doses from the staged box when the whole cell
+// visit_cell with the eight doses from the staged box B when the whole cell
 // lies inside it (b0x, b0y, b0z: grid coordinates of the box's first element).
-template <int N>
+template <int N, class B = WalkBox<N>>
 __device__ __forceinline__ float visit_cell_box(const Problem& P, const float* __restrict__ bx,
                                                 int b0x, int b0y, int b0z, int x, int y, int z,
                                                 int cx, int cy, int cz, float key, float dr,
                                                 float inv, float dnorm, float best, TailStats& st)
 {
-    using B = WalkBox<N>;
     const int px = x + cx, py = y + cy, pz = z + cz;
     if ((unsigned)px >= (unsigned)P.nx || (unsigned)py >= (unsigned)P.ny ||
         (N == 3 && (unsigned)pz >= (unsigned)P.nz))
@@ -947,6 +990,201 @@ __global__ void __launch_bounds__(256, MINB)
             break;
         }
         i = (unsigned)sh_next[buf];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_eval += __shfl_xor_sync(kFull, my_eval, o);
+        my_pass += __shfl_xor_sync(kFull, my_pass, o);
+        my_over += __shfl_xor_sync(kFull, my_over, o);
+        if (P.stats) {
+            st.visited += __shfl_xor_sync(kFull, st.visited, o);
+            st.pruned += __shfl_xor_sync(kFull, st.pruned, o);
+            st.keyed += __shfl_xor_sync(kFull, st.keyed, o);
+        }
+    }
+    if (lane == 0) {
+        if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
+        if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
+        if (my_over) atomicAdd(&P.ctr->overflow_count, my_over);
+        if (P.stats) {
+            atomicAdd(&P.ctr->cells_visited, st.visited);
+            atomicAdd(&P.ctr->cells_pruned, st.pruned);
+            atomicAdd(&P.ctr->cells_keyed, st.keyed);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// k_walk_rows: row-staged walk, one shell warp row per warp at a time
+// --------------------------------------------------------------------------
+
+// Halo box of one shell warp row (32 voxels along x): 4 voxels on each side in
+// x (the x start stays a multiple of 4 floats for the TMA copy) and RH in y
+// and z.  Cells whose corner lies within 3 voxels in x and RH - 1 in y and z
+// of the row's voxels read their doses from the box; others global memory.
+template <int N>
+struct RowBox {
+    static constexpr int RH = 3;
+    static constexpr int BX = 32 + 8, BY = 2 * RH + 1, BZ = N == 3 ? 2 * RH + 1 : 1;
+    static constexpr int ELEMS = BX * BY * BZ;
+    static constexpr int STRIDE = (ELEMS + 31) / 32 * 32;
+    static_assert(STRIDE * 4 % 128 == 0, "TMA destination must stay 128-byte aligned");
+};
+
+// Every warp, independently: take the next row item in cost order, stage the
+// row's halo box by one TMA copy into its own buffer (bounded wait), and walk
+// the table for the row's queued voxels, G lanes each (G chosen from the
+// number of queued voxels so that the warp's lanes are used), with the exact
+// stop of Algorithm A1 step 4b-ii and the dose-gap bound.  No block barrier:
+// a warp moves on as soon as its row is done, as in k_tail.
+template <int N, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_walk_rows(const __grid_constant__ Problem P, const __grid_constant__ CUtensorMap rmap, int use_tma)
+{
+    using T = ShellTile<N>;
+    using B = RowBox<N>;
+    // the warps' boxes in dynamic shared memory (8 x B::STRIDE floats, from a
+    // 128-byte boundary: TMA destinations)
+    extern __shared__ __align__(128) unsigned char dyn_raw[];
+    float* boxes = reinterpret_cast<float*>(dyn_raw + ((128u - (smem_addr(dyn_raw) & 127u)) & 127u));
+    __shared__ __align__(8) uint64_t bar[8];
+    __shared__ TableEntry sh_table[kWalkTableCache];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned nrows = P.ctr->row_count;
+    const unsigned long long* order = P.sort_tail ? P.row_sorted : P.row_items;
+    const int ncache = min(P.ntable, kWalkTableCache);
+    for (int i = tid; i < ncache; i += blockDim.x) sh_table[i] = P.table[i];
+    if (tid == 0) {
+        for (int i = 0; i < 8; ++i) mbar_init(&bar[i], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const float dnorm = resolve_dnorm(P);
+    const float rc2 = P.r_cover * P.r_cover;
+    const int ntx = (P.nx + T::TX - 1) / T::TX, nty = (P.ny + T::TY - 1) / T::TY;
+    float* bx = boxes + (size_t)w * B::STRIDE;
+    unsigned my_eval = 0, my_pass = 0, my_over = 0;
+    TailStats st;
+    uint32_t phase = 0;
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(&P.ctr->row_head, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= nrows) break;
+        const unsigned long long item = order[it];
+        const unsigned mask = (unsigned)item, rid = (unsigned)(item >> 32);
+        const unsigned lt = rid >> 3, wr = rid & 7u;
+        const int x0 = (int)(lt % (unsigned)ntx) * T::TX;
+        const int y = (int)((lt / (unsigned)ntx) % (unsigned)nty) * T::TY + (int)(wr % T::TY);
+        const int z = N == 3 ? (int)(lt / (unsigned)ntx / (unsigned)nty) * T::TZ + (int)(wr / T::TY) : 0;
+        const int b0x = x0 - 4, b0y = y - B::RH, b0z = N == 3 ? z - B::RH : 0;
+        // ---- the row's halo box ----
+        bool ok = true;
+        if (use_tma) {
+            if (lane == 0) {
+                fence_async_shared();                 // the box's previous reads come first
+                mbar_arrive_expect_tx(&bar[w], B::ELEMS * (uint32_t)sizeof(float));
+                if (N == 3) tma_load_3d(bx, &rmap, b0x, b0y, b0z, &bar[w]);
+                else tma_load_2d(bx, &rmap, b0x, b0y, &bar[w]);
+            }
+            ok = mbar_wait_bounded(&bar[w], phase & 1u);
+            ++phase;
+        } else {
+            for (int e = lane; e < B::ELEMS; e += 32) {
+                const int ex_ = e % B::BX, ey_ = (e / B::BX) % B::BY, ez_ = e / (B::BX * B::BY);
+                const int gx = b0x + ex_, gy = b0y + ey_, gz = b0z + ez_;
+                const bool in = (unsigned)gx < (unsigned)P.nx && (unsigned)gy < (unsigned)P.ny &&
+                                (N == 2 || (unsigned)gz < (unsigned)P.nz);
+                bx[e] = in ? __ldg(P.ev + ((long long)gz * P.ny + gy) * P.nx + gx) : 0.f;
+            }
+            __syncwarp();
+        }
+        if (!__all_sync(kFull, ok)) {
+            if (lane == 0) {
+                atomicOr(&P.ctr->flags, kFlagTimeout);
+                mbar_wait_bounded(&bar[w], (phase - 1) & 1u);     // its copy lands before the warp leaves
+            }
+            break;
+        }
+        // ---- the row's queued voxels, G lanes each ----
+        const int nq = __popc(mask);
+        int G = 32;
+        while (G > 2 && nq * G > 32) G >>= 1;
+        const int slots = 32 / G;
+        const int gl = lane & (G - 1);
+        const int gbase = lane & ~(G - 1);
+        const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
+        for (int k = lane / G; k < nq; k += slots) {           // group-uniform
+            unsigned mk = mask;                                // the k-th queued voxel of the row
+            for (int j = 0; j < k; ++j) mk &= mk - 1u;         // (k < popc(mask): mk stays non-zero)
+            const int xi = __ffs(mk) - 1;
+            const int x = x0 + xi;
+            const unsigned v = (unsigned)(((long long)z * P.ny + y) * P.nx + x);
+            const float dr = __ldg(P.ref + v);
+            const float dD = P.dd_frac * (P.local ? dr : dnorm);
+            const float inv = 1.0f / dD;
+            float best = P.out[v];                             // gamma^2 over the faces through v
+            int t = 0;
+            while (t < P.ntable) {
+                const int idx = t + gl;
+                float key = kInf;
+                uint32_t off = 0;
+                if (idx < P.ntable) {
+                    const TableEntry e = idx < kWalkTableCache ? sh_table[idx] : P.table[idx];
+                    key = e.key;
+                    off = e.off;
+                }
+                const float k0 = __shfl_sync(gmask, key, gbase);
+                if (k0 * k0 >= best) break;                     // A1 step 4b-ii, exact
+                float cb = best;
+                if (key * key < best) {
+                    if (P.stats) ++st.keyed;
+                    cb = visit_cell_box<N, B>(P, bx, b0x, b0y, b0z, x, y, z, unpack10(off, 0),
+                                              unpack10(off, 10), unpack10(off, 20), key, dr, inv,
+                                              dnorm, best, st);
+                }
+                best = group_min_rt(cb, G, gmask);
+                t += G;
+            }
+            if (t >= P.ntable && best > rc2) {
+                // past a truncated table: the exact scan of the remaining box
+                if (gl == 0) ++my_over;
+                const float g = sqrtf(best);
+                const int ax = (int)ceilf(g / P.hn[0]) + 1;
+                const int ay = (int)ceilf(g / P.hn[1]) + 1;
+                const int az = N == 3 ? (int)ceilf(g / P.hn[2]) + 1 : 0;
+                const int xa = max(-ax - 1, -x), xb = min(ax, P.nx - 1 - x);
+                const int ya = max(-ay - 1, -y), yb = min(ay, P.ny - 1 - y);
+                const int za = N == 3 ? max(-az - 1, -z) : 0, zb = N == 3 ? min(az, P.nz - 1 - z) : 0;
+                const long long wx = xb - xa + 1, wy = yb - ya + 1, wz = zb - za + 1;
+                const long long tot = wx * wy * wz;
+                const float lim = rc2 * 0.99999f;
+                float lb = best;
+                for (long long b = gl; b < tot; b += G) {
+                    const int cx = xa + (int)(b % wx);
+                    const long long rr = b / wx;
+                    const int cy = ya + (int)(rr % wy);
+                    const int cz = za + (int)(rr / wy);
+                    const float axd = (float)max(max(cx, -cx - 1), 0) * P.hn[0];
+                    const float ayd = (float)max(max(cy, -cy - 1), 0) * P.hn[1];
+                    const float azd = N == 3 ? (float)max(max(cz, -cz - 1), 0) * P.hn[2] : 0.f;
+                    float k2 = axd * axd + ayd * ayd + azd * azd;
+                    if (k2 == 0.f)
+                        k2 = P.key0_far2[(cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2)];
+                    if (k2 < lim || k2 >= lb) continue;
+                    lb = visit_cell_box<N, B>(P, bx, b0x, b0y, b0z, x, y, z, cx, cy, cz, sqrtf(k2), dr,
+                                              inv, dnorm, lb, st);
+                }
+                best = group_min_rt(lb, G, gmask);
+            }
+            if (gl == 0) {
+                const float gam = sqrtf(best);
+                P.out[v] = gam;
+                ++my_eval;
+                my_pass += gam <= 1.f;
+            }
+        }
+        __syncwarp();                                          // the box is free again
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1345,6 +1583,48 @@ cudaError_t launch_walk(const Problem& P, int walk_minblocks, cudaStream_t s)
     if (P.ndim == 3) launch_walk_n<3>(P, map, use_tma, per_sm, grid, s);
     else launch_walk_n<2>(P, map, use_tma, per_sm, grid, s);
     return cudaGetLastError();
+}
+
+cudaError_t launch_order_rows(const Problem& P, cudaStream_t s)
+{
+    if (!P.sort_tail) return cudaSuccess;
+    k_scatter_rows<<<device_sm_count() * 2, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <int N, int MINB>
+static cudaError_t launch_walk_rows_k(const Problem& P, const CUtensorMap& map, int use_tma, int grid,
+                                      cudaStream_t s)
+{
+    const int smem = 8 * RowBox<N>::STRIDE * (int)sizeof(float) + 128;
+    cudaError_t e = cudaFuncSetAttribute(k_walk_rows<N, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_walk_rows<N, MINB><<<grid, 256, smem, s>>>(P, map, use_tma);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t launch_walk_rows_n(const Problem& P, const CUtensorMap& map, int use_tma, int per_sm,
+                                      int grid, cudaStream_t s)
+{
+    if (per_sm >= 3) return launch_walk_rows_k<N, 3>(P, map, use_tma, grid, s);
+    if (per_sm == 2) return launch_walk_rows_k<N, 2>(P, map, use_tma, grid, s);
+    return launch_walk_rows_k<N, 1>(P, map, use_tma, grid, s);
+}
+
+cudaError_t launch_walk_rows(const Problem& P, int walk_minblocks, cudaStream_t s)
+{
+    if (!P.row_items) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    int use_tma;
+    if (P.ndim == 3) use_tma = encode_box_map(P, &map, RowBox<3>::BX, RowBox<3>::BY, RowBox<3>::BZ);
+    else use_tma = encode_box_map(P, &map, RowBox<2>::BX, RowBox<2>::BY, 1);
+    const int per_sm = std::min(3, std::max(1, walk_minblocks));
+    const int grid = device_sm_count() * per_sm;     // persistent
+    return P.ndim == 3 ? launch_walk_rows_n<3>(P, map, use_tma, per_sm, grid, s)
+                       : launch_walk_rows_n<2>(P, map, use_tma, per_sm, grid, s);
 }
 
 // --------------------------------------------------------------------------

@@ -43,12 +43,6 @@ __device__ __forceinline__ void tc_fence_after_sync()
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Make generic-proxy shared-memory writes visible to the tensor core.
-__device__ __forceinline__ void fence_async_shared()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // Shared-memory matrix descriptor (no swizzle, K-major canonical layout).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {

@@ -79,6 +79,13 @@ __device__ __forceinline__ void fence_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Order this thread's generic-proxy shared-memory accesses before later
+// async-proxy ones (tensor-core operand reads, TMA writes into the buffer).
+__device__ __forceinline__ void fence_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // 2D / 3D tiled TMA loads into shared memory, completing on `bar`.  The
 // innermost coordinate x must be a multiple of 4 (16 bytes of float32).
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,

@@ -177,11 +177,13 @@ def test_truncated_table_box_scan(ndim):
 @pytest.mark.parametrize("case", ["plane_128", "volume_local", "volume_ragged", "truncated_3d",
                                   "truncated_2d", "unsorted"])
 @pytest.mark.parametrize("blocks", [1, 3])
-def test_tile_staged_walk(case, blocks):
-    # Option walk = 1: the queued voxels walked tile by tile from a TMA-staged
-    # halo box (cells beyond the box read global memory; a tiny table sends
-    # voxels into the box scan; "unsorted" takes the tiles in discovery order).
-    opts = {"walk": 1, "tail_blocks_per_sm": blocks}
+@pytest.mark.parametrize("walk", [1, 2], ids=["tiles", "rows"])
+def test_staged_walks(case, blocks, walk):
+    # Options walk = 1 / 2: the queued voxels walked tile by tile or warp row
+    # by warp row from a TMA-staged halo box (cells beyond the box read global
+    # memory; a tiny table sends voxels into the box scan; "unsorted" takes the
+    # tiles or rows in discovery order).
+    opts = {"walk": walk, "tail_blocks_per_sm": blocks}
     if case == "plane_128":
         p, crit = synth.workload("plane_128"), synth.Criteria(0.03, 3.0)
     elif case in ("volume_local", "unsorted"):
