@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(256) k_grid_prepare(const __grid_constant__ Gr
 // key and dose range already keep it at least sqrt(best) away.
 template <int N>
 __device__ __forceinline__ float grid_cell(const GridProblem& G, const int (&p)[3],
-                                           const double (&u)[3], float key, float dr, float inv,
-                                           float dnorm, float best)
+                                           const double (&u)[3], const float (&cf)[3], float key,
+                                           float dr, float inv, float dnorm, float best)
 {
     const long long sy = G.en[0], sz = (long long)G.en[0] * G.en[1];
     const long long pidx = (long long)p[2] * sz + (long long)p[1] * sy + p[0];
@@ -100,10 +100,9 @@ __device__ __forceinline__ float grid_cell(const GridProblem& G, const int (&p)[
         }
     const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
     if (fmaf(gap, gap, key * key) >= best) return best;
-    const float cx = (float)((double)p[0] - u[0]), cy = (float)((double)p[1] - u[1]);
-    const float cz = N == 3 ? (float)((double)p[2] - u[2]) : 0.f;
+    // the cell's corner relative to the point (voxel units), cf = d - fraction
     CellGeom<float> g;
-    cell_geom<N, float>(cx, cy, cz, G.mt, g);
+    cell_geom<N, float>(cf[0], cf[1], N == 3 ? cf[2] : 0.f, G.mt, g);
     bool ill = false;
     const float dmax = G.tau > 0.f ? 0.99f * rsqrtf(G.tau) : kInf;
     float cb = cell_min_d2<N, float>(q, ok, g, G.mt, dmax, kInf, ill);
@@ -143,17 +142,19 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
         }
         const float dD = G.dd_frac * (G.local ? dr : dnorm);
         const float inv = 1.0f / dD;
-        // the cell that holds the voxel (clamped to the grid) first: a finite
-        // bound from the start
-        float best = grid_cell<N>(G, c0, u, 0.f, dr, inv, dnorm, kInf);
         // the point's position in its cell (voxel units; outside [0, 1) when
-        // the voxel lies beyond the evaluation grid), for the distance bound
+        // the voxel lies beyond the evaluation grid), for the cell offsets and
+        // the distance bound
         float fr[3] = {0.f, 0.f, 0.f}, ehf[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < N; ++a) {
             fr[a] = (float)(u[a] - (double)c0[a]);
             ehf[a] = (float)G.eh[a];
         }
+        // the cell that holds the voxel (clamped to the grid) first: a finite
+        // bound from the start
+        const float cf0[3] = {-fr[0], -fr[1], -fr[2]};
+        float best = grid_cell<N>(G, c0, u, cf0, 0.f, dr, inv, dnorm, kInf);
         int t = 0;
         for (; t < G.ntable; ++t) {
             const TableEntry e = G.table[t];
@@ -179,7 +180,8 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
             }
             k2 *= 0.99999f;
             if (!in || k2 >= best) continue;
-            best = grid_cell<N>(G, p, u, sqrtf(fmaxf(k2, e.key * e.key)), dr, inv, dnorm, best);
+            const float cf[3] = {(float)d[0] - fr[0], (float)d[1] - fr[1], (float)d[2] - fr[2]};
+            best = grid_cell<N>(G, p, u, cf, sqrtf(fmaxf(k2, e.key * e.key)), dr, inv, dnorm, best);
         }
         if (t >= G.ntable && best > rc2) {
             // past a truncated table: every remaining cell of the search box
@@ -209,7 +211,8 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
                             k2 = fmaf(gap, gap, k2);
                         }
                         if (!in || k2 < cut || k2 >= best) continue;
-                        best = grid_cell<N>(G, p, u, sqrtf(k2), dr, inv, dnorm, best);
+                        const float cf[3] = {(float)dx - fr[0], (float)dy - fr[1], (float)dz - fr[2]};
+                        best = grid_cell<N>(G, p, u, cf, sqrtf(k2), dr, inv, dnorm, best);
                     }
         }
         const float gam = sqrtf(best);
