@@ -6,13 +6,13 @@
 //
 //   k_grid_prepare  max of the reference dose (the global dose norm) and a
 //                   finite check of both grids
-//   k_grid_walk     one thread per reference voxel: the evaluation cell that
-//                   contains the voxel (clamped to the grid) first, then the
-//                   cell table in key order with the exact stop of A1 step
-//                   4b-ii; a cell is skipped when the distance from the
-//                   reference point to its box, with its dose gap, already
-//                   reaches the running gamma, else every face of it is
-//                   evaluated (real-valued cell offsets; FP64 redo when a
+//   k_grid_walk     eight lanes per reference voxel walk the cell table in
+//                   key order, eight cells a round, from the evaluation cell
+//                   that holds the voxel (clamped to the grid), with the exact
+//                   stop of A1 step 4b-ii; a cell is skipped when the distance
+//                   from the reference point to its box, with its dose gap,
+//                   already reaches the running gamma, else every face of it
+//                   is evaluated (real-valued cell offsets; FP64 redo when a
 //                   Gram matrix is near singular)
 //
 // The table is keyed by the distance between the box of the voxel's cell and
@@ -117,76 +117,97 @@ __device__ __forceinline__ float grid_cell(const GridProblem& G, const int (&p)[
     return fminf(best, cb);
 }
 
+constexpr int kGridLanes = 8;                 // lanes per reference voxel
+
+// G = kGridLanes lanes per reference voxel (G-aligned groups of a warp).  The
+// table starts with the voxel's own cell (offset 0), so the first round of G
+// cells gives a finite bound; later cells are skipped when the distance from
+// the point itself to the cell's box, with the dose gap, already reaches the
+// running gamma.  The exact stop (A1 step 4b-ii) takes the table's key.
 template <int N>
-__global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridProblem G)
+__global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ GridProblem G)
 {
+    constexpr int GL = kGridLanes;
+    const int lane = threadIdx.x & 31, gl = lane & (GL - 1), gbase = lane & ~(GL - 1);
+    const unsigned gmask = (((1u << GL) - 1u) << gbase);
     const float dnorm = G.dose_norm > 0.f ? G.dose_norm : fdec(G.ctr->dnorm_enc);
     const float thr = G.cutoff_frac * dnorm;
     const float rc2 = G.r_cover * G.r_cover;
     unsigned my_eval = 0, my_pass = 0, my_over = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < G.nref; v += stride) {
+    const long long ngroups = ((long long)gridDim.x * blockDim.x) / GL;
+    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / GL; v < G.nref;
+         v += ngroups) {                                     // group-uniform
         const float dr = __ldg(G.ref + v);
         if (!(dr >= thr && (!G.local || dr > 0.f))) {
-            G.out[v] = __int_as_float(0x7fc00000);
+            if (gl == 0) G.out[v] = __int_as_float(0x7fc00000);
             continue;
         }
         const long long ix[3] = {v % G.rn[0], (v / G.rn[0]) % G.rn[1], v / ((long long)G.rn[0] * G.rn[1])};
+        // the point in evaluation voxel units: its cell c0 (clamped to the
+        // grid) and its position fr in that cell (outside [0, 1) beyond the
+        // grid), from FP64 on one lane
         double u[3] = {0.0, 0.0, 0.0};
         int c0[3] = {0, 0, 0};
-#pragma unroll
-        for (int a = 0; a < N; ++a) {
-            u[a] = (G.ro[a] + (double)ix[a] * G.rh[a] - G.eo[a]) / G.eh[a];
-            const double f = floor(u[a]);
-            c0[a] = (int)fmin(fmax(f, 0.0), (double)(G.en[a] - 2));
-        }
-        const float dD = G.dd_frac * (G.local ? dr : dnorm);
-        const float inv = 1.0f / dD;
-        // the point's position in its cell (voxel units; outside [0, 1) when
-        // the voxel lies beyond the evaluation grid), for the cell offsets and
-        // the distance bound
         float fr[3] = {0.f, 0.f, 0.f}, ehf[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < N; ++a) {
+            double ua = 0.0, f = 0.0;
+            if (gl == 0) {
+                ua = (G.ro[a] + (double)ix[a] * G.rh[a] - G.eo[a]) / G.eh[a];
+                f = fmin(fmax(floor(ua), 0.0), (double)(G.en[a] - 2));
+            }
+            u[a] = __shfl_sync(gmask, ua, gbase);
+            c0[a] = (int)__shfl_sync(gmask, f, gbase);
             fr[a] = (float)(u[a] - (double)c0[a]);
             ehf[a] = (float)G.eh[a];
         }
-        // the cell that holds the voxel (clamped to the grid) first: a finite
-        // bound from the start
-        const float cf0[3] = {-fr[0], -fr[1], -fr[2]};
-        float best = grid_cell<N>(G, c0, u, cf0, 0.f, dr, inv, dnorm, kInf);
+        const float dD = G.dd_frac * (G.local ? dr : dnorm);
+        const float inv = 1.0f / dD;
+        float best = kInf;
         int t = 0;
-        for (; t < G.ntable; ++t) {
-            const TableEntry e = G.table[t];
-            if (e.key * e.key >= best) break;                 // A1 step 4b-ii, exact
-            const int d[3] = {unpack10(e.off, 0), unpack10(e.off, 10), N == 3 ? unpack10(e.off, 20) : 0};
-            if ((d[0] | d[1] | d[2]) == 0) continue;          // done above
-            const int p[3] = {c0[0] + d[0], c0[1] + d[1], c0[2] + d[2]};
-            bool in = true;
-            // the spatial distance from the reference point itself to the
-            // cell box: a tighter lower bound than the key of the table (which
-            // bounds it from any point of the voxel's cell); in FP32 from the
-            // integer offset and the point's fraction, each axis lowered by
-            // the rounding of that arithmetic (4 ulp of its operands) and the
-            // sum by 1e-5, so that it stays a lower bound
-            float k2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                in = in && p[a] >= 0 && p[a] < G.en[a];
-                const float lo = (float)d[a] - fr[a], hi = fr[a] - (float)(d[a] + 1);
-                const float slack = 4.8e-7f * (fabsf(fr[a]) + fabsf((float)d[a]) + 2.f);
-                const float gap = fmaxf(fmaxf(lo, hi) - slack, 0.f) * ehf[a];
-                k2 = fmaf(gap, gap, k2);
+        while (t < G.ntable) {
+            const int idx = t + gl;
+            float key = kInf;
+            uint32_t off = 0;
+            if (idx < G.ntable) {
+                const TableEntry e = G.table[idx];
+                key = e.key;
+                off = e.off;
             }
-            k2 *= 0.99999f;
-            if (!in || k2 >= best) continue;
-            const float cf[3] = {(float)d[0] - fr[0], (float)d[1] - fr[1], (float)d[2] - fr[2]};
-            best = grid_cell<N>(G, p, u, cf, sqrtf(fmaxf(k2, e.key * e.key)), dr, inv, dnorm, best);
+            const float k0 = __shfl_sync(gmask, key, gbase);
+            if (k0 * k0 >= best) break;                       // A1 step 4b-ii, exact
+            float cb = best;
+            if (key * key < best) {
+                const int d[3] = {unpack10(off, 0), unpack10(off, 10), N == 3 ? unpack10(off, 20) : 0};
+                const int p[3] = {c0[0] + d[0], c0[1] + d[1], c0[2] + d[2]};
+                bool in = true;
+                // the distance from the point to the cell's box: a lower bound
+                // in FP32 from the integer offset and the point's fraction,
+                // each axis lowered by its rounding (4 ulp of its operands) and
+                // the sum by 1e-5
+                float k2 = 0.f;
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    in = in && p[a] >= 0 && p[a] < G.en[a];
+                    const float lo = (float)d[a] - fr[a], hi = fr[a] - (float)(d[a] + 1);
+                    const float slack = 4.8e-7f * (fabsf(fr[a]) + fabsf((float)d[a]) + 2.f);
+                    const float gap = fmaxf(fmaxf(lo, hi) - slack, 0.f) * ehf[a];
+                    k2 = fmaf(gap, gap, k2);
+                }
+                k2 *= 0.99999f;
+                if (in && k2 < best) {
+                    const float cf[3] = {(float)d[0] - fr[0], (float)d[1] - fr[1], (float)d[2] - fr[2]};
+                    cb = grid_cell<N>(G, p, u, cf, sqrtf(fmaxf(k2, key * key)), dr, inv, dnorm, best);
+                }
+            }
+#pragma unroll
+            for (int o = GL / 2; o > 0; o >>= 1) cb = fminf(cb, __shfl_xor_sync(gmask, cb, o));
+            best = cb;
+            t += GL;
         }
         if (t >= G.ntable && best > rc2) {
             // past a truncated table: every remaining cell of the search box
-            ++my_over;
-            // the search box, clipped to the grid (so bounded for any best)
+            if (gl == 0) ++my_over;
             const float gm = sqrtf(best);
             int dlo[3] = {0, 0, 0}, dhi[3] = {0, 0, 0};
 #pragma unroll
@@ -196,29 +217,35 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
                 dlo[a] = max(-lim, -c0[a]);
                 dhi[a] = min(lim, G.en[a] - 1 - c0[a]);
             }
+            const long long wx = dhi[0] - dlo[0] + 1, wy = dhi[1] - dlo[1] + 1, wz = dhi[2] - dlo[2] + 1;
+            const long long tot = wx * wy * wz;
             const float cut = rc2 * 0.99999f;
-            for (int dz = dlo[2]; dz <= dhi[2]; ++dz)
-                for (int dy = dlo[1]; dy <= dhi[1]; ++dy)
-                    for (int dx = dlo[0]; dx <= dhi[0]; ++dx) {
-                        const int d[3] = {dx, dy, dz};
-                        const int p[3] = {c0[0] + dx, c0[1] + dy, c0[2] + dz};
-                        bool in = true;
-                        float k2 = 0.f;
+            float lb = best;
+            for (long long b = gl; b < tot; b += GL) {
+                const int d[3] = {dlo[0] + (int)(b % wx), dlo[1] + (int)((b / wx) % wy), dlo[2] + (int)(b / (wx * wy))};
+                const int p[3] = {c0[0] + d[0], c0[1] + d[1], c0[2] + d[2]};
+                bool in = true;
+                float k2 = 0.f;
 #pragma unroll
-                        for (int a = 0; a < N; ++a) {
-                            in = in && p[a] >= 0 && p[a] < G.en[a];
-                            const float gap = (float)max(abs(d[a]) - 1, 0) * (float)G.eh[a];
-                            k2 = fmaf(gap, gap, k2);
-                        }
-                        if (!in || k2 < cut || k2 >= best) continue;
-                        const float cf[3] = {(float)dx - fr[0], (float)dy - fr[1], (float)dz - fr[2]};
-                        best = grid_cell<N>(G, p, u, cf, sqrtf(k2), dr, inv, dnorm, best);
-                    }
+                for (int a = 0; a < N; ++a) {
+                    in = in && p[a] >= 0 && p[a] < G.en[a];
+                    const float gap = (float)max(abs(d[a]) - 1, 0) * (float)G.eh[a];
+                    k2 = fmaf(gap, gap, k2);
+                }
+                if (!in || k2 < cut || k2 >= lb) continue;
+                const float cf[3] = {(float)d[0] - fr[0], (float)d[1] - fr[1], (float)d[2] - fr[2]};
+                lb = grid_cell<N>(G, p, u, cf, sqrtf(k2), dr, inv, dnorm, lb);
+            }
+#pragma unroll
+            for (int o = GL / 2; o > 0; o >>= 1) lb = fminf(lb, __shfl_xor_sync(gmask, lb, o));
+            best = lb;
         }
-        const float gam = sqrtf(best);
-        G.out[v] = gam;
-        ++my_eval;
-        my_pass += gam <= 1.f;
+        if (gl == 0) {
+            const float gam = sqrtf(best);
+            G.out[v] = gam;
+            ++my_eval;
+            my_pass += gam <= 1.f;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -226,7 +253,7 @@ __global__ void __launch_bounds__(256) k_grid_walk(const __grid_constant__ GridP
         my_pass += __shfl_xor_sync(kFull, my_pass, o);
         my_over += __shfl_xor_sync(kFull, my_over, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (my_eval) atomicAdd(&G.ctr->n_eval, (unsigned long long)my_eval);
         if (my_pass) atomicAdd(&G.ctr->n_pass, (unsigned long long)my_pass);
         if (my_over) atomicAdd(&G.ctr->overflow_count, my_over);
@@ -277,6 +304,10 @@ int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
     }
     std::sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
         if (a.key != b.key) return a.key < b.key;
+        // the voxel's own cell first among the key-0 cells (a finite bound
+        // from the walk's first round), then z, y, x
+        const bool a0 = (a.x | a.y | a.z) == 0, b0 = (b.x | b.y | b.z) == 0;
+        if (a0 != b0) return a0;
         if (a.z != b.z) return a.z < b.z;
         if (a.y != b.y) return a.y < b.y;
         return a.x < b.x;
@@ -309,7 +340,8 @@ cudaError_t launch_grids(const GridProblem& G, cudaStream_t s)
     const long long nmax = std::max(G.nref, G.neval);
     const int gp = (int)std::max<long long>(1, std::min<long long>((nmax + 255) / 256, (long long)sms * 8));
     k_grid_prepare<<<gp, 256, 0, s>>>(G);
-    const int gw = (int)std::max<long long>(1, (G.nref + 255) / 256);
+    const int gw = (int)std::max<long long>(1, std::min<long long>((G.nref * kGridLanes + 255) / 256,
+                                                                   (long long)sms * 16));
     if (G.ndim == 3) k_grid_walk<3><<<gw, 256, 0, s>>>(G);
     else k_grid_walk<2><<<gw, 256, 0, s>>>(G);
     return cudaGetLastError();
