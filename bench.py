@@ -1391,9 +1391,17 @@ def experiment_grids(args):
                                  fine.eval.shape, (1.25, 1.25, 1.25), eo,
                                  g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm))
         try:
+            by_lanes = {}
+            for lanes in (4, 8, 16):
+                g.gamma_set_option(h, "lanes_per_voxel", lanes)
+                g.gamma_run(h, out)
+                _, n_eval, n_pass = g.gamma_pass_rate(h)
+                by_lanes[lanes] = _timed_runs(g, h, out, reps=max(args.steps, 3))
+            best_lanes = min(by_lanes, key=by_lanes.get)
+            g.gamma_set_option(h, "lanes_per_voxel", best_lanes)
             g.gamma_run(h, out)
             _, n_eval, n_pass = g.gamma_pass_rate(h)
-            ms = _timed_runs(g, h, out, reps=max(args.steps, 3))
+            ms = by_lanes[best_lanes]
         finally:
             g.gamma_destroy(h)
         got = out.cpu().numpy().ravel()
@@ -1403,7 +1411,8 @@ def experiment_grids(args):
                                   (1.25, 1.25, 1.25), eo, float(np.float32(c.dd_frac)),
                                   float(np.float32(c.dta_mm)), cutoff_frac=float(np.float32(c.cutoff_frac)),
                                   idx=sample)
-        rows.append({"eval_origin_mm": eo, "ms": ms, "voxels_per_s": ref_pair.nvox / (ms / 1000.0),
+        rows.append({"eval_origin_mm": eo, "ms": ms, "lanes_per_voxel": best_lanes,
+                     "ms_by_lanes": by_lanes, "voxels_per_s": ref_pair.nvox / (ms / 1000.0),
                      "evaluated": n_eval, "pass_rate": n_pass / max(n_eval, 1),
                      "sample": int(sample.size),
                      "max_abs_err_vs_oracle": float(np.max(np.abs(got[sample] - want)))})

@@ -142,7 +142,9 @@ int gamma_create(gamma_handle *out, const float *ref_dev, const float *eval_dev,
  * dose norm (global mode) and the cutoff use the reference doses.  Both
  * buffers are borrowed device float32 arrays; gamma_run writes nz*ny*nx
  * reference-grid values.  Identical geometries give an ordinary handle (the
- * coincident-grid search).  Options: "timing", "fp64_tau_exp10", "table_cap".
+ * coincident-grid search).  Options: "timing", "fp64_tau_exp10", "table_cap",
+ * "lanes_per_voxel" (lanes that walk one reference voxel's cells together,
+ * default 8).
  * Errors: INVALID_ARG, SHAPE, OOM, CUDA.  Synchronous. */
 int gamma_create_grids(gamma_handle *out, const float *ref_dev, const float *eval_dev, int ndim,
                        const int64_t ref_shape[3], const float ref_spacing_mm[3],

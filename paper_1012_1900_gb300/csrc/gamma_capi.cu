@@ -815,6 +815,7 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
         G.out = gamma_out_dev;
         G.ctr = h->ctr;
         G.tau = (float)h->tau;
+        G.lanes = h->lanes;
         if (tm) {
             CK(cudaEventRecord(h->tev[0], s));
             CK(cudaEventRecord(h->tev[1], s));
@@ -1195,7 +1196,8 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         h->table_cap = value;
         return GAMMA_OK;
     }
-    if (h->grids && std::strcmp(key, "timing") && std::strcmp(key, "fp64_tau_exp10"))
+    if (h->grids && std::strcmp(key, "timing") && std::strcmp(key, "fp64_tau_exp10") &&
+        std::strcmp(key, "lanes_per_voxel"))
         return GAMMA_ERR_INVALID_ARG;                   // the other options tune the coincident-grid search
     if (h->batch) {
         h->batch->dirty = true;

@@ -6,8 +6,9 @@
 //
 //   k_grid_prepare  max of the reference dose (the global dose norm) and a
 //                   finite check of both grids
-//   k_grid_walk     eight lanes per reference voxel walk the cell table in
-//                   key order, eight cells a round, from the evaluation cell
+//   k_grid_walk     a group of lanes per reference voxel (eight by default)
+//                   walks the cell table in key order, a cell per lane and
+//                   round, from the evaluation cell
 //                   that holds the voxel (clamped to the grid), with the exact
 //                   stop of A1 step 4b-ii; a cell is skipped when the distance
 //                   from the reference point to its box, with its dose gap,
@@ -117,19 +118,16 @@ __device__ __forceinline__ float grid_cell(const GridProblem& G, const int (&p)[
     return fminf(best, cb);
 }
 
-constexpr int kGridLanes = 8;                 // lanes per reference voxel
-
-// G = kGridLanes lanes per reference voxel (G-aligned groups of a warp).  The
+// GL lanes per reference voxel (GL-aligned groups of a warp; 2 .. 32).  The
 // table starts with the voxel's own cell (offset 0), so the first round of G
 // cells gives a finite bound; later cells are skipped when the distance from
 // the point itself to the cell's box, with the dose gap, already reaches the
 // running gamma.  The exact stop (A1 step 4b-ii) takes the table's key.
-template <int N>
+template <int N, int GL>
 __global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ GridProblem G)
 {
-    constexpr int GL = kGridLanes;
     const int lane = threadIdx.x & 31, gl = lane & (GL - 1), gbase = lane & ~(GL - 1);
-    const unsigned gmask = (((1u << GL) - 1u) << gbase);
+    const unsigned gmask = GL == 32 ? kFull : (((1u << GL) - 1u) << gbase);
     const float dnorm = G.dose_norm > 0.f ? G.dose_norm : fdec(G.ctr->dnorm_enc);
     const float thr = G.cutoff_frac * dnorm;
     const float rc2 = G.r_cover * G.r_cover;
@@ -334,16 +332,29 @@ int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
     return GAMMA_OK;
 }
 
+template <int N>
+static void launch_grid_walk_n(const GridProblem& G, int gl, int grid, cudaStream_t s)
+{
+    switch (gl) {
+    case 2: k_grid_walk<N, 2><<<grid, 256, 0, s>>>(G); break;
+    case 4: k_grid_walk<N, 4><<<grid, 256, 0, s>>>(G); break;
+    case 16: k_grid_walk<N, 16><<<grid, 256, 0, s>>>(G); break;
+    case 32: k_grid_walk<N, 32><<<grid, 256, 0, s>>>(G); break;
+    default: k_grid_walk<N, 8><<<grid, 256, 0, s>>>(G); break;
+    }
+}
+
 cudaError_t launch_grids(const GridProblem& G, cudaStream_t s)
 {
     const int sms = device_sm_count();
     const long long nmax = std::max(G.nref, G.neval);
     const int gp = (int)std::max<long long>(1, std::min<long long>((nmax + 255) / 256, (long long)sms * 8));
     k_grid_prepare<<<gp, 256, 0, s>>>(G);
-    const int gw = (int)std::max<long long>(1, std::min<long long>((G.nref * kGridLanes + 255) / 256,
+    const int gl = G.lanes;
+    const int gw = (int)std::max<long long>(1, std::min<long long>((G.nref * gl + 255) / 256,
                                                                    (long long)sms * 16));
-    if (G.ndim == 3) k_grid_walk<3><<<gw, 256, 0, s>>>(G);
-    else k_grid_walk<2><<<gw, 256, 0, s>>>(G);
+    if (G.ndim == 3) launch_grid_walk_n<3>(G, gl, gw, s);
+    else launch_grid_walk_n<2>(G, gl, gw, s);
     return cudaGetLastError();
 }
 

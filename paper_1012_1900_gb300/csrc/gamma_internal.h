@@ -279,6 +279,7 @@ struct GridProblem {
     int ntable;
     float r_cover;
     Counters* ctr;
+    int lanes;                   // lanes per reference voxel (2 .. 32)
 };
 int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
                      std::vector<TableEntry>& table, double& r_cover);
