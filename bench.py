@@ -523,8 +523,10 @@ def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
             g.gamma_destroy(h)
         hb = g.gamma_batch_create([d for d in descs])
         try:
-            for k, v in launch.items():
-                g.gamma_set_option(hb, k, v)
+            # the batched form's own launch shapes (its autotuner), used for
+            # the learned + batched runs too
+            batch_tuned = g.gamma_autotune(hb, stream=stream, reps=2)
+            batch_tuned.pop("ms", None)
             for _ in range(3):
                 g.gamma_batch_run(hb, stream)
             batched_ms = _event_ms(torch, stream, lambda: g.gamma_batch_run(hb, stream), reps)
@@ -552,6 +554,7 @@ def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
             "learned_batched": {"ms": learned_ms, "voxels_per_s": vox / (learned_ms / 1e3),
                                 "max_abs_diff_vs_plain": diff_l, "seeded": seeded,
                                 "queued": queued},
+            "launch_shapes": {"plain": launch, "batched": batch_tuned},
             "speedup_batched_vs_plain": plain_ms / batched_ms,
             "speedup_learned_batched_vs_plain": plain_ms / learned_ms,
             "speedup_learned_batched_vs_batched": batched_ms / learned_ms}
