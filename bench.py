@@ -90,7 +90,11 @@ def parse():
                     help="back-to-back maps before the timed steps, for the clock record "
                          "(0 for profiler runs)")
     ap.add_argument("--walk", type=int, default=-1,
-                    help="1: tile-staged walk, 0: voxel-queue walk (-1: library default)")
+                    help="0: voxel-queue walk, 1: tile-staged, 2: row-staged, 3: warp-evaluated "
+                         "(-1: library default)")
+    ap.add_argument("--group-bucket", type=int, default=-1,
+                    help="walk 3: cost bucket from which queued voxels walk 4 lanes each "
+                         "(-1: library default)")
     ap.add_argument("--no-vs-plain", action="store_true",
                     help="skip the learned + batched against plain comparison")
     ap.add_argument("--experiment", choices=["learned", "batch", "studies", "ablation", "mlp_infer",
@@ -638,6 +642,8 @@ def run_ours(args, pair, rank, world, local_rank):
     h = g.gamma_create(ref, ev, ndim, shape, spacing, crit)
     if args.walk >= 0:
         g.gamma_set_option(h, "walk", args.walk)
+    if args.group_bucket >= 0:
+        g.gamma_set_option(h, "group_bucket", args.group_bucket)
     walk_on = args.walk == 1          # the library walks voxel by voxel by default
     tuned = None
     if args.lanes or args.shell_blocks or args.tail_blocks:
@@ -707,6 +713,8 @@ def run_ours(args, pair, rank, world, local_rank):
         hh = g.gamma_create(None, None, ndim, shape, spacing, crit)
         if args.walk >= 0:
             g.gamma_set_option(hh, "walk", args.walk)
+        if args.group_bucket >= 0:
+            g.gamma_set_option(hh, "group_bucket", args.group_bucket)
         for k, v in launch.items():                  # the launch shapes tuned above
             g.gamma_set_option(hh, k, v)
         try:

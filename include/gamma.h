@@ -212,9 +212,17 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     by row: each warp independently takes one 32-voxel row
  *                     of a shell tile with queued voxels, stages the doses
  *                     around it in shared memory (one TMA copy) and walks the
- *                     table for the row's queued voxels (same results)
+ *                     table for the row's queued voxels (same results); 3:
+ *                     voxel by voxel, one lane per voxel: a cell that passes
+ *                     the dose-gap test joins a per-warp buffer, and the warp
+ *                     evaluates 32 such cells at a time, one per lane (same
+ *                     results; "lanes_per_voxel" does not apply)
+ *  "group_bucket"     "walk" 3: queued voxels whose cost bucket (1 + floor(2
+ *                     log2 of the cells below their starting bound)) is at
+ *                     least this value walk 4 lanes each, the rest one lane
+ *                     each (default 9; 32: every voxel one lane)
  *  "lanes_per_voxel"  2, 4, 8, 16 or 32 lanes search one queued voxel together
- *                     (the voxel-by-voxel walk)
+ *                     (the voxel-by-voxel walk, "walk" 0)
  *  "table_cap"        maximum cell-table length (rebuilds the table)
  *  "fp64_tau_exp10"   FP64 redo when the normalised Gram determinant
  *                     det(G)/prod(G_ii) < 10^-value; value <= 0 disables it
@@ -233,8 +241,9 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     change between (not with "timing", a model or "design")
  *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell
  *                     kernel's register budget is sized for (default 2)
- *  "tail_blocks_per_sm"   1 to 3: the same for the table-walk kernels
- *                     (default 2; lanes_per_voxel defaults to 8)
+ *  "tail_blocks_per_sm"   1 to 4: the same for the table-walk kernels
+ *                     (default 2; lanes_per_voxel defaults to 8; 4 applies
+ *                     to "walk" 3 only, the other walks take 3)
  *  "design"           ablation of the paper's GPU design (Algorithm A2;
  *                     single-pair handles): 0 this library's two-phase search
  *                     (default); 1 one thread per voxel in the order of a

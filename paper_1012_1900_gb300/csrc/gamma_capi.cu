@@ -114,8 +114,12 @@ struct gamma_ctx {
     unsigned long long* row_items = nullptr;
     unsigned char* row_bkt = nullptr;
     unsigned long long* row_sorted = nullptr;
+    // warp-evaluated walk: voxels left to its finishing pass (tail_cap entries)
+    unsigned* fix_list = nullptr;
+    int group_bucket = 9;             // ... queued voxels of this cost bucket and above walk 4 lanes each
     int walk = 0;                     // 0: voxel queue walk (k_tail); 1: tile-staged (k_walk);
-                                      // 2: row-staged (k_walk_rows)
+                                      // 2: row-staged (k_walk_rows); 3: voxel queue walk with
+                                      // the warp evaluating surviving cells together (k_tail_cq)
     // options
     int lanes = gk::kDefaultLanesPerVoxel;
     double tau = 1e-6;
@@ -303,6 +307,8 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.seed_X = h->seed_X;
     P.seed_Y = h->seed_Y;
     P.seed_cap = h->seed_cap;
+    P.fix_list = h->fix_list;
+    P.cq_group_bucket = h->group_bucket;
     if (h->walk == 1 && h->tile_mask) {
         P.tile_mask = h->tile_mask;
         P.tile_list = h->tile_list;
@@ -352,6 +358,7 @@ void free_ctx(gamma_ctx* h)
     cudaFree(h->row_items);
     cudaFree(h->row_bkt);
     cudaFree(h->row_sorted);
+    cudaFree(h->fix_list);
     cudaFree(h->seed_list);
     cudaFree(h->seed_X);
     cudaFree(h->seed_Y);
@@ -637,6 +644,7 @@ int gamma_create(gamma_handle* out, const float* ref_dev, const float* eval_dev,
     if ((e = cudaMalloc(&h->tail_raw, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = cudaMalloc(&h->tail_sorted, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = cudaMalloc(&h->tail_bucket, nvox)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = cudaMalloc(&h->fix_list, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     {
         Problem P0 = make_problem(h, nullptr);
         const int tiles = gk::shell_tiles(P0);
@@ -770,8 +778,9 @@ int gamma_set_inputs(gamma_handle h, const float* ref_dev, const float* eval_dev
     return GAMMA_OK;
 }
 
-// Order and walk the queued voxels: tile by tile from staged halo boxes
-// (k_walk) or voxel by voxel (k_tail).  tm: record the "order" event between.
+// Order and walk the queued voxels: tile by tile or row by row from staged
+// halo boxes (k_walk, k_walk_rows) or voxel by voxel (k_tail, k_tail_cq).
+// tm: record the "order" event between.
 static int enqueue_walk(gamma_handle h, const Problem& P, cudaStream_t s, bool tm)
 {
     if (P.row_items) {
@@ -785,7 +794,8 @@ static int enqueue_walk(gamma_handle h, const Problem& P, cudaStream_t s, bool t
     } else {
         CK(gk::launch_order_tail(P, s));
         if (tm) CK(cudaEventRecord(h->tev[4], s));
-        CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, s));
+        if (h->walk == 3) CK(gk::launch_tail_cq(P, h->tail_minblocks, s));
+        else CK(gk::launch_tail(P, h->lanes, h->tail_minblocks, s));
     }
     return GAMMA_OK;
 }
@@ -1220,8 +1230,13 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "walk")) {
-        if (h->batch || value < 0 || value > 2) return GAMMA_ERR_INVALID_ARG;
+        if (h->batch || value < 0 || value > 3) return GAMMA_ERR_INVALID_ARG;
         h->walk = (int)value;
+        return GAMMA_OK;
+    }
+    if (!std::strcmp(key, "group_bucket")) {
+        if (h->batch || value < 0 || value > gk::kNumBuckets) return GAMMA_ERR_INVALID_ARG;
+        h->group_bucket = (int)value;
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "lanes_per_voxel")) {
@@ -1248,7 +1263,7 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "design")) {
-        if (h->batch || value < 0 || value > 2) return GAMMA_ERR_INVALID_ARG;
+        if (h->batch || value < 0 || value > 3) return GAMMA_ERR_INVALID_ARG;
         if (value != 0 && !h->paper.keys) {
             DeviceGuard dg(h->device);
             if (!dg.ok) return GAMMA_ERR_CUDA;
@@ -1286,7 +1301,7 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "tail_blocks_per_sm")) {
-        if (value < 1 || value > 3) return GAMMA_ERR_INVALID_ARG;
+        if (value < 1 || value > 4) return GAMMA_ERR_INVALID_ARG;
         h->tail_minblocks = (int)value;
         return GAMMA_OK;
     }
@@ -1446,8 +1461,9 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     float best = INFINITY;
     int rc = GAMMA_OK;
     auto run = [&]() { return h->batch ? gamma_batch_run(h, s) : gamma_run(h, gamma_out_dev, s); };
-    // the tile-staged walk picks its lanes per tile: only the block budgets vary
-    const bool tile_walk = !h->batch && !h->grids && h->walk != 0 && h->tile_mask;
+    // the staged walks and the warp-evaluated queue walk do not take a lane
+    // count: only the block budgets vary
+    const bool tile_walk = !h->batch && !h->grids && h->walk != 0;
     const int nl = tile_walk ? 1 : 5;
     for (int li = 0; li < nl && rc == GAMMA_OK; ++li)
         for (int bl = 1; bl <= 4 && rc == GAMMA_OK; ++bl)

@@ -55,10 +55,34 @@ __device__ __noinline__ float cell_redo_f64(const float* __restrict__ ev, long l
     return (float)b;
 }
 
+// A cell whose FP32 pass raised the near-singular pre-filter (rare): the
+// exact test on the same relative doses, reloaded here from the evaluation
+// grid as the caller formed them ((D_e - D_r) * inv), then the FP64 redo when
+// the test holds.  Out of line, so that the callers keep no registers for it.
+template <int N>
+__device__ __noinline__ float cell_recheck(const Problem& P, uint32_t ok, int cx, int cy, int cz,
+                                           long long p, float dr, float inv, float dnorm, float cb)
+{
+    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+    float q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        q[u] = 0.f;
+        if (u < (1 << N) && ((ok >> u) & 1u)) {
+            const long long o = p + ((u & 1) ? 1 : 0) + ((u & 2) ? sy : 0) + ((u & 4) ? sz : 0);
+            q[u] = (__ldg(P.ev + o) - dr) * inv;
+        }
+    }
+    if (!cell_gram_ill<N>(q, ok, P.mt.kappa, P.tau)) return cb;
+    const double drd = dr;
+    const double invd = 1.0 / ((double)P.dd_frac * (P.local ? drd : (double)dnorm));
+    return cell_redo_f64<N>(P.ev, p, sy, sz, ok, cx, cy, cz, drd, invd, P.mtd, &P.ctr->fp64_cells);
+}
+
 // Every face of the cell with lower corner (x+cx, y+cy, z+cz) as squared
-// gamma, with the FP64 redo when a face's Gram matrix is near singular.  Out
-// of line: each kernel keeps one copy, and the callers keep their own
-// registers few.
+// gamma, with the FP64 redo when a face's Gram matrix is near singular.  q
+// holds (D_e - dr) * inv of the cell's vertices.  Out of line: each kernel
+// keeps one copy, and the callers keep their own registers few.
 template <int N>
 __device__ __noinline__ float cell_all_faces(const Problem& P, float q0, float q1, float q2,
                                              float q3, float q4, float q5, float q6, float q7,

@@ -84,6 +84,8 @@ struct Counters {
     unsigned int row_head;              // work counter of the row-staged walk
     unsigned int row_hist[kNumBuckets]; // those rows by their largest cost bucket
     unsigned int row_cursor[kNumBuckets];
+    unsigned int head_group;            // warp-evaluated walk: work counter of the grouped part
+    unsigned int fix_count;             // ... voxels it leaves to the finishing pass
 };
 
 // Order-preserving encoding of a float into an unsigned int (for atomicMax).
@@ -151,6 +153,11 @@ struct Problem {
     unsigned long long* row_items;
     unsigned char* row_bkt;
     unsigned long long* row_sorted;
+    // warp-evaluated walk (k_tail_cq): queued voxels of this cost bucket and
+    // above walk with several lanes each; fix_list (tail_cap entries) holds
+    // the voxels whose exact result the finishing pass completes
+    int cq_group_bucket;
+    unsigned* fix_list;
 };
 
 // Readiness of the evaluation dose by z slab, for a shell launch that starts
@@ -228,6 +235,8 @@ cudaError_t launch_patch_host(const Problem& P, float* host_out_mapped, Counters
                               cudaStream_t s);
 cudaError_t launch_order_tail(const Problem& P, cudaStream_t s);
 cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblocks, cudaStream_t s);
+// one lane per queued voxel, surviving cells evaluated by the whole warp
+cudaError_t launch_tail_cq(const Problem& P, int tail_minblocks, cudaStream_t s);
 // Tile-staged walk (P.tile_mask set): order the tiles with queued voxels by
 // cost, then one block per tile stages the tile's evaluation-dose halo box in
 // shared memory and walks the table for the tile's queued voxels.

@@ -595,6 +595,43 @@ __device__ __forceinline__ float group_min(float v, unsigned gmask)
     return v;
 }
 
+// The walk ran past a truncated table with the running bound still above
+// the cover radius: scan every cell of the remaining search box, G lanes
+// together (rare; keeps the result exact).
+template <int N, int G>
+__device__ __forceinline__ float tail_box_scan(const Problem& P, int x, int y, int z, float dr,
+                                            float inv, float dnorm, float best, int gl,
+                                            unsigned gmask, TailStats& st)
+{
+    const float rc2 = P.r_cover * P.r_cover;
+    const float g = sqrtf(best);
+    const int ax = (int)ceilf(g / P.hn[0]) + 1;
+    const int ay = (int)ceilf(g / P.hn[1]) + 1;
+    const int az = N == 3 ? (int)ceilf(g / P.hn[2]) + 1 : 0;
+    const int x0 = max(-ax - 1, -x), x1 = min(ax, P.nx - 1 - x);
+    const int y0 = max(-ay - 1, -y), y1 = min(ay, P.ny - 1 - y);
+    const int z0 = N == 3 ? max(-az - 1, -z) : 0, z1 = N == 3 ? min(az, P.nz - 1 - z) : 0;
+    const long long bx = x1 - x0 + 1, by = y1 - y0 + 1, bz = z1 - z0 + 1;
+    const long long tot = bx * by * bz;
+    const float lim = rc2 * 0.99999f;
+    float lb = best;
+    for (long long b = gl; b < tot; b += G) {
+        const int cx = x0 + (int)(b % bx);
+        const long long rr = b / bx;
+        const int cy = y0 + (int)(rr % by);
+        const int cz = z0 + (int)(rr / by);
+        const float axd = (float)max(max(cx, -cx - 1), 0) * P.hn[0];
+        const float ayd = (float)max(max(cy, -cy - 1), 0) * P.hn[1];
+        const float azd = N == 3 ? (float)max(max(cz, -cz - 1), 0) * P.hn[2] : 0.f;
+        float k2 = axd * axd + ayd * ayd + azd * azd;
+        if (k2 == 0.f)       // key-0 cell: only its faces off the voxel remain
+            k2 = P.key0_far2[(cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2)];
+        if (k2 < lim || k2 >= lb) continue;
+        lb = visit_cell<N>(P, x, y, z, cx, cy, cz, sqrtf(k2), dr, inv, dnorm, lb, st);
+    }
+    return group_min<G>(lb, gmask);
+}
+
 template <int N, int G, int MINB, bool BATCH>
 __global__ void __launch_bounds__(256, MINB)
     k_tail(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd)
@@ -670,35 +707,8 @@ __global__ void __launch_bounds__(256, MINB)
             t += G;
         }
         if (t >= P.ntable && best > rc2) {
-            // The walk ran past a truncated table: scan every cell of the
-            // remaining search box (rare; keeps the result exact).
             if (gl == 0) ++my_over;
-            const float g = sqrtf(best);
-            const int ax = (int)ceilf(g / P.hn[0]) + 1;
-            const int ay = (int)ceilf(g / P.hn[1]) + 1;
-            const int az = N == 3 ? (int)ceilf(g / P.hn[2]) + 1 : 0;
-            const int x0 = max(-ax - 1, -x), x1 = min(ax, P.nx - 1 - x);
-            const int y0 = max(-ay - 1, -y), y1 = min(ay, P.ny - 1 - y);
-            const int z0 = N == 3 ? max(-az - 1, -z) : 0, z1 = N == 3 ? min(az, P.nz - 1 - z) : 0;
-            const long long bx = x1 - x0 + 1, by = y1 - y0 + 1, bz = z1 - z0 + 1;
-            const long long tot = bx * by * bz;
-            const float lim = rc2 * 0.99999f;
-            float lb = best;
-            for (long long b = gl; b < tot; b += G) {
-                const int cx = x0 + (int)(b % bx);
-                const long long rr = b / bx;
-                const int cy = y0 + (int)(rr % by);
-                const int cz = z0 + (int)(rr / by);
-                const float axd = (float)max(max(cx, -cx - 1), 0) * P.hn[0];
-                const float ayd = (float)max(max(cy, -cy - 1), 0) * P.hn[1];
-                const float azd = N == 3 ? (float)max(max(cz, -cz - 1), 0) * P.hn[2] : 0.f;
-                float k2 = axd * axd + ayd * ayd + azd * azd;
-                if (k2 == 0.f)       // key-0 cell: only its faces off the voxel remain
-                    k2 = P.key0_far2[(cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2)];
-                if (k2 < lim || k2 >= lb) continue;
-                lb = visit_cell<N>(P, x, y, z, cx, cy, cz, sqrtf(k2), dr, inv, dnorm, lb, st);
-            }
-            best = group_min<G>(lb, gmask);
+            best = tail_box_scan<N, G>(P, x, y, z, dr, inv, dnorm, best, gl, gmask, st);
         }
         if (gl == 0) {
             const float gam = sqrtf(best);
@@ -730,6 +740,367 @@ __global__ void __launch_bounds__(256, MINB)
                 atomicAdd(&P.ctr->cells_pruned, st.pruned);
                 atomicAdd(&P.ctr->cells_keyed, st.keyed);
             }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// k_tail_cq: surviving cells of the walks evaluated 32 at a time by the warp
+// --------------------------------------------------------------------------
+
+// In k_tail the face evaluation of a cell (the bulk of the work) runs with
+// only the lanes whose cell passed the dose-gap test active.  Here a voxel's
+// walk appends each cell that passes the test, with its vertex doses, to a
+// ring buffer of the warp instead of evaluating it; whenever 32 cells wait,
+// the whole warp evaluates them together, one per lane, and lowers each
+// owner's running bound in shared memory (atomicMin on the bits of a
+// non-negative float).  A walk may therefore key and test a few cells against
+// a bound that is not yet the lowest: the stop (key >= bound) and the prune
+// (key^2 + gap^2 >= bound) stay exact with any bound that is at least the
+// true minimum, and each cell is evaluated with the arithmetic of k_tail, so
+// the map is the one k_tail writes.  A voxel is final once every cell it
+// appended has been evaluated; a walker has two voxel slots so that it can
+// start its next voxel while the cells of the previous one still wait.
+//
+// The queue is ordered by cost bucket, most expensive first: the voxels of
+// bucket cq_group_bucket and above walk GX lanes each (GX table entries per
+// step), which shortens the longest walks; the rest walk one lane each.  The
+// rare paths (a cell whose Gram matrix is near singular, a walk that runs past
+// a truncated table) are not taken here: such a voxel goes to fix_list with
+// its bound, and k_tail_fix finishes it, so that this kernel's registers stay
+// those of the FP32 evaluation.
+constexpr int kCqRing = 64;               // ring of pending cells per warp
+constexpr int kCqMinWalking = 16;         // flush a partial batch below this many walking lanes
+
+// Per-warp shared state.  A walker's state (one lane, or the first lane of a
+// group) lives here rather than in registers.
+struct CqWarp {
+    float q[8][kCqRing];       // vertex doses of a pending cell (relative, normalised)
+    unsigned off[kCqRing];     // its offset from the voxel, packed as in the table
+    unsigned meta[kCqRing];    // owner slot (bits 0-5), vertices inside the grid (bits 8-15)
+    unsigned best[64];         // running squared gamma per voxel slot (float bits)
+    unsigned vox[64];          // voxel index per slot
+    float dr[64];              // reference dose per slot
+    float inv[64];             // 1 / Delta D per slot
+    unsigned fixm[2];          // slots whose voxel goes to the finishing pass
+    int xyz[3][32];            // the walking voxel's grid position, per walker
+    int t[32];                 // its next table entry
+    unsigned wseq[32];         // sequence number of the last cell it appended
+    unsigned dseq[32];         // the same for the voxel in the drain slot
+    unsigned state[32];        // kCq* bits below
+    unsigned cnt[2][32];       // voxels finished and passed
+    unsigned long long stat[3][32];    // cells visited, pruned, keyed (option "stats")
+};
+constexpr unsigned kCqWalk = 1u, kCqEnded = 2u, kCqWPend = 4u, kCqDBusy = 8u, kCqDPend = 16u,
+                   kCqDOver = 32u, kCqSlot = 64u;     // slot bit: the walking slot is walker + 32
+
+template <int N, int MINB, int GX>
+__global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ Problem P)
+{
+    __shared__ CqWarp cqw[8];
+    __shared__ unsigned s_total, s_ngroup;
+    __shared__ float s_dnorm;
+    CqWarp& W = cqw[threadIdx.x >> 5];
+    volatile CqWarp& V = cqw[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (threadIdx.x < 32) {
+        // items [0, s_ngroup) of the cost-ordered queue walk GX lanes each
+        const unsigned total = min(P.ctr->tail_count, P.tail_cap);
+        unsigned h = (P.sort_tail && GX > 1 && lane >= P.cq_group_bucket) ? P.ctr->hist[lane] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+        if (lane == 0) {
+            s_total = total;
+            s_ngroup = min(h, total);
+            s_dnorm = resolve_dnorm(P);
+        }
+    }
+    W.state[lane] = 0;
+    W.wseq[lane] = W.dseq[lane] = 0;
+    W.cnt[0][lane] = W.cnt[1][lane] = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) W.stat[k][lane] = 0;
+    if (lane < 2) W.fixm[lane] = 0;
+    __syncthreads();
+
+    const float rc2 = P.r_cover * P.r_cover;
+    int g = s_ngroup > 0 ? GX : 1;     // lanes per voxel in the current part of the queue
+    unsigned head = 0, count = 0;      // the ring: pending cells are [head, head + count)
+    bool queue_done = false;           // warp-uniform, for the current part
+    for (;;) {
+        const int gl = lane & (g - 1), ld = lane - gl;
+        const bool leader = gl == 0;
+        const unsigned gmask = g == 32 ? kFull : ((1u << g) - 1u) << ld;
+        unsigned sta = V.state[ld];
+        if (leader) {
+            // 1. a drained voxel whose cells are all evaluated is final
+            if ((sta & kCqDBusy) && (!(sta & kCqDPend) || (int)(head - V.dseq[ld]) > 0)) {
+                const int ds = ld + ((sta & kCqSlot) ? 0 : 32);
+                const float best = __uint_as_float(V.best[ds]);
+                const unsigned v = V.vox[ds];
+                if (((V.fixm[ds >> 5] >> (ds & 31)) & 1u) || ((sta & kCqDOver) && best > rc2)) {
+                    P.out[v] = best;                        // gamma^2: k_tail_fix completes it
+                    P.fix_list[atomicAdd(&P.ctr->fix_count, 1u)] = v;
+                } else {
+                    const float gam = sqrtf(best);
+                    P.out[v] = gam;
+                    ++V.cnt[0][ld];
+                    if (gam <= 1.f) ++V.cnt[1][ld];
+                }
+                sta &= ~kCqDBusy;
+            }
+            // 2. an ended walk becomes the drain slot; the walker takes a new voxel
+            if ((sta & kCqEnded) && !(sta & kCqDBusy)) {
+                unsigned d = kCqDBusy;
+                if (sta & kCqWPend) d |= kCqDPend;
+                if (V.t[ld] >= P.ntable) d |= kCqDOver;
+                V.dseq[ld] = V.wseq[ld];
+                sta = d | ((sta & kCqSlot) ^ kCqSlot);
+            }
+        }
+        // 3. refill the empty walkers from the current part of the queue
+        const bool empty = leader && !(sta & (kCqWalk | kCqEnded));
+        const unsigned need = __ballot_sync(kFull, empty);
+        if (need && !queue_done) {
+            const unsigned lo = g > 1 ? 0u : s_ngroup, hi = g > 1 ? s_ngroup : s_total;
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(g > 1 ? &P.ctr->head_group : &P.ctr->head, (unsigned)__popc(need));
+            base = __shfl_sync(kFull, base, 0) + lo;
+            if (base + (unsigned)__popc(need) >= hi) queue_done = true;
+            if (empty) {
+                const unsigned item = base + (unsigned)__popc(need & lt_mask);
+                if (item < hi) {
+                    const unsigned v = P.sort_tail ? P.tail_sorted[item] : P.tail_raw[item];
+                    const int ws = ld + ((sta & kCqSlot) ? 32 : 0);
+                    V.xyz[0][ld] = (int)(v % (unsigned)P.nx);
+                    const unsigned r1 = v / (unsigned)P.nx;
+                    V.xyz[1][ld] = (int)(r1 % (unsigned)P.ny);
+                    V.xyz[2][ld] = (int)(r1 / (unsigned)P.ny);
+                    const float dr = __ldg(P.ref + v);
+                    V.dr[ws] = dr;
+                    V.inv[ws] = 1.0f / (P.dd_frac * (P.local ? dr : s_dnorm));
+                    V.best[ws] = __float_as_uint(P.out[v]);  // gamma^2 over the faces through v
+                    V.vox[ws] = v;
+                    atomicAnd(&W.fixm[ws >> 5], ~(1u << (ws & 31)));
+                    V.t[ld] = 0;
+                    sta = (sta & ~kCqWPend) | kCqWalk;
+                }
+            }
+        }
+        if (leader) V.state[ld] = sta;
+        __syncwarp();
+        sta = V.state[ld];                 // the group's lanes follow their walker
+        if (queue_done && !__any_sync(kFull, (sta & (kCqWalk | kCqEnded | kCqDBusy)) != 0)) {
+            if (g == 1) break;
+            g = 1;                         // the grouped part is done: one lane per voxel
+            queue_done = false;
+            V.state[lane] = 0;
+            __syncwarp();
+            continue;
+        }
+
+        // 4. one table step of every walking group: entries t .. t + g - 1
+        const bool walking = (sta & kCqWalk) != 0;
+        const int ws = ld + ((sta & kCqSlot) ? 32 : 0);
+        const int t0 = walking ? V.t[ld] : 0;
+        float key = kInf;
+        uint32_t off = 0;
+        if (walking && t0 + gl < P.ntable) {
+            const TableEntry e = P.table[t0 + gl];
+            key = e.key;
+            off = e.off;
+        }
+        const float k0 = __shfl_sync(kFull, key, ld);
+        bool cand = false, ended = false;
+        float q[8];
+        uint32_t ok = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = 0.f;
+        if (walking) {
+            const float bst = __uint_as_float(V.best[ws]);
+            ended = t0 >= P.ntable || k0 * k0 >= bst;         // A1 step 4b-ii, exact
+            if (!ended && key * key < bst) {
+                if (P.stats) ++V.stat[2][lane];
+                const int px = V.xyz[0][ld] + unpack10(off, 0);
+                const int py = V.xyz[1][ld] + unpack10(off, 10);
+                const int pz = V.xyz[2][ld] + unpack10(off, 20);
+                if ((unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny &&
+                    (N == 2 || (unsigned)pz < (unsigned)P.nz)) {
+                    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+                    const bool ex = px + 1 < P.nx, ey = py + 1 < P.ny, ez = N == 3 && pz + 1 < P.nz;
+                    const long long p = (long long)pz * sz + (long long)py * sy + px;
+                    const float dr = V.dr[ws], inv = V.inv[ws];
+                    float qmin = kInf, qmax = -kInf;
+#pragma unroll
+                    for (int u = 0; u < (1 << N); ++u) {
+                        const bool present = (!(u & 1) || ex) && (!(u & 2) || ey) && (!(u & 4) || ez);
+                        if (present) {
+                            const long long o = p + ((u & 1) ? 1 : 0) + ((u & 2) ? sy : 0) +
+                                                ((u & 4) ? sz : 0);
+                            q[u] = (__ldg(P.ev + o) - dr) * inv;
+                            qmin = fminf(qmin, q[u]);
+                            qmax = fmaxf(qmax, q[u]);
+                            ok |= 1u << u;
+                        }
+                    }
+                    const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
+                    if (fmaf(gap, gap, key * key) >= bst) {
+                        if (P.stats) ++V.stat[1][lane];
+                    } else {
+                        cand = true;
+                    }
+                }
+            }
+        }
+        // 5. append the surviving cells to the ring
+        const unsigned cm = __ballot_sync(kFull, cand);
+        if (cand) {
+            const unsigned seq = head + count + (unsigned)__popc(cm & lt_mask);
+            const int slot = (int)(seq & (kCqRing - 1));
+#pragma unroll
+            for (int u = 0; u < (1 << N); ++u) V.q[u][slot] = q[u];
+            V.off[slot] = off;
+            V.meta[slot] = (unsigned)ws | (ok << 8);
+        }
+        if (leader && walking) {
+            if (ended) {
+                sta = (sta & ~kCqWalk) | kCqEnded;
+            } else {
+                V.t[ld] = t0 + g;
+                const unsigned gm = cm & gmask;
+                if (gm) {                   // the group's last appended cell
+                    const int hl = 31 - __clz(gm);
+                    V.wseq[ld] = head + count + (unsigned)__popc(cm & ((1u << hl) - 1u));
+                    sta |= kCqWPend;
+                }
+            }
+            V.state[ld] = sta;
+        }
+        count += (unsigned)__popc(cm);
+        const int nwalk = g * __popc(__ballot_sync(kFull, leader && (sta & kCqWalk) && !ended));
+        __syncwarp();
+        // 6. evaluate the oldest 32 pending cells (or fewer, when few lanes walk)
+        if (count >= 32u || (count > 0u && nwalk < kCqMinWalking)) {
+            const unsigned n = min(count, 32u);
+            if ((unsigned)lane < n) {
+                const int slot = (int)((head + (unsigned)lane) & (kCqRing - 1));
+                const unsigned meta = V.meta[slot];
+                const int owner = (int)(meta & 63u);
+                const unsigned cok = meta >> 8;
+                const unsigned coff = V.off[slot];
+                float cq[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cq[u] = u < (1 << N) ? V.q[u][slot] : 0.f;
+                CellGeom<float> cg;
+                cell_geom<N, float>(unpack10(coff, 0), unpack10(coff, 10), unpack10(coff, 20), P.mt, cg);
+                bool ill = false;
+                const float cb = cell_min_d2<N, float>(cq, cok, cg, P.mt, ill_dmax(P), kInf, ill);
+                if (ill && cell_gram_ill<N>(cq, cok, P.mt.kappa, P.tau))
+                    atomicOr(&W.fixm[owner >> 5], 1u << (owner & 31));   // k_tail_fix redoes it
+                else
+                    atomicMin(&W.best[owner], __float_as_uint(cb + 0.f));   // -0 -> +0
+                if (P.stats) ++V.stat[0][lane];
+            }
+            head += n;
+            count -= n;
+        }
+        __syncwarp();
+    }
+    // per-warp totals
+    unsigned c0 = W.cnt[0][lane], c1 = W.cnt[1][lane];
+    unsigned long long s0 = W.stat[0][lane], s1 = W.stat[1][lane], s2 = W.stat[2][lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_xor_sync(kFull, c0, o);
+        c1 += __shfl_xor_sync(kFull, c1, o);
+        s0 += __shfl_xor_sync(kFull, s0, o);
+        s1 += __shfl_xor_sync(kFull, s1, o);
+        s2 += __shfl_xor_sync(kFull, s2, o);
+    }
+    if (lane == 0) {
+        if (c0) atomicAdd(&P.ctr->n_eval, (unsigned long long)c0);
+        if (c1) atomicAdd(&P.ctr->n_pass, (unsigned long long)c1);
+        if (P.stats) {
+            atomicAdd(&P.ctr->cells_visited, s0);
+            atomicAdd(&P.ctr->cells_pruned, s1);
+            atomicAdd(&P.ctr->cells_keyed, s2);
+        }
+    }
+}
+
+// Finishing pass of k_tail_cq: one warp per voxel of fix_list, whose bound
+// (gamma^2, an upper bound of the result) is in out.  The walk of k_tail
+// (32 lanes, FP64 redo of near-singular cells) from that bound, then the box
+// scan when it runs past the table.
+template <int N>
+__global__ void __launch_bounds__(256) k_tail_fix(const __grid_constant__ Problem P)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned nfix = P.ctr->fix_count;
+    const float dnorm = resolve_dnorm(P);
+    const float rc2 = P.r_cover * P.r_cover;
+    unsigned my_eval = 0, my_pass = 0, my_over = 0;
+    TailStats st;
+    for (unsigned i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nfix;
+         i += (gridDim.x * blockDim.x) >> 5) {
+        const unsigned v = P.fix_list[i];
+        const int x = (int)(v % (unsigned)P.nx);
+        const unsigned r1 = v / (unsigned)P.nx;
+        const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
+        const float dr = __ldg(P.ref + v);
+        const float inv = 1.0f / (P.dd_frac * (P.local ? dr : dnorm));
+        float best = P.out[v];
+        int t = 0;
+        while (t < P.ntable) {
+            const int idx = t + lane;
+            float key = kInf;
+            uint32_t off = 0;
+            if (idx < P.ntable) {
+                const TableEntry e = P.table[idx];
+                key = e.key;
+                off = e.off;
+            }
+            const float k0 = __shfl_sync(kFull, key, 0);
+            if (k0 * k0 >= best) break;
+            float cb = best;
+            if (key * key < best) {
+                if (P.stats) ++st.keyed;
+                cb = visit_cell<N>(P, x, y, z, unpack10(off, 0), unpack10(off, 10), unpack10(off, 20),
+                                   key, dr, inv, dnorm, best, st);
+            }
+            best = group_min<32>(cb, kFull);
+            t += 32;
+        }
+        if (t >= P.ntable && best > rc2) {
+            ++my_over;
+            best = tail_box_scan<N, 32>(P, x, y, z, dr, inv, dnorm, best, lane, kFull, st);
+        }
+        if (lane == 0) {
+            const float gam = sqrtf(best);
+            P.out[v] = gam;
+            ++my_eval;
+            my_pass += gam <= 1.f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_eval += __shfl_xor_sync(kFull, my_eval, o);
+        my_pass += __shfl_xor_sync(kFull, my_pass, o);
+        if (P.stats) {
+            st.visited += __shfl_xor_sync(kFull, st.visited, o);
+            st.pruned += __shfl_xor_sync(kFull, st.pruned, o);
+            st.keyed += __shfl_xor_sync(kFull, st.keyed, o);
+        }
+    }
+    if (lane == 0) {
+        if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
+        if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
+        if (my_over) atomicAdd(&P.ctr->overflow_count, my_over);
+        if (P.stats) {
+            atomicAdd(&P.ctr->cells_visited, st.visited);
+            atomicAdd(&P.ctr->cells_pruned, st.pruned);
+            atomicAdd(&P.ctr->cells_keyed, st.keyed);
         }
     }
 }
@@ -1551,6 +1922,26 @@ cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblock
     const int grid = sms * 8;      // persistent: enough warps to fill every SM
     if (P.ndim == 3) launch_tail_n<3, false>(P, nullptr, lanes_per_voxel, tail_minblocks, grid, s);
     else launch_tail_n<2, false>(P, nullptr, lanes_per_voxel, tail_minblocks, grid, s);
+    return cudaGetLastError();
+}
+
+template <int N>
+static void launch_tail_cq_n(const Problem& P, int per_sm, int grid, cudaStream_t s)
+{
+    if (per_sm >= 4) k_tail_cq<N, 4, 4><<<grid, 256, 0, s>>>(P);
+    else if (per_sm == 3) k_tail_cq<N, 3, 4><<<grid, 256, 0, s>>>(P);
+    else if (per_sm == 2) k_tail_cq<N, 2, 4><<<grid, 256, 0, s>>>(P);
+    else k_tail_cq<N, 1, 4><<<grid, 256, 0, s>>>(P);
+    k_tail_fix<N><<<device_sm_count() * 2, 256, 0, s>>>(P);
+}
+
+cudaError_t launch_tail_cq(const Problem& P, int tail_minblocks, cudaStream_t s)
+{
+    if (!P.fix_list) return cudaErrorInvalidValue;
+    const int per_sm = std::min(4, std::max(1, tail_minblocks));
+    const int grid = device_sm_count() * per_sm;      // persistent: one wave of resident blocks
+    if (P.ndim == 3) launch_tail_cq_n<3>(P, per_sm, grid, s);
+    else launch_tail_cq_n<2>(P, per_sm, grid, s);
     return cudaGetLastError();
 }
 

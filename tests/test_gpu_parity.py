@@ -177,12 +177,13 @@ def test_truncated_table_box_scan(ndim):
 @pytest.mark.parametrize("case", ["plane_128", "volume_local", "volume_ragged", "truncated_3d",
                                   "truncated_2d", "unsorted"])
 @pytest.mark.parametrize("blocks", [1, 3])
-@pytest.mark.parametrize("walk", [1, 2], ids=["tiles", "rows"])
+@pytest.mark.parametrize("walk", [1, 2, 3], ids=["tiles", "rows", "warp_cells"])
 def test_staged_walks(case, blocks, walk):
     # Options walk = 1 / 2: the queued voxels walked tile by tile or warp row
     # by warp row from a TMA-staged halo box (cells beyond the box read global
     # memory; a tiny table sends voxels into the box scan; "unsorted" takes the
-    # tiles or rows in discovery order).
+    # tiles or rows in discovery order).  walk = 3: voxel by voxel, one lane
+    # each, the surviving cells evaluated by the whole warp.
     opts = {"walk": walk, "tail_blocks_per_sm": blocks}
     if case == "plane_128":
         p, crit = synth.workload("plane_128"), synth.Criteria(0.03, 3.0)
@@ -209,6 +210,25 @@ def test_staged_walks(case, blocks, walk):
     want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
     for g_ in got:                                   # a direct run, then the graph replay
         assert_parity(g_, want, counts)
+
+
+@pytest.mark.parametrize("crit", [(0.03, 3.0, False), (0.01, 1.0, True)], ids=["3-3", "1-1-local"])
+@pytest.mark.parametrize("group_bucket", [0, 9, 32])
+@pytest.mark.parametrize("blocks", [1, 2, 3, 4])
+def test_warp_evaluated_walk_is_bitwise_the_voxel_walk(crit, group_bucket, blocks):
+    # walk = 3 evaluates every cell with the same arithmetic as walk = 0 and
+    # reaches the same minimising cell, so the two maps agree bit for bit,
+    # whichever voxels walk four lanes each (group_bucket 0: all of them; 32:
+    # none) and at every register budget
+    p = synth.workload("imrt_small")
+    c = synth.Criteria(crit[0], crit[1], local=crit[2])
+    a, ca, sa = gpu_gamma(p.ref, p.eval, p.spacing, c, {"walk": 0, "lanes_per_voxel": 2, "stats": 1})
+    b, cb, sb = gpu_gamma(p.ref, p.eval, p.spacing, c, {"walk": 3, "stats": 1, "group_bucket": group_bucket,
+                                                      "tail_blocks_per_sm": blocks})
+    np.testing.assert_array_equal(a, b)
+    assert ca == cb
+    assert sb["tail_voxels"] == sa["tail_voxels"] > 0
+    assert sb["cells_visited"] > 0 and sb["cells_keyed"] > 0
 
 
 @pytest.mark.parametrize("design", [1, 2])
@@ -241,17 +261,23 @@ def test_paper_design_truncated_table(face_eval):
     assert_parity(got, want, counts)
 
 
-def test_fp64_redo_paths():
+@pytest.mark.parametrize("walk", [0, 3])
+def test_fp64_redo_paths(walk):
+    # walk = 3 leaves voxels with a near-singular cell to its finishing pass
     p = synth.workload("imrt_small")
     crit = synth.Criteria(0.01, 1.0, local=True)
     want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
-    g_off, c_off, s_off = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"fp64_tau_exp10": 0})
-    g_all, c_all, s_all = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"fp64_tau_exp10": 1})
+    g_off, c_off, s_off = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"fp64_tau_exp10": 0, "walk": walk})
+    g_all, c_all, s_all = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"fp64_tau_exp10": 1, "walk": walk})
     assert s_off["fp64_cells"] == 0
     assert s_all["fp64_cells"] > 0
     assert_parity(g_off, want, c_off)
     e_all = assert_parity(g_all, want, c_all)
     assert e_all <= 1e-5
+    if walk == 3:
+        g0, c0, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"fp64_tau_exp10": 1, "walk": 0})
+        np.testing.assert_array_equal(g_all, g0)
+        assert c_all == c0
 
 
 def test_identical_doses_zero_and_flat_shift():
