@@ -59,7 +59,10 @@ SEED_GATES = (0, 9, 11, 13)
 FLOP_PER_CELL = {3: 615, 2: 103}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
-KERNELS_PER_RUN = 4          # prepare, shell, scatter, tail
+# kernels of one single-pair run: prepare, shell, scatter and the walk (the
+# warp-evaluated walk adds its finishing pass, k_tail_fix)
+WALKERS = {-1: ("k_tail_cq", 5), 3: ("k_tail_cq", 5), 0: ("k_tail", 4), 1: ("k_walk", 4),
+           2: ("k_walk_rows", 4)}
 LOAD_S = 1.5                 # back-to-back maps before the timed steps (clock samples)
 # gamma within this distance of 1 may pass on one side and fail on the other
 TIE_BAND = 1e-4
@@ -94,6 +97,9 @@ def parse():
                          "(-1: library default)")
     ap.add_argument("--group-bucket", type=int, default=-1,
                     help="walk 3: cost bucket from which queued voxels walk 4 lanes each "
+                         "(-1: library default)")
+    ap.add_argument("--group8-bucket", type=int, default=-1,
+                    help="walk 3: cost bucket from which queued voxels walk 8 lanes each "
                          "(-1: library default)")
     ap.add_argument("--no-vs-plain", action="store_true",
                     help="skip the learned + batched against plain comparison")
@@ -644,7 +650,8 @@ def run_ours(args, pair, rank, world, local_rank):
         g.gamma_set_option(h, "walk", args.walk)
     if args.group_bucket >= 0:
         g.gamma_set_option(h, "group_bucket", args.group_bucket)
-    walk_on = args.walk == 1          # the library walks voxel by voxel by default
+    if args.group8_bucket >= 0:
+        g.gamma_set_option(h, "group8_bucket", args.group8_bucket)
     tuned = None
     if args.lanes or args.shell_blocks or args.tail_blocks:
         launch = {k: v for k, v in (("lanes_per_voxel", args.lanes),
@@ -715,6 +722,8 @@ def run_ours(args, pair, rank, world, local_rank):
             g.gamma_set_option(hh, "walk", args.walk)
         if args.group_bucket >= 0:
             g.gamma_set_option(hh, "group_bucket", args.group_bucket)
+        if args.group8_bucket >= 0:
+            g.gamma_set_option(hh, "group8_bucket", args.group8_bucket)
         for k, v in launch.items():                  # the launch shapes tuned above
             g.gamma_set_option(hh, k, v)
         try:
@@ -761,11 +770,12 @@ def run_ours(args, pair, rank, world, local_rank):
         return
 
     # ---- roofline of the search ----
-    # The exact search runs as two launches, k_shell (faces through each
-    # voxel) and k_tail (the queued voxels' table walks); which launch
-    # certifies a voxel's remaining key-0 faces depends on the pruning, so the
-    # implementation-independent census is charged to the two together.  The
-    # per-kernel figures split it as census key-0 cells / other cells.
+    # The exact search runs as two phases, k_shell (faces through each voxel)
+    # and the queued voxels' table walks (k_tail_cq and its finishing pass by
+    # default); which phase certifies a voxel's remaining key-0 faces depends
+    # on the pruning, so the implementation-independent census is charged to
+    # the two together.  The per-kernel figures split it as census key-0
+    # cells / other cells.
     mean_ph = {k: statistics.mean(v) for k, v in phase.items()}
     shell_cells = tail_cells = None
     roofline = None
@@ -782,7 +792,7 @@ def run_ours(args, pair, rank, world, local_rank):
 
         t_search = mean_ph["shell_ms"] + mean_ph["tail_ms"]
         achieved = tflops(shell_cells + tail_cells, t_search)
-        walker = "k_walk" if walk_on else "k_tail"
+        walker = WALKERS[args.walk][0]
         traffic = [recorded_traffic(k, args.workload) for k in ("k_shell", walker)]
         clock_hz = (clocks.get("sm_mhz") or sm_max) * 1e6
 
@@ -875,7 +885,7 @@ def run_ours(args, pair, rank, world, local_rank):
         "vs_plain": vs_plain,
         "e2e": e2e,
         "clocks": clocks,
-        "gpu_launches": KERNELS_PER_RUN * args.steps,
+        "gpu_launches": WALKERS[args.walk][1] * args.steps,
     }
     print(json.dumps(line), flush=True)
 

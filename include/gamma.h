@@ -200,27 +200,29 @@ int gamma_get_stats(gamma_handle h, gamma_stats *out);
 int gamma_get_timings(gamma_handle h, gamma_timings *out);
 
 /* Tuning and diagnostic options (take effect at the next run):
- *  "walk"             0 (default): the queued voxels are walked voxel by
- *                     voxel from a queue ordered by cost, "lanes_per_voxel"
- *                     lanes each (batch handles and gamma_run_noalloc always
- *                     walk this way); 1: tile by tile: each block stages the
- *                     evaluation doses around one 256-voxel tile in shared
- *                     memory (one TMA copy) and walks the table for that
- *                     tile's queued voxels, the lanes per voxel chosen per
- *                     tile (same results; slower on the benchmark workloads,
- *                     where a tile waits for its most expensive voxel); 2: row
- *                     by row: each warp independently takes one 32-voxel row
- *                     of a shell tile with queued voxels, stages the doses
- *                     around it in shared memory (one TMA copy) and walks the
- *                     table for the row's queued voxels (same results); 3:
- *                     voxel by voxel, one lane per voxel: a cell that passes
- *                     the dose-gap test joins a per-warp buffer, and the warp
- *                     evaluates 32 such cells at a time, one per lane (same
- *                     results; "lanes_per_voxel" does not apply)
+ *  "walk"             3 (default for single-pair handles): voxel by voxel
+ *                     from a queue ordered by cost; a cell that passes the
+ *                     dose-gap test joins a per-warp buffer, and the warp
+ *                     evaluates 32 such cells at a time, one per lane; the
+ *                     most expensive voxels walk 4 lanes each (options
+ *                     "group_bucket", "group8_bucket"; "lanes_per_voxel" does
+ *                     not apply).  0: voxel by voxel, "lanes_per_voxel" lanes
+ *                     each, every lane evaluating its own cells (batch handles
+ *                     and gamma_run_noalloc always walk this way); 1: tile by
+ *                     tile: each block stages the evaluation doses around one
+ *                     256-voxel tile in shared memory (one TMA copy) and walks
+ *                     the table for that tile's queued voxels, the lanes per
+ *                     voxel chosen per tile; 2: row by row: each warp
+ *                     independently takes one 32-voxel row of a shell tile
+ *                     with queued voxels, stages the doses around it in shared
+ *                     memory (one TMA copy) and walks the table for the row's
+ *                     queued voxels.  Every walk gives the same map.
  *  "group_bucket"     "walk" 3: queued voxels whose cost bucket (1 + floor(2
  *                     log2 of the cells below their starting bound)) is at
  *                     least this value walk 4 lanes each, the rest one lane
  *                     each (default 9; 32: every voxel one lane)
+ *  "group8_bucket"    "walk" 3: ... and those of this bucket and above 8
+ *                     lanes each (default 32: none)
  *  "lanes_per_voxel"  2, 4, 8, 16 or 32 lanes search one queued voxel together
  *                     (the voxel-by-voxel walk, "walk" 0)
  *  "table_cap"        maximum cell-table length (rebuilds the table)
@@ -311,8 +313,9 @@ int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
 
 /* Autotuner: times the full run (single or batch handle) for every
  * combination of lanes_per_voxel in {2, 4, 8, 16, 32} (not varied for the
- * tile-staged walk, which picks its own), shell_blocks_per_sm in
- * {1, 2, 3, 4} and tail_blocks_per_sm in {1, 2, 3} (two warm-ups and `reps` timed
+ * staged and the warp-evaluated walks, which take none), shell_blocks_per_sm
+ * in {1, 2, 3, 4} and tail_blocks_per_sm in {1, 2, 3} ({1, 2, 3, 4} for the
+ * warp-evaluated walk) (two warm-ups and `reps` timed
  * runs each, CUDA events on `cuda_stream`), keeps the fastest as the handle's
  * options and returns it (any output pointer may be NULL).  gamma_out_dev receives the
  * gamma map of a single-pair handle (device, nz*ny*nx floats) and is ignored

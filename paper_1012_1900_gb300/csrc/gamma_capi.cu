@@ -117,7 +117,8 @@ struct gamma_ctx {
     // warp-evaluated walk: voxels left to its finishing pass (tail_cap entries)
     unsigned* fix_list = nullptr;
     int group_bucket = 9;             // ... queued voxels of this cost bucket and above walk 4 lanes each
-    int walk = 0;                     // 0: voxel queue walk (k_tail); 1: tile-staged (k_walk);
+    int group8_bucket = 32;           // ... and of this one and above 8 lanes each (32: none)
+    int walk = 3;                     // 0: voxel queue walk (k_tail); 1: tile-staged (k_walk);
                                       // 2: row-staged (k_walk_rows); 3: voxel queue walk with
                                       // the warp evaluating surviving cells together (k_tail_cq)
     // options
@@ -309,6 +310,7 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.seed_cap = h->seed_cap;
     P.fix_list = h->fix_list;
     P.cq_group_bucket = h->group_bucket;
+    P.cq_group8_bucket = h->group8_bucket;
     if (h->walk == 1 && h->tile_mask) {
         P.tile_mask = h->tile_mask;
         P.tile_list = h->tile_list;
@@ -1234,9 +1236,9 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         h->walk = (int)value;
         return GAMMA_OK;
     }
-    if (!std::strcmp(key, "group_bucket")) {
+    if (!std::strcmp(key, "group_bucket") || !std::strcmp(key, "group8_bucket")) {
         if (h->batch || value < 0 || value > gk::kNumBuckets) return GAMMA_ERR_INVALID_ARG;
-        h->group_bucket = (int)value;
+        (key[5] == '8' ? h->group8_bucket : h->group_bucket) = (int)value;
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "lanes_per_voxel")) {
@@ -1465,9 +1467,10 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     // count: only the block budgets vary
     const bool tile_walk = !h->batch && !h->grids && h->walk != 0;
     const int nl = tile_walk ? 1 : 5;
+    const int tb_max = tile_walk && h->walk == 3 ? 4 : 3;
     for (int li = 0; li < nl && rc == GAMMA_OK; ++li)
         for (int bl = 1; bl <= 4 && rc == GAMMA_OK; ++bl)
-            for (int tb = 1; tb <= 3 && rc == GAMMA_OK; ++tb) {
+            for (int tb = 1; tb <= tb_max && rc == GAMMA_OK; ++tb) {
                 h->lanes = tile_walk ? best_l : lanes[li];
                 h->shell_minblocks = bl;
                 h->tail_minblocks = tb;

@@ -84,7 +84,7 @@ struct Counters {
     unsigned int row_head;              // work counter of the row-staged walk
     unsigned int row_hist[kNumBuckets]; // those rows by their largest cost bucket
     unsigned int row_cursor[kNumBuckets];
-    unsigned int head_group;            // warp-evaluated walk: work counter of the grouped part
+    unsigned int head_part[3];          // warp-evaluated walk: work counters of the queue's parts
     unsigned int fix_count;             // ... voxels it leaves to the finishing pass
 };
 
@@ -153,10 +153,12 @@ struct Problem {
     unsigned long long* row_items;
     unsigned char* row_bkt;
     unsigned long long* row_sorted;
-    // warp-evaluated walk (k_tail_cq): queued voxels of this cost bucket and
-    // above walk with several lanes each; fix_list (tail_cap entries) holds
-    // the voxels whose exact result the finishing pass completes
+    // warp-evaluated walk (k_tail_cq): queued voxels of cost bucket
+    // cq_group8_bucket and above walk 8 lanes each, of cq_group_bucket and
+    // above 4; fix_list (tail_cap entries) holds the voxels whose exact result
+    // the finishing pass completes
     int cq_group_bucket;
+    int cq_group8_bucket;
     unsigned* fix_list;
 };
 

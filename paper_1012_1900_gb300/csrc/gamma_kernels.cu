@@ -763,8 +763,9 @@ __global__ void __launch_bounds__(256, MINB)
 // start its next voxel while the cells of the previous one still wait.
 //
 // The queue is ordered by cost bucket, most expensive first: the voxels of
-// bucket cq_group_bucket and above walk GX lanes each (GX table entries per
-// step), which shortens the longest walks; the rest walk one lane each.  The
+// bucket cq_group8_bucket and above walk 8 lanes each (8 table entries per
+// step), those of bucket cq_group_bucket and above 4 lanes each, which
+// shortens the longest walks; the rest walk one lane each.  The
 // rare paths (a cell whose Gram matrix is near singular, a walk that runs past
 // a truncated table) are not taken here: such a voxel goes to fix_list with
 // its bound, and k_tail_fix finishes it, so that this kernel's registers stay
@@ -794,25 +795,35 @@ struct CqWarp {
 constexpr unsigned kCqWalk = 1u, kCqEnded = 2u, kCqWPend = 4u, kCqDBusy = 8u, kCqDPend = 16u,
                    kCqDOver = 32u, kCqSlot = 64u;     // slot bit: the walking slot is walker + 32
 
-template <int N, int MINB, int GX>
+// Lanes per voxel of the three parts of the queue.
+__device__ __forceinline__ int cq_part_lanes(int part) { return part == 0 ? 8 : (part == 1 ? 4 : 1); }
+
+template <int N, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ Problem P)
 {
     __shared__ CqWarp cqw[8];
-    __shared__ unsigned s_total, s_ngroup;
+    __shared__ unsigned s_end[3];      // the parts of the queue end at these items
     __shared__ float s_dnorm;
     CqWarp& W = cqw[threadIdx.x >> 5];
     volatile CqWarp& V = cqw[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (threadIdx.x < 32) {
-        // items [0, s_ngroup) of the cost-ordered queue walk GX lanes each
+        // the cost-ordered queue: items of bucket >= cq_group8_bucket first,
+        // then those of bucket >= cq_group_bucket, then the rest
         const unsigned total = min(P.ctr->tail_count, P.tail_cap);
-        unsigned h = (P.sort_tail && GX > 1 && lane >= P.cq_group_bucket) ? P.ctr->hist[lane] : 0u;
+        const unsigned hb = P.sort_tail ? P.ctr->hist[lane] : 0u;
+        unsigned h8 = lane >= P.cq_group8_bucket ? hb : 0u;
+        unsigned h4 = lane >= min(P.cq_group_bucket, P.cq_group8_bucket) ? hb : 0u;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            h8 += __shfl_xor_sync(kFull, h8, o);
+            h4 += __shfl_xor_sync(kFull, h4, o);
+        }
         if (lane == 0) {
-            s_total = total;
-            s_ngroup = min(h, total);
+            s_end[0] = min(h8, total);
+            s_end[1] = min(h4, total);
+            s_end[2] = total;
             s_dnorm = resolve_dnorm(P);
         }
     }
@@ -825,7 +836,9 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
     __syncthreads();
 
     const float rc2 = P.r_cover * P.r_cover;
-    int g = s_ngroup > 0 ? GX : 1;     // lanes per voxel in the current part of the queue
+    int part = 0;                      // the part of the queue this warp takes voxels from
+    while (part < 2 && s_end[part] == (part ? s_end[part - 1] : 0u)) ++part;
+    int g = cq_part_lanes(part);       // its lanes per voxel
     unsigned head = 0, count = 0;      // the ring: pending cells are [head, head + count)
     bool queue_done = false;           // warp-uniform, for the current part
     for (;;) {
@@ -863,9 +876,9 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
         const bool empty = leader && !(sta & (kCqWalk | kCqEnded));
         const unsigned need = __ballot_sync(kFull, empty);
         if (need && !queue_done) {
-            const unsigned lo = g > 1 ? 0u : s_ngroup, hi = g > 1 ? s_ngroup : s_total;
+            const unsigned lo = part ? s_end[part - 1] : 0u, hi = s_end[part];
             unsigned base = 0;
-            if (lane == 0) base = atomicAdd(g > 1 ? &P.ctr->head_group : &P.ctr->head, (unsigned)__popc(need));
+            if (lane == 0) base = atomicAdd(&P.ctr->head_part[part], (unsigned)__popc(need));
             base = __shfl_sync(kFull, base, 0) + lo;
             if (base + (unsigned)__popc(need) >= hi) queue_done = true;
             if (empty) {
@@ -892,8 +905,9 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
         __syncwarp();
         sta = V.state[ld];                 // the group's lanes follow their walker
         if (queue_done && !__any_sync(kFull, (sta & (kCqWalk | kCqEnded | kCqDBusy)) != 0)) {
-            if (g == 1) break;
-            g = 1;                         // the grouped part is done: one lane per voxel
+            if (part == 2) break;
+            ++part;                        // this part is done: the next, with fewer lanes per voxel
+            g = cq_part_lanes(part);
             queue_done = false;
             V.state[lane] = 0;
             __syncwarp();
@@ -1928,10 +1942,10 @@ cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblock
 template <int N>
 static void launch_tail_cq_n(const Problem& P, int per_sm, int grid, cudaStream_t s)
 {
-    if (per_sm >= 4) k_tail_cq<N, 4, 4><<<grid, 256, 0, s>>>(P);
-    else if (per_sm == 3) k_tail_cq<N, 3, 4><<<grid, 256, 0, s>>>(P);
-    else if (per_sm == 2) k_tail_cq<N, 2, 4><<<grid, 256, 0, s>>>(P);
-    else k_tail_cq<N, 1, 4><<<grid, 256, 0, s>>>(P);
+    if (per_sm >= 4) k_tail_cq<N, 4><<<grid, 256, 0, s>>>(P);
+    else if (per_sm == 3) k_tail_cq<N, 3><<<grid, 256, 0, s>>>(P);
+    else if (per_sm == 2) k_tail_cq<N, 2><<<grid, 256, 0, s>>>(P);
+    else k_tail_cq<N, 1><<<grid, 256, 0, s>>>(P);
     k_tail_fix<N><<<device_sm_count() * 2, 256, 0, s>>>(P);
 }
 

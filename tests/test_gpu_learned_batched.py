@@ -136,6 +136,7 @@ def test_trained_network_on_a_held_out_pair_stays_exact_and_saves_cells():
                     g.gamma_set_model(h, model)
                     g.gamma_set_option(h, "seed_min_bucket", 0)
                 g.gamma_set_option(h, "stats", 1)
+                g.gamma_set_option(h, "walk", 0)      # cell counts of the voxel walk
                 g.gamma_run(h, o)
                 counts = g.gamma_pass_rate(h)
                 res[name] = (o.cpu().numpy().astype(np.float64), counts, g.gamma_get_stats(h))

@@ -153,22 +153,24 @@ def test_launch_shapes_agree(lanes, sort_tail, tail_blocks):
     p = synth.workload("imrt_small")
     crit = synth.Criteria(0.01, 1.0, local=True)
     got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit,
-                               {"lanes_per_voxel": lanes, "sort_tail": sort_tail,
+                               {"walk": 0, "lanes_per_voxel": lanes, "sort_tail": sort_tail,
                                 "tail_blocks_per_sm": tail_blocks})
     want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
     assert_parity(got, want, counts)
 
 
+@pytest.mark.parametrize("walk", [0, 3])
 @pytest.mark.parametrize("ndim", [2, 3])
-def test_truncated_table_box_scan(ndim):
-    # A tiny table forces most voxels past its end, into the box scan.
+def test_truncated_table_box_scan(ndim, walk):
+    # A tiny table forces most voxels past its end, into the box scan (for
+    # walk = 3, in its finishing pass).
     if ndim == 2:
         p = synth.make_pair_2d(shape=(30, 26), seed=5, shift_mm=(2.0, 1.0), scale=1.06)
     else:
         p = synth.make_pair_3d(shape=(14, 18, 16), spacing=(2.0, 2.0, 2.0), seed=6,
                                shift_mm=(1.0, 2.0, 2.5), scale=1.06)
     crit = synth.Criteria(0.01, 1.0, local=True)
-    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"table_cap": 16})
+    got, counts, st = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"table_cap": 16, "walk": walk})
     assert st["overflow_voxels"] > 0
     want = oracle_gamma(p.ref, p.eval, p.spacing, crit)
     assert_parity(got, want, counts)
@@ -213,17 +215,19 @@ def test_staged_walks(case, blocks, walk):
 
 
 @pytest.mark.parametrize("crit", [(0.03, 3.0, False), (0.01, 1.0, True)], ids=["3-3", "1-1-local"])
-@pytest.mark.parametrize("group_bucket", [0, 9, 32])
+@pytest.mark.parametrize("groups", [(0, 32), (32, 0), (9, 13), (32, 32), (5, 9)],
+                         ids=["all4", "all8", "default", "none", "low"])
 @pytest.mark.parametrize("blocks", [1, 2, 3, 4])
-def test_warp_evaluated_walk_is_bitwise_the_voxel_walk(crit, group_bucket, blocks):
+def test_warp_evaluated_walk_is_bitwise_the_voxel_walk(crit, groups, blocks):
     # walk = 3 evaluates every cell with the same arithmetic as walk = 0 and
     # reaches the same minimising cell, so the two maps agree bit for bit,
-    # whichever voxels walk four lanes each (group_bucket 0: all of them; 32:
-    # none) and at every register budget
+    # whichever voxels walk four or eight lanes each (a threshold of 0: all
+    # of them; 32: none) and at every register budget
     p = synth.workload("imrt_small")
     c = synth.Criteria(crit[0], crit[1], local=crit[2])
     a, ca, sa = gpu_gamma(p.ref, p.eval, p.spacing, c, {"walk": 0, "lanes_per_voxel": 2, "stats": 1})
-    b, cb, sb = gpu_gamma(p.ref, p.eval, p.spacing, c, {"walk": 3, "stats": 1, "group_bucket": group_bucket,
+    b, cb, sb = gpu_gamma(p.ref, p.eval, p.spacing, c, {"walk": 3, "stats": 1, "group_bucket": groups[0],
+                                                      "group8_bucket": groups[1],
                                                       "tail_blocks_per_sm": blocks})
     np.testing.assert_array_equal(a, b)
     assert ca == cb
