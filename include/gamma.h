@@ -200,15 +200,16 @@ int gamma_get_stats(gamma_handle h, gamma_stats *out);
 int gamma_get_timings(gamma_handle h, gamma_timings *out);
 
 /* Tuning and diagnostic options (take effect at the next run):
- *  "walk"             3 (default for single-pair handles): voxel by voxel
+ *  "walk"             3 (default): voxel by voxel
  *                     from a queue ordered by cost; a cell that passes the
  *                     dose-gap test joins a per-warp buffer, and the warp
  *                     evaluates 32 such cells at a time, one per lane; the
  *                     most expensive voxels walk 4 lanes each (options
  *                     "group_bucket", "group8_bucket"; "lanes_per_voxel" does
  *                     not apply).  0: voxel by voxel, "lanes_per_voxel" lanes
- *                     each, every lane evaluating its own cells (batch handles
- *                     and gamma_run_noalloc always walk this way); 1: tile by
+ *                     each, every lane evaluating its own cells
+ *                     (gamma_run_noalloc always walks this way; batch handles
+ *                     take 0 or 3 only); 1: tile by
  *                     tile: each block stages the evaluation doses around one
  *                     256-voxel tile in shared memory (one TMA copy) and walks
  *                     the table for that tile's queued voxels, the lanes per
@@ -223,6 +224,8 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     each (default 9; 32: every voxel one lane)
  *  "group8_bucket"    "walk" 3: ... and those of this bucket and above 8
  *                     lanes each (default 32: none)
+ *  "group32_bucket"   "walk" 3: ... and those of this bucket and above 32
+ *                     lanes, a whole warp, each (default 32: none)
  *  "lanes_per_voxel"  2, 4, 8, 16 or 32 lanes search one queued voxel together
  *                     (the voxel-by-voxel walk, "walk" 0)
  *  "table_cap"        maximum cell-table length (rebuilds the table)

@@ -118,6 +118,7 @@ struct gamma_ctx {
     unsigned* fix_list = nullptr;
     int group_bucket = 9;             // ... queued voxels of this cost bucket and above walk 4 lanes each
     int group8_bucket = 32;           // ... and of this one and above 8 lanes each (32: none)
+    int group32_bucket = 32;          // ... and of this one and above 32 lanes each (32: none)
     int walk = 3;                     // 0: voxel queue walk (k_tail); 1: tile-staged (k_walk);
                                       // 2: row-staged (k_walk_rows); 3: voxel queue walk with
                                       // the warp evaluating surviving cells together (k_tail_cq)
@@ -311,6 +312,7 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.fix_list = h->fix_list;
     P.cq_group_bucket = h->group_bucket;
     P.cq_group8_bucket = h->group8_bucket;
+    P.cq_group32_bucket = h->group32_bucket;
     if (h->walk == 1 && h->tile_mask) {
         P.tile_mask = h->tile_mask;
         P.tile_list = h->tile_list;
@@ -405,7 +407,10 @@ struct BatchState {
         unsigned* item_start = nullptr;
         unsigned* items_v = nullptr;
         unsigned short* items_p = nullptr;
-        unsigned* head = nullptr;          // walk, shell tiles, seed rows, seeding work
+        unsigned* head = nullptr;          // walk, shell tiles, seed rows, seeding work,
+                                           // warp-evaluated walk parts (3), its fix count
+        unsigned* fix_v = nullptr;         // warp-evaluated walk: voxels for its finishing pass
+        unsigned short* fix_p = nullptr;
         unsigned* seed_item = nullptr;     // with a model: (pair, item) rows past the gate
         unsigned short* seed_pair = nullptr;
         __nv_bfloat16* seed_X = nullptr;   // ... their network inputs and outputs
@@ -432,6 +437,8 @@ void free_group(BatchState::Group& g)
     cudaFree(g.items_v);
     cudaFree(g.items_p);
     cudaFree(g.head);
+    cudaFree(g.fix_v);
+    cudaFree(g.fix_p);
     cudaFree(g.seed_item);
     cudaFree(g.seed_pair);
     cudaFree(g.seed_X);
@@ -493,12 +500,15 @@ int batch_upload(gamma_ctx* h)
             CK(cudaMalloc(&G.maps, sizeof(CUtensorMap) * np));
             CK(cudaMalloc(&G.use_tma, sizeof(int) * np));
             CK(cudaMalloc(&G.tile_start, sizeof(int) * (np + 1)));
-            CK(cudaMalloc(&G.item_start, sizeof(unsigned) * (gk::kNumBuckets * np + 1)));
+            CK(cudaMalloc(&G.item_start, sizeof(unsigned) * (gk::kNumBuckets * np + 4)));
             size_t cap = 0;
             for (int k = 0; k < np; ++k) cap += b->pairs[mem[k]]->tail_cap;
             CK(cudaMalloc(&G.items_v, sizeof(unsigned) * std::max<size_t>(cap, 1)));
             CK(cudaMalloc(&G.items_p, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
-            CK(cudaMalloc(&G.head, 4 * sizeof(unsigned)));   // walk, shell tiles, seeding
+            CK(cudaMalloc(&G.fix_v, sizeof(unsigned) * std::max<size_t>(cap, 1)));
+            CK(cudaMalloc(&G.fix_p, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
+            CK(cudaMalloc(&G.head, 12 * sizeof(unsigned)));
+            CK(cudaMemset(G.head, 0, 12 * sizeof(unsigned)));
             CK(cudaMalloc(&G.desc, sizeof(gk::BatchDesc)));
         }
         if (h->model && !G.seed_item) {
@@ -525,6 +535,13 @@ int batch_upload(gamma_ctx* h)
         d.items_p = G.items_p;
         d.head = G.head;
         d.shell_next = G.head + 1;
+        d.group_bucket = h->walk == 3 ? h->group_bucket : 0;
+        d.group8_bucket = h->walk == 3 ? h->group8_bucket : 0;
+        d.group32_bucket = h->walk == 3 ? h->group32_bucket : 0;
+        d.part_head = G.head + 4;
+        d.fix_v = G.fix_v;
+        d.fix_p = G.fix_p;
+        d.fix_count = G.head + 8;
         if (h->model) {
             d.seed_item = G.seed_item;
             d.seed_pair = G.seed_pair;
@@ -572,7 +589,7 @@ int batch_enqueue(gamma_ctx* h, cudaStream_t s)
     if (tm) CK(cudaEventRecord(h->tev[3], s));
     for (auto& G : b->grp) CK(gk::launch_batch_order(G.host, s));
     if (tm) CK(cudaEventRecord(h->tev[4], s));
-    for (auto& G : b->grp) CK(gk::launch_batch_tail(G.host, h->lanes, h->tail_minblocks, s));
+    for (auto& G : b->grp) CK(gk::launch_batch_tail(G.host, h->walk, h->lanes, h->tail_minblocks, s));
     if (tm) {
         CK(cudaEventRecord(h->tev[5], s));
         CK(cudaEventRecord(h->tev[6], s));
@@ -1232,13 +1249,17 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "walk")) {
-        if (h->batch || value < 0 || value > 3) return GAMMA_ERR_INVALID_ARG;
+        // batch handles walk voxel by voxel: with (3) or without (0) the warp evaluation
+        if (value < 0 || value > 3 || (h->batch && value != 0 && value != 3)) return GAMMA_ERR_INVALID_ARG;
         h->walk = (int)value;
+        if (h->batch) h->batch->dirty = true;
         return GAMMA_OK;
     }
-    if (!std::strcmp(key, "group_bucket") || !std::strcmp(key, "group8_bucket")) {
-        if (h->batch || value < 0 || value > gk::kNumBuckets) return GAMMA_ERR_INVALID_ARG;
-        (key[5] == '8' ? h->group8_bucket : h->group_bucket) = (int)value;
+    if (!std::strcmp(key, "group_bucket") || !std::strcmp(key, "group8_bucket") ||
+        !std::strcmp(key, "group32_bucket")) {
+        if (value < 0 || value > gk::kNumBuckets) return GAMMA_ERR_INVALID_ARG;
+        (key[5] == '8' ? h->group8_bucket : key[5] == '3' ? h->group32_bucket : h->group_bucket) = (int)value;
+        if (h->batch) h->batch->dirty = true;
         return GAMMA_OK;
     }
     if (!std::strcmp(key, "lanes_per_voxel")) {
@@ -1465,7 +1486,7 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
     auto run = [&]() { return h->batch ? gamma_batch_run(h, s) : gamma_run(h, gamma_out_dev, s); };
     // the staged walks and the warp-evaluated queue walk do not take a lane
     // count: only the block budgets vary
-    const bool tile_walk = !h->batch && !h->grids && h->walk != 0;
+    const bool tile_walk = !h->grids && h->walk != 0;
     const int nl = tile_walk ? 1 : 5;
     const int tb_max = tile_walk && h->walk == 3 ? 4 : 3;
     for (int li = 0; li < nl && rc == GAMMA_OK; ++li)

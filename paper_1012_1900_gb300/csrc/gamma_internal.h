@@ -84,7 +84,7 @@ struct Counters {
     unsigned int row_head;              // work counter of the row-staged walk
     unsigned int row_hist[kNumBuckets]; // those rows by their largest cost bucket
     unsigned int row_cursor[kNumBuckets];
-    unsigned int head_part[3];          // warp-evaluated walk: work counters of the queue's parts
+    unsigned int head_part[4];          // warp-evaluated walk: work counters of the queue's parts
     unsigned int fix_count;             // ... voxels it leaves to the finishing pass
 };
 
@@ -154,11 +154,12 @@ struct Problem {
     unsigned char* row_bkt;
     unsigned long long* row_sorted;
     // warp-evaluated walk (k_tail_cq): queued voxels of cost bucket
-    // cq_group8_bucket and above walk 8 lanes each, of cq_group_bucket and
-    // above 4; fix_list (tail_cap entries) holds the voxels whose exact result
-    // the finishing pass completes
+    // cq_group32_bucket and above walk 32 lanes each, of cq_group8_bucket and
+    // above 8, of cq_group_bucket and above 4; fix_list (tail_cap entries)
+    // holds the voxels whose exact result the finishing pass completes
     int cq_group_bucket;
     int cq_group8_bucket;
+    int cq_group32_bucket;
     unsigned* fix_list;
 };
 
@@ -180,11 +181,21 @@ struct BatchDesc {
     const CUtensorMap* maps;       // [npairs] evaluation-dose tile maps
     const int* use_tma;            // [npairs] 1: the map is valid for TMA loads
     const int* tile_start;         // [npairs + 1] first global shell tile of each pair
-    unsigned* item_start;          // [npairs * kNumBuckets + 1] queued voxels ordered
-                                   // by (pair, cost bucket descending)
+    unsigned* item_start;          // [npairs * kNumBuckets + 4] start of each (pair, cost
+                                   // bucket) range of the queued voxels, their total, and
+                                   // the ends of the first three parts (k_bucket_scan_batch)
     unsigned* items_v;             // [sum of tail_cap] queued voxels in that order
     unsigned short* items_p;       // [sum of tail_cap] their pair
     unsigned* head;                // work counter of the group's table walk
+    // warp-evaluated walk: cost buckets from which the queued voxels walk 4,
+    // 8 and 32 lanes each (the queue's parts, costliest first; all 0 keeps one
+    // pair-major order), the work counters of the parts, and the voxels (with
+    // their pair) left to the finishing pass
+    int group_bucket, group8_bucket, group32_bucket;
+    unsigned* part_head;           // [4]
+    unsigned* fix_v;               // [sum of tail_cap]
+    unsigned short* fix_p;
+    unsigned* fix_count;
     unsigned* shell_next;          // tile counter of the group's shell (zeroed by its prepare)
     // learned seeding (null without a model): queue items of every pair past
     // the cost gate, as (pair, item) rows, their count and the work counter of
@@ -315,7 +326,8 @@ cudaError_t launch_labels(const Problem& P, const float* gmap, const unsigned* v
 cudaError_t launch_batch_prepare(const BatchGroup& g, cudaStream_t s);
 cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStream_t s);
 cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s);
-cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, int tail_minblocks,
+// walk: 3 the warp-evaluated walk, else the voxel walk with lanes_per_voxel.
+cudaError_t launch_batch_tail(const BatchGroup& g, int walk, int lanes_per_voxel, int tail_minblocks,
                               cudaStream_t s);
 // Tensor map of a row-major bf16 matrix (inner elements x rows, row stride in
 // bytes) with boxes of box_inner x box_rows elements; false when the driver's

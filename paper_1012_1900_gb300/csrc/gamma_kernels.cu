@@ -501,39 +501,109 @@ __global__ void __launch_bounds__(256) k_scatter_rows(const __grid_constant__ Pr
     }
 }
 
-// Global order of a batch group's queued voxels: pair by pair (so that the
-// walks in flight share one pair's doses in L2), most expensive bucket first
-// within a pair; each pair's cursor[b] starts at its range in that order.
-__global__ void k_bucket_scan_batch(const BatchDesc* __restrict__ bd)
+// Global order of a batch group's queued voxels, in four parts by cost
+// bucket: b >= group32_bucket, then b >= group8_bucket, then b >=
+// group_bucket, then the rest (the thresholds made non-increasing); within a
+// part pair by pair (so that the walks in flight share one pair's doses in
+// L2), most expensive bucket first within a pair.  All thresholds 0 give one
+// pair-major order.  Each pair's cursor[b] starts at its range in that order;
+// item_start holds those starts, the total and the ends of the first three
+// parts, and the walk's work counters restart.  One block.
+__global__ void __launch_bounds__(256) k_bucket_scan_batch(const BatchDesc* __restrict__ bd)
 {
-    const int np = bd->npairs;
-    if (threadIdx.x == 0) {
-        unsigned acc = 0;
-        int k = 0;
-        for (int p = 0; p < np; ++p)
-            for (int b = kNumBuckets - 1; b >= 0; --b) {
-                bd->item_start[k++] = acc;
-                acc += bd->probs[p].ctr->hist[b];
-            }
-        bd->item_start[k] = acc;
-        *bd->head = 0;
+    __shared__ unsigned tot[4];
+    __shared__ unsigned sc[4][256];
+    const int np = bd->npairs, tid = threadIdx.x;
+    const int b32 = bd->group32_bucket, b8 = min(bd->group8_bucket, b32),
+              b4 = min(bd->group_bucket, b8);
+    auto part_of = [&](int b) { return b >= b32 ? 0 : (b >= b8 ? 1 : (b >= b4 ? 2 : 3)); };
+    auto sums = [&](int p, unsigned (&u)[4]) {
+        u[0] = u[1] = u[2] = u[3] = 0;
+        if (p >= np) return;
+        const Counters* c = bd->probs[p].ctr;
+        for (int b = 0; b < kNumBuckets; ++b) u[part_of(b)] += c->hist[b];
+    };
+    if (tid < 4) tot[tid] = 0;
+    __syncthreads();
+    for (int p = tid; p < np; p += blockDim.x) {
+        unsigned u[4];
+        sums(p, u);
+        for (int r = 0; r < 4; ++r)
+            if (u[r]) atomicAdd(&tot[r], u[r]);
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        Counters* c = bd->probs[p].ctr;
-        for (int b = 0; b < kNumBuckets; ++b) c->cursor[b] = bd->item_start[p * kNumBuckets + (kNumBuckets - 1 - b)];
+    unsigned rb[4], carry[4] = {0, 0, 0, 0};
+    rb[0] = 0;
+    for (int r = 1; r < 4; ++r) rb[r] = rb[r - 1] + tot[r - 1];
+    for (int c0 = 0; c0 < np; c0 += blockDim.x) {
+        const int p = c0 + tid;
+        unsigned u[4];
+        sums(p, u);
+        for (int r = 0; r < 4; ++r) sc[r][tid] = u[r];
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {      // inclusive scans, per part
+            unsigned v[4];
+            for (int r = 0; r < 4; ++r) v[r] = tid >= o ? sc[r][tid - o] : 0u;
+            __syncthreads();
+            for (int r = 0; r < 4; ++r) sc[r][tid] += v[r];
+            __syncthreads();
+        }
+        if (p < np) {
+            Counters* c = bd->probs[p].ctr;
+            unsigned start[4];
+            for (int r = 0; r < 4; ++r) start[r] = rb[r] + carry[r] + sc[r][tid] - u[r];
+            for (int b = kNumBuckets - 1; b >= 0; --b) {
+                const int r = part_of(b);
+                bd->item_start[p * kNumBuckets + (kNumBuckets - 1 - b)] = start[r];
+                c->cursor[b] = start[r];
+                start[r] += c->hist[b];
+            }
+        }
+        for (int r = 0; r < 4; ++r) carry[r] += sc[r][blockDim.x - 1];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int nb = np * kNumBuckets;
+        bd->item_start[nb] = rb[3] + tot[3];
+        bd->item_start[nb + 1] = rb[1];
+        bd->item_start[nb + 2] = rb[2];
+        bd->item_start[nb + 3] = rb[3];
+        *bd->head = 0;
+        if (bd->part_head) {
+            for (int r = 0; r < 4; ++r) bd->part_head[r] = 0;
+            *bd->fix_count = 0;
+        }
     }
 }
 
+// Scatter one pair (blockIdx.y) of a batch group into the group order: per
+// chunk of 256 queued voxels one atomic per cost bucket on the pair's cursor
+// (as k_scatter), not one per voxel.
 __global__ void __launch_bounds__(256) k_scatter_batch(const BatchDesc* __restrict__ bd)
 {
+    __shared__ unsigned cnt[kNumBuckets], base[kNumBuckets];
     const Problem& P = bd->probs[blockIdx.y];
     const unsigned total = min(P.ctr->tail_count, P.tail_cap);
-    const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const unsigned pos = atomicAdd(&P.ctr->cursor[P.tail_bucket[i]], 1u);
-        bd->items_v[pos] = P.tail_raw[i];
-        bd->items_p[pos] = (unsigned short)blockIdx.y;
+    for (unsigned c0 = blockIdx.x * blockDim.x; c0 < total; c0 += gridDim.x * blockDim.x) {
+        if (threadIdx.x < kNumBuckets) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned i = c0 + threadIdx.x;
+        int b = -1;
+        unsigned rank = 0;
+        if (i < total) {
+            b = P.tail_bucket[i];
+            rank = atomicAdd(&cnt[b], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumBuckets && cnt[threadIdx.x])
+            base[threadIdx.x] = atomicAdd(&P.ctr->cursor[threadIdx.x], cnt[threadIdx.x]);
+        __syncthreads();
+        if (b >= 0) {
+            const unsigned pos = base[b] + rank;
+            bd->items_v[pos] = P.tail_raw[i];
+            bd->items_p[pos] = (unsigned short)blockIdx.y;
+        }
+        __syncthreads();
     }
 }
 
@@ -790,54 +860,101 @@ struct CqWarp {
     unsigned dseq[32];         // the same for the voxel in the drain slot
     unsigned state[32];        // kCq* bits below
     unsigned cnt[2][32];       // voxels finished and passed
+    int cpair[32];             // batched: the pair those counts belong to
+    unsigned short pair[64];   // batched: the pair of each voxel slot
     unsigned long long stat[3][32];    // cells visited, pruned, keyed (option "stats")
 };
 constexpr unsigned kCqWalk = 1u, kCqEnded = 2u, kCqWPend = 4u, kCqDBusy = 8u, kCqDPend = 16u,
                    kCqDOver = 32u, kCqSlot = 64u;     // slot bit: the walking slot is walker + 32
 
-// Lanes per voxel of the three parts of the queue.
-__device__ __forceinline__ int cq_part_lanes(int part) { return part == 0 ? 8 : (part == 1 ? 4 : 1); }
+// Lanes per voxel of the four parts of the queue.
+constexpr int kCqParts = 4;
+__device__ __forceinline__ int cq_part_lanes(int part)
+{
+    return part == 0 ? 32 : (part == 1 ? 8 : (part == 2 ? 4 : 1));
+}
 
-template <int N, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ Problem P)
+// The problem a voxel slot belongs to: the launch's own, or (batched) that of
+// the slot's pair.
+template <bool BATCH>
+__device__ __forceinline__ const Problem& cq_prob(const Problem& P0, const BatchDesc* bd,
+                                                  volatile const CqWarp& V, int slot)
+{
+    if constexpr (BATCH) return bd->probs[V.pair[slot]];
+    else return P0;
+}
+
+// Hands a walker's counts to their pair (batched launches).
+__device__ __forceinline__ void cq_flush_counts(const BatchDesc* bd, volatile CqWarp& V, int w)
+{
+    const int pr = V.cpair[w];
+    if (pr >= 0) {
+        Counters* c = bd->probs[pr].ctr;
+        if (V.cnt[0][w]) atomicAdd(&c->n_eval, (unsigned long long)V.cnt[0][w]);
+        if (V.cnt[1][w]) atomicAdd(&c->n_pass, (unsigned long long)V.cnt[1][w]);
+    }
+    V.cnt[0][w] = 0;
+    V.cnt[1][w] = 0;
+}
+
+template <int N, int MINB, bool BATCH>
+__global__ void __launch_bounds__(256, MINB)
+    k_tail_cq(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd)
 {
     __shared__ CqWarp cqw[8];
-    __shared__ unsigned s_end[3];      // the parts of the queue end at these items
-    __shared__ float s_dnorm;
+    __shared__ unsigned s_end[kCqParts];   // the parts of the queue end at these items
     CqWarp& W = cqw[threadIdx.x >> 5];
     volatile CqWarp& V = cqw[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (threadIdx.x < 32) {
-        // the cost-ordered queue: items of bucket >= cq_group8_bucket first,
-        // then those of bucket >= cq_group_bucket, then the rest
-        const unsigned total = min(P.ctr->tail_count, P.tail_cap);
-        const unsigned hb = P.sort_tail ? P.ctr->hist[lane] : 0u;
-        unsigned h8 = lane >= P.cq_group8_bucket ? hb : 0u;
-        unsigned h4 = lane >= min(P.cq_group_bucket, P.cq_group8_bucket) ? hb : 0u;
+        if constexpr (BATCH) {
+            // the group's queue: voxels of bucket >= the group bucket of every
+            // pair first, then the rest (k_bucket_scan_batch)
+            if (lane == 0) {
+                const int nb = kNumBuckets * bd->npairs;
+                s_end[0] = bd->item_start[nb + 1];
+                s_end[1] = bd->item_start[nb + 2];
+                s_end[2] = bd->item_start[nb + 3];
+                s_end[3] = bd->item_start[nb];
+            }
+        } else {
+            // the cost-ordered queue: items of bucket >= cq_group32_bucket
+            // first, then those of bucket >= cq_group8_bucket, then >=
+            // cq_group_bucket, then the rest
+            const Problem& P = P0;
+            const unsigned total = min(P.ctr->tail_count, P.tail_cap);
+            const unsigned hb = P.sort_tail ? P.ctr->hist[lane] : 0u;
+            const int b32 = P.cq_group32_bucket, b8 = min(P.cq_group8_bucket, b32),
+                      b4 = min(P.cq_group_bucket, b8);
+            unsigned h32 = lane >= b32 ? hb : 0u, h8 = lane >= b8 ? hb : 0u, h4 = lane >= b4 ? hb : 0u;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            h8 += __shfl_xor_sync(kFull, h8, o);
-            h4 += __shfl_xor_sync(kFull, h4, o);
-        }
-        if (lane == 0) {
-            s_end[0] = min(h8, total);
-            s_end[1] = min(h4, total);
-            s_end[2] = total;
-            s_dnorm = resolve_dnorm(P);
+            for (int o = 16; o > 0; o >>= 1) {
+                h32 += __shfl_xor_sync(kFull, h32, o);
+                h8 += __shfl_xor_sync(kFull, h8, o);
+                h4 += __shfl_xor_sync(kFull, h4, o);
+            }
+            if (lane == 0) {
+                s_end[0] = min(h32, total);
+                s_end[1] = min(h8, total);
+                s_end[2] = min(h4, total);
+                s_end[3] = total;
+            }
         }
     }
     W.state[lane] = 0;
     W.wseq[lane] = W.dseq[lane] = 0;
     W.cnt[0][lane] = W.cnt[1][lane] = 0;
+    W.cpair[lane] = -1;
+    W.pair[lane] = W.pair[lane + 32] = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) W.stat[k][lane] = 0;
     if (lane < 2) W.fixm[lane] = 0;
     __syncthreads();
+    unsigned* const heads = BATCH ? bd->part_head : P0.ctr->head_part;
 
-    const float rc2 = P.r_cover * P.r_cover;
     int part = 0;                      // the part of the queue this warp takes voxels from
-    while (part < 2 && s_end[part] == (part ? s_end[part - 1] : 0u)) ++part;
+    while (part < kCqParts - 1 && s_end[part] == (part ? s_end[part - 1] : 0u)) ++part;
     int g = cq_part_lanes(part);       // its lanes per voxel
     unsigned head = 0, count = 0;      // the ring: pending cells are [head, head + count)
     bool queue_done = false;           // warp-uniform, for the current part
@@ -850,14 +967,28 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
             // 1. a drained voxel whose cells are all evaluated is final
             if ((sta & kCqDBusy) && (!(sta & kCqDPend) || (int)(head - V.dseq[ld]) > 0)) {
                 const int ds = ld + ((sta & kCqSlot) ? 0 : 32);
+                const Problem& Q = cq_prob<BATCH>(P0, bd, V, ds);
                 const float best = __uint_as_float(V.best[ds]);
                 const unsigned v = V.vox[ds];
-                if (((V.fixm[ds >> 5] >> (ds & 31)) & 1u) || ((sta & kCqDOver) && best > rc2)) {
-                    P.out[v] = best;                        // gamma^2: k_tail_fix completes it
-                    P.fix_list[atomicAdd(&P.ctr->fix_count, 1u)] = v;
+                if (((V.fixm[ds >> 5] >> (ds & 31)) & 1u) ||
+                    ((sta & kCqDOver) && best > Q.r_cover * Q.r_cover)) {
+                    Q.out[v] = best;                        // gamma^2: k_tail_fix completes it
+                    if constexpr (BATCH) {
+                        const unsigned k = atomicAdd(bd->fix_count, 1u);
+                        bd->fix_v[k] = v;
+                        bd->fix_p[k] = V.pair[ds];
+                    } else {
+                        Q.fix_list[atomicAdd(&Q.ctr->fix_count, 1u)] = v;
+                    }
                 } else {
                     const float gam = sqrtf(best);
-                    P.out[v] = gam;
+                    Q.out[v] = gam;
+                    if constexpr (BATCH) {
+                        if (V.cpair[ld] != (int)V.pair[ds]) {
+                            cq_flush_counts(bd, V, ld);
+                            V.cpair[ld] = V.pair[ds];
+                        }
+                    }
                     ++V.cnt[0][ld];
                     if (gam <= 1.f) ++V.cnt[1][ld];
                 }
@@ -865,9 +996,10 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
             }
             // 2. an ended walk becomes the drain slot; the walker takes a new voxel
             if ((sta & kCqEnded) && !(sta & kCqDBusy)) {
+                const int ws = ld + ((sta & kCqSlot) ? 32 : 0);
                 unsigned d = kCqDBusy;
                 if (sta & kCqWPend) d |= kCqDPend;
-                if (V.t[ld] >= P.ntable) d |= kCqDOver;
+                if (V.t[ld] >= cq_prob<BATCH>(P0, bd, V, ws).ntable) d |= kCqDOver;
                 V.dseq[ld] = V.wseq[ld];
                 sta = d | ((sta & kCqSlot) ^ kCqSlot);
             }
@@ -878,22 +1010,29 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
         if (need && !queue_done) {
             const unsigned lo = part ? s_end[part - 1] : 0u, hi = s_end[part];
             unsigned base = 0;
-            if (lane == 0) base = atomicAdd(&P.ctr->head_part[part], (unsigned)__popc(need));
+            if (lane == 0) base = atomicAdd(&heads[part], (unsigned)__popc(need));
             base = __shfl_sync(kFull, base, 0) + lo;
             if (base + (unsigned)__popc(need) >= hi) queue_done = true;
             if (empty) {
                 const unsigned item = base + (unsigned)__popc(need & lt_mask);
                 if (item < hi) {
-                    const unsigned v = P.sort_tail ? P.tail_sorted[item] : P.tail_raw[item];
                     const int ws = ld + ((sta & kCqSlot) ? 32 : 0);
-                    V.xyz[0][ld] = (int)(v % (unsigned)P.nx);
-                    const unsigned r1 = v / (unsigned)P.nx;
-                    V.xyz[1][ld] = (int)(r1 % (unsigned)P.ny);
-                    V.xyz[2][ld] = (int)(r1 / (unsigned)P.ny);
-                    const float dr = __ldg(P.ref + v);
+                    unsigned v;
+                    if constexpr (BATCH) {
+                        v = bd->items_v[item];
+                        V.pair[ws] = bd->items_p[item];
+                    } else {
+                        v = P0.sort_tail ? P0.tail_sorted[item] : P0.tail_raw[item];
+                    }
+                    const Problem& Q = cq_prob<BATCH>(P0, bd, V, ws);
+                    V.xyz[0][ld] = (int)(v % (unsigned)Q.nx);
+                    const unsigned r1 = v / (unsigned)Q.nx;
+                    V.xyz[1][ld] = (int)(r1 % (unsigned)Q.ny);
+                    V.xyz[2][ld] = (int)(r1 / (unsigned)Q.ny);
+                    const float dr = __ldg(Q.ref + v);
                     V.dr[ws] = dr;
-                    V.inv[ws] = 1.0f / (P.dd_frac * (P.local ? dr : s_dnorm));
-                    V.best[ws] = __float_as_uint(P.out[v]);  // gamma^2 over the faces through v
+                    V.inv[ws] = 1.0f / (Q.dd_frac * (Q.local ? dr : resolve_dnorm(Q)));
+                    V.best[ws] = __float_as_uint(Q.out[v]);  // gamma^2 over the faces through v
                     V.vox[ws] = v;
                     atomicAnd(&W.fixm[ws >> 5], ~(1u << (ws & 31)));
                     V.t[ld] = 0;
@@ -905,7 +1044,7 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
         __syncwarp();
         sta = V.state[ld];                 // the group's lanes follow their walker
         if (queue_done && !__any_sync(kFull, (sta & (kCqWalk | kCqEnded | kCqDBusy)) != 0)) {
-            if (part == 2) break;
+            if (part == kCqParts - 1) break;
             ++part;                        // this part is done: the next, with fewer lanes per voxel
             g = cq_part_lanes(part);
             queue_done = false;
@@ -917,11 +1056,12 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
         // 4. one table step of every walking group: entries t .. t + g - 1
         const bool walking = (sta & kCqWalk) != 0;
         const int ws = ld + ((sta & kCqSlot) ? 32 : 0);
+        const Problem& Q = cq_prob<BATCH>(P0, bd, V, ws);
         const int t0 = walking ? V.t[ld] : 0;
         float key = kInf;
         uint32_t off = 0;
-        if (walking && t0 + gl < P.ntable) {
-            const TableEntry e = P.table[t0 + gl];
+        if (walking && t0 + gl < Q.ntable) {
+            const TableEntry e = Q.table[t0 + gl];
             key = e.key;
             off = e.off;
         }
@@ -933,16 +1073,16 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
         for (int u = 0; u < 8; ++u) q[u] = 0.f;
         if (walking) {
             const float bst = __uint_as_float(V.best[ws]);
-            ended = t0 >= P.ntable || k0 * k0 >= bst;         // A1 step 4b-ii, exact
+            ended = t0 >= Q.ntable || k0 * k0 >= bst;         // A1 step 4b-ii, exact
             if (!ended && key * key < bst) {
-                if (P.stats) ++V.stat[2][lane];
+                if (Q.stats) ++V.stat[2][lane];
                 const int px = V.xyz[0][ld] + unpack10(off, 0);
                 const int py = V.xyz[1][ld] + unpack10(off, 10);
                 const int pz = V.xyz[2][ld] + unpack10(off, 20);
-                if ((unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny &&
-                    (N == 2 || (unsigned)pz < (unsigned)P.nz)) {
-                    const long long sy = P.nx, sz = (long long)P.nx * P.ny;
-                    const bool ex = px + 1 < P.nx, ey = py + 1 < P.ny, ez = N == 3 && pz + 1 < P.nz;
+                if ((unsigned)px < (unsigned)Q.nx && (unsigned)py < (unsigned)Q.ny &&
+                    (N == 2 || (unsigned)pz < (unsigned)Q.nz)) {
+                    const long long sy = Q.nx, sz = (long long)Q.nx * Q.ny;
+                    const bool ex = px + 1 < Q.nx, ey = py + 1 < Q.ny, ez = N == 3 && pz + 1 < Q.nz;
                     const long long p = (long long)pz * sz + (long long)py * sy + px;
                     const float dr = V.dr[ws], inv = V.inv[ws];
                     float qmin = kInf, qmax = -kInf;
@@ -952,7 +1092,7 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
                         if (present) {
                             const long long o = p + ((u & 1) ? 1 : 0) + ((u & 2) ? sy : 0) +
                                                 ((u & 4) ? sz : 0);
-                            q[u] = (__ldg(P.ev + o) - dr) * inv;
+                            q[u] = (__ldg(Q.ev + o) - dr) * inv;
                             qmin = fminf(qmin, q[u]);
                             qmax = fmaxf(qmax, q[u]);
                             ok |= 1u << u;
@@ -960,7 +1100,7 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
                     }
                     const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
                     if (fmaf(gap, gap, key * key) >= bst) {
-                        if (P.stats) ++V.stat[1][lane];
+                        if (Q.stats) ++V.stat[1][lane];
                     } else {
                         cand = true;
                     }
@@ -1001,64 +1141,71 @@ __global__ void __launch_bounds__(256, MINB) k_tail_cq(const __grid_constant__ P
                 const int slot = (int)((head + (unsigned)lane) & (kCqRing - 1));
                 const unsigned meta = V.meta[slot];
                 const int owner = (int)(meta & 63u);
+                const Problem& C = cq_prob<BATCH>(P0, bd, V, owner);
                 const unsigned cok = meta >> 8;
                 const unsigned coff = V.off[slot];
                 float cq[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) cq[u] = u < (1 << N) ? V.q[u][slot] : 0.f;
                 CellGeom<float> cg;
-                cell_geom<N, float>(unpack10(coff, 0), unpack10(coff, 10), unpack10(coff, 20), P.mt, cg);
+                cell_geom<N, float>(unpack10(coff, 0), unpack10(coff, 10), unpack10(coff, 20), C.mt, cg);
                 bool ill = false;
-                const float cb = cell_min_d2<N, float>(cq, cok, cg, P.mt, ill_dmax(P), kInf, ill);
-                if (ill && cell_gram_ill<N>(cq, cok, P.mt.kappa, P.tau))
+                const float cb = cell_min_d2<N, float>(cq, cok, cg, C.mt, ill_dmax(C), kInf, ill);
+                if (ill && cell_gram_ill<N>(cq, cok, C.mt.kappa, C.tau))
                     atomicOr(&W.fixm[owner >> 5], 1u << (owner & 31));   // k_tail_fix redoes it
                 else
                     atomicMin(&W.best[owner], __float_as_uint(cb + 0.f));   // -0 -> +0
-                if (P.stats) ++V.stat[0][lane];
+                if (C.stats) ++V.stat[0][lane];
             }
             head += n;
             count -= n;
         }
         __syncwarp();
     }
-    // per-warp totals
-    unsigned c0 = W.cnt[0][lane], c1 = W.cnt[1][lane];
-    unsigned long long s0 = W.stat[0][lane], s1 = W.stat[1][lane], s2 = W.stat[2][lane];
+    if constexpr (BATCH) {
+        cq_flush_counts(bd, V, lane);          // per-pair counts of every walker
+    } else {
+        // per-warp totals
+        const Problem& P = P0;
+        unsigned c0 = W.cnt[0][lane], c1 = W.cnt[1][lane];
+        unsigned long long s0 = W.stat[0][lane], s1 = W.stat[1][lane], s2 = W.stat[2][lane];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c0 += __shfl_xor_sync(kFull, c0, o);
-        c1 += __shfl_xor_sync(kFull, c1, o);
-        s0 += __shfl_xor_sync(kFull, s0, o);
-        s1 += __shfl_xor_sync(kFull, s1, o);
-        s2 += __shfl_xor_sync(kFull, s2, o);
-    }
-    if (lane == 0) {
-        if (c0) atomicAdd(&P.ctr->n_eval, (unsigned long long)c0);
-        if (c1) atomicAdd(&P.ctr->n_pass, (unsigned long long)c1);
-        if (P.stats) {
-            atomicAdd(&P.ctr->cells_visited, s0);
-            atomicAdd(&P.ctr->cells_pruned, s1);
-            atomicAdd(&P.ctr->cells_keyed, s2);
+        for (int o = 16; o > 0; o >>= 1) {
+            c0 += __shfl_xor_sync(kFull, c0, o);
+            c1 += __shfl_xor_sync(kFull, c1, o);
+            s0 += __shfl_xor_sync(kFull, s0, o);
+            s1 += __shfl_xor_sync(kFull, s1, o);
+            s2 += __shfl_xor_sync(kFull, s2, o);
+        }
+        if (lane == 0) {
+            if (c0) atomicAdd(&P.ctr->n_eval, (unsigned long long)c0);
+            if (c1) atomicAdd(&P.ctr->n_pass, (unsigned long long)c1);
+            if (P.stats) {
+                atomicAdd(&P.ctr->cells_visited, s0);
+                atomicAdd(&P.ctr->cells_pruned, s1);
+                atomicAdd(&P.ctr->cells_keyed, s2);
+            }
         }
     }
 }
 
-// Finishing pass of k_tail_cq: one warp per voxel of fix_list, whose bound
-// (gamma^2, an upper bound of the result) is in out.  The walk of k_tail
-// (32 lanes, FP64 redo of near-singular cells) from that bound, then the box
-// scan when it runs past the table.
-template <int N>
-__global__ void __launch_bounds__(256) k_tail_fix(const __grid_constant__ Problem P)
+// Finishing pass of k_tail_cq: one warp per voxel of the fix list, whose
+// bound (gamma^2, an upper bound of the result) is in out.  The walk of
+// k_tail (32 lanes, FP64 redo of near-singular cells) from that bound, then
+// the box scan when it runs past the table.
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(256) k_tail_fix(const __grid_constant__ Problem P0,
+                                                  const BatchDesc* __restrict__ bd)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned nfix = P.ctr->fix_count;
-    const float dnorm = resolve_dnorm(P);
-    const float rc2 = P.r_cover * P.r_cover;
+    const unsigned nfix = BATCH ? *bd->fix_count : P0.ctr->fix_count;
     unsigned my_eval = 0, my_pass = 0, my_over = 0;
     TailStats st;
     for (unsigned i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nfix;
          i += (gridDim.x * blockDim.x) >> 5) {
-        const unsigned v = P.fix_list[i];
+        const Problem& P = BATCH ? bd->probs[bd->fix_p[i]] : P0;
+        const unsigned v = BATCH ? bd->fix_v[i] : P.fix_list[i];
+        const float dnorm = resolve_dnorm(P);
         const int x = (int)(v % (unsigned)P.nx);
         const unsigned r1 = v / (unsigned)P.nx;
         const int y = (int)(r1 % (unsigned)P.ny), z = (int)(r1 / (unsigned)P.ny);
@@ -1086,35 +1233,44 @@ __global__ void __launch_bounds__(256) k_tail_fix(const __grid_constant__ Proble
             best = group_min<32>(cb, kFull);
             t += 32;
         }
-        if (t >= P.ntable && best > rc2) {
-            ++my_over;
-            best = tail_box_scan<N, 32>(P, x, y, z, dr, inv, dnorm, best, lane, kFull, st);
-        }
+        const bool over = t >= P.ntable && best > P.r_cover * P.r_cover;
+        if (over) best = tail_box_scan<N, 32>(P, x, y, z, dr, inv, dnorm, best, lane, kFull, st);
         if (lane == 0) {
             const float gam = sqrtf(best);
             P.out[v] = gam;
-            ++my_eval;
-            my_pass += gam <= 1.f;
+            if constexpr (BATCH) {
+                atomicAdd(&P.ctr->n_eval, 1ull);
+                if (gam <= 1.f) atomicAdd(&P.ctr->n_pass, 1ull);
+                if (over) atomicAdd(&P.ctr->overflow_count, 1u);
+            } else {
+                ++my_eval;
+                my_pass += gam <= 1.f;
+                my_over += over;
+            }
         }
     }
+    if constexpr (!BATCH) {
+        const Problem& P = P0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_eval += __shfl_xor_sync(kFull, my_eval, o);
-        my_pass += __shfl_xor_sync(kFull, my_pass, o);
-        if (P.stats) {
-            st.visited += __shfl_xor_sync(kFull, st.visited, o);
-            st.pruned += __shfl_xor_sync(kFull, st.pruned, o);
-            st.keyed += __shfl_xor_sync(kFull, st.keyed, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            my_eval += __shfl_xor_sync(kFull, my_eval, o);
+            my_pass += __shfl_xor_sync(kFull, my_pass, o);
+            my_over += __shfl_xor_sync(kFull, my_over, o);
+            if (P.stats) {
+                st.visited += __shfl_xor_sync(kFull, st.visited, o);
+                st.pruned += __shfl_xor_sync(kFull, st.pruned, o);
+                st.keyed += __shfl_xor_sync(kFull, st.keyed, o);
+            }
         }
-    }
-    if (lane == 0) {
-        if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
-        if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
-        if (my_over) atomicAdd(&P.ctr->overflow_count, my_over);
-        if (P.stats) {
-            atomicAdd(&P.ctr->cells_visited, st.visited);
-            atomicAdd(&P.ctr->cells_pruned, st.pruned);
-            atomicAdd(&P.ctr->cells_keyed, st.keyed);
+        if (lane == 0) {
+            if (my_eval) atomicAdd(&P.ctr->n_eval, (unsigned long long)my_eval);
+            if (my_pass) atomicAdd(&P.ctr->n_pass, (unsigned long long)my_pass);
+            if (my_over) atomicAdd(&P.ctr->overflow_count, my_over);
+            if (P.stats) {
+                atomicAdd(&P.ctr->cells_visited, st.visited);
+                atomicAdd(&P.ctr->cells_pruned, st.pruned);
+                atomicAdd(&P.ctr->cells_keyed, st.keyed);
+            }
         }
     }
 }
@@ -1939,23 +2095,23 @@ cudaError_t launch_tail(const Problem& P, int lanes_per_voxel, int tail_minblock
     return cudaGetLastError();
 }
 
-template <int N>
-static void launch_tail_cq_n(const Problem& P, int per_sm, int grid, cudaStream_t s)
+template <int N, bool BATCH>
+static void launch_tail_cq_n(const Problem& P, const BatchDesc* bd, int per_sm, cudaStream_t s)
 {
-    if (per_sm >= 4) k_tail_cq<N, 4><<<grid, 256, 0, s>>>(P);
-    else if (per_sm == 3) k_tail_cq<N, 3><<<grid, 256, 0, s>>>(P);
-    else if (per_sm == 2) k_tail_cq<N, 2><<<grid, 256, 0, s>>>(P);
-    else k_tail_cq<N, 1><<<grid, 256, 0, s>>>(P);
-    k_tail_fix<N><<<device_sm_count() * 2, 256, 0, s>>>(P);
+    const int grid = device_sm_count() * per_sm;      // persistent: one wave of resident blocks
+    if (per_sm >= 4) k_tail_cq<N, 4, BATCH><<<grid, 256, 0, s>>>(P, bd);
+    else if (per_sm == 3) k_tail_cq<N, 3, BATCH><<<grid, 256, 0, s>>>(P, bd);
+    else if (per_sm == 2) k_tail_cq<N, 2, BATCH><<<grid, 256, 0, s>>>(P, bd);
+    else k_tail_cq<N, 1, BATCH><<<grid, 256, 0, s>>>(P, bd);
+    k_tail_fix<N, BATCH><<<device_sm_count() * 2, 256, 0, s>>>(P, bd);
 }
 
 cudaError_t launch_tail_cq(const Problem& P, int tail_minblocks, cudaStream_t s)
 {
     if (!P.fix_list) return cudaErrorInvalidValue;
     const int per_sm = std::min(4, std::max(1, tail_minblocks));
-    const int grid = device_sm_count() * per_sm;      // persistent: one wave of resident blocks
-    if (P.ndim == 3) launch_tail_cq_n<3>(P, per_sm, grid, s);
-    else launch_tail_cq_n<2>(P, per_sm, grid, s);
+    if (P.ndim == 3) launch_tail_cq_n<3, false>(P, nullptr, per_sm, s);
+    else launch_tail_cq_n<2, false>(P, nullptr, per_sm, s);
     return cudaGetLastError();
 }
 
@@ -2072,12 +2228,18 @@ cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_tail(const BatchGroup& g, int lanes_per_voxel, int tail_minblocks,
+cudaError_t launch_batch_tail(const BatchGroup& g, int walk, int lanes_per_voxel, int tail_minblocks,
                               cudaStream_t s)
 {
     if (g.npairs <= 0) return cudaSuccess;
     const int sms = device_sm_count();
     Problem dummy{};
+    if (walk == 3) {
+        const int per_sm = std::min(4, std::max(1, tail_minblocks));
+        if (g.ndim == 3) launch_tail_cq_n<3, true>(dummy, g.desc, per_sm, s);
+        else launch_tail_cq_n<2, true>(dummy, g.desc, per_sm, s);
+        return cudaGetLastError();
+    }
     if (g.ndim == 3) launch_tail_n<3, true>(dummy, g.desc, lanes_per_voxel, tail_minblocks, sms * 8, s);
     else launch_tail_n<2, true>(dummy, g.desc, lanes_per_voxel, tail_minblocks, sms * 8, s);
     return cudaGetLastError();

@@ -73,9 +73,15 @@ def test_batch_matches_oracle_and_single_runs():
         np.testing.assert_allclose(got, single, rtol=0, atol=1e-6, equal_nan=True)
 
 
-@pytest.mark.parametrize("opts", [{"graph": 0}, {"lanes_per_voxel": 32, "shell_blocks_per_sm": 1},
-                                  {"lanes_per_voxel": 4}, {"table_cap": 16}])
+@pytest.mark.parametrize("opts", [{"graph": 0}, {"walk": 0, "lanes_per_voxel": 32, "shell_blocks_per_sm": 1},
+                                  {"walk": 0, "lanes_per_voxel": 4}, {"walk": 0, "table_cap": 16},
+                                  {"table_cap": 16}, {"group_bucket": 0}, {"group_bucket": 32},
+                                  {"group8_bucket": 0}, {"group32_bucket": 0},
+                                  {"group_bucket": 5, "group8_bucket": 9, "group32_bucket": 13},
+                                  {"tail_blocks_per_sm": 4}, {"tail_blocks_per_sm": 1}])
 def test_batch_options_agree(opts):
+    # the default batched walk is the warp-evaluated one (walk 3); walk 0
+    # is the voxel walk with its lane counts
     ps = _pairs()
     base, _ = _batch_run(ps)
     other, _ = _batch_run(ps, opts)
@@ -106,7 +112,7 @@ def test_autotune_single_and_batch():
     try:
         t = g.gamma_autotune(h, o, reps=2)
         assert t["lanes_per_voxel"] in (2, 4, 8, 16, 32) and t["shell_blocks_per_sm"] in (1, 2, 3, 4)
-        assert t["tail_blocks_per_sm"] in (1, 2, 3) and t["ms"] > 0
+        assert t["tail_blocks_per_sm"] in (1, 2, 3, 4) and t["ms"] > 0
         g.gamma_run(h, o)
         g.gamma_pass_rate(h)
     finally:

@@ -215,19 +215,21 @@ def test_staged_walks(case, blocks, walk):
 
 
 @pytest.mark.parametrize("crit", [(0.03, 3.0, False), (0.01, 1.0, True)], ids=["3-3", "1-1-local"])
-@pytest.mark.parametrize("groups", [(0, 32), (32, 0), (9, 13), (32, 32), (5, 9)],
-                         ids=["all4", "all8", "default", "none", "low"])
+@pytest.mark.parametrize("groups", [(0, 32, 32), (32, 0, 32), (32, 32, 0), (9, 32, 32), (32, 32, 32),
+                                    (5, 9, 13)],
+                         ids=["all4", "all8", "all32", "default", "none", "tiers"])
 @pytest.mark.parametrize("blocks", [1, 2, 3, 4])
 def test_warp_evaluated_walk_is_bitwise_the_voxel_walk(crit, groups, blocks):
     # walk = 3 evaluates every cell with the same arithmetic as walk = 0 and
     # reaches the same minimising cell, so the two maps agree bit for bit,
-    # whichever voxels walk four or eight lanes each (a threshold of 0: all
-    # of them; 32: none) and at every register budget
+    # whichever voxels walk four, eight or 32 lanes each (a threshold of 0:
+    # all of them; 32: none) and at every register budget
     p = synth.workload("imrt_small")
     c = synth.Criteria(crit[0], crit[1], local=crit[2])
     a, ca, sa = gpu_gamma(p.ref, p.eval, p.spacing, c, {"walk": 0, "lanes_per_voxel": 2, "stats": 1})
     b, cb, sb = gpu_gamma(p.ref, p.eval, p.spacing, c, {"walk": 3, "stats": 1, "group_bucket": groups[0],
                                                       "group8_bucket": groups[1],
+                                                      "group32_bucket": groups[2],
                                                       "tail_blocks_per_sm": blocks})
     np.testing.assert_array_equal(a, b)
     assert ca == cb
