@@ -296,6 +296,7 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.stats = h->stats;
     P.table = h->table_dev;
     P.ntable = (int)h->table.size();
+    gk::fill_bucket_keys(h->table.data(), P.ntable, P.bucket_key);
     for (int s = 0; s < 8; ++s) P.key0_far2[s] = h->key0_far2[s];
     P.r_cover = std::isinf(h->r_cover) ? INFINITY : round_down(h->r_cover);
     P.tail_cap = h->tail_cap;

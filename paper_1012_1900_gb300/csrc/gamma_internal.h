@@ -1,5 +1,6 @@
 // Internal structures shared by the CUDA kernels and the C-ABI layer.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <vector>
 #include <cuda.h>
@@ -88,6 +89,26 @@ struct Counters {
     unsigned int fix_count;             // ... voxels it leaves to the finishing pass
 };
 
+// The cost bucket thresholds of a sorted table (Problem::bucket_key).
+inline void fill_bucket_keys(const TableEntry* table, int ntable, float* out)
+{
+    out[0] = -__builtin_huge_valf();
+    for (int b = 1; b < kNumBuckets; ++b) {
+        const double c = std::ceil(std::pow(2.0, 0.5 * (b - 1)));
+        out[b] = c <= (double)ntable ? table[(long long)c - 1].key : __builtin_huge_valf();
+    }
+}
+
+// The cost bucket of a voxel whose search radius (normalised) is g: the
+// number of thresholds below g, by bisection over the non-decreasing keys.
+__host__ __device__ inline int cost_bucket_of(const float* bucket_key, float g)
+{
+    int b = 0;
+    for (int step = kNumBuckets / 2; step > 0; step >>= 1)
+        if (b + step < kNumBuckets && bucket_key[b + step] < g) b += step;
+    return b;
+}
+
 // Order-preserving encoding of a float into an unsigned int (for atomicMax).
 __host__ __device__ inline unsigned int fenc(float f)
 {
@@ -121,6 +142,11 @@ struct Problem {
     int stats;               // count cells in the tail search
     const TableEntry* table;
     int ntable;
+    // cost bucket thresholds: bucket_key[b] (b >= 1) is the key of table entry
+    // ceil(2^((b - 1) / 2)) - 1 (+inf past the table), so that the cost bucket
+    // 1 + floor(2 log2 c) of a voxel with c table keys below g is the number
+    // of b >= 1 with bucket_key[b] < g (0 when c = 0); bucket_key[0] = -inf
+    float bucket_key[kNumBuckets];
     float r_cover;           // every cell with key < r_cover is in the table
     unsigned int tail_cap;
     Counters* ctr;

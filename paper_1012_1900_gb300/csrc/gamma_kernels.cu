@@ -322,14 +322,8 @@ __global__ void __launch_bounds__(256, MINB)
             tail = best > qlim;
             if (tail) {
                 P.out[v] = best;                       // gamma^2, finished by k_tail
-                const float gk_ = sqrtf(best);
-                int lo = 0, hi = P.ntable;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
-                }
-                const int cost = lo;
-                bucket = cost <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)cost)));
+                // 1 + floor(2 log2 of the table cells with key < gamma)
+                bucket = cost_bucket_of(P.bucket_key, sqrtf(best));
             } else {
                 const float gam = sqrtf(best);
                 P.out[v] = gam;

@@ -649,13 +649,7 @@ cudaError_t launch_mlp_infer(const MlpWeights& W, const bf16* X, long long M, fl
 // bucket k_shell gives.
 __device__ __forceinline__ int cost_bucket(const Problem& P, float g2)
 {
-    const float gk_ = sqrtf(g2);
-    int lo = 0, hi = P.ntable;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (P.table[mid].key < gk_) lo = mid + 1; else hi = mid;
-    }
-    return lo <= 0 ? 0 : min(kNumBuckets - 1, 1 + (int)(2.f * __log2f((float)lo)));
+    return cost_bucket_of(P.bucket_key, sqrtf(g2));
 }
 
 // The seed rows of one pair (BATCH = false: P0.seed_list items) or of every

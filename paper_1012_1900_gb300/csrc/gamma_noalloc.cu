@@ -234,6 +234,7 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
     P.stats = 0;
     P.table = (const gk::TableEntry*)(base + kOffTable);
     P.ntable = ntable;
+    gk::fill_bucket_keys(g_table_host, ntable, P.bucket_key);
     for (int s = 0; s < 8; ++s) P.key0_far2[s] = far2[s];
     P.r_cover = std::isinf(cover) ? INFINITY : round_down_f(cover);
     P.tail_cap = (unsigned)kMaxVoxels;
