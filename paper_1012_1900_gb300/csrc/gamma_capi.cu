@@ -410,6 +410,7 @@ struct BatchState {
         unsigned short* items_p = nullptr;
         unsigned* head = nullptr;          // walk, shell tiles, seed rows, seeding work,
                                            // warp-evaluated walk parts (3), its fix count
+        float4* metric4 = nullptr;         // per pair: metric constants of the warp-evaluated walk
         unsigned* fix_v = nullptr;         // warp-evaluated walk: voxels for its finishing pass
         unsigned short* fix_p = nullptr;
         unsigned* seed_item = nullptr;     // with a model: (pair, item) rows past the gate
@@ -439,6 +440,7 @@ void free_group(BatchState::Group& g)
     cudaFree(g.items_p);
     cudaFree(g.head);
     cudaFree(g.fix_v);
+    cudaFree(g.metric4);
     cudaFree(g.fix_p);
     cudaFree(g.seed_item);
     cudaFree(g.seed_pair);
@@ -507,6 +509,7 @@ int batch_upload(gamma_ctx* h)
             CK(cudaMalloc(&G.items_v, sizeof(unsigned) * std::max<size_t>(cap, 1)));
             CK(cudaMalloc(&G.items_p, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
             CK(cudaMalloc(&G.fix_v, sizeof(unsigned) * std::max<size_t>(cap, 1)));
+            CK(cudaMalloc(&G.metric4, sizeof(float4) * 3 * np));
             CK(cudaMalloc(&G.fix_p, sizeof(unsigned short) * std::max<size_t>(cap, 1)));
             CK(cudaMalloc(&G.head, 12 * sizeof(unsigned)));
             CK(cudaMemset(G.head, 0, 12 * sizeof(unsigned)));
@@ -525,6 +528,14 @@ int batch_upload(gamma_ctx* h)
         CK(cudaMemcpy(G.maps, maps.data(), sizeof(CUtensorMap) * np, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(G.use_tma, use.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(G.tile_start, tstart.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice));
+        std::vector<float4> m4(3 * (size_t)np);
+        for (int k = 0; k < np; ++k) {
+            const gk::Metric& mt = probs[k].mt;
+            m4[3 * k] = make_float4(mt.hn2[0], mt.hn2[1], mt.hn2[2], probs[k].tau);
+            m4[3 * k + 1] = make_float4(mt.kappa[1], mt.kappa[2], mt.kappa[3], mt.kappa[4]);
+            m4[3 * k + 2] = make_float4(mt.kappa[5], mt.kappa[6], mt.kappa[7], 0.f);
+        }
+        CK(cudaMemcpy(G.metric4, m4.data(), sizeof(float4) * m4.size(), cudaMemcpyHostToDevice));
         gk::BatchDesc d{};
         d.npairs = np;
         d.probs = G.probs;
@@ -540,6 +551,7 @@ int batch_upload(gamma_ctx* h)
         d.group8_bucket = h->walk == 3 ? h->group8_bucket : 0;
         d.group32_bucket = h->walk == 3 ? h->group32_bucket : 0;
         d.part_head = G.head + 4;
+        d.metric4 = G.metric4;
         d.fix_v = G.fix_v;
         d.fix_p = G.fix_p;
         d.fix_count = G.head + 8;

@@ -219,6 +219,8 @@ struct BatchDesc {
     // their pair) left to the finishing pass
     int group_bucket, group8_bucket, group32_bucket;
     unsigned* part_head;           // [4]
+    const float4* metric4;         // [npairs][3] per pair: hn2 x, y, z, tau; kappa 1-4;
+                                   // kappa 5-7, 0
     unsigned* fix_v;               // [sum of tail_cap]
     unsigned short* fix_p;
     unsigned* fix_count;

@@ -858,6 +858,13 @@ struct CqWarp {
     unsigned short pair[64];   // batched: the pair of each voxel slot
     unsigned long long stat[3][32];    // cells visited, pruned, keyed (option "stats")
 };
+// Batched launches: the walking voxel's grid and table, per walker, cached
+// when it takes the voxel (a pair's Problem lives in global memory).
+struct CqWalkDims {
+    int dim[4][32];            // nx, ny, nz, table length
+    const TableEntry* tab[32];
+    const float* ev[32];
+};
 constexpr unsigned kCqWalk = 1u, kCqEnded = 2u, kCqWPend = 4u, kCqDBusy = 8u, kCqDPend = 16u,
                    kCqDOver = 32u, kCqSlot = 64u;     // slot bit: the walking slot is walker + 32
 
@@ -896,9 +903,11 @@ __global__ void __launch_bounds__(256, MINB)
     k_tail_cq(const __grid_constant__ Problem P0, const BatchDesc* __restrict__ bd)
 {
     __shared__ CqWarp cqw[8];
+    __shared__ CqWalkDims cqd[BATCH ? 8 : 1];
     __shared__ unsigned s_end[kCqParts];   // the parts of the queue end at these items
     CqWarp& W = cqw[threadIdx.x >> 5];
     volatile CqWarp& V = cqw[threadIdx.x >> 5];
+    volatile CqWalkDims& VD = cqd[BATCH ? threadIdx.x >> 5 : 0];
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (threadIdx.x < 32) {
@@ -993,7 +1002,7 @@ __global__ void __launch_bounds__(256, MINB)
                 const int ws = ld + ((sta & kCqSlot) ? 32 : 0);
                 unsigned d = kCqDBusy;
                 if (sta & kCqWPend) d |= kCqDPend;
-                if (V.t[ld] >= cq_prob<BATCH>(P0, bd, V, ws).ntable) d |= kCqDOver;
+                if (V.t[ld] >= (BATCH ? VD.dim[3][ld] : P0.ntable)) d |= kCqDOver;
                 V.dseq[ld] = V.wseq[ld];
                 sta = d | ((sta & kCqSlot) ^ kCqSlot);
             }
@@ -1028,6 +1037,14 @@ __global__ void __launch_bounds__(256, MINB)
                     V.inv[ws] = 1.0f / (Q.dd_frac * (Q.local ? dr : resolve_dnorm(Q)));
                     V.best[ws] = __float_as_uint(Q.out[v]);  // gamma^2 over the faces through v
                     V.vox[ws] = v;
+                    if constexpr (BATCH) {
+                        VD.dim[0][ld] = Q.nx;
+                        VD.dim[1][ld] = Q.ny;
+                        VD.dim[2][ld] = Q.nz;
+                        VD.dim[3][ld] = Q.ntable;
+                        VD.tab[ld] = Q.table;
+                        VD.ev[ld] = Q.ev;
+                    }
                     atomicAnd(&W.fixm[ws >> 5], ~(1u << (ws & 31)));
                     V.t[ld] = 0;
                     sta = (sta & ~kCqWPend) | kCqWalk;
@@ -1050,12 +1067,17 @@ __global__ void __launch_bounds__(256, MINB)
         // 4. one table step of every walking group: entries t .. t + g - 1
         const bool walking = (sta & kCqWalk) != 0;
         const int ws = ld + ((sta & kCqSlot) ? 32 : 0);
-        const Problem& Q = cq_prob<BATCH>(P0, bd, V, ws);
+        // the walking voxel's grid and table (batched: cached at its refill)
+        const int qnx = BATCH ? VD.dim[0][ld] : P0.nx, qny = BATCH ? VD.dim[1][ld] : P0.ny;
+        const int qnz = BATCH ? VD.dim[2][ld] : P0.nz, qnt = BATCH ? VD.dim[3][ld] : P0.ntable;
+        const TableEntry* qtab = BATCH ? VD.tab[ld] : P0.table;
+        const float* qev = BATCH ? VD.ev[ld] : P0.ev;
+        const bool qstats = !BATCH && P0.stats;
         const int t0 = walking ? V.t[ld] : 0;
         float key = kInf;
         uint32_t off = 0;
-        if (walking && t0 + gl < Q.ntable) {
-            const TableEntry e = Q.table[t0 + gl];
+        if (walking && t0 + gl < qnt) {
+            const TableEntry e = qtab[t0 + gl];
             key = e.key;
             off = e.off;
         }
@@ -1067,16 +1089,16 @@ __global__ void __launch_bounds__(256, MINB)
         for (int u = 0; u < 8; ++u) q[u] = 0.f;
         if (walking) {
             const float bst = __uint_as_float(V.best[ws]);
-            ended = t0 >= Q.ntable || k0 * k0 >= bst;         // A1 step 4b-ii, exact
+            ended = t0 >= qnt || k0 * k0 >= bst;              // A1 step 4b-ii, exact
             if (!ended && key * key < bst) {
-                if (Q.stats) ++V.stat[2][lane];
+                if (qstats) ++V.stat[2][lane];
                 const int px = V.xyz[0][ld] + unpack10(off, 0);
                 const int py = V.xyz[1][ld] + unpack10(off, 10);
                 const int pz = V.xyz[2][ld] + unpack10(off, 20);
-                if ((unsigned)px < (unsigned)Q.nx && (unsigned)py < (unsigned)Q.ny &&
-                    (N == 2 || (unsigned)pz < (unsigned)Q.nz)) {
-                    const long long sy = Q.nx, sz = (long long)Q.nx * Q.ny;
-                    const bool ex = px + 1 < Q.nx, ey = py + 1 < Q.ny, ez = N == 3 && pz + 1 < Q.nz;
+                if ((unsigned)px < (unsigned)qnx && (unsigned)py < (unsigned)qny &&
+                    (N == 2 || (unsigned)pz < (unsigned)qnz)) {
+                    const long long sy = qnx, sz = (long long)qnx * qny;
+                    const bool ex = px + 1 < qnx, ey = py + 1 < qny, ez = N == 3 && pz + 1 < qnz;
                     const long long p = (long long)pz * sz + (long long)py * sy + px;
                     const float dr = V.dr[ws], inv = V.inv[ws];
                     float qmin = kInf, qmax = -kInf;
@@ -1086,7 +1108,7 @@ __global__ void __launch_bounds__(256, MINB)
                         if (present) {
                             const long long o = p + ((u & 1) ? 1 : 0) + ((u & 2) ? sy : 0) +
                                                 ((u & 4) ? sz : 0);
-                            q[u] = (__ldg(Q.ev + o) - dr) * inv;
+                            q[u] = (__ldg(qev + o) - dr) * inv;
                             qmin = fminf(qmin, q[u]);
                             qmax = fmaxf(qmax, q[u]);
                             ok |= 1u << u;
@@ -1094,7 +1116,7 @@ __global__ void __launch_bounds__(256, MINB)
                     }
                     const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
                     if (fmaf(gap, gap, key * key) >= bst) {
-                        if (Q.stats) ++V.stat[1][lane];
+                        if (qstats) ++V.stat[1][lane];
                     } else {
                         cand = true;
                     }
@@ -1135,21 +1157,35 @@ __global__ void __launch_bounds__(256, MINB)
                 const int slot = (int)((head + (unsigned)lane) & (kCqRing - 1));
                 const unsigned meta = V.meta[slot];
                 const int owner = (int)(meta & 63u);
-                const Problem& C = cq_prob<BATCH>(P0, bd, V, owner);
                 const unsigned cok = meta >> 8;
                 const unsigned coff = V.off[slot];
                 float cq[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) cq[u] = u < (1 << N) ? V.q[u][slot] : 0.f;
-                CellGeom<float> cg;
-                cell_geom<N, float>(unpack10(coff, 0), unpack10(coff, 10), unpack10(coff, 20), C.mt, cg);
-                bool ill = false;
-                const float cb = cell_min_d2<N, float>(cq, cok, cg, C.mt, ill_dmax(C), kInf, ill);
-                if (ill && cell_gram_ill<N>(cq, cok, C.mt.kappa, C.tau))
-                    atomicOr(&W.fixm[owner >> 5], 1u << (owner & 31));   // k_tail_fix redoes it
-                else
-                    atomicMin(&W.best[owner], __float_as_uint(cb + 0.f));   // -0 -> +0
-                if (C.stats) ++V.stat[0][lane];
+                auto evaluate = [&](const Metric& mt, float dmax, float tau) {
+                    CellGeom<float> cg;
+                    cell_geom<N, float>(unpack10(coff, 0), unpack10(coff, 10), unpack10(coff, 20), mt, cg);
+                    bool ill = false;
+                    const float cb = cell_min_d2<N, float>(cq, cok, cg, mt, dmax, kInf, ill);
+                    if (ill && cell_gram_ill<N>(cq, cok, mt.kappa, tau))
+                        atomicOr(&W.fixm[owner >> 5], 1u << (owner & 31));   // k_tail_fix redoes it
+                    else
+                        atomicMin(&W.best[owner], __float_as_uint(cb + 0.f));   // -0 -> +0
+                };
+                if constexpr (BATCH) {
+                    // the owner's pair's metric: three 16-byte loads
+                    const float4* m4 = bd->metric4 + 3 * (int)V.pair[owner];
+                    const float4 a = m4[0], b = m4[1], c = m4[2];
+                    Metric mt;
+                    mt.hn2[0] = a.x; mt.hn2[1] = a.y; mt.hn2[2] = a.z;
+                    mt.kappa[0] = 0.f;
+                    mt.kappa[1] = b.x; mt.kappa[2] = b.y; mt.kappa[3] = b.z; mt.kappa[4] = b.w;
+                    mt.kappa[5] = c.x; mt.kappa[6] = c.y; mt.kappa[7] = c.z;
+                    evaluate(mt, a.w > 0.f ? 0.99f * rsqrtf(a.w) : kInf, a.w);   // bound as ill_dmax
+                } else {
+                    evaluate(P0.mt, ill_dmax(P0), P0.tau);
+                }
+                if (!BATCH && P0.stats) ++V.stat[0][lane];
             }
             head += n;
             count -= n;
