@@ -2252,9 +2252,10 @@ cudaError_t launch_batch_order(const BatchGroup& g, cudaStream_t s)
 {
     if (g.npairs <= 0) return cudaSuccess;
     k_bucket_scan_batch<<<1, 256, 0, s>>>(g.desc);
+    // enough blocks per pair for the largest queue (one 256-voxel chunk per
+    // block and pass); the blocks of small pairs leave at once
     const int sms = device_sm_count();
-    const int bx = std::max(1, sms * 2 / std::max(1, g.npairs)) + 1;
-    k_scatter_batch<<<dim3(bx, g.npairs), 256, 0, s>>>(g.desc);
+    k_scatter_batch<<<dim3(sms * 4, g.npairs), 256, 0, s>>>(g.desc);
     return cudaGetLastError();
 }
 
