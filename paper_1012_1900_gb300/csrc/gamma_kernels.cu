@@ -395,6 +395,193 @@ __global__ void __launch_bounds__(256, MINB)
 }
 
 // --------------------------------------------------------------------------
+// k_shell_w: the same per-voxel work, one warp per tile, no block barriers
+// --------------------------------------------------------------------------
+
+// In k_shell the eight warps of a block share one staged tile and meet at a
+// block barrier per tile, so a tile takes as long as its slowest warp row.
+// Here each warp stages its own smaller tile (32 x 2 x 2 voxels in 3D, 32 x 4
+// in 2D, with a one-voxel halo) into a double buffer of its own, with its own
+// TMA copies and mbarriers, and takes its next tile from the work counter by
+// itself: warps never wait for one another until the end of the kernel.
+template <int N>
+struct WarpTile {
+    static constexpr int TX = 32, TY = N == 3 ? 2 : 4, TZ = N == 3 ? 2 : 1;
+    static constexpr int BX = 40, BY = TY + 2, BZ = N == 3 ? TZ + 2 : 1;
+    static constexpr int ELEMS = BX * BY * BZ;
+    static constexpr int STRIDE = (ELEMS + 31) / 32 * 32;   // 128-byte aligned buffers
+    static_assert(STRIDE * 4 % 128 == 0, "TMA destination must stay 128-byte aligned");
+};
+
+template <int N, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_shell_w(const __grid_constant__ Problem P, const __grid_constant__ CUtensorMap tmap, int ntiles,
+              unsigned* tile_next)
+{
+    using T = WarpTile<N>;
+    __shared__ __align__(128) float tiles[8][2][T::STRIDE];
+    __shared__ __align__(8) uint64_t bar[8][2];
+    __shared__ unsigned int sh_hist[kNumBuckets];
+    __shared__ unsigned long long sh_eval, sh_pass;
+    __shared__ unsigned int sh_rmax;
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < kNumBuckets) sh_hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        sh_eval = 0;
+        sh_pass = 0;
+        sh_rmax = 0;
+    }
+    if (lane == 0) {
+        mbar_init(&bar[w][0], 1);
+        mbar_init(&bar[w][1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    const int ntx = (P.nx + T::TX - 1) / T::TX, nty = (P.ny + T::TY - 1) / T::TY;
+    auto origin = [&](int t, int& x0, int& y0, int& z0) {
+        x0 = (t % ntx) * T::TX;
+        y0 = ((t / ntx) % nty) * T::TY;
+        z0 = (t / ntx / nty) * T::TZ;
+    };
+    auto issue = [&](int t, int b) {           // lane 0
+        if (t >= ntiles) return;
+        int x0, y0, z0;
+        origin(t, x0, y0, z0);
+        mbar_arrive_expect_tx(&bar[w][b], T::ELEMS * (uint32_t)sizeof(float));
+        if (N == 3) tma_load_3d(tiles[w][b], &tmap, x0 - 4, y0 - 1, z0 - 1, &bar[w][b]);
+        else tma_load_2d(tiles[w][b], &tmap, x0 - 4, y0 - 1, &bar[w][b]);
+    };
+    const int nwarps = (int)gridDim.x * 8;
+    int t = (int)blockIdx.x * 8 + w;           // the first tile of every warp, then the counter
+    if (lane == 0) issue(t, 0);
+
+    const float dnorm = resolve_dnorm(P);
+    const float thr = P.cutoff_frac * dnorm;
+    const float k0 = P.ntable > 0 ? P.table[0].key : kInf;
+    const float qlim = fminf(k0 * k0, P.r_cover * P.r_cover);
+    unsigned my_eval = 0, my_pass = 0;
+    float my_rmax = 0.f;
+    bool bad_ev = false;
+    bool timed_out = false;
+    uint32_t parity = 0;
+    int b = 0;
+    while (t < ntiles) {
+        int nt = 0;
+        if (lane == 0) {
+            nt = nwarps + (int)atomicAdd(tile_next, 1u);
+            issue(nt, b ^ 1);
+        }
+        nt = __shfl_sync(kFull, nt, 0);
+        if (!mbar_wait_bounded(&bar[w][b], (parity >> b) & 1u)) {
+            timed_out = true;                  // (warp-uniform: every lane polls the same phase)
+            break;
+        }
+        parity ^= 1u << b;
+        const float* tl = tiles[w][b];
+        int x0, y0, z0;
+        origin(t, x0, y0, z0);
+#pragma unroll 1
+        for (int r = 0; r < T::TY * T::TZ; ++r) {
+            const int ly = r % T::TY, lz = r / T::TY;
+            const int x = x0 + lane, y = y0 + ly, z = z0 + lz;
+            const bool inside = x < P.nx && y < P.ny && z < P.nz;
+            const long long v = inside ? ((long long)z * P.ny + y) * P.nx + x : 0;
+            const int tix = ((N == 3 ? lz + 1 : 0) * T::BY + (ly + 1)) * T::BX + (lane + 4);
+            float dr = 0.f, best = 0.f;
+            bool act = false;
+            if (inside) {
+                dr = __ldg(P.ref + v);
+                act = is_evaluated(P, dr, thr);
+                if (!act) P.out[v] = __int_as_float(0x7fc00000);
+                bad_ev |= !isfinite(tl[tix]);       // every evaluation dose is some tile's centre
+            }
+            uint32_t inm = 0, inp = 0;
+            inm |= (x > 0) ? 1u : 0u;
+            inp |= (x + 1 < P.nx) ? 1u : 0u;
+            inm |= (y > 0) ? 2u : 0u;
+            inp |= (y + 1 < P.ny) ? 2u : 0u;
+            if (N == 3) {
+                inm |= (z > 0) ? 4u : 0u;
+                inp |= (z + 1 < P.nz) ? 4u : 0u;
+            }
+            if (act) {
+                const float dD = P.dd_frac * (P.local ? dr : dnorm);
+                const float q0 = (tl[tix] - dr) / dD;
+                best = q0 * q0;
+                my_rmax = fmaxf(my_rmax, fabsf(q0));
+                if (best > 0.f) best = near_gamma2<N, T::BX, T::BX * T::BY>(tl, tix, inm, inp, dr, dD, P.mt.kappa);
+            }
+            bool tail = false;
+            int bucket = 0;
+            if (act) {
+                tail = best > qlim;
+                if (tail) {
+                    P.out[v] = best;                   // gamma^2, finished by the table walk
+                    // 1 + floor(2 log2 of the table cells with key < gamma)
+                    bucket = cost_bucket_of(P.bucket_key, sqrtf(best));
+                } else {
+                    const float gam = sqrtf(best);
+                    P.out[v] = gam;
+                    ++my_eval;
+                    my_pass += gam <= 1.f;             // decided on the value written
+                }
+            }
+            const unsigned tm = __ballot_sync(kFull, tail);
+            if (tm) {
+                unsigned pos0 = 0;
+                if (lane == 0) pos0 = atomicAdd(&P.ctr->tail_count, (unsigned)__popc(tm));
+                pos0 = __shfl_sync(kFull, pos0, 0);
+                if (tail) {
+                    const unsigned pos = pos0 + __popc(tm & ((1u << lane) - 1u));
+                    if (pos < P.tail_cap) {
+                        P.tail_raw[pos] = (unsigned)v;
+                        P.tail_bucket[pos] = (unsigned char)bucket;
+                        atomicAdd(&sh_hist[bucket], 1u);
+                    } else {
+                        atomicOr(&P.ctr->flags, kFlagTailFull);
+                    }
+                }
+            }
+        }
+        __syncwarp();                          // tiles[w][b] is free for the copy after next
+        t = nt;
+        b ^= 1;
+    }
+    if (timed_out) {
+        if (lane == 0) {
+            atomicOr(&P.ctr->flags, kFlagTimeout);
+            // let this warp's own copies land before the block leaves
+            mbar_wait_bounded(&bar[w][0], parity & 1u);
+            mbar_wait_bounded(&bar[w][1], (parity >> 1) & 1u);
+        }
+        __syncwarp();
+    }
+    // per-block counters -> the run's counters
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_eval += __shfl_xor_sync(kFull, my_eval, o);
+        my_pass += __shfl_xor_sync(kFull, my_pass, o);
+        my_rmax = fmaxf(my_rmax, __shfl_xor_sync(kFull, my_rmax, o));
+    }
+    if (__any_sync(kFull, bad_ev) && lane == 0) atomicOr(&P.ctr->flags, kFlagNonFinite);
+    if (lane == 0) {
+        if (my_eval) atomicAdd(&sh_eval, (unsigned long long)my_eval);
+        if (my_pass) atomicAdd(&sh_pass, (unsigned long long)my_pass);
+        atomicMax(&sh_rmax, fenc(my_rmax));
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBuckets && sh_hist[threadIdx.x])
+        atomicAdd(&P.ctr->hist[threadIdx.x], sh_hist[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        if (sh_eval) atomicAdd(&P.ctr->n_eval, sh_eval);
+        if (sh_pass) atomicAdd(&P.ctr->n_pass, sh_pass);
+        atomicMax(&P.ctr->rmax_enc, sh_rmax);
+    }
+}
+
+// --------------------------------------------------------------------------
 // Queue ordering: bucket offsets (most expensive first) and scatter
 // --------------------------------------------------------------------------
 
@@ -2050,10 +2237,49 @@ cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, i
     return cudaGetLastError();
 }
 
+template <int N>
+static void launch_shell_w_k(int per_sm, unsigned grid, cudaStream_t s, const Problem& P,
+                             const CUtensorMap& map, int tiles, unsigned* next)
+{
+    switch (per_sm) {
+    case 1: k_shell_w<N, 1><<<grid, 256, 0, s>>>(P, map, tiles, next); break;
+    case 2: k_shell_w<N, 2><<<grid, 256, 0, s>>>(P, map, tiles, next); break;
+    case 3: k_shell_w<N, 3><<<grid, 256, 0, s>>>(P, map, tiles, next); break;
+    default: k_shell_w<N, 4><<<grid, 256, 0, s>>>(P, map, tiles, next); break;
+    }
+}
+
+// The shell of a whole run: one warp per tile (k_shell_w) when the staged
+// walks do not need k_shell's tile layout and the evaluation dose takes a TMA
+// map; else k_shell.
 cudaError_t launch_shell(const Problem& P, cudaStream_t s)
 {
     const int tiles = shell_tiles(P);
     if (tiles < 0) return cudaErrorInvalidValue;
+    if (!P.tile_mask && !P.row_items) {
+        CUtensorMap map;
+        std::memset(&map, 0, sizeof(map));
+        const bool tma = P.ndim == 3
+                             ? encode_box_map(P, &map, WarpTile<3>::BX, WarpTile<3>::BY, WarpTile<3>::BZ)
+                             : encode_box_map(P, &map, WarpTile<2>::BX, WarpTile<2>::BY, 1);
+        long long wt;
+        if (P.ndim == 3) {
+            using T = WarpTile<3>;
+            wt = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY) *
+                 ((P.nz + T::TZ - 1) / T::TZ);
+        } else {
+            using T = WarpTile<2>;
+            wt = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
+        }
+        if (tma && wt <= 0x3fffffffLL) {
+            const int per_sm = std::min(4, std::max(1, P.shell_minblocks));
+            const unsigned grid =
+                (unsigned)std::max<long long>(1, std::min<long long>((wt + 7) / 8, (long long)device_sm_count() * per_sm));
+            if (P.ndim == 3) launch_shell_w_k<3>(per_sm, grid, s, P, map, (int)wt, &P.ctr->shell_next[0]);
+            else launch_shell_w_k<2>(per_sm, grid, s, P, map, (int)wt, &P.ctr->shell_next[0]);
+            return cudaGetLastError();
+        }
+    }
     return launch_shell_range(P, 0, tiles, 0, SlabGate{nullptr, 0u, 0}, s);
 }
 
