@@ -679,7 +679,7 @@ int gamma_create(gamma_handle* out, const float* ref_dev, const float* eval_dev,
     if ((e = cudaMalloc(&h->fix_list, sizeof(unsigned) * nvox)) != cudaSuccess) return fail(cuda_fail(e));
     {
         Problem P0 = make_problem(h, nullptr);
-        const int tiles = gk::shell_tiles(P0);
+        const int tiles = gk::block_tiles(P0);
         if (tiles < 0) return fail(GAMMA_ERR_SHAPE);
         const size_t nt = (size_t)std::max(tiles, 1);
         if ((e = cudaMalloc(&h->tile_mask, sizeof(unsigned) * 8 * nt)) != cudaSuccess ||

@@ -298,6 +298,8 @@ void key0_far(const double hn[3], int nd, double far[8]);
 // Tile-load map for a Problem; false when TMA cannot be used for it.
 bool encode_tile_map(const Problem& P, CUtensorMap* map);
 int shell_tiles(const Problem& P);
+// Tiles of k_shell's layout (the staged walks' units).
+int block_tiles(const Problem& P);
 
 // Learned proposal (gamma_learned.cu).
 bool model_weights(const gamma_model_s* m, MlpWeights* w);

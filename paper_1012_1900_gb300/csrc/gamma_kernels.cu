@@ -402,8 +402,11 @@ __global__ void __launch_bounds__(256, MINB)
 // block barrier per tile, so a tile takes as long as its slowest warp row.
 // Here each warp stages its own smaller tile (32 x 2 x 2 voxels in 3D, 32 x 4
 // in 2D, with a one-voxel halo) into a double buffer of its own, with its own
-// TMA copies and mbarriers, and takes its next tile from the work counter by
-// itself: warps never wait for one another until the end of the kernel.
+// TMA copies and mbarriers (or plain loads when the grid takes no TMA map),
+// and takes its next tile from the work counter by itself: warps never wait
+// for one another until the end of the kernel.  Batched launches number the
+// tiles of all pairs of a group in one range; a warp keeps a copy of its
+// current pair's Problem in shared memory.
 template <int N>
 struct WarpTile {
     static constexpr int TX = 32, TY = N == 3 ? 2 : 4, TZ = N == 3 ? 2 : 1;
@@ -413,24 +416,25 @@ struct WarpTile {
     static_assert(STRIDE * 4 % 128 == 0, "TMA destination must stay 128-byte aligned");
 };
 
-template <int N, int MINB>
+template <int N, int MINB, bool BATCH>
 __global__ void __launch_bounds__(256, MINB)
-    k_shell_w(const __grid_constant__ Problem P, const __grid_constant__ CUtensorMap tmap, int ntiles,
-              unsigned* tile_next)
+    k_shell_w(const __grid_constant__ Problem P0, const __grid_constant__ CUtensorMap tmap0,
+              int use_tma0, int t_first, int ntiles, unsigned* tile_next,
+              const __grid_constant__ SlabGate gate, const BatchDesc* __restrict__ bd)
 {
     using T = WarpTile<N>;
     __shared__ __align__(128) float tiles[8][2][T::STRIDE];
     __shared__ __align__(8) uint64_t bar[8][2];
+    __shared__ __align__(16) Problem sh_P[BATCH ? 8 : 1];   // batched: each warp's current pair
     __shared__ unsigned int sh_hist[kNumBuckets];
     __shared__ unsigned long long sh_eval, sh_pass;
-    __shared__ unsigned int sh_rmax;
+    __shared__ unsigned int sh_rmax, sh_bad;
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x < kNumBuckets) sh_hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
-        sh_eval = 0;
-        sh_pass = 0;
-        sh_rmax = 0;
+        sh_eval = sh_pass = 0;
+        sh_rmax = sh_bad = 0;
     }
     if (lane == 0) {
         mbar_init(&bar[w][0], 1);
@@ -439,49 +443,137 @@ __global__ void __launch_bounds__(256, MINB)
     }
     __syncthreads();
 
-    const int ntx = (P.nx + T::TX - 1) / T::TX, nty = (P.ny + T::TY - 1) / T::TY;
-    auto origin = [&](int t, int& x0, int& y0, int& z0) {
-        x0 = (t % ntx) * T::TX;
-        y0 = ((t / ntx) % nty) * T::TY;
-        z0 = (t / ntx / nty) * T::TZ;
+    // global tile -> (pair, tile of that pair)
+    auto locate = [&](int t, int& pr, int& lt) {
+        if constexpr (!BATCH) {
+            pr = 0;
+            lt = t;
+        } else {
+            int lo = 0, hi = bd->npairs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bd->tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            pr = lo;
+            lt = t - bd->tile_start[lo];
+        }
     };
-    auto issue = [&](int t, int b) {           // lane 0
+    auto origin = [&](int nx, int ny, int lt, int& x0, int& y0, int& z0) {
+        const int ntx = (nx + T::TX - 1) / T::TX, nty = (ny + T::TY - 1) / T::TY;
+        x0 = (lt % ntx) * T::TX;
+        y0 = ((lt / ntx) % nty) * T::TY;
+        z0 = (lt / ntx / nty) * T::TZ;
+    };
+    bool gate_failed = false;                 // lane 0: a slab wait gave up
+    // lane 0: the TMA copy of tile t into buffer b (tiles without a map are
+    // loaded when they are processed)
+    auto issue = [&](int t, int b) {
         if (t >= ntiles) return;
+        int pr, lt;
+        locate(t, pr, lt);
+        if (!(BATCH ? bd->use_tma[pr] : use_tma0)) return;
+        const Problem& Q = BATCH ? bd->probs[pr] : P0;
+        const CUtensorMap* map = BATCH ? &bd->maps[pr] : &tmap0;
         int x0, y0, z0;
-        origin(t, x0, y0, z0);
+        origin(Q.nx, Q.ny, lt, x0, y0, z0);
+        if (!BATCH && gate.flag && !gate_failed) {
+            // the box reads slices z0 - 1 .. z0 + TZ, from at most two slabs
+            const int zlo = max(z0 - 1, 0), zhi = min(z0 + T::TZ, Q.nz - 1);
+            if (!flag_wait_bounded(gate.flag + zlo / gate.depth, gate.epoch) ||
+                !flag_wait_bounded(gate.flag + zhi / gate.depth, gate.epoch)) {
+                atomicOr(&Q.ctr->flags, kFlagTimeout);     // the run reports a timeout
+                gate_failed = true;                        // and this warp waits no more
+            }
+            fence_async_global();
+        }
         mbar_arrive_expect_tx(&bar[w][b], T::ELEMS * (uint32_t)sizeof(float));
-        if (N == 3) tma_load_3d(tiles[w][b], &tmap, x0 - 4, y0 - 1, z0 - 1, &bar[w][b]);
-        else tma_load_2d(tiles[w][b], &tmap, x0 - 4, y0 - 1, &bar[w][b]);
+        if (N == 3) tma_load_3d(tiles[w][b], map, x0 - 4, y0 - 1, z0 - 1, &bar[w][b]);
+        else tma_load_2d(tiles[w][b], map, x0 - 4, y0 - 1, &bar[w][b]);
     };
     const int nwarps = (int)gridDim.x * 8;
-    int t = (int)blockIdx.x * 8 + w;           // the first tile of every warp, then the counter
+    int t = t_first + (int)blockIdx.x * 8 + w;     // the first tile of every warp, then the counter
     if (lane == 0) issue(t, 0);
 
-    const float dnorm = resolve_dnorm(P);
-    const float thr = P.cutoff_frac * dnorm;
-    const float k0 = P.ntable > 0 ? P.table[0].key : kInf;
-    const float qlim = fminf(k0 * k0, P.r_cover * P.r_cover);
     unsigned my_eval = 0, my_pass = 0;
     float my_rmax = 0.f;
-    bool bad_ev = false;
-    bool timed_out = false;
-    uint32_t parity = 0;
+    bool bad_ev = false, timed_out = false;
+    uint32_t parity = 0;                      // bit b: phase of bar[w][b] to wait for
     int b = 0;
+    int cur = -1;                             // batched: the pair in sh_P[w] and counted in my_*
+    // the current pair's constants: dose norm, cutoff, and the bound below
+    // which a voxel is final (every face not through the voxel is at spatial
+    // distance >= the first table key, or >= the cover radius when the table
+    // was cut)
+    float dnorm = 0.f, thr = 0.f, qlim = 0.f;
+    auto constants = [&](const Problem& Q) {
+        dnorm = resolve_dnorm(Q);
+        thr = Q.cutoff_frac * dnorm;
+        const float k0 = Q.ntable > 0 ? Q.table[0].key : kInf;
+        qlim = fminf(k0 * k0, Q.r_cover * Q.r_cover);
+    };
+    if constexpr (!BATCH) constants(P0);
+
+    // a warp's counts -> its pair's counters (batched: when its pair changes)
+    auto flush_counts = [&](const Problem& Q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            my_eval += __shfl_xor_sync(kFull, my_eval, o);
+            my_pass += __shfl_xor_sync(kFull, my_pass, o);
+            my_rmax = fmaxf(my_rmax, __shfl_xor_sync(kFull, my_rmax, o));
+        }
+        if (__any_sync(kFull, bad_ev) && lane == 0) atomicOr(&Q.ctr->flags, kFlagNonFinite);
+        if (lane == 0) {
+            if (my_eval) atomicAdd(&Q.ctr->n_eval, (unsigned long long)my_eval);
+            if (my_pass) atomicAdd(&Q.ctr->n_pass, (unsigned long long)my_pass);
+            if (my_rmax > 0.f) atomicMax(&Q.ctr->rmax_enc, fenc(my_rmax));
+        }
+        my_eval = my_pass = 0;
+        my_rmax = 0.f;
+        bad_ev = false;
+    };
+
     while (t < ntiles) {
         int nt = 0;
         if (lane == 0) {
-            nt = nwarps + (int)atomicAdd(tile_next, 1u);
+            nt = t_first + nwarps + (int)atomicAdd(tile_next, 1u);
             issue(nt, b ^ 1);
         }
         nt = __shfl_sync(kFull, nt, 0);
-        if (!mbar_wait_bounded(&bar[w][b], (parity >> b) & 1u)) {
-            timed_out = true;                  // (warp-uniform: every lane polls the same phase)
-            break;
+        int pr, lt;
+        locate(t, pr, lt);
+        if constexpr (BATCH) {
+            if (pr != cur) {                   // warp-uniform
+                if (cur >= 0) flush_counts(sh_P[w]);
+                __syncwarp();
+                const int* src = (const int*)&bd->probs[pr];
+                int* dst = (int*)&sh_P[w];
+                for (int i = lane; i < (int)(sizeof(Problem) / 4); i += 32) dst[i] = src[i];
+                __syncwarp();
+                cur = pr;
+                constants(sh_P[w]);
+            }
         }
-        parity ^= 1u << b;
-        const float* tl = tiles[w][b];
+        const Problem& P = BATCH ? sh_P[w] : P0;
+        float* tl = tiles[w][b];
         int x0, y0, z0;
-        origin(t, x0, y0, z0);
+        origin(P.nx, P.ny, lt, x0, y0, z0);
+        if (BATCH ? bd->use_tma[pr] : use_tma0) {
+            if (!mbar_wait_bounded(&bar[w][b], (parity >> b) & 1u)) {
+                timed_out = true;              // (warp-uniform: every lane polls the same phase)
+                break;
+            }
+            parity ^= 1u << b;
+        } else {
+            // no TMA map for this grid: the warp loads the box itself
+            for (int i = lane; i < T::ELEMS; i += 32) {
+                const int bx = i % T::BX, by = (i / T::BX) % T::BY, bz = i / (T::BX * T::BY);
+                const int gx = x0 - 4 + bx, gy = y0 - 1 + by, gz = (N == 3 ? z0 - 1 : 0) + bz;
+                const bool in = (unsigned)gx < (unsigned)P.nx && (unsigned)gy < (unsigned)P.ny &&
+                                (N == 2 || (unsigned)gz < (unsigned)P.nz);
+                tl[i] = in ? __ldg(P.ev + ((long long)gz * P.ny + gy) * P.nx + gx) : 0.f;
+            }
+            __syncwarp();
+        }
 #pragma unroll 1
         for (int r = 0; r < T::TY * T::TZ; ++r) {
             const int ly = r % T::TY, lz = r / T::TY;
@@ -497,7 +589,7 @@ __global__ void __launch_bounds__(256, MINB)
                 if (!act) P.out[v] = __int_as_float(0x7fc00000);
                 bad_ev |= !isfinite(tl[tix]);       // every evaluation dose is some tile's centre
             }
-            uint32_t inm = 0, inp = 0;
+            uint32_t inm = 0, inp = 0;         // neighbours at -1 / +1 inside the grid, per axis
             inm |= (x > 0) ? 1u : 0u;
             inp |= (x + 1 < P.nx) ? 1u : 0u;
             inm |= (y > 0) ? 2u : 0u;
@@ -533,15 +625,24 @@ __global__ void __launch_bounds__(256, MINB)
                 unsigned pos0 = 0;
                 if (lane == 0) pos0 = atomicAdd(&P.ctr->tail_count, (unsigned)__popc(tm));
                 pos0 = __shfl_sync(kFull, pos0, 0);
+                bool counted = false;
                 if (tail) {
                     const unsigned pos = pos0 + __popc(tm & ((1u << lane) - 1u));
                     if (pos < P.tail_cap) {
                         P.tail_raw[pos] = (unsigned)v;
                         P.tail_bucket[pos] = (unsigned char)bucket;
-                        atomicAdd(&sh_hist[bucket], 1u);
+                        counted = true;
                     } else {
                         atomicOr(&P.ctr->flags, kFlagTailFull);
                     }
+                }
+                if constexpr (BATCH) {
+                    // the pair's histogram, one atomic per distinct bucket of the row
+                    const unsigned peers = __match_any_sync(kFull, counted ? bucket : -1);
+                    if (counted && lane == __ffs(peers) - 1)
+                        atomicAdd(&P.ctr->hist[bucket], (unsigned)__popc(peers));
+                } else {
+                    if (counted) atomicAdd(&sh_hist[bucket], 1u);
                 }
             }
         }
@@ -551,33 +652,40 @@ __global__ void __launch_bounds__(256, MINB)
     }
     if (timed_out) {
         if (lane == 0) {
-            atomicOr(&P.ctr->flags, kFlagTimeout);
+            if constexpr (BATCH) atomicOr(&bd->probs[cur < 0 ? 0 : cur].ctr->flags, kFlagTimeout);
+            else atomicOr(&P0.ctr->flags, kFlagTimeout);
             // let this warp's own copies land before the block leaves
             mbar_wait_bounded(&bar[w][0], parity & 1u);
             mbar_wait_bounded(&bar[w][1], (parity >> 1) & 1u);
         }
         __syncwarp();
     }
-    // per-block counters -> the run's counters
+    if constexpr (BATCH) {
+        if (cur >= 0) flush_counts(sh_P[w]);
+    } else {
+        // per block, then one atomic each: same-address atomics serialise in L2
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_eval += __shfl_xor_sync(kFull, my_eval, o);
-        my_pass += __shfl_xor_sync(kFull, my_pass, o);
-        my_rmax = fmaxf(my_rmax, __shfl_xor_sync(kFull, my_rmax, o));
-    }
-    if (__any_sync(kFull, bad_ev) && lane == 0) atomicOr(&P.ctr->flags, kFlagNonFinite);
-    if (lane == 0) {
-        if (my_eval) atomicAdd(&sh_eval, (unsigned long long)my_eval);
-        if (my_pass) atomicAdd(&sh_pass, (unsigned long long)my_pass);
-        atomicMax(&sh_rmax, fenc(my_rmax));
-    }
-    __syncthreads();
-    if (threadIdx.x < kNumBuckets && sh_hist[threadIdx.x])
-        atomicAdd(&P.ctr->hist[threadIdx.x], sh_hist[threadIdx.x]);
-    if (threadIdx.x == 0) {
-        if (sh_eval) atomicAdd(&P.ctr->n_eval, sh_eval);
-        if (sh_pass) atomicAdd(&P.ctr->n_pass, sh_pass);
-        atomicMax(&P.ctr->rmax_enc, sh_rmax);
+        for (int o = 16; o > 0; o >>= 1) {
+            my_eval += __shfl_xor_sync(kFull, my_eval, o);
+            my_pass += __shfl_xor_sync(kFull, my_pass, o);
+            my_rmax = fmaxf(my_rmax, __shfl_xor_sync(kFull, my_rmax, o));
+        }
+        const bool bad = __any_sync(kFull, bad_ev);
+        if (lane == 0) {
+            if (my_eval) atomicAdd(&sh_eval, (unsigned long long)my_eval);
+            if (my_pass) atomicAdd(&sh_pass, (unsigned long long)my_pass);
+            atomicMax(&sh_rmax, fenc(my_rmax));
+            if (bad) sh_bad = 1;
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumBuckets && sh_hist[threadIdx.x])
+            atomicAdd(&P0.ctr->hist[threadIdx.x], sh_hist[threadIdx.x]);
+        if (threadIdx.x == 0) {
+            if (sh_eval) atomicAdd(&P0.ctr->n_eval, sh_eval);
+            if (sh_pass) atomicAdd(&P0.ctr->n_pass, sh_pass);
+            atomicMax(&P0.ctr->rmax_enc, sh_rmax);
+            if (sh_bad) atomicOr(&P0.ctr->flags, kFlagNonFinite);
+        }
     }
 }
 
@@ -1092,6 +1200,7 @@ __global__ void __launch_bounds__(256, MINB)
     __shared__ CqWarp cqw[8];
     __shared__ CqWalkDims cqd[BATCH ? 8 : 1];
     __shared__ unsigned s_end[kCqParts];   // the parts of the queue end at these items
+    __shared__ float s_dnorm;              // single pair: its dose norm
     CqWarp& W = cqw[threadIdx.x >> 5];
     volatile CqWarp& V = cqw[threadIdx.x >> 5];
     volatile CqWalkDims& VD = cqd[BATCH ? threadIdx.x >> 5 : 0];
@@ -1125,6 +1234,7 @@ __global__ void __launch_bounds__(256, MINB)
                 h4 += __shfl_xor_sync(kFull, h4, o);
             }
             if (lane == 0) {
+                s_dnorm = resolve_dnorm(P);
                 s_end[0] = min(h32, total);
                 s_end[1] = min(h8, total);
                 s_end[2] = min(h4, total);
@@ -1221,7 +1331,7 @@ __global__ void __launch_bounds__(256, MINB)
                     V.xyz[2][ld] = (int)(r1 / (unsigned)Q.ny);
                     const float dr = __ldg(Q.ref + v);
                     V.dr[ws] = dr;
-                    V.inv[ws] = 1.0f / (Q.dd_frac * (Q.local ? dr : resolve_dnorm(Q)));
+                    V.inv[ws] = 1.0f / (Q.dd_frac * (Q.local ? dr : (BATCH ? resolve_dnorm(Q) : s_dnorm)));
                     V.best[ws] = __float_as_uint(Q.out[v]);  // gamma^2 over the faces through v
                     V.vox[ws] = v;
                     if constexpr (BATCH) {
@@ -2156,23 +2266,36 @@ static bool encode_box_map(const Problem& P, CUtensorMap* map, int bx, int by, i
            CUDA_SUCCESS;
 }
 
+// The shell of a run uses k_shell_w (warp tiles) unless a staged walk needs
+// k_shell's tile layout for its queue.
+static bool warp_tiled(const Problem& P) { return !P.tile_mask && !P.row_items; }
+
 bool encode_tile_map(const Problem& P, CUtensorMap* map)
 {
+    if (warp_tiled(P))
+        return P.ndim == 3 ? encode_box_map(P, map, WarpTile<3>::BX, WarpTile<3>::BY, WarpTile<3>::BZ)
+                           : encode_box_map(P, map, WarpTile<2>::BX, WarpTile<2>::BY, 1);
     return P.ndim == 3 ? encode_box_map(P, map, ShellTile<3>::BX, ShellTile<3>::BY, ShellTile<3>::BZ)
                        : encode_box_map(P, map, ShellTile<2>::BX, ShellTile<2>::BY, 1);
 }
 
+template <class T>
+static long long tile_count(const Problem& P)
+{
+    const long long nxy = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
+    return P.ndim == 3 ? nxy * ((P.nz + T::TZ - 1) / T::TZ) : nxy;
+}
+
+int block_tiles(const Problem& P)
+{
+    const long long tiles = P.ndim == 3 ? tile_count<ShellTile<3>>(P) : tile_count<ShellTile<2>>(P);
+    return tiles > 0x3fffffffLL ? -1 : (int)tiles;
+}
+
 int shell_tiles(const Problem& P)
 {
-    long long tiles;
-    if (P.ndim == 3) {
-        using T = ShellTile<3>;
-        tiles = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY) *
-                ((P.nz + T::TZ - 1) / T::TZ);
-    } else {
-        using T = ShellTile<2>;
-        tiles = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
-    }
+    if (!warp_tiled(P)) return block_tiles(P);
+    const long long tiles = P.ndim == 3 ? tile_count<WarpTile<3>>(P) : tile_count<WarpTile<2>>(P);
     return tiles > 0x3fffffffLL ? -1 : (int)tiles;
 }
 
@@ -2196,18 +2319,35 @@ bool shell_gate_ok(const Problem& P)
     return encode_tile_map(P, &map);
 }
 
+template <class T>
+static void layers_of(const Problem& P, int* tiles_per_layer, int* layers, int* layer_depth)
+{
+    *tiles_per_layer = ((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
+    *layers = P.ndim == 3 ? (P.nz + T::TZ - 1) / T::TZ : 1;
+    *layer_depth = P.ndim == 3 ? T::TZ : 1;
+}
+
 void shell_layers(const Problem& P, int* tiles_per_layer, int* layers, int* layer_depth)
 {
-    if (P.ndim == 3) {
-        using T = ShellTile<3>;
-        *tiles_per_layer = ((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
-        *layers = (P.nz + T::TZ - 1) / T::TZ;
-        *layer_depth = T::TZ;
+    if (warp_tiled(P)) {
+        if (P.ndim == 3) layers_of<WarpTile<3>>(P, tiles_per_layer, layers, layer_depth);
+        else layers_of<WarpTile<2>>(P, tiles_per_layer, layers, layer_depth);
     } else {
-        using T = ShellTile<2>;
-        *tiles_per_layer = ((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
-        *layers = 1;
-        *layer_depth = 1;
+        if (P.ndim == 3) layers_of<ShellTile<3>>(P, tiles_per_layer, layers, layer_depth);
+        else layers_of<ShellTile<2>>(P, tiles_per_layer, layers, layer_depth);
+    }
+}
+
+template <int N, bool BATCH>
+static void launch_shell_w_k(int per_sm, unsigned grid, cudaStream_t s, const Problem& P,
+                             const CUtensorMap& map, int use_tma, int t_first, int tiles,
+                             unsigned* next, const SlabGate& gate, const BatchDesc* bd)
+{
+    switch (per_sm) {
+    case 1: k_shell_w<N, 1, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, next, gate, bd); break;
+    case 2: k_shell_w<N, 2, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, next, gate, bd); break;
+    case 3: k_shell_w<N, 3, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, next, gate, bd); break;
+    default: k_shell_w<N, 4, BATCH><<<grid, 256, 0, s>>>(P, map, use_tma, t_first, tiles, next, gate, bd); break;
     }
 }
 
@@ -2225,9 +2365,21 @@ cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, i
     if (tiles < 0 || tile_first < 0 || tile_end > tiles || tile_first > tile_end)
         return cudaErrorInvalidValue;
     if (tile_first == tile_end) return cudaSuccess;
+    unsigned* next = &P.ctr->shell_next[slot];
+    if (warp_tiled(P)) {
+        // eight tiles per block in flight
+        const unsigned grid = (unsigned)std::min<long long>((tile_end - tile_first + 7) / 8,
+                                                            (long long)sms * per_sm);
+        if (P.ndim == 3)
+            launch_shell_w_k<3, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, next, gate,
+                                       nullptr);
+        else
+            launch_shell_w_k<2, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, next, gate,
+                                       nullptr);
+        return cudaGetLastError();
+    }
     const unsigned grid =
         (unsigned)std::min<long long>(tile_end - tile_first, (long long)sms * per_sm);
-    unsigned* next = &P.ctr->shell_next[slot];
     if (P.ndim == 3)
         launch_shell_k<3, false>(per_sm, grid, s, P, map, use_tma, tile_first, tile_end, next, gate,
                                  nullptr);
@@ -2237,49 +2389,10 @@ cudaError_t launch_shell_range(const Problem& P, int tile_first, int tile_end, i
     return cudaGetLastError();
 }
 
-template <int N>
-static void launch_shell_w_k(int per_sm, unsigned grid, cudaStream_t s, const Problem& P,
-                             const CUtensorMap& map, int tiles, unsigned* next)
-{
-    switch (per_sm) {
-    case 1: k_shell_w<N, 1><<<grid, 256, 0, s>>>(P, map, tiles, next); break;
-    case 2: k_shell_w<N, 2><<<grid, 256, 0, s>>>(P, map, tiles, next); break;
-    case 3: k_shell_w<N, 3><<<grid, 256, 0, s>>>(P, map, tiles, next); break;
-    default: k_shell_w<N, 4><<<grid, 256, 0, s>>>(P, map, tiles, next); break;
-    }
-}
-
-// The shell of a whole run: one warp per tile (k_shell_w) when the staged
-// walks do not need k_shell's tile layout and the evaluation dose takes a TMA
-// map; else k_shell.
 cudaError_t launch_shell(const Problem& P, cudaStream_t s)
 {
     const int tiles = shell_tiles(P);
     if (tiles < 0) return cudaErrorInvalidValue;
-    if (!P.tile_mask && !P.row_items) {
-        CUtensorMap map;
-        std::memset(&map, 0, sizeof(map));
-        const bool tma = P.ndim == 3
-                             ? encode_box_map(P, &map, WarpTile<3>::BX, WarpTile<3>::BY, WarpTile<3>::BZ)
-                             : encode_box_map(P, &map, WarpTile<2>::BX, WarpTile<2>::BY, 1);
-        long long wt;
-        if (P.ndim == 3) {
-            using T = WarpTile<3>;
-            wt = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY) *
-                 ((P.nz + T::TZ - 1) / T::TZ);
-        } else {
-            using T = WarpTile<2>;
-            wt = (long long)((P.nx + T::TX - 1) / T::TX) * ((P.ny + T::TY - 1) / T::TY);
-        }
-        if (tma && wt <= 0x3fffffffLL) {
-            const int per_sm = std::min(4, std::max(1, P.shell_minblocks));
-            const unsigned grid =
-                (unsigned)std::max<long long>(1, std::min<long long>((wt + 7) / 8, (long long)device_sm_count() * per_sm));
-            if (P.ndim == 3) launch_shell_w_k<3>(per_sm, grid, s, P, map, (int)wt, &P.ctr->shell_next[0]);
-            else launch_shell_w_k<2>(per_sm, grid, s, P, map, (int)wt, &P.ctr->shell_next[0]);
-            return cudaGetLastError();
-        }
-    }
     return launch_shell_range(P, 0, tiles, 0, SlabGate{nullptr, 0u, 0}, s);
 }
 
@@ -2463,14 +2576,14 @@ cudaError_t launch_batch_shell(const BatchGroup& g, int shell_minblocks, cudaStr
     if (g.npairs <= 0 || g.total_tiles <= 0) return cudaSuccess;
     const int sms = device_sm_count();
     const int per_sm = std::min(4, std::max(1, shell_minblocks));
-    const unsigned grid = (unsigned)std::min<long long>(g.total_tiles, (long long)sms * per_sm);
+    const unsigned grid = (unsigned)std::min<long long>((g.total_tiles + 7) / 8, (long long)sms * per_sm);
     Problem dummy{};
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
-    if (g.ndim == 3) launch_shell_k<3, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.shell_next,
-                                        SlabGate{nullptr, 0u, 0}, g.desc);
-    else launch_shell_k<2, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.shell_next,
-                                        SlabGate{nullptr, 0u, 0}, g.desc);
+    if (g.ndim == 3) launch_shell_w_k<3, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.shell_next,
+                                          SlabGate{nullptr, 0u, 0}, g.desc);
+    else launch_shell_w_k<2, true>(per_sm, grid, s, dummy, map, 0, 0, g.total_tiles, g.shell_next,
+                                          SlabGate{nullptr, 0u, 0}, g.desc);
     return cudaGetLastError();
 }
 
