@@ -793,7 +793,8 @@ def run_ours(args, pair, rank, world, local_rank):
         t_search = mean_ph["shell_ms"] + mean_ph["tail_ms"]
         achieved = tflops(shell_cells + tail_cells, t_search)
         walker = WALKERS[args.walk][0]
-        traffic = [recorded_traffic(k, args.workload) for k in ("k_shell", walker)]
+        sheller = "k_shell" if args.walk in (1, 2) else "k_shell_w"     # the staged walks need k_shell's tiles
+        traffic = [recorded_traffic(k, args.workload) for k in (sheller, walker)]
         clock_hz = (clocks.get("sm_mhz") or sm_max) * 1e6
 
         def issue(kernel, ms):
@@ -808,7 +809,7 @@ def run_ours(args, pair, rank, world, local_rank):
                     "lane_efficiency": rec.get("lane_efficiency"),
                     "issue_active_pct_ncu": rec.get("issue_active_pct"),
                     "warps_active_pct": rec.get("warps_active_pct")}
-        roofline = {"bound": "alu", "kernel": f"k_shell+{walker}", "achieved": achieved,
+        roofline = {"bound": "alu", "kernel": f"{sheller}+{walker}", "achieved": achieved,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                     "traffic": None if None in traffic else sum(traffic),
                     "peak_basis": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
@@ -816,10 +817,10 @@ def run_ours(args, pair, rank, world, local_rank):
                     "work": f"{shell_cells + tail_cells} cells x {f} FLOP (census of whole cubes "
                             "with key < gamma*, +1 per evaluated voxel)",
                     "per_kernel": {
-                        "k_shell": {"ms": mean_ph["shell_ms"], "cells": shell_cells,
+                        sheller: {"ms": mean_ph["shell_ms"], "cells": shell_cells,
                                     "achieved": tflops(shell_cells, mean_ph["shell_ms"]),
                                     "traffic": traffic[0],
-                                    "executed_issue": issue("k_shell", mean_ph["shell_ms"])},
+                                    "executed_issue": issue(sheller, mean_ph["shell_ms"])},
                         walker: {"ms": mean_ph["tail_ms"], "cells": tail_cells,
                                  "achieved": tflops(tail_cells, mean_ph["tail_ms"]),
                                  "traffic": traffic[1],

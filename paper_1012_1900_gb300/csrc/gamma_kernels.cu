@@ -429,6 +429,11 @@ __global__ void __launch_bounds__(256, MINB)
     __shared__ unsigned int sh_hist[kNumBuckets];
     __shared__ unsigned long long sh_eval, sh_pass;
     __shared__ unsigned int sh_rmax, sh_bad;
+    // each warp's queued voxels (and cost buckets) not yet in the run's queue:
+    // one atomic on the queue counter per kShellQ of them, not one per row
+    constexpr int kShellQ = BATCH ? 64 : 128;     // (the batched kernel keeps 8 Problems too)
+    __shared__ unsigned qv[8][kShellQ];
+    __shared__ unsigned char qb[8][kShellQ];
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x < kNumBuckets) sh_hist[threadIdx.x] = 0;
@@ -532,6 +537,40 @@ __global__ void __launch_bounds__(256, MINB)
         bad_ev = false;
     };
 
+    int qn = 0;                               // entries in qv[w] (warp-uniform)
+    auto flush_queue = [&](const Problem& Q) {
+        if (qn == 0) return;
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&Q.ctr->tail_count, (unsigned)qn);
+        base = __shfl_sync(kFull, base, 0);
+        for (int i0 = 0; i0 < qn; i0 += 32) {
+            const int i = i0 + lane;
+            bool counted = false;
+            int bk = 0;
+            if (i < qn) {
+                const unsigned pos = base + (unsigned)i;
+                bk = qb[w][i];
+                if (pos < Q.tail_cap) {
+                    Q.tail_raw[pos] = qv[w][i];
+                    Q.tail_bucket[pos] = (unsigned char)bk;
+                    counted = true;
+                } else {
+                    atomicOr(&Q.ctr->flags, kFlagTailFull);
+                }
+            }
+            if constexpr (BATCH) {
+                // the pair's histogram, one atomic per distinct bucket of the 32
+                const unsigned peers = __match_any_sync(kFull, counted ? bk : -1);
+                if (counted && lane == __ffs(peers) - 1)
+                    atomicAdd(&Q.ctr->hist[bk], (unsigned)__popc(peers));
+            } else {
+                if (counted) atomicAdd(&sh_hist[bk], 1u);
+            }
+        }
+        __syncwarp();
+        qn = 0;
+    };
+
     while (t < ntiles) {
         int nt = 0;
         if (lane == 0) {
@@ -543,7 +582,10 @@ __global__ void __launch_bounds__(256, MINB)
         locate(t, pr, lt);
         if constexpr (BATCH) {
             if (pr != cur) {                   // warp-uniform
-                if (cur >= 0) flush_counts(sh_P[w]);
+                if (cur >= 0) {
+                    flush_queue(sh_P[w]);
+                    flush_counts(sh_P[w]);
+                }
                 __syncwarp();
                 const int* src = (const int*)&bd->probs[pr];
                 int* dst = (int*)&sh_P[w];
@@ -557,6 +599,16 @@ __global__ void __launch_bounds__(256, MINB)
         float* tl = tiles[w][b];
         int x0, y0, z0;
         origin(P.nx, P.ny, lt, x0, y0, z0);
+        // the tile's reference doses, loaded while its staged box may still
+        // be in flight (row r in drq[0] when row r is processed)
+        constexpr int ROWS = T::TY * T::TZ;
+        float drq[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int x = x0 + lane, y = y0 + r % T::TY, z = z0 + r / T::TY;
+            drq[r] = (x < P.nx && y < P.ny && z < P.nz) ? __ldg(P.ref + ((long long)z * P.ny + y) * P.nx + x)
+                                                         : 0.f;
+        }
         if (BATCH ? bd->use_tma[pr] : use_tma0) {
             if (!mbar_wait_bounded(&bar[w][b], (parity >> b) & 1u)) {
                 timed_out = true;              // (warp-uniform: every lane polls the same phase)
@@ -575,16 +627,18 @@ __global__ void __launch_bounds__(256, MINB)
             __syncwarp();
         }
 #pragma unroll 1
-        for (int r = 0; r < T::TY * T::TZ; ++r) {
+        for (int r = 0; r < ROWS; ++r) {
             const int ly = r % T::TY, lz = r / T::TY;
             const int x = x0 + lane, y = y0 + ly, z = z0 + lz;
             const bool inside = x < P.nx && y < P.ny && z < P.nz;
             const long long v = inside ? ((long long)z * P.ny + y) * P.nx + x : 0;
             const int tix = ((N == 3 ? lz + 1 : 0) * T::BY + (ly + 1)) * T::BX + (lane + 4);
-            float dr = 0.f, best = 0.f;
+            const float dr = drq[0];
+#pragma unroll
+            for (int k = 0; k + 1 < ROWS; ++k) drq[k] = drq[k + 1];
+            float best = 0.f;
             bool act = false;
             if (inside) {
-                dr = __ldg(P.ref + v);
                 act = is_evaluated(P, dr, thr);
                 if (!act) P.out[v] = __int_as_float(0x7fc00000);
                 bad_ev |= !isfinite(tl[tix]);       // every evaluation dose is some tile's centre
@@ -622,28 +676,14 @@ __global__ void __launch_bounds__(256, MINB)
             }
             const unsigned tm = __ballot_sync(kFull, tail);
             if (tm) {
-                unsigned pos0 = 0;
-                if (lane == 0) pos0 = atomicAdd(&P.ctr->tail_count, (unsigned)__popc(tm));
-                pos0 = __shfl_sync(kFull, pos0, 0);
-                bool counted = false;
+                if (qn + 32 > kShellQ) flush_queue(P);
                 if (tail) {
-                    const unsigned pos = pos0 + __popc(tm & ((1u << lane) - 1u));
-                    if (pos < P.tail_cap) {
-                        P.tail_raw[pos] = (unsigned)v;
-                        P.tail_bucket[pos] = (unsigned char)bucket;
-                        counted = true;
-                    } else {
-                        atomicOr(&P.ctr->flags, kFlagTailFull);
-                    }
+                    const int i = qn + __popc(tm & ((1u << lane) - 1u));
+                    qv[w][i] = (unsigned)v;
+                    qb[w][i] = (unsigned char)bucket;
                 }
-                if constexpr (BATCH) {
-                    // the pair's histogram, one atomic per distinct bucket of the row
-                    const unsigned peers = __match_any_sync(kFull, counted ? bucket : -1);
-                    if (counted && lane == __ffs(peers) - 1)
-                        atomicAdd(&P.ctr->hist[bucket], (unsigned)__popc(peers));
-                } else {
-                    if (counted) atomicAdd(&sh_hist[bucket], 1u);
-                }
+                qn += __popc(tm);
+                __syncwarp();
             }
         }
         __syncwarp();                          // tiles[w][b] is free for the copy after next
@@ -661,8 +701,12 @@ __global__ void __launch_bounds__(256, MINB)
         __syncwarp();
     }
     if constexpr (BATCH) {
-        if (cur >= 0) flush_counts(sh_P[w]);
+        if (cur >= 0) {
+            flush_queue(sh_P[w]);
+            flush_counts(sh_P[w]);
+        }
     } else {
+        flush_queue(P0);
         // per block, then one atomic each: same-address atomics serialise in L2
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
