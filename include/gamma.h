@@ -142,7 +142,7 @@ int gamma_create(gamma_handle *out, const float *ref_dev, const float *eval_dev,
  * dose norm (global mode) and the cutoff use the reference doses.  Both
  * buffers are borrowed device float32 arrays; gamma_run writes nz*ny*nx
  * reference-grid values.  Identical geometries give an ordinary handle (the
- * coincident-grid search).  Options: "timing", "fp64_tau_exp10", "table_cap",
+ * coincident-grid search).  Options: "timing", "fp64_tau_exp10", "walk", "table_cap",
  * "lanes_per_voxel" (lanes that walk one reference voxel's cells together,
  * default 8).
  * Errors: INVALID_ARG, SHAPE, OOM, CUDA.  Synchronous. */
@@ -217,7 +217,12 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     independently takes one 32-voxel row of a shell tile
  *                     with queued voxels, stages the doses around it in shared
  *                     memory (one TMA copy) and walks the table for the row's
- *                     queued voxels.  Every walk gives the same map.
+ *                     queued voxels.  Every walk gives the same map.  Handles
+ *                     of gamma_create_grids take 0 (default: lanes_per_voxel
+ *                     lanes per reference voxel, each lane evaluating its own
+ *                     cells) or 3 (cells evaluated 32 at a time by the warp,
+ *                     8 lanes per voxel; same map, slower on the measured
+ *                     two-grid workloads).
  *  "group_bucket"     "walk" 3: queued voxels whose cost bucket (1 + floor(2
  *                     log2 of the cells below their starting bound)) is at
  *                     least this value walk 4 lanes each, the rest one lane

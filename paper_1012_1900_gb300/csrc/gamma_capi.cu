@@ -69,6 +69,7 @@ void free_batch(BatchState* b);
 struct GridState {
     gk::GridProblem G{};
     TableEntry* table_dev = nullptr;
+    unsigned* walk_list = nullptr;     // voxels the warp-evaluated walk leaves to k_grid_walk
 };
 
 // Evaluation-dose z slabs of a host-buffer run: the shell starts on a slab
@@ -334,6 +335,7 @@ void free_ctx(gamma_ctx* h)
     if (h->batch) free_batch(h->batch);
     if (h->grids) {
         cudaFree(h->grids->table_dev);
+        cudaFree(h->grids->walk_list);
         delete h->grids;
     }
     if (h->own_model) gamma_model_destroy(h->model);
@@ -740,6 +742,7 @@ int gamma_create_grids(gamma_handle* out, const float* ref_dev, const float* eva
     auto fail = [&](int code) { free_ctx(h); return code; };
     h->grids = new (std::nothrow) GridState();
     if (!h->grids) return fail(GAMMA_ERR_OOM);
+    h->walk = 0;       // the lane walk: the warp-evaluated one measured slower on two grids
     if (cudaGetDevice(&h->device) != cudaSuccess) return fail(GAMMA_ERR_CUDA);
     h->ndim = ndim;
     h->nz = ndim == 3 ? ref_shape[0] : 1;
@@ -794,6 +797,8 @@ int gamma_create_grids(gamma_handle* out, const float* ref_dev, const float* eva
     G.table = h->grids->table_dev;
     G.ntable = (int)table.size();
     G.r_cover = std::isinf(cover) ? INFINITY : round_down(cover);
+    if ((e = cudaMalloc(&h->grids->walk_list, sizeof(unsigned) * (size_t)nref)) != cudaSuccess)
+        return fail(cuda_fail(e));
     for (auto& te : h->tev)
         if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(cuda_fail(e));
     if ((e = cudaMalloc(&h->ctr, sizeof(Counters))) != cudaSuccess) return fail(cuda_fail(e));
@@ -858,6 +863,9 @@ int gamma_run(gamma_handle h, float* gamma_out_dev, void* cuda_stream)
         G.ctr = h->ctr;
         G.tau = (float)h->tau;
         G.lanes = h->lanes;
+        G.walk = h->walk;
+        G.walk_list = h->grids->walk_list;
+        G.from_list = 0;
         if (tm) {
             CK(cudaEventRecord(h->tev[0], s));
             CK(cudaEventRecord(h->tev[1], s));
@@ -1239,8 +1247,13 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         return GAMMA_OK;
     }
     if (h->grids && std::strcmp(key, "timing") && std::strcmp(key, "fp64_tau_exp10") &&
-        std::strcmp(key, "lanes_per_voxel"))
+        std::strcmp(key, "lanes_per_voxel") && std::strcmp(key, "walk"))
         return GAMMA_ERR_INVALID_ARG;                   // the other options tune the coincident-grid search
+    if (h->grids && !std::strcmp(key, "walk")) {
+        if (value != 0 && value != 3) return GAMMA_ERR_INVALID_ARG;   // lane walk or warp-evaluated
+        h->walk = (int)value;
+        return GAMMA_OK;
+    }
     if (h->batch) {
         h->batch->dirty = true;
         if (!std::strcmp(key, "graph")) {

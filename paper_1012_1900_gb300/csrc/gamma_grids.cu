@@ -133,8 +133,11 @@ __global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ Gr
     const float rc2 = G.r_cover * G.r_cover;
     unsigned my_eval = 0, my_pass = 0, my_over = 0;
     const long long ngroups = ((long long)gridDim.x * blockDim.x) / GL;
-    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / GL; v < G.nref;
-         v += ngroups) {                                     // group-uniform
+    // every reference voxel, or (from_list) those k_grid_cq left in walk_list
+    const long long nwork = G.from_list ? (long long)G.ctr->fix_count : G.nref;
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / GL; i < nwork;
+         i += ngroups) {                                     // group-uniform
+        const long long v = G.from_list ? (long long)G.walk_list[i] : i;
         const float dr = __ldg(G.ref + v);
         if (!(dr >= thr && (!G.local || dr > 0.f))) {
             if (gl == 0) G.out[v] = __int_as_float(0x7fc00000);
@@ -259,6 +262,283 @@ __global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ Gr
 }
 
 // --------------------------------------------------------------------------
+// The warp-evaluated walk (default): cells collected per warp, evaluated 32
+// at a time
+// --------------------------------------------------------------------------
+
+// As for coincident grids (k_tail_cq), the face evaluation of a cell is not
+// done by the lane that reached it: a cell that passes the box and dose-gap
+// bounds is appended, with its vertex doses and its offset from the point, to
+// a ring of the warp, and the whole warp evaluates 32 such cells at once, one
+// per lane, lowering each owner's running bound in shared memory (atomicMin
+// on the bits of a non-negative float).  GL lanes walk one reference voxel's
+// table together (GL entries per step); a walker keeps two voxel slots so that
+// it starts its next voxel while the cells of its last one wait.  Every stop
+// and prune stays exact with a lagging bound, and each cell is evaluated with
+// the arithmetic of grid_cell, so the map is k_grid_walk's.  A voxel with a
+// near-singular cell, or whose walk runs past a truncated table, goes to
+// walk_list; k_grid_walk then searches it again from scratch (FP64 redo, box
+// scan), so that this kernel keeps the registers of the FP32 evaluation.
+constexpr int kGqRing = 64;
+
+struct GqWarp {
+    float q[8][kGqRing];       // vertex doses of a pending cell (relative, normalised)
+    float cf[3][kGqRing];      // its lower corner relative to the point (evaluation voxels)
+    unsigned meta[kGqRing];    // owner slot (bits 0-5), vertices inside the grid (bits 8-15)
+    unsigned best[64];         // running squared gamma per voxel slot (float bits)
+    unsigned vox[64];          // reference voxel per slot
+    float dr[32], inv[32];     // the walking voxel's reference dose and 1 / Delta D, per walker
+    float fr[3][32];           // its position in its evaluation cell
+    int c0[3][32];             // that cell
+    int t[32];                 // its next table entry
+    unsigned wseq[32], dseq[32], state[32];
+    unsigned fixm[2];          // slots whose voxel is searched again by k_grid_walk
+    unsigned cnt[2][32];       // voxels finished and passed
+    unsigned pend[64];         // evaluated reference voxels not yet taken by a walker
+};
+constexpr unsigned kGqWalk = 1u, kGqEnded = 2u, kGqWPend = 4u, kGqDBusy = 8u, kGqDPend = 16u,
+                   kGqDOver = 32u, kGqSlot = 64u;     // slot bit: the walking slot is walker + 32
+
+template <int N, int GL>
+__global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ GridProblem G)
+{
+    __shared__ GqWarp gqw[8];
+    GqWarp& W = gqw[threadIdx.x >> 5];
+    volatile GqWarp& V = gqw[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31, gl = lane & (GL - 1), ld = lane - gl;
+    const bool leader = gl == 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const unsigned gmask = GL == 32 ? kFull : ((1u << GL) - 1u) << ld;
+    const float dnorm = G.dose_norm > 0.f ? G.dose_norm : fdec(G.ctr->dnorm_enc);
+    const float thr = G.cutoff_frac * dnorm;
+    const float rc2 = G.r_cover * G.r_cover;
+    const float ehf[3] = {(float)G.eh[0], (float)G.eh[1], (float)G.eh[2]};
+    W.state[lane] = 0;
+    W.wseq[lane] = W.dseq[lane] = 0;
+    W.cnt[0][lane] = W.cnt[1][lane] = 0;
+    if (lane < 2) W.fixm[lane] = 0;
+    __syncwarp();
+
+    unsigned head = 0, count = 0;      // the ring: pending cells are [head, head + count)
+    unsigned pend_n = 0;               // entries of W.pend (warp-uniform)
+    bool queue_done = false;           // warp-uniform
+    for (;;) {
+        unsigned sta = V.state[ld];
+        if (leader) {
+            // 1. a drained voxel whose cells are all evaluated is final
+            if ((sta & kGqDBusy) && (!(sta & kGqDPend) || (int)(head - V.dseq[ld]) > 0)) {
+                const int ds = ld + ((sta & kGqSlot) ? 0 : 32);
+                const float best = __uint_as_float(V.best[ds]);
+                const unsigned v = V.vox[ds];
+                if (((V.fixm[ds >> 5] >> (ds & 31)) & 1u) || ((sta & kGqDOver) && best > rc2)) {
+                    G.walk_list[atomicAdd(&G.ctr->fix_count, 1u)] = v;   // k_grid_walk finishes it
+                } else {
+                    const float gam = sqrtf(best);
+                    G.out[v] = gam;
+                    ++V.cnt[0][ld];
+                    if (gam <= 1.f) ++V.cnt[1][ld];
+                }
+                sta &= ~kGqDBusy;
+            }
+            // 2. an ended walk becomes the drain slot; the walker takes a new voxel
+            if ((sta & kGqEnded) && !(sta & kGqDBusy)) {
+                unsigned d = kGqDBusy;
+                if (sta & kGqWPend) d |= kGqDPend;
+                if (V.t[ld] >= G.ntable) d |= kGqDOver;
+                V.dseq[ld] = V.wseq[ld];
+                sta = d | ((sta & kGqSlot) ^ kGqSlot);
+            }
+        }
+        // 3. refill the empty walkers, from a per-warp list of evaluated voxels
+        //    that the warp fills 32 grid voxels at a time (one atomic each)
+        const bool empty = leader && !(sta & (kGqWalk | kGqEnded));
+        const unsigned need = __ballot_sync(kFull, empty);
+        while (__popc(need) > (int)pend_n && !queue_done) {      // warp-uniform
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(&G.ctr->head, 32u);
+            base = __shfl_sync(kFull, base, 0);
+            const long long v = (long long)base + lane;
+            bool take = false;
+            if (v < G.nref) {
+                const float r = __ldg(G.ref + v);
+                take = r >= thr && (!G.local || r > 0.f);
+                if (!take) G.out[v] = __int_as_float(0x7fc00000);
+            }
+            const unsigned tk = __ballot_sync(kFull, take);
+            if (take) V.pend[pend_n + __popc(tk & lt_mask)] = (unsigned)v;
+            pend_n += __popc(tk);
+            if ((long long)base + 32 >= G.nref) queue_done = true;
+            __syncwarp();
+        }
+        if (empty) {
+            const int k = __popc(need & lt_mask);
+            if (k < (int)pend_n) {
+                const unsigned v = V.pend[pend_n - 1 - k];
+                const int ws = ld + ((sta & kGqSlot) ? 32 : 0);
+                const long long ix[3] = {v % G.rn[0], (v / G.rn[0]) % G.rn[1], v / ((long long)G.rn[0] * G.rn[1])};
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    // the point in evaluation voxel units: its cell (clamped to
+                    // the grid) and its position in that cell (FP64, once)
+                    const double ua = (G.ro[a] + (double)ix[a] * G.rh[a] - G.eo[a]) / G.eh[a];
+                    const double f = fmin(fmax(floor(ua), 0.0), (double)(G.en[a] - 2));
+                    V.c0[a][ld] = (int)f;
+                    V.fr[a][ld] = (float)(ua - f);
+                }
+                for (int a = N; a < 3; ++a) {
+                    V.c0[a][ld] = 0;
+                    V.fr[a][ld] = 0.f;
+                }
+                const float dr = __ldg(G.ref + v);
+                V.dr[ld] = dr;
+                V.inv[ld] = 1.0f / (G.dd_frac * (G.local ? dr : dnorm));
+                V.best[ws] = __float_as_uint(kInf);
+                V.vox[ws] = v;
+                atomicAnd(&W.fixm[ws >> 5], ~(1u << (ws & 31)));
+                V.t[ld] = 0;
+                sta = (sta & ~kGqWPend) | kGqWalk;
+            }
+        }
+        pend_n -= min((unsigned)__popc(need), pend_n);
+        if (leader) V.state[ld] = sta;
+        __syncwarp();
+        sta = V.state[ld];                 // the group's lanes follow their walker
+        if (queue_done && pend_n == 0 &&
+            !__any_sync(kFull, (sta & (kGqWalk | kGqEnded | kGqDBusy)) != 0))
+            break;
+
+        // 4. one table step of every walking group: entries t .. t + GL - 1
+        const bool walking = (sta & kGqWalk) != 0;
+        const int ws = ld + ((sta & kGqSlot) ? 32 : 0);
+        const int t0 = walking ? V.t[ld] : 0;
+        float key = kInf;
+        uint32_t off = 0;
+        if (walking && t0 + gl < G.ntable) {
+            const TableEntry e = G.table[t0 + gl];
+            key = e.key;
+            off = e.off;
+        }
+        const float k0 = __shfl_sync(kFull, key, ld);
+        bool cand = false, ended = false;
+        float q[8], cf[3] = {0.f, 0.f, 0.f};
+        uint32_t ok = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = 0.f;
+        if (walking) {
+            const float bst = __uint_as_float(V.best[ws]);
+            ended = t0 >= G.ntable || k0 * k0 >= bst;         // A1 step 4b-ii, exact
+            if (!ended && key * key < bst) {
+                const int d[3] = {unpack10(off, 0), unpack10(off, 10), N == 3 ? unpack10(off, 20) : 0};
+                int p[3];
+                bool in = true;
+                // the distance from the point to the cell's box: a lower bound
+                // in FP32 from the integer offset and the point's fraction,
+                // each axis lowered by its rounding and the sum by 1e-5
+                float k2 = 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    p[a] = V.c0[a][ld] + d[a];
+                    const float fr = V.fr[a][ld];
+                    cf[a] = (float)d[a] - fr;
+                    if (a < N) {
+                        in = in && p[a] >= 0 && p[a] < G.en[a];
+                        const float lo = (float)d[a] - fr, hi = fr - (float)(d[a] + 1);
+                        const float slack = 4.8e-7f * (fabsf(fr) + fabsf((float)d[a]) + 2.f);
+                        const float gap = fmaxf(fmaxf(lo, hi) - slack, 0.f) * ehf[a];
+                        k2 = fmaf(gap, gap, k2);
+                    }
+                }
+                k2 *= 0.99999f;
+                if (in && k2 < bst) {
+                    const long long sy = G.en[0], sz = (long long)G.en[0] * G.en[1];
+                    const long long pidx = (long long)p[2] * sz + (long long)p[1] * sy + p[0];
+                    const bool ex = p[0] + 1 < G.en[0], ey = p[1] + 1 < G.en[1], ez = N == 3 && p[2] + 1 < G.en[2];
+                    const float dr = V.dr[ld], inv = V.inv[ld];
+                    float qmin = kInf, qmax = -kInf;
+#pragma unroll
+                    for (int u = 0; u < (1 << N); ++u) {
+                        const bool present = (!(u & 1) || ex) && (!(u & 2) || ey) && (!(u & 4) || ez);
+                        if (present) {
+                            const long long o = pidx + ((u & 1) ? 1 : 0) + ((u & 2) ? sy : 0) + ((u & 4) ? sz : 0);
+                            q[u] = (__ldg(G.ev + o) - dr) * inv;
+                            qmin = fminf(qmin, q[u]);
+                            qmax = fmaxf(qmax, q[u]);
+                            ok |= 1u << u;
+                        }
+                    }
+                    const float gap = qmin > 0.f ? qmin : (qmax < 0.f ? -qmax : 0.f);
+                    const float kb = sqrtf(fmaxf(k2, key * key));
+                    cand = fmaf(gap, gap, kb * kb) < bst;
+                }
+            }
+        }
+        // 5. append the surviving cells to the ring
+        const unsigned cm = __ballot_sync(kFull, cand);
+        if (cand) {
+            const unsigned seq = head + count + (unsigned)__popc(cm & lt_mask);
+            const int slot = (int)(seq & (kGqRing - 1));
+#pragma unroll
+            for (int u = 0; u < (1 << N); ++u) V.q[u][slot] = q[u];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) V.cf[a][slot] = cf[a];
+            V.meta[slot] = (unsigned)ws | (ok << 8);
+        }
+        if (leader && walking) {
+            if (ended) {
+                sta = (sta & ~kGqWalk) | kGqEnded;
+            } else {
+                V.t[ld] = t0 + GL;
+                const unsigned gm = cm & gmask;
+                if (gm) {                   // the group's last appended cell
+                    const int hl = 31 - __clz(gm);
+                    V.wseq[ld] = head + count + (unsigned)__popc(cm & ((1u << hl) - 1u));
+                    sta |= kGqWPend;
+                }
+            }
+            V.state[ld] = sta;
+        }
+        count += (unsigned)__popc(cm);
+        const int nwalk = GL * __popc(__ballot_sync(kFull, leader && (sta & kGqWalk) && !ended));
+        __syncwarp();
+        // 6. evaluate the oldest 32 pending cells (or fewer, when few lanes walk)
+        if (count >= 32u || (count > 0u && nwalk < 16)) {
+            const unsigned n = min(count, 32u);
+            if ((unsigned)lane < n) {
+                const int slot = (int)((head + (unsigned)lane) & (kGqRing - 1));
+                const unsigned meta = V.meta[slot];
+                const int owner = (int)(meta & 63u);
+                const unsigned cok = meta >> 8;
+                float cq[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cq[u] = u < (1 << N) ? V.q[u][slot] : 0.f;
+                CellGeom<float> cg;
+                cell_geom<N, float>(V.cf[0][slot], V.cf[1][slot], N == 3 ? V.cf[2][slot] : 0.f, G.mt, cg);
+                bool ill = false;
+                const float dmax = G.tau > 0.f ? 0.99f * rsqrtf(G.tau) : kInf;
+                const float cb = cell_min_d2<N, float>(cq, cok, cg, G.mt, dmax, kInf, ill);
+                if (ill && cell_gram_ill<N>(cq, cok, G.mt.kappa, G.tau))
+                    atomicOr(&W.fixm[owner >> 5], 1u << (owner & 31));   // searched again
+                else
+                    atomicMin(&W.best[owner], __float_as_uint(cb + 0.f));   // -0 -> +0
+            }
+            head += n;
+            count -= n;
+        }
+        __syncwarp();
+    }
+    unsigned c0 = W.cnt[0][lane], c1 = W.cnt[1][lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_xor_sync(kFull, c0, o);
+        c1 += __shfl_xor_sync(kFull, c1, o);
+    }
+    if (lane == 0) {
+        if (c0) atomicAdd(&G.ctr->n_eval, (unsigned long long)c0);
+        if (c1) atomicAdd(&G.ctr->n_pass, (unsigned long long)c1);
+    }
+}
+
+// --------------------------------------------------------------------------
 // Host side
 // --------------------------------------------------------------------------
 
@@ -350,6 +630,16 @@ cudaError_t launch_grids(const GridProblem& G, cudaStream_t s)
     const long long nmax = std::max(G.nref, G.neval);
     const int gp = (int)std::max<long long>(1, std::min<long long>((nmax + 255) / 256, (long long)sms * 8));
     k_grid_prepare<<<gp, 256, 0, s>>>(G);
+    if (G.walk == 3 && G.walk_list) {
+        // the warp-evaluated walk, then a 32-lane search of the voxels it left
+        if (G.ndim == 3) k_grid_cq<3, 8><<<sms * 2, 256, 0, s>>>(G);
+        else k_grid_cq<2, 8><<<sms * 2, 256, 0, s>>>(G);
+        GridProblem F = G;
+        F.from_list = 1;
+        if (G.ndim == 3) launch_grid_walk_n<3>(F, 32, sms * 2, s);
+        else launch_grid_walk_n<2>(F, 32, sms * 2, s);
+        return cudaGetLastError();
+    }
     const int gl = G.lanes;
     const int gw = (int)std::max<long long>(1, std::min<long long>((G.nref * gl + 255) / 256,
                                                                    (long long)sms * 16));

@@ -332,6 +332,9 @@ struct GridProblem {
     float r_cover;
     Counters* ctr;
     int lanes;                   // lanes per reference voxel (2 .. 32)
+    int walk;                    // 3: the warp-evaluated walk (k_grid_cq), else k_grid_walk
+    unsigned* walk_list;         // voxels k_grid_cq leaves to k_grid_walk (nref entries)
+    int from_list;               // k_grid_walk: walk only walk_list[0 .. ctr->fix_count)
 };
 int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
                      std::vector<TableEntry>& table, double& r_cover);

@@ -62,8 +62,9 @@ def _volume_pair(seed, shape=(20, 24, 22)):
                               shift_mm=(0.5, -1.0, 1.5), scale=1.03)
 
 
+@pytest.mark.parametrize("walk", [0, 3], ids=["lane_walk", "warp_cells"])
 @pytest.mark.parametrize("local", [False, True])
-def test_volume_on_a_finer_shifted_grid(local):
+def test_volume_on_a_finer_shifted_grid(local, walk):
     # evaluation at 2.5 mm, reference resampled at 1.7 mm from another origin
     p = _volume_pair(31)
     ev = p.eval
@@ -76,12 +77,13 @@ def test_volume_on_a_finer_shifted_grid(local):
                                for n, h, o, s in zip(rshape, rsp, ro, ev.shape)], indexing="ij")
     ref = (p.ref[zz, yy, xx] * (1 + rng.normal(0, 0.01, rshape))).astype(np.float32)
     crit = synth.Criteria(0.02, 2.0, local=local)
-    got, counts, _ = gpu_grids(ref, rsp, ro, ev, esp, eo, crit)
+    got, counts, _ = gpu_grids(ref, rsp, ro, ev, esp, eo, crit, {"walk": walk})
     want = oracle_grids(ref, rsp, ro, ev, esp, eo, crit)
     check(got, want, counts)
 
 
-def test_plane_reaching_outside_the_evaluation_grid():
+@pytest.mark.parametrize("walk", [0, 3], ids=["lane_walk", "warp_cells"])
+def test_plane_reaching_outside_the_evaluation_grid(walk):
     rng = np.random.default_rng(7)
     p = synth.make_pair_2d(shape=(48, 52), spacing=(1.0, 1.0), seed=7, shift_mm=(0.6, -0.4))
     ev = p.eval
@@ -91,12 +93,13 @@ def test_plane_reaching_outside_the_evaluation_grid():
                            for n, h, o, s in zip(rshape, rsp, ro, ev.shape)], indexing="ij")
     ref = (p.ref[yy, xx] * (1 + rng.normal(0, 0.01, rshape))).astype(np.float32)
     crit = synth.Criteria(0.03, 3.0)
-    got, counts, _ = gpu_grids(ref, rsp, ro, ev, esp, eo, crit)
+    got, counts, _ = gpu_grids(ref, rsp, ro, ev, esp, eo, crit, {"walk": walk})
     want = oracle_grids(ref, rsp, ro, ev, esp, eo, crit)
     check(got, want, counts)
 
 
-def test_truncated_table_box_scan():
+@pytest.mark.parametrize("walk", [0, 3], ids=["lane_walk", "warp_cells"])
+def test_truncated_table_box_scan(walk):
     p = _volume_pair(33, shape=(12, 14, 13))
     ev = p.eval
     rshape, rsp, ro = (10, 12, 11), (2.9, 2.8, 3.1), (0.4, -0.3, 0.9)
@@ -104,7 +107,7 @@ def test_truncated_table_box_scan():
     ref = (rng.uniform(0.2, 1.0, rshape) * float(ev.max())).astype(np.float32)
     crit = synth.Criteria(0.01, 1.0, local=True)
     got, counts, st = gpu_grids(ref, rsp, ro, ev, (2.5, 2.5, 2.5), (0.0, 0.0, 0.0), crit,
-                                {"table_cap": 32})
+                                {"table_cap": 32, "walk": walk})
     assert st["overflow_voxels"] > 0
     want = oracle_grids(ref, rsp, ro, ev, (2.5, 2.5, 2.5), (0.0, 0.0, 0.0), crit)
     check(got, want, counts)
@@ -124,3 +127,25 @@ def test_identical_geometry_is_the_coincident_search():
     got2, counts2, _ = gpu_grids(p.ref, sp, o, p.eval, sp, o2, crit)
     want2 = oracle_grids(p.ref, sp, o, p.eval, sp, o2, crit)
     check(got2, want2, counts2)
+
+
+@pytest.mark.parametrize("fp64_all", [False, True], ids=["fp32", "fp64_every_cell"])
+def test_warp_evaluated_grid_walk_is_bitwise_the_lane_walk(fp64_all):
+    # walk = 3 evaluates each cell with the lane walk's arithmetic (with the
+    # FP64 redo forced on every cell, every voxel goes to the 32-lane re-search)
+    p = _volume_pair(35, shape=(24, 26, 28))
+    ev = p.eval
+    rshape, rsp, ro = (30, 34, 36), (1.9, 1.8, 1.7), (0.35, 0.6, -0.2)
+    rng = np.random.default_rng(11)
+    zz, yy, xx = np.meshgrid(*[np.clip(np.rint((o + np.arange(n) * h) / 2.5).astype(int), 0, s - 1)
+                               for n, h, o, s in zip(rshape, rsp, ro, ev.shape)], indexing="ij")
+    ref = (p.ref[zz, yy, xx] * (1 + rng.normal(0, 0.01, rshape))).astype(np.float32)
+    crit = synth.Criteria(0.02, 2.0)
+    extra = {"fp64_tau_exp10": 1} if fp64_all else {}
+    a, ca, sa = gpu_grids(ref, rsp, ro, ev, (2.5, 2.5, 2.5), (0.0, 0.0, 0.0), crit,
+                          {"walk": 0, "lanes_per_voxel": 8, **extra})
+    b, cb, sb = gpu_grids(ref, rsp, ro, ev, (2.5, 2.5, 2.5), (0.0, 0.0, 0.0), crit, {"walk": 3, **extra})
+    np.testing.assert_array_equal(a, b)
+    assert ca == cb
+    if fp64_all:
+        assert sb["fp64_cells"] > 0
