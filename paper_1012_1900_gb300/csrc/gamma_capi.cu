@@ -704,6 +704,45 @@ int gamma_create(gamma_handle* out, const float* ref_dev, const float* eval_dev,
     return GAMMA_OK;
 }
 
+// The nine cell tables of a two-grid handle (variants of gk::build_grid_table,
+// each capped at `cap` entries), concatenated in one device array.
+static int upload_grid_tables(gamma_ctx* h, long long cap)
+{
+    gk::GridProblem& G = h->grids->G;
+    const double hn[3] = {G.eh[0], G.eh[1], G.eh[2]};
+    std::vector<TableEntry> all, table;
+    int off[9], len[9];
+    float cov[9];
+    for (int k = 0; k < 9; ++k) {
+        double cover = 0;
+        table.clear();
+        if (int rc = gk::build_grid_table(G.ndim, hn, G.en, cap, k, table, cover)) return rc;
+        off[k] = (int)all.size();
+        len[k] = (int)table.size();
+        cov[k] = std::isinf(cover) ? INFINITY : round_down(cover);
+        all.insert(all.end(), table.begin(), table.end());
+    }
+    if (all.size() > (size_t)0x7fffffff) return GAMMA_ERR_TABLE_TOO_LARGE;
+    TableEntry* dev = nullptr;
+    CK(cudaMalloc(&dev, sizeof(TableEntry) * std::max<size_t>(all.size(), 1)));
+    if (!all.empty()) {
+        const cudaError_t e = cudaMemcpy(dev, all.data(), sizeof(TableEntry) * all.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(dev);
+            return cuda_fail(e);
+        }
+    }
+    cudaFree(h->grids->table_dev);
+    h->grids->table_dev = dev;
+    G.table = dev;
+    for (int k = 0; k < 9; ++k) {
+        G.toff[k] = off[k];
+        G.tlen[k] = len[k];
+        G.tcover[k] = cov[k];
+    }
+    return GAMMA_OK;
+}
+
 int gamma_create_grids(gamma_handle* out, const float* ref_dev, const float* eval_dev, int ndim,
                        const int64_t ref_shape[3], const float ref_spacing_mm[3],
                        const float ref_origin_mm[3], const int64_t eval_shape[3],
@@ -782,21 +821,8 @@ int gamma_create_grids(gamma_handle* out, const float* ref_dev, const float* eva
     G.cutoff_frac = crit->cutoff_frac;
     G.dose_norm = crit->dose_norm;
     G.local = crit->mode == GAMMA_LOCAL;
-    std::vector<TableEntry> table;
-    double cover = 0;
-    const double hn[3] = {G.eh[0], G.eh[1], G.eh[2]};
-    if (int rc = gk::build_grid_table(ndim, hn, G.en, h->table_cap, table, cover)) return fail(rc);
+    if (int rc = upload_grid_tables(h, h->table_cap)) return fail(rc);
     cudaError_t e;
-    if ((e = cudaMalloc(&h->grids->table_dev, sizeof(TableEntry) * std::max<size_t>(table.size(), 1))) !=
-        cudaSuccess)
-        return fail(cuda_fail(e));
-    if (!table.empty() &&
-        (e = cudaMemcpy(h->grids->table_dev, table.data(), sizeof(TableEntry) * table.size(),
-                        cudaMemcpyHostToDevice)) != cudaSuccess)
-        return fail(cuda_fail(e));
-    G.table = h->grids->table_dev;
-    G.ntable = (int)table.size();
-    G.r_cover = std::isinf(cover) ? INFINITY : round_down(cover);
     if ((e = cudaMalloc(&h->grids->walk_list, sizeof(unsigned) * (size_t)nref)) != cudaSuccess)
         return fail(cuda_fail(e));
     for (auto& te : h->tev)
@@ -1229,20 +1255,7 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         DeviceGuard dg(h->device);
         if (!dg.ok) return GAMMA_ERR_CUDA;
         if (h->ran) { CK(cudaStreamSynchronize(h->last_stream)); }
-        gk::GridProblem& G = h->grids->G;
-        std::vector<TableEntry> table;
-        double cover = 0;
-        const double hn[3] = {G.eh[0], G.eh[1], G.eh[2]};
-        if (int rc = gk::build_grid_table(G.ndim, hn, G.en, value, table, cover)) return rc;
-        cudaFree(h->grids->table_dev);
-        h->grids->table_dev = nullptr;
-        CK(cudaMalloc(&h->grids->table_dev, sizeof(TableEntry) * std::max<size_t>(table.size(), 1)));
-        if (!table.empty())
-            CK(cudaMemcpy(h->grids->table_dev, table.data(), sizeof(TableEntry) * table.size(),
-                          cudaMemcpyHostToDevice));
-        G.table = h->grids->table_dev;
-        G.ntable = (int)table.size();
-        G.r_cover = std::isinf(cover) ? INFINITY : round_down(cover);
+        if (int rc = upload_grid_tables(h, value)) return rc;
         h->table_cap = value;
         return GAMMA_OK;
     }

@@ -35,6 +35,30 @@
 
 namespace gk {
 
+// Table key of cell offset c along one axis, in cells: the smallest distance
+// from a point in its own cell to cell c.  Variant 8 holds for any point of
+// the cell (and, per axis, for a point outside the grid, from its clamped
+// cell); variants 0-7 for a point in one half of its cell per axis (bit a of
+// the variant: the upper half [0.5, 1) of axis a, else the lower [0, 0.5)).
+__host__ __device__ inline double grid_axis_key(int c, int variant, int a)
+{
+    if (variant == 8 || c == 0) return c == 0 ? 0.0 : (double)(c > 0 ? c - 1 : -c - 1);
+    const bool upper = (variant >> a) & 1;
+    return c > 0 ? (double)(c - 1) + (upper ? 0.0 : 0.5) : (double)(-c - 1) + (upper ? 0.5 : 0.0);
+}
+
+// The table variant for a point at fraction fr of its cell (0-7: its half of
+// the cell per axis; 8: outside [0, 1) on some axis, beyond the grid).
+__device__ __forceinline__ int grid_variant(const float (&fr)[3], int nd)
+{
+    int v = 0;
+    for (int a = 0; a < nd; ++a) {
+        if (!(fr[a] >= 0.f && fr[a] < 1.f)) return 8;
+        if (fr[a] >= 0.5f) v |= 1 << a;
+    }
+    return v;
+}
+
 // --------------------------------------------------------------------------
 // Prepare: dose norm over the reference grid, finite checks
 // --------------------------------------------------------------------------
@@ -130,7 +154,6 @@ __global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ Gr
     const unsigned gmask = GL == 32 ? kFull : (((1u << GL) - 1u) << gbase);
     const float dnorm = G.dose_norm > 0.f ? G.dose_norm : fdec(G.ctr->dnorm_enc);
     const float thr = G.cutoff_frac * dnorm;
-    const float rc2 = G.r_cover * G.r_cover;
     unsigned my_eval = 0, my_pass = 0, my_over = 0;
     const long long ngroups = ((long long)gridDim.x * blockDim.x) / GL;
     // every reference voxel, or (from_list) those k_grid_cq left in walk_list
@@ -164,14 +187,19 @@ __global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ Gr
         }
         const float dD = G.dd_frac * (G.local ? dr : dnorm);
         const float inv = 1.0f / dD;
+        // the table for the point's half of its cell per axis
+        const int var = grid_variant(fr, N);
+        const TableEntry* table = G.table + G.toff[var];
+        const int ntable = G.tlen[var];
+        const float rc2 = G.tcover[var] * G.tcover[var];
         float best = kInf;
         int t = 0;
-        while (t < G.ntable) {
+        while (t < ntable) {
             const int idx = t + gl;
             float key = kInf;
             uint32_t off = 0;
-            if (idx < G.ntable) {
-                const TableEntry e = G.table[idx];
+            if (idx < ntable) {
+                const TableEntry e = table[idx];
                 key = e.key;
                 off = e.off;
             }
@@ -206,7 +234,7 @@ __global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ Gr
             best = cb;
             t += GL;
         }
-        if (t >= G.ntable && best > rc2) {
+        if (t >= ntable && best > rc2) {
             // past a truncated table: every remaining cell of the search box
             if (gl == 0) ++my_over;
             const float gm = sqrtf(best);
@@ -230,7 +258,7 @@ __global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ Gr
 #pragma unroll
                 for (int a = 0; a < N; ++a) {
                     in = in && p[a] >= 0 && p[a] < G.en[a];
-                    const float gap = (float)max(abs(d[a]) - 1, 0) * (float)G.eh[a];
+                    const float gap = (float)grid_axis_key(d[a], var, a) * (float)G.eh[a];
                     k2 = fmaf(gap, gap, k2);
                 }
                 if (!in || k2 < cut || k2 >= lb) continue;
@@ -295,6 +323,7 @@ struct GqWarp {
     unsigned fixm[2];          // slots whose voxel is searched again by k_grid_walk
     unsigned cnt[2][32];       // voxels finished and passed
     unsigned pend[64];         // evaluated reference voxels not yet taken by a walker
+    int tv[64];                // table variant of each slot's voxel
 };
 constexpr unsigned kGqWalk = 1u, kGqEnded = 2u, kGqWPend = 4u, kGqDBusy = 8u, kGqDPend = 16u,
                    kGqDOver = 32u, kGqSlot = 64u;     // slot bit: the walking slot is walker + 32
@@ -311,11 +340,11 @@ __global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ Grid
     const unsigned gmask = GL == 32 ? kFull : ((1u << GL) - 1u) << ld;
     const float dnorm = G.dose_norm > 0.f ? G.dose_norm : fdec(G.ctr->dnorm_enc);
     const float thr = G.cutoff_frac * dnorm;
-    const float rc2 = G.r_cover * G.r_cover;
     const float ehf[3] = {(float)G.eh[0], (float)G.eh[1], (float)G.eh[2]};
     W.state[lane] = 0;
     W.wseq[lane] = W.dseq[lane] = 0;
     W.cnt[0][lane] = W.cnt[1][lane] = 0;
+    W.tv[lane] = W.tv[lane + 32] = 8;
     if (lane < 2) W.fixm[lane] = 0;
     __syncwarp();
 
@@ -330,7 +359,8 @@ __global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ Grid
                 const int ds = ld + ((sta & kGqSlot) ? 0 : 32);
                 const float best = __uint_as_float(V.best[ds]);
                 const unsigned v = V.vox[ds];
-                if (((V.fixm[ds >> 5] >> (ds & 31)) & 1u) || ((sta & kGqDOver) && best > rc2)) {
+                const float rc = G.tcover[V.tv[ds]];
+                if (((V.fixm[ds >> 5] >> (ds & 31)) & 1u) || ((sta & kGqDOver) && best > rc * rc)) {
                     G.walk_list[atomicAdd(&G.ctr->fix_count, 1u)] = v;   // k_grid_walk finishes it
                 } else {
                     const float gam = sqrtf(best);
@@ -344,7 +374,7 @@ __global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ Grid
             if ((sta & kGqEnded) && !(sta & kGqDBusy)) {
                 unsigned d = kGqDBusy;
                 if (sta & kGqWPend) d |= kGqDPend;
-                if (V.t[ld] >= G.ntable) d |= kGqDOver;
+                if (V.t[ld] >= G.tlen[V.tv[ld + ((sta & kGqSlot) ? 32 : 0)]]) d |= kGqDOver;
                 V.dseq[ld] = V.wseq[ld];
                 sta = d | ((sta & kGqSlot) ^ kGqSlot);
             }
@@ -389,6 +419,11 @@ __global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ Grid
                     V.c0[a][ld] = 0;
                     V.fr[a][ld] = 0.f;
                 }
+                {
+                    float frr[3];
+                    for (int a = 0; a < 3; ++a) frr[a] = V.fr[a][ld];
+                    V.tv[ws] = grid_variant(frr, N);
+                }
                 const float dr = __ldg(G.ref + v);
                 V.dr[ld] = dr;
                 V.inv[ld] = 1.0f / (G.dd_frac * (G.local ? dr : dnorm));
@@ -413,8 +448,10 @@ __global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ Grid
         const int t0 = walking ? V.t[ld] : 0;
         float key = kInf;
         uint32_t off = 0;
-        if (walking && t0 + gl < G.ntable) {
-            const TableEntry e = G.table[t0 + gl];
+        const int var = V.tv[ws];
+        const int ntable = G.tlen[var];
+        if (walking && t0 + gl < ntable) {
+            const TableEntry e = G.table[G.toff[var] + t0 + gl];
             key = e.key;
             off = e.off;
         }
@@ -426,7 +463,7 @@ __global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ Grid
         for (int u = 0; u < 8; ++u) q[u] = 0.f;
         if (walking) {
             const float bst = __uint_as_float(V.best[ws]);
-            ended = t0 >= G.ntable || k0 * k0 >= bst;         // A1 step 4b-ii, exact
+            ended = t0 >= ntable || k0 * k0 >= bst;           // A1 step 4b-ii, exact
             if (!ended && key * key < bst) {
                 const int d[3] = {unpack10(off, 0), unpack10(off, 10), N == 3 ? unpack10(off, 20) : 0};
                 int p[3];
@@ -542,7 +579,7 @@ __global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ Grid
 // Host side
 // --------------------------------------------------------------------------
 
-int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
+int build_grid_table(int nd, const double hn[3], const int en[3], long long cap, int variant,
                      std::vector<TableEntry>& table, double& r_cover)
 {
     // radius from a ball-volume estimate of about 2 * cap cells
@@ -571,7 +608,7 @@ int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
                     const int c[3] = {x, y, z};
                     double k2 = 0;
                     for (int a = 0; a < nd; ++a) {
-                        const double gap = std::max(std::abs(c[a]) - 1, 0) * hn[a];
+                        const double gap = grid_axis_key(c[a], variant, a) * hn[a];
                         k2 += gap * gap;
                     }
                     const double key = std::sqrt(k2);

@@ -327,16 +327,21 @@ struct GridProblem {
     float dd_frac, cutoff_frac, dose_norm;
     int local;
     float tau;
-    const TableEntry* table;     // keyed by the gap between cell boxes
-    int ntable;
-    float r_cover;
+    // nine cell tables, concatenated: variant 8 keyed by the gap between cell
+    // boxes (any point of the voxel's cell, or a point outside the grid),
+    // variants 0-7 by the smallest distance from a point in one half of its
+    // cell per axis (bit a: the upper half of axis a); entries toff[k] ..
+    // toff[k] + tlen[k] - 1, every cell with key < tcover[k] included
+    const TableEntry* table;
+    int toff[9], tlen[9];
+    float tcover[9];
     Counters* ctr;
     int lanes;                   // lanes per reference voxel (2 .. 32)
     int walk;                    // 3: the warp-evaluated walk (k_grid_cq), else k_grid_walk
     unsigned* walk_list;         // voxels k_grid_cq leaves to k_grid_walk (nref entries)
     int from_list;               // k_grid_walk: walk only walk_list[0 .. ctr->fix_count)
 };
-int build_grid_table(int nd, const double hn[3], const int en[3], long long cap,
+int build_grid_table(int nd, const double hn[3], const int en[3], long long cap, int variant,
                      std::vector<TableEntry>& table, double& r_cover);
 cudaError_t launch_grids(const GridProblem& G, cudaStream_t s);
 
