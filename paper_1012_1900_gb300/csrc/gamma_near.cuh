@@ -179,13 +179,15 @@ __device__ __forceinline__ float near_faces(std::integer_sequence<int, Es...>,
 {
     float t[NearTable<N>::NE], nu[NearTable<N>::NE];
     const float D0 = dD * dD;
-    float Dmax = D0;
+    // four running maxima (face F feeds Dm[F % 4]): the maximum does not
+    // depend on the order, and four short chains replace one long one
+    float Dm[4] = {D0, D0, D0, D0};
     (near_edge<N, Es, true>(e, g, kappa, t, nu), ...);
-    (near_face<N, Fs, 0>(t, nu, D0, Dmax), ...);
+    (near_face<N, Fs, 0>(t, nu, D0, Dm[Fs & 3]), ...);
     (near_edge<N, Es, false>(e, g, kappa, t, nu), ...);
-    (near_face<N, Fs, 1>(t, nu, D0, Dmax), ...);
-    (near_face<N, Fs, 2>(t, nu, D0, Dmax), ...);
-    return (g * g) / Dmax;
+    (near_face<N, Fs, 1>(t, nu, D0, Dm[Fs & 3]), ...);
+    (near_face<N, Fs, 2>(t, nu, D0, Dm[Fs & 3]), ...);
+    return (g * g) / fmaxf(fmaxf(Dm[0], Dm[1]), fmaxf(Dm[2], Dm[3]));
 }
 
 // Squared gamma over the faces through voxel v (node tix of a staged tile
