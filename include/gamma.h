@@ -54,7 +54,8 @@ typedef enum {
     GAMMA_ERR_NOT_RUN = -8,         /* results requested before any run */
     GAMMA_ERR_MODEL = -9,           /* model file missing, malformed or of the wrong shape */
     GAMMA_ERR_QUEUE_FULL = -10,     /* internal work queue overflowed (results incomplete) */
-    GAMMA_ERR_TOO_LARGE = -11       /* grid larger than gamma_run_noalloc's fixed scratch */
+    GAMMA_ERR_TOO_LARGE = -11,      /* grid larger than gamma_run_noalloc's fixed scratch */
+    GAMMA_ERR_DOSE_NORM = -12       /* global criteria without a positive dose norm (see below) */
 } gamma_status;
 
 typedef enum { GAMMA_GLOBAL = 0, GAMMA_LOCAL = 1 } gamma_mode;
@@ -68,7 +69,10 @@ typedef enum { GAMMA_GLOBAL = 0, GAMMA_LOCAL = 1 } gamma_mode;
  *              D_norm (and, in local mode, D_r(v) > 0); the comparison is
  *              taken in float32.  Others get NaN and are not counted.
  *  dose_norm   D_norm; <= 0 means the maximum of the reference dose,
- *              computed on the device at every run. */
+ *              computed on the device at every run.  Global criteria need
+ *              D_norm > 0: a run whose reference has no positive dose (and
+ *              no dose_norm given) evaluates no voxel (every gamma NaN) and
+ *              its pass rate reports GAMMA_ERR_DOSE_NORM. */
 typedef struct {
     float dd_frac;
     float dta_mm;
@@ -188,7 +192,9 @@ int gamma_run_host(gamma_handle h, const float *ref_host, const float *eval_host
 /* Pass rate of the last run: rate = n_pass / n_eval (0 when n_eval = 0),
  * pass iff gamma <= 1.  Synchronises the last run's stream.  Any output
  * pointer may be NULL.  Errors: NOT_RUN, NAN_INPUT (the last run saw a
- * non-finite dose; its results are meaningless), QUEUE_FULL, CUDA. */
+ * non-finite dose; its results are meaningless), QUEUE_FULL, DOSE_NORM
+ * (global criteria, no positive dose norm: no voxel evaluated; on a batch
+ * handle, any pair), CUDA. */
 int gamma_pass_rate(gamma_handle h, double *rate, int64_t *n_eval, int64_t *n_pass);
 
 /* Counters of the last run (synchronises its stream).  Errors: NOT_RUN, CUDA. */
@@ -312,7 +318,7 @@ int gamma_batch_run(gamma_handle h, void *cuda_stream);
 
 /* Pass rate and counts of one pair of the last batched run (synchronises).
  * Errors: INVALID_ARG (pair out of range or not a batch), NOT_RUN, NAN_INPUT,
- * QUEUE_FULL, CUDA. */
+ * QUEUE_FULL, DOSE_NORM, CUDA. */
 int gamma_batch_pass_rate(gamma_handle h, int pair, double *rate, int64_t *n_eval,
                           int64_t *n_pass);
 
@@ -442,8 +448,8 @@ const char *gamma_version(void);
  * it returns.  Voxels whose search runs past the GAMMA_NOALLOC_MAX_TABLE-entry
  * table finish with the exact box scan.  The launch shapes are the defaults
  * of a new handle.
- * Errors: INVALID_ARG, SHAPE, TOO_LARGE, NAN_INPUT (only when counts are
- * requested), CUDA. */
+ * Errors: INVALID_ARG, SHAPE, TOO_LARGE, NAN_INPUT and DOSE_NORM (only when
+ * counts are requested), CUDA. */
 #define GAMMA_NOALLOC_MAX_VOXELS 4194304
 #define GAMMA_NOALLOC_MAX_TABLE 32768
 int gamma_run_noalloc(const float *ref_dev, const float *eval_dev, float *gamma_out_dev, int ndim,

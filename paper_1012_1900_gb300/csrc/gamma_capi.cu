@@ -1173,6 +1173,13 @@ static int read_counters(gamma_handle h, Counters* c, int pair = -1)
     return GAMMA_OK;
 }
 
+// Global criteria whose run found no positive dose norm (no norm given and
+// no positive reference dose) evaluated no voxel (the kernels' cutoff).
+static bool missing_norm(const gamma_criteria& crit, const Counters& c)
+{
+    return crit.mode == GAMMA_GLOBAL && !(crit.dose_norm > 0.f) && !(gk::fdec(c.dnorm_enc) > 0.f);
+}
+
 int gamma_pass_rate(gamma_handle h, double* rate, int64_t* n_eval, int64_t* n_pass)
 {
     if (!h) return GAMMA_ERR_INVALID_ARG;
@@ -1181,6 +1188,12 @@ int gamma_pass_rate(gamma_handle h, double* rate, int64_t* n_eval, int64_t* n_pa
     if (c.flags & gk::kFlagNonFinite) return GAMMA_ERR_NAN_INPUT;
     if (c.flags & gk::kFlagTimeout) return GAMMA_ERR_TIMEOUT;
     if (c.flags & gk::kFlagTailFull) return GAMMA_ERR_QUEUE_FULL;
+    if (!h->batch && missing_norm(h->crit, c)) return GAMMA_ERR_DOSE_NORM;
+    for (int k = 0; h->batch && k < h->batch->n; ++k) {
+        Counters ck;
+        if (int rc = read_counters(h, &ck, k)) return rc;
+        if (missing_norm(h->batch->pairs[k]->crit, ck)) return GAMMA_ERR_DOSE_NORM;
+    }
     if (n_eval) *n_eval = (int64_t)c.n_eval;
     if (n_pass) *n_pass = (int64_t)c.n_pass;
     if (rate) *rate = c.n_eval ? (double)c.n_pass / (double)c.n_eval : 0.0;
@@ -1478,6 +1491,7 @@ int gamma_batch_pass_rate(gamma_handle h, int pair, double* rate, int64_t* n_eva
     if (c.flags & gk::kFlagNonFinite) return GAMMA_ERR_NAN_INPUT;
     if (c.flags & gk::kFlagTimeout) return GAMMA_ERR_TIMEOUT;
     if (c.flags & gk::kFlagTailFull) return GAMMA_ERR_QUEUE_FULL;
+    if (missing_norm(h->batch->pairs[pair]->crit, c)) return GAMMA_ERR_DOSE_NORM;
     if (n_eval) *n_eval = (int64_t)c.n_eval;
     if (n_pass) *n_pass = (int64_t)c.n_pass;
     if (rate) *rate = c.n_eval ? (double)c.n_pass / (double)c.n_eval : 0.0;
@@ -1668,6 +1682,7 @@ const char* gamma_strerror(int code)
     case GAMMA_ERR_MODEL: return "bad model";
     case GAMMA_ERR_QUEUE_FULL: return "work queue overflow";
     case GAMMA_ERR_TOO_LARGE: return "grid exceeds the fixed scratch of gamma_run_noalloc";
+    case GAMMA_ERR_DOSE_NORM: return "global criteria need a positive dose norm: the reference has no positive dose";
     default: return "unknown error";
     }
 }

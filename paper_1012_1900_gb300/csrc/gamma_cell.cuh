@@ -23,6 +23,17 @@ __device__ __forceinline__ float ill_dmax(const Problem& P)
     return P.tau > 0.f ? 0.99f * rsqrtf(P.tau) : kInf;
 }
 
+// The cutoff below which a reference voxel is not evaluated: cutoff_frac *
+// D_norm.  Global criteria need a positive dose norm (their Delta D is
+// dd_frac * D_norm); without one (a reference with no positive dose and no
+// norm given) no voxel is evaluated: the threshold is +inf, every voxel gets
+// NaN and the run reports GAMMA_ERR_DOSE_NORM, instead of searching with a
+// zero Delta D, whose infinite gamma would walk the whole grid per voxel.
+__host__ __device__ __forceinline__ float cutoff_threshold(int local, float cutoff_frac, float dnorm)
+{
+    return (local || dnorm > 0.f) ? cutoff_frac * dnorm : kInf;
+}
+
 __device__ __forceinline__ bool is_evaluated(const Problem& P, float dr, float thr)
 {
     return dr >= thr && (!P.local || dr > 0.f);

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256, 2) k_grid_walk(const __grid_constant__ Gr
     const int lane = threadIdx.x & 31, gl = lane & (GL - 1), gbase = lane & ~(GL - 1);
     const unsigned gmask = GL == 32 ? kFull : (((1u << GL) - 1u) << gbase);
     const float dnorm = G.dose_norm > 0.f ? G.dose_norm : fdec(G.ctr->dnorm_enc);
-    const float thr = G.cutoff_frac * dnorm;
+    const float thr = cutoff_threshold(G.local, G.cutoff_frac, dnorm);
     unsigned my_eval = 0, my_pass = 0, my_over = 0;
     const long long ngroups = ((long long)gridDim.x * blockDim.x) / GL;
     // every reference voxel, or (from_list) those k_grid_cq left in walk_list
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256, 2) k_grid_cq(const __grid_constant__ Grid
     const unsigned lt_mask = (1u << lane) - 1u;
     const unsigned gmask = GL == 32 ? kFull : ((1u << GL) - 1u) << ld;
     const float dnorm = G.dose_norm > 0.f ? G.dose_norm : fdec(G.ctr->dnorm_enc);
-    const float thr = G.cutoff_frac * dnorm;
+    const float thr = cutoff_threshold(G.local, G.cutoff_frac, dnorm);
     const float ehf[3] = {(float)G.eh[0], (float)G.eh[1], (float)G.eh[2]};
     W.state[lane] = 0;
     W.wseq[lane] = W.dseq[lane] = 0;

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256, MINB)
         const Problem& P = BATCH ? sh_P : P0;
         const bool use_tma = pair_tma(pr) != 0;
         const float dnorm = resolve_dnorm(P);
-        const float thr = P.cutoff_frac * dnorm;
+        const float thr = cutoff_threshold(P.local, P.cutoff_frac, dnorm);
         // every face not through the voxel is at spatial distance >= the
         // first table key, or >= the cover radius when the table was cut
         const float k0 = P.ntable > 0 ? P.table[0].key : kInf;
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(256, MINB)
     float dnorm = 0.f, thr = 0.f, qlim = 0.f;
     auto constants = [&](const Problem& Q) {
         dnorm = resolve_dnorm(Q);
-        thr = Q.cutoff_frac * dnorm;
+        thr = cutoff_threshold(Q.local, Q.cutoff_frac, dnorm);
         const float k0 = Q.ntable > 0 ? Q.table[0].key : kInf;
         qlim = fminf(k0 * k0, Q.r_cover * Q.r_cover);
     };

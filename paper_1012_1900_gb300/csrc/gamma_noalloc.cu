@@ -271,6 +271,8 @@ extern "C" int gamma_run_noalloc(const float* ref_dev, const float* eval_dev, fl
             cudaStreamSynchronize(s) != cudaSuccess)
             return GAMMA_ERR_CUDA;
         if (c.flags & gk::kFlagNonFinite) return GAMMA_ERR_NAN_INPUT;
+        if (crit->mode == GAMMA_GLOBAL && !(crit->dose_norm > 0.f) && !(gk::fdec(c.dnorm_enc) > 0.f))
+            return GAMMA_ERR_DOSE_NORM;            // no voxel was evaluated
         if (n_eval) *n_eval = (int64_t)c.n_eval;
         if (n_pass) *n_pass = (int64_t)c.n_pass;
     }

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_paper_dd(const __grid_constant__ Proble
                                                   unsigned* __restrict__ ids)
 {
     const float dnorm = resolve_dnorm(P);
-    const float thr = P.cutoff_frac * dnorm;
+    const float thr = cutoff_threshold(P.local, P.cutoff_frac, dnorm);
     float my_rmax = 0.f;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < P.nvox; v += stride) {
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) k_paper_walk(const __grid_constant__ Prob
                                                     const unsigned* __restrict__ ids)
 {
     const float dnorm = resolve_dnorm(P);
-    const float thr = P.cutoff_frac * dnorm;
+    const float thr = cutoff_threshold(P.local, P.cutoff_frac, dnorm);
     const float rc2 = P.r_cover * P.r_cover;
     unsigned my_eval = 0, my_pass = 0, my_over = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;

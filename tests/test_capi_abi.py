@@ -50,6 +50,7 @@ def test_strerror_and_version_without_gpu(lib):
     lib.gamma_version.restype = ctypes.c_char_p
     assert lib.gamma_strerror(0) == b"ok"
     assert lib.gamma_strerror(-2) == b"invalid shape"
+    assert b"dose norm" in lib.gamma_strerror(-12)
     assert b"sm_103a" in lib.gamma_version()
 
 
