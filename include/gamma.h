@@ -252,9 +252,10 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *                     whole dose); 0 runs in order
  *  "graph"            0 launches directly instead of capturing and replaying
  *                     a CUDA graph (default 1).  Batch handles capture at
- *                     their first run; single-pair handles once gamma_run has
- *                     run twice on the same output with no option or input
- *                     change between (not with "timing", a model or "design")
+ *                     their first run (not with "timing"); single-pair
+ *                     handles once gamma_run has run twice on the same
+ *                     output with no option or input change between (not
+ *                     with "timing", a model or "design")
  *  "shell_blocks_per_sm"  1 to 4: resident blocks per SM the key-0 cell
  *                     kernel's register budget is sized for (default 2)
  *  "tail_blocks_per_sm"   1 to 4: the same for the table-walk kernels

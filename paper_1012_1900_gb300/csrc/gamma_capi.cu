@@ -24,6 +24,10 @@ thread_local std::string g_last_cuda;
 int cuda_fail(cudaError_t e)
 {
     g_last_cuda = cudaGetErrorString(e);
+    // the runtime also keeps a failed call's error as its last error; clear
+    // it (a sticky error stays), so that the launch checks of the next call
+    // do not report it again
+    cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? GAMMA_ERR_OOM : GAMMA_ERR_CUDA;
 }
 
@@ -1459,7 +1463,7 @@ int gamma_batch_run(gamma_handle h, void* cuda_stream)
         if (int rc = batch_upload(h)) return rc;
         b->dirty = false;
     }
-    if (h->graph) {
+    if (h->graph && !h->timing) {            // phase events are recorded by direct launches
         if (!b->exec) {
             CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
             const int rc = batch_enqueue(h, b->cap);

@@ -151,3 +151,39 @@ def test_non_finite_input_reported_per_pair(which):
                 g.gamma_batch_pass_rate(h, i)
     finally:
         g.gamma_destroy(h)
+
+
+def test_batch_phase_timings_then_graph_runs():
+    # "timing" runs a batch by direct launches (its phase events cannot time
+    # a replayed graph); switching it off again returns to the captured graph,
+    # and every run gives the same maps
+    import paper_1012_1900_gb300 as g
+    ps = _pairs()
+    base, _ = _batch_run(ps)
+    refs, evs, outs, descs = [], [], [], []
+    for p in ps:
+        r = torch.from_numpy(p.ref).cuda()
+        e = torch.from_numpy(p.eval).cuda()
+        o = torch.full_like(r, -7.0)
+        refs.append(r)
+        evs.append(e)
+        outs.append(o)
+        nd = p.ref.ndim
+        c = p.criteria
+        descs.append((r, e, o, nd, p.ref.shape if nd == 3 else (1,) + p.ref.shape,
+                      p.spacing if nd == 3 else (1.0,) + p.spacing,
+                      g.criteria(c.dd_frac, c.dta_mm, c.local, c.cutoff_frac, c.dose_norm)))
+    h = g.gamma_batch_create(descs)
+    try:
+        for timing in (0, 1, 1, 0, 0):
+            g.gamma_set_option(h, "timing", timing)
+            g.gamma_batch_run(h)
+            if timing:
+                tm = g.gamma_get_timings(h)
+                assert tm["shell_ms"] > 0 and tm["tail_ms"] > 0 and tm["prepare_ms"] > 0
+                assert tm["total_ms"] >= tm["shell_ms"] + tm["tail_ms"]
+            maps = [o.cpu().numpy().astype(np.float64) for o in outs]
+            for got, want in zip(maps, base[0][0]):
+                np.testing.assert_array_equal(got, want)
+    finally:
+        g.gamma_destroy(h)
