@@ -470,34 +470,55 @@ __global__ void __launch_bounds__(256, MINB)
         z0 = (lt / ntx / nty) * T::TZ;
     };
     bool gate_failed = false;                 // lane 0: a slab wait gave up
-    // lane 0: the TMA copy of tile t into buffer b (tiles without a map are
-    // loaded when they are processed)
+    // the copy of tile t's box into buffer b, by the whole warp: one TMA copy
+    // issued by lane 0, or, for a grid without a TMA map (its rows are not
+    // 16-byte aligned), 4-byte asynchronous copies by every lane; either way
+    // the box of the next tile is in flight while this one is computed.  One
+    // cp.async group per call (empty for TMA tiles), so that the group of
+    // the tile to compute is the second most recent one.  (Slab gates come
+    // only with a TMA map.)
     auto issue = [&](int t, int b) {
-        if (t >= ntiles) return;
-        int pr, lt;
-        locate(t, pr, lt);
-        if (!(BATCH ? bd->use_tma[pr] : use_tma0)) return;
-        const Problem& Q = BATCH ? bd->probs[pr] : P0;
-        const CUtensorMap* map = BATCH ? &bd->maps[pr] : &tmap0;
-        int x0, y0, z0;
-        origin(Q.nx, Q.ny, lt, x0, y0, z0);
-        if (!BATCH && gate.flag && !gate_failed) {
-            // the box reads slices z0 - 1 .. z0 + TZ, from at most two slabs
-            const int zlo = max(z0 - 1, 0), zhi = min(z0 + T::TZ, Q.nz - 1);
-            if (!flag_wait_bounded(gate.flag + zlo / gate.depth, gate.epoch) ||
-                !flag_wait_bounded(gate.flag + zhi / gate.depth, gate.epoch)) {
-                atomicOr(&Q.ctr->flags, kFlagTimeout);     // the run reports a timeout
-                gate_failed = true;                        // and this warp waits no more
+        if (t < ntiles) {
+            int pr, lt;
+            locate(t, pr, lt);
+            const Problem& Q = BATCH ? bd->probs[pr] : P0;
+            int x0, y0, z0;
+            origin(Q.nx, Q.ny, lt, x0, y0, z0);
+            if (BATCH ? bd->use_tma[pr] : use_tma0) {
+                if (lane == 0) {
+                    const CUtensorMap* map = BATCH ? &bd->maps[pr] : &tmap0;
+                    if (!BATCH && gate.flag && !gate_failed) {
+                        // the box reads slices z0 - 1 .. z0 + TZ, from at most two slabs
+                        const int zlo = max(z0 - 1, 0), zhi = min(z0 + T::TZ, Q.nz - 1);
+                        if (!flag_wait_bounded(gate.flag + zlo / gate.depth, gate.epoch) ||
+                            !flag_wait_bounded(gate.flag + zhi / gate.depth, gate.epoch)) {
+                            atomicOr(&Q.ctr->flags, kFlagTimeout);     // the run reports a timeout
+                            gate_failed = true;                        // and this warp waits no more
+                        }
+                        fence_async_global();
+                    }
+                    mbar_arrive_expect_tx(&bar[w][b], T::ELEMS * (uint32_t)sizeof(float));
+                    if (N == 3) tma_load_3d(tiles[w][b], map, x0 - 4, y0 - 1, z0 - 1, &bar[w][b]);
+                    else tma_load_2d(tiles[w][b], map, x0 - 4, y0 - 1, &bar[w][b]);
+                }
+            } else {
+                const int nx = Q.nx, ny = Q.ny, nz = Q.nz;
+                const float* ev = Q.ev;
+                float* dst = tiles[w][b];
+                for (int i = lane; i < T::ELEMS; i += 32) {
+                    const int bx = i % T::BX, by = (i / T::BX) % T::BY, bz = i / (T::BX * T::BY);
+                    const int gx = x0 - 4 + bx, gy = y0 - 1 + by, gz = (N == 3 ? z0 - 1 : 0) + bz;
+                    const bool in = (unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny &&
+                                    (N == 2 || (unsigned)gz < (unsigned)nz);
+                    cp_async_f32(dst + i, ev + (in ? ((long long)gz * ny + gy) * nx + gx : 0), in);
+                }
             }
-            fence_async_global();
         }
-        mbar_arrive_expect_tx(&bar[w][b], T::ELEMS * (uint32_t)sizeof(float));
-        if (N == 3) tma_load_3d(tiles[w][b], map, x0 - 4, y0 - 1, z0 - 1, &bar[w][b]);
-        else tma_load_2d(tiles[w][b], map, x0 - 4, y0 - 1, &bar[w][b]);
+        cp_async_commit();
     };
     const int nwarps = (int)gridDim.x * 8;
     int t = t_first + (int)blockIdx.x * 8 + w;     // the first tile of every warp, then the counter
-    if (lane == 0) issue(t, 0);
+    issue(t, 0);
 
     unsigned my_eval = 0, my_pass = 0;
     float my_rmax = 0.f;
@@ -573,11 +594,9 @@ __global__ void __launch_bounds__(256, MINB)
 
     while (t < ntiles) {
         int nt = 0;
-        if (lane == 0) {
-            nt = t_first + nwarps + (int)atomicAdd(tile_next, 1u);
-            issue(nt, b ^ 1);
-        }
+        if (lane == 0) nt = t_first + nwarps + (int)atomicAdd(tile_next, 1u);
         nt = __shfl_sync(kFull, nt, 0);
+        issue(nt, b ^ 1);
         int pr, lt;
         locate(t, pr, lt);
         if constexpr (BATCH) {
@@ -616,14 +635,7 @@ __global__ void __launch_bounds__(256, MINB)
             }
             parity ^= 1u << b;
         } else {
-            // no TMA map for this grid: the warp loads the box itself
-            for (int i = lane; i < T::ELEMS; i += 32) {
-                const int bx = i % T::BX, by = (i / T::BX) % T::BY, bz = i / (T::BX * T::BY);
-                const int gx = x0 - 4 + bx, gy = y0 - 1 + by, gz = (N == 3 ? z0 - 1 : 0) + bz;
-                const bool in = (unsigned)gx < (unsigned)P.nx && (unsigned)gy < (unsigned)P.ny &&
-                                (N == 2 || (unsigned)gz < (unsigned)P.nz);
-                tl[i] = in ? __ldg(P.ev + ((long long)gz * P.ny + gy) * P.nx + gx) : 0.f;
-            }
+            cp_async_wait<1>();                // this tile's copies (the next tile's may be in flight)
             __syncwarp();
         }
 #pragma unroll 1
@@ -690,6 +702,7 @@ __global__ void __launch_bounds__(256, MINB)
         t = nt;
         b ^= 1;
     }
+    cp_async_wait<0>();                        // no copy into this block's memory outlives it
     if (timed_out) {
         if (lane == 0) {
             if constexpr (BATCH) atomicOr(&bd->probs[cur < 0 ? 0 : cur].ctr->flags, kFlagTimeout);

@@ -88,6 +88,28 @@ __device__ __forceinline__ void fence_async_shared()
 
 // 2D / 3D tiled TMA loads into shared memory, completing on `bar`.  The
 // innermost coordinate x must be a multiple of 4 (16 bytes of float32).
+// One float from global to shared memory by an asynchronous copy (cp.async,
+// 4 bytes, no alignment rule); in == false reads nothing and writes 0.
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src, bool in)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(in ? 4 : 0)
+                 : "memory");
+}
+
+// Close the thread's current group of cp.async copies.
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Wait until at most N of the thread's committed cp.async groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar)
 {
