@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-# BASELINE's headline metric; `value` is the plain search on the clinical-size
-# pair, and the line's vs_plain object holds the learned + batched comparison
+# The headline metric; `value` is the plain search on the clinical-size pair,
+# and the line's vs_plain object holds the learned + batched comparison
 METRIC = "3D gamma voxels/s at 3%/3mm: learned+batched vs plain, same GB300, |\u0394\u03b3|\u22641e-4"
 UNIT = "voxels/s"
 WORKLOAD = "imrt_160"
