@@ -66,7 +66,8 @@ WALKERS = {-1: ("k_tail_cq", 5), 3: ("k_tail_cq", 5), 0: ("k_tail", 4), 1: ("k_w
 LOAD_S = 1.5                 # back-to-back maps before the timed steps (clock samples)
 # gamma within this distance of 1 may pass on one side and fail on the other
 TIE_BAND = 1e-4
-# proposal network trained by the committed training command
+# proposal network made by `python -m paper_1012_1900_gb300.train --pairs 200
+# --steps 3000 --out paper_1012_1900_gb300/proposal_2pct2mm.gmlp`
 MODEL_PATH = os.path.join(ROOT, "paper_1012_1900_gb300", "proposal_2pct2mm.gmlp")
 VS_PLAIN_TEST_PAIRS = 4      # held-out 200x200x150 pairs timed plain against learned
 VS_PLAIN_GATES = (15, 17, 19)  # further cost gates timed on them (the library default is 13)
