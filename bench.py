@@ -930,6 +930,46 @@ def _timed_runs(g, h, out, reps=5):
     return statistics.median(ts)
 
 
+def proposal_quality(g, m, p, ref, ev, crit, gmap, n=20000, seed=5):
+    """How good the network's proposals are, on a sample of the voxels the
+    search queues past the key-0 cells (gamma above the first cell key): the
+    share whose nearest surface point (the exact search's label) lies in the
+    2^3 cells the seed evaluates (lower corners floor(offset) + {0, 1}^3 in
+    voxel units), and the median error of the proposed log(gamma + 1e-3)."""
+    import torch
+    flat = gmap.ravel()
+    k1 = min(p.spacing) / p.criteria.dta_mm
+    far = np.nonzero(np.isfinite(flat) & (flat > k1))[0]
+    if far.size == 0:
+        return {"sample": 0, "in_seed_cells": 0.0, "log_gamma_abs_err_median": 0.0}
+    vox = np.sort(np.random.default_rng(seed).choice(far, min(n, far.size), replace=False)).astype(np.int32)
+    h = g.gamma_create(ref, ev, 3, p.ref.shape, p.spacing, crit)
+    try:
+        out = torch.empty_like(ref)
+        g.gamma_run(h, out)
+        g.gamma_pass_rate(h)
+        vt = torch.from_numpy(vox).cuda()
+        X = torch.empty((vox.size, 384), dtype=torch.bfloat16, device="cuda")
+        T = torch.empty((vox.size, 4), dtype=torch.float32, device="cuda")
+        Y = torch.empty((vox.size, 4), dtype=torch.float32, device="cuda")
+        g.gamma_features(h, vt, X)
+        g.gamma_labels(h, out, vt, T)
+        g.gamma_model_infer(m, X, Y)
+        torch.cuda.synchronize()
+    finally:
+        g.gamma_destroy(h)
+    T, Y = T.cpu().numpy().astype(np.float64), Y.cpu().numpy().astype(np.float64)
+    keep = np.isfinite(T).all(axis=1)
+    T, Y = T[keep], Y[keep]
+    # offsets in DTA units -> voxel units, x y z order as the network's outputs
+    hn = np.array([p.spacing[2], p.spacing[1], p.spacing[0]]) / p.criteria.dta_mm
+    o = np.floor(np.clip(Y[:, :3] / hn, -256.0, 256.0))
+    foot = T[:, :3] / hn
+    inside = np.all((foot >= o - 1e-6) & (foot <= o + 2.0 + 1e-6), axis=1)
+    return {"sample": int(keep.sum()), "in_seed_cells": float(inside.mean()) if keep.any() else 0.0,
+            "log_gamma_abs_err_median": float(np.median(np.abs(Y[:, 3] - T[:, 3]))) if keep.any() else 0.0}
+
+
 def experiment_learned(args):
     """Train the proposal network on the learned-config recipe and compare
     seeded against plain runs on held-out pairs (exactness, cells, time)."""
@@ -986,7 +1026,8 @@ def experiment_learned(args):
         sp = res["plain"][2]
         tv = max(1, sp["tail_voxels"])
         row = {"pair": p.name, "voxels": p.nvox, "evaluated": int(ok.sum()),
-               "tail_voxels": sp["tail_voxels"], "ms_plain": res["plain"][1]}
+               "tail_voxels": sp["tail_voxels"], "ms_plain": res["plain"][1],
+               "proposals": proposal_quality(g, m, p, ref, ev, crit, a)}
         for b_ in SEED_GATES:
             b, _, sl = res[f"learned{b_}"]
             row[f"gate{b_}"] = {
@@ -1002,6 +1043,14 @@ def experiment_learned(args):
     pool.close()
     tot_p = sum(r["ms_plain"] for r in rows)
     vox = sum(r["voxels"] for r in rows)
+    nprop = sum(r["proposals"]["sample"] for r in rows)
+    proposals = {
+        "sample": nprop,
+        "in_seed_cells": sum(r["proposals"]["in_seed_cells"] * r["proposals"]["sample"] for r in rows) / max(1, nprop),
+        "log_gamma_abs_err_median": float(np.median([r["proposals"]["log_gamma_abs_err_median"] for r in rows])),
+        "note": "queued voxels (gamma above the first cell key), sampled per pair: the share whose nearest "
+                "point lies in the 2^3 cells the seed evaluates around the proposal, and the network's "
+                "error in log(gamma + 1e-3)"}
     gates = {}
     for b_ in SEED_GATES:
         k = f"gate{b_}"
@@ -1024,6 +1073,7 @@ def experiment_learned(args):
         "first_loss": float(np.mean(losses[:10])) if losses else None,
         "train_seconds": t_train,
         "plain_voxels_per_s": vox / (tot_p / 1000.0),
+        "proposals": proposals,
         "gates": gates,
         "pairs": rows,
     }
