@@ -1037,6 +1037,7 @@ def experiment_learned(args):
                 "cells_keyed_per_tail_voxel": [sp["cells_keyed"] / tv, sl["cells_keyed"] / tv],
                 "cells_visited_per_tail_voxel": [sp["cells_visited"] / tv, sl["cells_visited"] / tv],
                 "cells_pruned_per_tail_voxel": [sp["cells_pruned"] / tv, sl["cells_pruned"] / tv],
+                "lane_slot_steps_per_tail_voxel": [sp["lane_slot_steps"] / tv, sl["lane_slot_steps"] / tv],
                 "seed_improved_frac": sl["seed_improved"] / max(1, sl["seeded"])}
         rows.append(row)
     g.gamma_model_destroy(m)
@@ -1064,6 +1065,7 @@ def experiment_learned(args):
             "cells_keyed_per_tail_voxel": [mean("cells_keyed_per_tail_voxel", i) for i in (0, 1)],
             "cells_visited_per_tail_voxel": [mean("cells_visited_per_tail_voxel", i) for i in (0, 1)],
             "cells_pruned_per_tail_voxel": [mean("cells_pruned_per_tail_voxel", i) for i in (0, 1)],
+            "lane_slot_steps_per_tail_voxel": [mean("lane_slot_steps_per_tail_voxel", i) for i in (0, 1)],
             "seed_improved_frac": float(np.mean([r[k]["seed_improved_frac"] for r in rows])),
         }
     summary = {

@@ -99,6 +99,8 @@ typedef struct {
     int64_t table_entries;   /* cell table length */
     double table_radius;     /* every cell with key < table_radius is in the table */
     uint32_t flags;          /* internal flags (non-finite input, queue overflow) */
+    int64_t lane_slot_steps; /* stats mode, default walk: 32 x the warps' loop steps of the
+                                queue walk, idle lanes included (0 for the other walks) */
 } gamma_stats;
 
 /* Per-phase device times of the last run, in ms, measured with CUDA events

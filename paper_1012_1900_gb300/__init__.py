@@ -45,7 +45,8 @@ class gamma_stats(ctypes.Structure):
                 ("cells_keyed", ctypes.c_int64), ("cells_visited", ctypes.c_int64),
                 ("cells_pruned", ctypes.c_int64), ("d_norm", ctypes.c_double),
                 ("r_max", ctypes.c_double), ("table_entries", ctypes.c_int64),
-                ("table_radius", ctypes.c_double), ("flags", ctypes.c_uint32)]
+                ("table_radius", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("lane_slot_steps", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -626,6 +626,7 @@ Counters sum_counters(const std::vector<Counters>& cs)
         t.cells_visited += c.cells_visited;
         t.cells_pruned += c.cells_pruned;
         t.cells_keyed += c.cells_keyed;
+        t.lane_steps += c.lane_steps;
         t.flags |= c.flags;
         t.tail_count += c.tail_count;
         t.overflow_count += c.overflow_count;
@@ -1226,6 +1227,7 @@ int gamma_get_stats(gamma_handle h, gamma_stats* out)
     out->cells_keyed = (int64_t)c.cells_keyed;
     out->cells_visited = (int64_t)c.cells_visited;
     out->cells_pruned = (int64_t)c.cells_pruned;
+    out->lane_slot_steps = (int64_t)c.lane_steps;
     out->d_norm = h->crit.dose_norm > 0 ? (double)h->crit.dose_norm : (double)gk::fdec(c.dnorm_enc);
     out->r_max = (double)gk::fdec(c.rmax_enc);
     out->table_entries = (int64_t)h->table.size();

@@ -87,6 +87,7 @@ struct Counters {
     unsigned int row_cursor[kNumBuckets];
     unsigned int head_part[4];          // warp-evaluated walk: work counters of the queue's parts
     unsigned int fix_count;             // ... voxels it leaves to the finishing pass
+    unsigned long long lane_steps;      // stats mode: lane slots of its loop steps, idle lanes included
 };
 
 // The cost bucket thresholds of a sorted table (Problem::bucket_key).

@@ -1315,7 +1315,9 @@ __global__ void __launch_bounds__(256, MINB)
     int g = cq_part_lanes(part);       // its lanes per voxel
     unsigned head = 0, count = 0;      // the ring: pending cells are [head, head + count)
     bool queue_done = false;           // warp-uniform, for the current part
+    unsigned long long steps = 0;      // loop steps of this warp (option "stats")
     for (;;) {
+        if (!BATCH && P0.stats) ++steps;
         const int gl = lane & (g - 1), ld = lane - gl;
         const bool leader = gl == 0;
         const unsigned gmask = g == 32 ? kFull : ((1u << g) - 1u) << ld;
@@ -1568,6 +1570,7 @@ __global__ void __launch_bounds__(256, MINB)
                 atomicAdd(&P.ctr->cells_visited, s0);
                 atomicAdd(&P.ctr->cells_pruned, s1);
                 atomicAdd(&P.ctr->cells_keyed, s2);
+                atomicAdd(&P.ctr->lane_steps, 32ull * steps);
             }
         }
     }

@@ -416,6 +416,11 @@ def test_stats_mode_counts_cells():
     assert st["cells_visited"] > 0 and st["cells_pruned"] > 0
     # keyed cells whose corner falls outside the grid are neither visited nor pruned
     assert st["cells_keyed"] >= st["cells_visited"] + st["cells_pruned"]
+    # the default walk's lane slots: whole warp steps, and every keyed cell takes one
+    assert st["lane_slot_steps"] > 0 and st["lane_slot_steps"] % 32 == 0
+    assert st["lane_slot_steps"] >= st["cells_keyed"]
+    _, _, st0 = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"stats": 1, "walk": 0})
+    assert st0["lane_slot_steps"] == 0 and st0["cells_keyed"] > 0
 
 
 # --------------------------------------------------------------------------
