@@ -234,11 +234,20 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  *  "group_bucket"     "walk" 3: queued voxels whose cost bucket (1 + floor(2
  *                     log2 of the cells below their starting bound)) is at
  *                     least this value walk 4 lanes each, the rest one lane
- *                     each (default 9; 32: every voxel one lane)
- *  "group8_bucket"    "walk" 3: ... and those of this bucket and above 8
- *                     lanes each (default 32: none)
- *  "group32_bucket"   "walk" 3: ... and those of this bucket and above 32
- *                     lanes, a whole warp, each (default 32: none)
+ *                     each (default 9; 32: every voxel one lane).  -1: the
+ *                     walk chooses this and the next two thresholds from the
+ *                     queue: with c(b) = 2^((2b - 1)/4) cells per voxel of
+ *                     bucket b and T = (sum of c over the queue) / (the
+ *                     walk's lanes), a voxel walks 4 lanes above s T cells,
+ *                     8 above 4 s T and 32 above 8 s T (s = group_auto_pct
+ *                     / 100, default 100).  gamma_autotune keeps whichever of
+ *                     the two runs faster.
+ *  "group8_bucket"    "walk" 3, group_bucket >= 0: ... and those of this
+ *                     bucket and above 8 lanes each (default 32: none)
+ *  "group32_bucket"   "walk" 3, group_bucket >= 0: ... and those of this
+ *                     bucket and above 32 lanes, a whole warp, each (default
+ *                     32: none)
+ *  "group_auto_pct"   the slack s of the automatic choice, in percent
  *  "lanes_per_voxel"  2, 4, 8, 16 or 32 lanes search one queued voxel together
  *                     (the voxel-by-voxel walk, "walk" 0)
  *  "table_cap"        maximum cell-table length (rebuilds the table)
@@ -334,7 +343,10 @@ int gamma_batch_get_stats(gamma_handle h, int pair, gamma_stats *out);
  * in {1, 2, 3, 4} and tail_blocks_per_sm in {1, 2, 3} ({1, 2, 3, 4} for the
  * warp-evaluated walk) (two warm-ups and `reps` timed
  * runs each, CUDA events on `cuda_stream`), keeps the fastest as the handle's
- * options and returns it (any output pointer may be NULL).  gamma_out_dev receives the
+ * options and returns it (any output pointer may be NULL).  For the
+ * warp-evaluated walk it then times the other choice of queue parts
+ * ("group_bucket" fixed or -1, chosen from the queue) at those shapes and
+ * keeps the faster.  gamma_out_dev receives the
  * gamma map of a single-pair handle (device, nz*ny*nx floats) and is ignored
  * for a batch handle.  Errors as for the runs. */
 int gamma_autotune(gamma_handle h, float *gamma_out_dev, void *cuda_stream, int reps,

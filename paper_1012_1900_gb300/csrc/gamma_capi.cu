@@ -122,6 +122,8 @@ struct gamma_ctx {
     // warp-evaluated walk: voxels left to its finishing pass (tail_cap entries)
     unsigned* fix_list = nullptr;
     int group_bucket = 9;             // ... queued voxels of this cost bucket and above walk 4 lanes each
+                                      //     (< 0: the walk chooses the parts from the queue)
+    int group_auto_pct = 100;         // ... with this slack (percent)
     int group8_bucket = 32;           // ... and of this one and above 8 lanes each (32: none)
     int group32_bucket = 32;          // ... and of this one and above 32 lanes each (32: none)
     int walk = 3;                     // 0: voxel queue walk (k_tail); 1: tile-staged (k_walk);
@@ -319,6 +321,7 @@ Problem make_problem(const gamma_ctx* h, float* out)
     P.cq_group_bucket = h->group_bucket;
     P.cq_group8_bucket = h->group8_bucket;
     P.cq_group32_bucket = h->group32_bucket;
+    P.cq_auto_scale = 0.01f * (float)h->group_auto_pct;
     if (h->walk == 1 && h->tile_mask) {
         P.tile_mask = h->tile_mask;
         P.tile_list = h->tile_list;
@@ -556,6 +559,8 @@ int batch_upload(gamma_ctx* h)
         d.group_bucket = h->walk == 3 ? h->group_bucket : 0;
         d.group8_bucket = h->walk == 3 ? h->group8_bucket : 0;
         d.group32_bucket = h->walk == 3 ? h->group32_bucket : 0;
+        d.auto_scale = 0.01f * (float)h->group_auto_pct;
+        d.walk_lanes = (unsigned)(gk::device_sm_count() * std::min(4, std::max(1, h->tail_minblocks)) * 256);
         d.part_head = G.head + 4;
         d.metric4 = G.metric4;
         d.fix_v = G.fix_v;
@@ -1313,9 +1318,15 @@ int gamma_set_option(gamma_handle h, const char* key, int64_t value)
         if (h->batch) h->batch->dirty = true;
         return GAMMA_OK;
     }
+    if (!std::strcmp(key, "group_auto_pct")) {
+        if (value < 1 || value > 100000) return GAMMA_ERR_INVALID_ARG;
+        h->group_auto_pct = (int)value;
+        if (h->batch) h->batch->dirty = true;
+        return GAMMA_OK;
+    }
     if (!std::strcmp(key, "group_bucket") || !std::strcmp(key, "group8_bucket") ||
         !std::strcmp(key, "group32_bucket")) {
-        if (value < 0 || value > gk::kNumBuckets) return GAMMA_ERR_INVALID_ARG;
+        if (value < (key[5] == '_' ? -1 : 0) || value > gk::kNumBuckets) return GAMMA_ERR_INVALID_ARG;
         (key[5] == '8' ? h->group8_bucket : key[5] == '3' ? h->group32_bucket : h->group_bucket) = (int)value;
         if (h->batch) h->batch->dirty = true;
         return GAMMA_OK;
@@ -1567,11 +1578,33 @@ int gamma_autotune(gamma_handle h, float* gamma_out_dev, void* cuda_stream, int 
                 ms /= reps;
                 if (ms < best) { best = ms; best_l = h->lanes; best_b = bl; best_t = tb; }
             }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     h->lanes = best_l;
     h->shell_minblocks = best_b;
     h->tail_minblocks = best_t;
+    // the warp-evaluated walk's queue parts: the fixed thresholds or the
+    // choice from the queue (long queues of global criteria walk faster one
+    // lane per voxel), whichever runs faster at the best shapes
+    if (rc == GAMMA_OK && !h->grids && h->walk == 3 && best < INFINITY) {
+        const int keep = h->group_bucket;
+        h->group_bucket = keep >= 0 ? -1 : 9;
+        h->sg_dirty = true;
+        if (h->batch) h->batch->dirty = true;
+        float ms = INFINITY;
+        if (!(rc = run()) && !(rc = run())) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == GAMMA_OK; ++r) rc = run();
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = GAMMA_ERR_CUDA;
+            else {
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+            }
+        }
+        if (rc == GAMMA_OK && ms < best) best = ms;
+        else h->group_bucket = keep;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     h->sg_dirty = true;
     if (h->batch) h->batch->dirty = true;
     if (rc) return rc;

@@ -184,9 +184,10 @@ struct Problem {
     // cq_group32_bucket and above walk 32 lanes each, of cq_group8_bucket and
     // above 8, of cq_group_bucket and above 4; fix_list (tail_cap entries)
     // holds the voxels whose exact result the finishing pass completes
-    int cq_group_bucket;
+    int cq_group_bucket;         // < 0: the walk chooses the three from the queue (auto_part_buckets)
     int cq_group8_bucket;
     int cq_group32_bucket;
+    float cq_auto_scale;         // ... with this slack
     unsigned* fix_list;
 };
 
@@ -218,7 +219,9 @@ struct BatchDesc {
     // 8 and 32 lanes each (the queue's parts, costliest first; all 0 keeps one
     // pair-major order), the work counters of the parts, and the voxels (with
     // their pair) left to the finishing pass
-    int group_bucket, group8_bucket, group32_bucket;
+    int group_bucket, group8_bucket, group32_bucket;   // group_bucket < 0: chosen from the queue
+    float auto_scale;              // ... with this slack, for a walk of walk_lanes lanes
+    unsigned walk_lanes;
     unsigned* part_head;           // [4]
     const float4* metric4;         // [npairs][3] per pair: hn2 x, y, z, tau; kappa 1-4;
                                    // kappa 5-7, 0

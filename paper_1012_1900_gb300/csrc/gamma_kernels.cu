@@ -746,6 +746,33 @@ __global__ void __launch_bounds__(256, MINB)
     }
 }
 
+// The queue's parts chosen from the queue itself (option group_bucket < 0):
+// a queued voxel of cost bucket b is estimated to key c(b) = 2^((2b - 1) / 4)
+// table cells (the middle of the bucket), the walk's W = sum of c over the
+// queue, spread over its L lanes, ideally takes T = W / L steps per lane.  A
+// voxel walks alone unless that takes longer than s T; it walks 4 lanes
+// above s T, 8 above 4 s T and a whole warp above 8 s T, so that no voxel's
+// own walk sets the kernel's length while the lanes stay busy.  Called by a
+// full warp, lane b holding the count of bucket b; every lane gets the
+// three thresholds.
+__device__ __forceinline__ void auto_part_buckets(unsigned count, unsigned lanes, float scale, int& b4,
+                                                  int& b8, int& b32)
+{
+    const int lane = threadIdx.x & 31;
+    const float c = lane > 0 ? exp2f((2 * lane - 1) * 0.25f) : 0.f;
+    float w = (float)count * c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(kFull, w, o);
+    const float t = scale * w / (float)max(lanes, 1u);
+    auto first_above = [&](float lim) {
+        const unsigned m = __ballot_sync(kFull, lane > 0 && c > lim);
+        return m ? __ffs(m) - 1 : kNumBuckets;
+    };
+    b4 = first_above(t);
+    b8 = first_above(4.f * t);
+    b32 = first_above(8.f * t);
+}
+
 // --------------------------------------------------------------------------
 // Queue ordering: bucket offsets (most expensive first) and scatter
 // --------------------------------------------------------------------------
@@ -859,9 +886,32 @@ __global__ void __launch_bounds__(256) k_bucket_scan_batch(const BatchDesc* __re
 {
     __shared__ unsigned tot[4];
     __shared__ unsigned sc[4][256];
+    __shared__ unsigned hsum[kNumBuckets];
+    __shared__ int sh_b[3];
     const int np = bd->npairs, tid = threadIdx.x;
-    const int b32 = bd->group32_bucket, b8 = min(bd->group8_bucket, b32),
-              b4 = min(bd->group_bucket, b8);
+    if (bd->group_bucket < 0) {
+        // parts chosen from the group's queue (auto_part_buckets over every pair's histogram)
+        if (tid < kNumBuckets) hsum[tid] = 0;
+        __syncthreads();
+        for (int i = tid; i < np * kNumBuckets; i += blockDim.x) {
+            const unsigned v = bd->probs[i / kNumBuckets].ctr->hist[i % kNumBuckets];
+            if (v) atomicAdd(&hsum[i % kNumBuckets], v);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            int a4, a8, a32;
+            auto_part_buckets(hsum[tid], bd->walk_lanes, bd->auto_scale, a4, a8, a32);
+            if (tid == 0) {
+                sh_b[0] = a4;
+                sh_b[1] = a8;
+                sh_b[2] = a32;
+            }
+        }
+        __syncthreads();
+    }
+    const bool autop = bd->group_bucket < 0;
+    const int b32 = autop ? sh_b[2] : bd->group32_bucket, b8 = min(autop ? sh_b[1] : bd->group8_bucket, b32),
+              b4 = min(autop ? sh_b[0] : bd->group_bucket, b8);
     auto part_of = [&](int b) { return b >= b32 ? 0 : (b >= b8 ? 1 : (b >= b4 ? 2 : 3)); };
     auto sums = [&](int p, unsigned (&u)[4]) {
         u[0] = u[1] = u[2] = u[3] = 0;
@@ -1281,8 +1331,9 @@ __global__ void __launch_bounds__(256, MINB)
             const Problem& P = P0;
             const unsigned total = min(P.ctr->tail_count, P.tail_cap);
             const unsigned hb = P.sort_tail ? P.ctr->hist[lane] : 0u;
-            const int b32 = P.cq_group32_bucket, b8 = min(P.cq_group8_bucket, b32),
-                      b4 = min(P.cq_group_bucket, b8);
+            int b32 = P.cq_group32_bucket, b8 = min(P.cq_group8_bucket, b32), b4 = min(P.cq_group_bucket, b8);
+            if (P.cq_group_bucket < 0)
+                auto_part_buckets(hb, gridDim.x * blockDim.x, P.cq_auto_scale, b4, b8, b32);
             unsigned h32 = lane >= b32 ? hb : 0u, h8 = lane >= b8 ? hb : 0u, h4 = lane >= b4 ? hb : 0u;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {

@@ -78,7 +78,8 @@ def test_batch_matches_oracle_and_single_runs():
                                   {"table_cap": 16}, {"group_bucket": 0}, {"group_bucket": 32},
                                   {"group8_bucket": 0}, {"group32_bucket": 0},
                                   {"group_bucket": 5, "group8_bucket": 9, "group32_bucket": 13},
-                                  {"tail_blocks_per_sm": 4}, {"tail_blocks_per_sm": 1}])
+                                  {"tail_blocks_per_sm": 4}, {"tail_blocks_per_sm": 1},
+                                  {"group_bucket": -1}, {"group_bucket": -1, "group_auto_pct": 5}])
 def test_batch_options_agree(opts):
     # the default batched walk is the warp-evaluated one (walk 3); walk 0
     # is the voxel walk with its lane counts

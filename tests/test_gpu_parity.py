@@ -408,6 +408,18 @@ def test_run_host_matches_device_run(name, mode):
         g.gamma_destroy(h)
 
 
+@pytest.mark.parametrize("pct", [5, 100, 2000])
+def test_queue_parts_chosen_from_the_queue(pct):
+    # group_bucket -1: the walk picks its 4-, 8- and 32-lane parts from the
+    # queue; only the lanes per voxel change, so the map is the default one
+    p = synth.workload("imrt_small")
+    crit = synth.Criteria(0.01, 1.0, local=True)
+    base, _, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit)
+    got, counts, _ = gpu_gamma(p.ref, p.eval, p.spacing, crit, {"group_bucket": -1, "group_auto_pct": pct})
+    np.testing.assert_array_equal(got, base)
+    assert_parity(got, oracle_gamma(p.ref, p.eval, p.spacing, crit), counts)
+
+
 def test_stats_mode_counts_cells():
     p = synth.workload("imrt_small")
     crit = synth.Criteria(0.01, 1.0, local=True)
