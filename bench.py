@@ -489,6 +489,15 @@ def _event_ms(torch, stream, fn, reps, flush=None):
     return statistics.median(ts)
 
 
+def queue_parts(g, h) -> str:
+    """The walk's queue parts a handle runs with (after its autotuner)."""
+    gb = g.gamma_get_option(h, "group_bucket")
+    if gb < 0:
+        return f"chosen from the queue (slack {g.gamma_get_option(h, 'group_auto_pct')} %)"
+    return (f"fixed: 4 lanes from bucket {gb}, 8 from {g.gamma_get_option(h, 'group8_bucket')}, "
+            f"32 from {g.gamma_get_option(h, 'group32_bucket')}")
+
+
 def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
     """The learned + batched form against the plain search on one GPU, each map
     kept equal to the plain one: the 64 uneven batch pairs run one by one
@@ -538,6 +547,7 @@ def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
             # the learned + batched runs too
             batch_tuned = g.gamma_autotune(hb, stream=stream, reps=2)
             batch_tuned.pop("ms", None)
+            batch_parts = queue_parts(g, hb)
             for _ in range(3):
                 g.gamma_batch_run(hb, stream)
             batched_ms = _event_ms(torch, stream, lambda: g.gamma_batch_run(hb, stream), reps)
@@ -566,6 +576,7 @@ def measure_vs_plain(args, g, torch, dev, stream, launch, flush):
                                 "max_abs_diff_vs_plain": diff_l, "seeded": seeded,
                                 "queued": queued},
             "launch_shapes": {"plain": launch, "batched": batch_tuned},
+            "queue_parts": {"plain": "fixed (the default)", "batched": batch_parts},
             "speedup_batched_vs_plain": plain_ms / batched_ms,
             "speedup_learned_batched_vs_plain": plain_ms / learned_ms,
             "speedup_learned_batched_vs_batched": batched_ms / learned_ms}
@@ -664,6 +675,7 @@ def run_ours(args, pair, rank, world, local_rank):
         tuned = g.gamma_autotune(h, out, stream, reps=3)   # setup, not timed
         tuned.pop("ms")
         launch = dict(tuned)
+        tuned["queue_parts"] = queue_parts(g, h)
 
     def barrier():
         if world > 1:

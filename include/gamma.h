@@ -291,6 +291,13 @@ int gamma_get_timings(gamma_handle h, gamma_timings *out);
  * Errors: INVALID_ARG (unknown key or value), TABLE_TOO_LARGE, OOM. */
 int gamma_set_option(gamma_handle h, const char *key, int64_t value);
 
+/* Current value of a launch option (the ones gamma_autotune chooses and the
+ * walk's queue parts): "lanes_per_voxel", "shell_blocks_per_sm",
+ * "tail_blocks_per_sm", "walk", "group_bucket", "group8_bucket",
+ * "group32_bucket", "group_auto_pct".  No counterpart in the paper.
+ * Errors: INVALID_ARG (null pointer or unknown key). */
+int gamma_get_option(gamma_handle h, const char *key, int64_t *value);
+
 /* Release the handle and everything it owns (synchronises its last stream).
  * NULL is allowed. */
 void gamma_destroy(gamma_handle h);

@@ -101,6 +101,7 @@ def _load():
     lib.gamma_get_stats.argtypes = [vp, ctypes.POINTER(gamma_stats)]
     lib.gamma_get_timings.argtypes = [vp, ctypes.POINTER(gamma_timings)]
     lib.gamma_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_int64]
+    lib.gamma_get_option.argtypes = [vp, ctypes.c_char_p, i64p]
     lib.gamma_run_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, i64p, f32p,
                                       ctypes.POINTER(gamma_criteria), vp, i64p, i64p]
     lib.gamma_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int,
@@ -261,6 +262,12 @@ def gamma_get_timings(h: int) -> dict:
 
 def gamma_set_option(h: int, key: str, value: int) -> None:
     _check(_lib.gamma_set_option(h, key.encode(), int(value)), f"gamma_set_option({key})")
+
+
+def gamma_get_option(h: int, key: str) -> int:
+    v = ctypes.c_int64()
+    _check(_lib.gamma_get_option(h, key.encode(), ctypes.byref(v)), f"gamma_get_option({key})")
+    return v.value
 
 
 def gamma_run_noalloc(ref_dev, eval_dev, gamma_out_dev, ndim: int, shape: Sequence[int],

@@ -1269,6 +1269,22 @@ int gamma_get_timings(gamma_handle h, gamma_timings* out)
     return GAMMA_OK;
 }
 
+int gamma_get_option(gamma_handle h, const char* key, int64_t* value)
+{
+    if (!h || !key || !value) return GAMMA_ERR_INVALID_ARG;
+    const struct { const char* k; int v; } opts[] = {
+        {"lanes_per_voxel", h->lanes}, {"shell_blocks_per_sm", h->shell_minblocks},
+        {"tail_blocks_per_sm", h->tail_minblocks}, {"walk", h->walk}, {"group_bucket", h->group_bucket},
+        {"group8_bucket", h->group8_bucket}, {"group32_bucket", h->group32_bucket},
+        {"group_auto_pct", h->group_auto_pct}};
+    for (const auto& o : opts)
+        if (!std::strcmp(key, o.k)) {
+            *value = o.v;
+            return GAMMA_OK;
+        }
+    return GAMMA_ERR_INVALID_ARG;
+}
+
 int gamma_set_option(gamma_handle h, const char* key, int64_t value)
 {
     if (!h || !key) return GAMMA_ERR_INVALID_ARG;

@@ -114,6 +114,14 @@ def test_autotune_single_and_batch():
         t = g.gamma_autotune(h, o, reps=2)
         assert t["lanes_per_voxel"] in (2, 4, 8, 16, 32) and t["shell_blocks_per_sm"] in (1, 2, 3, 4)
         assert t["tail_blocks_per_sm"] in (1, 2, 3, 4) and t["ms"] > 0
+        for k in ("shell_blocks_per_sm", "tail_blocks_per_sm"):
+            assert g.gamma_get_option(h, k) == t[k]
+        # the queue parts it kept: the fixed thresholds or the choice from the queue
+        assert g.gamma_get_option(h, "group_bucket") in (9, -1)
+        g.gamma_set_option(h, "group_auto_pct", 250)
+        assert g.gamma_get_option(h, "group_auto_pct") == 250
+        with pytest.raises(g.GammaError):
+            g.gamma_get_option(h, "no_such_option")
         g.gamma_run(h, o)
         g.gamma_pass_rate(h)
     finally:
