@@ -98,6 +98,8 @@ def test_more_argument_validation_without_gpu(lib):
     INVALID = -1
     assert lib.gamma_measure_fp32_peak(None, None, None) == INVALID
     assert lib.gamma_set_option(None, b"pipeline", 1) == INVALID
+    v = ctypes.c_int64()
+    assert lib.gamma_get_option(None, b"walk", ctypes.byref(v)) == INVALID
     assert lib.gamma_run_host(None, None, None, None, None) == INVALID
     assert lib.gamma_run(None, None, None) == INVALID
     assert lib.gamma_pass_rate(None, None, None, None) == INVALID
